@@ -1,0 +1,12 @@
+"""Seeded synthetic inputs for the multilayer quasi-periodic scattering solver.
+
+This package only *describes* problems (interface shapes, layer wavenumbers,
+incidence angles and discretisation sizes).  It holds none of the method's
+arithmetic: both the CPU oracle (``oracle/``) and the CUDA path read the same
+problem descriptions from here.
+"""
+from .problems import (Interface, Params, Problem, config1, config2, config4,
+                       config5, flat_stack, small_stack, wood_angle, CONFIGS)
+
+__all__ = ["Interface", "Params", "Problem", "config1", "config2", "config4",
+           "config5", "flat_stack", "small_stack", "wood_angle", "CONFIGS"]
