@@ -1,0 +1,191 @@
+/*
+ * mlqp.h -- C ABI of the GB300 (sm_103a) solver for 2D multilayer
+ * quasi-periodic scattering by the periodizing integral-equation scheme of
+ * Cho & Barnett, "Robust fast direct integral equation solver for
+ * quasi-periodic scattering problems with a large number of layers"
+ * (arXiv 1410.5003).
+ *
+ * Problem (Sec. 1, eqs. ui, al, layer_helmholtz, interface_cond1/2, QP, RB1,
+ * RB3): I interfaces Gamma_1..Gamma_I, each one period x in [-d/2, d/2) of a
+ * d-periodic graph, separate I+1 layers with wavenumbers k_1..k_{I+1}
+ * (layer i lies above Gamma_i).  A plane wave exp(i k_1 (cos th x + sin th y)),
+ * -pi < th < 0, is incident from layer 1.  The solver returns, per angle, the
+ * interface densities eta = [tau_1; sigma_1; ...; tau_I; sigma_I] (Sec. 2.5,
+ * eq. Nden) and the Bragg amplitudes a^U_n, a^D_n, n = -K..K, of
+ *    u_1     = sum_n a^U_n exp(i kappa_n x) exp( i k^U_n (y - y_U)),  y >= y_U
+ *    u_{I+1} = sum_n a^D_n exp(i kappa_n x) exp( i k^D_n (y_D - y)),  y <= y_D
+ * (eqs. RB1, RB3), stored at index n + K, plus the flux error of Remark
+ * r:flux (NaN when some k_i is not real).
+ *
+ * The device path (Secs. 2.5-3.3): node generation, Nystrom fill of the
+ * near-field blocks A, proxy / wall / radiation blocks B, C, Q, Z, V, W,
+ * per-layer least-squares Schur complements, block-tridiagonal LU sweep,
+ * amplitude recovery and flux -- all in CUDA kernels on the bound stream.
+ *
+ * Ownership: every pointer passed to mlqp_setup is read during the call
+ * and may be freed afterwards.  The caller owns the device workspace given to
+ * mlqp_bind (the library never allocates device memory) and every output
+ * buffer.  No C++ exception crosses this interface; a context is not
+ * thread-safe and uses one CUDA stream.
+ */
+#ifndef MLQP_H
+#define MLQP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MLQP_OK = 0,
+  MLQP_EINVAL = 1,     /* invalid argument (message in mlqp_last_error) */
+  MLQP_ENOMEM = 2,     /* host allocation failed or workspace too small */
+  MLQP_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+  MLQP_ESINGULAR = 4,  /* a block-LU pivot was zero or not finite */
+  MLQP_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+  MLQP_ENOTCONV = 6,   /* iterative refinement missed its tolerance */
+  MLQP_ESTATE = 7      /* call out of order (e.g. solve before bind) */
+} mlqp_status;
+
+enum { MLQP_FP64 = 0, MLQP_MIXED = 1 };
+
+typedef struct mlqp_ctx mlqp_ctx;
+
+/* One interface: y(x) = y0 + sum_{m=1}^{n_modes} a[m-1] cos(2 pi m x/d)
+ *                                         + b[m-1] sin(2 pi m x/d),
+ * discretised by the periodic trapezoid rule with n_nodes (even) nodes
+ * s_j = 2 pi (j - 1/2)/N (Sec. 2.5, eq. Giquad). */
+typedef struct {
+  double y0;
+  int n_modes;
+  const double* a;
+  const double* b;
+  int n_nodes;
+} mlqp_interface;
+
+/* Discretisation parameters (Sec. 2.5): P proxies on a circle of radius R
+ * per layer (eq. phi); Mw Gauss-Legendre nodes per wall (eq. Qi); M
+ * trapezoid nodes on U and D; Rayleigh-Bloch orders -K..K (eq. WUD).
+ * U lies gap_U above the bound y0_1 + sum |(a_m, b_m)| of Gamma_1, D gap_D
+ * below the matching bound of Gamma_I.  The self-interaction log-split uses a
+ * smooth window equal to 1 for |s - t| <= cut_a and 0 for |s - t| >= cut_b
+ * (0 <= cut_a < cut_b <= pi).  The per-layer least squares keep the pivots
+ * |R_kk| > lsq_rcond |R_11| (Sec. 3.2).  precision: MLQP_FP64 (every step
+ * in FP64) or MLQP_MIXED (FP32 Schur / block LU, FP64 refinement of the
+ * block-tridiagonal system up to max_refine steps to refine_tol). */
+typedef struct {
+  int P;
+  double R;
+  int Mw;
+  int M;
+  int K;
+  double gap_U;
+  double gap_D;
+  double cut_a;
+  double cut_b;
+  double lsq_rcond;
+  int precision;
+  int max_refine;
+  double refine_tol;
+} mlqp_params;
+
+/* Validates the problem and records it on the host (no device work).
+ * k: 2(I+1) doubles (Re k_1, Im k_1, ..., Re k_{I+1}, Im k_{I+1}); k_1 real,
+ * every Im k_i >= 0, Re k_i > 0.  theta: n_theta angles in (-pi, 0).
+ * Errors: MLQP_EINVAL (bad sizes, odd or too small n_nodes, theta out of
+ * range, M < 2K+1, ...), MLQP_ENOMEM.  *out receives a context in both
+ * cases (NULL only if even that allocation failed): after an error it only
+ * carries the message for mlqp_last_error and must be destroyed. */
+mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k,
+                       double d, const double* theta, int n_theta,
+                       const mlqp_params* p, mlqp_ctx** out);
+
+/* n_den = 2 sum_i N_i (eq. Nden) and n_modes = 2K+1. */
+mlqp_status mlqp_sizes(const mlqp_ctx* ctx, long* n_den, int* n_modes);
+
+/* Bytes of device workspace the context needs (all blocks of every angle). */
+size_t mlqp_workspace_bytes(const mlqp_ctx* ctx);
+
+/* Attaches a caller-owned device buffer (256-byte aligned, >= the size above)
+ * and a CUDA stream (a cudaStream_t; NULL = legacy default stream), and
+ * uploads the problem description (H2D, on that stream, from a pinned host
+ * buffer the context keeps until mlqp_destroy; mlqp_upload_bytes bytes).
+ * May be called again to re-bind or to re-upload.
+ * Errors: MLQP_ENOMEM (buffer too small), MLQP_EINVAL (misaligned),
+ * MLQP_ECUDA. */
+mlqp_status mlqp_bind(mlqp_ctx* ctx, void* dev_workspace, size_t bytes, void* stream);
+
+/* Runs the whole device path for all angles, asynchronously on the bound
+ * stream, writing device buffers: d_eta (n_theta x n_den complex128,
+ * interleaved re/im, may be NULL), d_aU and d_aD (n_theta x (2K+1)
+ * complex128), d_flux (n_theta doubles, may be NULL).  Returns after the
+ * launches; errors detected on the device (MLQP_ESINGULAR) are reported by
+ * mlqp_check_device. */
+mlqp_status mlqp_solve_device(mlqp_ctx* ctx, void* d_eta, void* d_aU, void* d_aD, void* d_flux);
+
+/* Synchronises the bound stream and returns the device-side status word. */
+mlqp_status mlqp_check_device(mlqp_ctx* ctx);
+
+/* Host-buffer variant: runs mlqp_solve_device into workspace-resident
+ * outputs, copies them to the host buffers (same layouts, any may be NULL
+ * except aU and aD) and synchronises. */
+mlqp_status mlqp_solve(mlqp_ctx* ctx, double* eta, double* aU, double* aD, double* flux);
+
+/* Stages of the device path, for tests and profiling: each runs on the
+ * bound stream after the previous ones.
+ *   MLQP_STAGE_GEOM   nodes, weights, normals, Kress tables, walls, proxies,
+ *                     Bloch data (Sec. 1, Sec. 2.5)
+ *   MLQP_STAGE_FILL   A (eq. Ablocks), B (eq. Bblocks), Q', C' (eqs. Cii,
+ *                     Qiop, VUD, WUD, linsys), right-hand side
+ *   MLQP_STAGE_LSQ    X_j = Q'_j \ C'_j (Sec. 3.2)
+ *   MLQP_STAGE_SCHUR  A' = A - B X (eqs. Schur1-Schuri)
+ *   MLQP_STAGE_SWEEP  block-tridiagonal forward and backward sweeps (Sec. 3.3)
+ *   MLQP_STAGE_RECOVER amplitudes and flux error (Sec. 3.3, Remark r:flux) */
+enum { MLQP_STAGE_GEOM = 0, MLQP_STAGE_FILL = 1, MLQP_STAGE_LSQ = 2,
+       MLQP_STAGE_SCHUR = 3, MLQP_STAGE_SWEEP = 4, MLQP_STAGE_RECOVER = 5 };
+mlqp_status mlqp_run_stage(mlqp_ctx* ctx, int stage);
+
+/* Location of a workspace block (for inspection by tests):
+ *   MLQP_BLK_ROW    interface i (1..I), angle a: the block row
+ *                   [A_{i,i-1} | A_{i,i} | A_{i,i+1}] (A' after the Schur
+ *                   stage), n_i x (n_{i-1} + n_i + n_{i+1}), column-major
+ *   MLQP_BLK_B      interface i: [B_{i,i} | B_{i,i+1}], n_i x 2P
+ *   MLQP_BLK_QP     layer j (1..I+1), angle a: Q'_j (before the LSQ stage)
+ *   MLQP_BLK_CP     layer j, angle a: C'_j (before the LSQ stage)
+ *   MLQP_BLK_X      layer j, angle a: X_j = Q'_j \ C'_j
+ *   MLQP_BLK_RHS    interface i, angle a: f_i (f~_i after the sweep)
+ *   MLQP_BLK_NODES  interface i: x, y, nx, ny, speed (5 x N_i doubles)
+ *   MLQP_BLK_ETA    interface i, angle a: eta_i after the sweep (n_i x 1)
+ *   MLQP_BLK_AMP    index 1, angle a: [a^U; a^D] after recovery (2(2K+1) x 1)
+ * Complex blocks are interleaved complex128.  Offsets are in bytes from the
+ * workspace base; ld is the leading dimension in elements. */
+enum { MLQP_BLK_ROW = 0, MLQP_BLK_B = 1, MLQP_BLK_QP = 2, MLQP_BLK_CP = 3,
+       MLQP_BLK_X = 4, MLQP_BLK_RHS = 5, MLQP_BLK_NODES = 6, MLQP_BLK_ETA = 7,
+       MLQP_BLK_AMP = 8 };
+mlqp_status mlqp_block_info(const mlqp_ctx* ctx, int kind, int index, int angle,
+                            size_t* offset_bytes, int* rows, int* cols, int* ld);
+
+/* Test hook for the special functions: for n points given as (Re k, Im k,
+ * rho) triples in device memory, writes H0^(1)(k rho), H1^(1)(k rho),
+ * J0(k rho), J1(k rho) as 8 doubles (re, im pairs) per point to d_out, on
+ * `stream`.  Same device routines as the fill kernels.  Errors: MLQP_EINVAL,
+ * MLQP_ECUDA. */
+mlqp_status mlqp_debug_hankel(const double* d_krho, int n, double* d_out, void* stream);
+
+/* Bytes of the problem description mlqp_bind copies host -> device. */
+size_t mlqp_upload_bytes(const mlqp_ctx* ctx);
+
+/* Kernel launches this context has issued so far (all stages, all solves). */
+long mlqp_launch_count(const mlqp_ctx* ctx);
+
+/* Message of the last error on this context ("" if none). */
+const char* mlqp_last_error(const mlqp_ctx* ctx);
+
+/* Frees the host-side context (never the caller's workspace). */
+void mlqp_destroy(mlqp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLQP_H */

@@ -34,10 +34,13 @@ Readings of the paper that this oracle fixes (each is listed in the design doc):
   * Flux error uses the incident vertical flux k_1 |sin theta|.
   * Forward sweep f~_i = f_i - A'_{i,i-1} A~_{i-1}^{-1} f~_{i-1}.
   * C'_{I+1,I} = [C_{I+1,I}; Z_D];  C entries use targets x_m + 2d and x_m - d.
-  * "Backslash" is column-pivoted Householder QR with the basic solution
-    and numerical rank #{|R_kk| > rcond |R_11|}, rcond = 1e-10 by default
-    (MATLAB's max(m,n) eps tolerance keeps directions that only carry
-    rounding noise into A').
+  * "Backslash" (a backward-stable dense least-squares solve) is the
+    regularised least squares min ||Q X - C||^2 + lam^2 ||X||^2 with
+    lam = rcond * (largest column norm of Q), rcond = 1e-10, by Householder
+    QR of [Q; lam I].  The truncated pivoted-QR basic solution (MATLAB's
+    rectangular backslash) gives the same amplitudes to discretisation
+    accuracy but jumps with rounding-level changes of Q (pivot and rank
+    flips); the regularised solution is smooth in the data.
   * U/D nodes x_m = -d/2 + d (m - 1/2)/M; y_U = y0_1 + sum_m |c_m| + gap_U
     (an upper bound of Gamma_1), y_D likewise below Gamma_I; the wall of
     layer j spans x = -d/2 between its bounding interfaces (or U, D); proxy
@@ -528,10 +531,11 @@ def pivoted_qr(A, rcond):
     return refl, np.triu(R[:steps, :]), piv, rank
 
 
-def lsq(Q, C, rcond):
+def lsq_pivoted(Q, C, rcond):
     """X = Q \\ C: least-squares basic solution (zeros in the non-pivot
-    columns) via pivoted QR of numerical rank #{|R_kk| > rcond |R_00|};
-    never forms the pseudo-inverse (Sec. 3.2)."""
+    columns) via pivoted QR of numerical rank #{|R_kk| > rcond |R_00|}
+    (MATLAB's rectangular backslash with a relative tolerance).  Kept as a
+    cross-check of lsq(); the solver itself uses lsq()."""
     refl, R, piv, r = pivoted_qr(Q, rcond)
     B = np.array(C, dtype=np.complex128, copy=True)
     for j, (v, beta) in enumerate(refl):
@@ -541,6 +545,21 @@ def lsq(Q, C, rcond):
     if r:
         X[piv[:r]] = sla.solve_triangular(R[:r, :r], B[:r], lower=False)
     return X
+
+
+def lsq(Q, C, rcond):
+    """X_j = Q'_j \\ C'_j (Sec. 3.2) as the regularised least-squares solution
+    argmin ||Q X - C||^2 + lam^2 ||X||^2, lam = rcond * max_c ||Q[:, c]||,
+    computed by Householder QR of the stacked matrix [Q; lam I] (backward
+    stable; the pseudo-inverse is never formed).  It selects small-norm proxy
+    strengths, the property the remark after eq. Schuri relies on, and it
+    depends smoothly on Q and C, unlike a rank-truncated basic solution."""
+    m, p = Q.shape
+    lam = rcond * np.max(np.sqrt(np.sum(np.abs(Q) ** 2, axis=0)))
+    A = np.vstack([Q, lam * np.eye(p)])
+    B = np.vstack([C, np.zeros((p, C.shape[1]), np.complex128)])
+    q, r = np.linalg.qr(A)
+    return sla.solve_triangular(r, q.conj().T @ B, lower=False)
 
 
 # ----------------------------------------------------------------------------

@@ -1,0 +1,589 @@
+// Host side of the mlqp C ABI (include/mlqp.h): validation, workspace layout,
+// descriptor upload and the ordered launches of the device path.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mlqp.h"
+#include "mlqp_internal.h"
+
+namespace mlqp {
+cudaError_t launch_geometry(const Dev& D, double* scal, cudaStream_t s);
+cudaError_t launch_fill(const Dev& D, const double* scal, cudaStream_t s);
+cudaError_t launch_lsq(const Dev& D, int max_m, int max_p, int max_c, cudaStream_t s);
+cudaError_t launch_schur(const Dev& D, int max_tiles, cudaStream_t s);
+cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s);
+cudaError_t launch_recover(const Dev& D, cudaStream_t s);
+cudaError_t sweep_configure(int maxn);
+cudaError_t launch_hankel_eval(const double* kr, int n, double* out, cudaStream_t s);
+extern thread_local long g_launches;
+}  // namespace mlqp
+
+using namespace mlqp;
+
+struct Region {
+  size_t off = 0, bytes = 0;
+};
+
+struct mlqp_ctx {
+  // problem (host copies)
+  int I = 0, L = 0, n_theta = 0;
+  double d = 0;
+  mlqp_params prm{};
+  std::vector<double> k;      // 2(I+1)
+  std::vector<double> theta;  // n_theta
+  std::vector<double> coef_a, coef_b;
+  std::vector<IfaceDesc> ifc;
+  std::vector<LayerDesc> lay;
+  std::vector<SchurTask> tasks;
+  std::vector<int> n_host;
+  int maxN = 0, maxn = 0, total_nodes = 0, max_m = 0, max_p = 0, max_c = 0, max_tiles = 0;
+  long n_den = 0;
+  size_t r_stride = 0, f_stride = 0, b_total = 0, qp_stride = 0, cp_stride = 0, x_stride = 0, sum_p = 0;
+  // layout
+  Region r_ifc, r_lay, r_tasks, r_k, r_ca, r_cb, r_theta, r_scal, r_geo[7], r_wy, r_gl, r_ux, r_alpha, r_kappa,
+      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LUPIV, r_ETA, r_AMP, r_FLUX, r_STATUS;
+  size_t ws_bytes = 0;
+  // binding
+  char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  bool bound = false;
+  Dev D{};
+  char* staging = nullptr;  // pinned host copy of the descriptors and inputs
+  size_t staging_bytes = 0;
+  std::string err;
+  bool valid = false;
+  long launches = 0;  // kernel launches issued by this context
+};
+
+static mlqp_status fail(mlqp_ctx* c, mlqp_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+static mlqp_status cuda_fail(mlqp_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, MLQP_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static void take(size_t& cur, Region& r, size_t bytes) {
+  r.off = cur;
+  r.bytes = bytes;
+  cur = align256(cur + bytes);
+}
+
+template <typename T>
+static T* at(mlqp_ctx* c, const Region& r) {
+  return reinterpret_cast<T*>(c->ws + r.off);
+}
+
+extern "C" {
+
+mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, double d, const double* theta,
+                       int n_theta, const mlqp_params* p, mlqp_ctx** out) {
+  if (!out) return MLQP_EINVAL;
+  *out = nullptr;
+  mlqp_ctx* c = new (std::nothrow) mlqp_ctx();
+  if (!c) return MLQP_ENOMEM;
+  auto bad = [&](const char* msg) {
+    // keep the context so that the caller can read the message; it is not usable
+    c->err = msg;
+    *out = c;
+    return MLQP_EINVAL;
+  };
+  if (!ifaces || !k || !theta || !p) return bad("null argument");
+  if (I < 1) return bad("need at least one interface");
+  if (n_theta < 1) return bad("need at least one angle");
+  if (!(d > 0) || !std::isfinite(d)) return bad("period d must be positive");
+  c->I = I;
+  c->L = I + 1;
+  c->n_theta = n_theta;
+  c->d = d;
+  c->prm = *p;
+  const mlqp_params& q = c->prm;
+  if (q.P < 4 || q.Mw < 2 || q.M < 2 || q.K < 0) return bad("P >= 4, Mw >= 2, M >= 2, K >= 0 required");
+  if (q.M < 2 * q.K + 1) return bad("M must be at least 2K+1");
+  if (!(q.R > 0)) return bad("proxy radius R must be positive");
+  if (!(q.cut_a >= 0 && q.cut_a < q.cut_b && q.cut_b <= M_PI + 1e-15)) return bad("need 0 <= cut_a < cut_b <= pi");
+  if (!(q.lsq_rcond > 0 && q.lsq_rcond < 1)) return bad("lsq_rcond must be in (0, 1)");
+  if (!(q.gap_U > 0 && q.gap_D > 0)) return bad("gap_U and gap_D must be positive");
+  if (q.precision != MLQP_FP64) return bad("only MLQP_FP64 is available in this build");
+  c->k.assign(k, k + 2 * (I + 1));
+  for (int j = 0; j <= I; ++j) {
+    if (!(c->k[2 * j] > 0) || !(c->k[2 * j + 1] >= 0) || !std::isfinite(c->k[2 * j]) ||
+        !std::isfinite(c->k[2 * j + 1]))
+      return bad("every k_i needs Re k > 0 and Im k >= 0");
+  }
+  if (c->k[1] != 0.0) return bad("k_1 (the incident layer) must be real");
+  c->theta.assign(theta, theta + n_theta);
+  for (double t : c->theta)
+    if (!(t > -M_PI && t < 0)) return bad("incidence angles must lie in (-pi, 0)");
+  // interfaces
+  c->ifc.resize(I);
+  c->n_host.resize(I);
+  int node = 0, coef = 0;
+  for (int i = 0; i < I; ++i) {
+    const mlqp_interface& f = ifaces[i];
+    if (f.n_nodes < 8 || (f.n_nodes & 1)) return bad("n_nodes must be even and >= 8");
+    if (f.n_modes < 0 || (f.n_modes > 0 && (!f.a || !f.b))) return bad("bad Fourier coefficients");
+    if (!std::isfinite(f.y0)) return bad("y0 must be finite");
+    IfaceDesc& D = c->ifc[i];
+    D.N = f.n_nodes;
+    D.n = 2 * f.n_nodes;
+    D.node_off = node;
+    D.n_modes = f.n_modes;
+    D.coef_off = coef;
+    D.y0 = f.y0;
+    for (int m = 0; m < f.n_modes; ++m) {
+      if (!std::isfinite(f.a[m]) || !std::isfinite(f.b[m])) return bad("coefficients must be finite");
+      c->coef_a.push_back(f.a[m]);
+      c->coef_b.push_back(f.b[m]);
+    }
+    node += f.n_nodes;
+    coef += f.n_modes;
+    c->n_host[i] = D.n;
+    c->maxN = std::max(c->maxN, D.N);
+    c->maxn = std::max(c->maxn, D.n);
+  }
+  if (c->coef_a.empty()) {
+    c->coef_a.push_back(0.0);
+    c->coef_b.push_back(0.0);
+  }
+  c->total_nodes = node;
+  // ordering of the interfaces: strictly decreasing bounds
+  for (int i = 0; i + 1 < I; ++i) {
+    double s0 = 0, s1 = 0;
+    for (int m = 0; m < ifaces[i].n_modes; ++m) s0 += std::hypot(ifaces[i].a[m], ifaces[i].b[m]);
+    for (int m = 0; m < ifaces[i + 1].n_modes; ++m) s1 += std::hypot(ifaces[i + 1].a[m], ifaces[i + 1].b[m]);
+    if (!(ifaces[i].y0 - s0 > ifaces[i + 1].y0 + s1)) return bad("interfaces must be separated and ordered top to bottom");
+  }
+  // block rows, rhs, B
+  size_t roff = 0, foff = 0, boff = 0;
+  long eoff = 0;
+  for (int i = 0; i < I; ++i) {
+    IfaceDesc& D = c->ifc[i];
+    D.nl = (i > 0) ? c->ifc[i - 1].n : 0;
+    D.nr = (i + 1 < I) ? 2 * ifaces[i + 1].n_nodes : 0;
+    D.row_cols = D.nl + D.n + D.nr;
+    D.row_off = roff;
+    roff += (size_t)D.n * D.row_cols;
+    D.rhs_off = foff;
+    foff += D.n;
+    D.b_off = boff;
+    boff += (size_t)D.n * 2 * q.P;
+    D.eta_off = eoff;
+    eoff += D.n;
+  }
+  c->r_stride = roff;
+  c->f_stride = foff;
+  c->b_total = boff;
+  c->n_den = eoff;
+  // layers
+  const int nK = 2 * q.K + 1;
+  c->lay.resize(c->L);
+  size_t qo = 0, co = 0, xo = 0, ao = 0;
+  for (int j = 0; j < c->L; ++j) {
+    LayerDesc& Ly = c->lay[j];
+    Ly.end = (j == 0) ? 1 : (j == I) ? 2 : 0;
+    Ly.m = 2 * q.Mw + (Ly.end ? 2 * q.M : 0);
+    Ly.p = q.P + (Ly.end ? nK : 0);
+    Ly.if0 = (j >= 1) ? j - 1 : -1;
+    Ly.if1 = (j <= I - 1) ? j : -1;
+    Ly.c0 = 0;
+    Ly.c1 = (Ly.if0 >= 0) ? c->ifc[j - 1].n : 0;
+    Ly.c = (Ly.if0 >= 0 ? c->ifc[Ly.if0].n : 0) + (Ly.if1 >= 0 ? c->ifc[Ly.if1].n : 0);
+    Ly.ldq = Ly.m + Ly.p;
+    Ly.qp_off = qo;
+    qo += (size_t)Ly.ldq * Ly.p;
+    Ly.cp_off = co;
+    co += (size_t)Ly.ldq * Ly.c;
+    Ly.x_off = xo;
+    xo += (size_t)Ly.p * Ly.c;
+    Ly.aux_off = ao;
+    ao += Ly.p;
+    Ly.ybot = Ly.ytop = Ly.cy = 0;
+    c->max_m = std::max(c->max_m, Ly.m);
+    c->max_p = std::max(c->max_p, Ly.p);
+    c->max_c = std::max(c->max_c, Ly.c);
+  }
+  c->qp_stride = qo;
+  c->cp_stride = co;
+  c->x_stride = xo;
+  c->sum_p = ao;
+  // Schur tasks (eqs. Schur1-Schuri), see mlqp_internal.h
+  auto tiles = [](int r, int cc) { return ((r + 63) / 64) * ((cc + 63) / 64); };
+  for (int i = 0; i < I; ++i) {
+    const IfaceDesc& F = c->ifc[i];
+    const LayerDesc& La = c->lay[i];      // layer above interface i: interface i is its if1
+    const LayerDesc& Lb = c->lay[i + 1];  // layer below: interface i is its if0
+    SchurTask T{};
+    T.c_off = F.row_off + (size_t)F.nl * F.n;
+    T.ldc = F.n;
+    T.rows = F.n;
+    T.cols = F.n;
+    T.a1_off = F.b_off;
+    T.lda1 = F.n;
+    T.b1_off = La.x_off + (size_t)La.c1 * La.p;
+    T.ldb1 = La.p;
+    T.k1 = q.P;
+    T.a2_off = F.b_off + (size_t)q.P * F.n;
+    T.lda2 = F.n;
+    T.b2_off = Lb.x_off + (size_t)Lb.c0 * Lb.p;
+    T.ldb2 = Lb.p;
+    T.k2 = q.P;
+    c->tasks.push_back(T);
+    c->max_tiles = std::max(c->max_tiles, tiles(T.rows, T.cols));
+    if (i + 1 < I) {
+      SchurTask U{};
+      U.c_off = F.row_off + (size_t)(F.nl + F.n) * F.n;
+      U.ldc = F.n;
+      U.rows = F.n;
+      U.cols = F.nr;
+      U.a1_off = F.b_off + (size_t)q.P * F.n;
+      U.lda1 = F.n;
+      U.b1_off = Lb.x_off + (size_t)Lb.c1 * Lb.p;
+      U.ldb1 = Lb.p;
+      U.k1 = q.P;
+      U.k2 = 0;
+      c->tasks.push_back(U);
+      c->max_tiles = std::max(c->max_tiles, tiles(U.rows, U.cols));
+    }
+    if (i > 0) {
+      SchurTask W{};
+      W.c_off = F.row_off;
+      W.ldc = F.n;
+      W.rows = F.n;
+      W.cols = F.nl;
+      W.a1_off = F.b_off;
+      W.lda1 = F.n;
+      W.b1_off = La.x_off + (size_t)La.c0 * La.p;
+      W.ldb1 = La.p;
+      W.k1 = q.P;
+      W.k2 = 0;
+      c->tasks.push_back(W);
+      c->max_tiles = std::max(c->max_tiles, tiles(W.rows, W.cols));
+    }
+  }
+  // workspace layout
+  const size_t nt = n_theta, d8 = sizeof(double), z16 = sizeof(double2);
+  size_t cur = 0;
+  take(cur, c->r_ifc, sizeof(IfaceDesc) * I);
+  take(cur, c->r_lay, sizeof(LayerDesc) * c->L);
+  take(cur, c->r_tasks, sizeof(SchurTask) * c->tasks.size());
+  take(cur, c->r_k, d8 * c->k.size());
+  take(cur, c->r_ca, d8 * c->coef_a.size());
+  take(cur, c->r_cb, d8 * c->coef_b.size());
+  take(cur, c->r_theta, d8 * nt);
+  take(cur, c->r_scal, d8 * 4);
+  for (int g = 0; g < 7; ++g) take(cur, c->r_geo[g], d8 * c->total_nodes);
+  take(cur, c->r_wy, d8 * c->L * q.Mw);
+  take(cur, c->r_gl, d8 * q.Mw);
+  take(cur, c->r_ux, d8 * q.M);
+  take(cur, c->r_alpha, z16 * nt);
+  take(cur, c->r_kappa, d8 * nt * nK);
+  take(cur, c->r_ku, z16 * nt * nK);
+  take(cur, c->r_kd, z16 * nt * nK);
+  take(cur, c->r_R, z16 * nt * c->r_stride);
+  take(cur, c->r_F, z16 * nt * c->f_stride);
+  take(cur, c->r_B, z16 * c->b_total);
+  take(cur, c->r_QP, z16 * nt * c->qp_stride);
+  take(cur, c->r_CP, z16 * nt * c->cp_stride);
+  take(cur, c->r_X, z16 * nt * c->x_stride);
+  take(cur, c->r_LAUX, d8 * nt * 6 * c->sum_p);
+  take(cur, c->r_LUPIV, sizeof(int) * nt * c->n_den);
+  take(cur, c->r_ETA, z16 * nt * c->n_den);
+  take(cur, c->r_AMP, z16 * nt * 2 * nK);
+  take(cur, c->r_FLUX, d8 * nt);
+  take(cur, c->r_STATUS, 256);
+  c->ws_bytes = cur;
+  c->valid = true;
+  *out = c;
+  return MLQP_OK;
+}
+
+mlqp_status mlqp_sizes(const mlqp_ctx* c, long* n_den, int* n_modes) {
+  if (!c || !c->valid) return MLQP_EINVAL;
+  if (n_den) *n_den = c->n_den;
+  if (n_modes) *n_modes = 2 * c->prm.K + 1;
+  return MLQP_OK;
+}
+
+size_t mlqp_workspace_bytes(const mlqp_ctx* c) { return (c && c->valid) ? c->ws_bytes : 0; }
+
+mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->valid) return fail(c, MLQP_ESTATE, "context was not set up successfully");
+  if (!dev_ws) return fail(c, MLQP_EINVAL, "null workspace");
+  if (reinterpret_cast<uintptr_t>(dev_ws) & 255) return fail(c, MLQP_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < c->ws_bytes) return fail(c, MLQP_ENOMEM, "workspace too small: %zu < %zu bytes", bytes, c->ws_bytes);
+  c->ws = static_cast<char*>(dev_ws);
+  c->stream = static_cast<cudaStream_t>(stream);
+  Dev& D = c->D;
+  const mlqp_params& q = c->prm;
+  D.I = c->I;
+  D.L = c->L;
+  D.n_theta = c->n_theta;
+  D.P = q.P;
+  D.Mw = q.Mw;
+  D.M = q.M;
+  D.K = q.K;
+  D.nK = 2 * q.K + 1;
+  D.d = c->d;
+  D.R = q.R;
+  D.cut_a = q.cut_a;
+  D.cut_b = q.cut_b;
+  D.rcond = q.lsq_rcond;
+  D.yU = q.gap_U;  // the geometry kernel turns the gaps into y_U, y_D (stored in scal)
+  D.yD = q.gap_D;
+  D.maxN = c->maxN;
+  D.maxn = c->maxn;
+  D.total_nodes = c->total_nodes;
+  D.ifc = at<IfaceDesc>(c, c->r_ifc);
+  D.lay = at<LayerDesc>(c, c->r_lay);
+  D.kre = at<double>(c, c->r_k);
+  D.coef_a = at<double>(c, c->r_ca);
+  D.coef_b = at<double>(c, c->r_cb);
+  D.theta = at<double>(c, c->r_theta);
+  D.X = at<double>(c, c->r_geo[0]);
+  D.Y = at<double>(c, c->r_geo[1]);
+  D.NX = at<double>(c, c->r_geo[2]);
+  D.NY = at<double>(c, c->r_geo[3]);
+  D.SP = at<double>(c, c->r_geo[4]);
+  D.TABC = at<double>(c, c->r_geo[5]);
+  D.TABCHI = at<double>(c, c->r_geo[6]);
+  D.WY = at<double>(c, c->r_wy);
+  D.GL = at<double>(c, c->r_gl);
+  D.UX = at<double>(c, c->r_ux);
+  D.ALPHA = at<double2>(c, c->r_alpha);
+  D.KAPPA = at<double>(c, c->r_kappa);
+  D.KU = at<double2>(c, c->r_ku);
+  D.KD = at<double2>(c, c->r_kd);
+  D.ROW = at<double2>(c, c->r_R);
+  D.r_stride = c->r_stride;
+  D.F = at<double2>(c, c->r_F);
+  D.f_stride = c->f_stride;
+  D.B = at<double2>(c, c->r_B);
+  D.QP = at<double2>(c, c->r_QP);
+  D.qp_stride = c->qp_stride;
+  D.CP = at<double2>(c, c->r_CP);
+  D.cp_stride = c->cp_stride;
+  D.Xb = at<double2>(c, c->r_X);
+  D.x_stride = c->x_stride;
+  D.LAUX = at<double>(c, c->r_LAUX);
+  D.laux_stride = 6 * c->sum_p;
+  D.LUPIV = at<int>(c, c->r_LUPIV);
+  D.piv_stride = c->n_den;
+  D.ETA = at<double2>(c, c->r_ETA);
+  D.eta_stride = c->n_den;
+  D.AMP = at<double2>(c, c->r_AMP);
+  D.FLUX = at<double>(c, c->r_FLUX);
+  D.STATUS = at<int>(c, c->r_STATUS);
+  D.tasks = at<SchurTask>(c, c->r_tasks);
+  D.n_tasks = (int)c->tasks.size();
+  // stage the descriptors and inputs in pinned host memory, one H2D copy
+  const size_t hdr = c->r_geo[0].off;
+  if (c->staging_bytes < hdr) {
+    if (c->staging) cudaFreeHost(c->staging);
+    c->staging = nullptr;
+    c->staging_bytes = 0;
+    cudaError_t ea = cudaMallocHost(reinterpret_cast<void**>(&c->staging), hdr);
+    if (ea != cudaSuccess) return cuda_fail(c, ea, "pinned staging buffer");
+    c->staging_bytes = hdr;
+  }
+  // the previous upload from this buffer must be complete before it is rewritten
+  if (c->bound) {
+    cudaError_t es = cudaStreamSynchronize(c->stream);
+    if (es != cudaSuccess) return cuda_fail(c, es, "stream synchronize");
+  }
+  std::memset(c->staging, 0, hdr);
+  auto put = [&](const Region& r, const void* src, size_t n) { if (n) std::memcpy(c->staging + r.off, src, n); };
+  put(c->r_ifc, c->ifc.data(), sizeof(IfaceDesc) * c->ifc.size());
+  put(c->r_lay, c->lay.data(), sizeof(LayerDesc) * c->lay.size());
+  put(c->r_tasks, c->tasks.data(), sizeof(SchurTask) * c->tasks.size());
+  put(c->r_k, c->k.data(), sizeof(double) * c->k.size());
+  put(c->r_ca, c->coef_a.data(), sizeof(double) * c->coef_a.size());
+  put(c->r_cb, c->coef_b.data(), sizeof(double) * c->coef_b.size());
+  put(c->r_theta, c->theta.data(), sizeof(double) * c->theta.size());
+  cudaError_t e = cudaMemcpyAsync(c->ws, c->staging, hdr, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "descriptor upload");
+  if ((e = sweep_configure(c->maxn)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
+  c->bound = true;
+  return MLQP_OK;
+}
+
+mlqp_status mlqp_run_stage(mlqp_ctx* c, int stage) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  double* scal = at<double>(c, c->r_scal);
+  cudaError_t e = cudaSuccess;
+  g_launches = 0;
+  switch (stage) {
+    case MLQP_STAGE_GEOM:
+      e = cudaMemsetAsync(c->D.STATUS, 0, sizeof(int), c->stream);
+      if (e == cudaSuccess) e = launch_geometry(c->D, scal, c->stream);
+      break;
+    case MLQP_STAGE_FILL: e = launch_fill(c->D, scal, c->stream); break;
+    case MLQP_STAGE_LSQ: e = launch_lsq(c->D, c->max_m, c->max_p, c->max_c, c->stream); break;
+    case MLQP_STAGE_SCHUR: e = launch_schur(c->D, c->max_tiles, c->stream); break;
+    case MLQP_STAGE_SWEEP: e = launch_sweep(c->D, c->n_host.data(), c->stream); break;
+    case MLQP_STAGE_RECOVER: e = launch_recover(c->D, c->stream); break;
+    default: return fail(c, MLQP_EINVAL, "unknown stage %d", stage);
+  }
+  c->launches += g_launches;
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  return MLQP_OK;
+}
+
+mlqp_status mlqp_solve_device(mlqp_ctx* c, void* d_eta, void* d_aU, void* d_aD, void* d_flux) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  for (int s = MLQP_STAGE_GEOM; s <= MLQP_STAGE_RECOVER; ++s) {
+    mlqp_status st = mlqp_run_stage(c, s);
+    if (st != MLQP_OK) return st;
+  }
+  const int nK = 2 * c->prm.K + 1;
+  cudaError_t e = cudaSuccess;
+  if (d_eta && e == cudaSuccess)
+    e = cudaMemcpyAsync(d_eta, c->D.ETA, sizeof(double2) * c->n_den * c->n_theta, cudaMemcpyDeviceToDevice, c->stream);
+  if (d_aU && e == cudaSuccess)
+    e = cudaMemcpy2DAsync(d_aU, sizeof(double2) * nK, c->D.AMP, sizeof(double2) * 2 * nK, sizeof(double2) * nK,
+                          c->n_theta, cudaMemcpyDeviceToDevice, c->stream);
+  if (d_aD && e == cudaSuccess)
+    e = cudaMemcpy2DAsync(d_aD, sizeof(double2) * nK, c->D.AMP + nK, sizeof(double2) * 2 * nK, sizeof(double2) * nK,
+                          c->n_theta, cudaMemcpyDeviceToDevice, c->stream);
+  if (d_flux && e == cudaSuccess)
+    e = cudaMemcpyAsync(d_flux, c->D.FLUX, sizeof(double) * c->n_theta, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "output copy");
+  return MLQP_OK;
+}
+
+mlqp_status mlqp_check_device(mlqp_ctx* c) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, c->D.STATUS, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device status");
+  if (st == MLQP_ESINGULAR) return fail(c, MLQP_ESINGULAR, "block LU met a zero or non-finite pivot");
+  if (st == MLQP_ETIMEOUT) return fail(c, MLQP_ETIMEOUT, "a bounded device wait gave up");
+  if (st != 0) return fail(c, (mlqp_status)st, "device status %d", st);
+  return MLQP_OK;
+}
+
+mlqp_status mlqp_solve(mlqp_ctx* c, double* eta, double* aU, double* aD, double* flux) {
+  if (!c) return MLQP_EINVAL;
+  if (!aU || !aD) return fail(c, MLQP_EINVAL, "aU and aD are required");
+  mlqp_status st = mlqp_solve_device(c, nullptr, nullptr, nullptr, nullptr);
+  if (st != MLQP_OK) return st;
+  const int nK = 2 * c->prm.K + 1;
+  cudaError_t e = cudaSuccess;
+  if (eta) e = cudaMemcpyAsync(eta, c->D.ETA, sizeof(double2) * c->n_den * c->n_theta, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(aU, sizeof(double2) * nK, c->D.AMP, sizeof(double2) * 2 * nK, sizeof(double2) * nK,
+                          c->n_theta, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(aD, sizeof(double2) * nK, c->D.AMP + nK, sizeof(double2) * 2 * nK, sizeof(double2) * nK,
+                          c->n_theta, cudaMemcpyDeviceToHost, c->stream);
+  if (flux && e == cudaSuccess)
+    e = cudaMemcpyAsync(flux, c->D.FLUX, sizeof(double) * c->n_theta, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "result copy");
+  return mlqp_check_device(c);
+}
+
+mlqp_status mlqp_block_info(const mlqp_ctx* c, int kind, int index, int angle, size_t* offset_bytes, int* rows,
+                            int* cols, int* ld) {
+  if (!c || !c->valid || !offset_bytes || !rows || !cols || !ld) return MLQP_EINVAL;
+  if (angle < 0 || angle >= c->n_theta) return MLQP_EINVAL;
+  const size_t z = sizeof(double2);
+  const size_t a = angle;
+  if (kind == MLQP_BLK_AMP) {
+    if (index != 1) return MLQP_EINVAL;
+    *offset_bytes = c->r_AMP.off + z * a * 2 * (2 * c->prm.K + 1);
+    *rows = 2 * (2 * c->prm.K + 1); *cols = 1; *ld = *rows;
+    return MLQP_OK;
+  }
+  if (kind == MLQP_BLK_ROW || kind == MLQP_BLK_B || kind == MLQP_BLK_RHS || kind == MLQP_BLK_NODES ||
+      kind == MLQP_BLK_ETA) {
+    if (index < 1 || index > c->I) return MLQP_EINVAL;
+    const IfaceDesc& F = c->ifc[index - 1];
+    switch (kind) {
+      case MLQP_BLK_ROW:
+        *offset_bytes = c->r_R.off + z * (a * c->r_stride + F.row_off);
+        *rows = F.n; *cols = F.row_cols; *ld = F.n;
+        return MLQP_OK;
+      case MLQP_BLK_B:
+        *offset_bytes = c->r_B.off + z * F.b_off;
+        *rows = F.n; *cols = 2 * c->prm.P; *ld = F.n;
+        return MLQP_OK;
+      case MLQP_BLK_RHS:
+        *offset_bytes = c->r_F.off + z * (a * c->f_stride + F.rhs_off);
+        *rows = F.n; *cols = 1; *ld = F.n;
+        return MLQP_OK;
+      case MLQP_BLK_ETA:
+        *offset_bytes = c->r_ETA.off + z * (a * c->n_den + F.eta_off);
+        *rows = F.n; *cols = 1; *ld = F.n;
+        return MLQP_OK;
+      default:
+        *offset_bytes = c->r_geo[0].off + sizeof(double) * F.node_off;
+        *rows = F.N; *cols = 5; *ld = (int)(c->r_geo[1].off - c->r_geo[0].off) / (int)sizeof(double);
+        return MLQP_OK;
+    }
+  }
+  if (index < 1 || index > c->L) return MLQP_EINVAL;
+  const LayerDesc& Ly = c->lay[index - 1];
+  switch (kind) {
+    case MLQP_BLK_QP:
+      *offset_bytes = c->r_QP.off + z * (a * c->qp_stride + Ly.qp_off);
+      *rows = Ly.m; *cols = Ly.p; *ld = Ly.ldq;
+      return MLQP_OK;
+    case MLQP_BLK_CP:
+      *offset_bytes = c->r_CP.off + z * (a * c->cp_stride + Ly.cp_off);
+      *rows = Ly.m; *cols = Ly.c; *ld = Ly.ldq;
+      return MLQP_OK;
+    case MLQP_BLK_X:
+      *offset_bytes = c->r_X.off + z * (a * c->x_stride + Ly.x_off);
+      *rows = Ly.p; *cols = Ly.c; *ld = Ly.p;
+      return MLQP_OK;
+    default:
+      return MLQP_EINVAL;
+  }
+}
+
+long mlqp_launch_count(const mlqp_ctx* c) { return c ? c->launches : 0; }
+
+const char* mlqp_last_error(const mlqp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void mlqp_destroy(mlqp_ctx* c) {
+  if (!c) return;
+  if (c->staging) {
+    if (c->bound) cudaStreamSynchronize(c->stream);
+    cudaFreeHost(c->staging);
+  }
+  delete c;
+}
+
+size_t mlqp_upload_bytes(const mlqp_ctx* c) { return (c && c->valid) ? c->r_geo[0].off : 0; }
+
+/* Test hook: H0, H1, J0, J1 (complex, 8 doubles per point) of z = k rho for
+ * n points given as (Re k, Im k, rho) triples; device pointers, on `stream`. */
+mlqp_status mlqp_debug_hankel(const double* d_krho, int n, double* d_out, void* stream) {
+  if (n < 0 || (n > 0 && (!d_krho || !d_out))) return MLQP_EINVAL;
+  cudaError_t e = launch_hankel_eval(d_krho, n, d_out, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? MLQP_OK : MLQP_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,522 @@
+// Geometry, quadrature and Nystrom fill kernels (Cho & Barnett, Secs. 1-2).
+//
+// Layout: every complex block is column-major, interleaved complex128
+// (double2).  The near-field blocks of interface i are stored as one block
+// row R_i = [A_{i,i-1} | A_{i,i} | A_{i,i+1}] (n_i rows), so that the Schur
+// updates and the block-tridiagonal sweep work in place.  Each fill thread
+// owns one (target, source) pair of a block, evaluates the Hankel functions
+// once per Bloch copy and writes the alpha-phased sum for every angle.
+#include "mlqp_internal.h"
+#include "mlqp_math.cuh"
+
+namespace mlqp {
+
+thread_local long g_launches = 0;  // launches issued by the current stage call
+
+// ---------------------------------------------------------------------------
+// Sec. 2.5: interface nodes s_j = 2 pi (j - 1/2)/N on Z(s) = (x(s), y(x(s))),
+// x(s) = -d/2 + s d/(2 pi); downward unit normals; speed |Z'(s)|.
+// Also the per-|q| tables of the periodic log-split for this N:
+//   R_q = -(2 pi/n) sum_{m=1}^{n-1} cos(m t_q)/m - (pi/n^2) cos(n t_q), t_q = 2 pi q/N,
+//   TABC[q] = R_q - (2 pi/N) log(4 sin^2(t_q/2))   (q >= 1), TABC[0] = R_0,
+//   TABCHI[q] = chi(t_q), the C-infinity window.
+// ---------------------------------------------------------------------------
+__device__ double cutoff_window(double delta, double a, double b) {
+  const double ad = fabs(delta);
+  if (ad <= a) return 1.0;
+  if (ad >= b) return 0.0;
+  const double u = (b - ad) / (b - a);
+  const double e1 = exp(-1.0 / u), e2 = exp(-1.0 / (1.0 - u));
+  return e1 / (e1 + e2);
+}
+
+__global__ void k_geom_nodes(Dev D) {
+  const int i = blockIdx.y;
+  const IfaceDesc f = D.ifc[i];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= f.N) return;
+  const int N = f.N;
+  const double x = -0.5 * D.d + D.d * ((double)j + 0.5) / N;
+  double y = f.y0, fp = 0.0;
+  for (int m = 1; m <= f.n_modes; ++m) {
+    const double w = TWO_PI * m / D.d;
+    double s, c;
+    sincos(w * x, &s, &c);
+    const double a = D.coef_a[f.coef_off + m - 1], b = D.coef_b[f.coef_off + m - 1];
+    y = fma(a, c, fma(b, s, y));
+    fp = fma(w, fma(-a, s, b * c), fp);
+  }
+  const double h = sqrt(1.0 + fp * fp);
+  const int o = f.node_off + j;
+  D.X[o] = x;
+  D.Y[o] = y;
+  D.NX[o] = fp / h;
+  D.NY[o] = -1.0 / h;
+  D.SP[o] = (D.d / TWO_PI) * h;
+  // log-split tables for q = j
+  const int n = N / 2;
+  const int q = j;
+  double Rq = 0.0;
+  for (int m = 1; m <= n - 1; ++m) {
+    const int r = (int)(((long long)m * q) % N);
+    Rq += cospi(2.0 * r / N) / m;
+  }
+  Rq = -(TWO_PI / n) * Rq - (PI / ((double)n * n)) * ((q & 1) ? -1.0 : 1.0);
+  double c = Rq;
+  if (q > 0) {
+    const double sq = sinpi((double)q / N);
+    c = Rq - (TWO_PI / N) * log(4.0 * sq * sq);
+  }
+  D.TABC[o] = c;
+  D.TABCHI[o] = (q <= n - 1) ? cutoff_window((TWO_PI / N) * q, D.cut_a, D.cut_b) : 0.0;
+}
+
+// Gauss-Legendre abscissae (Newton on P_M), U/D nodes, bounds of U and D,
+// walls and proxy centres of every layer, Bloch data of every angle.
+__device__ double interface_height_at(const Dev& D, int i, double x) {
+  const IfaceDesc f = D.ifc[i];
+  double y = f.y0;
+  for (int m = 1; m <= f.n_modes; ++m) {
+    double s, c;
+    sincos(TWO_PI * m * x / D.d, &s, &c);
+    y = fma(D.coef_a[f.coef_off + m - 1], c, fma(D.coef_b[f.coef_off + m - 1], s, y));
+  }
+  return y;
+}
+
+__device__ cplx vertical_wavenumber(cplx k, double kappa) {
+  cplx w = csqrt_(k * k - C(kappa * kappa));
+  if (w.im < 0.0) w = -w;
+  return w;
+}
+
+__global__ void k_geom_misc(Dev D, double* scal) {
+  const int t = threadIdx.x;
+  // y_U, y_D: bounds of Gamma_1 (resp. Gamma_I) plus the gaps
+  __shared__ double sYU, sYD;
+  if (t == 0) {
+    const IfaceDesc f0 = D.ifc[0], fl = D.ifc[D.I - 1];
+    double s0 = 0.0, sl = 0.0;
+    for (int m = 0; m < f0.n_modes; ++m) s0 += hypot(D.coef_a[f0.coef_off + m], D.coef_b[f0.coef_off + m]);
+    for (int m = 0; m < fl.n_modes; ++m) sl += hypot(D.coef_a[fl.coef_off + m], D.coef_b[fl.coef_off + m]);
+    sYU = f0.y0 + s0 + D.yU;   // D.yU holds gap_U here
+    sYD = fl.y0 - sl - D.yD;   // D.yD holds gap_D here
+    scal[0] = sYU;
+    scal[1] = sYD;
+  }
+  // Gauss-Legendre nodes on [-1, 1], ascending
+  for (int g = t; g < D.Mw; g += blockDim.x) {
+    const int M = D.Mw;
+    const int r = g + 1;  // root index counted from the largest
+    double x = cos(PI * (r - 0.25) / (M + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int j = 1; j < M; ++j) {
+        const double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      const double dp = M * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-16) break;
+    }
+    D.GL[M - 1 - g] = x;
+  }
+  for (int m = t; m < D.M; m += blockDim.x) D.UX[m] = -0.5 * D.d + D.d * ((double)m + 0.5) / D.M;
+  __syncthreads();
+  // walls and proxy centres
+  for (int j = t; j <= D.I; j += blockDim.x) {
+    const double top = (j == 0) ? sYU : interface_height_at(D, j - 1, -0.5 * D.d);
+    const double bot = (j == D.I) ? sYD : interface_height_at(D, j, -0.5 * D.d);
+    D.lay[j].ytop = top;
+    D.lay[j].ybot = bot;
+    D.lay[j].cy = 0.5 * (top + bot);
+  }
+  __syncthreads();
+  for (int e = t; e < (D.I + 1) * D.Mw; e += blockDim.x) {
+    const int j = e / D.Mw, g = e % D.Mw;
+    const double top = D.lay[j].ytop, bot = D.lay[j].ybot;
+    D.WY[e] = 0.5 * (top + bot) + 0.5 * (top - bot) * D.GL[g];
+  }
+  // Bloch data (Sec. 1): alpha, kappa_n, k^U_n, k^D_n
+  const double k1 = D.kre[0];
+  const cplx kl = C(D.kre[2 * D.I], D.kre[2 * D.I + 1]);
+  for (int e = t; e < D.n_theta * D.nK; e += blockDim.x) {
+    const int a = e / D.nK, n = e % D.nK - D.K;
+    const double ct = cos(D.theta[a]);
+    const double kap = k1 * ct + TWO_PI * n / D.d;
+    D.KAPPA[e] = kap;
+    const cplx u = vertical_wavenumber(C(k1), kap), w = vertical_wavenumber(kl, kap);
+    D.KU[e] = make_double2(u.re, u.im);
+    D.KD[e] = make_double2(w.re, w.im);
+    if (n == 0) {
+      double s, c;
+      sincos(D.d * k1 * ct, &s, &c);
+      D.ALPHA[a] = make_double2(c, s);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// eq. Ablocks: A_{i,i} (Mueller-Rokhlin differences, log-split self part),
+// A_{i,i+1} = -[[D,S],[T,D*]]^{i+1}, A_{i,i-1} = +[[D,S],[T,D*]]^{i}, each a
+// sum over the copies l = -1, 0, 1 with weight alpha^l (eqs. SDopsum, DtTopsum).
+// Self part: for the unwrapped source index p = j + l N and q = p - m,
+//   entry = (2pi/N) K + chi_q K1 (R_q - (2pi/N) log(4 sin^2(pi q/N)))  (|q| < N/2)
+//   entry = (2pi/N) K2(t,t) + R_0 K1(t,t)                              (q = 0)
+// with K, K1 the kernel differences times |Z'(s)|.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void diag_limits(cplx k1, cplx k2, double sp, cplx out2[4], cplx out1[4]) {
+  // order: S, D, Ds, T
+  const cplx lk1 = clog_(k1), lk2 = clog_(k2);
+  const double q = sp * INV_4PI;
+  const cplx c = C(-0.5 + EULER_GAMMA - 0.69314718055994530942 + log(sp), -0.5 * PI);
+  const cplx k1s = k1 * k1, k2s = k2 * k2;
+  out2[0] = (-2.0 * q) * (lk1 - lk2);
+  out2[1] = C(0.0);
+  out2[2] = C(0.0);
+  out2[3] = (-q) * ((k1s - k2s) * c + k1s * lk1 - k2s * lk2);
+  out1[0] = C(0.0);
+  out1[1] = C(0.0);
+  out1[2] = C(0.0);
+  out1[3] = (-0.5 * q) * (k1s - k2s);
+}
+
+__global__ void __launch_bounds__(128) k_fill_A(Dev D) {
+  const int i = blockIdx.z / 3, type = blockIdx.z % 3;  // 0 self, 1 upper (i+1), 2 lower (i-1)
+  if (type == 1 && i == D.I - 1) return;
+  if (type == 2 && i == 0) return;
+  const IfaceDesc ft = D.ifc[i];
+  const int si = (type == 0) ? i : (type == 1) ? i + 1 : i - 1;
+  const IfaceDesc fs = D.ifc[si];
+  const int m = blockIdx.x * 32 + threadIdx.x;  // target node
+  const int j = blockIdx.y * 4 + threadIdx.y;   // source node
+  if (m >= ft.N || j >= fs.N) return;
+  const int to = ft.node_off + m, so = fs.node_off + j;
+  const double tx = D.X[to], ty = D.Y[to], tnx = D.NX[to], tny = D.NY[to];
+  const double sx0 = D.X[so], sy = D.Y[so], snx = D.NX[so], sny = D.NY[so], sp = D.SP[so];
+  const int Ns = fs.N;
+  const double h = TWO_PI / Ns;
+  cplx v[3][4];  // per copy: D, S, T, Ds
+  if (type == 0) {
+    const cplx k1 = C(D.kre[2 * i], D.kre[2 * i + 1]);
+    const cplx k2 = C(D.kre[2 * i + 2], D.kre[2 * i + 3]);
+    const int n = Ns / 2;
+#pragma unroll 1
+    for (int l = -1; l <= 1; ++l) {
+      const int q = j + l * Ns - m;
+      if (q == 0) {
+        cplx l2[4], l1[4];
+        diag_limits(k1, k2, sp, l2, l1);
+        const double R0 = D.TABC[fs.node_off];
+        v[l + 1][0] = h * l2[1] + R0 * l1[1] + C(-1.0);  // D (with -I)
+        v[l + 1][1] = h * l2[0] + R0 * l1[0];            // S
+        v[l + 1][2] = h * l2[3] + R0 * l1[3];            // T
+        v[l + 1][3] = h * l2[2] + R0 * l1[2] + C(1.0);   // Ds (with +I)
+        continue;
+      }
+      const double sx = sx0 + l * D.d;
+      const Geo g = geo(tx, ty, tnx, tny, sx, sy, snx, sny);
+      const int aq = q < 0 ? -q : q;
+      const bool win = aq <= n - 1;
+      if (win) {
+        const KernL a = kernels_log(k1, g, hankel(k1, g.rho));
+        const KernL b = kernels_log(k2, g, hankel(k2, g.rho));
+        const double cw = D.TABCHI[fs.node_off + aq] * D.TABC[fs.node_off + aq] * sp;
+        const double hs = h * sp;
+        v[l + 1][0] = hs * (a.D - b.D) + cw * (a.K1D - b.K1D);
+        v[l + 1][1] = hs * (a.S - b.S) + cw * (a.K1S - b.K1S);
+        v[l + 1][2] = hs * (a.T - b.T) + cw * (a.K1T - b.K1T);
+        v[l + 1][3] = hs * (a.Ds - b.Ds) + cw * (a.K1Ds - b.K1Ds);
+      } else {
+        const Kern a = kernels(k1, g, hankel(k1, g.rho));
+        const Kern b = kernels(k2, g, hankel(k2, g.rho));
+        const double hs = h * sp;
+        v[l + 1][0] = hs * (a.D - b.D);
+        v[l + 1][1] = hs * (a.S - b.S);
+        v[l + 1][2] = hs * (a.T - b.T);
+        v[l + 1][3] = hs * (a.Ds - b.Ds);
+      }
+    }
+  } else {
+    const int layer = (type == 1) ? i + 1 : i;
+    const cplx k = C(D.kre[2 * layer], D.kre[2 * layer + 1]);
+    const double sgn = (type == 1) ? -1.0 : 1.0;
+    const double ws = sgn * h * sp;
+#pragma unroll 1
+    for (int l = -1; l <= 1; ++l) {
+      const Geo g = geo(tx, ty, tnx, tny, sx0 + l * D.d, sy, snx, sny);
+      const Kern a = kernels(k, g, hankel(k, g.rho));
+      v[l + 1][0] = ws * a.D;
+      v[l + 1][1] = ws * a.S;
+      v[l + 1][2] = ws * a.T;
+      v[l + 1][3] = ws * a.Ds;
+    }
+  }
+  const int coff = (type == 0) ? ft.nl : (type == 1) ? ft.nl + ft.n : 0;
+  const int ld = ft.n, Nt = ft.N;
+  for (int a = 0; a < D.n_theta; ++a) {
+    const cplx al = ld2(&D.ALPHA[a]);
+    const cplx ali = conj(al);
+    double2* base = D.ROW + a * D.r_stride + ft.row_off;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const cplx s = ali * v[0][kk] + v[1][kk] + al * v[2][kk];
+      const int row = m + ((kk >= 2) ? Nt : 0);
+      const int col = coff + j + ((kk == 1 || kk == 3) ? Ns : 0);
+      st2(base + (size_t)col * ld + row, s);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// eq. Bblocks / Bblockmat: B_{i,i} = [phi^i_p; d phi^i_p/dn] on Gamma_i,
+// B_{i,i+1} = -[phi^{i+1}_p; ...], phi_p = dG/dn_p + i k G (eq. phi).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void proxy_point(const Dev& D, int layer, int p, double& px, double& py,
+                                            double& pnx, double& pny) {
+  double s, c;
+  sincospi(2.0 * p / D.P, &s, &c);
+  px = D.R * c;
+  py = D.lay[layer].cy + D.R * s;
+  pnx = c;
+  pny = s;
+}
+
+__device__ __forceinline__ void proxy_field(cplx k, double tx, double ty, double tnx, double tny, double px,
+                                            double py, double pnx, double pny, cplx& phi, cplx& dphi) {
+  const Geo g = geo(tx, ty, tnx, tny, px, py, pnx, pny);
+  const Kern a = kernels(k, g, hankel(k, g.rho));
+  const cplx ik = mul_i(k);
+  phi = a.D + ik * a.S;
+  dphi = a.T + ik * a.Ds;
+}
+
+__global__ void __launch_bounds__(128) k_fill_B(Dev D) {
+  const int i = blockIdx.z >> 1, which = blockIdx.z & 1;  // 0: B_{i,i}, 1: B_{i,i+1}
+  const IfaceDesc f = D.ifc[i];
+  const int j = blockIdx.x * 32 + threadIdx.x, p = blockIdx.y * 4 + threadIdx.y;
+  if (j >= f.N || p >= D.P) return;
+  const int layer = i + which;
+  const cplx k = C(D.kre[2 * layer], D.kre[2 * layer + 1]);
+  double px, py, pnx, pny;
+  proxy_point(D, layer, p, px, py, pnx, pny);
+  const int o = f.node_off + j;
+  cplx phi, dphi;
+  proxy_field(k, D.X[o], D.Y[o], D.NX[o], D.NY[o], px, py, pnx, pny, phi, dphi);
+  const double sgn = which ? -1.0 : 1.0;
+  double2* base = D.B + f.b_off + (size_t)(which * D.P + p) * f.n;
+  st2(base + j, sgn * phi);
+  st2(base + f.N + j, sgn * dphi);
+}
+
+// ---------------------------------------------------------------------------
+// C'_j wall rows (eq. Cii with targets x_m + 2d and x_m - d, the 3-copy sums
+// reduced to two terms):  (alpha^{-2} K(x_m + 2d, z) - alpha K(x_m - d, z)) w,
+// values then x-derivatives (wall normal +x), kernel of layer j.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_fill_C(Dev D) {
+  const int jl = blockIdx.z >> 1, side = blockIdx.z & 1;
+  const LayerDesc L = D.lay[jl];
+  const int ifs = side ? L.if1 : L.if0;
+  if (ifs < 0) return;
+  const int coff = side ? L.c1 : L.c0;
+  const IfaceDesc f = D.ifc[ifs];
+  const int g = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 4 + threadIdx.y;
+  if (g >= D.Mw || j >= f.N) return;
+  const cplx k = C(D.kre[2 * jl], D.kre[2 * jl + 1]);
+  const int o = f.node_off + j;
+  const double sx = D.X[o], sy = D.Y[o], snx = D.NX[o], sny = D.NY[o];
+  const double w = (TWO_PI / f.N) * D.SP[o];
+  const double yw = D.WY[jl * D.Mw + g];
+  const double xw = -0.5 * D.d;
+  const Geo gp = geo(xw + 2.0 * D.d, yw, 1.0, 0.0, sx, sy, snx, sny);
+  const Kern kp = kernels(k, gp, hankel(k, gp.rho));
+  const Geo gm = geo(xw - D.d, yw, 1.0, 0.0, sx, sy, snx, sny);
+  const Kern km = kernels(k, gm, hankel(k, gm.rho));
+  for (int a = 0; a < D.n_theta; ++a) {
+    const cplx al = ld2(&D.ALPHA[a]);
+    const cplx am2 = conj(al * al);
+    double2* base = D.CP + a * D.cp_stride + L.cp_off;
+    const int ld = L.ldq;
+    st2(base + (size_t)(coff + j) * ld + g, w * (am2 * kp.D - al * km.D));
+    st2(base + (size_t)(coff + f.N + j) * ld + g, w * (am2 * kp.S - al * km.S));
+    st2(base + (size_t)(coff + j) * ld + D.Mw + g, w * (am2 * kp.T - al * km.T));
+    st2(base + (size_t)(coff + f.N + j) * ld + D.Mw + g, w * (am2 * kp.Ds - al * km.Ds));
+  }
+}
+
+// Z_U (Gamma_1 -> U, layer 1 kernels) and Z_D (Gamma_I -> D, layer I+1
+// kernels), 3-copy sums, target normal +y (eq. VUD); rows 2Mw.. of C'.
+__global__ void __launch_bounds__(128) k_fill_Z(Dev D, const double* scal) {
+  const int which = blockIdx.z;  // 0: U, 1: D
+  const int jl = which ? D.I : 0;
+  const LayerDesc L = D.lay[jl];
+  const int ifs = which ? D.I - 1 : 0;
+  const IfaceDesc f = D.ifc[ifs];
+  const int m = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 4 + threadIdx.y;
+  if (m >= D.M || j >= f.N) return;
+  const cplx k = C(D.kre[2 * jl], D.kre[2 * jl + 1]);
+  const int o = f.node_off + j;
+  const double sy = D.Y[o], snx = D.NX[o], sny = D.NY[o];
+  const double w = (TWO_PI / f.N) * D.SP[o];
+  const double tx = D.UX[m], ty = which ? scal[1] : scal[0];
+  Kern v[3];
+#pragma unroll 1
+  for (int l = -1; l <= 1; ++l) {
+    const Geo g = geo(tx, ty, 0.0, 1.0, D.X[o] + l * D.d, sy, snx, sny);
+    v[l + 1] = kernels(k, g, hankel(k, g.rho));
+  }
+  const int coff = 0;  // the single interface column block of an end layer
+  const int ld = L.ldq, r0 = 2 * D.Mw;
+  for (int a = 0; a < D.n_theta; ++a) {
+    const cplx al = ld2(&D.ALPHA[a]);
+    const cplx ali = conj(al);
+    double2* base = D.CP + a * D.cp_stride + L.cp_off;
+    st2(base + (size_t)(coff + j) * ld + r0 + m, w * (ali * v[0].D + v[1].D + al * v[2].D));
+    st2(base + (size_t)(coff + f.N + j) * ld + r0 + m, w * (ali * v[0].S + v[1].S + al * v[2].S));
+    st2(base + (size_t)(coff + j) * ld + r0 + D.M + m, w * (ali * v[0].T + v[1].T + al * v[2].T));
+    st2(base + (size_t)(coff + f.N + j) * ld + r0 + D.M + m, w * (ali * v[0].Ds + v[1].Ds + al * v[2].Ds));
+  }
+}
+
+// Q'_j: wall rows alpha^{-1} phi_p(x_m + d) - phi_p(x_m) (and d/dx) (eq. Qi);
+// at the end layers also the zero block under the amplitude columns.
+__global__ void __launch_bounds__(128) k_fill_Q(Dev D) {
+  const int jl = blockIdx.z;
+  const LayerDesc L = D.lay[jl];
+  const int g = blockIdx.x * 32 + threadIdx.x, p = blockIdx.y * 4 + threadIdx.y;
+  if (g >= D.Mw || p >= L.p) return;
+  const int ld = L.ldq;
+  if (p >= D.P) {
+    for (int a = 0; a < D.n_theta; ++a) {
+      double2* base = D.QP + a * D.qp_stride + L.qp_off;
+      st2(base + (size_t)p * ld + g, C(0.0));
+      st2(base + (size_t)p * ld + D.Mw + g, C(0.0));
+    }
+    return;
+  }
+  const cplx k = C(D.kre[2 * jl], D.kre[2 * jl + 1]);
+  double px, py, pnx, pny;
+  proxy_point(D, jl, p, px, py, pnx, pny);
+  const double yw = D.WY[jl * D.Mw + g], xw = -0.5 * D.d;
+  cplx f0, d0, f1, d1;
+  proxy_field(k, xw + D.d, yw, 1.0, 0.0, px, py, pnx, pny, f1, d1);
+  proxy_field(k, xw, yw, 1.0, 0.0, px, py, pnx, pny, f0, d0);
+  for (int a = 0; a < D.n_theta; ++a) {
+    const cplx ali = conj(ld2(&D.ALPHA[a]));
+    double2* base = D.QP + a * D.qp_stride + L.qp_off;
+    st2(base + (size_t)p * ld + g, ali * f1 - f0);
+    st2(base + (size_t)p * ld + D.Mw + g, ali * d1 - d0);
+  }
+}
+
+// V_U, V_D (proxy fields on U/D, normal +y) and W_U, W_D (eq. WUD).
+__global__ void __launch_bounds__(128) k_fill_VW(Dev D, const double* scal) {
+  const int which = blockIdx.z;
+  const int jl = which ? D.I : 0;
+  const LayerDesc L = D.lay[jl];
+  const int m = blockIdx.x * 32 + threadIdx.x, c = blockIdx.y * 4 + threadIdx.y;
+  if (m >= D.M || c >= L.p) return;
+  const int ld = L.ldq, r0 = 2 * D.Mw;
+  const double tx = D.UX[m], ty = which ? scal[1] : scal[0];
+  if (c < D.P) {
+    const cplx k = C(D.kre[2 * jl], D.kre[2 * jl + 1]);
+    double px, py, pnx, pny;
+    proxy_point(D, jl, c, px, py, pnx, pny);
+    cplx f, df;
+    proxy_field(k, tx, ty, 0.0, 1.0, px, py, pnx, pny, f, df);
+    for (int a = 0; a < D.n_theta; ++a) {
+      double2* base = D.QP + a * D.qp_stride + L.qp_off;
+      st2(base + (size_t)c * ld + r0 + m, f);
+      st2(base + (size_t)c * ld + r0 + D.M + m, df);
+    }
+  } else {
+    const int n = c - D.P;
+    for (int a = 0; a < D.n_theta; ++a) {
+      const double kap = D.KAPPA[a * D.nK + n];
+      const cplx e = expi(kap * tx);
+      const cplx kv = ld2(which ? &D.KD[a * D.nK + n] : &D.KU[a * D.nK + n]);
+      double2* base = D.QP + a * D.qp_stride + L.qp_off;
+      st2(base + (size_t)c * ld + r0 + m, -e);
+      const cplx ike = mul_i(kv * e);
+      st2(base + (size_t)c * ld + r0 + D.M + m, which ? ike : -ike);
+    }
+  }
+}
+
+// f_1 = [-u_inc; -du_inc/dn] on Gamma_1 (eq. rokhlin_muller_matrix), f_i = 0.
+__global__ void k_fill_rhs(Dev D) {
+  const int i = blockIdx.y;
+  const IfaceDesc f = D.ifc[i];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= f.N) return;
+  const int o = f.node_off + j;
+  for (int a = 0; a < D.n_theta; ++a) {
+    double2* base = D.F + a * D.f_stride + f.rhs_off;
+    if (i == 0) {
+      double s, c;
+      sincos(D.theta[a], &s, &c);
+      const double kx = D.kre[0] * c, ky = D.kre[0] * s;
+      const cplx u = expi(kx * D.X[o] + ky * D.Y[o]);
+      const double kn = kx * D.NX[o] + ky * D.NY[o];
+      st2(base + j, -u);
+      st2(base + f.N + j, -(kn * mul_i(u)));
+    } else {
+      st2(base + j, C(0.0));
+      st2(base + f.N + j, C(0.0));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_geometry(const Dev& D, double* scal, cudaStream_t s) {
+  ++g_launches;
+  k_geom_nodes<<<dim3((D.maxN + 127) / 128, D.I), 128, 0, s>>>(D);
+  ++g_launches;
+  k_geom_misc<<<1, 256, 0, s>>>(D, scal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(const Dev& D, const double* scal, cudaStream_t s) {
+  const int nx = (D.maxN + 31) / 32, ny = (D.maxN + 3) / 4;
+  ++g_launches;
+  k_fill_A<<<dim3(nx, ny, 3 * D.I), dim3(32, 4), 0, s>>>(D);
+  ++g_launches;
+  k_fill_B<<<dim3(nx, (D.P + 3) / 4, 2 * D.I), dim3(32, 4), 0, s>>>(D);
+  ++g_launches;
+  k_fill_C<<<dim3((D.Mw + 31) / 32, ny, 2 * D.L), dim3(32, 4), 0, s>>>(D);
+  ++g_launches;
+  k_fill_Z<<<dim3((D.M + 31) / 32, ny, 2), dim3(32, 4), 0, s>>>(D, scal);
+  ++g_launches;
+  k_fill_Q<<<dim3((D.Mw + 31) / 32, (D.P + D.nK + 3) / 4, D.L), dim3(32, 4), 0, s>>>(D);
+  ++g_launches;
+  k_fill_VW<<<dim3((D.M + 31) / 32, (D.P + D.nK + 3) / 4, 2), dim3(32, 4), 0, s>>>(D, scal);
+  ++g_launches;
+  k_fill_rhs<<<dim3((D.maxN + 127) / 128, D.I), 128, 0, s>>>(D);
+  return cudaGetLastError();
+}
+
+// Test hook: H0, H1, J0, J1 at n arguments z = k rho given as (k, rho) pairs.
+__global__ void k_hankel_eval(const double* kr, int n, double* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const cplx k = C(kr[3 * e], kr[3 * e + 1]);
+  const Hank h = hankel(k, kr[3 * e + 2]);
+  out[8 * e + 0] = h.H0.re; out[8 * e + 1] = h.H0.im;
+  out[8 * e + 2] = h.H1.re; out[8 * e + 3] = h.H1.im;
+  out[8 * e + 4] = h.J0.re; out[8 * e + 5] = h.J0.im;
+  out[8 * e + 6] = h.J1.re; out[8 * e + 7] = h.J1.im;
+}
+
+cudaError_t launch_hankel_eval(const double* kr, int n, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ++g_launches;
+  k_hankel_eval<<<(n + 127) / 128, 128, 0, s>>>(kr, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mlqp

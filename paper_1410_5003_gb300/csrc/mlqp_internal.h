@@ -1,0 +1,92 @@
+// Internal descriptors shared by the host side (layout, launches) and the
+// kernels of the mlqp library.  Everything lives in the caller's workspace.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace mlqp {
+
+// Per interface i (0-based here; the paper's Gamma_{i+1}).
+struct IfaceDesc {
+  int N;          // quadrature nodes
+  int n;          // 2N unknowns (tau, sigma)
+  int node_off;   // offset into the node arrays (doubles)
+  int n_modes;    // Fourier modes of the profile
+  int coef_off;   // offset into the coefficient arrays a, b
+  int nl, nr;     // unknowns of the neighbours above (i-1) and below (i+1); 0 at the ends
+  size_t row_off;  // element offset of the block row [A_{i,i-1} | A_{i,i} | A_{i,i+1}] in one angle
+  int row_cols;    // nl + n + nr
+  size_t rhs_off;  // element offset of f_i in one angle
+  size_t b_off;    // element offset of [B_{i,i} | B_{i,i+1}] (angle independent)
+  size_t eta_off;  // offset of eta_i within one angle's eta (= sum_{i'<i} n_{i'})
+  double y0;
+};
+
+// Per layer j (0-based; the paper's layer j+1).
+struct LayerDesc {
+  int m;          // rows of Q'_j / C'_j: 2 Mw (+ 2M at the two ends)
+  int p;          // columns of Q'_j: P (+ 2K+1 at the ends)
+  int ldq;        // leading dimension of Q'_j and C'_j: m + p (room for the lam I rows)
+  int c;          // columns of C'_j: n of the interfaces it touches
+  int if0, if1;   // interfaces (0-based) whose densities C'_j acts on (-1: none)
+  int c0, c1;     // column offsets of those interfaces' blocks in C'_j
+  int end;        // 0 middle, 1 top (U), 2 bottom (D)
+  size_t qp_off;  // element offsets within one angle's regions
+  size_t cp_off;
+  size_t x_off;
+  size_t aux_off;  // sum of p over the previous layers (LSQ auxiliaries at 6 aux_off doubles)
+  double ybot, ytop, cy;  // wall extent and proxy-circle centre (filled on the device)
+};
+
+// One Schur update  C -= A1 B1 (+ A2 B2)   (eqs. Schur1-Schuri).
+struct SchurTask {
+  size_t c_off;   // output block (within one angle's R region)
+  int ldc, rows, cols;
+  size_t a1_off, a2_off;  // B blocks (angle independent)
+  int lda1, lda2;
+  size_t b1_off, b2_off;  // X blocks (within one angle's X region)
+  int ldb1, ldb2;
+  int k1, k2;             // inner dimensions (k2 = 0: single term)
+};
+
+// Problem scalars and workspace pointers, passed by value to the kernels.
+struct Dev {
+  int I, L, n_theta, P, Mw, M, K, nK;
+  double d, R, cut_a, cut_b, rcond, yU, yD;
+  int maxN, maxn, total_nodes;
+  // per-interface / per-layer tables
+  const IfaceDesc* ifc;
+  LayerDesc* lay;
+  const double* kre;  // k_j (real, imag), j = 0..I
+  const double* coef_a;
+  const double* coef_b;
+  const double* theta;
+  // geometry (doubles, total_nodes each)
+  double *X, *Y, *NX, *NY, *SP;
+  double *TABC, *TABCHI;  // Kress-minus-log weights (TABC[0] = R_0) and window values, per |q|
+  double* WY;             // wall nodes y, (I+1) x Mw
+  double* GL;             // Gauss-Legendre abscissae on [-1, 1], Mw
+  double* UX;             // U/D nodes x, M
+  // per-angle Bloch data
+  double2* ALPHA;  // n_theta
+  double* KAPPA;   // n_theta x nK
+  double2* KU;     // n_theta x nK
+  double2* KD;     // n_theta x nK
+  // blocks
+  double2* ROW; size_t r_stride;    // block rows R_i, per angle
+  double2* F;   size_t f_stride;
+  double2* B;
+  double2* QP;  size_t qp_stride;
+  double2* CP;  size_t cp_stride;
+  double2* Xb;  size_t x_stride;
+  double* LAUX; size_t laux_stride;  // per layer 6p doubles: R_kk[p], v0[p] (complex), beta[p], pad
+  int* LUPIV;   size_t piv_stride;    // block-LU pivots, per angle, indexed like eta
+  double2* ETA; size_t eta_stride;
+  double2* AMP;                        // n_theta x 2 nK
+  double* FLUX;                        // n_theta
+  int* STATUS;
+  const SchurTask* tasks; int n_tasks;
+};
+
+}  // namespace mlqp

@@ -1,0 +1,351 @@
+// FP64 complex arithmetic and Hankel functions H_0^(1), H_1^(1) for the
+// Helmholtz kernels G = (i/4) H0(k r) of Cho & Barnett, eq. Gi.
+//
+// Bessel/Hankel evaluation (own code, from the published formulas):
+//   |z| < 4        ascending series (Abramowitz & Stegun 9.1.10, 9.1.11)
+//   4 <= |z| < 20  Miller's backward recurrence J_{n-1} = (2n/z) J_n - J_{n+1}
+//                  (A&S 9.12), normalised by e^{-iz} = J_0 + 2 sum (-i)^n J_n
+//                  (real z: 1 = J_0 + 2 sum J_{2k}); Y_0 from Neumann's series
+//                  Y_0 = (2/pi)(ln(z/2)+gamma) J_0 - (4/pi) sum (-1)^k J_{2k}/k
+//                  (A&S 9.1.88) and Y_1 = -Y_0' from the same J_n
+//   |z| >= 20      Hankel's asymptotic expansion H_nu = sqrt(2/(pi z)) (P + iQ)
+//                  e^{i(z - (nu/2 + 1/4) pi)} (A&S 9.2.5-9.2.10)
+// Returned: H_0, H_1 and J_0, J_1 (the latter are the coefficients of the
+// logarithmic singularity used by the log-split quadrature).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace mlqp {
+
+struct cplx {
+  double re, im;
+};
+
+__device__ __forceinline__ cplx C(double r, double i = 0.0) { return cplx{r, i}; }
+__device__ __forceinline__ cplx operator+(cplx a, cplx b) { return C(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ cplx operator-(cplx a, cplx b) { return C(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ cplx operator-(cplx a) { return C(-a.re, -a.im); }
+__device__ __forceinline__ cplx operator*(cplx a, cplx b) {
+  return C(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+}
+__device__ __forceinline__ cplx operator*(double s, cplx a) { return C(s * a.re, s * a.im); }
+__device__ __forceinline__ cplx operator*(cplx a, double s) { return C(s * a.re, s * a.im); }
+__device__ __forceinline__ cplx conj(cplx a) { return C(a.re, -a.im); }
+__device__ __forceinline__ cplx mul_i(cplx a) { return C(-a.im, a.re); }  // i*a
+__device__ __forceinline__ double abs2(cplx a) { return fma(a.re, a.re, a.im * a.im); }
+__device__ __forceinline__ double cabs(cplx a) { return hypot(a.re, a.im); }
+__device__ __forceinline__ cplx inv(cplx a) {
+  // 1/a, scaled to avoid overflow/underflow of |a|^2
+  double s = fmax(fabs(a.re), fabs(a.im));
+  double ar = a.re / s, ai = a.im / s;
+  double d = 1.0 / (s * fma(ar, ar, ai * ai));
+  return C(ar * d, -ai * d);
+}
+__device__ __forceinline__ cplx operator/(cplx a, cplx b) { return a * inv(b); }
+__device__ __forceinline__ cplx cexp_(cplx a) {
+  double s, c;
+  sincos(a.im, &s, &c);
+  double e = exp(a.re);
+  return C(e * c, e * s);
+}
+__device__ __forceinline__ cplx expi(double t) {  // e^{i t}
+  double s, c;
+  sincos(t, &s, &c);
+  return C(c, s);
+}
+__device__ __forceinline__ cplx clog_(cplx a) { return C(log(cabs(a)), atan2(a.im, a.re)); }
+__device__ __forceinline__ cplx csqrt_(cplx a) {
+  // principal square root
+  double r = cabs(a);
+  double t = sqrt(0.5 * (r + fabs(a.re)));
+  if (t == 0.0) return C(0.0, 0.0);
+  if (a.re >= 0.0) return C(t, 0.5 * a.im / t);
+  return C(0.5 * fabs(a.im) / t, copysign(t, a.im));
+}
+__device__ __forceinline__ cplx ld2(const double2* p) {
+  double2 v = *p;
+  return C(v.x, v.y);
+}
+__device__ __forceinline__ void st2(double2* p, cplx v) { *p = make_double2(v.re, v.im); }
+
+constexpr double PI = 3.14159265358979323846;
+constexpr double TWO_PI = 6.28318530717958647693;
+constexpr double INV_PI = 0.31830988618379067154;
+constexpr double TWO_OVER_PI = 0.63661977236758134308;
+constexpr double EULER_GAMMA = 0.57721566490153286061;
+constexpr double SQRT_HALF = 0.70710678118654752440;
+constexpr double INV_4PI = 0.07957747154594766788;
+
+// ---------------------------------------------------------------------------
+// Real argument x > 0
+// ---------------------------------------------------------------------------
+struct Hank {
+  cplx H0, H1;  // Hankel functions of the first kind
+  cplx J0, J1;  // Bessel functions of the first kind
+};
+
+static __device__ __noinline__ Hank hankel_real(double x) {
+  Hank h;
+  double J0, J1, Y0, Y1;
+  if (x < 4.0) {
+    // J0 = sum (-q)^k/(k!)^2, J1 = (x/2) sum (-q)^k/(k!(k+1)!), q = x^2/4;
+    // Y0 = (2/pi)[(ln(x/2)+g) J0 - sum H_k (-q)^k/(k!)^2];
+    // Y1 = -2/(pi x) + (2/pi)(ln(x/2)+g) J1 - (x/(2 pi)) sum (H_k + H_{k+1}) (-q)^k/(k!(k+1)!)
+    const double q = 0.25 * x * x;
+    double t0 = 1.0, t1 = 1.0, Hk = 0.0;
+    double s0 = 1.0, s1 = 1.0, sy0 = 0.0, sy1 = 1.0;
+#pragma unroll
+    for (int k = 1; k <= 18; ++k) {
+      t0 *= -q * (1.0 / ((double)k * k));
+      t1 *= -q * (1.0 / ((double)k * (k + 1)));
+      Hk += 1.0 / k;
+      s0 += t0;
+      s1 += t1;
+      sy0 = fma(Hk, t0, sy0);
+      sy1 = fma(2.0 * Hk + 1.0 / (k + 1), t1, sy1);
+    }
+    const double L = log(0.5 * x) + EULER_GAMMA;
+    J0 = s0;
+    J1 = 0.5 * x * s1;
+    Y0 = TWO_OVER_PI * (L * J0 - sy0);
+    Y1 = -TWO_OVER_PI / x + TWO_OVER_PI * L * J1 - 0.5 * INV_PI * x * sy1;
+  } else if (x < 20.0) {
+    const int N = 2 * (((int)(x + 36.0)) / 2);
+    const double tx = 2.0 / x;
+    double jn1 = 0.0, jn = 1e-30;  // J_{n+1}, J_n (unnormalised), n = N
+    double norm = 0.0, sy0 = 0.0, sy1 = 0.0;
+    double j1 = 0.0;
+    for (int n = N; n >= 1; --n) {
+      // accumulate the contributions of J_n
+      if ((n & 1) == 0) {
+        const int k = n >> 1;
+        norm += 2.0 * jn;
+        const double sgn = (k & 1) ? -1.0 : 1.0;
+        sy0 = fma(sgn / k, jn, sy0);
+      } else {
+        // odd n = 2m+1: + (-1)^{m+1}/(m+1) J_n  (term k=m+1), - (-1)^m/m J_n (term k=m, m>=1)
+        const int m = n >> 1;
+        const double sgn = (m & 1) ? -1.0 : 1.0;  // (-1)^m
+        double c = -sgn / (m + 1);
+        if (m >= 1) c -= sgn / m;
+        sy1 = fma(c, jn, sy1);
+      }
+      const double jm1 = fma(n * tx, jn, -jn1);
+      jn1 = jn;
+      jn = jm1;
+      if (n == 1) j1 = jn1;
+    }
+    // now jn = J_0 (unnormalised), j1 = J_1
+    norm += jn;
+    const double sc = 1.0 / norm;
+    J0 = jn * sc;
+    J1 = j1 * sc;
+    const double L = log(0.5 * x) + EULER_GAMMA;
+    Y0 = TWO_OVER_PI * (L * J0 - 2.0 * sy0 * sc);
+    Y1 = TWO_OVER_PI * (L * J1 - J0 / x + sy1 * sc);
+  } else {
+    // Hankel's expansion: t_k = prod_{i<=k} (mu - (2i-1)^2) / (k! (8x)^k)
+    const double r8 = 0.125 / x;
+    double P0 = 1.0, Q0 = 0.0, P1 = 1.0, Q1 = 0.0;
+    double t0 = 1.0, t1 = 1.0;
+    for (int k = 1; k <= 40; ++k) {
+      const double o = (double)(2 * k - 1) * (2 * k - 1);
+      t0 *= (0.0 - o) * r8 / k;
+      t1 *= (4.0 - o) * r8 / k;
+      const int ph = k & 3;  // k mod 4: 1 -> +Q, 2 -> -P, 3 -> -Q, 0 -> +P
+      if (ph == 1) { Q0 += t0; Q1 += t1; }
+      else if (ph == 2) { P0 -= t0; P1 -= t1; }
+      else if (ph == 3) { Q0 -= t0; Q1 -= t1; }
+      else { P0 += t0; P1 += t1; }
+      if (fabs(t0) < 1e-17 && fabs(t1) < 1e-17) break;
+    }
+    double s, c;
+    sincos(x, &s, &c);
+    const double amp = sqrt(TWO_OVER_PI / x);
+    // e^{i(x - pi/4)} and e^{i(x - 3pi/4)}
+    const double c0 = SQRT_HALF * (c + s), s0 = SQRT_HALF * (s - c);
+    const double c1 = SQRT_HALF * (s - c), s1 = -SQRT_HALF * (s + c);
+    J0 = amp * (P0 * c0 - Q0 * s0);
+    Y0 = amp * (P0 * s0 + Q0 * c0);
+    J1 = amp * (P1 * c1 - Q1 * s1);
+    Y1 = amp * (P1 * s1 + Q1 * c1);
+  }
+  h.H0 = C(J0, Y0);
+  h.H1 = C(J1, Y1);
+  h.J0 = C(J0);
+  h.J1 = C(J1);
+  return h;
+}
+
+// ---------------------------------------------------------------------------
+// Complex argument z, Im z >= 0, z != 0 (lossy layers)
+// ---------------------------------------------------------------------------
+static __device__ __noinline__ Hank hankel_cplx(cplx z) {
+  Hank h;
+  const double az = cabs(z);
+  if (az < 4.0) {
+    const cplx q = 0.25 * (z * z);
+    cplx t0 = C(1.0), t1 = C(1.0);
+    double Hk = 0.0;
+    cplx s0 = C(1.0), s1 = C(1.0), sy0 = C(0.0), sy1 = C(1.0);
+#pragma unroll
+    for (int k = 1; k <= 18; ++k) {
+      t0 = (-(1.0 / ((double)k * k))) * (q * t0);
+      t1 = (-(1.0 / ((double)k * (k + 1)))) * (q * t1);
+      Hk += 1.0 / k;
+      s0 = s0 + t0;
+      s1 = s1 + t1;
+      sy0 = sy0 + Hk * t0;
+      sy1 = sy1 + (2.0 * Hk + 1.0 / (k + 1)) * t1;
+    }
+    const cplx L = clog_(0.5 * z) + C(EULER_GAMMA);
+    const cplx J0 = s0;
+    const cplx J1 = (0.5 * z) * s1;
+    const cplx Y0 = TWO_OVER_PI * (L * J0 - sy0);
+    const cplx Y1 = (-TWO_OVER_PI) * inv(z) + TWO_OVER_PI * (L * J1) - (0.5 * INV_PI) * (z * sy1);
+    h.J0 = J0;
+    h.J1 = J1;
+    h.H0 = J0 + mul_i(Y0);
+    h.H1 = J1 + mul_i(Y1);
+  } else if (az < 20.0) {
+    const int N = 2 * (((int)(az + 36.0)) / 2);
+    const cplx tz = 2.0 * inv(z);
+    cplx jn1 = C(0.0), jn = C(1e-30);
+    cplx norm = C(0.0), sy0 = C(0.0), sy1 = C(0.0), j1 = C(0.0);
+    for (int n = N; n >= 1; --n) {
+      // e^{-iz} = J0 + 2 sum_{n>=1} (-i)^n J_n
+      const int r = n & 3;
+      const cplx w = (r == 0) ? jn : (r == 1) ? C(jn.im, -jn.re) : (r == 2) ? -jn : C(-jn.im, jn.re);
+      norm = norm + 2.0 * w;
+      if ((n & 1) == 0) {
+        const int k = n >> 1;
+        const double sgn = (k & 1) ? -1.0 : 1.0;
+        sy0 = sy0 + (sgn / k) * jn;
+      } else {
+        const int m = n >> 1;
+        const double sgn = (m & 1) ? -1.0 : 1.0;
+        double c = -sgn / (m + 1);
+        if (m >= 1) c -= sgn / m;
+        sy1 = sy1 + c * jn;
+      }
+      const cplx jm1 = ((double)n * tz) * jn - jn1;
+      jn1 = jn;
+      jn = jm1;
+      if (n == 1) j1 = jn1;
+    }
+    norm = norm + jn;
+    // scale = e^{-iz} / norm
+    const cplx emiz = cexp_(C(z.im, -z.re));
+    const cplx sc = emiz * inv(norm);
+    const cplx J0 = jn * sc, J1 = j1 * sc;
+    const cplx L = clog_(0.5 * z) + C(EULER_GAMMA);
+    const cplx Y0 = TWO_OVER_PI * (L * J0 - 2.0 * (sy0 * sc));
+    const cplx Y1 = TWO_OVER_PI * (L * J1 - J0 * inv(z) + sy1 * sc);
+    h.J0 = J0;
+    h.J1 = J1;
+    h.H0 = J0 + mul_i(Y0);
+    h.H1 = J1 + mul_i(Y1);
+  } else {
+    const cplx r8 = 0.125 * inv(z);
+    cplx P0 = C(1.0), Q0 = C(0.0), P1 = C(1.0), Q1 = C(0.0);
+    cplx t0 = C(1.0), t1 = C(1.0);
+    for (int k = 1; k <= 40; ++k) {
+      const double o = (double)(2 * k - 1) * (2 * k - 1);
+      t0 = ((0.0 - o) / k) * (t0 * r8);
+      t1 = ((4.0 - o) / k) * (t1 * r8);
+      const int ph = k & 3;
+      if (ph == 1) { Q0 = Q0 + t0; Q1 = Q1 + t1; }
+      else if (ph == 2) { P0 = P0 - t0; P1 = P1 - t1; }
+      else if (ph == 3) { Q0 = Q0 - t0; Q1 = Q1 - t1; }
+      else { P0 = P0 + t0; P1 = P1 + t1; }
+      if (abs2(t0) < 1e-34 && abs2(t1) < 1e-34) break;
+    }
+    const cplx amp = csqrt_(TWO_OVER_PI * inv(z));
+    const cplx e = cexp_(mul_i(z));          // e^{iz}
+    const cplx em = cexp_(-mul_i(z));        // e^{-iz}
+    const cplx r0 = C(SQRT_HALF, -SQRT_HALF);   // e^{-i pi/4}
+    const cplx r1 = C(-SQRT_HALF, -SQRT_HALF);  // e^{-3 i pi/4}
+    const cplx a0 = amp * (e * r0), b0 = amp * (em * conj(r0));
+    const cplx a1 = amp * (e * r1), b1 = amp * (em * conj(r1));
+    h.H0 = (P0 + mul_i(Q0)) * a0;
+    h.H1 = (P1 + mul_i(Q1)) * a1;
+    const cplx H20 = (P0 - mul_i(Q0)) * b0;  // H^(2)
+    const cplx H21 = (P1 - mul_i(Q1)) * b1;
+    h.J0 = 0.5 * (h.H0 + H20);
+    h.J1 = 0.5 * (h.H1 + H21);
+  }
+  return h;
+}
+
+// Dispatch on whether the wavenumber is real.
+__device__ __forceinline__ Hank hankel(cplx k, double rho) {
+  if (k.im == 0.0) return hankel_real(k.re * rho);
+  return hankel_cplx(k * rho);
+}
+
+// ---------------------------------------------------------------------------
+// The four Helmholtz kernels (Sec. 2.2) at one target/source pair.
+//   S  = G,  D = dG/dn' (source normal),  Ds = dG/dn (target normal),
+//   T  = d^2 G / dn dn';   with g(r) = (i/4) H0(k r):
+//   g' = -(ik/4) H1,  g'' = -(ik^2/4)(H0 - H1/(k r)),
+//   D = -g' (u.n')/r, Ds = g' (u.n)/r,
+//   T = -[(g'' - g'/r)(u.n)(u.n')/r^2 + g' (n.n')/r].
+// K1* are the coefficients of log(4 sin^2((t-s)/2)) (without |Z'|).
+// ---------------------------------------------------------------------------
+struct Kern {
+  cplx S, D, Ds, T;
+};
+struct KernL {
+  cplx S, D, Ds, T;
+  cplx K1S, K1D, K1Ds, K1T;
+};
+
+struct Geo {
+  double rho, rinv, un, unp, nn;  // |u|, 1/|u|, (u.n)/r, (u.n')/r, n.n'
+};
+
+__device__ __forceinline__ Geo geo(double tx, double ty, double tnx, double tny, double sx, double sy,
+                                   double snx, double sny) {
+  Geo g;
+  const double ux = tx - sx, uy = ty - sy;
+  g.rho = hypot(ux, uy);
+  g.rinv = 1.0 / g.rho;
+  g.un = (ux * tnx + uy * tny) * g.rinv;
+  g.unp = (ux * snx + uy * sny) * g.rinv;
+  g.nn = tnx * snx + tny * sny;
+  return g;
+}
+
+__device__ __forceinline__ Kern kernels(cplx k, const Geo& g, const Hank& h) {
+  Kern o;
+  const cplx ik4 = 0.25 * mul_i(k);           // ik/4
+  const cplx gp = -(ik4 * h.H1);              // g'
+  const cplx zinv = inv(k * g.rho);
+  const cplx gpp = -((ik4 * k) * (h.H0 - h.H1 * zinv));
+  o.S = 0.25 * mul_i(h.H0);
+  o.D = -(gp * g.unp);
+  o.Ds = gp * g.un;
+  o.T = -((gpp - gp * g.rinv) * (g.un * g.unp) + gp * (g.nn * g.rinv));
+  return o;
+}
+
+__device__ __forceinline__ KernL kernels_log(cplx k, const Geo& g, const Hank& h) {
+  KernL o;
+  const cplx ik4 = 0.25 * mul_i(k);
+  const cplx gp = -(ik4 * h.H1);
+  const cplx zinv = inv(k * g.rho);
+  const cplx gpp = -((ik4 * k) * (h.H0 - h.H1 * zinv));
+  o.S = 0.25 * mul_i(h.H0);
+  o.D = -(gp * g.unp);
+  o.Ds = gp * g.un;
+  o.T = -((gpp - gp * g.rinv) * (g.un * g.unp) + gp * (g.nn * g.rinv));
+  const cplx kq = INV_4PI * k;
+  o.K1S = (-INV_4PI) * h.J0;
+  o.K1D = -(kq * h.J1) * g.unp;
+  o.K1Ds = (kq * h.J1) * g.un;
+  o.K1T = -((kq * k) * (h.J0 - 2.0 * (h.J1 * zinv))) * (g.un * g.unp) - (kq * h.J1) * (g.nn * g.rinv);
+  return o;
+}
+
+}  // namespace mlqp

@@ -1,0 +1,448 @@
+// Block-tridiagonal LU sweep over the layers (Cho & Barnett, Sec. 3.3) and
+// the recovery of the Bragg amplitudes (Sec. 3.3) and flux (Remark r:flux).
+//
+// Forward step i (i = 2..I) eliminates the unknowns eta_{i-1} from the
+// augmented block system
+//      [ A~_{i-1}   A'_{i-1,i} | f~_{i-1} ]   (top rows, block row i-1)
+//      [ A'_{i,i-1} A'_{i,i}   | f_i      ]   (bottom rows, block row i)
+// by a right-looking partial LU with row pivoting restricted to the top rows.
+// Afterwards the bottom-right block is A~_i = A'_{i,i} - A'_{i,i-1} A~_{i-1}^{-1}
+// A'_{i-1,i}, the bottom right-hand side is f~_i = f_i - A'_{i,i-1} A~_{i-1}^{-1}
+// f~_{i-1} (the forward sweep, with f~ read as the block-LU recursion), the top
+// blocks hold U_{i-1}, L^{-1}P A'_{i-1,i} and L^{-1}P f~_{i-1}, and the bottom-
+// left block holds the multipliers.  Everything stays in place in the block
+// rows R_{i-1}, R_i.  The backward sweep solves U_i eta_i = g_i - U12_i eta_{i+1}.
+//
+// Each panel of NB columns takes three launches: the panel factorisation
+// (one CTA per angle, panel in shared memory), the row swaps / U12 rows /
+// bottom multipliers (column- and row-parallel), and the trailing update
+// (64 x 64 tiles, complex 3M products, FP64).
+#include "mlqp_internal.h"
+#include "mlqp_math.cuh"
+
+namespace mlqp {
+
+extern thread_local long g_launches;
+
+constexpr int NB = 16;        // panel width
+constexpr int PANEL_THREADS = 256;
+constexpr int MLQP_ESINGULAR_CODE = 4;
+
+struct Step {
+  int t, b;        // top interface, bottom interface (-1: none)
+  int nt, nb;      // unknowns
+  int nlt;         // columns left of the top diagonal block
+};
+
+__device__ __forceinline__ Step make_step(const Dev& D, int t) {
+  Step s;
+  s.t = t;
+  s.b = (t + 1 < D.I) ? t + 1 : -1;
+  s.nt = D.ifc[t].n;
+  s.nb = (s.b >= 0) ? D.ifc[s.b].n : 0;
+  s.nlt = D.ifc[t].nl;
+  return s;
+}
+
+__device__ __forceinline__ double cabs1(cplx a) { return fabs(a.re) + fabs(a.im); }
+
+// ---------------------------------------------------------------------------
+// Panel factorisation: top rows k..nt-1 of the E columns k..k+w-1.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k, int only_bottom_flag) {
+  const int a = blockIdx.x;
+  const Step S = make_step(D, t);
+  const IfaceDesc ft = D.ifc[t];
+  const int w = min(NB, S.nt - k);
+  const int rows = S.nt - k;
+  double2* top = D.ROW + a * D.r_stride + ft.row_off;
+  const int ld = S.nt;
+  extern __shared__ double2 pan[];  // rows x w, column-major
+  __shared__ double s_val[PANEL_THREADS];
+  __shared__ int s_idx[PANEL_THREADS];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < rows * w; e += PANEL_THREADS) {
+    const int r = e % rows, c = e / rows;
+    pan[e] = top[(size_t)(S.nlt + k + c) * ld + k + r];
+  }
+  __syncthreads();
+  int* piv = D.LUPIV + a * D.piv_stride + ft.eta_off;
+  for (int c = 0; c < w; ++c) {
+    // pivot: max |re| + |im| over rows c..rows-1 (first index on ties)
+    double bv = -1.0;
+    int bi = c;
+    for (int r = c + tid; r < rows; r += PANEL_THREADS) {
+      const double v = cabs1(ld2(&pan[(size_t)c * rows + r]));
+      if (v > bv) { bv = v; bi = r; }
+    }
+    s_val[tid] = bv;
+    s_idx[tid] = bi;
+    __syncthreads();
+    for (int o = PANEL_THREADS / 2; o > 0; o >>= 1) {
+      if (tid < o) {
+        const double v2 = s_val[tid + o];
+        const int i2 = s_idx[tid + o];
+        if (v2 > s_val[tid] || (v2 == s_val[tid] && i2 < s_idx[tid])) {
+          s_val[tid] = v2;
+          s_idx[tid] = i2;
+        }
+      }
+      __syncthreads();
+    }
+    const int pr = s_idx[0];
+    const double pv = s_val[0];
+    if (tid == 0) {
+      piv[k + c] = k + pr;
+      if (!(pv > 0.0) || !isfinite(pv)) atomicExch(D.STATUS, MLQP_ESINGULAR_CODE);
+    }
+    // swap rows c and pr within the panel
+    if (pr != c) {
+      for (int cc = tid; cc < w; cc += PANEL_THREADS) {
+        const double2 x = pan[(size_t)cc * rows + c];
+        pan[(size_t)cc * rows + c] = pan[(size_t)cc * rows + pr];
+        pan[(size_t)cc * rows + pr] = x;
+      }
+    }
+    __syncthreads();
+    const cplx ip = inv(ld2(&pan[(size_t)c * rows + c]));
+    for (int r = c + 1 + tid; r < rows; r += PANEL_THREADS) {
+      double2* p = &pan[(size_t)c * rows + r];
+      st2(p, ld2(p) * ip);
+    }
+    __syncthreads();
+    const int nrem = rows - c - 1, crem = w - c - 1;
+    for (int e = tid; e < nrem * crem; e += PANEL_THREADS) {
+      const int r = c + 1 + e % nrem, cc = c + 1 + e / nrem;
+      double2* p = &pan[(size_t)cc * rows + r];
+      st2(p, ld2(p) - ld2(&pan[(size_t)c * rows + r]) * ld2(&pan[(size_t)cc * rows + c]));
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < rows * w; e += PANEL_THREADS) {
+    const int r = e % rows, c = e / rows;
+    top[(size_t)(S.nlt + k + c) * ld + k + r] = pan[e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row swaps on every top column outside the panel, U12 rows (forward
+// substitution with the unit-lower L11) on the trailing columns, and the
+// bottom multipliers L21 = A21 U11^{-1} on the panel columns.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_lu_prep(Dev D, int t, int k, int n_col_ctas) {
+  const int a = blockIdx.y;
+  const Step S = make_step(D, t);
+  const IfaceDesc ft = D.ifc[t];
+  const int w = min(NB, S.nt - k);
+  double2* top = D.ROW + a * D.r_stride + ft.row_off;
+  double2* ftop = D.F + a * D.f_stride + ft.rhs_off;
+  const int ldt = S.nt;
+  __shared__ double2 blk[NB * NB];  // factored top w x w block (L11 \ U11), column-major
+  __shared__ int spiv[NB];
+  for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+    const int r = e % w, c = e / w;
+    blk[c * w + r] = top[(size_t)(S.nlt + k + c) * ldt + k + r];
+  }
+  const int* piv = D.LUPIV + a * D.piv_stride + ft.eta_off;
+  for (int e = threadIdx.x; e < w; e += blockDim.x) spiv[e] = piv[k + e];
+  __syncthreads();
+  if ((int)blockIdx.x < n_col_ctas) {
+    // one thread per top column u: R_t columns [0, nlt + nt + nb) then the rhs
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ncol = S.nlt + S.nt + S.nb + 1;
+    if (u >= ncol) return;
+    const int pc0 = S.nlt + k, pc1 = S.nlt + k + w;
+    if (u >= pc0 && u < pc1) return;  // panel columns: done by the panel kernel
+    double2* col = (u == ncol - 1) ? ftop : top + (size_t)u * ldt;
+    for (int r = 0; r < w; ++r) {
+      const int pr = spiv[r];
+      if (pr != k + r) {
+        const double2 x = col[k + r];
+        col[k + r] = col[pr];
+        col[pr] = x;
+      }
+    }
+    if (u >= pc1) {
+      cplx x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < w) x[r] = ld2(&col[k + r]);
+#pragma unroll
+      for (int r = 1; r < NB; ++r) {
+        if (r < w) {
+          cplx s = x[r];
+          for (int q = 0; q < r; ++q) s = s - ld2(&blk[q * w + r]) * x[q];
+          x[r] = s;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < w) st2(&col[k + r], x[r]);
+    }
+  } else {
+    if (S.b < 0) return;
+    const int r = (blockIdx.x - n_col_ctas) * blockDim.x + threadIdx.x;
+    if (r >= S.nb) return;
+    const IfaceDesc fb = D.ifc[S.b];
+    double2* bot = D.ROW + a * D.r_stride + fb.row_off;  // left block = E columns
+    const int ldb = S.nb;
+    cplx x[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c < w) x[c] = ld2(&bot[(size_t)(k + c) * ldb + r]);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      if (c < w) {
+        cplx s = x[c];
+        for (int q = 0; q < c; ++q) s = s - x[q] * ld2(&blk[c * w + q]);
+        x[c] = s * inv(ld2(&blk[c * w + c]));
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c < w) st2(&bot[(size_t)(k + c) * ldb + r], x[c]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Trailing update: rows  v in [0, nt-k-w) (top rows k+w..) then [0, nb) (bottom),
+// columns u in [0, nt-k-w) (E), [0, nb) (T), then the rhs.
+// ---------------------------------------------------------------------------
+constexpr int UT = 64;
+
+__device__ __forceinline__ double2* row_col_ptr(double2* top, int ldt, double2* ftop, double2* bot, int ldb,
+                                                double2* fbot, const Step& S, int k, int w, int v, int u) {
+  const int tr = S.nt - k - w;  // trailing top rows / E columns
+  if (v < tr) {
+    const int row = k + w + v;
+    if (u < tr) return top + (size_t)(S.nlt + k + w + u) * ldt + row;
+    if (u < tr + S.nb) return top + (size_t)(S.nlt + S.nt + (u - tr)) * ldt + row;
+    return ftop + row;
+  }
+  const int row = v - tr;
+  if (u < tr) return bot + (size_t)(k + w + u) * ldb + row;
+  if (u < tr + S.nb) return bot + (size_t)(S.nt + (u - tr)) * ldb + row;
+  return fbot + row;
+}
+
+__global__ void __launch_bounds__(256) k_lu_update(Dev D, int t, int k) {
+  const int a = blockIdx.y;
+  const Step S = make_step(D, t);
+  const IfaceDesc ft = D.ifc[t];
+  const int w = min(NB, S.nt - k);
+  const int tr = S.nt - k - w;
+  const int nrows = tr + S.nb, ncols = tr + S.nb + 1;
+  const int tiles_c = (ncols + UT - 1) / UT;
+  const int tile_r = blockIdx.x / tiles_c, tile_c = blockIdx.x % tiles_c;
+  const int row0 = tile_r * UT, col0 = tile_c * UT;
+  if (row0 >= nrows) return;
+  double2* top = D.ROW + a * D.r_stride + ft.row_off;
+  double2* ftop = D.F + a * D.f_stride + ft.rhs_off;
+  double2* bot = nullptr;
+  double2* fbot = nullptr;
+  if (S.b >= 0) {
+    const IfaceDesc fb = D.ifc[S.b];
+    bot = D.ROW + a * D.r_stride + fb.row_off;
+    fbot = D.F + a * D.f_stride + fb.rhs_off;
+  }
+  const int ldt = S.nt, ldb = S.nb;
+  __shared__ double As[NB][3][UT];
+  __shared__ double Bs[NB][3][UT];
+  const int tid = threadIdx.x;
+  // L21 tile (rows v, panel columns): top rows -> panel's L part, bottom rows -> multipliers
+  for (int e = tid; e < UT * NB; e += 256) {
+    const int r = e % UT, kk = e / UT;
+    const int v = row0 + r;
+    double2 x = make_double2(0.0, 0.0);
+    if (v < nrows && kk < w) {
+      if (v < tr) x = top[(size_t)(S.nlt + k + kk) * ldt + k + w + v];
+      else x = bot[(size_t)(k + kk) * ldb + (v - tr)];
+    }
+    As[kk][0][r] = x.x;
+    As[kk][1][r] = x.y;
+    As[kk][2][r] = x.x + x.y;
+  }
+  // U12 tile (panel rows k..k+w-1, trailing columns u)
+  for (int e = tid; e < UT * NB; e += 256) {
+    const int kk = e % NB, c = e / NB;
+    const int u = col0 + c;
+    double2 x = make_double2(0.0, 0.0);
+    if (u < ncols && kk < w) {
+      const int row = k + kk;
+      if (u < tr) x = top[(size_t)(S.nlt + k + w + u) * ldt + row];
+      else if (u < tr + S.nb) x = top[(size_t)(S.nlt + S.nt + (u - tr)) * ldt + row];
+      else x = ftop[row];
+    }
+    Bs[kk][0][c] = x.x;
+    Bs[kk][1][c] = x.y;
+    Bs[kk][2][c] = x.x + x.y;
+  }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;
+  double t1[4][4] = {}, t2[4][4] = {}, t3[4][4] = {};
+  for (int kk = 0; kk < w; ++kk) {
+    double ar[4], ai[4], as[4], br[4], bi[4], bs[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ar[q] = As[kk][0][ty * 4 + q];
+      ai[q] = As[kk][1][ty * 4 + q];
+      as[q] = As[kk][2][ty * 4 + q];
+      br[q] = Bs[kk][0][tx * 4 + q];
+      bi[q] = Bs[kk][1][tx * 4 + q];
+      bs[q] = Bs[kk][2][tx * 4 + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int z = 0; z < 4; ++z) {
+        t1[q][z] = fma(ar[q], br[z], t1[q][z]);
+        t2[q][z] = fma(ai[q], bi[z], t2[q][z]);
+        t3[q][z] = fma(as[q], bs[z], t3[q][z]);
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int z = 0; z < 4; ++z) {
+      const int v = row0 + ty * 4 + q, u = col0 + tx * 4 + z;
+      if (v < nrows && u < ncols) {
+        double2* p = row_col_ptr(top, ldt, ftop, bot, ldb, fbot, S, k, w, v, u);
+        double2 x = *p;
+        x.x -= t1[q][z] - t2[q][z];
+        x.y -= t3[q][z] - t1[q][z] - t2[q][z];
+        *p = x;
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward sweep: y = g_t - U12_t eta_{t+1};  U_t eta_t = y.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_back_matvec(Dev D, int t) {
+  const int a = blockIdx.y;
+  const IfaceDesc ft = D.ifc[t];
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ft.n) return;
+  const double2* top = D.ROW + a * D.r_stride + ft.row_off;
+  const double2* g = D.F + a * D.f_stride + ft.rhs_off;
+  double2* eta = D.ETA + a * D.eta_stride;
+  cplx y = ld2(&g[r]);
+  if (t + 1 < D.I) {
+    const IfaceDesc fb = D.ifc[t + 1];
+    const double2* eb = eta + fb.eta_off;
+    const double2* U12 = top + (size_t)(ft.nl + ft.n) * ft.n;
+    for (int c = 0; c < fb.n; ++c) y = y - ld2(&U12[(size_t)c * ft.n + r]) * ld2(&eb[c]);
+  }
+  st2(&eta[ft.eta_off + r], y);
+}
+
+__global__ void __launch_bounds__(256) k_back_trsv(Dev D, int t) {
+  const int a = blockIdx.x;
+  const IfaceDesc ft = D.ifc[t];
+  const int n = ft.n;
+  const double2* U = D.ROW + a * D.r_stride + ft.row_off + (size_t)ft.nl * n;
+  double2* y = D.ETA + a * D.eta_stride + ft.eta_off;
+  __shared__ double2 sx;
+  for (int j = n - 1; j >= 0; --j) {
+    if (threadIdx.x == 0) {
+      const cplx v = ld2(&y[j]) * inv(ld2(&U[(size_t)j * n + j]));
+      st2(&y[j], v);
+      sx = make_double2(v.re, v.im);
+    }
+    __syncthreads();
+    const cplx v = C(sx.x, sx.y);
+    for (int r = threadIdx.x; r < j; r += blockDim.x) st2(&y[r], ld2(&y[r]) - ld2(&U[(size_t)j * n + r]) * v);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Recovery (Sec. 3.3): x_1 = -X_1 eta_1, x_{I+1} = -X_{I+1} eta_I; the Bragg
+// amplitudes are the last 2K+1 entries.  Flux error (Remark r:flux) with the
+// incident vertical flux k_1 |sin theta|.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_recover(Dev D) {
+  const int a = blockIdx.x;
+  __shared__ double sflux[128];
+  double fl = 0.0;
+  for (int e = threadIdx.x; e < 2 * D.nK; e += blockDim.x) {
+    const int which = e / D.nK, n = e % D.nK;
+    const int jl = which ? D.I : 0;
+    const int it = which ? D.I - 1 : 0;
+    const LayerDesc L = D.lay[jl];
+    const IfaceDesc f = D.ifc[it];
+    const double2* X = D.Xb + a * D.x_stride + L.x_off;
+    const double2* eta = D.ETA + a * D.eta_stride + f.eta_off;
+    cplx s = C(0.0);
+    for (int c = 0; c < f.n; ++c) s = s + ld2(&X[(size_t)c * L.p + D.P + n]) * ld2(&eta[c]);
+    s = -s;
+    st2(&D.AMP[(size_t)a * 2 * D.nK + e], s);
+    const cplx kv = ld2(which ? &D.KD[a * D.nK + n] : &D.KU[a * D.nK + n]);
+    if (kv.im == 0.0 && kv.re > 0.0) fl += kv.re * abs2(s);
+  }
+  sflux[threadIdx.x] = fl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < blockDim.x; ++q) tot += sflux[q];
+    bool real = true;
+    for (int j = 0; j <= D.I; ++j)
+      if (D.kre[2 * j + 1] != 0.0) real = false;
+    const double inc = D.kre[0] * fabs(sin(D.theta[a]));
+    D.FLUX[a] = real ? (tot - inc) / inc : __longlong_as_double(0x7ff8000000000000LL);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s) {
+  const int I = D.I;
+  cudaError_t e;
+  for (int t = 0; t < I; ++t) {
+    const int nt = n_host[t];
+    const int nb = (t + 1 < I) ? n_host[t + 1] : 0;
+    const int nlt = (t > 0) ? n_host[t - 1] : 0;
+    for (int k = 0; k < nt; k += NB) {
+      const int w = (nt - k < NB) ? nt - k : NB;
+      const size_t smem = (size_t)(nt - k) * w * sizeof(double2);
+      ++g_launches;
+      k_lu_panel<<<D.n_theta, PANEL_THREADS, smem, s>>>(D, t, k, 0);
+      const int ncol = nlt + nt + nb + 1;
+      const int n_col_ctas = (ncol + 127) / 128;
+      const int n_row_ctas = (nb + 127) / 128;
+      ++g_launches;
+      k_lu_prep<<<dim3(n_col_ctas + n_row_ctas, D.n_theta), 128, 0, s>>>(D, t, k, n_col_ctas);
+      const int tr = nt - k - w;
+      const int nrows = tr + nb, ncols = tr + nb + 1;
+      if (nrows > 0) {
+        const int tiles = ((nrows + UT - 1) / UT) * ((ncols + UT - 1) / UT);
+        ++g_launches;
+        k_lu_update<<<dim3(tiles, D.n_theta), 256, 0, s>>>(D, t, k);
+      }
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  for (int t = I - 1; t >= 0; --t) {
+    ++g_launches;
+    k_back_matvec<<<dim3((n_host[t] + 127) / 128, D.n_theta), 128, 0, s>>>(D, t);
+    ++g_launches;
+    k_back_trsv<<<D.n_theta, 256, 0, s>>>(D, t);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recover(const Dev& D, cudaStream_t s) {
+  ++g_launches;
+  k_recover<<<D.n_theta, 128, 0, s>>>(D);
+  return cudaGetLastError();
+}
+
+size_t sweep_panel_smem_max(int maxn) { return (size_t)maxn * NB * sizeof(double2); }
+
+cudaError_t sweep_configure(int maxn) {
+  const size_t smem = sweep_panel_smem_max(maxn);
+  return cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace mlqp

@@ -1,0 +1,249 @@
+"""Python binding of libmlqp (include/mlqp.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; PyTorch provides
+the device workspace, the output tensors and the stream.  The functions keep
+the C names (mlqp_setup, mlqp_bind, ...); ``Context`` bundles them for one
+problem.  Importing this module never builds anything; ``load()`` raises if
+the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmlqp.so")
+
+MLQP_OK, MLQP_EINVAL, MLQP_ENOMEM, MLQP_ECUDA, MLQP_ESINGULAR, MLQP_ETIMEOUT, MLQP_ENOTCONV, MLQP_ESTATE = range(8)
+MLQP_FP64, MLQP_MIXED = 0, 1
+STAGE_GEOM, STAGE_FILL, STAGE_LSQ, STAGE_SCHUR, STAGE_SWEEP, STAGE_RECOVER = range(6)
+BLK_ROW, BLK_B, BLK_QP, BLK_CP, BLK_X, BLK_RHS, BLK_NODES, BLK_ETA, BLK_AMP = range(9)
+
+
+class mlqp_interface(ct.Structure):
+    _fields_ = [("y0", ct.c_double), ("n_modes", ct.c_int), ("a", ct.POINTER(ct.c_double)),
+                ("b", ct.POINTER(ct.c_double)), ("n_nodes", ct.c_int)]
+
+
+class mlqp_params(ct.Structure):
+    _fields_ = [("P", ct.c_int), ("R", ct.c_double), ("Mw", ct.c_int), ("M", ct.c_int), ("K", ct.c_int),
+                ("gap_U", ct.c_double), ("gap_D", ct.c_double), ("cut_a", ct.c_double), ("cut_b", ct.c_double),
+                ("lsq_rcond", ct.c_double), ("precision", ct.c_int), ("max_refine", ct.c_int),
+                ("refine_tol", ct.c_double)]
+
+
+class MlqpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"mlqp status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmlqp.so (built in-tree by paper_1410_5003_gb300/build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmlqp.so not found at {path}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ct.CDLL(path)
+    P, I, D, Z, V = ct.c_void_p, ct.c_int, ct.c_double, ct.c_size_t, ct.c_void_p
+    lib.mlqp_setup.argtypes = [ct.POINTER(mlqp_interface), I, ct.POINTER(D), D, ct.POINTER(D), I,
+                               ct.POINTER(mlqp_params), ct.POINTER(P)]
+    lib.mlqp_setup.restype = I
+    lib.mlqp_sizes.argtypes = [P, ct.POINTER(ct.c_long), ct.POINTER(I)]
+    lib.mlqp_sizes.restype = I
+    lib.mlqp_workspace_bytes.argtypes = [P]
+    lib.mlqp_workspace_bytes.restype = Z
+    lib.mlqp_bind.argtypes = [P, V, Z, V]
+    lib.mlqp_bind.restype = I
+    lib.mlqp_solve_device.argtypes = [P, V, V, V, V]
+    lib.mlqp_solve_device.restype = I
+    lib.mlqp_check_device.argtypes = [P]
+    lib.mlqp_check_device.restype = I
+    lib.mlqp_solve.argtypes = [P, V, V, V, V]
+    lib.mlqp_solve.restype = I
+    lib.mlqp_run_stage.argtypes = [P, I]
+    lib.mlqp_run_stage.restype = I
+    lib.mlqp_block_info.argtypes = [P, I, I, I, ct.POINTER(Z), ct.POINTER(I), ct.POINTER(I), ct.POINTER(I)]
+    lib.mlqp_block_info.restype = I
+    lib.mlqp_last_error.argtypes = [P]
+    lib.mlqp_last_error.restype = ct.c_char_p
+    lib.mlqp_destroy.argtypes = [P]
+    lib.mlqp_destroy.restype = None
+    lib.mlqp_debug_hankel.argtypes = [V, I, V, V]
+    lib.mlqp_debug_hankel.restype = I
+    lib.mlqp_launch_count.argtypes = [P]
+    lib.mlqp_launch_count.restype = ct.c_long
+    lib.mlqp_upload_bytes.argtypes = [P]
+    lib.mlqp_upload_bytes.restype = Z
+    _lib = lib
+    return lib
+
+
+EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_solve_device",
+            "mlqp_check_device", "mlqp_solve", "mlqp_run_stage", "mlqp_block_info", "mlqp_last_error",
+            "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes"]
+
+
+def _check(ctx, st):
+    if st != MLQP_OK:
+        msg = load().mlqp_last_error(ctx).decode() if ctx else ""
+        raise MlqpError(st, msg)
+
+
+def _dptr(a):
+    return ct.cast(a.ctypes.data, ct.POINTER(ct.c_double))
+
+
+def make_params(p, precision=MLQP_FP64, max_refine=0, refine_tol=0.0):
+    return mlqp_params(int(p.P), float(p.R), int(p.Mw), int(p.M), int(p.K), float(p.gap_U), float(p.gap_D),
+                       float(p.cut_a), float(p.cut_b), float(p.lsq_rcond), int(precision), int(max_refine),
+                       float(refine_tol))
+
+
+def mlqp_setup(prob, precision=MLQP_FP64):
+    """prob: an object with .ifaces (y0, a, b, N), .k (complex, I+1), .d,
+    .theta, .params (P, R, Mw, M, K, gap_U, gap_D, cut_a, cut_b, lsq_rcond).
+    Returns (ctx handle, keep-alive list)."""
+    lib = load()
+    I = len(prob.ifaces)
+    keep = []
+    arr = (mlqp_interface * I)()
+    for i, f in enumerate(prob.ifaces):
+        a = np.ascontiguousarray(f.a, dtype=np.float64)
+        b = np.ascontiguousarray(f.b, dtype=np.float64)
+        keep += [a, b]
+        arr[i] = mlqp_interface(float(f.y0), len(a), _dptr(a), _dptr(b), int(f.N))
+    k = np.ascontiguousarray(np.stack([np.real(prob.k), np.imag(prob.k)], axis=1).ravel(), dtype=np.float64)
+    th = np.ascontiguousarray(prob.theta, dtype=np.float64)
+    keep += [k, th]
+    prm = make_params(prob.params, precision)
+    ctx = ct.c_void_p()
+    st = lib.mlqp_setup(arr, I, _dptr(k), float(prob.d), _dptr(th), len(th), ct.byref(prm), ct.byref(ctx))
+    if st != MLQP_OK:
+        msg = lib.mlqp_last_error(ctx).decode() if ctx.value else ""
+        if ctx.value:
+            lib.mlqp_destroy(ctx)
+        raise MlqpError(st, msg)
+    return ctx, keep
+
+
+class Context:
+    """One problem on one device: owns the host context and a torch workspace."""
+
+    def __init__(self, prob, device="cuda", stream=None, precision=MLQP_FP64):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.prob = prob
+        self.ctx, self._keep = mlqp_setup(prob, precision)
+        n_den = ct.c_long()
+        n_modes = ct.c_int()
+        _check(self.ctx, self.lib.mlqp_sizes(self.ctx, ct.byref(n_den), ct.byref(n_modes)))
+        self.n_den, self.n_modes = n_den.value, n_modes.value
+        self.n_theta = len(prob.theta)
+        self.ws_bytes = self.lib.mlqp_workspace_bytes(self.ctx)
+        self.device = torch.device(device)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self.ws_off = (-base) % 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.bind()
+
+    def bind(self):
+        _check(self.ctx, self.lib.mlqp_bind(self.ctx, ct.c_void_p(self.ws.data_ptr() + self.ws_off),
+                                            self.ws_bytes, ct.c_void_p(self.stream.cuda_stream)))
+
+    def close(self):
+        if self.ctx:
+            self.lib.mlqp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- device path -----------------------------------------------------
+    def outputs(self):
+        t = self.torch
+        return dict(eta=t.empty((self.n_theta, self.n_den), dtype=t.complex128, device=self.device),
+                    aU=t.empty((self.n_theta, self.n_modes), dtype=t.complex128, device=self.device),
+                    aD=t.empty((self.n_theta, self.n_modes), dtype=t.complex128, device=self.device),
+                    flux=t.empty((self.n_theta,), dtype=t.float64, device=self.device))
+
+    def solve_device(self, out=None, eta=True):
+        out = out or self.outputs()
+        p = lambda x: ct.c_void_p(x.data_ptr())
+        _check(self.ctx, self.lib.mlqp_solve_device(self.ctx, p(out["eta"]) if eta else None, p(out["aU"]),
+                                                    p(out["aD"]), p(out["flux"])))
+        return out
+
+    def check(self):
+        _check(self.ctx, self.lib.mlqp_check_device(self.ctx))
+
+    def host_outputs(self, eta=False, pinned=False):
+        t = self.torch
+        mk = lambda shape, dt: t.empty(shape, dtype=dt, pin_memory=pinned)
+        return dict(aU=mk((self.n_theta, self.n_modes), t.complex128),
+                    aD=mk((self.n_theta, self.n_modes), t.complex128),
+                    flux=mk((self.n_theta,), t.float64),
+                    eta=mk((self.n_theta, self.n_den), t.complex128) if eta else None)
+
+    def solve_host(self, eta=False, out=None):
+        """mlqp_solve into host buffers (torch CPU tensors; pinned if given so);
+        returns numpy views."""
+        out = out or self.host_outputs(eta)
+        p = lambda x: ct.c_void_p(x.data_ptr()) if x is not None else None
+        _check(self.ctx, self.lib.mlqp_solve(self.ctx, p(out["eta"]), p(out["aU"]), p(out["aD"]),
+                                             p(out["flux"])))
+        return {k: (v.numpy() if v is not None else None) for k, v in out.items()}
+
+    def upload_bytes(self):
+        return int(self.lib.mlqp_upload_bytes(self.ctx))
+
+    def launch_count(self):
+        return int(self.lib.mlqp_launch_count(self.ctx))
+
+    def run_stage(self, stage):
+        _check(self.ctx, self.lib.mlqp_run_stage(self.ctx, int(stage)))
+
+    def block(self, kind, index, angle=0):
+        """A torch view of a workspace block (complex128 (rows, cols) matrix,
+        or float64 (5, N) for the nodes)."""
+        t = self.torch
+        off = ct.c_size_t()
+        r, c, ld = ct.c_int(), ct.c_int(), ct.c_int()
+        _check(self.ctx, self.lib.mlqp_block_info(self.ctx, int(kind), int(index), int(angle), ct.byref(off),
+                                                  ct.byref(r), ct.byref(c), ct.byref(ld)))
+        start = self.ws_off + off.value
+        if kind == BLK_NODES:
+            v = self.ws[start:].view(t.float64)
+            return t.stack([v[q * ld.value: q * ld.value + r.value] for q in range(5)])
+        nbytes = 16 * ld.value * c.value
+        v = self.ws[start:start + nbytes].view(t.complex128).view(c.value, ld.value)
+        return v[:, :r.value].transpose(0, 1)
+
+
+def hankel_eval(k, rho, device="cuda"):
+    """H0, H1, J0, J1 of k*rho evaluated by the library's device routines."""
+    import torch
+    lib = load()
+    k = np.broadcast_to(np.asarray(k, np.complex128), np.shape(rho))
+    kr = np.stack([k.real, k.imag, np.asarray(rho, np.float64)], axis=-1).reshape(-1)
+    n = kr.size // 3
+    d_in = torch.from_numpy(np.ascontiguousarray(kr)).to(device)
+    d_out = torch.empty(8 * n, dtype=torch.float64, device=device)
+    st = lib.mlqp_debug_hankel(ct.c_void_p(d_in.data_ptr()), n, ct.c_void_p(d_out.data_ptr()),
+                               ct.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != MLQP_OK:
+        raise MlqpError(st, "mlqp_debug_hankel")
+    o = d_out.cpu().numpy().reshape(n, 4, 2)
+    return o[..., 0] + 1j * o[..., 1]

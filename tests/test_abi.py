@@ -1,0 +1,127 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+include/mlqp.h declares, validates its inputs and sizes its workspace."""
+import ctypes as ct
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from workloads import config1, config2, small_stack
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_1410_5003_gb300 import build
+    build.build()
+    from paper_1410_5003_gb300 import mlqp
+    mlqp.load()
+    return mlqp
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mlqp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mlqp_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(M):
+    lib = M.load()
+    names = declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(M.EXPORTED)
+
+
+def _setup_status(mod, prob, **over):
+    M = mod
+    p = M.make_params(prob.params)
+    for k, v in over.items():
+        setattr(p, k, v)
+    lib = M.load()
+    I = len(prob.ifaces)
+    arr = (M.mlqp_interface * I)()
+    keep = []
+    for i, f in enumerate(prob.ifaces):
+        a = np.ascontiguousarray(f.a, float)
+        b = np.ascontiguousarray(f.b, float)
+        keep += [a, b]
+        arr[i] = M.mlqp_interface(f.y0, len(a), M._dptr(a), M._dptr(b), f.N)
+    k = np.ascontiguousarray(np.stack([prob.k.real, prob.k.imag], 1).ravel())
+    th = np.ascontiguousarray(prob.theta, float)
+    ctx = ct.c_void_p()
+    st = lib.mlqp_setup(arr, I, M._dptr(k), prob.d, M._dptr(th), len(th), ct.byref(p), ct.byref(ctx))
+    msg = lib.mlqp_last_error(ctx).decode() if ctx.value else ""
+    size = lib.mlqp_workspace_bytes(ctx) if ctx.value else 0
+    if ctx.value:
+        lib.mlqp_destroy(ctx)
+    return st, msg, size
+
+
+def test_setup_accepts_valid_problems(M):
+    for prob in (config1(), config2(), small_stack(I=3)):
+        st, msg, size = _setup_status(M, prob)
+        assert st == M.MLQP_OK, msg
+        assert size > 0
+
+
+@pytest.mark.parametrize("mutate, field", [
+    (lambda p: setattr(p.ifaces[0], "N", 101), "odd N"),
+    (lambda p: setattr(p, "theta", np.array([0.3])), "theta"),
+    (lambda p: setattr(p, "k", np.array([5.0 + 0.1j, 10.0])), "complex k1"),
+    (lambda p: setattr(p, "k", np.array([5.0, -10.0])), "negative k"),
+])
+def test_setup_rejects_invalid_problems(M, mutate, field):
+    prob = config1()
+    mutate(prob)
+    st, msg, _ = _setup_status(M, prob)
+    assert st == M.MLQP_EINVAL, field
+    assert msg
+
+
+def test_setup_rejects_bad_parameters(M):
+    prob = config1()
+    assert _setup_status(M, prob, M=10)[0] == M.MLQP_EINVAL           # M < 2K + 1
+    assert _setup_status(M, prob, cut_b=4.0)[0] == M.MLQP_EINVAL      # window wider than pi
+    assert _setup_status(M, prob, lsq_rcond=0.0)[0] == M.MLQP_EINVAL
+    assert _setup_status(M, prob, precision=7)[0] == M.MLQP_EINVAL
+
+
+def test_setup_rejects_overlapping_interfaces(M):
+    prob = small_stack(I=2)
+    prob.ifaces[1].y0 = prob.ifaces[0].y0
+    st, msg, _ = _setup_status(M, prob)
+    assert st == M.MLQP_EINVAL and "separated" in msg
+
+
+def test_workspace_grows_with_angles(M):
+    p1 = small_stack(I=3, n_angles=1)
+    p4 = small_stack(I=3, n_angles=4)
+    s1 = _setup_status(M, p1)[2]
+    s4 = _setup_status(M, p4)[2]
+    assert s4 > 3 * s1 * 0.9
+
+
+def test_bind_checks_size_and_alignment_before_any_device_work(M):
+    lib = M.load()
+    ctx, keep = M.mlqp_setup(config1())
+    need = lib.mlqp_workspace_bytes(ctx)
+    # a fake, never dereferenced address: both checks fail before any CUDA call
+    assert lib.mlqp_bind(ctx, ct.c_void_p(0x100000), need - 1, None) == M.MLQP_ENOMEM
+    assert lib.mlqp_bind(ctx, ct.c_void_p(0x100001), need, None) == M.MLQP_EINVAL
+    assert lib.mlqp_solve_device(ctx, None, None, None, None) == M.MLQP_ESTATE
+    lib.mlqp_destroy(ctx)
+
+
+def test_product_path_does_not_import_the_oracle():
+    """The package and its binding never reference the oracle."""
+    pkg = os.path.join(ROOT, "paper_1410_5003_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in txt.replace("oracle_", ""), f

@@ -1,0 +1,287 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Stage by stage on the same inputs: special functions, nodes and every filled
+block (A, B, Q', C', f), the least-squares kernel (against the oracle's
+solution of the GPU's own blocks and against LAPACK on a well-conditioned
+synthetic block), the Schur update and the block sweep (exact identities on
+the GPU's own blocks), then end to end: Bragg amplitudes within 1e-9
+relative (max over all 2(2K+1) orders of an angle) on small stacks, the flat
+Fresnel case, lossy layers, uneven node counts and the full 20-interface,
+3-angle benchmark stack."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+from scipy.special import hankel1, jv  # noqa: E402
+
+from oracle import mlqp_oracle as O  # noqa: E402
+from workloads import config1, config2, small_stack, flat_stack  # noqa: E402
+from workloads.problems import Interface, Params, Problem  # noqa: E402
+from tests.closed_forms import fresnel  # noqa: E402
+
+AMP_TOL = 1e-9      # relative, max over the orders of an angle
+BLOCK_TOL = 1e-11   # relative to the block's largest entry
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1410_5003_gb300 import build
+    build.build()
+    from paper_1410_5003_gb300 import mlqp
+    mlqp.load()
+    return mlqp
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def uneven_stack():
+    """Three interfaces with different node counts (ragged blocks, tails)."""
+    rng = np.random.default_rng(77)
+    ifs = []
+    for i, N in enumerate((72, 90, 56)):
+        m = np.arange(1, 4)
+        ifs.append(Interface(-1.5 * (i + 1), rng.normal(0, 0.04 / m), rng.normal(0, 0.04 / m), N))
+    p = Params(P=60, R=1.5 * 2 * math.pi, Mw=40, M=40, K=10, gap_U=0.15 * 2 * math.pi,
+               gap_D=0.15 * 2 * math.pi)
+    return Problem(2 * math.pi, [4.2, 5.5, 3.9 + 0.2j, 6.1], [-1.0, -2.2], ifs, p, name="uneven")
+
+
+# ---------------------------------------------------------------------------
+def test_hankel_functions_match_scipy(M):
+    """FP64 H0, H1, J0, J1 (series / Miller-Neumann / asymptotic regimes and
+    their switch points) against SciPy's AMOS routines, for real wavenumbers
+    and absorbing ones with Im k / Re k up to 0.1."""
+    for k in (1.0, 12.0 + 0.5j, 3.0 + 0.3j):
+        z_abs = np.concatenate([np.linspace(1e-3, 60, 6001), [3.9999999, 4.0, 4.0000001, 19.9999999, 20.0,
+                                                               20.0000001, 250.0, 1000.0]])
+        rho = z_abs / abs(k)
+        out = M.hankel_eval(k, rho)
+        z = k * rho
+        for q, ref in enumerate((hankel1(0, z), hankel1(1, z), jv(0, z), jv(1, z))):
+            err = np.abs(out[:, q] - ref) / np.maximum(np.abs(ref), 1.0)
+            assert err.max() < 5e-14, (k, q, err.max(), z[np.argmax(err)])
+
+
+PROBLEMS = {
+    "config1": lambda: config1(),
+    "flat": lambda: config1(flat=True),
+    "small3": lambda: small_stack(I=3, N=80, P=60, Mw=40, K=10, M=40),
+    "small3_lossy": lambda: small_stack(I=3, N=80, P=60, Mw=40, K=10, M=40, lossy=True),
+    "uneven": uneven_stack,
+}
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_fill_blocks_match_oracle(M, name):
+    """Nodes, A_{i,i}, A_{i,i+-1}, B, Q', C' and f equal the oracle's blocks."""
+    prob = PROBLEMS[name]()
+    ctx = M.Context(prob)
+    ctx.run_stage(M.STAGE_GEOM)
+    ctx.run_stage(M.STAGE_FILL)
+    torch.cuda.synchronize()
+    asm = O.Assembler(prob)
+    I, P = prob.I, prob.params.P
+    for a in range(prob.n_theta):
+        bl = O.bloch(prob, prob.theta[a])
+        al = bl["alpha"]
+        for i in range(1, I + 1):
+            nd = O.interface_nodes(prob.ifaces[i - 1], prob.d)
+            g = ctx.block(M.BLK_NODES, i).cpu().numpy()
+            for q, ref in enumerate((nd.x, nd.y, nd.nx, nd.ny, nd.speed)):
+                assert rel(g[q], ref) < 1e-13
+            row = ctx.block(M.BLK_ROW, i, a).cpu().numpy()
+            n = 2 * prob.ifaces[i - 1].N
+            nl = 2 * prob.ifaces[i - 2].N if i > 1 else 0
+            assert rel(row[:, nl:nl + n], asm.A(i, i, al)) < BLOCK_TOL
+            if i < I:
+                assert rel(row[:, nl + n:], asm.A(i, i + 1, al)) < BLOCK_TOL
+            if i > 1:
+                assert rel(row[:, :nl], asm.A(i, i - 1, al)) < BLOCK_TOL
+            B = ctx.block(M.BLK_B, i).cpu().numpy()
+            assert rel(B[:, :P], asm.B(i, i)) < BLOCK_TOL
+            assert rel(B[:, P:], asm.B(i, i + 1)) < BLOCK_TOL
+        for j in range(1, I + 2):
+            assert rel(ctx.block(M.BLK_QP, j, a).cpu().numpy(), asm.Qp(j, al, bl)) < BLOCK_TOL
+            assert rel(ctx.block(M.BLK_CP, j, a).cpu().numpy(), asm.Cp(j, al)) < BLOCK_TOL
+        f = ctx.block(M.BLK_RHS, 1, a).cpu().numpy()[:, 0]
+        assert rel(f, O.rhs(prob, prob.theta[a])) < 1e-13
+    ctx.close()
+
+
+def test_lsq_kernel_on_well_conditioned_blocks(M):
+    """The regularised QR kernel on synthetic well-conditioned Q', C'
+    (written into the workspace): X equals LAPACK least squares."""
+    prob = small_stack(I=2, N=40, P=30, Mw=24, K=5, M=24)
+    ctx = M.Context(prob)
+    ctx.run_stage(M.STAGE_GEOM)
+    ctx.run_stage(M.STAGE_FILL)
+    rng = np.random.default_rng(3)
+    refs = {}
+    for j in range(1, prob.I + 2):
+        Q = ctx.block(M.BLK_QP, j, 0)
+        C = ctx.block(M.BLK_CP, j, 0)
+        q = rng.standard_normal(Q.shape) + 1j * rng.standard_normal(Q.shape)
+        c = rng.standard_normal(C.shape) + 1j * rng.standard_normal(C.shape)
+        Q.copy_(torch.from_numpy(q))
+        C.copy_(torch.from_numpy(c))
+        refs[j] = np.linalg.lstsq(q, c, rcond=None)[0]
+    ctx.run_stage(M.STAGE_LSQ)
+    torch.cuda.synchronize()
+    for j in refs:
+        assert rel(ctx.block(M.BLK_X, j, 0).cpu().numpy(), refs[j]) < 1e-11
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["config1", "small3_lossy", "uneven"])
+def test_lsq_schur_sweep_stages(M, name):
+    """LSQ: X solves the regularised problem of the GPU's own Q', C' (fitted
+    values to 1e-12; X itself to 1e-5, its conditioning is 1/lam).  Schur:
+    A' = A - B X exactly on the GPU's blocks.  Sweep: eta solves the dense
+    A' to backward error 1e-13.  Recovery: a = -X eta."""
+    prob = PROBLEMS[name]()
+    ctx = M.Context(prob)
+    ctx.run_stage(M.STAGE_GEOM)
+    ctx.run_stage(M.STAGE_FILL)
+    torch.cuda.synchronize()
+    I, P = prob.I, prob.params.P
+    rcond = prob.params.lsq_rcond
+    Qs = {(j, a): ctx.block(M.BLK_QP, j, a).cpu().numpy().copy() for j in range(1, I + 2) for a in range(prob.n_theta)}
+    Cs = {(j, a): ctx.block(M.BLK_CP, j, a).cpu().numpy().copy() for j in range(1, I + 2) for a in range(prob.n_theta)}
+    rows0 = {(i, a): ctx.block(M.BLK_ROW, i, a).cpu().numpy().copy() for i in range(1, I + 1) for a in range(prob.n_theta)}
+    Bs = {i: ctx.block(M.BLK_B, i).cpu().numpy().copy() for i in range(1, I + 1)}
+    ctx.run_stage(M.STAGE_LSQ)
+    torch.cuda.synchronize()
+    Xs = {}
+    for (j, a), Q in Qs.items():
+        X = ctx.block(M.BLK_X, j, a).cpu().numpy().copy()
+        Xo = O.lsq(Q, Cs[(j, a)], rcond)
+        assert rel(Q @ X, Q @ Xo) < 1e-12
+        assert rel(X, Xo) < 1e-5
+        Xs[(j, a)] = X
+    ctx.run_stage(M.STAGE_SCHUR)
+    torch.cuda.synchronize()
+    n = [2 * f.N for f in prob.ifaces]
+
+    def xcols(j, i, a):
+        off = 0
+        for ii in O.layer_columns(prob, j):
+            if ii == i:
+                return Xs[(j, a)][:P, off:off + n[i - 1]]
+            off += n[ii - 1]
+
+    dense = {}
+    for a in range(prob.n_theta):
+        Ad, Al, Au, f = {}, {}, {}, {}
+        for i in range(1, I + 1):
+            row = ctx.block(M.BLK_ROW, i, a).cpu().numpy().copy()
+            r0 = rows0[(i, a)]
+            nl = n[i - 2] if i > 1 else 0
+            ni = n[i - 1]
+            ref_d = r0[:, nl:nl + ni] - Bs[i][:, :P] @ xcols(i, i, a) - Bs[i][:, P:] @ xcols(i + 1, i, a)
+            assert rel(row[:, nl:nl + ni], ref_d) < 1e-12
+            Ad[i] = row[:, nl:nl + ni]
+            if i < I:
+                ref_u = r0[:, nl + ni:] - Bs[i][:, P:] @ xcols(i + 1, i + 1, a)
+                assert rel(row[:, nl + ni:], ref_u) < 1e-12
+                Au[i] = row[:, nl + ni:]
+            if i > 1:
+                ref_l = r0[:, :nl] - Bs[i][:, :P] @ xcols(i, i - 1, a)
+                assert rel(row[:, :nl], ref_l) < 1e-12
+                Al[i] = row[:, :nl]
+            f[i] = ctx.block(M.BLK_RHS, i, a).cpu().numpy()[:, 0].copy()
+        dense[a] = O.dense_reduced_system(prob, dict(Ad=Ad, Al=Al, Au=Au, f=f))
+    ctx.run_stage(M.STAGE_SWEEP)
+    ctx.run_stage(M.STAGE_RECOVER)
+    ctx.check()
+    nK = 2 * prob.params.K + 1
+    for a in range(prob.n_theta):
+        A, fv = dense[a]
+        eta = np.concatenate([ctx.block(M.BLK_ETA, i, a).cpu().numpy()[:, 0] for i in range(1, I + 1)])
+        back = np.linalg.norm(A @ eta - fv) / (np.linalg.norm(A, 2) * np.linalg.norm(eta) + np.linalg.norm(fv))
+        assert back < 1e-13
+        amp = ctx.block(M.BLK_AMP, 1, a).cpu().numpy()[:, 0]
+        aU = -(Xs[(1, a)][P:] @ eta[:n[0]])
+        aD = -(Xs[(I + 1, a)][P:] @ eta[-n[-1]:])
+        assert rel(amp, np.concatenate([aU, aD])) < 1e-12
+        assert amp.shape == (2 * nK,)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_end_to_end_amplitudes_match_oracle(M, name):
+    prob = PROBLEMS[name]()
+    ctx = M.Context(prob)
+    out = ctx.solve_host(eta=True)
+    asm = O.Assembler(prob)
+    for a in range(prob.n_theta):
+        r = O.solve(prob, a, asm)
+        ag = np.concatenate([out["aU"][a], out["aD"][a]])
+        ao = np.concatenate([r["aU"], r["aD"]])
+        assert rel(ag, ao) < AMP_TOL, (name, a, rel(ag, ao))
+        if math.isnan(r["flux"]):
+            assert math.isnan(out["flux"][a])
+        else:
+            assert abs(out["flux"][a] - r["flux"]) < 1e-9
+    if name == "flat":
+        th = float(prob.theta[0])
+        rr, tt, q1, q2 = fresnel(5.0, 10.0, th)
+        K = prob.params.K
+        assert abs(out["aU"][0, K] - rr * np.exp(1j * q1 * O.y_upper(prob))) < 5e-10
+        assert abs(out["aD"][0, K] - tt * np.exp(-1j * q2 * O.y_lower(prob))) < 5e-10
+    ctx.close()
+
+
+def test_benchmark_stack_parity_all_angles(M):
+    """The 20-interface stack with a lossy layer and three angles (one 1e-8
+    past a Wood anomaly) in the launch configuration the benchmark times."""
+    prob = config2()
+    ctx = M.Context(prob)
+    out = ctx.solve_device()
+    ctx.check()
+    aU, aD = out["aU"].cpu().numpy(), out["aD"].cpu().numpy()
+    asm = O.Assembler(prob)
+    for a in range(prob.n_theta):
+        r = O.solve(prob, a, asm)
+        ag = np.concatenate([aU[a], aD[a]])
+        ao = np.concatenate([r["aU"], r["aD"]])
+        assert rel(ag, ao) < AMP_TOL, (a, rel(ag, ao))
+    assert torch.isnan(out["flux"]).all()  # a lossy layer: flux undefined (Remark r:flux)
+    ctx.close()
+
+
+def test_repeated_solves_are_bitwise_identical(M):
+    """No atomics on the numeric path: reruns reproduce every bit."""
+    prob = small_stack(I=3, N=64, P=50, Mw=30, K=8, M=30)
+    ctx = M.Context(prob)
+    o1 = ctx.solve_host(eta=True)
+    o2 = ctx.solve_host(eta=True)
+    assert np.array_equal(o1["eta"], o2["eta"])
+    assert np.array_equal(o1["aU"], o2["aU"]) and np.array_equal(o1["aD"], o2["aD"])
+    ctx.close()
+
+
+def test_zero_pivot_is_reported_not_faulted(M):
+    """A singular diagonal block (zeroed on the host side of the workspace
+    between stages) gives MLQP_ESINGULAR, and the context stays usable."""
+    prob = small_stack(I=2, N=40, P=30, Mw=24, K=5, M=24)
+    ctx = M.Context(prob)
+    for s in (M.STAGE_GEOM, M.STAGE_FILL, M.STAGE_LSQ, M.STAGE_SCHUR):
+        ctx.run_stage(s)
+    row = ctx.block(M.BLK_ROW, 1, 0)
+    row.zero_()
+    ctx.run_stage(M.STAGE_SWEEP)
+    with pytest.raises(M.MlqpError) as e:
+        ctx.check()
+    assert e.value.status == M.MLQP_ESINGULAR
+    out = ctx.solve_host()   # a fresh solve refills everything
+    assert np.all(np.isfinite(out["aU"]))
+    ctx.close()

@@ -151,13 +151,13 @@ def test_pivoted_qr_semantics():
     R2, P2 = sla.qr(A, mode="r", pivoting=True)
     assert r == 25
     assert np.allclose(np.abs(np.diag(R)), np.abs(np.diag(R2[0] if isinstance(R2, tuple) else R2)), rtol=1e-12)
-    X = O.lsq(A, B, 1e-10)
+    X = O.lsq_pivoted(A, B, 1e-10)
     assert np.allclose(X, np.linalg.lstsq(A, B, rcond=None)[0], atol=1e-12)
     # rank 10 matrix
     L = rng.standard_normal((40, 10)) + 1j * rng.standard_normal((40, 10))
     Rr = rng.standard_normal((10, 25))
     A2 = L @ Rr
-    X2 = O.lsq(A2, B, 1e-10)
+    X2 = O.lsq_pivoted(A2, B, 1e-10)
     _, _, piv2, r2 = O.pivoted_qr(A2, 1e-10)
     assert r2 == 10
     assert np.all(X2[piv2[10:]] == 0)
@@ -175,3 +175,36 @@ def test_self_convergence_in_N():
     d2 = np.max(np.abs(vals[2] - vals[1]))
     d3 = np.max(np.abs(vals[3] - vals[2]))
     assert d2 < 0.3 * d1 and d3 < 0.3 * d2 and d3 < 1e-9
+
+
+def test_regularised_lsq_definition():
+    """lsq() is the minimiser of ||Q X - C||^2 + lam^2 ||X||^2 with
+    lam = rcond * max column norm: it satisfies the normal equations
+    (Q^H Q + lam^2 I) X = Q^H C, and for a well-conditioned full-rank Q with
+    rcond -> 0 it tends to the least-squares solution."""
+    rng = np.random.default_rng(9)
+    Q = rng.standard_normal((50, 20)) + 1j * rng.standard_normal((50, 20))
+    C = rng.standard_normal((50, 6)) + 1j * rng.standard_normal((50, 6))
+    rc = 1e-3
+    lam = rc * np.max(np.linalg.norm(Q, axis=0))
+    X = O.lsq(Q, C, rc)
+    lhs = (Q.conj().T @ Q + lam ** 2 * np.eye(20)) @ X
+    assert np.allclose(lhs, Q.conj().T @ C, atol=1e-11)
+    X0 = O.lsq(Q, C, 1e-14)
+    assert np.allclose(X0, np.linalg.lstsq(Q, C, rcond=None)[0], atol=1e-11)
+
+
+def test_regularised_and_pivoted_lsq_agree_on_amplitudes():
+    """The two readings of the per-layer 'backslash' (Sec. 3.2) give the same
+    Bragg amplitudes to discretisation accuracy on resolved problems."""
+    for prob in (config1(N=140, P=80, Mw=60), small_stack(I=3, N=80, P=60, Mw=40, K=10, M=40)):
+        asm = O.Assembler(prob)
+        r = O.solve(prob, 0, asm)
+        orig = O.lsq
+        O.lsq = O.lsq_pivoted
+        try:
+            rp = O.solve(prob, 0, asm)
+        finally:
+            O.lsq = orig
+        scale = np.max(np.abs(_amps(r)))
+        assert np.max(np.abs(_amps(r) - _amps(rp))) < 1e-9 * scale

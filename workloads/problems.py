@@ -48,8 +48,8 @@ class Params:
                                             max Gamma_1 / of D below min Gamma_I
     cut_a, cut_b  the smooth window of the periodic log-split: 1 for |t-s|<=a,
                   0 for |t-s| >= b (parameter units, 0 <= a < b <= pi)
-    lsq_rcond     numerical-rank tolerance of the per-layer least-squares
-                  solves, relative to the largest pivot |R_11|
+    lsq_rcond     regularisation of the per-layer least-squares solves,
+                  relative to the largest column norm of Q'_j
     """
     P: int = 60
     R: float = 1.5 * 2 * math.pi
