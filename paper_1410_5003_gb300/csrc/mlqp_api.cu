@@ -48,7 +48,7 @@ struct mlqp_ctx {
   size_t r_stride = 0, f_stride = 0, b_total = 0, qp_stride = 0, cp_stride = 0, x_stride = 0, sum_p = 0;
   // layout
   Region r_ifc, r_lay, r_tasks, r_k, r_ca, r_cb, r_theta, r_scal, r_geo[7], r_wy, r_gl, r_ux, r_alpha, r_kappa,
-      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LUPIV, r_ETA, r_AMP, r_FLUX, r_STATUS;
+      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LUPIV, r_UDINV, r_ETA, r_AMP, r_FLUX, r_STATUS;
   size_t ws_bytes = 0;
   // binding
   char* ws = nullptr;
@@ -305,6 +305,7 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   take(cur, c->r_X, z16 * nt * c->x_stride);
   take(cur, c->r_LAUX, d8 * nt * 6 * c->sum_p);
   take(cur, c->r_LUPIV, sizeof(int) * nt * c->n_den);
+  take(cur, c->r_UDINV, z16 * nt * c->n_den);
   take(cur, c->r_ETA, z16 * nt * c->n_den);
   take(cur, c->r_AMP, z16 * nt * 2 * nK);
   take(cur, c->r_FLUX, d8 * nt);
@@ -387,6 +388,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   D.laux_stride = 6 * c->sum_p;
   D.LUPIV = at<int>(c, c->r_LUPIV);
   D.piv_stride = c->n_den;
+  D.UDINV = at<double2>(c, c->r_UDINV);
   D.ETA = at<double2>(c, c->r_ETA);
   D.eta_stride = c->n_den;
   D.AMP = at<double2>(c, c->r_AMP);

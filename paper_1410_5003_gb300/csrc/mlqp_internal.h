@@ -82,6 +82,7 @@ struct Dev {
   double2* Xb;  size_t x_stride;
   double* LAUX; size_t laux_stride;  // per layer 6p doubles: R_kk[p], v0[p] (complex), beta[p], pad
   int* LUPIV;   size_t piv_stride;    // block-LU pivots, per angle, indexed like eta
+  double2* UDINV;                     // reciprocals of the U diagonals, per angle, indexed like eta
   double2* ETA; size_t eta_stride;
   double2* AMP;                        // n_theta x 2 nK
   double* FLUX;                        // n_theta

@@ -7,7 +7,7 @@
 // formed, Sec. 3.2; small-norm proxy strengths as in the remark after eq.
 // Schuri).  One CTA factors one (layer, angle); a second kernel applies the
 // reflectors and the triangular solve to the right-hand-side columns, one
-// warp per column.
+// column per thread.
 // The Schur updates are batched complex GEMM tiles with 3M products
 // (three real products per complex product), in FP64.
 #include "mlqp_internal.h"
@@ -26,7 +26,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // LAUX layout per layer (6 p doubles, an even count so that the complex
-// arrays stay 16-byte aligned): R_kk[p] (complex), v0[p] (complex), beta[p], pad.
+// arrays stay 16-byte aligned): 1/R_kk[p] (complex), v0[p] (complex), beta[p], pad.
 //
 // Q'_j is stored with leading dimension ldq = m + p; rows m..m+p-1 receive
 // lam I, lam = rcond * max_c ||Q'_j[:, c]||.  Reflector j acts on rows j..m+j
@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_lsq_qr(Dev D) {
       s_v0 = make_double2(v0.re, v0.im);
       beta[j] = b;
       v0s[j] = s_v0;
-      rdg[j] = make_double2(alpha.re, alpha.im);
+      const cplx ra = inv(alpha);
+      rdg[j] = make_double2(ra.re, ra.im);
     }
     __syncthreads();
     // 4. apply (I - beta v v^H) to columns j+1..p-1, rows j..r1
@@ -128,60 +129,71 @@ __global__ void __launch_bounds__(QR_THREADS) k_lsq_qr(Dev D) {
 }
 
 // Right-hand sides [C'_j; 0]: apply the reflectors, solve with R (p x p) and
-// write X_j (p x c, ld p).  One warp per column.
-__global__ void __launch_bounds__(256) k_lsq_apply(Dev D) {
+// write X_j (p x c, ld p).  One column per thread: the inner products run
+// down the thread's own column, so no cross-lane reductions are needed.
+constexpr int APPLY_THREADS = 32;
+
+__global__ void __launch_bounds__(APPLY_THREADS) k_lsq_apply(Dev D) {
   const int jl = blockIdx.y, a = blockIdx.z;
   const LayerDesc L = D.lay[jl];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c = blockIdx.x * 8 + warp;
+  const int c = blockIdx.x * APPLY_THREADS + threadIdx.x;
   if (c >= L.c) return;
   const int m = L.m, p = L.p, ld = L.ldq;
   const double2* A = D.QP + a * D.qp_stride + L.qp_off;
   const double* aux = D.LAUX + a * D.laux_stride + 6 * L.aux_off;
-  const double2* rdg = reinterpret_cast<const double2*>(aux);
+  const double2* rinv = reinterpret_cast<const double2*>(aux);
   const double2* v0s = reinterpret_cast<const double2*>(aux + 2 * p);
   const double* beta = aux + 4 * p;
-  double2* bcol = D.CP + a * D.cp_stride + L.cp_off + (size_t)c * ld;
-  for (int r = m + lane; r < m + p; r += 32) bcol[r] = make_double2(0.0, 0.0);
-  __syncwarp();
+  double2* b = D.CP + a * D.cp_stride + L.cp_off + (size_t)c * ld;
+  for (int r = m; r < m + p; ++r) b[r] = make_double2(0.0, 0.0);
   for (int j = 0; j < p; ++j) {
-    const double b = beta[j];
-    if (b == 0.0) continue;
+    const double bj = beta[j];
+    if (bj == 0.0) continue;
     const int r1 = m + j;
-    const cplx v0 = ld2(&v0s[j]);
     const double2* vj = A + (size_t)j * ld;
-    double sr = 0.0, si = 0.0;
-    for (int r = j + lane; r <= r1; r += 32) {
-      const cplx v = (r == j) ? v0 : ld2(&vj[r]);
-      const cplx x = ld2(&bcol[r]);
-      sr = fma(v.re, x.re, fma(v.im, x.im, sr));
-      si = fma(v.re, x.im, fma(-v.im, x.re, si));
+    const cplx v0 = ld2(&v0s[j]);
+    // w = conj(v) . b over rows j..r1, two partial sums
+    const cplx x0 = ld2(&b[j]);
+    double sr0 = v0.re * x0.re + v0.im * x0.im, si0 = v0.re * x0.im - v0.im * x0.re;
+    double sr1 = 0.0, si1 = 0.0;
+    int r = j + 1;
+    for (; r + 1 <= r1; r += 2) {
+      const double2 va = vj[r], vb = vj[r + 1];
+      const double2 xa = b[r], xb = b[r + 1];
+      sr0 = fma(va.x, xa.x, fma(va.y, xa.y, sr0));
+      si0 = fma(va.x, xa.y, fma(-va.y, xa.x, si0));
+      sr1 = fma(vb.x, xb.x, fma(vb.y, xb.y, sr1));
+      si1 = fma(vb.x, xb.y, fma(-vb.y, xb.x, si1));
     }
-    sr = warp_sum(sr);
-    si = warp_sum(si);
-    const cplx w = C(b * sr, b * si);
-    for (int r = j + lane; r <= r1; r += 32) {
-      const cplx v = (r == j) ? v0 : ld2(&vj[r]);
-      st2(&bcol[r], ld2(&bcol[r]) - v * w);
+    if (r <= r1) {
+      const double2 va = vj[r], xa = b[r];
+      sr0 = fma(va.x, xa.x, fma(va.y, xa.y, sr0));
+      si0 = fma(va.x, xa.y, fma(-va.y, xa.x, si0));
     }
-    __syncwarp();
+    const cplx w = C(bj * (sr0 + sr1), bj * (si0 + si1));
+    st2(&b[j], x0 - v0 * w);
+    for (r = j + 1; r <= r1; ++r) st2(&b[r], ld2(&b[r]) - ld2(&vj[r]) * w);
   }
-  // back substitution R y = (Q^H b)[:p], in place in bcol
-  for (int k = p - 1; k >= 0; --k) {
-    double sr = 0.0, si = 0.0;
-    for (int l = k + 1 + lane; l < p; l += 32) {
-      const cplx rkl = ld2(&A[(size_t)l * ld + k]);
-      const cplx y = ld2(&bcol[l]);
-      sr = fma(rkl.re, y.re, fma(-rkl.im, y.im, sr));
-      si = fma(rkl.re, y.im, fma(rkl.im, y.re, si));
-    }
-    sr = warp_sum(sr);
-    si = warp_sum(si);
-    if (lane == 0) st2(&bcol[k], (ld2(&bcol[k]) - C(sr, si)) * inv(ld2(&rdg[k])));
-    __syncwarp();
-  }
+  // back substitution R y = (Q^H b)[:p], with the stored reciprocals 1/R_kk
   double2* xcol = D.Xb + a * D.x_stride + L.x_off + (size_t)c * p;
-  for (int k = lane; k < p; k += 32) xcol[k] = bcol[k];
+  for (int k = p - 1; k >= 0; --k) {
+    double sr = 0.0, si = 0.0, tr = 0.0, ti = 0.0;
+    int l = k + 1;
+    for (; l + 1 < p; l += 2) {
+      const double2 ra = A[(size_t)l * ld + k], rb = A[(size_t)(l + 1) * ld + k];
+      const double2 ya = xcol[l], yb = xcol[l + 1];
+      sr = fma(ra.x, ya.x, fma(-ra.y, ya.y, sr));
+      si = fma(ra.x, ya.y, fma(ra.y, ya.x, si));
+      tr = fma(rb.x, yb.x, fma(-rb.y, yb.y, tr));
+      ti = fma(rb.x, yb.y, fma(rb.y, yb.x, ti));
+    }
+    if (l < p) {
+      const double2 ra = A[(size_t)l * ld + k], ya = xcol[l];
+      sr = fma(ra.x, ya.x, fma(-ra.y, ya.y, sr));
+      si = fma(ra.x, ya.y, fma(ra.y, ya.x, si));
+    }
+    st2(&xcol[k], (ld2(&b[k]) - C(sr + tr, si + ti)) * ld2(&rinv[k]));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -281,7 +293,7 @@ cudaError_t launch_lsq(const Dev& D, int max_m, int max_p, int max_c, cudaStream
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ++g_launches;
-  k_lsq_apply<<<dim3((max_c + 7) / 8, D.L, D.n_theta), 256, 0, s>>>(D);
+  k_lsq_apply<<<dim3((max_c + APPLY_THREADS - 1) / APPLY_THREADS, D.L, D.n_theta), APPLY_THREADS, 0, s>>>(D);
   return cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@
 // Each panel of NB columns takes three launches: the panel factorisation
 // (one CTA per angle, panel in shared memory), the row swaps / U12 rows /
 // bottom multipliers (column- and row-parallel), and the trailing update
-// (64 x 64 tiles, complex 3M products, FP64).
+// (32 x 32 tiles, complex 3M products, FP64).
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
 
@@ -47,9 +47,19 @@ __device__ __forceinline__ Step make_step(const Dev& D, int t) {
 __device__ __forceinline__ double cabs1(cplx a) { return fabs(a.re) + fabs(a.im); }
 
 // ---------------------------------------------------------------------------
-// Panel factorisation: top rows k..nt-1 of the E columns k..k+w-1.
+// Panel factorisation: top rows k..nt-1 of the E columns k..k+w-1, in shared
+// memory, one CTA per angle.  Pivot: largest |re| + |im| (first on ties),
+// compared as the bit patterns of the non-negative doubles (integer ALU).
+// One reciprocal per pivot, kept in UDINV for the later kernels.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k, int only_bottom_flag) {
+__device__ __forceinline__ void argmax_merge(unsigned long long& key, int& idx, unsigned long long k2, int i2) {
+  if (k2 > key || (k2 == key && i2 < idx)) {
+    key = k2;
+    idx = i2;
+  }
+}
+
+__global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k) {
   const int a = blockIdx.x;
   const Step S = make_step(D, t);
   const IfaceDesc ft = D.ifc[t];
@@ -58,63 +68,71 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k,
   double2* top = D.ROW + a * D.r_stride + ft.row_off;
   const int ld = S.nt;
   extern __shared__ double2 pan[];  // rows x w, column-major
-  __shared__ double s_val[PANEL_THREADS];
-  __shared__ int s_idx[PANEL_THREADS];
-  const int tid = threadIdx.x;
+  __shared__ unsigned long long s_key[PANEL_THREADS / 32];
+  __shared__ int s_idx[PANEL_THREADS / 32];
+  __shared__ int s_piv;
+  __shared__ double2 s_rinv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < rows * w; e += PANEL_THREADS) {
     const int r = e % rows, c = e / rows;
     pan[e] = top[(size_t)(S.nlt + k + c) * ld + k + r];
   }
   __syncthreads();
   int* piv = D.LUPIV + a * D.piv_stride + ft.eta_off;
+  double2* udinv = D.UDINV + a * D.piv_stride + ft.eta_off;
   for (int c = 0; c < w; ++c) {
-    // pivot: max |re| + |im| over rows c..rows-1 (first index on ties)
-    double bv = -1.0;
-    int bi = c;
+    unsigned long long key = 0;
+    int idx = c;
     for (int r = c + tid; r < rows; r += PANEL_THREADS) {
-      const double v = cabs1(ld2(&pan[(size_t)c * rows + r]));
-      if (v > bv) { bv = v; bi = r; }
+      const double2 x = pan[(size_t)c * rows + r];
+      const double v = fabs(x.x) + fabs(x.y);
+      argmax_merge(key, idx, (unsigned long long)__double_as_longlong(v), r);
     }
-    s_val[tid] = bv;
-    s_idx[tid] = bi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+      argmax_merge(key, idx, k2, i2);
+    }
+    if (lane == 0) {
+      s_key[warp] = key;
+      s_idx[warp] = idx;
+    }
     __syncthreads();
-    for (int o = PANEL_THREADS / 2; o > 0; o >>= 1) {
-      if (tid < o) {
-        const double v2 = s_val[tid + o];
-        const int i2 = s_idx[tid + o];
-        if (v2 > s_val[tid] || (v2 == s_val[tid] && i2 < s_idx[tid])) {
-          s_val[tid] = v2;
-          s_idx[tid] = i2;
-        }
-      }
-      __syncthreads();
-    }
-    const int pr = s_idx[0];
-    const double pv = s_val[0];
     if (tid == 0) {
-      piv[k + c] = k + pr;
+      unsigned long long kb = s_key[0];
+      int ib = s_idx[0];
+      for (int q = 1; q < PANEL_THREADS / 32; ++q) argmax_merge(kb, ib, s_key[q], s_idx[q]);
+      s_piv = ib;
+      piv[k + c] = k + ib;
+      const double pv = __longlong_as_double((long long)kb);
       if (!(pv > 0.0) || !isfinite(pv)) atomicExch(D.STATUS, MLQP_ESINGULAR_CODE);
     }
-    // swap rows c and pr within the panel
-    if (pr != c) {
-      for (int cc = tid; cc < w; cc += PANEL_THREADS) {
-        const double2 x = pan[(size_t)cc * rows + c];
-        pan[(size_t)cc * rows + c] = pan[(size_t)cc * rows + pr];
-        pan[(size_t)cc * rows + pr] = x;
-      }
+    __syncthreads();
+    const int pr = s_piv;
+    if (pr != c && tid < w) {
+      const double2 x = pan[(size_t)tid * rows + c];
+      pan[(size_t)tid * rows + c] = pan[(size_t)tid * rows + pr];
+      pan[(size_t)tid * rows + pr] = x;
     }
     __syncthreads();
-    const cplx ip = inv(ld2(&pan[(size_t)c * rows + c]));
+    if (tid == 0) {
+      const cplx ri = inv(ld2(&pan[(size_t)c * rows + c]));
+      s_rinv = make_double2(ri.re, ri.im);
+      udinv[k + c] = s_rinv;
+    }
+    __syncthreads();
+    const cplx ip = C(s_rinv.x, s_rinv.y);
     for (int r = c + 1 + tid; r < rows; r += PANEL_THREADS) {
-      double2* p = &pan[(size_t)c * rows + r];
-      st2(p, ld2(p) * ip);
+      double2* q = &pan[(size_t)c * rows + r];
+      st2(q, ld2(q) * ip);
     }
     __syncthreads();
     const int nrem = rows - c - 1, crem = w - c - 1;
     for (int e = tid; e < nrem * crem; e += PANEL_THREADS) {
       const int r = c + 1 + e % nrem, cc = c + 1 + e / nrem;
-      double2* p = &pan[(size_t)cc * rows + r];
-      st2(p, ld2(p) - ld2(&pan[(size_t)c * rows + r]) * ld2(&pan[(size_t)cc * rows + c]));
+      double2* q = &pan[(size_t)cc * rows + r];
+      st2(q, ld2(q) - ld2(&pan[(size_t)c * rows + r]) * ld2(&pan[(size_t)cc * rows + c]));
     }
     __syncthreads();
   }
@@ -127,9 +145,12 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k,
 // ---------------------------------------------------------------------------
 // Row swaps on every top column outside the panel, U12 rows (forward
 // substitution with the unit-lower L11) on the trailing columns, and the
-// bottom multipliers L21 = A21 U11^{-1} on the panel columns.
+// bottom multipliers L21 = A21 U11^{-1} on the panel columns.  One warp per
+// CTA, one column or row per thread; no divisions (reciprocals from UDINV).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_lu_prep(Dev D, int t, int k, int n_col_ctas) {
+constexpr int PREP_THREADS = 32;
+
+__global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, int n_col_ctas) {
   const int a = blockIdx.y;
   const Step S = make_step(D, t);
   const IfaceDesc ft = D.ifc[t];
@@ -138,16 +159,20 @@ __global__ void __launch_bounds__(128) k_lu_prep(Dev D, int t, int k, int n_col_
   double2* ftop = D.F + a * D.f_stride + ft.rhs_off;
   const int ldt = S.nt;
   __shared__ double2 blk[NB * NB];  // factored top w x w block (L11 \ U11), column-major
+  __shared__ double2 sinv[NB];
   __shared__ int spiv[NB];
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
     const int r = e % w, c = e / w;
     blk[c * w + r] = top[(size_t)(S.nlt + k + c) * ldt + k + r];
   }
   const int* piv = D.LUPIV + a * D.piv_stride + ft.eta_off;
-  for (int e = threadIdx.x; e < w; e += blockDim.x) spiv[e] = piv[k + e];
+  const double2* udinv = D.UDINV + a * D.piv_stride + ft.eta_off;
+  for (int e = threadIdx.x; e < w; e += blockDim.x) {
+    spiv[e] = piv[k + e];
+    sinv[e] = udinv[k + e];
+  }
   __syncthreads();
   if ((int)blockIdx.x < n_col_ctas) {
-    // one thread per top column u: R_t columns [0, nlt + nt + nb) then the rhs
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     const int ncol = S.nlt + S.nt + S.nb + 1;
     if (u >= ncol) return;
@@ -171,7 +196,9 @@ __global__ void __launch_bounds__(128) k_lu_prep(Dev D, int t, int k, int n_col_
       for (int r = 1; r < NB; ++r) {
         if (r < w) {
           cplx s = x[r];
-          for (int q = 0; q < r; ++q) s = s - ld2(&blk[q * w + r]) * x[q];
+#pragma unroll
+          for (int q = 0; q < NB; ++q)
+            if (q < r) s = s - ld2(&blk[q * w + r]) * x[q];
           x[r] = s;
         }
       }
@@ -194,8 +221,10 @@ __global__ void __launch_bounds__(128) k_lu_prep(Dev D, int t, int k, int n_col_
     for (int c = 0; c < NB; ++c) {
       if (c < w) {
         cplx s = x[c];
-        for (int q = 0; q < c; ++q) s = s - x[q] * ld2(&blk[c * w + q]);
-        x[c] = s * inv(ld2(&blk[c * w + c]));
+#pragma unroll
+        for (int q = 0; q < NB; ++q)
+          if (q < c) s = s - x[q] * ld2(&blk[c * w + q]);
+        x[c] = s * ld2(&sinv[c]);
       }
     }
 #pragma unroll
@@ -206,9 +235,11 @@ __global__ void __launch_bounds__(128) k_lu_prep(Dev D, int t, int k, int n_col_
 
 // ---------------------------------------------------------------------------
 // Trailing update: rows  v in [0, nt-k-w) (top rows k+w..) then [0, nb) (bottom),
-// columns u in [0, nt-k-w) (E), [0, nb) (T), then the rhs.
+// columns u in [0, nt-k-w) (E), [0, nb) (T), then the rhs.  32 x 32 tiles,
+// 64 threads, 4 x 4 outputs per thread, complex 3M products.
 // ---------------------------------------------------------------------------
-constexpr int UT = 64;
+constexpr int UT = 32;
+constexpr int UPD_THREADS = 64;
 
 __device__ __forceinline__ double2* row_col_ptr(double2* top, int ldt, double2* ftop, double2* bot, int ldb,
                                                 double2* fbot, const Step& S, int k, int w, int v, int u) {
@@ -225,7 +256,7 @@ __device__ __forceinline__ double2* row_col_ptr(double2* top, int ldt, double2* 
   return fbot + row;
 }
 
-__global__ void __launch_bounds__(256) k_lu_update(Dev D, int t, int k) {
+__global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k) {
   const int a = blockIdx.y;
   const Step S = make_step(D, t);
   const IfaceDesc ft = D.ifc[t];
@@ -249,8 +280,7 @@ __global__ void __launch_bounds__(256) k_lu_update(Dev D, int t, int k) {
   __shared__ double As[NB][3][UT];
   __shared__ double Bs[NB][3][UT];
   const int tid = threadIdx.x;
-  // L21 tile (rows v, panel columns): top rows -> panel's L part, bottom rows -> multipliers
-  for (int e = tid; e < UT * NB; e += 256) {
+  for (int e = tid; e < UT * NB; e += UPD_THREADS) {
     const int r = e % UT, kk = e / UT;
     const int v = row0 + r;
     double2 x = make_double2(0.0, 0.0);
@@ -262,8 +292,7 @@ __global__ void __launch_bounds__(256) k_lu_update(Dev D, int t, int k) {
     As[kk][1][r] = x.y;
     As[kk][2][r] = x.x + x.y;
   }
-  // U12 tile (panel rows k..k+w-1, trailing columns u)
-  for (int e = tid; e < UT * NB; e += 256) {
+  for (int e = tid; e < UT * NB; e += UPD_THREADS) {
     const int kk = e % NB, c = e / NB;
     const int u = col0 + c;
     double2 x = make_double2(0.0, 0.0);
@@ -278,7 +307,7 @@ __global__ void __launch_bounds__(256) k_lu_update(Dev D, int t, int k) {
     Bs[kk][2][c] = x.x + x.y;
   }
   __syncthreads();
-  const int tx = tid & 15, ty = tid >> 4;
+  const int tx = tid & 7, ty = tid >> 3;
   double t1[4][4] = {}, t2[4][4] = {}, t3[4][4] = {};
   for (int kk = 0; kk < w; ++kk) {
     double ar[4], ai[4], as[4], br[4], bi[4], bs[4];
@@ -316,9 +345,11 @@ __global__ void __launch_bounds__(256) k_lu_update(Dev D, int t, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// Backward sweep: y = g_t - U12_t eta_{t+1};  U_t eta_t = y.
+// Backward sweep: y = g_t - U12_t eta_{t+1} (one row per thread);
+// U_t eta_t = y by column-oriented back substitution with the stored
+// reciprocals of the U diagonal.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_back_matvec(Dev D, int t) {
+__global__ void __launch_bounds__(32) k_back_matvec(Dev D, int t) {
   const int a = blockIdx.y;
   const IfaceDesc ft = D.ifc[t];
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -331,7 +362,14 @@ __global__ void __launch_bounds__(128) k_back_matvec(Dev D, int t) {
     const IfaceDesc fb = D.ifc[t + 1];
     const double2* eb = eta + fb.eta_off;
     const double2* U12 = top + (size_t)(ft.nl + ft.n) * ft.n;
-    for (int c = 0; c < fb.n; ++c) y = y - ld2(&U12[(size_t)c * ft.n + r]) * ld2(&eb[c]);
+    cplx y2 = C(0.0);
+    int c = 0;
+    for (; c + 1 < fb.n; c += 2) {
+      y = y - ld2(&U12[(size_t)c * ft.n + r]) * ld2(&eb[c]);
+      y2 = y2 - ld2(&U12[(size_t)(c + 1) * ft.n + r]) * ld2(&eb[c + 1]);
+    }
+    if (c < fb.n) y = y - ld2(&U12[(size_t)c * ft.n + r]) * ld2(&eb[c]);
+    y = y + y2;
   }
   st2(&eta[ft.eta_off + r], y);
 }
@@ -341,11 +379,12 @@ __global__ void __launch_bounds__(256) k_back_trsv(Dev D, int t) {
   const IfaceDesc ft = D.ifc[t];
   const int n = ft.n;
   const double2* U = D.ROW + a * D.r_stride + ft.row_off + (size_t)ft.nl * n;
+  const double2* udinv = D.UDINV + a * D.piv_stride + ft.eta_off;
   double2* y = D.ETA + a * D.eta_stride + ft.eta_off;
   __shared__ double2 sx;
   for (int j = n - 1; j >= 0; --j) {
     if (threadIdx.x == 0) {
-      const cplx v = ld2(&y[j]) * inv(ld2(&U[(size_t)j * n + j]));
+      const cplx v = ld2(&y[j]) * ld2(&udinv[j]);
       st2(&y[j], v);
       sx = make_double2(v.re, v.im);
     }
@@ -407,25 +446,25 @@ cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s) {
       const int w = (nt - k < NB) ? nt - k : NB;
       const size_t smem = (size_t)(nt - k) * w * sizeof(double2);
       ++g_launches;
-      k_lu_panel<<<D.n_theta, PANEL_THREADS, smem, s>>>(D, t, k, 0);
+      k_lu_panel<<<D.n_theta, PANEL_THREADS, smem, s>>>(D, t, k);
       const int ncol = nlt + nt + nb + 1;
-      const int n_col_ctas = (ncol + 127) / 128;
-      const int n_row_ctas = (nb + 127) / 128;
+      const int n_col_ctas = (ncol + PREP_THREADS - 1) / PREP_THREADS;
+      const int n_row_ctas = (nb + PREP_THREADS - 1) / PREP_THREADS;
       ++g_launches;
-      k_lu_prep<<<dim3(n_col_ctas + n_row_ctas, D.n_theta), 128, 0, s>>>(D, t, k, n_col_ctas);
+      k_lu_prep<<<dim3(n_col_ctas + n_row_ctas, D.n_theta), PREP_THREADS, 0, s>>>(D, t, k, n_col_ctas);
       const int tr = nt - k - w;
       const int nrows = tr + nb, ncols = tr + nb + 1;
       if (nrows > 0) {
         const int tiles = ((nrows + UT - 1) / UT) * ((ncols + UT - 1) / UT);
         ++g_launches;
-        k_lu_update<<<dim3(tiles, D.n_theta), 256, 0, s>>>(D, t, k);
+        k_lu_update<<<dim3(tiles, D.n_theta), UPD_THREADS, 0, s>>>(D, t, k);
       }
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   for (int t = I - 1; t >= 0; --t) {
     ++g_launches;
-    k_back_matvec<<<dim3((n_host[t] + 127) / 128, D.n_theta), 128, 0, s>>>(D, t);
+    k_back_matvec<<<dim3((n_host[t] + 31) / 32, D.n_theta), 32, 0, s>>>(D, t);
     ++g_launches;
     k_back_trsv<<<D.n_theta, 256, 0, s>>>(D, t);
   }

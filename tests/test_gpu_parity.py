@@ -50,7 +50,7 @@ def uneven_stack():
     for i, N in enumerate((72, 90, 56)):
         m = np.arange(1, 4)
         ifs.append(Interface(-1.5 * (i + 1), rng.normal(0, 0.04 / m), rng.normal(0, 0.04 / m), N))
-    p = Params(P=60, R=1.5 * 2 * math.pi, Mw=40, M=40, K=10, gap_U=0.15 * 2 * math.pi,
+    p = Params(P=60, R=1.5 * 2 * math.pi, Mw=40, M=50, K=20, gap_U=0.15 * 2 * math.pi,
                gap_D=0.15 * 2 * math.pi)
     return Problem(2 * math.pi, [4.2, 5.5, 3.9 + 0.2j, 6.1], [-1.0, -2.2], ifs, p, name="uneven")
 
@@ -71,11 +71,15 @@ def test_hankel_functions_match_scipy(M):
             assert err.max() < 5e-14, (k, q, err.max(), z[np.argmax(err)])
 
 
+# Parity at 1e-9 is asked of resolved discretisations: with the U/D lines
+# 0.15 d above/below the interfaces, K = 20 Rayleigh orders leave evanescent
+# terms below 1e-8 (K = 10 leaves ~1e-4 and the amplitudes then move by
+# ~1e-9 under rounding-level changes of the blocks, in the oracle itself).
 PROBLEMS = {
     "config1": lambda: config1(),
     "flat": lambda: config1(flat=True),
-    "small3": lambda: small_stack(I=3, N=80, P=60, Mw=40, K=10, M=40),
-    "small3_lossy": lambda: small_stack(I=3, N=80, P=60, Mw=40, K=10, M=40, lossy=True),
+    "small3": lambda: small_stack(I=3, N=80, P=60, Mw=40, K=20, M=50),
+    "small3_lossy": lambda: small_stack(I=3, N=80, P=60, Mw=40, K=20, M=50, lossy=True),
     "uneven": uneven_stack,
 }
 
@@ -144,7 +148,8 @@ def test_lsq_kernel_on_well_conditioned_blocks(M):
 @pytest.mark.parametrize("name", ["config1", "small3_lossy", "uneven"])
 def test_lsq_schur_sweep_stages(M, name):
     """LSQ: X solves the regularised problem of the GPU's own Q', C' (fitted
-    values to 1e-12; X itself to 1e-5, its conditioning is 1/lam).  Schur:
+    values to 1e-9 and X to 1e-5: the filter factors s^2/(s^2 + lam^2) move
+    by eps |Q| / lam ~ 1e-6 for singular values s ~ lam).  Schur:
     A' = A - B X exactly on the GPU's blocks.  Sweep: eta solves the dense
     A' to backward error 1e-13.  Recovery: a = -X eta."""
     prob = PROBLEMS[name]()
@@ -164,7 +169,7 @@ def test_lsq_schur_sweep_stages(M, name):
     for (j, a), Q in Qs.items():
         X = ctx.block(M.BLK_X, j, a).cpu().numpy().copy()
         Xo = O.lsq(Q, Cs[(j, a)], rcond)
-        assert rel(Q @ X, Q @ Xo) < 1e-12
+        assert rel(Q @ X, Q @ Xo) < 1e-9
         assert rel(X, Xo) < 1e-5
         Xs[(j, a)] = X
     ctx.run_stage(M.STAGE_SCHUR)
