@@ -179,6 +179,32 @@ size_t mlqp_upload_bytes(const mlqp_ctx* ctx);
 /* Kernel launches this context has issued so far (all stages, all solves). */
 long mlqp_launch_count(const mlqp_ctx* ctx);
 
+/* One regularised least-squares solve without any device allocation (the
+ * paper has no counterpart: this is an interface for callers that cannot
+ * allocate device memory -- code running under a fixed preallocated memory
+ * budget, inside a host callback, or from a runtime without a device
+ * allocator -- and so cannot provide the workspace mlqp_bind needs).
+ * Computes X = argmin ||Q X - C||^2 + lam^2 ||X||^2, lam = rcond * (largest
+ * column norm of Q), by the same Householder QR of [Q; lam I] as the
+ * per-layer solves of the device path.  Q (m x p, leading dimension ldq),
+ * C (m x nc, ldc) and X (p x nc, ldx) are interleaved complex128,
+ * column-major, in device memory owned by the caller; work is queued on
+ * `stream` and the call returns without synchronising.
+ * Scratch is one fixed device array inside the library (4 MiB, held by every
+ * GPU that loads the library until the process exits): the problem must
+ * satisfy (m + p)(p + nc) + 3p <= 262144 complex entries, else MLQP_ENOMEM
+ * is returned before any device work.  Every call overwrites the scratch it
+ * uses before reading it; calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race on the shared array and must be
+ * serialised by the caller.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  No cudaMalloc, cudaFree
+ * or allocating library routine is called.
+ * Errors: MLQP_EINVAL (sizes, leading dimensions, rcond not in (0, 1), null
+ * pointers), MLQP_ENOMEM (beyond the fixed scratch), MLQP_ECUDA. */
+mlqp_status mlqp_lsq_solve_noalloc(const void* d_Q, int m, int p, int ldq, const void* d_C, int nc, int ldc,
+                                   double rcond, void* d_X, int ldx, void* stream);
+
 /* Message of the last error on this context ("" if none). */
 const char* mlqp_last_error(const mlqp_ctx* ctx);
 

@@ -82,13 +82,16 @@ def load(path: str = LIB_PATH):
     lib.mlqp_launch_count.restype = ct.c_long
     lib.mlqp_upload_bytes.argtypes = [P]
     lib.mlqp_upload_bytes.restype = Z
+    lib.mlqp_lsq_solve_noalloc.argtypes = [V, I, I, I, V, I, I, D, V, I, V]
+    lib.mlqp_lsq_solve_noalloc.restype = I
     _lib = lib
     return lib
 
 
 EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_solve_device",
             "mlqp_check_device", "mlqp_solve", "mlqp_run_stage", "mlqp_block_info", "mlqp_last_error",
-            "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes"]
+            "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes",
+            "mlqp_lsq_solve_noalloc"]
 
 
 def _check(ctx, st):
