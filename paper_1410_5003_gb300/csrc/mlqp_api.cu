@@ -21,6 +21,7 @@ cudaError_t launch_schur(const Dev& D, int max_tiles, cudaStream_t s);
 cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s);
 cudaError_t launch_recover(const Dev& D, cudaStream_t s);
 cudaError_t sweep_configure(int maxn);
+cudaError_t lsq_configure(int max_m, int max_p);
 cudaError_t launch_hankel_eval(const double* kr, int n, double* out, cudaStream_t s);
 extern thread_local long g_launches;
 }  // namespace mlqp
@@ -45,10 +46,11 @@ struct mlqp_ctx {
   std::vector<int> n_host;
   int maxN = 0, maxn = 0, total_nodes = 0, max_m = 0, max_p = 0, max_c = 0, max_tiles = 0;
   long n_den = 0;
-  size_t r_stride = 0, f_stride = 0, b_total = 0, qp_stride = 0, cp_stride = 0, x_stride = 0, sum_p = 0;
+  size_t r_stride = 0, f_stride = 0, b_total = 0, qp_stride = 0, cp_stride = 0, x_stride = 0, sum_p = 0,
+         t_stride = 0;
   // layout
   Region r_ifc, r_lay, r_tasks, r_k, r_ca, r_cb, r_theta, r_scal, r_geo[7], r_wy, r_gl, r_ux, r_alpha, r_kappa,
-      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LUPIV, r_UDINV, r_ETA, r_AMP, r_FLUX, r_STATUS;
+      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ETA, r_AMP, r_FLUX, r_STATUS;
   size_t ws_bytes = 0;
   // binding
   char* ws = nullptr;
@@ -195,7 +197,7 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   // layers
   const int nK = 2 * q.K + 1;
   c->lay.resize(c->L);
-  size_t qo = 0, co = 0, xo = 0, ao = 0;
+  size_t qo = 0, co = 0, xo = 0, ao = 0, to = 0;
   for (int j = 0; j < c->L; ++j) {
     LayerDesc& Ly = c->lay[j];
     Ly.end = (j == 0) ? 1 : (j == I) ? 2 : 0;
@@ -215,6 +217,8 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
     xo += (size_t)Ly.p * Ly.c;
     Ly.aux_off = ao;
     ao += Ly.p;
+    Ly.t_off = to;
+    to += (size_t)256 * ((Ly.p + 15) / 16);
     Ly.ybot = Ly.ytop = Ly.cy = 0;
     c->max_m = std::max(c->max_m, Ly.m);
     c->max_p = std::max(c->max_p, Ly.p);
@@ -224,6 +228,7 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   c->cp_stride = co;
   c->x_stride = xo;
   c->sum_p = ao;
+  c->t_stride = to;
   // Schur tasks (eqs. Schur1-Schuri), see mlqp_internal.h
   auto tiles = [](int r, int cc) { return ((r + 63) / 64) * ((cc + 63) / 64); };
   for (int i = 0; i < I; ++i) {
@@ -304,8 +309,10 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   take(cur, c->r_CP, z16 * nt * c->cp_stride);
   take(cur, c->r_X, z16 * nt * c->x_stride);
   take(cur, c->r_LAUX, d8 * nt * 6 * c->sum_p);
+  take(cur, c->r_LT, z16 * nt * c->t_stride);
   take(cur, c->r_LUPIV, sizeof(int) * nt * c->n_den);
   take(cur, c->r_UDINV, z16 * nt * c->n_den);
+  take(cur, c->r_PERM, sizeof(int) * nt * 80);
   take(cur, c->r_ETA, z16 * nt * c->n_den);
   take(cur, c->r_AMP, z16 * nt * 2 * nK);
   take(cur, c->r_FLUX, d8 * nt);
@@ -386,9 +393,12 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   D.x_stride = c->x_stride;
   D.LAUX = at<double>(c, c->r_LAUX);
   D.laux_stride = 6 * c->sum_p;
+  D.LT = at<double2>(c, c->r_LT);
+  D.lt_stride = c->t_stride;
   D.LUPIV = at<int>(c, c->r_LUPIV);
   D.piv_stride = c->n_den;
   D.UDINV = at<double2>(c, c->r_UDINV);
+  D.PERM = at<int>(c, c->r_PERM);
   D.ETA = at<double2>(c, c->r_ETA);
   D.eta_stride = c->n_den;
   D.AMP = at<double2>(c, c->r_AMP);
@@ -423,6 +433,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   cudaError_t e = cudaMemcpyAsync(c->ws, c->staging, hdr, cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "descriptor upload");
   if ((e = sweep_configure(c->maxn)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
+  if ((e = lsq_configure(c->max_m, c->max_p)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
   c->bound = true;
   return MLQP_OK;
 }

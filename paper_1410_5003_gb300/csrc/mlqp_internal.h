@@ -36,6 +36,7 @@ struct LayerDesc {
   size_t cp_off;
   size_t x_off;
   size_t aux_off;  // sum of p over the previous layers (LSQ auxiliaries at 6 aux_off doubles)
+  size_t t_off;    // offset of this layer's block-reflector factors T (16 x 16 complex per block)
   double ybot, ytop, cy;  // wall extent and proxy-circle centre (filled on the device)
 };
 
@@ -80,9 +81,11 @@ struct Dev {
   double2* QP;  size_t qp_stride;
   double2* CP;  size_t cp_stride;
   double2* Xb;  size_t x_stride;
-  double* LAUX; size_t laux_stride;  // per layer 6p doubles: R_kk[p], v0[p] (complex), beta[p], pad
+  double* LAUX; size_t laux_stride;  // per layer 6p doubles: 1/R_kk[p], v0[p] (complex), beta[p], pad
+  double2* LT; size_t lt_stride;      // block reflector factors T of the least-squares QRs, per angle
   int* LUPIV;   size_t piv_stride;    // block-LU pivots, per angle, indexed like eta
   double2* UDINV;                     // reciprocals of the U diagonals, per angle, indexed like eta
+  int* PERM;                          // per angle 80 ints: row map of the current panel's swaps
   double2* ETA; size_t eta_stride;
   double2* AMP;                        // n_theta x 2 nK
   double* FLUX;                        // n_theta

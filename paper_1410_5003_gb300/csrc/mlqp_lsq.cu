@@ -5,9 +5,9 @@
 // lam^2 ||X||^2, lam = rcond * (largest column norm of Q'), solved by
 // Householder QR of [Q'; lam I] (backward stable, the pseudo-inverse is never
 // formed, Sec. 3.2; small-norm proxy strengths as in the remark after eq.
-// Schuri).  One CTA factors one (layer, angle); a second kernel applies the
-// reflectors and the triangular solve to the right-hand-side columns, one
-// column per thread.
+// Schuri).  One CTA factors one (layer, angle); the reflectors are then
+// applied to the right-hand sides 16 at a time in compact WY form and X is
+// obtained by a blocked back substitution (rows x columns parallel).
 // The Schur updates are batched complex GEMM tiles with 3M products
 // (three real products per complex product), in FP64.
 #include "mlqp_internal.h"
@@ -128,71 +128,185 @@ __global__ void __launch_bounds__(QR_THREADS) k_lsq_qr(Dev D) {
   }
 }
 
-// Right-hand sides [C'_j; 0]: apply the reflectors, solve with R (p x p) and
-// write X_j (p x c, ld p).  One column per thread: the inner products run
-// down the thread's own column, so no cross-lane reductions are needed.
-constexpr int APPLY_THREADS = 32;
+// Right-hand sides [C'_j; 0]: the reflectors are applied 16 at a time in
+// compact WY form, H_{j0+15}...H_{j0} = I - V T^H V^H (T upper triangular,
+// LAPACK's forward column-wise convention), then X = R^{-1} (Q^H [C'; 0])[:p]
+// by a blocked back substitution.  Every step is parallel over rows and
+// columns; the only serial chains are 16 long.
+constexpr int WYB = 16;
+constexpr int WY_THREADS = 256;
 
-__global__ void __launch_bounds__(APPLY_THREADS) k_lsq_apply(Dev D) {
+// Column i of block b of V (rows r_lo .. r_lo + nr - 1, r_lo = 16 b), as stored by k_lsq_qr.
+__device__ __forceinline__ double2 wy_v(const double2* A, const double2* v0s, int ld, int m, int j0, int w, int row,
+                                        int i) {
+  if (i >= w) return make_double2(0.0, 0.0);
+  const int jg = j0 + i;
+  if (row == jg) return v0s[jg];
+  if (row > jg && row <= m + jg) return A[(size_t)jg * ld + row];
+  return make_double2(0.0, 0.0);
+}
+
+__global__ void __launch_bounds__(WY_THREADS) k_lsq_T(Dev D) {
+  const int b = blockIdx.x, jl = blockIdx.y, a = blockIdx.z;
+  const LayerDesc L = D.lay[jl];
+  const int m = L.m, p = L.p, ld = L.ldq;
+  if (b * WYB >= p) return;
+  const int j0 = b * WYB, w = min(WYB, p - j0), nr = m + w;
+  const double2* A = D.QP + a * D.qp_stride + L.qp_off;
+  const double* aux = D.LAUX + a * D.laux_stride + 6 * L.aux_off;
+  const double2* v0s = reinterpret_cast<const double2*>(aux + 2 * p);
+  const double* beta = aux + 4 * p;
+  extern __shared__ double2 smem_t[];
+  double2* V = smem_t;  // nr x 16, column-major
+  __shared__ double2 G[WYB * WYB], T[WYB * WYB];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nr * WYB; e += WY_THREADS) {
+    const int r = e % nr, i = e / nr;
+    V[e] = wy_v(A, v0s, ld, m, j0, w, j0 + r, i);
+  }
+  __syncthreads();
+  {
+    const int i = tid / WYB, q = tid % WYB;  // G[i][q] = v_i^H v_q
+    double sr = 0.0, si = 0.0;
+    for (int r = 0; r < nr; ++r) {
+      const double2 x = V[i * nr + r], y = V[q * nr + r];
+      sr = fma(x.x, y.x, fma(x.y, y.y, sr));
+      si = fma(x.x, y.y, fma(-x.y, y.x, si));
+    }
+    G[q * WYB + i] = make_double2(sr, si);  // column-major: G(i, q)
+    T[tid] = make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  if (tid < WYB && tid < w) T[tid * WYB + tid] = make_double2(beta[j0 + tid], 0.0);
+  __syncthreads();
+  for (int i = 1; i < w; ++i) {
+    // T(0:i, i) = -beta_i T(0:i, 0:i) G(0:i, i)
+    if (tid < i) {
+      cplx s = C(0.0);
+      for (int q2 = tid; q2 < i; ++q2) s = s + ld2(&T[q2 * WYB + tid]) * ld2(&G[i * WYB + q2]);
+      st2(&T[i * WYB + tid], (-beta[j0 + i]) * s);
+    }
+    __syncthreads();
+  }
+  double2* Tout = D.LT + a * D.lt_stride + L.t_off + (size_t)b * WYB * WYB;
+  Tout[tid] = T[tid];
+}
+
+__global__ void __launch_bounds__(WY_THREADS) k_lsq_wy(Dev D, int b) {
   const int jl = blockIdx.y, a = blockIdx.z;
   const LayerDesc L = D.lay[jl];
-  const int c = blockIdx.x * APPLY_THREADS + threadIdx.x;
-  if (c >= L.c) return;
   const int m = L.m, p = L.p, ld = L.ldq;
+  if (b * WYB >= p) return;
+  const int c0 = blockIdx.x * WYB;
+  if (c0 >= L.c) return;
+  const int ncol = min(WYB, L.c - c0);
+  const int j0 = b * WYB, w = min(WYB, p - j0), nr = m + w;
+  const double2* A = D.QP + a * D.qp_stride + L.qp_off;
+  const double* aux = D.LAUX + a * D.laux_stride + 6 * L.aux_off;
+  const double2* v0s = reinterpret_cast<const double2*>(aux + 2 * p);
+  double2* Bg = D.CP + a * D.cp_stride + L.cp_off + (size_t)c0 * ld;
+  extern __shared__ double2 smem_w[];
+  double2* V = smem_w;             // nr x 16
+  double2* Bt = smem_w + nr * WYB;  // nr x 16 (rows r_lo.., columns c0..)
+  __shared__ double2 T[WYB * WYB], W[WYB * WYB], W2[WYB * WYB];
+  const int tid = threadIdx.x;
+  if (b == 0) {
+    for (int e = tid; e < p * ncol; e += WY_THREADS) {
+      const int r = e % p, c = e / p;
+      Bg[(size_t)c * ld + m + r] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nr * WYB; e += WY_THREADS) {
+    const int r = e % nr, i = e / nr;
+    V[e] = wy_v(A, v0s, ld, m, j0, w, j0 + r, i);
+    Bt[e] = (i < ncol) ? Bg[(size_t)i * ld + j0 + r] : make_double2(0.0, 0.0);
+  }
+  T[tid] = D.LT[a * D.lt_stride + L.t_off + (size_t)b * WYB * WYB + tid];
+  __syncthreads();
+  {
+    const int i = tid / WYB, c = tid % WYB;  // W(i, c) = v_i^H b_c
+    double sr = 0.0, si = 0.0, tr = 0.0, ti = 0.0;
+    int r = 0;
+    for (; r + 1 < nr; r += 2) {
+      const double2 x = V[i * nr + r], y = Bt[c * nr + r];
+      const double2 x2 = V[i * nr + r + 1], y2 = Bt[c * nr + r + 1];
+      sr = fma(x.x, y.x, fma(x.y, y.y, sr));
+      si = fma(x.x, y.y, fma(-x.y, y.x, si));
+      tr = fma(x2.x, y2.x, fma(x2.y, y2.y, tr));
+      ti = fma(x2.x, y2.y, fma(-x2.y, y2.x, ti));
+    }
+    if (r < nr) {
+      const double2 x = V[i * nr + r], y = Bt[c * nr + r];
+      sr = fma(x.x, y.x, fma(x.y, y.y, sr));
+      si = fma(x.x, y.y, fma(-x.y, y.x, si));
+    }
+    W[c * WYB + i] = make_double2(sr + tr, si + ti);
+  }
+  __syncthreads();
+  {
+    const int i = tid / WYB, c = tid % WYB;  // W2(i, c) = sum_{q <= i} conj(T(q, i)) W(q, c)
+    cplx s = C(0.0);
+    for (int q = 0; q <= i; ++q) s = s + conj(ld2(&T[i * WYB + q])) * ld2(&W[c * WYB + q]);
+    W2[c * WYB + i] = make_double2(s.re, s.im);
+  }
+  __syncthreads();
+  for (int e = tid; e < nr * ncol; e += WY_THREADS) {
+    const int r = e % nr, c = e / nr;
+    cplx s = ld2(&Bt[c * nr + r]);
+#pragma unroll
+    for (int i = 0; i < WYB; ++i) s = s - ld2(&V[i * nr + r]) * ld2(&W2[c * WYB + i]);
+    st2(&Bg[(size_t)c * ld + j0 + r], s);
+  }
+}
+
+__global__ void __launch_bounds__(WY_THREADS) k_lsq_trsm(Dev D) {
+  const int jl = blockIdx.y, a = blockIdx.z;
+  const LayerDesc L = D.lay[jl];
+  const int p = L.p, ld = L.ldq;
+  const int c0 = blockIdx.x * WYB;
+  if (c0 >= L.c) return;
+  const int ncol = min(WYB, L.c - c0);
   const double2* A = D.QP + a * D.qp_stride + L.qp_off;
   const double* aux = D.LAUX + a * D.laux_stride + 6 * L.aux_off;
   const double2* rinv = reinterpret_cast<const double2*>(aux);
-  const double2* v0s = reinterpret_cast<const double2*>(aux + 2 * p);
-  const double* beta = aux + 4 * p;
-  double2* b = D.CP + a * D.cp_stride + L.cp_off + (size_t)c * ld;
-  for (int r = m; r < m + p; ++r) b[r] = make_double2(0.0, 0.0);
-  for (int j = 0; j < p; ++j) {
-    const double bj = beta[j];
-    if (bj == 0.0) continue;
-    const int r1 = m + j;
-    const double2* vj = A + (size_t)j * ld;
-    const cplx v0 = ld2(&v0s[j]);
-    // w = conj(v) . b over rows j..r1, two partial sums
-    const cplx x0 = ld2(&b[j]);
-    double sr0 = v0.re * x0.re + v0.im * x0.im, si0 = v0.re * x0.im - v0.im * x0.re;
-    double sr1 = 0.0, si1 = 0.0;
-    int r = j + 1;
-    for (; r + 1 <= r1; r += 2) {
-      const double2 va = vj[r], vb = vj[r + 1];
-      const double2 xa = b[r], xb = b[r + 1];
-      sr0 = fma(va.x, xa.x, fma(va.y, xa.y, sr0));
-      si0 = fma(va.x, xa.y, fma(-va.y, xa.x, si0));
-      sr1 = fma(vb.x, xb.x, fma(vb.y, xb.y, sr1));
-      si1 = fma(vb.x, xb.y, fma(-vb.y, xb.x, si1));
+  const double2* Bg = D.CP + a * D.cp_stride + L.cp_off + (size_t)c0 * ld;
+  extern __shared__ double2 Xs[];  // p x 16
+  __shared__ double2 ys[WYB * WYB];
+  const int tid = threadIdx.x;
+  const int nbk = (p + WYB - 1) / WYB;
+  for (int kb = nbk - 1; kb >= 0; --kb) {
+    const int i0 = kb * WYB, w = min(WYB, p - i0), i1 = i0 + w;
+    {
+      const int ii = tid / WYB, c = tid % WYB;
+      if (ii < w && c < ncol) {
+        const int row = i0 + ii;
+        double sr = 0.0, si = 0.0;
+        for (int l = i1; l < p; ++l) {
+          const double2 rr = A[(size_t)l * ld + row], x = Xs[l * WYB + c];
+          sr = fma(rr.x, x.x, fma(-rr.y, x.y, sr));
+          si = fma(rr.x, x.y, fma(rr.y, x.x, si));
+        }
+        const double2 bv = Bg[(size_t)c * ld + row];
+        ys[ii * WYB + c] = make_double2(bv.x - sr, bv.y - si);
+      }
     }
-    if (r <= r1) {
-      const double2 va = vj[r], xa = b[r];
-      sr0 = fma(va.x, xa.x, fma(va.y, xa.y, sr0));
-      si0 = fma(va.x, xa.y, fma(-va.y, xa.x, si0));
+    __syncthreads();
+    if (tid < ncol) {
+      const int c = tid;
+      for (int ii = w - 1; ii >= 0; --ii) {
+        const int row = i0 + ii;
+        cplx s = ld2(&ys[ii * WYB + c]);
+        for (int l = ii + 1; l < w; ++l) s = s - ld2(&A[(size_t)(i0 + l) * ld + row]) * ld2(&Xs[(i0 + l) * WYB + c]);
+        st2(&Xs[row * WYB + c], s * ld2(&rinv[row]));
+      }
     }
-    const cplx w = C(bj * (sr0 + sr1), bj * (si0 + si1));
-    st2(&b[j], x0 - v0 * w);
-    for (r = j + 1; r <= r1; ++r) st2(&b[r], ld2(&b[r]) - ld2(&vj[r]) * w);
+    __syncthreads();
   }
-  // back substitution R y = (Q^H b)[:p], with the stored reciprocals 1/R_kk
-  double2* xcol = D.Xb + a * D.x_stride + L.x_off + (size_t)c * p;
-  for (int k = p - 1; k >= 0; --k) {
-    double sr = 0.0, si = 0.0, tr = 0.0, ti = 0.0;
-    int l = k + 1;
-    for (; l + 1 < p; l += 2) {
-      const double2 ra = A[(size_t)l * ld + k], rb = A[(size_t)(l + 1) * ld + k];
-      const double2 ya = xcol[l], yb = xcol[l + 1];
-      sr = fma(ra.x, ya.x, fma(-ra.y, ya.y, sr));
-      si = fma(ra.x, ya.y, fma(ra.y, ya.x, si));
-      tr = fma(rb.x, yb.x, fma(-rb.y, yb.y, tr));
-      ti = fma(rb.x, yb.y, fma(rb.y, yb.x, ti));
-    }
-    if (l < p) {
-      const double2 ra = A[(size_t)l * ld + k], ya = xcol[l];
-      sr = fma(ra.x, ya.x, fma(-ra.y, ya.y, sr));
-      si = fma(ra.x, ya.y, fma(ra.y, ya.x, si));
-    }
-    st2(&xcol[k], (ld2(&b[k]) - C(sr + tr, si + ti)) * ld2(&rinv[k]));
+  double2* X = D.Xb + a * D.x_stride + L.x_off;
+  for (int e = tid; e < p * ncol; e += WY_THREADS) {
+    const int k = e % p, c = e / p;
+    X[(size_t)(c0 + c) * p + k] = Xs[k * WYB + c];
   }
 }
 
@@ -292,9 +406,29 @@ cudaError_t launch_lsq(const Dev& D, int max_m, int max_p, int max_c, cudaStream
   k_lsq_qr<<<dim3(D.L, D.n_theta), QR_THREADS, smem, s>>>(D);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const int nbmax = (max_p + WYB - 1) / WYB;
+  const size_t smem_t = (size_t)(max_m + WYB) * WYB * sizeof(double2);
   ++g_launches;
-  k_lsq_apply<<<dim3((max_c + APPLY_THREADS - 1) / APPLY_THREADS, D.L, D.n_theta), APPLY_THREADS, 0, s>>>(D);
+  k_lsq_T<<<dim3(nbmax, D.L, D.n_theta), WY_THREADS, smem_t, s>>>(D);
+  const int nct = (max_c + WYB - 1) / WYB;
+  for (int b = 0; b < nbmax; ++b) {
+    ++g_launches;
+    k_lsq_wy<<<dim3(nct, D.L, D.n_theta), WY_THREADS, 2 * smem_t, s>>>(D, b);
+  }
+  ++g_launches;
+  k_lsq_trsm<<<dim3(nct, D.L, D.n_theta), WY_THREADS, (size_t)max_p * WYB * sizeof(double2), s>>>(D);
   return cudaGetLastError();
+}
+
+cudaError_t lsq_configure(int max_m, int max_p) {
+  const size_t smem_t = (size_t)(max_m + WYB) * WYB * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(k_lsq_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_lsq_wy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smem_t));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_lsq_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)max_p * WYB * sizeof(double2)));
+  return e;
 }
 
 cudaError_t launch_schur(const Dev& D, int max_tiles, cudaStream_t s) {

@@ -43,6 +43,17 @@ __device__ __forceinline__ cplx inv(cplx a) {
   return C(ar * d, -ai * d);
 }
 __device__ __forceinline__ cplx operator/(cplx a, cplx b) { return a * inv(b); }
+// 1/a by Newton-Raphson on the real |a|^2 from an FP32 seed (x <- x (2 - d x),
+// two steps: 24 -> 48 -> 96 correct bits), falling back to inv() outside the
+// FP32 range.  Shorter dependent FP64 chain than a division.
+__device__ __forceinline__ cplx inv_fast(cplx a) {
+  const double d = fma(a.re, a.re, a.im * a.im);
+  if (!(d > 1e-30 && d < 1e30)) return inv(a);
+  double x = (double)__frcp_rn((float)d);
+  x = x * fma(-d, x, 2.0);
+  x = x * fma(-d, x, 2.0);
+  return C(a.re * x, -a.im * x);
+}
 __device__ __forceinline__ cplx cexp_(cplx a) {
   double s, c;
   sincos(a.im, &s, &c);

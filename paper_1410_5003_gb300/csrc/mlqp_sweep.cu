@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k)
   extern __shared__ double2 pan[];  // rows x w, column-major
   __shared__ unsigned long long s_key[PANEL_THREADS / 32];
   __shared__ int s_idx[PANEL_THREADS / 32];
-  __shared__ int s_piv;
+  __shared__ int s_piv[NB];
   __shared__ double2 s_rinv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < rows * w; e += PANEL_THREADS) {
@@ -81,12 +81,12 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k)
   int* piv = D.LUPIV + a * D.piv_stride + ft.eta_off;
   double2* udinv = D.UDINV + a * D.piv_stride + ft.eta_off;
   for (int c = 0; c < w; ++c) {
+    // (1) candidate pivots: largest |re| + |im| per warp (bit patterns compared as integers)
     unsigned long long key = 0;
     int idx = c;
     for (int r = c + tid; r < rows; r += PANEL_THREADS) {
       const double2 x = pan[(size_t)c * rows + r];
-      const double v = fabs(x.x) + fabs(x.y);
-      argmax_merge(key, idx, (unsigned long long)__double_as_longlong(v), r);
+      argmax_merge(key, idx, (unsigned long long)__double_as_longlong(fabs(x.x) + fabs(x.y)), r);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -99,40 +99,43 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k)
       s_idx[warp] = idx;
     }
     __syncthreads();
-    if (tid == 0) {
-      unsigned long long kb = s_key[0];
-      int ib = s_idx[0];
-      for (int q = 1; q < PANEL_THREADS / 32; ++q) argmax_merge(kb, ib, s_key[q], s_idx[q]);
-      s_piv = ib;
-      piv[k + c] = k + ib;
-      const double pv = __longlong_as_double((long long)kb);
-      if (!(pv > 0.0) || !isfinite(pv)) atomicExch(D.STATUS, MLQP_ESINGULAR_CODE);
+    // (2) warp 0: pivot, row swap within the panel, reciprocal of the pivot
+    if (warp == 0) {
+      key = (lane < PANEL_THREADS / 32) ? s_key[lane] : 0ull;
+      idx = (lane < PANEL_THREADS / 32) ? s_idx[lane] : 0x7fffffff;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+        argmax_merge(key, idx, k2, i2);
+      }
+      const int pr = idx;
+      if (pr != c && lane < w) {
+        const double2 x = pan[(size_t)lane * rows + c];
+        pan[(size_t)lane * rows + c] = pan[(size_t)lane * rows + pr];
+        pan[(size_t)lane * rows + pr] = x;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        const double pv = __longlong_as_double((long long)key);
+        if (!(pv > 0.0) || !isfinite(pv)) atomicExch(D.STATUS, MLQP_ESINGULAR_CODE);
+        piv[k + c] = k + pr;
+        s_piv[c] = k + pr;
+        const cplx ri = inv_fast(ld2(&pan[(size_t)c * rows + c]));
+        s_rinv = make_double2(ri.re, ri.im);
+        udinv[k + c] = s_rinv;
+      }
     }
     __syncthreads();
-    const int pr = s_piv;
-    if (pr != c && tid < w) {
-      const double2 x = pan[(size_t)tid * rows + c];
-      pan[(size_t)tid * rows + c] = pan[(size_t)tid * rows + pr];
-      pan[(size_t)tid * rows + pr] = x;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      const cplx ri = inv(ld2(&pan[(size_t)c * rows + c]));
-      s_rinv = make_double2(ri.re, ri.im);
-      udinv[k + c] = s_rinv;
-    }
-    __syncthreads();
+    // (3) multipliers and rank-1 update of the remaining panel columns, row by row
     const cplx ip = C(s_rinv.x, s_rinv.y);
     for (int r = c + 1 + tid; r < rows; r += PANEL_THREADS) {
-      double2* q = &pan[(size_t)c * rows + r];
-      st2(q, ld2(q) * ip);
-    }
-    __syncthreads();
-    const int nrem = rows - c - 1, crem = w - c - 1;
-    for (int e = tid; e < nrem * crem; e += PANEL_THREADS) {
-      const int r = c + 1 + e % nrem, cc = c + 1 + e / nrem;
-      double2* q = &pan[(size_t)cc * rows + r];
-      st2(q, ld2(q) - ld2(&pan[(size_t)c * rows + r]) * ld2(&pan[(size_t)cc * rows + c]));
+      const cplx l = ld2(&pan[(size_t)c * rows + r]) * ip;
+      st2(&pan[(size_t)c * rows + r], l);
+      for (int cc = c + 1; cc < w; ++cc) {
+        double2* q = &pan[(size_t)cc * rows + r];
+        st2(q, ld2(q) - l * ld2(&pan[(size_t)cc * rows + c]));
+      }
     }
     __syncthreads();
   }
@@ -140,15 +143,49 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k)
     const int r = e % rows, c = e / rows;
     top[(size_t)(S.nlt + k + c) * ld + k + r] = pan[e];
   }
+  // row map of the w sequential swaps (row k+r <-> piv[k+r]): new[pos] = old[src],
+  // rows k..k+w-1 first (in order), then the displaced rows below the block.
+  if (tid == 0) {
+    int pos[2 * NB], src[2 * NB];
+    int n = 0;
+    for (int r = 0; r < w; ++r) {
+      pos[n] = k + r;
+      src[n] = k + r;
+      ++n;
+    }
+    for (int r = 0; r < w; ++r) {
+      const int p2 = s_piv[r];
+      int f = -1;
+      for (int q = 0; q < n; ++q)
+        if (pos[q] == p2) f = q;
+      if (f < 0) {
+        pos[n] = p2;
+        src[n] = p2;
+        f = n++;
+      }
+      const int tmp = src[r];  // position k + r is entry r
+      src[r] = src[f];
+      src[f] = tmp;
+    }
+    int* pm = D.PERM + 80 * a;
+    pm[0] = n;
+    for (int q = 0; q < n; ++q) {
+      pm[1 + q] = pos[q];
+      pm[1 + 2 * NB + q] = src[q];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
-// Row swaps on every top column outside the panel, U12 rows (forward
-// substitution with the unit-lower L11) on the trailing columns, and the
-// bottom multipliers L21 = A21 U11^{-1} on the panel columns.  One warp per
-// CTA, one column or row per thread; no divisions (reciprocals from UDINV).
+// Row permutation of every top column outside the panel (gathered from the
+// row map with independent loads), U12 rows (forward substitution with the
+// unit-lower L11) on the trailing columns, and the bottom multipliers
+// L21 = A21 U11^{-1} on the panel columns.  A 16-lane half-warp per column
+// (or bottom row), one lane per row (or column) of the 16 x 16 block, so each
+// warp executes only a few dozen FP64 instructions.
 // ---------------------------------------------------------------------------
-constexpr int PREP_THREADS = 32;
+constexpr int PREP_THREADS = 128;
+constexpr int PREP_COLS = PREP_THREADS / 16;  // columns (or rows) per CTA
 
 __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, int n_col_ctas) {
   const int a = blockIdx.y;
@@ -160,76 +197,67 @@ __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, i
   const int ldt = S.nt;
   __shared__ double2 blk[NB * NB];  // factored top w x w block (L11 \ U11), column-major
   __shared__ double2 sinv[NB];
-  __shared__ int spiv[NB];
+  __shared__ int spos[2 * NB], ssrc[2 * NB], sn;
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
     const int r = e % w, c = e / w;
     blk[c * w + r] = top[(size_t)(S.nlt + k + c) * ldt + k + r];
   }
-  const int* piv = D.LUPIV + a * D.piv_stride + ft.eta_off;
   const double2* udinv = D.UDINV + a * D.piv_stride + ft.eta_off;
-  for (int e = threadIdx.x; e < w; e += blockDim.x) {
-    spiv[e] = piv[k + e];
-    sinv[e] = udinv[k + e];
+  const int* pm = D.PERM + 80 * a;
+  for (int e = threadIdx.x; e < w; e += blockDim.x) sinv[e] = udinv[k + e];
+  if (threadIdx.x == 0) sn = pm[0];
+  for (int e = threadIdx.x; e < 2 * NB; e += blockDim.x) {
+    spos[e] = pm[1 + e];
+    ssrc[e] = pm[1 + 2 * NB + e];
   }
   __syncthreads();
+  const int lane16 = threadIdx.x & 15;
+  const int slot = threadIdx.x >> 4;
+  const unsigned hmask = 0xffffu << (threadIdx.x & 16);  // this half-warp
   if ((int)blockIdx.x < n_col_ctas) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int u = blockIdx.x * PREP_COLS + slot;
     const int ncol = S.nlt + S.nt + S.nb + 1;
-    if (u >= ncol) return;
     const int pc0 = S.nlt + k, pc1 = S.nlt + k + w;
-    if (u >= pc0 && u < pc1) return;  // panel columns: done by the panel kernel
-    double2* col = (u == ncol - 1) ? ftop : top + (size_t)u * ldt;
-    for (int r = 0; r < w; ++r) {
-      const int pr = spiv[r];
-      if (pr != k + r) {
-        const double2 x = col[k + r];
-        col[k + r] = col[pr];
-        col[pr] = x;
+    const bool live = (u < ncol) && !(u >= pc0 && u < pc1);  // panel columns: done by the panel kernel
+    double2* col = live ? ((u == ncol - 1) ? ftop : top + (size_t)u * ldt) : nullptr;
+    const int n = sn;
+    cplx x = C(0.0);
+    double2 extra = make_double2(0.0, 0.0);
+    if (live) {
+      if (lane16 < w) x = ld2(&col[ssrc[lane16]]);
+      if (lane16 < n - w) extra = col[ssrc[w + lane16]];
+    }
+    __syncwarp();
+    if (live && lane16 < n - w) col[spos[w + lane16]] = extra;
+    if (live && u >= pc1) {
+      for (int q = 0; q + 1 < w; ++q) {
+        const double xr = __shfl_sync(hmask, x.re, q, 16), xi = __shfl_sync(hmask, x.im, q, 16);
+        if (lane16 > q && lane16 < w) x = x - ld2(&blk[q * w + lane16]) * C(xr, xi);
+      }
+    } else {
+      for (int q = 0; q + 1 < w; ++q) {  // keep the shuffles converged across the half-warp
+        __shfl_sync(hmask, x.re, q, 16);
+        __shfl_sync(hmask, x.im, q, 16);
       }
     }
-    if (u >= pc1) {
-      cplx x[NB];
-#pragma unroll
-      for (int r = 0; r < NB; ++r)
-        if (r < w) x[r] = ld2(&col[k + r]);
-#pragma unroll
-      for (int r = 1; r < NB; ++r) {
-        if (r < w) {
-          cplx s = x[r];
-#pragma unroll
-          for (int q = 0; q < NB; ++q)
-            if (q < r) s = s - ld2(&blk[q * w + r]) * x[q];
-          x[r] = s;
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < NB; ++r)
-        if (r < w) st2(&col[k + r], x[r]);
-    }
+    __syncwarp();
+    if (live && lane16 < w) st2(&col[k + lane16], x);
   } else {
     if (S.b < 0) return;
-    const int r = (blockIdx.x - n_col_ctas) * blockDim.x + threadIdx.x;
-    if (r >= S.nb) return;
+    const int r = (blockIdx.x - n_col_ctas) * PREP_COLS + slot;
+    const bool live = r < S.nb;
     const IfaceDesc fb = D.ifc[S.b];
     double2* bot = D.ROW + a * D.r_stride + fb.row_off;  // left block = E columns
     const int ldb = S.nb;
-    cplx x[NB];
-#pragma unroll
-    for (int c = 0; c < NB; ++c)
-      if (c < w) x[c] = ld2(&bot[(size_t)(k + c) * ldb + r]);
-#pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      if (c < w) {
-        cplx s = x[c];
-#pragma unroll
-        for (int q = 0; q < NB; ++q)
-          if (q < c) s = s - x[q] * ld2(&blk[c * w + q]);
-        x[c] = s * ld2(&sinv[c]);
-      }
+    cplx x = C(0.0);
+    if (live && lane16 < w) x = ld2(&bot[(size_t)(k + lane16) * ldb + r]);
+    for (int q = 0; q < w; ++q) {
+      // lane q finalises x_q = (a_q - sum_{q' < q} x_q' U_q'q) / U_qq, then all lanes c > q use it
+      if (lane16 == q) x = x * ld2(&sinv[q]);
+      const double xr = __shfl_sync(hmask, x.re, q, 16), xi = __shfl_sync(hmask, x.im, q, 16);
+      if (lane16 > q && lane16 < w) x = x - C(xr, xi) * ld2(&blk[lane16 * w + q]);
     }
-#pragma unroll
-    for (int c = 0; c < NB; ++c)
-      if (c < w) st2(&bot[(size_t)(k + c) * ldb + r], x[c]);
+    if (live && lane16 < w) st2(&bot[(size_t)(k + lane16) * ldb + r], x);
   }
 }
 
@@ -239,7 +267,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, i
 // 64 threads, 4 x 4 outputs per thread, complex 3M products.
 // ---------------------------------------------------------------------------
 constexpr int UT = 32;
-constexpr int UPD_THREADS = 64;
+constexpr int UPD_THREADS = 128;
 
 __device__ __forceinline__ double2* row_col_ptr(double2* top, int ldt, double2* ftop, double2* bot, int ldb,
                                                 double2* fbot, const Step& S, int k, int w, int v, int u) {
@@ -307,21 +335,24 @@ __global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k) 
     Bs[kk][2][c] = x.x + x.y;
   }
   __syncthreads();
-  const int tx = tid & 7, ty = tid >> 3;
-  double t1[4][4] = {}, t2[4][4] = {}, t3[4][4] = {};
+  const int tx = tid & 7, ty = tid >> 3;  // 2 rows x 4 columns per thread
+  double t1[2][4] = {}, t2[2][4] = {}, t3[2][4] = {};
   for (int kk = 0; kk < w; ++kk) {
-    double ar[4], ai[4], as[4], br[4], bi[4], bs[4];
+    double ar[2], ai[2], as[2], br[4], bi[4], bs[4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      ar[q] = As[kk][0][ty * 2 + q];
+      ai[q] = As[kk][1][ty * 2 + q];
+      as[q] = As[kk][2][ty * 2 + q];
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      ar[q] = As[kk][0][ty * 4 + q];
-      ai[q] = As[kk][1][ty * 4 + q];
-      as[q] = As[kk][2][ty * 4 + q];
       br[q] = Bs[kk][0][tx * 4 + q];
       bi[q] = Bs[kk][1][tx * 4 + q];
       bs[q] = Bs[kk][2][tx * 4 + q];
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 2; ++q)
 #pragma unroll
       for (int z = 0; z < 4; ++z) {
         t1[q][z] = fma(ar[q], br[z], t1[q][z]);
@@ -330,10 +361,10 @@ __global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k) 
       }
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < 2; ++q)
 #pragma unroll
     for (int z = 0; z < 4; ++z) {
-      const int v = row0 + ty * 4 + q, u = col0 + tx * 4 + z;
+      const int v = row0 + ty * 2 + q, u = col0 + tx * 4 + z;
       if (v < nrows && u < ncols) {
         double2* p = row_col_ptr(top, ldt, ftop, bot, ldb, fbot, S, k, w, v, u);
         double2 x = *p;
@@ -345,33 +376,43 @@ __global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k) 
 }
 
 // ---------------------------------------------------------------------------
-// Backward sweep: y = g_t - U12_t eta_{t+1} (one row per thread);
-// U_t eta_t = y by column-oriented back substitution with the stored
-// reciprocals of the U diagonal.
+// Backward sweep: y = g_t - U12_t eta_{t+1} (one row per warp, lanes over the
+// columns, shuffle reduction); U_t eta_t = y by blocks of 32 rows from the
+// bottom: one warp solves the 32 x 32 diagonal block (lane = row, pivot
+// reciprocals from UDINV), then every thread updates one row above it.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) k_back_matvec(Dev D, int t) {
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_back_matvec(Dev D, int t) {
   const int a = blockIdx.y;
   const IfaceDesc ft = D.ifc[t];
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (r >= ft.n) return;
   const double2* top = D.ROW + a * D.r_stride + ft.row_off;
   const double2* g = D.F + a * D.f_stride + ft.rhs_off;
   double2* eta = D.ETA + a * D.eta_stride;
-  cplx y = ld2(&g[r]);
+  double sr = 0.0, si = 0.0;
   if (t + 1 < D.I) {
     const IfaceDesc fb = D.ifc[t + 1];
     const double2* eb = eta + fb.eta_off;
     const double2* U12 = top + (size_t)(ft.nl + ft.n) * ft.n;
-    cplx y2 = C(0.0);
-    int c = 0;
-    for (; c + 1 < fb.n; c += 2) {
-      y = y - ld2(&U12[(size_t)c * ft.n + r]) * ld2(&eb[c]);
-      y2 = y2 - ld2(&U12[(size_t)(c + 1) * ft.n + r]) * ld2(&eb[c + 1]);
+    for (int c = lane; c < fb.n; c += 32) {
+      const double2 u = U12[(size_t)c * ft.n + r], e = eb[c];
+      sr = fma(u.x, e.x, fma(-u.y, e.y, sr));
+      si = fma(u.x, e.y, fma(u.y, e.x, si));
     }
-    if (c < fb.n) y = y - ld2(&U12[(size_t)c * ft.n + r]) * ld2(&eb[c]);
-    y = y + y2;
+    sr = warp_sum_d(sr);
+    si = warp_sum_d(si);
   }
-  st2(&eta[ft.eta_off + r], y);
+  if (lane == 0) {
+    const double2 gv = g[r];
+    eta[ft.eta_off + r] = make_double2(gv.x - sr, gv.y - si);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_back_trsv(Dev D, int t) {
@@ -381,16 +422,34 @@ __global__ void __launch_bounds__(256) k_back_trsv(Dev D, int t) {
   const double2* U = D.ROW + a * D.r_stride + ft.row_off + (size_t)ft.nl * n;
   const double2* udinv = D.UDINV + a * D.piv_stride + ft.eta_off;
   double2* y = D.ETA + a * D.eta_stride + ft.eta_off;
-  __shared__ double2 sx;
-  for (int j = n - 1; j >= 0; --j) {
-    if (threadIdx.x == 0) {
-      const cplx v = ld2(&y[j]) * ld2(&udinv[j]);
-      st2(&y[j], v);
-      sx = make_double2(v.re, v.im);
+  __shared__ double2 xb[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nblk = (n + 31) / 32;
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int i0 = 32 * b, w = min(32, n - i0);
+    if (warp == 0) {
+      cplx v = (lane < w) ? ld2(&y[i0 + lane]) : C(0.0);
+      for (int j = w - 1; j >= 0; --j) {
+        if (lane == j) v = v * ld2(&udinv[i0 + j]);
+        const double xr = __shfl_sync(0xffffffffu, v.re, j), xi = __shfl_sync(0xffffffffu, v.im, j);
+        if (lane < j) v = v - ld2(&U[(size_t)(i0 + j) * n + i0 + lane]) * C(xr, xi);
+      }
+      if (lane < w) {
+        st2(&y[i0 + lane], v);
+        xb[lane] = make_double2(v.re, v.im);
+      }
     }
     __syncthreads();
-    const cplx v = C(sx.x, sx.y);
-    for (int r = threadIdx.x; r < j; r += blockDim.x) st2(&y[r], ld2(&y[r]) - ld2(&U[(size_t)j * n + r]) * v);
+    for (int r = tid; r < i0; r += blockDim.x) {
+      double sr = 0.0, si = 0.0;
+      for (int j = 0; j < w; ++j) {
+        const double2 u = U[(size_t)(i0 + j) * n + r], x = xb[j];
+        sr = fma(u.x, x.x, fma(-u.y, x.y, sr));
+        si = fma(u.x, x.y, fma(u.y, x.x, si));
+      }
+      const double2 yv = y[r];
+      y[r] = make_double2(yv.x - sr, yv.y - si);
+    }
     __syncthreads();
   }
 }
@@ -448,8 +507,8 @@ cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s) {
       ++g_launches;
       k_lu_panel<<<D.n_theta, PANEL_THREADS, smem, s>>>(D, t, k);
       const int ncol = nlt + nt + nb + 1;
-      const int n_col_ctas = (ncol + PREP_THREADS - 1) / PREP_THREADS;
-      const int n_row_ctas = (nb + PREP_THREADS - 1) / PREP_THREADS;
+      const int n_col_ctas = (ncol + PREP_COLS - 1) / PREP_COLS;
+      const int n_row_ctas = (nb + PREP_COLS - 1) / PREP_COLS;
       ++g_launches;
       k_lu_prep<<<dim3(n_col_ctas + n_row_ctas, D.n_theta), PREP_THREADS, 0, s>>>(D, t, k, n_col_ctas);
       const int tr = nt - k - w;
@@ -464,7 +523,7 @@ cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s) {
   }
   for (int t = I - 1; t >= 0; --t) {
     ++g_launches;
-    k_back_matvec<<<dim3((n_host[t] + 31) / 32, D.n_theta), 32, 0, s>>>(D, t);
+    k_back_matvec<<<dim3((n_host[t] + 7) / 8, D.n_theta), 256, 0, s>>>(D, t);
     ++g_launches;
     k_back_trsv<<<D.n_theta, 256, 0, s>>>(D, t);
   }
