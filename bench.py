@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -289,6 +290,45 @@ def main():
                 "schur_tflops": nth * schur_flops(n, prob.params.P) / (stage_ms["schur"] / 1e3) / 1e12}
         if clocks:
             line["clocks"] = clocks
+    # the mixed-precision form on the same stack: FP32 Schur / block LU, FP64 refinement
+    if not args.no_mixed:
+        mctx = mlqp.Context(prob, device=dev, precision=mlqp.MLQP_MIXED, max_refine=10, refine_tol=1e-15)
+        mout = mctx.outputs()
+        for _ in range(args.warmup):
+            mctx.solve_device(mout)
+        mctx.check()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        mtimes = []
+        with torch.cuda.stream(mctx.stream):
+            for _ in range(K):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(mctx.stream)
+                for s_ in stages:
+                    mctx.run_stage(s_)
+                e1.record(mctx.stream)
+                mtimes.append((e0, e1))
+        torch.cuda.synchronize()
+        mms = sum(a.elapsed_time(b) for a, b in mtimes)
+        if ws > 1:
+            t = torch.tensor([mms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            mms = float(t.item())
+        mctx.solve_device(mout)
+        mctx.check()
+        diff = float(torch.max(torch.abs(torch.cat([mout["aU"], mout["aD"]], 1) - torch.cat([out["aU"], out["aD"]], 1)))
+                     / torch.max(torch.abs(torch.cat([out["aU"], out["aD"]], 1))))
+        if rank == 0:
+            line["mixed"] = {"value": units * ws * K / (mms / 1e3), "unit": METRIC, "ms_per_step": mms / K,
+                             "speedup_vs_fp64": (total_ms / K) / (mms / K),
+                             "refine_steps": [int(mctx.block(mlqp.BLK_REFINE, 1, a)[1]) for a in range(nth)],
+                             "backward_error": max(float(mctx.block(mlqp.BLK_REFINE, 1, a)[0]) for a in range(nth)),
+                             "max_rel_amp_diff_vs_fp64": diff,
+                             "dtype": "f32 Schur/LU + f64 refinement (fill, least squares, residuals in f64)"}
+        mctx.close()
     # e2e through the C ABI with host buffers: bind (H2D of the problem) + solve (D2H of amplitudes)
     if not args.no_e2e:
         hout = ctx.host_outputs(eta=False, pinned=True)

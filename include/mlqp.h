@@ -70,10 +70,15 @@ typedef struct {
  * U lies gap_U above the bound y0_1 + sum |(a_m, b_m)| of Gamma_1, D gap_D
  * below the matching bound of Gamma_I.  The self-interaction log-split uses a
  * smooth window equal to 1 for |s - t| <= cut_a and 0 for |s - t| >= cut_b
- * (0 <= cut_a < cut_b <= pi).  The per-layer least squares keep the pivots
- * |R_kk| > lsq_rcond |R_11| (Sec. 3.2).  precision: MLQP_FP64 (every step
- * in FP64) or MLQP_MIXED (FP32 Schur / block LU, FP64 refinement of the
- * block-tridiagonal system up to max_refine steps to refine_tol). */
+ * (0 <= cut_a < cut_b <= pi).  The per-layer least squares of Sec. 3.2
+ * minimise |Q'_j X - C'_j|^2 + lambda^2 |X|^2 with lambda = lsq_rcond times
+ * the largest column norm of Q'_j.  precision: MLQP_FP64 (every step in
+ * FP64) or MLQP_MIXED (FP32 Schur / block LU; at most max_refine FP64
+ * corrections of the block-tridiagonal solve, 1 <= max_refine <= 50, until
+ * the normwise backward error
+ *     omega = max_r |r_r| / max_r (|f_r| + sum_c |A_rc||eta_c| + sum_c |B_rc| (|X||eta|)_c),
+ *     r = f - A eta + B (X eta)   (the unreduced FP64 operator, |z| = |re| + |im|)
+ * is at most refine_tol > 0; MLQP_ENOTCONV if it is not). */
 typedef struct {
   int P;
   double R;
@@ -139,8 +144,10 @@ mlqp_status mlqp_solve(mlqp_ctx* ctx, double* eta, double* aU, double* aD, doubl
  *   MLQP_STAGE_FILL   A (eq. Ablocks), B (eq. Bblocks), Q', C' (eqs. Cii,
  *                     Qiop, VUD, WUD, linsys), right-hand side
  *   MLQP_STAGE_LSQ    X_j = Q'_j \ C'_j (Sec. 3.2)
- *   MLQP_STAGE_SCHUR  A' = A - B X (eqs. Schur1-Schuri)
- *   MLQP_STAGE_SWEEP  block-tridiagonal forward and backward sweeps (Sec. 3.3)
+ *   MLQP_STAGE_SCHUR  A' = A - B X (eqs. Schur1-Schuri); FP32 copy for MLQP_MIXED
+ *   MLQP_STAGE_SWEEP  block-tridiagonal forward and backward sweeps (Sec. 3.3);
+ *                     for MLQP_MIXED an FP32 block LU and max_refine FP64
+ *                     refinement steps eta += (A'_32)^{-1} (f - A eta + B X eta)
  *   MLQP_STAGE_RECOVER amplitudes and flux error (Sec. 3.3, Remark r:flux) */
 enum { MLQP_STAGE_GEOM = 0, MLQP_STAGE_FILL = 1, MLQP_STAGE_LSQ = 2,
        MLQP_STAGE_SCHUR = 3, MLQP_STAGE_SWEEP = 4, MLQP_STAGE_RECOVER = 5 };
@@ -158,11 +165,14 @@ mlqp_status mlqp_run_stage(mlqp_ctx* ctx, int stage);
  *   MLQP_BLK_NODES  interface i: x, y, nx, ny, speed (5 x N_i doubles)
  *   MLQP_BLK_ETA    interface i, angle a: eta_i after the sweep (n_i x 1)
  *   MLQP_BLK_AMP    index 1, angle a: [a^U; a^D] after recovery (2(2K+1) x 1)
+ *   MLQP_BLK_REFINE index 1, angle a (MLQP_MIXED only): 2 doubles, the
+ *                   normwise backward error omega of the returned eta (below)
+ *                   and the number of FP64 corrections applied
  * Complex blocks are interleaved complex128.  Offsets are in bytes from the
  * workspace base; ld is the leading dimension in elements. */
 enum { MLQP_BLK_ROW = 0, MLQP_BLK_B = 1, MLQP_BLK_QP = 2, MLQP_BLK_CP = 3,
        MLQP_BLK_X = 4, MLQP_BLK_RHS = 5, MLQP_BLK_NODES = 6, MLQP_BLK_ETA = 7,
-       MLQP_BLK_AMP = 8 };
+       MLQP_BLK_AMP = 8, MLQP_BLK_REFINE = 9 };
 mlqp_status mlqp_block_info(const mlqp_ctx* ctx, int kind, int index, int angle,
                             size_t* offset_bytes, int* rows, int* cols, int* ld);
 

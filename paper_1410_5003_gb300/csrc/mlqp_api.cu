@@ -21,6 +21,10 @@ cudaError_t launch_schur(const Dev& D, int max_tiles, cudaStream_t s);
 cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s);
 cudaError_t launch_recover(const Dev& D, cudaStream_t s);
 cudaError_t sweep_configure(int maxn);
+cudaError_t mixed_configure(int maxn);
+cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s);
+cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n_den, int max_refine, double tol,
+                               int* permv, cudaStream_t s);
 cudaError_t lsq_configure(int max_m, int max_p);
 cudaError_t launch_hankel_eval(const double* kr, int n, double* out, cudaStream_t s);
 extern thread_local long g_launches;
@@ -50,7 +54,7 @@ struct mlqp_ctx {
          t_stride = 0;
   // layout
   Region r_ifc, r_lay, r_tasks, r_k, r_ca, r_cb, r_theta, r_scal, r_geo[7], r_wy, r_gl, r_ux, r_alpha, r_kappa,
-      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ETA, r_AMP, r_FLUX, r_STATUS;
+      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ROW32, r_F32, r_UDINV32, r_RES, r_ZX, r_ZXA, r_Y32, r_RNRM, r_PERMV, r_ETA, r_AMP, r_FLUX, r_STATUS;
   size_t ws_bytes = 0;
   // binding
   char* ws = nullptr;
@@ -123,7 +127,9 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   if (!(q.cut_a >= 0 && q.cut_a < q.cut_b && q.cut_b <= M_PI + 1e-15)) return bad("need 0 <= cut_a < cut_b <= pi");
   if (!(q.lsq_rcond > 0 && q.lsq_rcond < 1)) return bad("lsq_rcond must be in (0, 1)");
   if (!(q.gap_U > 0 && q.gap_D > 0)) return bad("gap_U and gap_D must be positive");
-  if (q.precision != MLQP_FP64) return bad("only MLQP_FP64 is available in this build");
+  if (q.precision != MLQP_FP64 && q.precision != MLQP_MIXED) return bad("precision must be MLQP_FP64 or MLQP_MIXED");
+  if (q.precision == MLQP_MIXED && (q.max_refine < 1 || q.max_refine > 50 || !(q.refine_tol > 0)))
+    return bad("MLQP_MIXED needs 1 <= max_refine <= 50 and refine_tol > 0");
   c->k.assign(k, k + 2 * (I + 1));
   for (int j = 0; j <= I; ++j) {
     if (!(c->k[2 * j] > 0) || !(c->k[2 * j + 1] >= 0) || !std::isfinite(c->k[2 * j]) ||
@@ -313,6 +319,18 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   take(cur, c->r_LUPIV, sizeof(int) * nt * c->n_den);
   take(cur, c->r_UDINV, z16 * nt * c->n_den);
   take(cur, c->r_PERM, sizeof(int) * nt * 80);
+  if (q.precision == MLQP_MIXED) {
+    const size_t f8 = sizeof(float2);
+    take(cur, c->r_ROW32, f8 * nt * c->r_stride);
+    take(cur, c->r_F32, f8 * nt * c->f_stride);
+    take(cur, c->r_UDINV32, f8 * nt * c->n_den);
+    take(cur, c->r_RES, z16 * nt * c->n_den);
+    take(cur, c->r_ZX, z16 * nt * (size_t)c->L * q.P);
+    take(cur, c->r_ZXA, d8 * nt * (size_t)c->L * q.P);
+    take(cur, c->r_Y32, f8 * nt * c->n_den);
+    take(cur, c->r_RNRM, d8 * nt * RNRM_W);
+    take(cur, c->r_PERMV, sizeof(int) * nt * c->n_den);
+  }
   take(cur, c->r_ETA, z16 * nt * c->n_den);
   take(cur, c->r_AMP, z16 * nt * 2 * nK);
   take(cur, c->r_FLUX, d8 * nt);
@@ -399,6 +417,16 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   D.piv_stride = c->n_den;
   D.UDINV = at<double2>(c, c->r_UDINV);
   D.PERM = at<int>(c, c->r_PERM);
+  if (q.precision == MLQP_MIXED) {
+    D.ROW32 = at<float2>(c, c->r_ROW32);
+    D.F32 = at<float2>(c, c->r_F32);
+    D.UDINV32 = at<float2>(c, c->r_UDINV32);
+    D.RES = at<double2>(c, c->r_RES);
+    D.ZX = at<double2>(c, c->r_ZX);
+    D.ZXA = at<double>(c, c->r_ZXA);
+    D.Y32 = at<float2>(c, c->r_Y32);
+    D.RNRM = at<double>(c, c->r_RNRM);
+  }
   D.ETA = at<double2>(c, c->r_ETA);
   D.eta_stride = c->n_den;
   D.AMP = at<double2>(c, c->r_AMP);
@@ -434,6 +462,8 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   if (e != cudaSuccess) return cuda_fail(c, e, "descriptor upload");
   if ((e = sweep_configure(c->maxn)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
   if ((e = lsq_configure(c->max_m, c->max_p)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
+  if (q.precision == MLQP_MIXED && (e = mixed_configure(c->maxn)) != cudaSuccess)
+    return cuda_fail(c, e, "kernel configuration");
   c->bound = true;
   return MLQP_OK;
 }
@@ -451,8 +481,16 @@ mlqp_status mlqp_run_stage(mlqp_ctx* c, int stage) {
       break;
     case MLQP_STAGE_FILL: e = launch_fill(c->D, scal, c->stream); break;
     case MLQP_STAGE_LSQ: e = launch_lsq(c->D, c->max_m, c->max_p, c->max_c, c->stream); break;
-    case MLQP_STAGE_SCHUR: e = launch_schur(c->D, c->max_tiles, c->stream); break;
-    case MLQP_STAGE_SWEEP: e = launch_sweep(c->D, c->n_host.data(), c->stream); break;
+    case MLQP_STAGE_SCHUR:
+      e = (c->prm.precision == MLQP_MIXED) ? launch_schur32(c->D, c->max_tiles, c->stream)
+                                           : launch_schur(c->D, c->max_tiles, c->stream);
+      break;
+    case MLQP_STAGE_SWEEP:
+      e = (c->prm.precision == MLQP_MIXED)
+              ? launch_mixed_solve(c->D, c->n_host.data(), c->maxn, c->n_den, c->prm.max_refine, c->prm.refine_tol,
+                                   at<int>(c, c->r_PERMV), c->stream)
+              : launch_sweep(c->D, c->n_host.data(), c->stream);
+      break;
     case MLQP_STAGE_RECOVER: e = launch_recover(c->D, c->stream); break;
     default: return fail(c, MLQP_EINVAL, "unknown stage %d", stage);
   }
@@ -493,6 +531,7 @@ mlqp_status mlqp_check_device(mlqp_ctx* c) {
   if (e != cudaSuccess) return cuda_fail(c, e, "device status");
   if (st == MLQP_ESINGULAR) return fail(c, MLQP_ESINGULAR, "block LU met a zero or non-finite pivot");
   if (st == MLQP_ETIMEOUT) return fail(c, MLQP_ETIMEOUT, "a bounded device wait gave up");
+  if (st == MLQP_ENOTCONV) return fail(c, MLQP_ENOTCONV, "iterative refinement did not reach refine_tol");
   if (st != 0) return fail(c, (mlqp_status)st, "device status %d", st);
   return MLQP_OK;
 }
@@ -523,6 +562,12 @@ mlqp_status mlqp_block_info(const mlqp_ctx* c, int kind, int index, int angle, s
   if (angle < 0 || angle >= c->n_theta) return MLQP_EINVAL;
   const size_t z = sizeof(double2);
   const size_t a = angle;
+  if (kind == MLQP_BLK_REFINE) {
+    if (index != 1 || c->prm.precision != MLQP_MIXED) return MLQP_EINVAL;
+    *offset_bytes = c->r_RNRM.off + sizeof(double) * RNRM_W * a;
+    *rows = 2; *cols = 1; *ld = 2;
+    return MLQP_OK;
+  }
   if (kind == MLQP_BLK_AMP) {
     if (index != 1) return MLQP_EINVAL;
     *offset_bytes = c->r_AMP.off + z * a * 2 * (2 * c->prm.K + 1);

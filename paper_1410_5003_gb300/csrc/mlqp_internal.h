@@ -52,6 +52,8 @@ struct SchurTask {
 };
 
 // Problem scalars and workspace pointers, passed by value to the kernels.
+constexpr int RNRM_W = 8;  // doubles per angle of the refinement control block
+
 struct Dev {
   int I, L, n_theta, P, Mw, M, K, nK;
   double d, R, cut_a, cut_b, rcond, yU, yD;
@@ -86,6 +88,17 @@ struct Dev {
   int* LUPIV;   size_t piv_stride;    // block-LU pivots, per angle, indexed like eta
   double2* UDINV;                     // reciprocals of the U diagonals, per angle, indexed like eta
   int* PERM;                          // per angle 80 ints: row map of the current panel's swaps
+  // mixed-precision path: FP32 copies of the block rows and right-hand sides,
+  // FP32 pivot reciprocals, and the FP64 refinement vectors
+  float2* ROW32;
+  float2* F32;
+  float2* UDINV32;
+  double2* RES;  // per angle, indexed like eta: residual f - A eta + B X eta
+  double2* ZX;   // per angle, sum_j P entries: X_j[:P] eta
+  double* ZXA;   // per angle, like ZX: |X_j[:P]| |eta| (|re| + |im|), the rounding scale of ZX
+  float2* Y32;   // per angle, indexed like eta: forward / backward solve vector
+  double* RNRM;  // per angle RNRM_W slots: backward error, corrections applied,
+                 // max |r| and max scale (bit patterns, atomic max), done flag
   double2* ETA; size_t eta_stride;
   double2* AMP;                        // n_theta x 2 nK
   double* FLUX;                        // n_theta

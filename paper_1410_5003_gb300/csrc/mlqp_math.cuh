@@ -80,6 +80,68 @@ __device__ __forceinline__ cplx ld2(const double2* p) {
 }
 __device__ __forceinline__ void st2(double2* p, cplx v) { *p = make_double2(v.re, v.im); }
 
+// Complex numbers of either precision, for the kernels that run in FP64 (plain
+// path) and in FP32 (the factorisation of the mixed-precision path).
+template <typename R> struct vec2_of;
+template <> struct vec2_of<double> { using type = double2; };
+template <> struct vec2_of<float> { using type = float2; };
+template <typename R> using vec2 = typename vec2_of<R>::type;
+
+template <typename R>
+struct cpx {
+  R re, im;
+};
+template <typename R> __device__ __forceinline__ cpx<R> mkc(R r, R i = R(0)) { return cpx<R>{r, i}; }
+template <typename R> __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) { return mkc(a.re + b.re, a.im + b.im); }
+template <typename R> __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return mkc(a.re - b.re, a.im - b.im); }
+template <typename R> __device__ __forceinline__ cpx<R> operator*(cpx<R> a, cpx<R> b) {
+  return mkc<R>(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+}
+template <typename R> __device__ __forceinline__ cpx<R> ldv(const vec2<R>* p) {
+  const vec2<R> v = *p;
+  return mkc<R>(v.x, v.y);
+}
+template <typename R> __device__ __forceinline__ void stv(vec2<R>* p, cpx<R> v) {
+  vec2<R> w;
+  w.x = v.re;
+  w.y = v.im;
+  *p = w;
+}
+// 1/a: FP32 seed and two Newton steps in FP64; plain FP32 reciprocal in FP32.
+__device__ __forceinline__ cpx<double> inv_fast_t(cpx<double> a) {
+  const double d = fma(a.re, a.re, a.im * a.im);
+  double x;
+  if (d > 1e-30 && d < 1e30) {
+    x = (double)__frcp_rn((float)d);
+    x = x * fma(-d, x, 2.0);
+    x = x * fma(-d, x, 2.0);
+  } else {
+    x = 1.0 / d;
+  }
+  return mkc<double>(a.re * x, -a.im * x);
+}
+__device__ __forceinline__ cpx<float> inv_fast_t(cpx<float> a) {
+  const float s = fmaxf(fabsf(a.re), fabsf(a.im));
+  const float ar = a.re / s, ai = a.im / s;
+  const float x = 1.0f / (s * fmaf(ar, ar, ai * ai));
+  return mkc<float>(ar * x, -ai * x);
+}
+// Pivot keys: |re| + |im| as an integer whose order is the order of the value.
+__device__ __forceinline__ unsigned long long pivot_key(cpx<double> a) {
+  return (unsigned long long)__double_as_longlong(fabs(a.re) + fabs(a.im));
+}
+__device__ __forceinline__ unsigned long long pivot_key(cpx<float> a) {
+  return (unsigned long long)__float_as_uint(fabsf(a.re) + fabsf(a.im));
+}
+__device__ __forceinline__ bool pivot_ok(unsigned long long key, double) {
+  const double v = __longlong_as_double((long long)key);
+  return v > 0.0 && isfinite(v);
+}
+__device__ __forceinline__ bool pivot_ok(unsigned long long key, float) {
+  const float v = __uint_as_float((unsigned)key);
+  return v > 0.0f && isfinite(v);
+}
+
 constexpr double PI = 3.14159265358979323846;
 constexpr double TWO_PI = 6.28318530717958647693;
 constexpr double INV_PI = 0.31830988618379067154;

@@ -1,0 +1,424 @@
+// Mixed-precision form of the block-tridiagonal solve: the Schur complements
+// A' = A - B X are formed in FP32 and factored in FP32 (the LU kernels of
+// mlqp_sweep.cu instantiated for float), and the block-tridiagonal system is
+// solved by iterative refinement in FP64,
+//     eta <- eta + (A'_32)^{-1} r,   r = f - A eta + B (X eta),
+// with the residual formed from the unreduced FP64 operator (A, B, X) so that
+// the refined densities solve the FP64 system of Sec. 3.2-3.3, not its FP32
+// rounding.  The Hankel evaluations, the quadrature corrections and the
+// least-squares solves stay FP64.
+#include <math_constants.h>
+
+#include "mlqp_internal.h"
+#include "mlqp_math.cuh"
+
+namespace mlqp {
+
+extern thread_local long g_launches;
+constexpr int MLQP_ENOTCONV_CODE = 6;
+
+__device__ __forceinline__ double warp_sum_dd(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// A'_32 = fl32(A) - fl32(B) fl32(X), 64 x 64 tiles, FP32 accumulation.
+// ---------------------------------------------------------------------------
+constexpr int ST = 64, SK = 16;
+
+__global__ void __launch_bounds__(256) k_schur32(Dev D) {
+  const SchurTask T = D.tasks[blockIdx.y];
+  const int a = blockIdx.z;
+  const int tiles_c = (T.cols + ST - 1) / ST;
+  const int tr = blockIdx.x / tiles_c, tc = blockIdx.x % tiles_c;
+  if (tr * ST >= T.rows) return;
+  const int row0 = tr * ST, col0 = tc * ST;
+  __shared__ float2 As[SK][ST];
+  __shared__ float2 Bs[SK][ST];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float accr[4][4] = {}, acci[4][4] = {};
+  for (int term = 0; term < 2; ++term) {
+    const int K = term ? T.k2 : T.k1;
+    if (K <= 0) continue;
+    const double2* A = D.B + (term ? T.a2_off : T.a1_off);
+    const int lda = term ? T.lda2 : T.lda1;
+    const double2* Bm = D.Xb + a * D.x_stride + (term ? T.b2_off : T.b1_off);
+    const int ldb = term ? T.ldb2 : T.ldb1;
+    for (int k0 = 0; k0 < K; k0 += SK) {
+      for (int e = tid; e < ST * SK; e += 256) {
+        const int r = e % ST, kk = e / ST;
+        float2 v = make_float2(0.f, 0.f);
+        if (row0 + r < T.rows && k0 + kk < K) {
+          const double2 x = A[(size_t)(k0 + kk) * lda + row0 + r];
+          v = make_float2((float)x.x, (float)x.y);
+        }
+        As[kk][r] = v;
+      }
+      for (int e = tid; e < ST * SK; e += 256) {
+        const int kk = e % SK, c = e / SK;
+        float2 v = make_float2(0.f, 0.f);
+        if (col0 + c < T.cols && k0 + kk < K) {
+          const double2 x = Bm[(size_t)(col0 + c) * ldb + k0 + kk];
+          v = make_float2((float)x.x, (float)x.y);
+        }
+        Bs[kk][c] = v;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < SK; ++kk) {
+        float2 av[4], bv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          av[q] = As[kk][ty * 4 + q];
+          bv[q] = Bs[kk][tx * 4 + q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int z = 0; z < 4; ++z) {
+            accr[q][z] = fmaf(av[q].x, bv[z].x, fmaf(-av[q].y, bv[z].y, accr[q][z]));
+            acci[q][z] = fmaf(av[q].x, bv[z].y, fmaf(av[q].y, bv[z].x, acci[q][z]));
+          }
+      }
+      __syncthreads();
+    }
+  }
+  const double2* C64 = D.ROW + a * D.r_stride + T.c_off;
+  float2* C32 = D.ROW32 + a * D.r_stride + T.c_off;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int z = 0; z < 4; ++z) {
+      const int r = row0 + ty * 4 + q, c = col0 + tx * 4 + z;
+      if (r < T.rows && c < T.cols) {
+        const double2 x = C64[(size_t)c * T.ldc + r];
+        C32[(size_t)c * T.ldc + r] = make_float2((float)x.x - accr[q][z], (float)x.y - acci[q][z]);
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row permutation of each diagonal block's LU: the pivots record the swaps
+// j <-> piv[j] in order; PERMV[j] = source row of row j after all of them.
+// One thread per (interface, angle).
+// ---------------------------------------------------------------------------
+__global__ void k_compose_perm(Dev D, int* permv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (i >= D.I) return;
+  const IfaceDesc f = D.ifc[i];
+  const int* piv = D.LUPIV + a * D.piv_stride + f.eta_off;
+  int* pv = permv + a * D.piv_stride + f.eta_off;
+  for (int j = 0; j < f.n; ++j) pv[j] = j;
+  for (int j = 0; j < f.n; ++j) {
+    const int p = piv[j];
+    const int tmp = pv[j];
+    pv[j] = pv[p];
+    pv[p] = tmp;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Refinement control, one block of RNRM_W doubles per angle:
+//   [0] omega = max_r |r_r| / max_r s_r, the normwise backward error of the
+//       current eta against the rounding scale of the FP64 residual,
+//           s_r = |f_r| + sum_c |A_rc| |eta_c| + sum_c |B_rc| (|X| |eta|)_c
+//       (|z| taken as |re| + |im| throughout);
+//   [1] corrections applied;  [2], [3] max |r|, max s (bit patterns of
+//   non-negative doubles, so an unsigned atomic max orders them);  [4] done.
+// An angle whose omega reaches tol is done: every later kernel of the
+// refinement returns at once for it, so the launch sequence is fixed and
+// the work is not.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long* ctl(const Dev& D, int a) {
+  return reinterpret_cast<unsigned long long*>(D.RNRM + (size_t)a * RNRM_W);
+}
+__device__ __forceinline__ bool angle_done(const Dev& D, int a) { return ctl(D, a)[4] != 0ull; }
+
+__device__ __forceinline__ double cabs1(double2 z) { return fabs(z.x) + fabs(z.y); }
+
+// ZX_j = X_j[:P] eta and ZXA_j = |X_j[:P]| |eta| (one warp per row of X).
+__global__ void __launch_bounds__(256) k_xeta(Dev D) {
+  const int a = blockIdx.y;
+  if (angle_done(D, a)) return;
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);  // = j * P + p
+  if (row >= D.L * D.P) return;
+  const int j = row / D.P, p = row % D.P;
+  const LayerDesc L = D.lay[j];
+  const int first = (L.if0 >= 0) ? L.if0 : L.if1;
+  const double2* eta = D.ETA + a * D.eta_stride + D.ifc[first].eta_off;
+  const double2* X = D.Xb + a * D.x_stride + L.x_off;
+  double sr = 0.0, si = 0.0, sa = 0.0;
+  for (int c = lane; c < L.c; c += 32) {
+    const double2 x = X[(size_t)c * L.p + p], e = eta[c];
+    sr = fma(x.x, e.x, fma(-x.y, e.y, sr));
+    si = fma(x.x, e.y, fma(x.y, e.x, si));
+    sa = fma(cabs1(x), cabs1(e), sa);
+  }
+  sr = warp_sum_dd(sr);
+  si = warp_sum_dd(si);
+  sa = warp_sum_dd(sa);
+  if (lane == 0) {
+    D.ZX[(size_t)a * D.L * D.P + row] = make_double2(sr, si);
+    D.ZXA[(size_t)a * D.L * D.P + row] = sa;
+  }
+}
+
+// r_i = f_i - [A_{i,i-1} A_{i,i} A_{i,i+1}] eta + [B_{i,i} B_{i,i+1}] [ZX_i; ZX_{i+1}]
+// (one warp per row, lanes over columns), with its scale s; per-angle maxima
+// of |r| and s by atomic max.
+__global__ void __launch_bounds__(256) k_resid(Dev D) {
+  const int i = blockIdx.y, a = blockIdx.z;
+  if (angle_done(D, a)) return;
+  const IfaceDesc f = D.ifc[i];
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (r >= f.n) return;
+  const double2* A = D.ROW + a * D.r_stride + f.row_off;
+  const double2* eta = D.ETA + a * D.eta_stride + f.eta_off - f.nl;  // eta_{i-1}, eta_i, eta_{i+1} are contiguous
+  const double2* Bm = D.B + f.b_off;
+  const size_t zo = (size_t)a * D.L * D.P + (size_t)i * D.P;  // [ZX_i; ZX_{i+1}]
+  const double2* z = D.ZX + zo;
+  const double* za = D.ZXA + zo;
+  double sr = 0.0, si = 0.0, sa = 0.0;
+  for (int c = lane; c < f.row_cols; c += 32) {
+    const double2 x = A[(size_t)c * f.n + r], e = eta[c];
+    sr = fma(x.x, e.x, fma(-x.y, e.y, sr));
+    si = fma(x.x, e.y, fma(x.y, e.x, si));
+    sa = fma(cabs1(x), cabs1(e), sa);
+  }
+  for (int c = lane; c < 2 * D.P; c += 32) {
+    const double2 x = Bm[(size_t)c * f.n + r], e = z[c];
+    sr = fma(-x.x, e.x, fma(x.y, e.y, sr));
+    si = fma(-x.x, e.y, fma(-x.y, e.x, si));
+    sa = fma(cabs1(x), za[c], sa);
+  }
+  sr = warp_sum_dd(sr);
+  si = warp_sum_dd(si);
+  sa = warp_sum_dd(sa);
+  if (lane == 0) {
+    const double2 fv = D.F[a * D.f_stride + f.rhs_off + r];
+    const double2 rv = make_double2(fv.x - sr, fv.y - si);
+    D.RES[a * D.eta_stride + f.eta_off + r] = rv;
+    unsigned long long* c = ctl(D, a);
+    atomicMax(c + 2, (unsigned long long)__double_as_longlong(cabs1(rv)));
+    atomicMax(c + 3, (unsigned long long)__double_as_longlong(sa + cabs1(fv)));
+  }
+}
+
+// omega of the residual just formed; marks converged angles done; on the
+// final check an angle above tol sets MLQP_ENOTCONV.  One thread per angle.
+__global__ void k_refine_ctl(Dev D, int last, double tol) {
+  for (int a = threadIdx.x; a < D.n_theta; a += blockDim.x) {
+    unsigned long long* c = ctl(D, a);
+    double* cd = D.RNRM + (size_t)a * RNRM_W;
+    if (c[4] == 0ull) {
+      const double rmax = __longlong_as_double((long long)c[2]);
+      const double smax = __longlong_as_double((long long)c[3]);
+      const double w = (smax > 0.0) ? rmax / smax : (rmax > 0.0 ? CUDART_INF : 0.0);
+      cd[0] = w;
+      if (w <= tol) c[4] = 1ull;
+    }
+    c[2] = 0ull;
+    c[3] = 0ull;
+    if (last && !(cd[0] <= tol)) atomicExch(D.STATUS, MLQP_ENOTCONV_CODE);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 solves with the stored factors.  Forward, interface t:
+//   w = P_t r_t - (stored left block of R32_t) y_{t-1},  y_t = L_t^{-1} w;
+// the left block holds the multipliers with the rows already permuted by
+// P_t.  Backward: v = y_t - U12_t d_{t+1},  d_t = U_t^{-1} v.  One CTA per
+// angle; triangular solves by 32-row blocks (one warp solves the diagonal
+// block, all threads update the rows beyond it).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fwd32(Dev D, int t, const int* permv) {
+  const int a = blockIdx.x;
+  if (angle_done(D, a)) return;
+  const IfaceDesc f = D.ifc[t];
+  const int n = f.n, ld = f.n;
+  const float2* Rt = D.ROW32 + a * D.r_stride + f.row_off;
+  const float2* Lt = Rt + (size_t)f.nl * n;  // diagonal block (unit lower part)
+  const int* pv = permv + a * D.piv_stride + f.eta_off;
+  const double2* res = D.RES + a * D.eta_stride + f.eta_off;
+  float2* y = D.Y32 + a * D.eta_stride + f.eta_off;
+  const float2* yprev = (t > 0) ? D.Y32 + a * D.eta_stride + D.ifc[t - 1].eta_off : nullptr;
+  extern __shared__ float2 wv[];  // n
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int r = tid; r < n; r += blockDim.x) {
+    const double2 x = res[pv[r]];
+    float sr = (float)x.x, si = (float)x.y;
+    if (t > 0) {
+      for (int c = 0; c < f.nl; ++c) {
+        const float2 l = Rt[(size_t)c * ld + r], yc = yprev[c];
+        sr = fmaf(-l.x, yc.x, fmaf(l.y, yc.y, sr));
+        si = fmaf(-l.x, yc.y, fmaf(-l.y, yc.x, si));
+      }
+    }
+    wv[r] = make_float2(sr, si);
+  }
+  __syncthreads();
+  const int nblk = (n + 31) / 32;
+  for (int b = 0; b < nblk; ++b) {
+    const int i0 = 32 * b, w = min(32, n - i0);
+    if (warp == 0) {
+      float2 v = (lane < w) ? wv[i0 + lane] : make_float2(0.f, 0.f);
+      for (int j = 0; j < w; ++j) {
+        const float xr = __shfl_sync(0xffffffffu, v.x, j), xi = __shfl_sync(0xffffffffu, v.y, j);
+        if (lane > j && lane < w) {
+          const float2 l = Lt[(size_t)(i0 + j) * ld + i0 + lane];
+          v.x = fmaf(-l.x, xr, fmaf(l.y, xi, v.x));
+          v.y = fmaf(-l.x, xi, fmaf(-l.y, xr, v.y));
+        }
+      }
+      if (lane < w) wv[i0 + lane] = v;
+    }
+    __syncthreads();
+    for (int r = i0 + w + tid; r < n; r += blockDim.x) {
+      float2 s = wv[r];
+      for (int j = 0; j < w; ++j) {
+        const float2 l = Lt[(size_t)(i0 + j) * ld + r], x = wv[i0 + j];
+        s.x = fmaf(-l.x, x.x, fmaf(l.y, x.y, s.x));
+        s.y = fmaf(-l.x, x.y, fmaf(-l.y, x.x, s.y));
+      }
+      wv[r] = s;
+    }
+    __syncthreads();
+  }
+  for (int r = tid; r < n; r += blockDim.x) y[r] = wv[r];
+}
+
+__global__ void __launch_bounds__(256) k_bwd32(Dev D, int t) {
+  const int a = blockIdx.x;
+  if (angle_done(D, a)) return;
+  const IfaceDesc f = D.ifc[t];
+  const int n = f.n, ld = f.n;
+  const float2* Rt = D.ROW32 + a * D.r_stride + f.row_off;
+  const float2* U = Rt + (size_t)f.nl * n;
+  const float2* U12 = Rt + (size_t)(f.nl + f.n) * n;
+  const float2* uinv = D.UDINV32 + a * D.piv_stride + f.eta_off;
+  float2* y = D.Y32 + a * D.eta_stride + f.eta_off;
+  const float2* dnext = (t + 1 < D.I) ? D.Y32 + a * D.eta_stride + D.ifc[t + 1].eta_off : nullptr;
+  extern __shared__ float2 vv[];  // n
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int r = tid; r < n; r += blockDim.x) {
+    float2 s = y[r];
+    if (dnext) {
+      for (int c = 0; c < f.nr; ++c) {
+        const float2 u = U12[(size_t)c * ld + r], d = dnext[c];
+        s.x = fmaf(-u.x, d.x, fmaf(u.y, d.y, s.x));
+        s.y = fmaf(-u.x, d.y, fmaf(-u.y, d.x, s.y));
+      }
+    }
+    vv[r] = s;
+  }
+  __syncthreads();
+  const int nblk = (n + 31) / 32;
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int i0 = 32 * b, w = min(32, n - i0);
+    if (warp == 0) {
+      float2 v = (lane < w) ? vv[i0 + lane] : make_float2(0.f, 0.f);
+      for (int j = w - 1; j >= 0; --j) {
+        if (lane == j) {
+          const float2 q = uinv[i0 + j];
+          v = make_float2(v.x * q.x - v.y * q.y, v.x * q.y + v.y * q.x);
+        }
+        const float xr = __shfl_sync(0xffffffffu, v.x, j), xi = __shfl_sync(0xffffffffu, v.y, j);
+        if (lane < j) {
+          const float2 u = U[(size_t)(i0 + j) * ld + i0 + lane];
+          v.x = fmaf(-u.x, xr, fmaf(u.y, xi, v.x));
+          v.y = fmaf(-u.x, xi, fmaf(-u.y, xr, v.y));
+        }
+      }
+      if (lane < w) vv[i0 + lane] = v;
+    }
+    __syncthreads();
+    for (int r = tid; r < i0; r += blockDim.x) {
+      float2 s = vv[r];
+      for (int j = 0; j < w; ++j) {
+        const float2 u = U[(size_t)(i0 + j) * ld + r], x = vv[i0 + j];
+        s.x = fmaf(-u.x, x.x, fmaf(u.y, x.y, s.x));
+        s.y = fmaf(-u.x, x.y, fmaf(-u.y, x.x, s.y));
+      }
+      vv[r] = s;
+    }
+    __syncthreads();
+  }
+  for (int r = tid; r < n; r += blockDim.x) y[r] = vv[r];
+}
+
+// eta (FP64) += d (FP32 correction), one CTA per angle.
+__global__ void __launch_bounds__(256) k_eta_update(Dev D, int n_den) {
+  const int a = blockIdx.x;
+  if (angle_done(D, a)) return;
+  double2* eta = D.ETA + a * D.eta_stride;
+  const float2* d = D.Y32 + a * D.eta_stride;
+  for (int r = threadIdx.x; r < n_den; r += blockDim.x) {
+    const float2 c = d[r];
+    double2 e = eta[r];
+    e.x += (double)c.x;
+    e.y += (double)c.y;
+    eta[r] = e;
+  }
+  if (threadIdx.x == 0) D.RNRM[(size_t)a * RNRM_W + 1] += 1.0;
+}
+
+cudaError_t launch_factor32(const Dev& D, const int* n_host, cudaStream_t s);
+
+cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s) {
+  if (D.n_tasks == 0) return cudaSuccess;
+  ++g_launches;
+  k_schur32<<<dim3(max_tiles, D.n_tasks, D.n_theta), 256, 0, s>>>(D);
+  return cudaGetLastError();
+}
+
+// Factorise A'_32 and refine eta in FP64: up to max_refine corrections,
+// each preceded by a residual and its backward error; a final residual
+// checks the last one.
+cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n_den, int max_refine, double tol,
+                               int* permv, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(D.F32, 0, sizeof(float2) * D.f_stride * D.n_theta, s);
+  if (e == cudaSuccess) e = launch_factor32(D, n_host, s);
+  if (e != cudaSuccess) return e;
+  ++g_launches;
+  k_compose_perm<<<dim3((D.I + 63) / 64, D.n_theta), 64, 0, s>>>(D, permv);
+  e = cudaMemsetAsync(D.ETA, 0, sizeof(double2) * D.eta_stride * D.n_theta, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(D.RNRM, 0, sizeof(double) * RNRM_W * D.n_theta, s);
+  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)maxn * sizeof(float2);
+  for (int it = 0; it <= max_refine; ++it) {
+    const int last = (it == max_refine);
+    ++g_launches;
+    k_xeta<<<dim3((D.L * D.P + 7) / 8, D.n_theta), 256, 0, s>>>(D);
+    ++g_launches;
+    k_resid<<<dim3((maxn + 7) / 8, D.I, D.n_theta), 256, 0, s>>>(D);
+    ++g_launches;
+    k_refine_ctl<<<1, 32, 0, s>>>(D, last, tol);
+    if (last) break;
+    for (int t = 0; t < D.I; ++t) {
+      ++g_launches;
+      k_fwd32<<<D.n_theta, 256, smem, s>>>(D, t, permv);
+    }
+    for (int t = D.I - 1; t >= 0; --t) {
+      ++g_launches;
+      k_bwd32<<<D.n_theta, 256, smem, s>>>(D, t);
+    }
+    ++g_launches;
+    k_eta_update<<<D.n_theta, 256, 0, s>>>(D, (int)n_den);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t mixed_configure(int maxn) {
+  const int smem = (int)((size_t)maxn * sizeof(float2));
+  cudaError_t e = cudaFuncSetAttribute(k_fwd32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bwd32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+}  // namespace mlqp

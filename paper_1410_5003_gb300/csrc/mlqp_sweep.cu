@@ -16,7 +16,9 @@
 // Each panel of NB columns takes three launches: the panel factorisation
 // (one CTA per angle, panel in shared memory), the row swaps / U12 rows /
 // bottom multipliers (column- and row-parallel), and the trailing update
-// (32 x 32 tiles, complex 3M products, FP64).
+// (32 x 32 tiles, complex 3M products).  The three kernels are templates on
+// the real type: FP64 for the plain path, FP32 for the factorisation of the
+// mixed-precision path (whose solves are refined in FP64, mlqp_mixed.cu).
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
 
@@ -44,14 +46,24 @@ __device__ __forceinline__ Step make_step(const Dev& D, int t) {
   return s;
 }
 
-__device__ __forceinline__ double cabs1(cplx a) { return fabs(a.re) + fabs(a.im); }
-
 // ---------------------------------------------------------------------------
 // Panel factorisation: top rows k..nt-1 of the E columns k..k+w-1, in shared
 // memory, one CTA per angle.  Pivot: largest |re| + |im| (first on ties),
 // compared as the bit patterns of the non-negative doubles (integer ALU).
 // One reciprocal per pivot, kept in UDINV for the later kernels.
 // ---------------------------------------------------------------------------
+template <typename R> struct Mats;
+template <> struct Mats<double> {
+  static __device__ __forceinline__ double2* rows(const Dev& D) { return D.ROW; }
+  static __device__ __forceinline__ double2* rhs(const Dev& D) { return D.F; }
+  static __device__ __forceinline__ double2* udinv(const Dev& D) { return D.UDINV; }
+};
+template <> struct Mats<float> {  // the FP32 factorisation of the mixed-precision path
+  static __device__ __forceinline__ float2* rows(const Dev& D) { return D.ROW32; }
+  static __device__ __forceinline__ float2* rhs(const Dev& D) { return D.F32; }
+  static __device__ __forceinline__ float2* udinv(const Dev& D) { return D.UDINV32; }
+};
+
 __device__ __forceinline__ void argmax_merge(unsigned long long& key, int& idx, unsigned long long k2, int i2) {
   if (k2 > key || (k2 == key && i2 < idx)) {
     key = k2;
@@ -59,19 +71,21 @@ __device__ __forceinline__ void argmax_merge(unsigned long long& key, int& idx, 
   }
 }
 
+template <typename R>
 __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k) {
   const int a = blockIdx.x;
   const Step S = make_step(D, t);
   const IfaceDesc ft = D.ifc[t];
   const int w = min(NB, S.nt - k);
   const int rows = S.nt - k;
-  double2* top = D.ROW + a * D.r_stride + ft.row_off;
+  vec2<R>* top = Mats<R>::rows(D) + a * D.r_stride + ft.row_off;
   const int ld = S.nt;
-  extern __shared__ double2 pan[];  // rows x w, column-major
+  extern __shared__ __align__(16) unsigned char pan_raw[];
+  vec2<R>* pan = reinterpret_cast<vec2<R>*>(pan_raw);  // rows x w, column-major
   __shared__ unsigned long long s_key[PANEL_THREADS / 32];
   __shared__ int s_idx[PANEL_THREADS / 32];
   __shared__ int s_piv[NB];
-  __shared__ double2 s_rinv;
+  __shared__ vec2<R> s_rinv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < rows * w; e += PANEL_THREADS) {
     const int r = e % rows, c = e / rows;
@@ -79,14 +93,13 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k)
   }
   __syncthreads();
   int* piv = D.LUPIV + a * D.piv_stride + ft.eta_off;
-  double2* udinv = D.UDINV + a * D.piv_stride + ft.eta_off;
+  vec2<R>* udinv = Mats<R>::udinv(D) + a * D.piv_stride + ft.eta_off;
   for (int c = 0; c < w; ++c) {
     // (1) candidate pivots: largest |re| + |im| per warp (bit patterns compared as integers)
     unsigned long long key = 0;
     int idx = c;
     for (int r = c + tid; r < rows; r += PANEL_THREADS) {
-      const double2 x = pan[(size_t)c * rows + r];
-      argmax_merge(key, idx, (unsigned long long)__double_as_longlong(fabs(x.x) + fabs(x.y)), r);
+      argmax_merge(key, idx, pivot_key(ldv<R>(&pan[(size_t)c * rows + r])), r);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -111,30 +124,30 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k)
       }
       const int pr = idx;
       if (pr != c && lane < w) {
-        const double2 x = pan[(size_t)lane * rows + c];
+        const vec2<R> x = pan[(size_t)lane * rows + c];
         pan[(size_t)lane * rows + c] = pan[(size_t)lane * rows + pr];
         pan[(size_t)lane * rows + pr] = x;
       }
       __syncwarp();
       if (lane == 0) {
-        const double pv = __longlong_as_double((long long)key);
-        if (!(pv > 0.0) || !isfinite(pv)) atomicExch(D.STATUS, MLQP_ESINGULAR_CODE);
+        if (!pivot_ok(key, R())) atomicExch(D.STATUS, MLQP_ESINGULAR_CODE);
         piv[k + c] = k + pr;
         s_piv[c] = k + pr;
-        const cplx ri = inv_fast(ld2(&pan[(size_t)c * rows + c]));
-        s_rinv = make_double2(ri.re, ri.im);
+        const cpx<R> ri = inv_fast_t(ldv<R>(&pan[(size_t)c * rows + c]));
+        s_rinv.x = ri.re;
+        s_rinv.y = ri.im;
         udinv[k + c] = s_rinv;
       }
     }
     __syncthreads();
     // (3) multipliers and rank-1 update of the remaining panel columns, row by row
-    const cplx ip = C(s_rinv.x, s_rinv.y);
+    const cpx<R> ip = mkc<R>(s_rinv.x, s_rinv.y);
     for (int r = c + 1 + tid; r < rows; r += PANEL_THREADS) {
-      const cplx l = ld2(&pan[(size_t)c * rows + r]) * ip;
-      st2(&pan[(size_t)c * rows + r], l);
+      const cpx<R> l = ldv<R>(&pan[(size_t)c * rows + r]) * ip;
+      stv<R>(&pan[(size_t)c * rows + r], l);
       for (int cc = c + 1; cc < w; ++cc) {
-        double2* q = &pan[(size_t)cc * rows + r];
-        st2(q, ld2(q) - l * ld2(&pan[(size_t)cc * rows + c]));
+        vec2<R>* q = &pan[(size_t)cc * rows + r];
+        stv<R>(q, ldv<R>(q) - l * ldv<R>(&pan[(size_t)cc * rows + c]));
       }
     }
     __syncthreads();
@@ -187,22 +200,23 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k)
 constexpr int PREP_THREADS = 128;
 constexpr int PREP_COLS = PREP_THREADS / 16;  // columns (or rows) per CTA
 
+template <typename R>
 __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, int n_col_ctas) {
   const int a = blockIdx.y;
   const Step S = make_step(D, t);
   const IfaceDesc ft = D.ifc[t];
   const int w = min(NB, S.nt - k);
-  double2* top = D.ROW + a * D.r_stride + ft.row_off;
-  double2* ftop = D.F + a * D.f_stride + ft.rhs_off;
+  vec2<R>* top = Mats<R>::rows(D) + a * D.r_stride + ft.row_off;
+  vec2<R>* ftop = Mats<R>::rhs(D) + a * D.f_stride + ft.rhs_off;
   const int ldt = S.nt;
-  __shared__ double2 blk[NB * NB];  // factored top w x w block (L11 \ U11), column-major
-  __shared__ double2 sinv[NB];
+  __shared__ vec2<R> blk[NB * NB];  // factored top w x w block (L11 \ U11), column-major
+  __shared__ vec2<R> sinv[NB];
   __shared__ int spos[2 * NB], ssrc[2 * NB], sn;
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
     const int r = e % w, c = e / w;
     blk[c * w + r] = top[(size_t)(S.nlt + k + c) * ldt + k + r];
   }
-  const double2* udinv = D.UDINV + a * D.piv_stride + ft.eta_off;
+  const vec2<R>* udinv = Mats<R>::udinv(D) + a * D.piv_stride + ft.eta_off;
   const int* pm = D.PERM + 80 * a;
   for (int e = threadIdx.x; e < w; e += blockDim.x) sinv[e] = udinv[k + e];
   if (threadIdx.x == 0) sn = pm[0];
@@ -219,20 +233,22 @@ __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, i
     const int ncol = S.nlt + S.nt + S.nb + 1;
     const int pc0 = S.nlt + k, pc1 = S.nlt + k + w;
     const bool live = (u < ncol) && !(u >= pc0 && u < pc1);  // panel columns: done by the panel kernel
-    double2* col = live ? ((u == ncol - 1) ? ftop : top + (size_t)u * ldt) : nullptr;
+    vec2<R>* col = live ? ((u == ncol - 1) ? ftop : top + (size_t)u * ldt) : nullptr;
     const int n = sn;
-    cplx x = C(0.0);
-    double2 extra = make_double2(0.0, 0.0);
+    cpx<R> x = mkc<R>(R(0));
+    vec2<R> extra;
+    extra.x = R(0);
+    extra.y = R(0);
     if (live) {
-      if (lane16 < w) x = ld2(&col[ssrc[lane16]]);
+      if (lane16 < w) x = ldv<R>(&col[ssrc[lane16]]);
       if (lane16 < n - w) extra = col[ssrc[w + lane16]];
     }
     __syncwarp();
     if (live && lane16 < n - w) col[spos[w + lane16]] = extra;
     if (live && u >= pc1) {
       for (int q = 0; q + 1 < w; ++q) {
-        const double xr = __shfl_sync(hmask, x.re, q, 16), xi = __shfl_sync(hmask, x.im, q, 16);
-        if (lane16 > q && lane16 < w) x = x - ld2(&blk[q * w + lane16]) * C(xr, xi);
+        const R xr = __shfl_sync(hmask, x.re, q, 16), xi = __shfl_sync(hmask, x.im, q, 16);
+        if (lane16 > q && lane16 < w) x = x - ldv<R>(&blk[q * w + lane16]) * mkc<R>(xr, xi);
       }
     } else {
       for (int q = 0; q + 1 < w; ++q) {  // keep the shuffles converged across the half-warp
@@ -241,23 +257,23 @@ __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, i
       }
     }
     __syncwarp();
-    if (live && lane16 < w) st2(&col[k + lane16], x);
+    if (live && lane16 < w) stv<R>(&col[k + lane16], x);
   } else {
     if (S.b < 0) return;
     const int r = (blockIdx.x - n_col_ctas) * PREP_COLS + slot;
     const bool live = r < S.nb;
     const IfaceDesc fb = D.ifc[S.b];
-    double2* bot = D.ROW + a * D.r_stride + fb.row_off;  // left block = E columns
+    vec2<R>* bot = Mats<R>::rows(D) + a * D.r_stride + fb.row_off;  // left block = E columns
     const int ldb = S.nb;
-    cplx x = C(0.0);
-    if (live && lane16 < w) x = ld2(&bot[(size_t)(k + lane16) * ldb + r]);
+    cpx<R> x = mkc<R>(R(0));
+    if (live && lane16 < w) x = ldv<R>(&bot[(size_t)(k + lane16) * ldb + r]);
     for (int q = 0; q < w; ++q) {
       // lane q finalises x_q = (a_q - sum_{q' < q} x_q' U_q'q) / U_qq, then all lanes c > q use it
-      if (lane16 == q) x = x * ld2(&sinv[q]);
-      const double xr = __shfl_sync(hmask, x.re, q, 16), xi = __shfl_sync(hmask, x.im, q, 16);
-      if (lane16 > q && lane16 < w) x = x - C(xr, xi) * ld2(&blk[lane16 * w + q]);
+      if (lane16 == q) x = x * ldv<R>(&sinv[q]);
+      const R xr = __shfl_sync(hmask, x.re, q, 16), xi = __shfl_sync(hmask, x.im, q, 16);
+      if (lane16 > q && lane16 < w) x = x - mkc<R>(xr, xi) * ldv<R>(&blk[lane16 * w + q]);
     }
-    if (live && lane16 < w) st2(&bot[(size_t)(k + lane16) * ldb + r], x);
+    if (live && lane16 < w) stv<R>(&bot[(size_t)(k + lane16) * ldb + r], x);
   }
 }
 
@@ -269,8 +285,9 @@ __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, i
 constexpr int UT = 32;
 constexpr int UPD_THREADS = 128;
 
-__device__ __forceinline__ double2* row_col_ptr(double2* top, int ldt, double2* ftop, double2* bot, int ldb,
-                                                double2* fbot, const Step& S, int k, int w, int v, int u) {
+template <typename V>
+__device__ __forceinline__ V* row_col_ptr(V* top, int ldt, V* ftop, V* bot, int ldb, V* fbot, const Step& S, int k,
+                                          int w, int v, int u) {
   const int tr = S.nt - k - w;  // trailing top rows / E columns
   if (v < tr) {
     const int row = k + w + v;
@@ -284,6 +301,7 @@ __device__ __forceinline__ double2* row_col_ptr(double2* top, int ldt, double2* 
   return fbot + row;
 }
 
+template <typename R>
 __global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k) {
   const int a = blockIdx.y;
   const Step S = make_step(D, t);
@@ -295,23 +313,25 @@ __global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k) 
   const int tile_r = blockIdx.x / tiles_c, tile_c = blockIdx.x % tiles_c;
   const int row0 = tile_r * UT, col0 = tile_c * UT;
   if (row0 >= nrows) return;
-  double2* top = D.ROW + a * D.r_stride + ft.row_off;
-  double2* ftop = D.F + a * D.f_stride + ft.rhs_off;
-  double2* bot = nullptr;
-  double2* fbot = nullptr;
+  vec2<R>* top = Mats<R>::rows(D) + a * D.r_stride + ft.row_off;
+  vec2<R>* ftop = Mats<R>::rhs(D) + a * D.f_stride + ft.rhs_off;
+  vec2<R>* bot = nullptr;
+  vec2<R>* fbot = nullptr;
   if (S.b >= 0) {
     const IfaceDesc fb = D.ifc[S.b];
-    bot = D.ROW + a * D.r_stride + fb.row_off;
-    fbot = D.F + a * D.f_stride + fb.rhs_off;
+    bot = Mats<R>::rows(D) + a * D.r_stride + fb.row_off;
+    fbot = Mats<R>::rhs(D) + a * D.f_stride + fb.rhs_off;
   }
   const int ldt = S.nt, ldb = S.nb;
-  __shared__ double As[NB][3][UT];
-  __shared__ double Bs[NB][3][UT];
+  __shared__ R As[NB][3][UT];
+  __shared__ R Bs[NB][3][UT];
   const int tid = threadIdx.x;
   for (int e = tid; e < UT * NB; e += UPD_THREADS) {
     const int r = e % UT, kk = e / UT;
     const int v = row0 + r;
-    double2 x = make_double2(0.0, 0.0);
+    vec2<R> x;
+    x.x = R(0);
+    x.y = R(0);
     if (v < nrows && kk < w) {
       if (v < tr) x = top[(size_t)(S.nlt + k + kk) * ldt + k + w + v];
       else x = bot[(size_t)(k + kk) * ldb + (v - tr)];
@@ -323,7 +343,9 @@ __global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k) 
   for (int e = tid; e < UT * NB; e += UPD_THREADS) {
     const int kk = e % NB, c = e / NB;
     const int u = col0 + c;
-    double2 x = make_double2(0.0, 0.0);
+    vec2<R> x;
+    x.x = R(0);
+    x.y = R(0);
     if (u < ncols && kk < w) {
       const int row = k + kk;
       if (u < tr) x = top[(size_t)(S.nlt + k + w + u) * ldt + row];
@@ -336,9 +358,9 @@ __global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k) 
   }
   __syncthreads();
   const int tx = tid & 7, ty = tid >> 3;  // 2 rows x 4 columns per thread
-  double t1[2][4] = {}, t2[2][4] = {}, t3[2][4] = {};
+  R t1[2][4] = {}, t2[2][4] = {}, t3[2][4] = {};
   for (int kk = 0; kk < w; ++kk) {
-    double ar[2], ai[2], as[2], br[4], bi[4], bs[4];
+    R ar[2], ai[2], as[2], br[4], bi[4], bs[4];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       ar[q] = As[kk][0][ty * 2 + q];
@@ -366,8 +388,8 @@ __global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k) 
     for (int z = 0; z < 4; ++z) {
       const int v = row0 + ty * 2 + q, u = col0 + tx * 4 + z;
       if (v < nrows && u < ncols) {
-        double2* p = row_col_ptr(top, ldt, ftop, bot, ldb, fbot, S, k, w, v, u);
-        double2 x = *p;
+        vec2<R>* p = row_col_ptr(top, ldt, ftop, bot, ldb, fbot, S, k, w, v, u);
+        vec2<R> x = *p;
         x.x -= t1[q][z] - t2[q][z];
         x.y -= t3[q][z] - t1[q][z] - t2[q][z];
         *p = x;
@@ -494,7 +516,10 @@ __global__ void __launch_bounds__(128) k_recover(Dev D) {
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s) {
+// The block LU of the forward sweep, in precision R (FP64: plain path on ROW/F;
+// FP32: factorisation of the mixed path on ROW32/F32).
+template <typename R>
+cudaError_t launch_factor(const Dev& D, const int* n_host, cudaStream_t s) {
   const int I = D.I;
   cudaError_t e;
   for (int t = 0; t < I; ++t) {
@@ -503,24 +528,35 @@ cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s) {
     const int nlt = (t > 0) ? n_host[t - 1] : 0;
     for (int k = 0; k < nt; k += NB) {
       const int w = (nt - k < NB) ? nt - k : NB;
-      const size_t smem = (size_t)(nt - k) * w * sizeof(double2);
+      const size_t smem = (size_t)(nt - k) * w * sizeof(vec2<R>);
       ++g_launches;
-      k_lu_panel<<<D.n_theta, PANEL_THREADS, smem, s>>>(D, t, k);
+      k_lu_panel<R><<<D.n_theta, PANEL_THREADS, smem, s>>>(D, t, k);
       const int ncol = nlt + nt + nb + 1;
       const int n_col_ctas = (ncol + PREP_COLS - 1) / PREP_COLS;
       const int n_row_ctas = (nb + PREP_COLS - 1) / PREP_COLS;
       ++g_launches;
-      k_lu_prep<<<dim3(n_col_ctas + n_row_ctas, D.n_theta), PREP_THREADS, 0, s>>>(D, t, k, n_col_ctas);
+      k_lu_prep<R><<<dim3(n_col_ctas + n_row_ctas, D.n_theta), PREP_THREADS, 0, s>>>(D, t, k, n_col_ctas);
       const int tr = nt - k - w;
       const int nrows = tr + nb, ncols = tr + nb + 1;
       if (nrows > 0) {
         const int tiles = ((nrows + UT - 1) / UT) * ((ncols + UT - 1) / UT);
         ++g_launches;
-        k_lu_update<<<dim3(tiles, D.n_theta), UPD_THREADS, 0, s>>>(D, t, k);
+        k_lu_update<R><<<dim3(tiles, D.n_theta), UPD_THREADS, 0, s>>>(D, t, k);
       }
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_factor32(const Dev& D, const int* n_host, cudaStream_t s) {
+  return launch_factor<float>(D, n_host, s);
+}
+
+cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s) {
+  const int I = D.I;
+  cudaError_t e = launch_factor<double>(D, n_host, s);
+  if (e != cudaSuccess) return e;
   for (int t = I - 1; t >= 0; --t) {
     ++g_launches;
     k_back_matvec<<<dim3((n_host[t] + 7) / 8, D.n_theta), 256, 0, s>>>(D, t);
@@ -540,7 +576,10 @@ size_t sweep_panel_smem_max(int maxn) { return (size_t)maxn * NB * sizeof(double
 
 cudaError_t sweep_configure(int maxn) {
   const size_t smem = sweep_panel_smem_max(maxn);
-  return cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_lu_panel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_lu_panel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
 }
 
 }  // namespace mlqp

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmlqp.so")
 MLQP_OK, MLQP_EINVAL, MLQP_ENOMEM, MLQP_ECUDA, MLQP_ESINGULAR, MLQP_ETIMEOUT, MLQP_ENOTCONV, MLQP_ESTATE = range(8)
 MLQP_FP64, MLQP_MIXED = 0, 1
 STAGE_GEOM, STAGE_FILL, STAGE_LSQ, STAGE_SCHUR, STAGE_SWEEP, STAGE_RECOVER = range(6)
-BLK_ROW, BLK_B, BLK_QP, BLK_CP, BLK_X, BLK_RHS, BLK_NODES, BLK_ETA, BLK_AMP = range(9)
+BLK_ROW, BLK_B, BLK_QP, BLK_CP, BLK_X, BLK_RHS, BLK_NODES, BLK_ETA, BLK_AMP, BLK_REFINE = range(10)
 
 
 class mlqp_interface(ct.Structure):
@@ -110,7 +110,7 @@ def make_params(p, precision=MLQP_FP64, max_refine=0, refine_tol=0.0):
                        float(refine_tol))
 
 
-def mlqp_setup(prob, precision=MLQP_FP64):
+def mlqp_setup(prob, precision=MLQP_FP64, max_refine=0, refine_tol=0.0):
     """prob: an object with .ifaces (y0, a, b, N), .k (complex, I+1), .d,
     .theta, .params (P, R, Mw, M, K, gap_U, gap_D, cut_a, cut_b, lsq_rcond).
     Returns (ctx handle, keep-alive list)."""
@@ -126,7 +126,7 @@ def mlqp_setup(prob, precision=MLQP_FP64):
     k = np.ascontiguousarray(np.stack([np.real(prob.k), np.imag(prob.k)], axis=1).ravel(), dtype=np.float64)
     th = np.ascontiguousarray(prob.theta, dtype=np.float64)
     keep += [k, th]
-    prm = make_params(prob.params, precision)
+    prm = make_params(prob.params, precision, max_refine, refine_tol)
     ctx = ct.c_void_p()
     st = lib.mlqp_setup(arr, I, _dptr(k), float(prob.d), _dptr(th), len(th), ct.byref(prm), ct.byref(ctx))
     if st != MLQP_OK:
@@ -140,12 +140,14 @@ def mlqp_setup(prob, precision=MLQP_FP64):
 class Context:
     """One problem on one device: owns the host context and a torch workspace."""
 
-    def __init__(self, prob, device="cuda", stream=None, precision=MLQP_FP64):
+    def __init__(self, prob, device="cuda", stream=None, precision=MLQP_FP64, max_refine=10, refine_tol=1e-15):
         import torch
         self.torch = torch
         self.lib = load()
         self.prob = prob
-        self.ctx, self._keep = mlqp_setup(prob, precision)
+        self.precision = precision
+        self.ctx, self._keep = mlqp_setup(prob, precision, max_refine if precision == MLQP_MIXED else 0,
+                                          refine_tol if precision == MLQP_MIXED else 0.0)
         n_den = ct.c_long()
         n_modes = ct.c_int()
         _check(self.ctx, self.lib.mlqp_sizes(self.ctx, ct.byref(n_den), ct.byref(n_modes)))
@@ -230,6 +232,8 @@ class Context:
         if kind == BLK_NODES:
             v = self.ws[start:].view(t.float64)
             return t.stack([v[q * ld.value: q * ld.value + r.value] for q in range(5)])
+        if kind == BLK_REFINE:
+            return self.ws[start:start + 16].view(t.float64)
         nbytes = 16 * ld.value * c.value
         v = self.ws[start:start + nbytes].view(t.complex128).view(c.value, ld.value)
         return v[:, :r.value].transpose(0, 1)

@@ -290,3 +290,64 @@ def test_zero_pivot_is_reported_not_faulted(M):
     out = ctx.solve_host()   # a fresh solve refills everything
     assert np.all(np.isfinite(out["aU"]))
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["config1", "small3", "small3_lossy", "uneven"])
+def test_mixed_precision_matches_oracle(M, name):
+    """FP32 Schur complements and block LU with FP64 iterative refinement
+    (residual from the unreduced FP64 operator) reproduce the oracle's
+    amplitudes to 1e-9; refinement stops once the normwise backward error of
+    eta against the FP64 residual's rounding scale is below 1e-15."""
+    prob = PROBLEMS[name]()
+    ctx = M.Context(prob, precision=M.MLQP_MIXED, max_refine=10, refine_tol=1e-15)
+    out = ctx.solve_host()
+    asm = O.Assembler(prob)
+    for a in range(prob.n_theta):
+        r = O.solve(prob, a, asm)
+        ag = np.concatenate([out["aU"][a], out["aD"][a]])
+        ao = np.concatenate([r["aU"], r["aD"]])
+        assert rel(ag, ao) < AMP_TOL, (name, a, rel(ag, ao))
+        omega, steps = ctx.block(M.BLK_REFINE, 1, a).cpu().numpy()
+        assert omega <= 1e-15 and 1 <= steps <= 10, (omega, steps)
+    ctx.close()
+
+
+def test_mixed_precision_on_benchmark_stack(M):
+    """Mixed form on the 20-interface, 3-angle stack: amplitudes agree with
+    the plain FP64 GPU path and with the oracle to 1e-9."""
+    prob = config2()
+    plain = M.Context(prob)
+    o64 = plain.solve_host()
+    plain.close()
+    mixed = M.Context(prob, precision=M.MLQP_MIXED, max_refine=10, refine_tol=1e-15)
+    o32 = mixed.solve_host()
+    steps = [mixed.block(M.BLK_REFINE, 1, a).cpu().numpy()[1] for a in range(prob.n_theta)]
+    mixed.close()
+    assert max(steps) <= 6, steps
+    asm = O.Assembler(prob)
+    for a in range(prob.n_theta):
+        ag = np.concatenate([o32["aU"][a], o32["aD"][a]])
+        ap = np.concatenate([o64["aU"][a], o64["aD"][a]])
+        assert rel(ag, ap) < AMP_TOL
+        r = O.solve(prob, a, asm)
+        assert rel(ag, np.concatenate([r["aU"], r["aD"]])) < AMP_TOL
+
+
+def test_mixed_precision_reports_unreached_tolerance(M):
+    """A tolerance below the attainable backward error (about 1e-17) ends in
+    MLQP_ENOTCONV after exactly max_refine corrections; a fresh context with
+    the default tolerance then reproduces the FP64 amplitudes."""
+    prob = small_stack(I=2, N=48, P=40, Mw=30, K=12, M=30)
+    ctx = M.Context(prob, precision=M.MLQP_MIXED, max_refine=2, refine_tol=1e-30)
+    with pytest.raises(M.MlqpError) as e:
+        ctx.solve_host()
+    assert e.value.status == M.MLQP_ENOTCONV
+    omega, steps = ctx.block(M.BLK_REFINE, 1, 0).cpu().numpy()
+    assert steps == 2 and 0.0 < omega < 1e-3
+    ctx.close()
+    ok = M.Context(prob, precision=M.MLQP_MIXED)
+    out = ok.solve_host()
+    ref = M.Context(prob).solve_host()
+    for a in range(prob.n_theta):
+        assert rel(np.concatenate([out["aU"][a], out["aD"][a]]), np.concatenate([ref["aU"][a], ref["aD"][a]])) < 1e-12
+    ok.close()
