@@ -54,7 +54,7 @@ typedef struct mlqp_ctx mlqp_ctx;
 
 /* One interface: y(x) = y0 + sum_{m=1}^{n_modes} a[m-1] cos(2 pi m x/d)
  *                                         + b[m-1] sin(2 pi m x/d),
- * discretised by the periodic trapezoid rule with n_nodes (even) nodes
+ * discretised by the periodic trapezoid rule with n_nodes (even, 8..512) nodes
  * s_j = 2 pi (j - 1/2)/N (Sec. 2.5, eq. Giquad). */
 typedef struct {
   double y0;
@@ -98,7 +98,7 @@ typedef struct {
 /* Validates the problem and records it on the host (no device work).
  * k: 2(I+1) doubles (Re k_1, Im k_1, ..., Re k_{I+1}, Im k_{I+1}); k_1 real,
  * every Im k_i >= 0, Re k_i > 0.  theta: n_theta angles in (-pi, 0).
- * Errors: MLQP_EINVAL (bad sizes, odd or too small n_nodes, theta out of
+ * Errors: MLQP_EINVAL (bad sizes, odd n_nodes or outside 8..512, theta out of
  * range, M < 2K+1, ...), MLQP_ENOMEM.  *out receives a context in both
  * cases (NULL only if even that allocation failed): after an error it only
  * carries the message for mlqp_last_error and must be destroyed. */

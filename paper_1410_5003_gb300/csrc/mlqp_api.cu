@@ -18,13 +18,13 @@ cudaError_t launch_geometry(const Dev& D, double* scal, cudaStream_t s);
 cudaError_t launch_fill(const Dev& D, const double* scal, cudaStream_t s);
 cudaError_t launch_lsq(const Dev& D, int max_m, int max_p, int max_c, cudaStream_t s);
 cudaError_t launch_schur(const Dev& D, int max_tiles, cudaStream_t s);
-cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s);
+cudaError_t launch_sweep(const Dev& D, const int* n_host, const AngleStreams& A);
 cudaError_t launch_recover(const Dev& D, cudaStream_t s);
 cudaError_t sweep_configure(int maxn);
 cudaError_t mixed_configure(int maxn);
 cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s);
 cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n_den, int max_refine, double tol,
-                               int* permv, cudaStream_t s);
+                               int* permv, const AngleStreams& A);
 cudaError_t lsq_configure(int max_m, int max_p);
 cudaError_t launch_hankel_eval(const double* kr, int n, double* out, cudaStream_t s);
 extern thread_local long g_launches;
@@ -66,7 +66,77 @@ struct mlqp_ctx {
   std::string err;
   bool valid = false;
   long launches = 0;  // kernel launches issued by this context
+  AngleStreams astr;  // the sweep's angle groups (streams and events owned here)
+  int astr_dev = -1;
+  // Each stage is captured once into a CUDA graph (on the internal stream
+  // cap) and replayed on the bound stream; the kernels take the workspace
+  // pointers by value, so a new workspace address drops the graphs.
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec[MLQP_STAGE_RECOVER + 1] = {};
+  long glaunches[MLQP_STAGE_RECOVER + 1] = {};
 };
+
+static void drop_graphs(mlqp_ctx* c) {
+  for (auto& g : c->gexec) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
+static void destroy_angle_streams(mlqp_ctx* c) {
+  drop_graphs(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  c->cap = nullptr;
+  AngleStreams& A = c->astr;
+  for (int g = 0; g < MAX_ANGLE_STREAMS; ++g) {
+    if (A.s[g]) cudaStreamDestroy(A.s[g]);
+    if (A.ps[g]) cudaStreamDestroy(A.ps[g]);
+    if (A.join[g]) cudaEventDestroy(A.join[g]);
+    if (A.ev_next[g]) cudaEventDestroy(A.ev_next[g]);
+    if (A.ev_panel[g]) cudaEventDestroy(A.ev_panel[g]);
+    A.s[g] = A.ps[g] = nullptr;
+    A.join[g] = A.ev_next[g] = A.ev_panel[g] = nullptr;
+  }
+  if (A.fork) cudaEventDestroy(A.fork);
+  A.fork = nullptr;
+  A.n = 0;
+  c->astr_dev = -1;
+}
+
+// Streams of the sweep's angle groups, on the device of the bound stream:
+// min(n_theta, MAX_ANGLE_STREAMS) contiguous groups.
+static cudaError_t make_angle_streams(mlqp_ctx* c) {
+  int dev = 0, cur = 0;
+  cudaError_t e = cudaStreamGetDevice(c->stream, &dev);
+  if (e != cudaSuccess) return e;
+  AngleStreams& A = c->astr;
+  if (c->astr_dev != dev) {
+    destroy_angle_streams(c);
+    if ((e = cudaGetDevice(&cur)) != cudaSuccess) return e;
+    if ((e = cudaSetDevice(dev)) != cudaSuccess) return e;
+    e = cudaEventCreateWithFlags(&A.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    for (int g = 0; g < MAX_ANGLE_STREAMS && e == cudaSuccess; ++g) {
+      e = cudaStreamCreateWithFlags(&A.s[g], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&A.ps[g], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&A.join[g], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&A.ev_next[g], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&A.ev_panel[g], cudaEventDisableTiming);
+    }
+    const cudaError_t r = cudaSetDevice(cur);
+    if (e != cudaSuccess) return e;
+    if (r != cudaSuccess) return r;
+    c->astr_dev = dev;
+  }
+  A.main = c->stream;
+  A.n = c->n_theta < MAX_ANGLE_STREAMS ? c->n_theta : MAX_ANGLE_STREAMS;
+  for (int g = 0, a = 0; g < A.n; ++g) {
+    A.a0[g] = a;
+    A.na[g] = c->n_theta / A.n + (g < c->n_theta % A.n ? 1 : 0);
+    a += A.na[g];
+  }
+  return cudaSuccess;
+}
 
 static mlqp_status fail(mlqp_ctx* c, mlqp_status s, const char* fmt, ...) {
   if (c) {
@@ -147,6 +217,7 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   for (int i = 0; i < I; ++i) {
     const mlqp_interface& f = ifaces[i];
     if (f.n_nodes < 8 || (f.n_nodes & 1)) return bad("n_nodes must be even and >= 8");
+    if (f.n_nodes > 512) return bad("n_nodes must be <= 512");
     if (f.n_modes < 0 || (f.n_modes > 0 && (!f.a || !f.b))) return bad("bad Fourier coefficients");
     if (!std::isfinite(f.y0)) return bad("y0 must be finite");
     IfaceDesc& D = c->ifc[i];
@@ -356,6 +427,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   if (!dev_ws) return fail(c, MLQP_EINVAL, "null workspace");
   if (reinterpret_cast<uintptr_t>(dev_ws) & 255) return fail(c, MLQP_EINVAL, "workspace must be 256-byte aligned");
   if (bytes < c->ws_bytes) return fail(c, MLQP_ENOMEM, "workspace too small: %zu < %zu bytes", bytes, c->ws_bytes);
+  if (c->ws != static_cast<char*>(dev_ws)) drop_graphs(c);
   c->ws = static_cast<char*>(dev_ws);
   c->stream = static_cast<cudaStream_t>(stream);
   Dev& D = c->D;
@@ -464,38 +536,66 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   if ((e = lsq_configure(c->max_m, c->max_p)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
   if (q.precision == MLQP_MIXED && (e = mixed_configure(c->maxn)) != cudaSuccess)
     return cuda_fail(c, e, "kernel configuration");
+  if ((e = make_angle_streams(c)) != cudaSuccess) return cuda_fail(c, e, "sweep streams");
   c->bound = true;
   return MLQP_OK;
+}
+
+// Enqueues the kernels of one stage on stream st (angle groups forked from st).
+static cudaError_t enqueue_stage(mlqp_ctx* c, int stage, cudaStream_t st) {
+  double* scal = at<double>(c, c->r_scal);
+  AngleStreams A = c->astr;
+  A.main = st;
+  cudaError_t e = cudaSuccess;
+  switch (stage) {
+    case MLQP_STAGE_GEOM:
+      e = cudaMemsetAsync(c->D.STATUS, 0, sizeof(int), st);
+      if (e == cudaSuccess) e = launch_geometry(c->D, scal, st);
+      break;
+    case MLQP_STAGE_FILL: e = launch_fill(c->D, scal, st); break;
+    case MLQP_STAGE_LSQ: e = launch_lsq(c->D, c->max_m, c->max_p, c->max_c, st); break;
+    case MLQP_STAGE_SCHUR:
+      e = (c->prm.precision == MLQP_MIXED) ? launch_schur32(c->D, c->max_tiles, st)
+                                           : launch_schur(c->D, c->max_tiles, st);
+      break;
+    case MLQP_STAGE_SWEEP:
+      e = (c->prm.precision == MLQP_MIXED)
+              ? launch_mixed_solve(c->D, c->n_host.data(), c->maxn, c->n_den, c->prm.max_refine, c->prm.refine_tol,
+                                   at<int>(c, c->r_PERMV), A)
+              : launch_sweep(c->D, c->n_host.data(), A);
+      break;
+    case MLQP_STAGE_RECOVER: e = launch_recover(c->D, st); break;
+    default: e = cudaErrorInvalidValue;
+  }
+  return e;
 }
 
 mlqp_status mlqp_run_stage(mlqp_ctx* c, int stage) {
   if (!c) return MLQP_EINVAL;
   if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
-  double* scal = at<double>(c, c->r_scal);
+  if (stage < MLQP_STAGE_GEOM || stage > MLQP_STAGE_RECOVER) return fail(c, MLQP_EINVAL, "unknown stage %d", stage);
   cudaError_t e = cudaSuccess;
-  g_launches = 0;
-  switch (stage) {
-    case MLQP_STAGE_GEOM:
-      e = cudaMemsetAsync(c->D.STATUS, 0, sizeof(int), c->stream);
-      if (e == cudaSuccess) e = launch_geometry(c->D, scal, c->stream);
-      break;
-    case MLQP_STAGE_FILL: e = launch_fill(c->D, scal, c->stream); break;
-    case MLQP_STAGE_LSQ: e = launch_lsq(c->D, c->max_m, c->max_p, c->max_c, c->stream); break;
-    case MLQP_STAGE_SCHUR:
-      e = (c->prm.precision == MLQP_MIXED) ? launch_schur32(c->D, c->max_tiles, c->stream)
-                                           : launch_schur(c->D, c->max_tiles, c->stream);
-      break;
-    case MLQP_STAGE_SWEEP:
-      e = (c->prm.precision == MLQP_MIXED)
-              ? launch_mixed_solve(c->D, c->n_host.data(), c->maxn, c->n_den, c->prm.max_refine, c->prm.refine_tol,
-                                   at<int>(c, c->r_PERMV), c->stream)
-              : launch_sweep(c->D, c->n_host.data(), c->stream);
-      break;
-    case MLQP_STAGE_RECOVER: e = launch_recover(c->D, c->stream); break;
-    default: return fail(c, MLQP_EINVAL, "unknown stage %d", stage);
+  if (!c->gexec[stage]) {
+    g_launches = 0;
+    e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stage capture");
+    const cudaError_t el = enqueue_stage(c, stage, c->cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(c->cap, &graph);
+    if (el != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(c, el != cudaSuccess ? el : e, "stage capture");
+    }
+    e = cudaGraphInstantiate(&c->gexec[stage], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->gexec[stage] = nullptr;
+      return cuda_fail(c, e, "stage graph");
+    }
+    c->glaunches[stage] = g_launches;
   }
-  c->launches += g_launches;
-  if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  if ((e = cudaGraphLaunch(c->gexec[stage], c->stream)) != cudaSuccess) return cuda_fail(c, e, "stage launch");
+  c->launches += c->glaunches[stage];
   return MLQP_OK;
 }
 
@@ -627,10 +727,9 @@ const char* mlqp_last_error(const mlqp_ctx* c) { return c ? c->err.c_str() : "nu
 
 void mlqp_destroy(mlqp_ctx* c) {
   if (!c) return;
-  if (c->staging) {
-    if (c->bound) cudaStreamSynchronize(c->stream);
-    cudaFreeHost(c->staging);
-  }
+  if (c->bound) cudaStreamSynchronize(c->stream);
+  if (c->staging) cudaFreeHost(c->staging);
+  destroy_angle_streams(c);
   delete c;
 }
 

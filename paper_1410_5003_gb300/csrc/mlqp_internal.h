@@ -51,6 +51,19 @@ struct SchurTask {
   int k1, k2;             // inner dimensions (k2 = 0: single term)
 };
 
+// Angle groups of the sweep, each on its own stream (forked from and joined
+// back into the context's stream), with a second stream per group for the
+// look-ahead panel factorisations.
+constexpr int MAX_ANGLE_STREAMS = 4;
+struct AngleStreams {
+  cudaStream_t main = nullptr;
+  int n = 0;
+  int a0[MAX_ANGLE_STREAMS] = {}, na[MAX_ANGLE_STREAMS] = {};
+  cudaStream_t s[MAX_ANGLE_STREAMS] = {}, ps[MAX_ANGLE_STREAMS] = {};
+  cudaEvent_t fork = nullptr, join[MAX_ANGLE_STREAMS] = {};
+  cudaEvent_t ev_next[MAX_ANGLE_STREAMS] = {}, ev_panel[MAX_ANGLE_STREAMS] = {};
+};
+
 // Problem scalars and workspace pointers, passed by value to the kernels.
 constexpr int RNRM_W = 8;  // doubles per angle of the refinement control block
 

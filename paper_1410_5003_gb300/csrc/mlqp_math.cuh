@@ -133,6 +133,20 @@ __device__ __forceinline__ unsigned long long pivot_key(cpx<double> a) {
 __device__ __forceinline__ unsigned long long pivot_key(cpx<float> a) {
   return (unsigned long long)__float_as_uint(fabsf(a.re) + fabsf(a.im));
 }
+// 32-bit pivot keys: the high word of the double |re| + |im| (order-preserving
+// truncation: a >= b implies key(a) >= key(b)), or the float's bits.
+__device__ __forceinline__ unsigned pivot_key32(cpx<double> a) {
+  return (unsigned)((unsigned long long)__double_as_longlong(fabs(a.re) + fabs(a.im)) >> 32);
+}
+__device__ __forceinline__ unsigned pivot_key32(cpx<float> a) { return __float_as_uint(fabsf(a.re) + fabsf(a.im)); }
+__device__ __forceinline__ bool pivot_ok32(unsigned key, double) {
+  const double v = __longlong_as_double((long long)((unsigned long long)key << 32));
+  return v > 0.0 && isfinite(v);
+}
+__device__ __forceinline__ bool pivot_ok32(unsigned key, float) {
+  const float v = __uint_as_float(key);
+  return v > 0.0f && isfinite(v);
+}
 __device__ __forceinline__ bool pivot_ok(unsigned long long key, double) {
   const double v = __longlong_as_double((long long)key);
   return v > 0.0 && isfinite(v);

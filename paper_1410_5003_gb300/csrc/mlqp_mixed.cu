@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256) k_eta_update(Dev D, int n_den) {
   if (threadIdx.x == 0) D.RNRM[(size_t)a * RNRM_W + 1] += 1.0;
 }
 
-cudaError_t launch_factor32(const Dev& D, const int* n_host, cudaStream_t s);
+cudaError_t launch_factor32(const Dev& D, const int* n_host, const AngleStreams& A);
 
 cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s) {
   if (D.n_tasks == 0) return cudaSuccess;
@@ -380,9 +380,10 @@ cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s) {
 // each preceded by a residual and its backward error; a final residual
 // checks the last one.
 cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n_den, int max_refine, double tol,
-                               int* permv, cudaStream_t s) {
+                               int* permv, const AngleStreams& A) {
+  cudaStream_t s = A.main;
   cudaError_t e = cudaMemsetAsync(D.F32, 0, sizeof(float2) * D.f_stride * D.n_theta, s);
-  if (e == cudaSuccess) e = launch_factor32(D, n_host, s);
+  if (e == cudaSuccess) e = launch_factor32(D, n_host, A);
   if (e != cudaSuccess) return e;
   ++g_launches;
   k_compose_perm<<<dim3((D.I + 63) / 64, D.n_theta), 64, 0, s>>>(D, permv);

@@ -13,12 +13,17 @@
 // left block holds the multipliers.  Everything stays in place in the block
 // rows R_{i-1}, R_i.  The backward sweep solves U_i eta_i = g_i - U12_i eta_{i+1}.
 //
-// Each panel of NB columns takes three launches: the panel factorisation
-// (one CTA per angle, panel in shared memory), the row swaps / U12 rows /
-// bottom multipliers (column- and row-parallel), and the trailing update
-// (32 x 32 tiles, complex 3M products).  The three kernels are templates on
-// the real type: FP64 for the plain path, FP32 for the factorisation of the
+// Each panel of NB columns takes three kernels: the panel factorisation (a
+// cluster of PCL CTAs per angle, panel rows split over their shared memory),
+// the row swaps / U12 rows / bottom multipliers (column- and row-parallel),
+// and the trailing update (32 x 32 tiles, complex 3M products).  With
+// look-ahead, the update first finishes the next panel's columns, and that
+// panel is factored on a second stream while the rest of the update runs.
+// Angle groups run on streams of their own.  The kernels are templates on the
+// real type: FP64 for the plain path, FP32 for the factorisation of the
 // mixed-precision path (whose solves are refined in FP64, mlqp_mixed.cu).
+#include <cooperative_groups.h>
+
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
 
@@ -27,7 +32,10 @@ namespace mlqp {
 extern thread_local long g_launches;
 
 constexpr int NB = 16;        // panel width
-constexpr int PANEL_THREADS = 256;
+// Look-ahead (panel k+1 factored on a second stream beside the rest of update
+// k) is off: measured on GB300, the latency-bound panel slows down more from
+// sharing the SMs' FP64 pipes with the update than the overlap saves.
+constexpr bool LOOKAHEAD = false;
 constexpr int MLQP_ESINGULAR_CODE = 4;
 
 struct Step {
@@ -47,10 +55,9 @@ __device__ __forceinline__ Step make_step(const Dev& D, int t) {
 }
 
 // ---------------------------------------------------------------------------
-// Panel factorisation: top rows k..nt-1 of the E columns k..k+w-1, in shared
-// memory, one CTA per angle.  Pivot: largest |re| + |im| (first on ties),
-// compared as the bit patterns of the non-negative doubles (integer ALU).
-// One reciprocal per pivot, kept in UDINV for the later kernels.
+// Pivot rule of the panel factorisation: largest |re| + |im| (smallest
+// position on ties), compared as the bit patterns of the non-negative values
+// (integer ALU).  One reciprocal per pivot, kept in UDINV for later kernels.
 // ---------------------------------------------------------------------------
 template <typename R> struct Mats;
 template <> struct Mats<double> {
@@ -71,122 +78,233 @@ __device__ __forceinline__ void argmax_merge(unsigned long long& key, int& idx, 
   }
 }
 
+// Row map of the w sequential swaps (row k+r <-> piv[k+r]): new[pos] = old[src],
+// rows k..k+w-1 first (in order), then the displaced rows below the block.
+// One warp: lane i holds slot i (position, source row); each swap finds its
+// slot by a ballot.  Written to PERM (80 ints per angle) for k_lu_prep.
+__device__ void write_row_map(const Dev& D, int a, int k, int w, const int* s_piv, int lane) {
+  int mypos = (lane < w) ? k + lane : -1;
+  int mysrc = mypos;
+  int n = w;
+  for (int r = 0; r < w; ++r) {
+    const int p2 = s_piv[r];
+    const unsigned m = __ballot_sync(0xffffffffu, mypos == p2);
+    int f;
+    if (m) {
+      f = __ffs(m) - 1;
+    } else {
+      f = n;
+      if (lane == n) {
+        mypos = p2;
+        mysrc = p2;
+      }
+      ++n;
+    }
+    const int sr = __shfl_sync(0xffffffffu, mysrc, r), sf = __shfl_sync(0xffffffffu, mysrc, f);
+    if (lane == r) mysrc = sf;
+    if (lane == f) mysrc = sr;
+  }
+  int* pm = D.PERM + 80 * a;
+  if (lane == 0) pm[0] = n;
+  if (lane < n) {
+    pm[1 + lane] = mypos;
+    pm[1 + 2 * NB + lane] = mysrc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Panel factorisation of the top rows k..nt-1 of the E columns k..k+w-1 on a
+// thread-block cluster of PCL CTAs per angle.  CTA q holds panel positions
+// [q RC, (q+1) RC), RC = ceil(rows / PCL), in shared memory; lane l of every
+// warp owns local rows l, l + 32, ... .
+//
+// Per column c:
+//  A (warp 0) write back the multipliers of column c-1; the local candidate
+//    is the largest 32-bit key among own positions >= c (smallest position
+//    on ties, by two warp reductions); publish its key, position, pivot
+//    reciprocal and row, and (owner of position c) row c, into buffers
+//    indexed by the parity of c;
+//  cluster barrier;
+//  B (warp 0) gather all PCL candidates and row c through distributed shared
+//    memory in one round of independent loads, agree on the pivot, swap
+//    rows c and the pivot's position;
+//  C every warp forms the multipliers l_r = a_rc / p of its rows in
+//    registers; warp 0 updates column c+1 and precomputes each row's key and
+//    reciprocal there (the next column's candidates), warps 1.. update
+//    columns c+2.. .
+// A CTA reuses a parity buffer two columns later, after the next barrier,
+// which every reader of the previous use has passed: one barrier per column.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+constexpr int PCL = 8;
+constexpr int PCL_THREADS = 128;
+constexpr int PCL_SLOTS = 4;  // rows per lane: RC <= 32 PCL_SLOTS, so n_i <= 1024
+constexpr int PCL_WARPS = PCL_THREADS / 32;
+
 template <typename R>
-__global__ void __launch_bounds__(PANEL_THREADS) k_lu_panel(Dev D, int t, int k) {
-  const int a = blockIdx.x;
+__global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
+    k_lu_panel_cl(Dev D, int t, int k, int a0) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank();
+  const int a = a0 + blockIdx.y;
   const Step S = make_step(D, t);
   const IfaceDesc ft = D.ifc[t];
   const int w = min(NB, S.nt - k);
   const int rows = S.nt - k;
+  const int RC = (rows + PCL - 1) / PCL;
+  const int p0 = q * RC;
+  const int nown = max(0, min(rows, p0 + RC) - p0);
   vec2<R>* top = Mats<R>::rows(D) + a * D.r_stride + ft.row_off;
   const int ld = S.nt;
   extern __shared__ __align__(16) unsigned char pan_raw[];
-  vec2<R>* pan = reinterpret_cast<vec2<R>*>(pan_raw);  // rows x w, column-major
-  __shared__ unsigned long long s_key[PANEL_THREADS / 32];
-  __shared__ int s_idx[PANEL_THREADS / 32];
+  vec2<R>* pan = reinterpret_cast<vec2<R>*>(pan_raw);  // own rows x w, column-major, leading dimension RC
+  vec2<R>* rrow = pan + (size_t)RC * w;                 // per row: 1 / (its entry in the current column)
+  unsigned* krow = reinterpret_cast<unsigned*>(rrow + RC);  // per row: its pivot key there
+  __shared__ unsigned s_key[2];
+  __shared__ int s_idx[2];
+  __shared__ __align__(16) vec2<R> s_crinv[2];
+  __shared__ __align__(16) vec2<R> s_cand[2][NB];
+  __shared__ __align__(16) vec2<R> s_rowc[2][NB];
+  __shared__ __align__(16) vec2<R> s_all[PCL][NB];
+  __shared__ __align__(16) vec2<R> s_arinv[PCL];
+  __shared__ __align__(16) vec2<R> s_rowcl[NB];
+  __shared__ __align__(16) vec2<R> s_prow[NB];
+  __shared__ __align__(16) vec2<R> s_prinv;
   __shared__ int s_piv[NB];
-  __shared__ vec2<R> s_rinv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < rows * w; e += PANEL_THREADS) {
-    const int r = e % rows, c = e / rows;
-    pan[e] = top[(size_t)(S.nlt + k + c) * ld + k + r];
+  for (int e = tid; e < nown * w; e += PCL_THREADS) {
+    const int r = e % nown, c = e / nown;
+    pan[c * RC + r] = top[(size_t)(S.nlt + k + c) * ld + k + p0 + r];
   }
   __syncthreads();
   int* piv = D.LUPIV + a * D.piv_stride + ft.eta_off;
   vec2<R>* udinv = Mats<R>::udinv(D) + a * D.piv_stride + ft.eta_off;
-  for (int c = 0; c < w; ++c) {
-    // (1) candidate pivots: largest |re| + |im| per warp (bit patterns compared as integers)
-    unsigned long long key = 0;
-    int idx = c;
-    for (int r = c + tid; r < rows; r += PANEL_THREADS) {
-      argmax_merge(key, idx, pivot_key(ldv<R>(&pan[(size_t)c * rows + r])), r);
-    }
+  cpx<R> lreg[PCL_SLOTS];  // warp 0: multipliers of the previous column
+  if (warp == 0) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-      argmax_merge(key, idx, k2, i2);
-    }
-    if (lane == 0) {
-      s_key[warp] = key;
-      s_idx[warp] = idx;
-    }
-    __syncthreads();
-    // (2) warp 0: pivot, row swap within the panel, reciprocal of the pivot
-    if (warp == 0) {
-      key = (lane < PANEL_THREADS / 32) ? s_key[lane] : 0ull;
-      idx = (lane < PANEL_THREADS / 32) ? s_idx[lane] : 0x7fffffff;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-        argmax_merge(key, idx, k2, i2);
+    for (int sl = 0; sl < PCL_SLOTS; ++sl) {
+      const int r = lane + 32 * sl;
+      if (r < nown) {
+        const cpx<R> v = ldv<R>(&pan[r]);
+        krow[r] = pivot_key32(v);
+        const cpx<R> iv = inv_fast_t(v);
+        rrow[r].x = iv.re;
+        rrow[r].y = iv.im;
       }
-      const int pr = idx;
-      if (pr != c && lane < w) {
-        const vec2<R> x = pan[(size_t)lane * rows + c];
-        pan[(size_t)lane * rows + c] = pan[(size_t)lane * rows + pr];
-        pan[(size_t)lane * rows + pr] = x;
+    }
+  }
+  for (int c = 0; c < w; ++c) {
+    const int cb = c & 1;
+    const int qc = c / RC;
+    if (warp == 0) {
+      if (c > 0) {
+#pragma unroll
+        for (int sl = 0; sl < PCL_SLOTS; ++sl) {
+          const int r = lane + 32 * sl;
+          if (r < nown && p0 + r > c - 1) stv<R>(&pan[(c - 1) * RC + r], lreg[sl]);
+        }
+      }
+      unsigned kb = 0, pb = 0xffffffffu;
+#pragma unroll
+      for (int sl = 0; sl < PCL_SLOTS; ++sl) {
+        const int r = lane + 32 * sl;
+        if (r < nown && p0 + r >= c) {
+          const unsigned kk = krow[r];
+          if (kk > kb || pb == 0xffffffffu) {
+            kb = kk;
+            pb = (unsigned)(p0 + r);
+          }
+        }
       }
       __syncwarp();
+      const unsigned kmax = __reduce_max_sync(0xffffffffu, kb);
+      const unsigned pmin = __reduce_min_sync(0xffffffffu, (kb == kmax) ? pb : 0xffffffffu);
+      const bool have = pmin != 0xffffffffu;
       if (lane == 0) {
-        if (!pivot_ok(key, R())) atomicExch(D.STATUS, MLQP_ESINGULAR_CODE);
-        piv[k + c] = k + pr;
+        s_key[cb] = kmax;
+        s_idx[cb] = have ? (int)pmin : 0x7fffffff;
+        if (have) s_crinv[cb] = rrow[pmin - p0];
+      }
+      if (have && lane < w) s_cand[cb][lane] = pan[lane * RC + (pmin - p0)];
+      if (q == qc && lane < w) s_rowc[cb][lane] = pan[lane * RC + (c - p0)];
+    }
+    cl.sync();
+    if (warp == 0) {
+#pragma unroll
+      for (int u = 0; u < (PCL * NB) / 32; ++u) {
+        const int e = lane + 32 * u, rk = e / NB, j = e % NB;
+        if (j < w) s_all[rk][j] = *cl.map_shared_rank(&s_cand[cb][j], rk);
+      }
+      unsigned key = 0, pos = 0xffffffffu;
+      if (lane < PCL) {
+        key = *cl.map_shared_rank(&s_key[cb], lane);
+        const int ix = *cl.map_shared_rank(&s_idx[cb], lane);
+        pos = (ix == 0x7fffffff) ? 0xffffffffu : (unsigned)ix;
+        s_arinv[lane] = *cl.map_shared_rank(&s_crinv[cb], lane);
+      }
+      if (lane < w) s_rowcl[lane] = *cl.map_shared_rank(&s_rowc[cb][lane], qc);
+      const unsigned kmax = __reduce_max_sync(0xffffffffu, (pos != 0xffffffffu) ? key : 0u);
+      const unsigned pr_u = __reduce_min_sync(0xffffffffu, (pos != 0xffffffffu && key == kmax) ? pos : 0xffffffffu);
+      __syncwarp();
+      const int pr = (int)pr_u, qp = pr / RC;
+      if (lane < w) {
+        const vec2<R> pv = s_all[qp][lane];
+        s_prow[lane] = pv;
+        if (q == qp && pr != c) pan[lane * RC + (pr - p0)] = s_rowcl[lane];
+        if (q == qc) pan[lane * RC + (c - p0)] = pv;
+      }
+      if (lane == 0) {
         s_piv[c] = k + pr;
-        const cpx<R> ri = inv_fast_t(ldv<R>(&pan[(size_t)c * rows + c]));
-        s_rinv.x = ri.re;
-        s_rinv.y = ri.im;
-        udinv[k + c] = s_rinv;
+        s_prinv = s_arinv[qp];
+        if (q == 0) {
+          if (!pivot_ok32(kmax, R())) atomicExch(D.STATUS, MLQP_ESINGULAR_CODE);
+          piv[k + c] = k + pr;
+          udinv[k + c] = s_arinv[qp];
+        }
       }
     }
     __syncthreads();
-    // (3) multipliers and rank-1 update of the remaining panel columns, row by row
-    const cpx<R> ip = mkc<R>(s_rinv.x, s_rinv.y);
-    for (int r = c + 1 + tid; r < rows; r += PANEL_THREADS) {
-      const cpx<R> l = ldv<R>(&pan[(size_t)c * rows + r]) * ip;
-      stv<R>(&pan[(size_t)c * rows + r], l);
-      for (int cc = c + 1; cc < w; ++cc) {
-        vec2<R>* q = &pan[(size_t)cc * rows + r];
-        stv<R>(q, ldv<R>(q) - l * ldv<R>(&pan[(size_t)cc * rows + c]));
+    const cpx<R> ip = ldv<R>(&s_prinv);
+#pragma unroll
+    for (int sl = 0; sl < PCL_SLOTS; ++sl) {
+      const int r = lane + 32 * sl;
+      if (r < nown && p0 + r > c) {
+        const cpx<R> l = ldv<R>(&pan[c * RC + r]) * ip;
+        if (warp == 0) {
+          lreg[sl] = l;
+          if (c + 1 < w) {
+            vec2<R>* x = &pan[(c + 1) * RC + r];
+            const cpx<R> v = ldv<R>(x) - l * ldv<R>(&s_prow[c + 1]);
+            stv<R>(x, v);
+            krow[r] = pivot_key32(v);
+            const cpx<R> iv = inv_fast_t(v);
+            rrow[r].x = iv.re;
+            rrow[r].y = iv.im;
+          }
+        } else {
+          for (int cc = c + 1 + warp; cc < w; cc += PCL_WARPS - 1) {
+            vec2<R>* x = &pan[cc * RC + r];
+            stv<R>(x, ldv<R>(x) - l * ldv<R>(&s_prow[cc]));
+          }
+        }
       }
     }
     __syncthreads();
   }
-  for (int e = tid; e < rows * w; e += PANEL_THREADS) {
-    const int r = e % rows, c = e / rows;
-    top[(size_t)(S.nlt + k + c) * ld + k + r] = pan[e];
-  }
-  // row map of the w sequential swaps (row k+r <-> piv[k+r]): new[pos] = old[src],
-  // rows k..k+w-1 first (in order), then the displaced rows below the block.
-  if (tid == 0) {
-    int pos[2 * NB], src[2 * NB];
-    int n = 0;
-    for (int r = 0; r < w; ++r) {
-      pos[n] = k + r;
-      src[n] = k + r;
-      ++n;
-    }
-    for (int r = 0; r < w; ++r) {
-      const int p2 = s_piv[r];
-      int f = -1;
-      for (int q = 0; q < n; ++q)
-        if (pos[q] == p2) f = q;
-      if (f < 0) {
-        pos[n] = p2;
-        src[n] = p2;
-        f = n++;
-      }
-      const int tmp = src[r];  // position k + r is entry r
-      src[r] = src[f];
-      src[f] = tmp;
-    }
-    int* pm = D.PERM + 80 * a;
-    pm[0] = n;
-    for (int q = 0; q < n; ++q) {
-      pm[1 + q] = pos[q];
-      pm[1 + 2 * NB + q] = src[q];
+  if (warp == 0) {
+#pragma unroll
+    for (int sl = 0; sl < PCL_SLOTS; ++sl) {
+      const int r = lane + 32 * sl;
+      if (r < nown && p0 + r > w - 1) stv<R>(&pan[(w - 1) * RC + r], lreg[sl]);
     }
   }
+  __syncthreads();
+  cl.sync();  // no CTA exits while another may still read its shared memory
+  for (int e = tid; e < nown * w; e += PCL_THREADS) {
+    const int r = e % nown, c = e / nown;
+    top[(size_t)(S.nlt + k + c) * ld + k + p0 + r] = pan[c * RC + r];
+  }
+  if (q == 0 && warp == 0) write_row_map(D, a, k, w, s_piv, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -201,8 +319,8 @@ constexpr int PREP_THREADS = 128;
 constexpr int PREP_COLS = PREP_THREADS / 16;  // columns (or rows) per CTA
 
 template <typename R>
-__global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, int n_col_ctas) {
-  const int a = blockIdx.y;
+__global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, int n_col_ctas, int a0) {
+  const int a = a0 + blockIdx.y;
   const Step S = make_step(D, t);
   const IfaceDesc ft = D.ifc[t];
   const int w = min(NB, S.nt - k);
@@ -302,14 +420,17 @@ __device__ __forceinline__ V* row_col_ptr(V* top, int ldt, V* ftop, V* bot, int 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k) {
-  const int a = blockIdx.y;
+__global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k, int a0, int mode, int wn) {
+  // mode 0: the whole trailing block.  Look-ahead split: mode 1 updates only
+  // the next panel's columns u < wn of the top rows v < tr (so that panel can
+  // be factored), mode 2 everything else.
+  const int a = a0 + blockIdx.y;
   const Step S = make_step(D, t);
   const IfaceDesc ft = D.ifc[t];
   const int w = min(NB, S.nt - k);
   const int tr = S.nt - k - w;
-  const int nrows = tr + S.nb, ncols = tr + S.nb + 1;
-  const int tiles_c = (ncols + UT - 1) / UT;
+  const int nrows = (mode == 1) ? tr : tr + S.nb, ncols = tr + S.nb + 1;
+  const int tiles_c = (mode == 1) ? 1 : (ncols + UT - 1) / UT;
   const int tile_r = blockIdx.x / tiles_c, tile_c = blockIdx.x % tiles_c;
   const int row0 = tile_r * UT, col0 = tile_c * UT;
   if (row0 >= nrows) return;
@@ -387,7 +508,8 @@ __global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k) 
 #pragma unroll
     for (int z = 0; z < 4; ++z) {
       const int v = row0 + ty * 2 + q, u = col0 + tx * 4 + z;
-      if (v < nrows && u < ncols) {
+      const bool next_block = v < tr && u < wn;
+      if (v < nrows && u < ncols && (mode == 0 || (mode == 1) == next_block)) {
         vec2<R>* p = row_col_ptr(top, ldt, ftop, bot, ldb, fbot, S, k, w, v, u);
         vec2<R> x = *p;
         x.x -= t1[q][z] - t2[q][z];
@@ -409,8 +531,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(256) k_back_matvec(Dev D, int t) {
-  const int a = blockIdx.y;
+__global__ void __launch_bounds__(256) k_back_matvec(Dev D, int t, int a0) {
+  const int a = a0 + blockIdx.y;
   const IfaceDesc ft = D.ifc[t];
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -437,26 +559,36 @@ __global__ void __launch_bounds__(256) k_back_matvec(Dev D, int t) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_back_trsv(Dev D, int t) {
-  const int a = blockIdx.x;
+__global__ void __launch_bounds__(256) k_back_trsv(Dev D, int t, int a0) {
+  const int a = a0 + blockIdx.x;
   const IfaceDesc ft = D.ifc[t];
   const int n = ft.n;
   const double2* U = D.ROW + a * D.r_stride + ft.row_off + (size_t)ft.nl * n;
   const double2* udinv = D.UDINV + a * D.piv_stride + ft.eta_off;
   double2* y = D.ETA + a * D.eta_stride + ft.eta_off;
+  // diagonal block with its columns scaled by the pivot reciprocals, so the
+  // serial recurrence is one complex multiply-add per step:
+  //   v_r -= (U_rj / U_jj) v_j for r < j, then eta_j = v_j / U_jj.
+  __shared__ double2 ub[32][33];
   __shared__ double2 xb[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nblk = (n + 31) / 32;
   for (int b = nblk - 1; b >= 0; --b) {
     const int i0 = 32 * b, w = min(32, n - i0);
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int r = e % w, j = e / w;
+      const cplx u = ld2(&U[(size_t)(i0 + j) * n + i0 + r]) * ld2(&udinv[i0 + j]);
+      ub[j][r] = make_double2(u.re, u.im);
+    }
+    __syncthreads();
     if (warp == 0) {
       cplx v = (lane < w) ? ld2(&y[i0 + lane]) : C(0.0);
-      for (int j = w - 1; j >= 0; --j) {
-        if (lane == j) v = v * ld2(&udinv[i0 + j]);
+      for (int j = w - 1; j > 0; --j) {
         const double xr = __shfl_sync(0xffffffffu, v.re, j), xi = __shfl_sync(0xffffffffu, v.im, j);
-        if (lane < j) v = v - ld2(&U[(size_t)(i0 + j) * n + i0 + lane]) * C(xr, xi);
+        if (lane < j) v = v - ld2(&ub[j][lane]) * C(xr, xi);
       }
       if (lane < w) {
+        v = v * ld2(&udinv[i0 + lane]);
         st2(&y[i0 + lane], v);
         xb[lane] = make_double2(v.re, v.im);
       }
@@ -517,53 +649,103 @@ __global__ void __launch_bounds__(128) k_recover(Dev D) {
 // Host launchers
 // ---------------------------------------------------------------------------
 // The block LU of the forward sweep, in precision R (FP64: plain path on ROW/F;
-// FP32: factorisation of the mixed path on ROW32/F32).
+// FP32: factorisation of the mixed path on ROW32/F32), for angles a0..a0+na-1.
 template <typename R>
-cudaError_t launch_factor(const Dev& D, const int* n_host, cudaStream_t s) {
+cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaStream_t s, cudaStream_t ps,
+                          cudaEvent_t ev_next, cudaEvent_t ev_panel) {
   const int I = D.I;
-  cudaError_t e;
-  for (int t = 0; t < I; ++t) {
+  cudaError_t e = cudaSuccess;
+  for (int t = 0; t < I && e == cudaSuccess; ++t) {
     const int nt = n_host[t];
     const int nb = (t + 1 < I) ? n_host[t + 1] : 0;
     const int nlt = (t > 0) ? n_host[t - 1] : 0;
-    for (int k = 0; k < nt; k += NB) {
+    auto panel = [&](int k, cudaStream_t st) {
       const int w = (nt - k < NB) ? nt - k : NB;
-      const size_t smem = (size_t)(nt - k) * w * sizeof(vec2<R>);
+      const size_t rc = (size_t)((nt - k + PCL - 1) / PCL);
+      const size_t smem = rc * (w + 1) * sizeof(vec2<R>) + rc * sizeof(unsigned);
       ++g_launches;
-      k_lu_panel<R><<<D.n_theta, PANEL_THREADS, smem, s>>>(D, t, k);
+      k_lu_panel_cl<R><<<dim3(PCL, na), PCL_THREADS, smem, st>>>(D, t, k, a0);
+    };
+    panel(0, s);
+    for (int k = 0; k < nt && e == cudaSuccess; k += NB) {
+      const int w = (nt - k < NB) ? nt - k : NB;
       const int ncol = nlt + nt + nb + 1;
       const int n_col_ctas = (ncol + PREP_COLS - 1) / PREP_COLS;
       const int n_row_ctas = (nb + PREP_COLS - 1) / PREP_COLS;
       ++g_launches;
-      k_lu_prep<R><<<dim3(n_col_ctas + n_row_ctas, D.n_theta), PREP_THREADS, 0, s>>>(D, t, k, n_col_ctas);
+      k_lu_prep<R><<<dim3(n_col_ctas + n_row_ctas, na), PREP_THREADS, 0, s>>>(D, t, k, n_col_ctas, a0);
       const int tr = nt - k - w;
       const int nrows = tr + nb, ncols = tr + nb + 1;
-      if (nrows > 0) {
-        const int tiles = ((nrows + UT - 1) / UT) * ((ncols + UT - 1) / UT);
+      const int tiles = ((nrows + UT - 1) / UT) * ((ncols + UT - 1) / UT);
+      const int k2 = k + w;
+      if (LOOKAHEAD && k2 < nt) {
+        // look-ahead: the next panel's columns first, then its factorisation on
+        // the panel stream beside the rest of this update
+        const int wn = (nt - k2 < NB) ? nt - k2 : NB;
         ++g_launches;
-        k_lu_update<R><<<dim3(tiles, D.n_theta), UPD_THREADS, 0, s>>>(D, t, k);
+        k_lu_update<R><<<dim3((tr + UT - 1) / UT, na), UPD_THREADS, 0, s>>>(D, t, k, a0, 1, wn);
+        if ((e = cudaEventRecord(ev_next, s)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(ps, ev_next, 0)) != cudaSuccess) break;
+        panel(k2, ps);
+        if ((e = cudaEventRecord(ev_panel, ps)) != cudaSuccess) break;
+        ++g_launches;
+        k_lu_update<R><<<dim3(tiles, na), UPD_THREADS, 0, s>>>(D, t, k, a0, 2, wn);
+        e = cudaStreamWaitEvent(s, ev_panel, 0);
+      } else {
+        if (nrows > 0) {
+          ++g_launches;
+          k_lu_update<R><<<dim3(tiles, na), UPD_THREADS, 0, s>>>(D, t, k, a0, 0, 0);
+        }
+        if (k2 < nt) panel(k2, s);
       }
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e == cudaSuccess) e = cudaGetLastError();
   }
-  return cudaSuccess;
+  return e;
 }
 
-cudaError_t launch_factor32(const Dev& D, const int* n_host, cudaStream_t s) {
-  return launch_factor<float>(D, n_host, s);
+// Angle groups run on their own streams: the latency-bound panel of one
+// group overlaps the trailing updates of the others.  Fork from and join
+// back into the context's stream.
+static cudaError_t fork(const AngleStreams& A) {
+  cudaError_t e = cudaEventRecord(A.fork, A.main);
+  for (int g = 0; g < A.n && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(A.s[g], A.fork, 0);
+  return e;
+}
+static cudaError_t join(const AngleStreams& A) {
+  cudaError_t e = cudaSuccess;
+  for (int g = 0; g < A.n && e == cudaSuccess; ++g) {
+    e = cudaEventRecord(A.join[g], A.s[g]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(A.main, A.join[g], 0);
+  }
+  return e;
 }
 
-cudaError_t launch_sweep(const Dev& D, const int* n_host, cudaStream_t s) {
+cudaError_t launch_factor32(const Dev& D, const int* n_host, const AngleStreams& A) {
+  cudaError_t e = fork(A);
+  for (int g = 0; g < A.n && e == cudaSuccess; ++g)
+    e = launch_factor<float>(D, n_host, A.a0[g], A.na[g], A.s[g], A.ps[g], A.ev_next[g], A.ev_panel[g]);
+  const cudaError_t j = join(A);
+  return e != cudaSuccess ? e : j;
+}
+
+cudaError_t launch_sweep(const Dev& D, const int* n_host, const AngleStreams& A) {
   const int I = D.I;
-  cudaError_t e = launch_factor<double>(D, n_host, s);
-  if (e != cudaSuccess) return e;
-  for (int t = I - 1; t >= 0; --t) {
-    ++g_launches;
-    k_back_matvec<<<dim3((n_host[t] + 7) / 8, D.n_theta), 256, 0, s>>>(D, t);
-    ++g_launches;
-    k_back_trsv<<<D.n_theta, 256, 0, s>>>(D, t);
+  cudaError_t e = fork(A);
+  for (int g = 0; g < A.n && e == cudaSuccess; ++g) {
+    const int a0 = A.a0[g], na = A.na[g];
+    cudaStream_t s = A.s[g];
+    e = launch_factor<double>(D, n_host, a0, na, s, A.ps[g], A.ev_next[g], A.ev_panel[g]);
+    for (int t = I - 1; t >= 0 && e == cudaSuccess; --t) {
+      ++g_launches;
+      k_back_matvec<<<dim3((n_host[t] + 7) / 8, na), 256, 0, s>>>(D, t, a0);
+      ++g_launches;
+      k_back_trsv<<<na, 256, 0, s>>>(D, t, a0);
+      e = cudaGetLastError();
+    }
   }
-  return cudaGetLastError();
+  const cudaError_t j = join(A);
+  return e != cudaSuccess ? e : j;
 }
 
 cudaError_t launch_recover(const Dev& D, cudaStream_t s) {
@@ -572,13 +754,16 @@ cudaError_t launch_recover(const Dev& D, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-size_t sweep_panel_smem_max(int maxn) { return (size_t)maxn * NB * sizeof(double2); }
+size_t sweep_panel_smem_max(int maxn) {
+  const size_t rc = (size_t)((maxn + PCL - 1) / PCL);
+  return rc * (NB + 1) * sizeof(double2) + rc * sizeof(unsigned);
+}
 
 cudaError_t sweep_configure(int maxn) {
   const size_t smem = sweep_panel_smem_max(maxn);
-  cudaError_t e = cudaFuncSetAttribute(k_lu_panel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_lu_panel_cl<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_lu_panel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_lu_panel_cl<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return e;
 }
 

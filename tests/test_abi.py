@@ -71,6 +71,7 @@ def test_setup_accepts_valid_problems(M):
 
 @pytest.mark.parametrize("mutate, field", [
     (lambda p: setattr(p.ifaces[0], "N", 101), "odd N"),
+    (lambda p: setattr(p.ifaces[0], "N", 514), "N above 512"),
     (lambda p: setattr(p, "theta", np.array([0.3])), "theta"),
     (lambda p: setattr(p, "k", np.array([5.0 + 0.1j, 10.0])), "complex k1"),
     (lambda p: setattr(p, "k", np.array([5.0, -10.0])), "negative k"),

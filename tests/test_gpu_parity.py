@@ -337,7 +337,7 @@ def test_mixed_precision_reports_unreached_tolerance(M):
     """A tolerance below the attainable backward error (about 1e-17) ends in
     MLQP_ENOTCONV after exactly max_refine corrections; a fresh context with
     the default tolerance then reproduces the FP64 amplitudes."""
-    prob = small_stack(I=2, N=48, P=40, Mw=30, K=12, M=30)
+    prob = PROBLEMS["small3"]()
     ctx = M.Context(prob, precision=M.MLQP_MIXED, max_refine=2, refine_tol=1e-30)
     with pytest.raises(M.MlqpError) as e:
         ctx.solve_host()
@@ -347,7 +347,9 @@ def test_mixed_precision_reports_unreached_tolerance(M):
     ctx.close()
     ok = M.Context(prob, precision=M.MLQP_MIXED)
     out = ok.solve_host()
-    ref = M.Context(prob).solve_host()
+    plain = M.Context(prob)
+    ref = plain.solve_host()
+    plain.close()
     for a in range(prob.n_theta):
         assert rel(np.concatenate([out["aU"][a], out["aD"][a]]), np.concatenate([ref["aU"][a], ref["aD"][a]])) < 1e-12
     ok.close()
