@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(128) k_fill_A(Dev D) {
     double2* base = D.ROW + a * D.r_stride + ft.row_off;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
-      const cplx s = ali * v[0][kk] + v[1][kk] + al * v[2][kk];
+      const cplx s = cfma(al, v[2][kk], cfma(ali, v[0][kk], v[1][kk]));
       const int row = m + ((kk >= 2) ? Nt : 0);
       const int col = coff + j + ((kk == 1 || kk == 3) ? Ns : 0);
       st2(base + (size_t)col * ld + row, s);

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(WY_THREADS) k_lsq_T(Dev D) {
     // T(0:i, i) = -beta_i T(0:i, 0:i) G(0:i, i)
     if (tid < i) {
       cplx s = C(0.0);
-      for (int q2 = tid; q2 < i; ++q2) s = s + ld2(&T[q2 * WYB + tid]) * ld2(&G[i * WYB + q2]);
+      for (int q2 = tid; q2 < i; ++q2) s = cfma(ld2(&T[q2 * WYB + tid]), ld2(&G[i * WYB + q2]), s);
       st2(&T[i * WYB + tid], (-beta[j0 + i]) * s);
     }
     __syncthreads();
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(WY_THREADS) k_lsq_wy(Dev D, int b) {
   {
     const int i = tid / WYB, c = tid % WYB;  // W2(i, c) = sum_{q <= i} conj(T(q, i)) W(q, c)
     cplx s = C(0.0);
-    for (int q = 0; q <= i; ++q) s = s + conj(ld2(&T[i * WYB + q])) * ld2(&W[c * WYB + q]);
+    for (int q = 0; q <= i; ++q) s = cfma(conj(ld2(&T[i * WYB + q])), ld2(&W[c * WYB + q]), s);
     W2[c * WYB + i] = make_double2(s.re, s.im);
   }
   __syncthreads();
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(WY_THREADS) k_lsq_wy(Dev D, int b) {
     const int r = e % nr, c = e / nr;
     cplx s = ld2(&Bt[c * nr + r]);
 #pragma unroll
-    for (int i = 0; i < WYB; ++i) s = s - ld2(&V[i * nr + r]) * ld2(&W2[c * WYB + i]);
+    for (int i = 0; i < WYB; ++i) s = cfms(ld2(&V[i * nr + r]), ld2(&W2[c * WYB + i]), s);
     st2(&Bg[(size_t)c * ld + j0 + r], s);
   }
 }
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(WY_THREADS) k_lsq_trsm(Dev D) {
       for (int ii = w - 1; ii >= 0; --ii) {
         const int row = i0 + ii;
         cplx s = ld2(&ys[ii * WYB + c]);
-        for (int l = ii + 1; l < w; ++l) s = s - ld2(&A[(size_t)(i0 + l) * ld + row]) * ld2(&Xs[(i0 + l) * WYB + c]);
+        for (int l = ii + 1; l < w; ++l) s = cfms(ld2(&A[(size_t)(i0 + l) * ld + row]), ld2(&Xs[(i0 + l) * WYB + c]), s);
         st2(&Xs[row * WYB + c], s * ld2(&rinv[row]));
       }
     }

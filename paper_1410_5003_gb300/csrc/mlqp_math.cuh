@@ -32,6 +32,14 @@ __device__ __forceinline__ cplx operator*(cplx a, cplx b) {
 __device__ __forceinline__ cplx operator*(double s, cplx a) { return C(s * a.re, s * a.im); }
 __device__ __forceinline__ cplx operator*(cplx a, double s) { return C(s * a.re, s * a.im); }
 __device__ __forceinline__ cplx conj(cplx a) { return C(a.re, -a.im); }
+// s + a b and s - a b in four FMAs: the product is never rounded on its own,
+// and an accumulation costs four FP64 instructions instead of six.
+__device__ __forceinline__ cplx cfma(cplx a, cplx b, cplx s) {
+  return C(fma(a.re, b.re, fma(-a.im, b.im, s.re)), fma(a.re, b.im, fma(a.im, b.re, s.im)));
+}
+__device__ __forceinline__ cplx cfms(cplx a, cplx b, cplx s) {
+  return C(fma(-a.re, b.re, fma(a.im, b.im, s.re)), fma(-a.re, b.im, fma(-a.im, b.re, s.im)));
+}
 __device__ __forceinline__ cplx mul_i(cplx a) { return C(-a.im, a.re); }  // i*a
 __device__ __forceinline__ double abs2(cplx a) { return fma(a.re, a.re, a.im * a.im); }
 __device__ __forceinline__ double cabs(cplx a) { return hypot(a.re, a.im); }
@@ -96,6 +104,12 @@ template <typename R> __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<
 template <typename R> __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return mkc(a.re - b.re, a.im - b.im); }
 template <typename R> __device__ __forceinline__ cpx<R> operator*(cpx<R> a, cpx<R> b) {
   return mkc<R>(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+}
+template <typename R> __device__ __forceinline__ cpx<R> cfma(cpx<R> a, cpx<R> b, cpx<R> s) {  // s + a b
+  return mkc<R>(fma(a.re, b.re, fma(-a.im, b.im, s.re)), fma(a.re, b.im, fma(a.im, b.re, s.im)));
+}
+template <typename R> __device__ __forceinline__ cpx<R> cfms(cpx<R> a, cpx<R> b, cpx<R> s) {  // s - a b
+  return mkc<R>(fma(-a.re, b.re, fma(a.im, b.im, s.re)), fma(-a.re, b.im, fma(-a.im, b.re, s.im)));
 }
 template <typename R> __device__ __forceinline__ cpx<R> ldv(const vec2<R>* p) {
   const vec2<R> v = *p;

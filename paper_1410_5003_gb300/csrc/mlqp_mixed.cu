@@ -11,6 +11,7 @@
 
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
+#include "mlqp_trsv.cuh"
 
 namespace mlqp {
 
@@ -229,126 +230,93 @@ __global__ void k_refine_ctl(Dev D, int last, double tol) {
 }
 
 // ---------------------------------------------------------------------------
-// FP32 solves with the stored factors.  Forward, interface t:
-//   w = P_t r_t - (stored left block of R32_t) y_{t-1},  y_t = L_t^{-1} w;
-// the left block holds the multipliers with the rows already permuted by
-// P_t.  Backward: v = y_t - U12_t d_{t+1},  d_t = U_t^{-1} v.  One CTA per
-// angle; triangular solves by 32-row blocks (one warp solves the diagonal
-// block, all threads update the rows beyond it).
+// FP32 solves with the stored factors, per interface t.
+// Forward:  w = P_t r_t - (stored left block of R32_t) y_{t-1}  (k_mv32, mode 0;
+//           the left block holds the multipliers with the rows already
+//           permuted by P_t),  y_t = L_t^{-1} w  (k_lower32).
+// Backward: v = y_t - U12_t d_{t+1}  (k_mv32, mode 1),  d_t = U_t^{-1} v
+//           (k_upper32).
+// k_mv32: 32 rows per CTA, warp w sums columns w, w+8, ... (coalesced over the
+// rows), partial sums reduced through shared memory.  The triangular solves
+// are those of mlqp_trsv.cuh.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_fwd32(Dev D, int t, const int* permv) {
-  const int a = blockIdx.x;
+__global__ void __launch_bounds__(256) k_mv32(Dev D, int t, int mode, const int* permv) {
+  const int a = blockIdx.y;
   if (angle_done(D, a)) return;
   const IfaceDesc f = D.ifc[t];
   const int n = f.n, ld = f.n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + lane;
   const float2* Rt = D.ROW32 + a * D.r_stride + f.row_off;
-  const float2* Lt = Rt + (size_t)f.nl * n;  // diagonal block (unit lower part)
-  const int* pv = permv + a * D.piv_stride + f.eta_off;
-  const double2* res = D.RES + a * D.eta_stride + f.eta_off;
   float2* y = D.Y32 + a * D.eta_stride + f.eta_off;
-  const float2* yprev = (t > 0) ? D.Y32 + a * D.eta_stride + D.ifc[t - 1].eta_off : nullptr;
-  extern __shared__ float2 wv[];  // n
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int r = tid; r < n; r += blockDim.x) {
-    const double2 x = res[pv[r]];
-    float sr = (float)x.x, si = (float)x.y;
-    if (t > 0) {
-      for (int c = 0; c < f.nl; ++c) {
-        const float2 l = Rt[(size_t)c * ld + r], yc = yprev[c];
-        sr = fmaf(-l.x, yc.x, fmaf(l.y, yc.y, sr));
-        si = fmaf(-l.x, yc.y, fmaf(-l.y, yc.x, si));
+  const float2* A = nullptr;
+  const float2* x = nullptr;
+  int nc = 0;
+  if (mode == 0 && t > 0) {
+    A = Rt;  // left block, n x nl
+    x = D.Y32 + a * D.eta_stride + D.ifc[t - 1].eta_off;
+    nc = f.nl;
+  } else if (mode == 1 && t + 1 < D.I) {
+    A = Rt + (size_t)(f.nl + f.n) * n;  // U12, n x nr
+    x = D.Y32 + a * D.eta_stride + D.ifc[t + 1].eta_off;
+    nc = f.nr;
+  }
+  float sr = 0.f, si = 0.f;
+  if (r < n) {
+    for (int c0 = warp; c0 < nc; c0 += 8 * 8) {
+      float2 u[8], xv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = c0 + 8 * q;
+        u[q] = (c < nc) ? A[(size_t)c * ld + r] : make_float2(0.f, 0.f);
+        xv[q] = (c < nc) ? x[c] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        sr = fmaf(u[q].x, xv[q].x, fmaf(-u[q].y, xv[q].y, sr));
+        si = fmaf(u[q].x, xv[q].y, fmaf(u[q].y, xv[q].x, si));
       }
     }
-    wv[r] = make_float2(sr, si);
   }
+  __shared__ float2 part[8][32];
+  part[warp][lane] = make_float2(sr, si);
   __syncthreads();
-  const int nblk = (n + 31) / 32;
-  for (int b = 0; b < nblk; ++b) {
-    const int i0 = 32 * b, w = min(32, n - i0);
-    if (warp == 0) {
-      float2 v = (lane < w) ? wv[i0 + lane] : make_float2(0.f, 0.f);
-      for (int j = 0; j < w; ++j) {
-        const float xr = __shfl_sync(0xffffffffu, v.x, j), xi = __shfl_sync(0xffffffffu, v.y, j);
-        if (lane > j && lane < w) {
-          const float2 l = Lt[(size_t)(i0 + j) * ld + i0 + lane];
-          v.x = fmaf(-l.x, xr, fmaf(l.y, xi, v.x));
-          v.y = fmaf(-l.x, xi, fmaf(-l.y, xr, v.y));
-        }
-      }
-      if (lane < w) wv[i0 + lane] = v;
+  if (warp == 0 && r < n) {
+    float tr = 0.f, ti = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      tr += part[q][lane].x;
+      ti += part[q][lane].y;
     }
-    __syncthreads();
-    for (int r = i0 + w + tid; r < n; r += blockDim.x) {
-      float2 s = wv[r];
-      for (int j = 0; j < w; ++j) {
-        const float2 l = Lt[(size_t)(i0 + j) * ld + r], x = wv[i0 + j];
-        s.x = fmaf(-l.x, x.x, fmaf(l.y, x.y, s.x));
-        s.y = fmaf(-l.x, x.y, fmaf(-l.y, x.x, s.y));
-      }
-      wv[r] = s;
+    float2 b;
+    if (mode == 0) {
+      const int* pv = permv + a * D.piv_stride + f.eta_off;
+      const double2 rv = D.RES[a * D.eta_stride + f.eta_off + pv[r]];
+      b = make_float2((float)rv.x, (float)rv.y);
+    } else {
+      b = y[r];
     }
-    __syncthreads();
+    y[r] = make_float2(b.x - tr, b.y - ti);
   }
-  for (int r = tid; r < n; r += blockDim.x) y[r] = wv[r];
 }
 
-__global__ void __launch_bounds__(256) k_bwd32(Dev D, int t) {
+__global__ void __launch_bounds__(TRSV_THREADS) k_lower32(Dev D, int t) {
   const int a = blockIdx.x;
   if (angle_done(D, a)) return;
   const IfaceDesc f = D.ifc[t];
-  const int n = f.n, ld = f.n;
-  const float2* Rt = D.ROW32 + a * D.r_stride + f.row_off;
-  const float2* U = Rt + (size_t)f.nl * n;
-  const float2* U12 = Rt + (size_t)(f.nl + f.n) * n;
-  const float2* uinv = D.UDINV32 + a * D.piv_stride + f.eta_off;
-  float2* y = D.Y32 + a * D.eta_stride + f.eta_off;
-  const float2* dnext = (t + 1 < D.I) ? D.Y32 + a * D.eta_stride + D.ifc[t + 1].eta_off : nullptr;
-  extern __shared__ float2 vv[];  // n
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int r = tid; r < n; r += blockDim.x) {
-    float2 s = y[r];
-    if (dnext) {
-      for (int c = 0; c < f.nr; ++c) {
-        const float2 u = U12[(size_t)c * ld + r], d = dnext[c];
-        s.x = fmaf(-u.x, d.x, fmaf(u.y, d.y, s.x));
-        s.y = fmaf(-u.x, d.y, fmaf(-u.y, d.x, s.y));
-      }
-    }
-    vv[r] = s;
-  }
-  __syncthreads();
-  const int nblk = (n + 31) / 32;
-  for (int b = nblk - 1; b >= 0; --b) {
-    const int i0 = 32 * b, w = min(32, n - i0);
-    if (warp == 0) {
-      float2 v = (lane < w) ? vv[i0 + lane] : make_float2(0.f, 0.f);
-      for (int j = w - 1; j >= 0; --j) {
-        if (lane == j) {
-          const float2 q = uinv[i0 + j];
-          v = make_float2(v.x * q.x - v.y * q.y, v.x * q.y + v.y * q.x);
-        }
-        const float xr = __shfl_sync(0xffffffffu, v.x, j), xi = __shfl_sync(0xffffffffu, v.y, j);
-        if (lane < j) {
-          const float2 u = U[(size_t)(i0 + j) * ld + i0 + lane];
-          v.x = fmaf(-u.x, xr, fmaf(u.y, xi, v.x));
-          v.y = fmaf(-u.x, xi, fmaf(-u.y, xr, v.y));
-        }
-      }
-      if (lane < w) vv[i0 + lane] = v;
-    }
-    __syncthreads();
-    for (int r = tid; r < i0; r += blockDim.x) {
-      float2 s = vv[r];
-      for (int j = 0; j < w; ++j) {
-        const float2 u = U[(size_t)(i0 + j) * ld + r], x = vv[i0 + j];
-        s.x = fmaf(-u.x, x.x, fmaf(u.y, x.y, s.x));
-        s.y = fmaf(-u.x, x.y, fmaf(-u.y, x.x, s.y));
-      }
-      vv[r] = s;
-    }
-    __syncthreads();
-  }
-  for (int r = tid; r < n; r += blockDim.x) y[r] = vv[r];
+  extern __shared__ __align__(16) unsigned char trsv_raw[];
+  unit_lower_solve<float>(D.ROW32 + a * D.r_stride + f.row_off + (size_t)f.nl * f.n, f.n,
+                          D.Y32 + a * D.eta_stride + f.eta_off, reinterpret_cast<float2*>(trsv_raw));
+}
+
+__global__ void __launch_bounds__(TRSV_THREADS) k_upper32(Dev D, int t) {
+  const int a = blockIdx.x;
+  if (angle_done(D, a)) return;
+  const IfaceDesc f = D.ifc[t];
+  extern __shared__ __align__(16) unsigned char trsv_raw[];
+  upper_solve<float>(D.ROW32 + a * D.r_stride + f.row_off + (size_t)f.nl * f.n, f.n,
+                     D.UDINV32 + a * D.piv_stride + f.eta_off, D.Y32 + a * D.eta_stride + f.eta_off,
+                     reinterpret_cast<float2*>(trsv_raw));
 }
 
 // eta (FP64) += d (FP32 correction), one CTA per angle.
@@ -390,7 +358,6 @@ cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n
   e = cudaMemsetAsync(D.ETA, 0, sizeof(double2) * D.eta_stride * D.n_theta, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(D.RNRM, 0, sizeof(double) * RNRM_W * D.n_theta, s);
   if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)maxn * sizeof(float2);
   for (int it = 0; it <= max_refine; ++it) {
     const int last = (it == max_refine);
     ++g_launches;
@@ -401,12 +368,17 @@ cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n
     k_refine_ctl<<<1, 32, 0, s>>>(D, last, tol);
     if (last) break;
     for (int t = 0; t < D.I; ++t) {
-      ++g_launches;
-      k_fwd32<<<D.n_theta, 256, smem, s>>>(D, t, permv);
+      g_launches += 2;
+      k_mv32<<<dim3((n_host[t] + 31) / 32, D.n_theta), 256, 0, s>>>(D, t, 0, permv);
+      k_lower32<<<D.n_theta, TRSV_THREADS, sizeof(float2) * n_host[t], s>>>(D, t);
     }
     for (int t = D.I - 1; t >= 0; --t) {
+      if (t + 1 < D.I) {
+        ++g_launches;
+        k_mv32<<<dim3((n_host[t] + 31) / 32, D.n_theta), 256, 0, s>>>(D, t, 1, permv);
+      }
       ++g_launches;
-      k_bwd32<<<D.n_theta, 256, smem, s>>>(D, t);
+      k_upper32<<<D.n_theta, TRSV_THREADS, sizeof(float2) * n_host[t], s>>>(D, t);
     }
     ++g_launches;
     k_eta_update<<<D.n_theta, 256, 0, s>>>(D, (int)n_den);
@@ -415,11 +387,6 @@ cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n
   return cudaGetLastError();
 }
 
-cudaError_t mixed_configure(int maxn) {
-  const int smem = (int)((size_t)maxn * sizeof(float2));
-  cudaError_t e = cudaFuncSetAttribute(k_fwd32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bwd32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  return e;
-}
+cudaError_t mixed_configure(int) { return cudaSuccess; }
 
 }  // namespace mlqp

@@ -26,6 +26,7 @@
 
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
+#include "mlqp_trsv.cuh"
 
 namespace mlqp {
 
@@ -170,15 +171,16 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
   __shared__ __align__(16) vec2<R> s_rowcl[NB];
   __shared__ __align__(16) vec2<R> s_prow[NB];
   __shared__ __align__(16) vec2<R> s_prinv;
+  __shared__ __align__(16) vec2<R> s_pinv[NB];
   __shared__ int s_piv[NB];
+  __shared__ int s_sing;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_sing = 0;
   for (int e = tid; e < nown * w; e += PCL_THREADS) {
     const int r = e % nown, c = e / nown;
     pan[c * RC + r] = top[(size_t)(S.nlt + k + c) * ld + k + p0 + r];
   }
   __syncthreads();
-  int* piv = D.LUPIV + a * D.piv_stride + ft.eta_off;
-  vec2<R>* udinv = Mats<R>::udinv(D) + a * D.piv_stride + ft.eta_off;
   cpx<R> lreg[PCL_SLOTS];  // warp 0: multipliers of the previous column
   if (warp == 0) {
 #pragma unroll
@@ -254,13 +256,12 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
         if (q == qc) pan[lane * RC + (c - p0)] = pv;
       }
       if (lane == 0) {
+        // pivots stay in shared memory until the end: a global store here
+        // would have to complete before the next barrier's release
         s_piv[c] = k + pr;
         s_prinv = s_arinv[qp];
-        if (q == 0) {
-          if (!pivot_ok32(kmax, R())) atomicExch(D.STATUS, MLQP_ESINGULAR_CODE);
-          piv[k + c] = k + pr;
-          udinv[k + c] = s_arinv[qp];
-        }
+        s_pinv[c] = s_arinv[qp];
+        if (!pivot_ok32(kmax, R())) s_sing = 1;
       }
     }
     __syncthreads();
@@ -274,7 +275,7 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
           lreg[sl] = l;
           if (c + 1 < w) {
             vec2<R>* x = &pan[(c + 1) * RC + r];
-            const cpx<R> v = ldv<R>(x) - l * ldv<R>(&s_prow[c + 1]);
+            const cpx<R> v = cfms(l, ldv<R>(&s_prow[c + 1]), ldv<R>(x));
             stv<R>(x, v);
             krow[r] = pivot_key32(v);
             const cpx<R> iv = inv_fast_t(v);
@@ -284,7 +285,7 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
         } else {
           for (int cc = c + 1 + warp; cc < w; cc += PCL_WARPS - 1) {
             vec2<R>* x = &pan[cc * RC + r];
-            stv<R>(x, ldv<R>(x) - l * ldv<R>(&s_prow[cc]));
+            stv<R>(x, cfms(l, ldv<R>(&s_prow[cc]), ldv<R>(x)));
           }
         }
       }
@@ -304,7 +305,16 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
     const int r = e % nown, c = e / nown;
     top[(size_t)(S.nlt + k + c) * ld + k + p0 + r] = pan[c * RC + r];
   }
-  if (q == 0 && warp == 0) write_row_map(D, a, k, w, s_piv, lane);
+  if (q == 0 && warp == 0) {
+    int* piv = D.LUPIV + a * D.piv_stride + ft.eta_off;
+    vec2<R>* udinv = Mats<R>::udinv(D) + a * D.piv_stride + ft.eta_off;
+    if (lane < w) {
+      piv[k + lane] = s_piv[lane];
+      udinv[k + lane] = s_pinv[lane];
+    }
+    if (lane == 0 && s_sing) atomicExch(D.STATUS, MLQP_ESINGULAR_CODE);
+    write_row_map(D, a, k, w, s_piv, lane);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -366,7 +376,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, i
     if (live && u >= pc1) {
       for (int q = 0; q + 1 < w; ++q) {
         const R xr = __shfl_sync(hmask, x.re, q, 16), xi = __shfl_sync(hmask, x.im, q, 16);
-        if (lane16 > q && lane16 < w) x = x - ldv<R>(&blk[q * w + lane16]) * mkc<R>(xr, xi);
+        if (lane16 > q && lane16 < w) x = cfms(ldv<R>(&blk[q * w + lane16]), mkc<R>(xr, xi), x);
       }
     } else {
       for (int q = 0; q + 1 < w; ++q) {  // keep the shuffles converged across the half-warp
@@ -389,7 +399,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, i
       // lane q finalises x_q = (a_q - sum_{q' < q} x_q' U_q'q) / U_qq, then all lanes c > q use it
       if (lane16 == q) x = x * ldv<R>(&sinv[q]);
       const R xr = __shfl_sync(hmask, x.re, q, 16), xi = __shfl_sync(hmask, x.im, q, 16);
-      if (lane16 > q && lane16 < w) x = x - mkc<R>(xr, xi) * ldv<R>(&blk[lane16 * w + q]);
+      if (lane16 > q && lane16 < w) x = cfms(mkc<R>(xr, xi), ldv<R>(&blk[lane16 * w + q]), x);
     }
     if (live && lane16 < w) stv<R>(&bot[(size_t)(k + lane16) * ldb + r], x);
   }
@@ -559,53 +569,13 @@ __global__ void __launch_bounds__(256) k_back_matvec(Dev D, int t, int a0) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_back_trsv(Dev D, int t, int a0) {
+__global__ void __launch_bounds__(TRSV_THREADS) k_back_trsv(Dev D, int t, int a0) {
   const int a = a0 + blockIdx.x;
   const IfaceDesc ft = D.ifc[t];
-  const int n = ft.n;
-  const double2* U = D.ROW + a * D.r_stride + ft.row_off + (size_t)ft.nl * n;
-  const double2* udinv = D.UDINV + a * D.piv_stride + ft.eta_off;
-  double2* y = D.ETA + a * D.eta_stride + ft.eta_off;
-  // diagonal block with its columns scaled by the pivot reciprocals, so the
-  // serial recurrence is one complex multiply-add per step:
-  //   v_r -= (U_rj / U_jj) v_j for r < j, then eta_j = v_j / U_jj.
-  __shared__ double2 ub[32][33];
-  __shared__ double2 xb[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nblk = (n + 31) / 32;
-  for (int b = nblk - 1; b >= 0; --b) {
-    const int i0 = 32 * b, w = min(32, n - i0);
-    for (int e = tid; e < w * w; e += blockDim.x) {
-      const int r = e % w, j = e / w;
-      const cplx u = ld2(&U[(size_t)(i0 + j) * n + i0 + r]) * ld2(&udinv[i0 + j]);
-      ub[j][r] = make_double2(u.re, u.im);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      cplx v = (lane < w) ? ld2(&y[i0 + lane]) : C(0.0);
-      for (int j = w - 1; j > 0; --j) {
-        const double xr = __shfl_sync(0xffffffffu, v.re, j), xi = __shfl_sync(0xffffffffu, v.im, j);
-        if (lane < j) v = v - ld2(&ub[j][lane]) * C(xr, xi);
-      }
-      if (lane < w) {
-        v = v * ld2(&udinv[i0 + lane]);
-        st2(&y[i0 + lane], v);
-        xb[lane] = make_double2(v.re, v.im);
-      }
-    }
-    __syncthreads();
-    for (int r = tid; r < i0; r += blockDim.x) {
-      double sr = 0.0, si = 0.0;
-      for (int j = 0; j < w; ++j) {
-        const double2 u = U[(size_t)(i0 + j) * n + r], x = xb[j];
-        sr = fma(u.x, x.x, fma(-u.y, x.y, sr));
-        si = fma(u.x, x.y, fma(u.y, x.x, si));
-      }
-      const double2 yv = y[r];
-      y[r] = make_double2(yv.x - sr, yv.y - si);
-    }
-    __syncthreads();
-  }
+  extern __shared__ __align__(16) unsigned char trsv_raw[];
+  upper_solve<double>(D.ROW + a * D.r_stride + ft.row_off + (size_t)ft.nl * ft.n, ft.n,
+                      D.UDINV + a * D.piv_stride + ft.eta_off, D.ETA + a * D.eta_stride + ft.eta_off,
+                      reinterpret_cast<double2*>(trsv_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -626,7 +596,7 @@ __global__ void __launch_bounds__(128) k_recover(Dev D) {
     const double2* X = D.Xb + a * D.x_stride + L.x_off;
     const double2* eta = D.ETA + a * D.eta_stride + f.eta_off;
     cplx s = C(0.0);
-    for (int c = 0; c < f.n; ++c) s = s + ld2(&X[(size_t)c * L.p + D.P + n]) * ld2(&eta[c]);
+    for (int c = 0; c < f.n; ++c) s = cfma(ld2(&X[(size_t)c * L.p + D.P + n]), ld2(&eta[c]), s);
     s = -s;
     st2(&D.AMP[(size_t)a * 2 * D.nK + e], s);
     const cplx kv = ld2(which ? &D.KD[a * D.nK + n] : &D.KU[a * D.nK + n]);
@@ -740,7 +710,7 @@ cudaError_t launch_sweep(const Dev& D, const int* n_host, const AngleStreams& A)
       ++g_launches;
       k_back_matvec<<<dim3((n_host[t] + 7) / 8, na), 256, 0, s>>>(D, t, a0);
       ++g_launches;
-      k_back_trsv<<<na, 256, 0, s>>>(D, t, a0);
+      k_back_trsv<<<na, TRSV_THREADS, sizeof(double2) * n_host[t], s>>>(D, t, a0);
       e = cudaGetLastError();
     }
   }
