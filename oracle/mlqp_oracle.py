@@ -41,6 +41,12 @@ Readings of the paper that this oracle fixes (each is listed in the design doc):
     rectangular backslash) gives the same amplitudes to discretisation
     accuracy but jumps with rounding-level changes of Q (pivot and rank
     flips); the regularised solution is smooth in the data.
+  * Corner (polyline) interfaces: graded Gauss-Legendre panels, `levels`
+    panels per corner side halving toward the corner; the log-singular part
+    of the self kernels is integrated by product integration on the target's
+    own panel (Legendre log moments, exact) and on panels within one panel
+    length (composite Gauss-Legendre graded toward the nearest point); the
+    rest by the panel Gauss-Legendre rule.
   * U/D nodes x_m = -d/2 + d (m - 1/2)/M; y_U = y0_1 + sum_m |c_m| + gap_U
     (an upper bound of Gamma_1), y_D likewise below Gamma_I; the wall of
     layer j spans x = -d/2 between its bounding interfaces (or U, D); proxy
@@ -97,13 +103,33 @@ class Nodes:
     s: np.ndarray       # parameter values
 
 
+def is_polyline(iface):
+    return hasattr(iface, "vx")
+
+
+def polyline_breaks(iface, d):
+    """Breakpoints of a polyline interface: (-d/2, y0), the corners, (d/2, y0)."""
+    xs = np.concatenate([[-d / 2], iface.vx, [d / 2]])
+    ys = np.concatenate([[iface.y0], iface.vy, [iface.y0]])
+    return xs, ys
+
+
 def interface_height(iface, d, x):
+    if is_polyline(iface):
+        xs, ys = polyline_breaks(iface, d)
+        return np.interp(np.atleast_1d(x), xs, ys)
     m = np.arange(1, len(iface.a) + 1)
     ph = TWO_PI * np.outer(np.atleast_1d(x), m) / d
     return iface.y0 + np.cos(ph) @ iface.a + np.sin(ph) @ iface.b
 
 
 def interface_nodes(iface, d):
+    if is_polyline(iface):
+        return polyline_panels(iface, d).nodes
+    return fourier_nodes(iface, d)
+
+
+def fourier_nodes(iface, d):
     """Periodic trapezoid rule s_j = 2 pi (j - 1/2)/N on the graph
     parametrisation Z(s) = (-d/2 + s d/(2 pi), y(x(s))); unit normals point
     down, into the layer below (Sec. 2.1)."""
@@ -120,13 +146,154 @@ def interface_nodes(iface, d):
     return Nodes(x, y, fp / h, -1.0 / h, speed, (TWO_PI / N) * speed, s)
 
 
+@dataclass
+class Panels:
+    """Gauss-Legendre panels of a polyline interface, in curve order.
+    Panel q runs from (xa[q], ya[q]) to (xb[q], yb[q]) (length h[q]); node j
+    lies on panel pan[j] at local coordinate loc[j] in [-1, 1]."""
+    xa: np.ndarray
+    ya: np.ndarray
+    xb: np.ndarray
+    yb: np.ndarray
+    h: np.ndarray
+    pan: np.ndarray
+    loc: np.ndarray
+    gl_x: np.ndarray    # reference nodes and weights on [-1, 1]
+    gl_w: np.ndarray
+    nodes: Nodes
+
+
+def polyline_panels(iface, d):
+    """Panels of a polyline interface.  A segment with corners at both ends is
+    split at its midpoint; every corner side (corner c to far point f) carries
+    `levels` panels with breakpoints c + (f - c) * {0, 2^-(L-1), ..., 1/2, 1},
+    i.e. panel sizes halving toward the corner.  `order` Gauss-Legendre nodes
+    per panel; arc-length parametrisation (speed 1), downward unit normals
+    (dy, -dx)/h for a panel running in the +x direction."""
+    xs, ys = polyline_breaks(iface, d)
+    L, order = iface.levels, iface.order
+    fr = np.concatenate([[0.0], 2.0 ** -np.arange(L - 1, -1, -1)])
+    pts = []
+    nseg = len(xs) - 1
+    for g in range(nseg):
+        a = np.array([xs[g], ys[g]])
+        b = np.array([xs[g + 1], ys[g + 1]])
+        ca, cb = g > 0, g < nseg - 1
+        if ca and cb:
+            m = 0.5 * (a + b)
+            side = [a + (m - a) * f for f in fr] + [b + (m - b) * f for f in fr[::-1]][1:]
+        elif cb:
+            side = [b + (a - b) * f for f in fr[::-1]]
+        else:
+            side = [a + (b - a) * f for f in fr]
+        if pts:
+            side = side[1:]
+        pts.extend(side)
+    pts = np.array(pts)
+    xa, ya = pts[:-1, 0], pts[:-1, 1]
+    xb, yb = pts[1:, 0], pts[1:, 1]
+    h = np.hypot(xb - xa, yb - ya)
+    g, w = np.polynomial.legendre.leggauss(order)
+    npan = len(h)
+    pan = np.repeat(np.arange(npan), order)
+    loc = np.tile(g, npan)
+    t = 0.5 * (loc + 1.0)
+    x = xa[pan] + (xb - xa)[pan] * t
+    y = ya[pan] + (yb - ya)[pan] * t
+    nx = (yb - ya)[pan] / h[pan]
+    ny = -(xb - xa)[pan] / h[pan]
+    wts = 0.5 * h[pan] * np.tile(w, npan)
+    nodes = Nodes(x, y, nx, ny, np.ones_like(x), wts, loc)
+    return Panels(xa, ya, xb, yb, h, pan, loc, g, w, nodes)
+
+
+def legendre_log_moments(t, nmax):
+    """L_n(t) = int_{-1}^{1} P_n(s) log|s - t| ds, n = 0..nmax, for -1 < t < 1.
+    L_0 = (1 - t) log(1 - t) + (1 + t) log(1 + t) - 2; for n >= 1, integrating
+    (2n+1) P_n = P'_{n+1} - P'_{n-1} by parts and using Neumann's formula
+    PV int P_m(s)/(s - t) ds = -2 Q_m(t):  L_n = 2 (Q_{n+1}(t) - Q_{n-1}(t))/(2n+1),
+    with Q_0 = (1/2) log((1+t)/(1-t)), Q_1 = t Q_0 - 1 and Bonnet's recursion
+    (m+1) Q_{m+1} = (2m+1) t Q_m - m Q_{m-1} (stable on the cut)."""
+    Q = np.zeros(nmax + 2)
+    Q[0] = 0.5 * math.log((1.0 + t) / (1.0 - t))
+    Q[1] = t * Q[0] - 1.0
+    for m in range(1, nmax + 1):
+        Q[m + 1] = ((2 * m + 1) * t * Q[m] - m * Q[m - 1]) / (m + 1)
+    out = np.empty(nmax + 1)
+    out[0] = (1 - t) * math.log(1 - t) + (1 + t) * math.log(1 + t) - 2.0
+    for n in range(1, nmax + 1):
+        out[n] = 2.0 * (Q[n + 1] - Q[n - 1]) / (2 * n + 1)
+    return out
+
+
+def lagrange_legendre(gl_x, gl_w, s):
+    """Values l_j(s) of the Lagrange basis of the Gauss-Legendre nodes at the
+    points s, through l_j = sum_n (2n+1)/2 w_j P_n(x_j) P_n (exact: the
+    Gauss rule integrates l_j P_n, of degree <= 2p-2, exactly)."""
+    p = len(gl_x)
+    c = (2 * np.arange(p) + 1) / 2.0
+    Pj = np.polynomial.legendre.legvander(gl_x, p - 1)          # (p, p): P_n(x_j)
+    Ps = np.polynomial.legendre.legvander(np.atleast_1d(s), p - 1)  # (m, p)
+    return (Ps * c) @ (Pj * gl_w[:, None]).T                       # (m, p): l_j(s_i)
+
+
+def own_panel_log_weights(t, half, gl_x, gl_w):
+    """W_j = int_panel l_j log|x(t) - y| ds_arc for the target at local
+    coordinate t of the same straight panel (half-length `half`):
+    |x(t) - y(s)| = half |t - s|, so W_j = half (w_j log(half) + int l_j log|t - s| ds)."""
+    p = len(gl_x)
+    c = (2 * np.arange(p) + 1) / 2.0
+    Pj = np.polynomial.legendre.legvander(gl_x, p - 1)
+    Lm = legendre_log_moments(t, p - 1)
+    return half * (gl_w * math.log(half) + gl_w * (Pj @ (c * Lm)))
+
+
+def near_panel_log_weights(px, py, xa, ya, xb, yb, gl_x, gl_w, pieces_min=1e-14):
+    """W_j = int_panel l_j(s) log|x - y(s)| ds_arc for a target x = (px, py) off
+    the panel: composite Gauss-Legendre rule on pieces of [-1, 1] graded
+    geometrically (ratio 2) toward the local coordinate of the panel point
+    nearest the target, starting from the target's distance."""
+    dx, dy = xb - xa, yb - ya
+    h = math.hypot(dx, dy)
+    half = 0.5 * h
+    cx, cy = 0.5 * (xa + xb), 0.5 * (ya + yb)
+    sstar = ((px - cx) * dx + (py - cy) * dy) / (h * half)
+    sstar = min(1.0, max(-1.0, sstar))
+    qx, qy = cx + half * sstar * dx / h, cy + half * sstar * dy / h
+    dist = max(math.hypot(px - qx, py - qy) / half, pieces_min)
+    cuts = {-1.0, 1.0, sstar}
+    step = dist
+    while step < 2.0:
+        cuts.update({sstar - step, sstar + step})
+        step *= 2.0
+    cuts = np.array(sorted(c for c in cuts if -1.0 <= c <= 1.0))
+    W = np.zeros(len(gl_x))
+    for u0, u1 in zip(cuts[:-1], cuts[1:]):
+        su = 0.5 * (u0 + u1) + 0.5 * (u1 - u0) * gl_x
+        wu = 0.5 * (u1 - u0) * gl_w
+        yx, yy = cx + half * su * dx / h, cy + half * su * dy / h
+        f = np.log(np.hypot(px - yx, py - yy))
+        W += (lagrange_legendre(gl_x, gl_w, su) * (f * wu)[:, None]).sum(axis=0)
+    return half * W
+
+
+def panel_distance(px, py, xa, ya, xb, yb):
+    dx, dy = xb - xa, yb - ya
+    t = np.clip(((px - xa) * dx + (py - ya) * dy) / (dx * dx + dy * dy), 0.0, 1.0)
+    return np.hypot(px - (xa + t * dx), py - (ya + t * dy))
+
+
 def y_upper(prob):
     f = prob.ifaces[0]
+    if is_polyline(f):
+        return max(f.y0, float(np.max(f.vy))) + prob.params.gap_U
     return f.y0 + np.sum(np.hypot(f.a, f.b)) + prob.params.gap_U
 
 
 def y_lower(prob):
     f = prob.ifaces[-1]
+    if is_polyline(f):
+        return min(f.y0, float(np.min(f.vy))) - prob.params.gap_D
     return f.y0 - np.sum(np.hypot(f.a, f.b)) - prob.params.gap_D
 
 
@@ -264,10 +431,78 @@ def _copies_xy(nd, d):
 # eq. Ablocks: near-field Nystrom blocks, as alpha-power -> matrix dictionaries
 # (Sec. 3.4: the integrals of each copy do not depend on alpha)
 # ----------------------------------------------------------------------------
+NEAR_PANELS = 1.0  # a source panel closer to the target than this many of its lengths is "near"
+
+
+def panel_self_block_terms(prob, i):
+    """Per-copy parts of A_{i,i} for a polyline interface (graded
+    Gauss-Legendre panels).  The difference kernels are split as
+    K = K_L log(rho) + K_R, K_L = 2 K1 (the coefficient of log rho; K1 is
+    the coefficient of log(4 sin^2(./2)), i.e. of 2 log rho).  Far panels
+    take the Gauss-Legendre rule w_j K.  Near panels (the target's own panel
+    and any panel within NEAR_PANELS of its lengths, in any copy) integrate
+    the log part by product integration: w_j (K - K_L log rho_j) + W_j K_L,
+    W_j = int_panel l_j log|x - y| ds.  At the target's own node the entry is
+    w_j K_R(t,t) + W_j K_L(t,t), the diagonal limits at unit speed (arc
+    length).  Identities -I, +I sit in l = 0."""
+    d = prob.d
+    P = polyline_panels(prob.ifaces[i - 1], d)
+    nd = P.nodes
+    N = len(nd.x)
+    k1, k2 = prob.k[i - 1], prob.k[i]
+    lim = self_diag_limits(k1, k2, 1.0)
+    keys = ("S", "D", "Ds", "T")
+    out = {}
+    for l in (-1, 0, 1):
+        TX, SX = np.meshgrid(nd.x, nd.x + l * d, indexing="ij")
+        TY, SY = np.meshgrid(nd.y, nd.y, indexing="ij")
+        TNX, SNX = np.meshgrid(nd.nx, nd.nx, indexing="ij")
+        TNY, SNY = np.meshgrid(nd.ny, nd.ny, indexing="ij")
+        off = np.ones((N, N), bool)
+        if l == 0:
+            off[np.arange(N), np.arange(N)] = False
+        g1 = green_kernels(k1, TX[off], TY[off], TNX[off], TNY[off], SX[off], SY[off], SNX[off], SNY[off], log_parts=True)
+        g2 = green_kernels(k2, TX[off], TY[off], TNX[off], TNY[off], SX[off], SY[off], SNX[off], SNY[off], log_parts=True)
+        rho = np.full((N, N), np.nan)
+        rho[off] = np.hypot(TX[off] - SX[off], TY[off] - SY[off])
+        K, KL = {}, {}
+        for key in keys:
+            K[key] = np.zeros((N, N), np.complex128)
+            KL[key] = np.zeros((N, N), np.complex128)
+            K[key][off] = g1[key] - g2[key]
+            KL[key][off] = 2.0 * (g1["K1" + key] - g2["K1" + key])
+        M = {key: K[key] * nd.w[None, :] for key in keys}
+        for m in range(N):
+            for q in range(len(P.h)):
+                xa, xb = P.xa[q] + l * d, P.xb[q] + l * d
+                own = (l == 0 and P.pan[m] == q)
+                if not own and panel_distance(nd.x[m], nd.y[m], xa, P.ya[q], xb, P.yb[q]) >= NEAR_PANELS * P.h[q]:
+                    continue
+                idx = np.nonzero(P.pan == q)[0]
+                if own:
+                    W = own_panel_log_weights(P.loc[m], 0.5 * P.h[q], P.gl_x, P.gl_w)
+                else:
+                    W = near_panel_log_weights(nd.x[m], nd.y[m], xa, P.ya[q], xb, P.yb[q], P.gl_x, P.gl_w)
+                for jj, j in enumerate(idx):
+                    for key in keys:
+                        if own and j == m:
+                            M[key][m, m] = nd.w[m] * lim[key + "2"] + W[jj] * 2.0 * lim[key + "1"]
+                        else:
+                            M[key][m, j] += (W[jj] - nd.w[j] * math.log(rho[m, j])) * KL[key][m, j]
+        blk = np.block([[M["D"], M["S"]], [M["T"], M["Ds"]]])
+        if l == 0:
+            blk = blk + np.diag(np.concatenate([-np.ones(N), np.ones(N)]))
+        out[l] = blk
+    return out
+
+
 def self_block_terms(prob, i):
     """Per-copy parts of A_{i,i} (i is 1-based): dict {l: (2N x 2N)} with
     A_{i,i} = sum_l alpha^l M_l.  Kernels are the differences of layer i and
-    layer i+1 kernels (Mueller-Rokhlin pairs); identities -I, +I sit in l=0."""
+    layer i+1 kernels (Mueller-Rokhlin pairs); identities -I, +I sit in l=0.
+    Smooth interfaces: the periodic log-split below; polylines: panels."""
+    if is_polyline(prob.ifaces[i - 1]):
+        return panel_self_block_terms(prob, i)
     prm = prob.params
     nd = interface_nodes(prob.ifaces[i - 1], prob.d)
     N = len(nd.x)

@@ -16,7 +16,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field, replace
-from typing import List, Optional
+from typing import List, Optional, Union
 
 import numpy as np
 
@@ -36,6 +36,29 @@ class Interface:
         self.b = np.asarray(self.b, dtype=np.float64).ravel()
         if self.a.shape != self.b.shape:
             raise ValueError("a and b must have the same length")
+
+
+@dataclass
+class PolyInterface:
+    """One d-periodic polyline interface: from (-d/2, y0) through the corners
+    (vx[c], vy[c]) (vx increasing inside (-d/2, d/2)) to (d/2, y0).  It is
+    discretised by Gauss-Legendre panels of `order` nodes, `levels` panels on
+    each side of every corner, graded dyadically toward the corner."""
+    y0: float
+    vx: np.ndarray
+    vy: np.ndarray
+    levels: int = 2
+    order: int = 16
+
+    def __post_init__(self):
+        self.vx = np.asarray(self.vx, dtype=np.float64).ravel()
+        self.vy = np.asarray(self.vy, dtype=np.float64).ravel()
+        if self.vx.shape != self.vy.shape or len(self.vx) == 0:
+            raise ValueError("vx and vy must be non-empty and of equal length")
+
+    @property
+    def N(self) -> int:
+        return 2 * len(self.vx) * self.levels * self.order
 
 
 @dataclass
@@ -68,7 +91,7 @@ class Problem:
     d: float
     k: np.ndarray            # complex, length I+1
     theta: np.ndarray        # float, n_theta angles in (-pi, 0)
-    ifaces: List[Interface]
+    ifaces: List[Union[Interface, PolyInterface]]
     params: Params
     name: str = ""
 
@@ -138,6 +161,46 @@ def config2(N: int = 120, P: int = 60, Mw: int = 30, K: int = 25, M: int = 60,
                gap_U=0.15 * d, gap_D=0.15 * d)
     return Problem(d, k, [th_w, -math.pi / 5, -math.pi / 3], ifaces, p,
                    name="config2")
+
+
+def trapezoid(y0: float, levels: int = 2, order: int = 16, height: float = 0.4,
+              x_outer: float = 0.3, x_inner: float = 0.1) -> PolyInterface:
+    """Trapezoidal profile of a unit-period corner grating: flat at y0 for
+    |x| >= x_outer, flat top y0 + height for |x| <= x_inner, straight flanks."""
+    return PolyInterface(y0, [-x_outer, -x_inner, x_inner, x_outer],
+                         [y0, y0 + height, y0 + height, y0], levels, order)
+
+
+def config3(I: int = 1000, levels: int = 2, P: int = 60, Mw: int = 30, K: int = 20,
+            M: int = 60, theta: float = -math.pi / 4) -> Problem:
+    """Paper-scale corner stack: I trapezoidal interfaces 1 apart (d = 1,
+    height 0.4, corners at x = +-0.3, +-0.1), graded Gauss-Legendre panels;
+    k_i alternating 10 and 20 with a uniform +-5 % jitter; one angle."""
+    rng = np.random.default_rng(SEED_BASE + 3)
+    d = 1.0
+    ifaces = [trapezoid(-1.0 * i, levels) for i in range(1, I + 1)]
+    base = np.where(np.arange(I + 1) % 2 == 0, 10.0, 20.0)
+    k = (base * (1.0 + rng.uniform(-0.05, 0.05, size=I + 1))).astype(np.complex128)
+    p = Params(P=P, R=1.5 * d, Mw=Mw, M=M, K=K, gap_U=0.15 * d, gap_D=0.15 * d)
+    return Problem(d, k, [theta], ifaces, p, name="config3")
+
+
+def corner_stack(I: int = 2, levels: int = 2, P: int = 60, Mw: int = 30, K: int = 12,
+                 M: int = 30, kvals=(10.0, 20.0), theta: float = -math.pi / 4,
+                 lossy: bool = False, flat: bool = False) -> Problem:
+    """A few interfaces of the corner grating (d = 1), small enough for the
+    oracle; `flat` replaces the trapezoids by flat polylines with the same
+    panels (corners of angle pi), `lossy` gives the middle layer Im k = 0.5."""
+    d = 1.0
+    ifaces = []
+    for i in range(1, I + 1):
+        t = trapezoid(-1.0 * i, levels, height=0.0 if flat else 0.4)
+        ifaces.append(t)
+    k = np.array([kvals[j % 2] for j in range(I + 1)], dtype=np.complex128)
+    if lossy and I >= 2:
+        k[1] += 0.5j
+    p = Params(P=P, R=1.5 * d, Mw=Mw, M=M, K=K, gap_U=0.15 * d, gap_D=0.15 * d)
+    return Problem(d, k, [theta], ifaces, p, name="corner_stack")
 
 
 def config4(I: int = 100, n_angles: int = 256, P: int = 60, Mw: int = 30,
@@ -211,5 +274,5 @@ def small_stack(I=3, N=64, P=50, Mw=30, K=10, M=40, seed=7, kmin=3.0,
     return Problem(d, k, th, ifaces, p, name=f"small{I}")
 
 
-CONFIGS = {"config1": config1, "config2": config2, "config4": config4,
+CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "config4": config4,
            "config5": config5}
