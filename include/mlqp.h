@@ -52,16 +52,28 @@ enum { MLQP_FP64 = 0, MLQP_MIXED = 1 };
 
 typedef struct mlqp_ctx mlqp_ctx;
 
-/* One interface: y(x) = y0 + sum_{m=1}^{n_modes} a[m-1] cos(2 pi m x/d)
+/* One interface, of one of two kinds.
+ * Smooth (n_corners = 0): y(x) = y0 + sum_{m=1}^{n_modes} a[m-1] cos(2 pi m x/d)
  *                                         + b[m-1] sin(2 pi m x/d),
- * discretised by the periodic trapezoid rule with n_nodes (even, 8..512) nodes
- * s_j = 2 pi (j - 1/2)/N (Sec. 2.5, eq. Giquad). */
+ *   discretised by the periodic trapezoid rule with n_nodes (even, 8..512)
+ *   nodes s_j = 2 pi (j - 1/2)/N (Sec. 2.5, eq. Giquad); the self term by the
+ *   periodic log-split.
+ * Corner (n_corners > 0, n_modes = 0): the polyline from (-d/2, y0) through
+ *   (vx[c], vy[c]), c = 0..n_corners-1 (vx strictly increasing inside
+ *   (-d/2, d/2)), to (d/2, y0) (Sec. 2.5, corner panels); `levels` 16-node
+ *   Gauss-Legendre panels on each side of every corner, halving toward it,
+ *   so n_nodes = 32 n_corners levels (<= 512); the log-singular self terms by
+ *   product integration on the target's own and nearby panels. */
 typedef struct {
   double y0;
   int n_modes;
   const double* a;
   const double* b;
   int n_nodes;
+  int n_corners;
+  const double* vx;
+  const double* vy;
+  int levels;
 } mlqp_interface;
 
 /* Discretisation parameters (Sec. 2.5): P proxies on a circle of radius R

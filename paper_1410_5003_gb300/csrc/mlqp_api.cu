@@ -48,12 +48,13 @@ struct mlqp_ctx {
   std::vector<LayerDesc> lay;
   std::vector<SchurTask> tasks;
   std::vector<int> n_host;
-  int maxN = 0, maxn = 0, total_nodes = 0, max_m = 0, max_p = 0, max_c = 0, max_tiles = 0;
+  int maxN = 0, maxn = 0, total_nodes = 0, total_panels = 0, max_m = 0, max_p = 0, max_c = 0, max_tiles = 0;
+  bool any_poly = false;
   long n_den = 0;
   size_t r_stride = 0, f_stride = 0, b_total = 0, qp_stride = 0, cp_stride = 0, x_stride = 0, sum_p = 0,
          t_stride = 0;
   // layout
-  Region r_ifc, r_lay, r_tasks, r_k, r_ca, r_cb, r_theta, r_scal, r_geo[7], r_wy, r_gl, r_ux, r_alpha, r_kappa,
+  Region r_ifc, r_lay, r_tasks, r_k, r_ca, r_cb, r_theta, r_scal, r_geo[8], r_pan[4], r_gl16, r_nidx, r_nw, r_wy, r_gl, r_ux, r_alpha, r_kappa,
       r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ROW32, r_F32, r_UDINV32, r_RES, r_ZX, r_ZXA, r_Y32, r_RNRM, r_PERMV, r_ETA, r_AMP, r_FLUX, r_STATUS;
   size_t ws_bytes = 0;
   // binding
@@ -213,27 +214,60 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   // interfaces
   c->ifc.resize(I);
   c->n_host.resize(I);
-  int node = 0, coef = 0;
+  int node = 0, coef = 0, pan = 0;
+  std::vector<double> ub(I), lb(I);  // bounds of each interface, for the ordering check
   for (int i = 0; i < I; ++i) {
     const mlqp_interface& f = ifaces[i];
     if (f.n_nodes < 8 || (f.n_nodes & 1)) return bad("n_nodes must be even and >= 8");
     if (f.n_nodes > 512) return bad("n_nodes must be <= 512");
-    if (f.n_modes < 0 || (f.n_modes > 0 && (!f.a || !f.b))) return bad("bad Fourier coefficients");
     if (!std::isfinite(f.y0)) return bad("y0 must be finite");
     IfaceDesc& D = c->ifc[i];
     D.N = f.n_nodes;
     D.n = 2 * f.n_nodes;
     D.node_off = node;
-    D.n_modes = f.n_modes;
     D.coef_off = coef;
     D.y0 = f.y0;
-    for (int m = 0; m < f.n_modes; ++m) {
-      if (!std::isfinite(f.a[m]) || !std::isfinite(f.b[m])) return bad("coefficients must be finite");
-      c->coef_a.push_back(f.a[m]);
-      c->coef_b.push_back(f.b[m]);
+    D.n_corners = 0;
+    D.levels = 0;
+    D.pan_off = pan;
+    if (f.n_corners > 0) {  // polyline: corners stored in the coefficient arrays
+      if (f.n_modes != 0) return bad("a corner interface has no Fourier modes");
+      if (!f.vx || !f.vy) return bad("corner interface without vertices");
+      if (f.levels < 1 || f.n_nodes != 2 * PANEL_P * f.n_corners * f.levels)
+        return bad("corner interface needs levels >= 1 and n_nodes = 32 n_corners levels");
+      double lo = f.y0, hi = f.y0, prev = -0.5 * d;
+      for (int m = 0; m < f.n_corners; ++m) {
+        if (!std::isfinite(f.vx[m]) || !std::isfinite(f.vy[m])) return bad("vertices must be finite");
+        if (!(f.vx[m] > prev && f.vx[m] < 0.5 * d)) return bad("corner abscissae must increase inside (-d/2, d/2)");
+        prev = f.vx[m];
+        lo = std::min(lo, f.vy[m]);
+        hi = std::max(hi, f.vy[m]);
+        c->coef_a.push_back(f.vx[m]);
+        c->coef_b.push_back(f.vy[m]);
+      }
+      D.n_modes = 0;
+      D.n_corners = f.n_corners;
+      D.levels = f.levels;
+      coef += f.n_corners;
+      pan += 2 * f.n_corners * f.levels;
+      c->any_poly = true;
+      ub[i] = hi;
+      lb[i] = lo;
+    } else {
+      if (f.n_modes < 0 || (f.n_modes > 0 && (!f.a || !f.b))) return bad("bad Fourier coefficients");
+      D.n_modes = f.n_modes;
+      double sum = 0.0;
+      for (int m = 0; m < f.n_modes; ++m) {
+        if (!std::isfinite(f.a[m]) || !std::isfinite(f.b[m])) return bad("coefficients must be finite");
+        c->coef_a.push_back(f.a[m]);
+        c->coef_b.push_back(f.b[m]);
+        sum += std::hypot(f.a[m], f.b[m]);
+      }
+      coef += f.n_modes;
+      ub[i] = f.y0 + sum;
+      lb[i] = f.y0 - sum;
     }
     node += f.n_nodes;
-    coef += f.n_modes;
     c->n_host[i] = D.n;
     c->maxN = std::max(c->maxN, D.N);
     c->maxn = std::max(c->maxn, D.n);
@@ -243,13 +277,10 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
     c->coef_b.push_back(0.0);
   }
   c->total_nodes = node;
+  c->total_panels = pan;
   // ordering of the interfaces: strictly decreasing bounds
-  for (int i = 0; i + 1 < I; ++i) {
-    double s0 = 0, s1 = 0;
-    for (int m = 0; m < ifaces[i].n_modes; ++m) s0 += std::hypot(ifaces[i].a[m], ifaces[i].b[m]);
-    for (int m = 0; m < ifaces[i + 1].n_modes; ++m) s1 += std::hypot(ifaces[i + 1].a[m], ifaces[i + 1].b[m]);
-    if (!(ifaces[i].y0 - s0 > ifaces[i + 1].y0 + s1)) return bad("interfaces must be separated and ordered top to bottom");
-  }
+  for (int i = 0; i + 1 < I; ++i)
+    if (!(lb[i] > ub[i + 1])) return bad("interfaces must be separated and ordered top to bottom");
   // block rows, rhs, B
   size_t roff = 0, foff = 0, boff = 0;
   long eoff = 0;
@@ -371,7 +402,12 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   take(cur, c->r_cb, d8 * c->coef_b.size());
   take(cur, c->r_theta, d8 * nt);
   take(cur, c->r_scal, d8 * 4);
-  for (int g = 0; g < 7; ++g) take(cur, c->r_geo[g], d8 * c->total_nodes);
+  for (int g = 0; g < 8; ++g) take(cur, c->r_geo[g], d8 * c->total_nodes);
+  for (int g = 0; g < 4; ++g) take(cur, c->r_pan[g], d8 * std::max(1, c->total_panels));
+  take(cur, c->r_gl16, d8 * (2 * PANEL_P + PANEL_P * PANEL_P));
+  const size_t near_nodes = c->any_poly ? (size_t)c->total_nodes : 1;
+  take(cur, c->r_nidx, sizeof(int) * near_nodes * NEAR_MAX);
+  take(cur, c->r_nw, d8 * near_nodes * NEAR_MAX * PANEL_P);
   take(cur, c->r_wy, d8 * c->L * q.Mw);
   take(cur, c->r_gl, d8 * q.Mw);
   take(cur, c->r_ux, d8 * q.M);
@@ -463,6 +499,15 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   D.SP = at<double>(c, c->r_geo[4]);
   D.TABC = at<double>(c, c->r_geo[5]);
   D.TABCHI = at<double>(c, c->r_geo[6]);
+  D.WQ = at<double>(c, c->r_geo[7]);
+  D.PXA = at<double>(c, c->r_pan[0]);
+  D.PYA = at<double>(c, c->r_pan[1]);
+  D.PXB = at<double>(c, c->r_pan[2]);
+  D.PYB = at<double>(c, c->r_pan[3]);
+  D.GL16 = at<double>(c, c->r_gl16);
+  D.NEAR_IDX = at<int>(c, c->r_nidx);
+  D.NEAR_W = at<double>(c, c->r_nw);
+  D.any_poly = c->any_poly ? 1 : 0;
   D.WY = at<double>(c, c->r_wy);
   D.GL = at<double>(c, c->r_gl);
   D.UX = at<double>(c, c->r_ux);

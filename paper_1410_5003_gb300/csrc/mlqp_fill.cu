@@ -36,6 +36,22 @@ __global__ void k_geom_nodes(Dev D) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= f.N) return;
   const int N = f.N;
+  if (f.n_corners > 0) {
+    // Gauss-Legendre node g of panel q (arc length, speed 1), downward normal
+    const int q = f.pan_off + j / PANEL_P, g = j % PANEL_P;
+    const double xa = D.PXA[q], ya = D.PYA[q], dx = D.PXB[q] - xa, dy = D.PYB[q] - ya;
+    const double h = sqrt(dx * dx + dy * dy), t = 0.5 * (D.GL16[g] + 1.0);
+    const int o = f.node_off + j;
+    D.X[o] = xa + dx * t;
+    D.Y[o] = ya + dy * t;
+    D.NX[o] = dy / h;
+    D.NY[o] = -dx / h;
+    D.SP[o] = 1.0;
+    D.WQ[o] = 0.5 * h * D.GL16[PANEL_P + g];
+    D.TABC[o] = 0.0;
+    D.TABCHI[o] = 0.0;
+    return;
+  }
   const double x = -0.5 * D.d + D.d * ((double)j + 0.5) / N;
   double y = f.y0, fp = 0.0;
   for (int m = 1; m <= f.n_modes; ++m) {
@@ -53,6 +69,7 @@ __global__ void k_geom_nodes(Dev D) {
   D.NX[o] = fp / h;
   D.NY[o] = -1.0 / h;
   D.SP[o] = (D.d / TWO_PI) * h;
+  D.WQ[o] = (TWO_PI / N) * D.SP[o];
   // log-split tables for q = j
   const int n = N / 2;
   const int q = j;
@@ -71,10 +88,210 @@ __global__ void k_geom_nodes(Dev D) {
   D.TABCHI[o] = (q <= n - 1) ? cutoff_window((TWO_PI / N) * q, D.cut_a, D.cut_b) : 0.0;
 }
 
+// ---------------------------------------------------------------------------
+// Corner interfaces (Sec. 2.5, corner panels).  k_geom_panels: the panel end
+// points of every polyline, one thread per interface, in curve order from
+// x = -d/2: a segment with corners at both ends is split at its midpoint,
+// every corner side (corner c to far point f) carries `levels` panels with
+// breakpoints c + (f - c) {0, 2^-(L-1), ..., 1/2, 1}.  Block 0 also builds
+// the 16-point Gauss-Legendre rule (Newton on P_16) and the table
+// (2n+1)/2 w_j P_n(x_j) that turns node values into Legendre coefficients.
+// ---------------------------------------------------------------------------
+__device__ void legendre_upto(double x, double* P) {  // P_0..P_{PANEL_P-1}(x)
+  P[0] = 1.0;
+  P[1] = x;
+  for (int n = 1; n + 1 < PANEL_P; ++n) P[n + 1] = ((2 * n + 1) * x * P[n] - n * P[n - 1]) / (n + 1);
+}
+
+__global__ void k_geom_panels(Dev D) {
+  if (blockIdx.x == 0 && threadIdx.x < PANEL_P) {
+    const int M = PANEL_P, r = threadIdx.x + 1;
+    double x = cos(PI * (r - 0.25) / (M + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int j = 1; j < M; ++j) {
+        const double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = M * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-16) break;
+    }
+    const int g = M - 1 - threadIdx.x;  // ascending
+    D.GL16[g] = x;
+    D.GL16[M + g] = 2.0 / ((1.0 - x * x) * dp * dp);
+    double P[PANEL_P];
+    legendre_upto(x, P);
+    for (int n = 0; n < M; ++n) D.GL16[2 * M + g * M + n] = 0.5 * (2 * n + 1) * D.GL16[M + g] * P[n];
+  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D.I) return;
+  const IfaceDesc f = D.ifc[i];
+  if (f.n_corners <= 0) return;
+  const int nc = f.n_corners, L = f.levels;
+  int q = f.pan_off;
+  bool first = true;
+  double px = 0.0, py = 0.0;
+  auto point = [&](double x, double y) {
+    if (!first) {
+      D.PXA[q] = px;
+      D.PYA[q] = py;
+      D.PXB[q] = x;
+      D.PYB[q] = y;
+      ++q;
+    }
+    first = false;
+    px = x;
+    py = y;
+  };
+  auto frac = [&](int k) { return (k == 0) ? 0.0 : ldexp(1.0, k - L); };  // k = 0..L
+  for (int g = 0; g <= nc; ++g) {
+    const double ax = (g == 0) ? -0.5 * D.d : D.coef_a[f.coef_off + g - 1];
+    const double ay = (g == 0) ? f.y0 : D.coef_b[f.coef_off + g - 1];
+    const double bx = (g == nc) ? 0.5 * D.d : D.coef_a[f.coef_off + g];
+    const double by = (g == nc) ? f.y0 : D.coef_b[f.coef_off + g];
+    const bool ca = g > 0, cb = g < nc;
+    const int k0 = (g == 0) ? 0 : 1;  // the segment's first point closes the previous one
+    if (ca && cb) {
+      const double mx = 0.5 * (ax + bx), my = 0.5 * (ay + by);
+      for (int k = k0; k <= L; ++k) point(ax + (mx - ax) * frac(k), ay + (my - ay) * frac(k));
+      for (int k = L - 1; k >= 0; --k) point(bx + (mx - bx) * frac(k), by + (my - by) * frac(k));
+    } else if (cb) {
+      for (int k = L - k0; k >= 0; --k) point(bx + (ax - bx) * frac(k), by + (ay - by) * frac(k));
+    } else {
+      for (int k = k0; k <= L; ++k) point(ax + (bx - ax) * frac(k), ay + (by - ay) * frac(k));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Near-panel product-integration weights of a corner interface, one CTA per
+// target node x: the source panels (in the copies l = -1, 0, 1) closer to x
+// than their own length, and for each W_j = int_panel l_j log|x - y| ds.
+//  Own panel (target at local t): |x - y(s)| = (h/2)|t - s|, so
+//    W_j = (h/2) (w_j log(h/2) + sum_n c_jn L_n(t)),  c_jn = (2n+1)/2 w_j P_n(x_j),
+//    L_0 = (1-t)log(1-t) + (1+t)log(1+t) - 2,  L_n = 2 (Q_{n+1} - Q_{n-1})/(2n+1)
+//    (Legendre functions of the second kind on the cut, Bonnet's recursion).
+//  Other near panels: composite Gauss-Legendre on pieces of [-1, 1] graded
+//    geometrically (ratio 2) toward the panel point nearest x, starting from
+//    x's distance; l_j(s) = sum_n c_jn P_n(s).
+// One warp per near panel; lane u < 16 takes Gauss point u of each piece and
+// accumulates all 16 weights, reduced across the lanes at the end.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_geom_near(Dev D) {
+  const int i = blockIdx.y;
+  const IfaceDesc f = D.ifc[i];
+  const int m = blockIdx.x;
+  if (f.n_corners <= 0 || m >= f.N) return;
+  const int npan = 2 * f.n_corners * f.levels;
+  const int o = f.node_off + m;
+  const double x = D.X[o], y = D.Y[o];
+  const int own = m / PANEL_P;
+  __shared__ int s_code[NEAR_MAX];
+  __shared__ int s_cnt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_cnt = 0;
+  __syncthreads();
+  for (int c = tid; c < 3 * npan; c += blockDim.x) {
+    const int l = c / npan - 1, q = c % npan;
+    const int pq = f.pan_off + q;
+    const double xa = D.PXA[pq] + l * D.d, ya = D.PYA[pq], xb = D.PXB[pq] + l * D.d, yb = D.PYB[pq];
+    const double dx = xb - xa, dy = yb - ya, h2 = dx * dx + dy * dy;
+    double t = ((x - xa) * dx + (y - ya) * dy) / h2;
+    t = fmin(1.0, fmax(0.0, t));
+    const double ex = x - (xa + t * dx), ey = y - (ya + t * dy);
+    if ((l == 0 && q == own) || ex * ex + ey * ey < h2) {
+      const int slot = atomicAdd(&s_cnt, 1);
+      if (slot < NEAR_MAX) s_code[slot] = q + npan * (l + 1);
+    }
+  }
+  __syncthreads();
+  const int cnt = s_cnt;
+  if (cnt > NEAR_MAX && tid == 0) atomicExch(D.STATUS, 1);  // more near panels than slots: MLQP_EINVAL
+  int* idx = D.NEAR_IDX + (size_t)o * NEAR_MAX;
+  double* W = D.NEAR_W + (size_t)o * NEAR_MAX * PANEL_P;
+  for (int s = tid; s < NEAR_MAX; s += blockDim.x) idx[s] = (s < cnt) ? s_code[s] : -1;
+  const double* cjn = D.GL16 + 2 * PANEL_P;
+  for (int s = warp; s < min(cnt, NEAR_MAX); s += blockDim.x / 32) {
+    const int code = s_code[s], l = code / npan - 1, q = code % npan, pq = f.pan_off + q;
+    const double xa = D.PXA[pq] + l * D.d, ya = D.PYA[pq], xb = D.PXB[pq] + l * D.d, yb = D.PYB[pq];
+    const double dx = xb - xa, dy = yb - ya, h = sqrt(dx * dx + dy * dy), half = 0.5 * h;
+    double acc[PANEL_P];
+    for (int j = 0; j < PANEL_P; ++j) acc[j] = 0.0;
+    if (l == 0 && q == own) {
+      if (lane < PANEL_P) {
+        const double t = D.GL16[m % PANEL_P];
+        double Lm[PANEL_P], Qm[PANEL_P + 1];
+        Qm[0] = 0.5 * log((1.0 + t) / (1.0 - t));
+        Qm[1] = t * Qm[0] - 1.0;
+        for (int k = 1; k < PANEL_P; ++k) Qm[k + 1] = ((2 * k + 1) * t * Qm[k] - k * Qm[k - 1]) / (k + 1);
+        Lm[0] = (1.0 - t) * log(1.0 - t) + (1.0 + t) * log(1.0 + t) - 2.0;
+        for (int n = 1; n < PANEL_P; ++n) Lm[n] = 2.0 * (Qm[n + 1] - Qm[n - 1]) / (2 * n + 1);
+        const int j = lane;
+        double sum = 0.0;
+        for (int n = 0; n < PANEL_P; ++n) sum = fma(cjn[j * PANEL_P + n], Lm[n], sum);
+        W[s * PANEL_P + j] = half * (D.GL16[PANEL_P + j] * log(half) + sum);
+      }
+      continue;
+    }
+    // nearest point of the panel, in local coordinates
+    const double cx = 0.5 * (xa + xb), cy = 0.5 * (ya + yb);
+    double ss = ((x - cx) * dx + (y - cy) * dy) / (h * half);
+    ss = fmin(1.0, fmax(-1.0, ss));
+    const double qx = cx + ss * 0.5 * dx, qy = cy + ss * 0.5 * dy;
+    const double dist = fmax(sqrt((x - qx) * (x - qx) + (y - qy) * (y - qy)) / half, 1e-14);
+    // pieces: [ss - 2^k dist, ...] on both sides, clipped to [-1, 1]
+    for (int side = 0; side < 2; ++side) {
+      double lo = ss, step = dist;
+      const double end = side ? 1.0 : -1.0;
+      for (int it = 0; it < 64 && lo != end; ++it) {
+        double hi = side ? fmin(1.0, ss + step) : fmax(-1.0, ss - step);
+        if (step >= 2.0) hi = end;
+        if (lane < PANEL_P) {
+          const double u0 = fmin(lo, hi), u1 = fmax(lo, hi);
+          const double su = 0.5 * (u0 + u1) + 0.5 * (u1 - u0) * D.GL16[lane];
+          const double wu = 0.5 * (u1 - u0) * D.GL16[PANEL_P + lane];
+          const double yx = cx + su * 0.5 * dx, yy = cy + su * 0.5 * dy;
+          const double fw = wu * log(sqrt((x - yx) * (x - yx) + (y - yy) * (y - yy)));
+          double P[PANEL_P];
+          legendre_upto(su, P);
+#pragma unroll
+          for (int j = 0; j < PANEL_P; ++j) {
+            double lj = 0.0;
+            for (int n = 0; n < PANEL_P; ++n) lj = fma(cjn[j * PANEL_P + n], P[n], lj);
+            acc[j] = fma(lj, fw, acc[j]);
+          }
+        }
+        lo = hi;
+        step *= 2.0;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < PANEL_P; ++j) {
+      double v = (lane < PANEL_P) ? acc[j] : 0.0;
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) W[s * PANEL_P + j] = half * v;
+    }
+  }
+}
+
 // Gauss-Legendre abscissae (Newton on P_M), U/D nodes, bounds of U and D,
 // walls and proxy centres of every layer, Bloch data of every angle.
 __device__ double interface_height_at(const Dev& D, int i, double x) {
   const IfaceDesc f = D.ifc[i];
+  if (f.n_corners > 0) {  // piecewise linear through (-d/2, y0), the corners, (d/2, y0)
+    double xa = -0.5 * D.d, ya = f.y0;
+    for (int c = 0; c <= f.n_corners; ++c) {
+      const double xb = (c == f.n_corners) ? 0.5 * D.d : D.coef_a[f.coef_off + c];
+      const double yb = (c == f.n_corners) ? f.y0 : D.coef_b[f.coef_off + c];
+      if (x <= xb) return ya + (yb - ya) * (x - xa) / (xb - xa);
+      xa = xb;
+      ya = yb;
+    }
+    return f.y0;
+  }
   double y = f.y0;
   for (int m = 1; m <= f.n_modes; ++m) {
     double s, c;
@@ -96,11 +313,19 @@ __global__ void k_geom_misc(Dev D, double* scal) {
   __shared__ double sYU, sYD;
   if (t == 0) {
     const IfaceDesc f0 = D.ifc[0], fl = D.ifc[D.I - 1];
-    double s0 = 0.0, sl = 0.0;
-    for (int m = 0; m < f0.n_modes; ++m) s0 += hypot(D.coef_a[f0.coef_off + m], D.coef_b[f0.coef_off + m]);
-    for (int m = 0; m < fl.n_modes; ++m) sl += hypot(D.coef_a[fl.coef_off + m], D.coef_b[fl.coef_off + m]);
-    sYU = f0.y0 + s0 + D.yU;   // D.yU holds gap_U here
-    sYD = fl.y0 - sl - D.yD;   // D.yD holds gap_D here
+    double top = f0.y0, bot = fl.y0;
+    if (f0.n_corners > 0) {
+      for (int c = 0; c < f0.n_corners; ++c) top = fmax(top, D.coef_b[f0.coef_off + c]);
+    } else {
+      for (int m = 0; m < f0.n_modes; ++m) top += hypot(D.coef_a[f0.coef_off + m], D.coef_b[f0.coef_off + m]);
+    }
+    if (fl.n_corners > 0) {
+      for (int c = 0; c < fl.n_corners; ++c) bot = fmin(bot, D.coef_b[fl.coef_off + c]);
+    } else {
+      for (int m = 0; m < fl.n_modes; ++m) bot -= hypot(D.coef_a[fl.coef_off + m], D.coef_b[fl.coef_off + m]);
+    }
+    sYU = top + D.yU;   // D.yU holds gap_U here
+    sYD = bot - D.yD;   // D.yD holds gap_D here
     scal[0] = sYU;
     scal[1] = sYD;
   }
@@ -199,7 +424,52 @@ __global__ void __launch_bounds__(128) k_fill_A(Dev D) {
   const int Ns = fs.N;
   const double h = TWO_PI / Ns;
   cplx v[3][4];  // per copy: D, S, T, Ds
-  if (type == 0) {
+  if (type == 0 && fs.n_corners > 0) {
+    // graded panels: K = K_L log rho + K_R, K_L = 2 K1; far panels take the
+    // Gauss-Legendre rule, near panels add (W_j - w_j log rho) K_L, the own
+    // node is w_j K_R(t,t) + W_j K_L(t,t) (diagonal limits at unit speed)
+    const cplx k1 = C(D.kre[2 * i], D.kre[2 * i + 1]);
+    const cplx k2 = C(D.kre[2 * i + 2], D.kre[2 * i + 3]);
+    const int npan = 2 * fs.n_corners * fs.levels;
+    const int qj = j / PANEL_P, gj = j % PANEL_P;
+    const double wq = D.WQ[so];
+    const int* nidx = D.NEAR_IDX + (size_t)to * NEAR_MAX;
+    const double* nw = D.NEAR_W + (size_t)to * NEAR_MAX * PANEL_P;
+#pragma unroll 1
+    for (int l = -1; l <= 1; ++l) {
+      const int code = qj + npan * (l + 1);
+      int slot = -1;
+      for (int q = 0; q < NEAR_MAX; ++q)
+        if (nidx[q] == code) slot = q;
+      const double W = (slot >= 0) ? nw[slot * PANEL_P + gj] : 0.0;
+      if (l == 0 && j == m) {
+        cplx l2[4], l1[4];
+        diag_limits(k1, k2, 1.0, l2, l1);
+        v[1][0] = wq * l2[1] + (2.0 * W) * l1[1] + C(-1.0);  // D (with -I)
+        v[1][1] = wq * l2[0] + (2.0 * W) * l1[0];            // S
+        v[1][2] = wq * l2[3] + (2.0 * W) * l1[3];            // T
+        v[1][3] = wq * l2[2] + (2.0 * W) * l1[2] + C(1.0);   // Ds (with +I)
+        continue;
+      }
+      const Geo g = geo(tx, ty, tnx, tny, sx0 + l * D.d, sy, snx, sny);
+      if (slot >= 0) {
+        const KernL a = kernels_log(k1, g, hankel(k1, g.rho));
+        const KernL b = kernels_log(k2, g, hankel(k2, g.rho));
+        const double cw = 2.0 * (W - wq * log(g.rho));
+        v[l + 1][0] = wq * (a.D - b.D) + cw * (a.K1D - b.K1D);
+        v[l + 1][1] = wq * (a.S - b.S) + cw * (a.K1S - b.K1S);
+        v[l + 1][2] = wq * (a.T - b.T) + cw * (a.K1T - b.K1T);
+        v[l + 1][3] = wq * (a.Ds - b.Ds) + cw * (a.K1Ds - b.K1Ds);
+      } else {
+        const Kern a = kernels(k1, g, hankel(k1, g.rho));
+        const Kern b = kernels(k2, g, hankel(k2, g.rho));
+        v[l + 1][0] = wq * (a.D - b.D);
+        v[l + 1][1] = wq * (a.S - b.S);
+        v[l + 1][2] = wq * (a.T - b.T);
+        v[l + 1][3] = wq * (a.Ds - b.Ds);
+      }
+    }
+  } else if (type == 0) {
     const cplx k1 = C(D.kre[2 * i], D.kre[2 * i + 1]);
     const cplx k2 = C(D.kre[2 * i + 2], D.kre[2 * i + 3]);
     const int n = Ns / 2;
@@ -243,7 +513,7 @@ __global__ void __launch_bounds__(128) k_fill_A(Dev D) {
     const int layer = (type == 1) ? i + 1 : i;
     const cplx k = C(D.kre[2 * layer], D.kre[2 * layer + 1]);
     const double sgn = (type == 1) ? -1.0 : 1.0;
-    const double ws = sgn * h * sp;
+    const double ws = sgn * D.WQ[so];
 #pragma unroll 1
     for (int l = -1; l <= 1; ++l) {
       const Geo g = geo(tx, ty, tnx, tny, sx0 + l * D.d, sy, snx, sny);
@@ -328,7 +598,7 @@ __global__ void __launch_bounds__(128) k_fill_C(Dev D) {
   const cplx k = C(D.kre[2 * jl], D.kre[2 * jl + 1]);
   const int o = f.node_off + j;
   const double sx = D.X[o], sy = D.Y[o], snx = D.NX[o], sny = D.NY[o];
-  const double w = (TWO_PI / f.N) * D.SP[o];
+  const double w = D.WQ[o];
   const double yw = D.WY[jl * D.Mw + g];
   const double xw = -0.5 * D.d;
   const Geo gp = geo(xw + 2.0 * D.d, yw, 1.0, 0.0, sx, sy, snx, sny);
@@ -360,7 +630,7 @@ __global__ void __launch_bounds__(128) k_fill_Z(Dev D, const double* scal) {
   const cplx k = C(D.kre[2 * jl], D.kre[2 * jl + 1]);
   const int o = f.node_off + j;
   const double sy = D.Y[o], snx = D.NX[o], sny = D.NY[o];
-  const double w = (TWO_PI / f.N) * D.SP[o];
+  const double w = D.WQ[o];
   const double tx = D.UX[m], ty = which ? scal[1] : scal[0];
   Kern v[3];
 #pragma unroll 1
@@ -475,7 +745,15 @@ __global__ void k_fill_rhs(Dev D) {
 // ---------------------------------------------------------------------------
 cudaError_t launch_geometry(const Dev& D, double* scal, cudaStream_t s) {
   ++g_launches;
+  if (D.any_poly) {
+    ++g_launches;
+    k_geom_panels<<<(D.I + 127) / 128, 128, 0, s>>>(D);
+  }
   k_geom_nodes<<<dim3((D.maxN + 127) / 128, D.I), 128, 0, s>>>(D);
+  if (D.any_poly) {
+    ++g_launches;
+    k_geom_near<<<dim3(D.maxN, D.I), 128, 0, s>>>(D);
+  }
   ++g_launches;
   k_geom_misc<<<1, 256, 0, s>>>(D, scal);
   return cudaGetLastError();

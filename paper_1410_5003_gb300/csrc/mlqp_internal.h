@@ -15,6 +15,9 @@ struct IfaceDesc {
   int n_modes;    // Fourier modes of the profile
   int coef_off;   // offset into the coefficient arrays a, b
   int nl, nr;     // unknowns of the neighbours above (i-1) and below (i+1); 0 at the ends
+  int n_corners;   // > 0: polyline interface with graded Gauss-Legendre panels
+  int levels;      // panels per corner side
+  int pan_off;     // offset of its panels in the panel arrays
   size_t row_off;  // element offset of the block row [A_{i,i-1} | A_{i,i} | A_{i,i+1}] in one angle
   int row_cols;    // nl + n + nr
   size_t rhs_off;  // element offset of f_i in one angle
@@ -66,6 +69,8 @@ struct AngleStreams {
 
 // Problem scalars and workspace pointers, passed by value to the kernels.
 constexpr int RNRM_W = 8;  // doubles per angle of the refinement control block
+constexpr int PANEL_P = 16;  // Gauss-Legendre nodes per corner panel
+constexpr int NEAR_MAX = 12; // near-panel slots per node of a corner interface
 
 struct Dev {
   int I, L, n_theta, P, Mw, M, K, nK;
@@ -81,6 +86,16 @@ struct Dev {
   // geometry (doubles, total_nodes each)
   double *X, *Y, *NX, *NY, *SP;
   double *TABC, *TABCHI;  // Kress-minus-log weights (TABC[0] = R_0) and window values, per |q|
+  double* WQ;              // quadrature weight of every interface node
+  // corner interfaces: panel end points, 16-point Gauss-Legendre rule (nodes,
+  // weights, then the Lagrange-to-Legendre table (2n+1)/2 w_j P_n(x_j)), and
+  // per node NEAR_MAX near-panel slots: panel code (panel + npan (copy + 1),
+  // -1 empty) and 16 product-integration weights each
+  double *PXA, *PYA, *PXB, *PYB;
+  double* GL16;
+  int* NEAR_IDX;
+  double* NEAR_W;
+  int any_poly;
   double* WY;             // wall nodes y, (I+1) x Mw
   double* GL;             // Gauss-Legendre abscissae on [-1, 1], Mw
   double* UX;             // U/D nodes x, M

@@ -24,7 +24,8 @@ BLK_ROW, BLK_B, BLK_QP, BLK_CP, BLK_X, BLK_RHS, BLK_NODES, BLK_ETA, BLK_AMP, BLK
 
 class mlqp_interface(ct.Structure):
     _fields_ = [("y0", ct.c_double), ("n_modes", ct.c_int), ("a", ct.POINTER(ct.c_double)),
-                ("b", ct.POINTER(ct.c_double)), ("n_nodes", ct.c_int)]
+                ("b", ct.POINTER(ct.c_double)), ("n_nodes", ct.c_int), ("n_corners", ct.c_int),
+                ("vx", ct.POINTER(ct.c_double)), ("vy", ct.POINTER(ct.c_double)), ("levels", ct.c_int)]
 
 
 class mlqp_params(ct.Structure):
@@ -111,7 +112,8 @@ def make_params(p, precision=MLQP_FP64, max_refine=0, refine_tol=0.0):
 
 
 def mlqp_setup(prob, precision=MLQP_FP64, max_refine=0, refine_tol=0.0):
-    """prob: an object with .ifaces (y0, a, b, N), .k (complex, I+1), .d,
+    """prob: an object with .ifaces (y0, a, b, N; or y0, vx, vy, levels for a
+    corner interface), .k (complex, I+1), .d,
     .theta, .params (P, R, Mw, M, K, gap_U, gap_D, cut_a, cut_b, lsq_rcond).
     Returns (ctx handle, keep-alive list)."""
     lib = load()
@@ -119,10 +121,19 @@ def mlqp_setup(prob, precision=MLQP_FP64, max_refine=0, refine_tol=0.0):
     keep = []
     arr = (mlqp_interface * I)()
     for i, f in enumerate(prob.ifaces):
-        a = np.ascontiguousarray(f.a, dtype=np.float64)
-        b = np.ascontiguousarray(f.b, dtype=np.float64)
-        keep += [a, b]
-        arr[i] = mlqp_interface(float(f.y0), len(a), _dptr(a), _dptr(b), int(f.N))
+        if hasattr(f, "vx"):  # corner interface (polyline with graded panels)
+            if getattr(f, "order", 16) != 16:
+                raise ValueError("corner interfaces use 16-node panels")
+            vx = np.ascontiguousarray(f.vx, dtype=np.float64)
+            vy = np.ascontiguousarray(f.vy, dtype=np.float64)
+            keep += [vx, vy]
+            arr[i] = mlqp_interface(float(f.y0), 0, None, None, int(f.N), len(vx), _dptr(vx), _dptr(vy),
+                                    int(f.levels))
+        else:
+            a = np.ascontiguousarray(f.a, dtype=np.float64)
+            b = np.ascontiguousarray(f.b, dtype=np.float64)
+            keep += [a, b]
+            arr[i] = mlqp_interface(float(f.y0), len(a), _dptr(a), _dptr(b), int(f.N), 0, None, None, 0)
     k = np.ascontiguousarray(np.stack([np.real(prob.k), np.imag(prob.k)], axis=1).ravel(), dtype=np.float64)
     th = np.ascontiguousarray(prob.theta, dtype=np.float64)
     keep += [k, th]

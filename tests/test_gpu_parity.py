@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 from scipy.special import hankel1, jv  # noqa: E402
 
 from oracle import mlqp_oracle as O  # noqa: E402
-from workloads import config1, config2, small_stack, flat_stack  # noqa: E402
+from workloads import config1, config2, corner_stack, small_stack, flat_stack  # noqa: E402
 from workloads.problems import Interface, Params, Problem  # noqa: E402
 from tests.closed_forms import fresnel  # noqa: E402
 
@@ -81,6 +81,11 @@ PROBLEMS = {
     "small3": lambda: small_stack(I=3, N=80, P=60, Mw=40, K=20, M=50),
     "small3_lossy": lambda: small_stack(I=3, N=80, P=60, Mw=40, K=20, M=50, lossy=True),
     "uneven": uneven_stack,
+    # corner gratings (d = 1, graded 16-node panels, K large enough for the
+    # U/D lines 0.15 d away): trapezoids, a lossy middle layer, a flat polyline
+    "corner2": lambda: corner_stack(I=2, levels=2, K=24, M=50),
+    "corner2_lossy": lambda: corner_stack(I=2, levels=2, K=24, M=50, lossy=True),
+    "corner_flat": lambda: corner_stack(I=1, levels=2, K=24, M=50, flat=True, kvals=(5.0, 10.0)),
 }
 
 
@@ -292,7 +297,7 @@ def test_zero_pivot_is_reported_not_faulted(M):
     ctx.close()
 
 
-@pytest.mark.parametrize("name", ["config1", "small3", "small3_lossy", "uneven"])
+@pytest.mark.parametrize("name", ["config1", "small3", "small3_lossy", "uneven", "corner2"])
 def test_mixed_precision_matches_oracle(M, name):
     """FP32 Schur complements and block LU with FP64 iterative refinement
     (residual from the unreduced FP64 operator) reproduce the oracle's
