@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--config3", action="store_true",
+                    help="also time the 1000-interface corner grating (one solve per form, after a warm-up)")
+    ap.add_argument("--corner-levels", type=int, default=2)
     return ap.parse_args()
 
 
@@ -186,6 +189,40 @@ def run_reference(args):
                              "sample": "one angle of the stack per step, all 20 interfaces"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def corner_grating(mlqp, dev, levels):
+    """The paper-scale corner stack (1000 trapezoidal interfaces, d = 1, graded
+    panels): one timed solve per form after a warm-up, per-stage CUDA events."""
+    import torch
+    from workloads import config3
+    out = {"workload": f"1000 trapezoidal interfaces, {levels} panel levels per corner side, one angle",
+           "unit": METRIC}
+    for name, prec in (("fp64", mlqp.MLQP_FP64), ("mixed", mlqp.MLQP_MIXED)):
+        prob = config3(levels=levels)
+        ctx = mlqp.Context(prob, device=dev, precision=prec)
+        st = [mlqp.STAGE_GEOM, mlqp.STAGE_FILL, mlqp.STAGE_LSQ, mlqp.STAGE_SCHUR, mlqp.STAGE_SWEEP,
+              mlqp.STAGE_RECOVER]
+        for s_ in st:
+            ctx.run_stage(s_)
+        ctx.check()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(st) + 1)]
+        with torch.cuda.stream(ctx.stream):
+            for q, s_ in enumerate(st):
+                evs[q].record(ctx.stream)
+                ctx.run_stage(s_)
+            evs[-1].record(ctx.stream)
+        torch.cuda.synchronize()
+        ctx.check()
+        ms = [evs[q].elapsed_time(evs[q + 1]) for q in range(len(st))]
+        res = ctx.solve_host()
+        out[name] = {"value": prob.I / (sum(ms) / 1e3), "ms_per_solve": sum(ms),
+                     "stage_ms": dict(zip(["geometry", "fill", "lsq", "schur", "sweep", "recover"], ms)),
+                     "flux_error": float(res["flux"][0]), "unknowns": int(sum(2 * f.N for f in prob.ifaces)),
+                     "workspace_gb": ctx.ws_bytes / 1e9}
+        ctx.close()
+    return out
 
 
 def main():
@@ -350,6 +387,8 @@ def main():
             d2h = sum(v.numel() * v.element_size() for v in hout.values() if v is not None) + 4
             line["e2e"] = {"value": units * ws * K / el, "unit": METRIC, "h2d_bytes_per_step": ctx.upload_bytes(),
                            "d2h_bytes_per_step": d2h}
+    if args.config3 and rank == 0:
+        line["config3"] = corner_grating(mlqp, dev, args.corner_levels)
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(1)
