@@ -22,6 +22,7 @@
 // Angle groups run on streams of their own.  The kernels are templates on the
 // real type: FP64 for the plain path, FP32 for the factorisation of the
 // mixed-precision path (whose solves are refined in FP64, mlqp_mixed.cu).
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "mlqp_internal.h"
@@ -141,6 +142,7 @@ constexpr int PCL = 8;
 constexpr int PCL_THREADS = 128;
 constexpr int PCL_SLOTS = 4;  // rows per lane: RC <= 32 PCL_SLOTS, so n_i <= 1024
 constexpr int PCL_WARPS = PCL_THREADS / 32;
+constexpr size_t PANEL_SMEM_MIN = 116 * 1024;  // more than half of an SM's shared memory
 
 template <typename R>
 __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
@@ -232,19 +234,32 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
     }
     cl.sync();
     if (warp == 0) {
+      // every remote load is issued before any shared-memory store, so they
+      // overlap (the stores could otherwise alias the generic remote pointers)
+      constexpr int GU = (PCL * NB) / 32;
+      vec2<R> cand[GU];
 #pragma unroll
-      for (int u = 0; u < (PCL * NB) / 32; ++u) {
+      for (int u = 0; u < GU; ++u) {
         const int e = lane + 32 * u, rk = e / NB, j = e % NB;
-        if (j < w) s_all[rk][j] = *cl.map_shared_rank(&s_cand[cb][j], rk);
+        if (j < w) cand[u] = *cl.map_shared_rank(&s_cand[cb][j], rk);
       }
-      unsigned key = 0, pos = 0xffffffffu;
+      unsigned key = 0;
+      int ix = 0x7fffffff;
+      vec2<R> rinv_r, rowc_r;
       if (lane < PCL) {
         key = *cl.map_shared_rank(&s_key[cb], lane);
-        const int ix = *cl.map_shared_rank(&s_idx[cb], lane);
-        pos = (ix == 0x7fffffff) ? 0xffffffffu : (unsigned)ix;
-        s_arinv[lane] = *cl.map_shared_rank(&s_crinv[cb], lane);
+        ix = *cl.map_shared_rank(&s_idx[cb], lane);
+        rinv_r = *cl.map_shared_rank(&s_crinv[cb], lane);
       }
-      if (lane < w) s_rowcl[lane] = *cl.map_shared_rank(&s_rowc[cb][lane], qc);
+      if (lane < w) rowc_r = *cl.map_shared_rank(&s_rowc[cb][lane], qc);
+#pragma unroll
+      for (int u = 0; u < GU; ++u) {
+        const int e = lane + 32 * u, rk = e / NB, j = e % NB;
+        if (j < w) s_all[rk][j] = cand[u];
+      }
+      if (lane < PCL) s_arinv[lane] = rinv_r;
+      if (lane < w) s_rowcl[lane] = rowc_r;
+      const unsigned pos = (lane < PCL && ix != 0x7fffffff) ? (unsigned)ix : 0xffffffffu;
       const unsigned kmax = __reduce_max_sync(0xffffffffu, (pos != 0xffffffffu) ? key : 0u);
       const unsigned pr_u = __reduce_min_sync(0xffffffffu, (pos != 0xffffffffu && key == kmax) ? pos : 0xffffffffu);
       __syncwarp();
@@ -632,7 +647,8 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
     auto panel = [&](int k, cudaStream_t st) {
       const int w = (nt - k < NB) ? nt - k : NB;
       const size_t rc = (size_t)((nt - k + PCL - 1) / PCL);
-      const size_t smem = rc * (w + 1) * sizeof(vec2<R>) + rc * sizeof(unsigned);
+      // at least PANEL_SMEM_MIN, so that no two panel CTAs share an SM's FP64 pipes
+      const size_t smem = std::max(rc * (w + 1) * sizeof(vec2<R>) + rc * sizeof(unsigned), PANEL_SMEM_MIN);
       ++g_launches;
       k_lu_panel_cl<R><<<dim3(PCL, na), PCL_THREADS, smem, st>>>(D, t, k, a0);
     };
@@ -726,7 +742,7 @@ cudaError_t launch_recover(const Dev& D, cudaStream_t s) {
 
 size_t sweep_panel_smem_max(int maxn) {
   const size_t rc = (size_t)((maxn + PCL - 1) / PCL);
-  return rc * (NB + 1) * sizeof(double2) + rc * sizeof(unsigned);
+  return std::max(rc * (NB + 1) * sizeof(double2) + rc * sizeof(unsigned), PANEL_SMEM_MIN);
 }
 
 cudaError_t sweep_configure(int maxn) {
