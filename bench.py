@@ -198,9 +198,10 @@ def corner_grating(mlqp, dev, levels):
     from workloads import config3
     out = {"workload": f"1000 trapezoidal interfaces, {levels} panel levels per corner side, one angle",
            "unit": METRIC}
-    for name, prec in (("fp64", mlqp.MLQP_FP64), ("mixed", mlqp.MLQP_MIXED)):
+    for name, prec, solver in (("fp64", mlqp.MLQP_FP64, mlqp.MLQP_SWEEP), ("mixed", mlqp.MLQP_MIXED, mlqp.MLQP_SWEEP),
+                               ("mixed_cyclic", mlqp.MLQP_MIXED, mlqp.MLQP_CYCLIC)):
         prob = config3(levels=levels)
-        ctx = mlqp.Context(prob, device=dev, precision=prec)
+        ctx = mlqp.Context(prob, device=dev, precision=prec, block_solver=solver)
         st = [mlqp.STAGE_GEOM, mlqp.STAGE_FILL, mlqp.STAGE_LSQ, mlqp.STAGE_SCHUR, mlqp.STAGE_SWEEP,
               mlqp.STAGE_RECOVER]
         for s_ in st:
@@ -327,9 +328,11 @@ def main():
                 "schur_tflops": nth * schur_flops(n, prob.params.P) / (stage_ms["schur"] / 1e3) / 1e12}
         if clocks:
             line["clocks"] = clocks
-    # the mixed-precision form on the same stack: FP32 Schur / block LU, FP64 refinement
-    if not args.no_mixed:
-        mctx = mlqp.Context(prob, device=dev, precision=mlqp.MLQP_MIXED, max_refine=10, refine_tol=1e-15)
+    # the mixed-precision form on the same stack: FP32 Schur / block LU (sweep, then
+    # block cyclic reduction), FP64 refinement
+    def time_mixed(solver):
+        mctx = mlqp.Context(prob, device=dev, precision=mlqp.MLQP_MIXED, max_refine=10, refine_tol=1e-15,
+                            block_solver=solver)
         mout = mctx.outputs()
         for _ in range(args.warmup):
             mctx.solve_device(mout)
@@ -356,16 +359,23 @@ def main():
             mms = float(t.item())
         mctx.solve_device(mout)
         mctx.check()
-        diff = float(torch.max(torch.abs(torch.cat([mout["aU"], mout["aD"]], 1) - torch.cat([out["aU"], out["aD"]], 1)))
-                     / torch.max(torch.abs(torch.cat([out["aU"], out["aD"]], 1))))
-        if rank == 0:
-            line["mixed"] = {"value": units * ws * K / (mms / 1e3), "unit": METRIC, "ms_per_step": mms / K,
-                             "speedup_vs_fp64": (total_ms / K) / (mms / K),
-                             "refine_steps": [int(mctx.block(mlqp.BLK_REFINE, 1, a)[1]) for a in range(nth)],
-                             "backward_error": max(float(mctx.block(mlqp.BLK_REFINE, 1, a)[0]) for a in range(nth)),
-                             "max_rel_amp_diff_vs_fp64": diff,
-                             "dtype": "f32 Schur/LU + f64 refinement (fill, least squares, residuals in f64)"}
+        ref = torch.cat([out["aU"], out["aD"]], 1)
+        diff = float(torch.max(torch.abs(torch.cat([mout["aU"], mout["aD"]], 1) - ref)) / torch.max(torch.abs(ref)))
+        res = {"value": units * ws * K / (mms / 1e3), "unit": METRIC, "ms_per_step": mms / K,
+               "speedup_vs_fp64": (total_ms / K) / (mms / K),
+               "refine_steps": [int(mctx.block(mlqp.BLK_REFINE, 1, a)[1]) for a in range(nth)],
+               "backward_error": max(float(mctx.block(mlqp.BLK_REFINE, 1, a)[0]) for a in range(nth)),
+               "max_rel_amp_diff_vs_fp64": diff,
+               "block_solver": "sweep" if solver == mlqp.MLQP_SWEEP else "cyclic reduction",
+               "dtype": "f32 Schur/LU + f64 refinement (fill, least squares, residuals in f64)"}
         mctx.close()
+        return res
+
+    if not args.no_mixed:
+        for key, solver in (("mixed", mlqp.MLQP_SWEEP), ("mixed_cyclic", mlqp.MLQP_CYCLIC)):
+            res = time_mixed(solver)
+            if rank == 0:
+                line[key] = res
     # e2e through the C ABI with host buffers: bind (H2D of the problem) + solve (D2H of amplitudes)
     if not args.no_e2e:
         hout = ctx.host_outputs(eta=False, pinned=True)

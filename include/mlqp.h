@@ -49,6 +49,7 @@ typedef enum {
 } mlqp_status;
 
 enum { MLQP_FP64 = 0, MLQP_MIXED = 1 };
+enum { MLQP_SWEEP = 0, MLQP_CYCLIC = 1 };
 
 typedef struct mlqp_ctx mlqp_ctx;
 
@@ -90,7 +91,12 @@ typedef struct {
  * the normwise backward error
  *     omega = max_r |r_r| / max_r (|f_r| + sum_c |A_rc||eta_c| + sum_c |B_rc| (|X||eta|)_c),
  *     r = f - A eta + B (X eta)   (the unreduced FP64 operator, |z| = |re| + |im|)
- * is at most refine_tol > 0; MLQP_ENOTCONV if it is not). */
+ * is at most refine_tol > 0; MLQP_ENOTCONV if it is not).  block_solver:
+ * MLQP_SWEEP (the block-tridiagonal LU sweep of Sec. 3.3, sequential over
+ * interfaces) or, for MLQP_MIXED with equal n_nodes on every interface,
+ * MLQP_CYCLIC (block cyclic reduction over the interfaces: log2 I levels of
+ * batched FP32 LU, triangular solves and Schur updates, the parallel block
+ * solve the paper's closing remarks name for deep stacks). */
 typedef struct {
   int P;
   double R;
@@ -105,6 +111,7 @@ typedef struct {
   int precision;
   int max_refine;
   double refine_tol;
+  int block_solver;
 } mlqp_params;
 
 /* Validates the problem and records it on the host (no device work).

@@ -24,7 +24,9 @@ cudaError_t sweep_configure(int maxn);
 cudaError_t mixed_configure(int maxn);
 cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s);
 cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n_den, int max_refine, double tol,
-                               int* permv, const AngleStreams& A);
+                               int* permv, const AngleStreams& A, bool cyclic);
+cudaError_t cr_configure(int maxn);
+int cr_slots(int I);
 cudaError_t lsq_configure(int max_m, int max_p);
 cudaError_t launch_hankel_eval(const double* kr, int n, double* out, cudaStream_t s);
 extern thread_local long g_launches;
@@ -55,7 +57,7 @@ struct mlqp_ctx {
          t_stride = 0;
   // layout
   Region r_ifc, r_lay, r_tasks, r_k, r_ca, r_cb, r_theta, r_scal, r_geo[8], r_pan[4], r_gl16, r_nidx, r_nw, r_wy, r_gl, r_ux, r_alpha, r_kappa,
-      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ROW32, r_F32, r_UDINV32, r_RES, r_ZX, r_ZXA, r_Y32, r_RNRM, r_PERMV, r_ETA, r_AMP, r_FLUX, r_STATUS;
+      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ROW32, r_F32, r_UDINV32, r_RES, r_ZX, r_ZXA, r_Y32, r_RNRM, r_CRSAVE, r_PERMV, r_ETA, r_AMP, r_FLUX, r_STATUS;
   size_t ws_bytes = 0;
   // binding
   char* ws = nullptr;
@@ -201,6 +203,12 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   if (q.precision != MLQP_FP64 && q.precision != MLQP_MIXED) return bad("precision must be MLQP_FP64 or MLQP_MIXED");
   if (q.precision == MLQP_MIXED && (q.max_refine < 1 || q.max_refine > 50 || !(q.refine_tol > 0)))
     return bad("MLQP_MIXED needs 1 <= max_refine <= 50 and refine_tol > 0");
+  if (q.block_solver != MLQP_SWEEP && q.block_solver != MLQP_CYCLIC) return bad("block_solver must be MLQP_SWEEP or MLQP_CYCLIC");
+  if (q.block_solver == MLQP_CYCLIC) {
+    if (q.precision != MLQP_MIXED) return bad("MLQP_CYCLIC is the block solver of the MLQP_MIXED form");
+    for (int i = 1; i < I; ++i)
+      if (ifaces[i].n_nodes != ifaces[0].n_nodes) return bad("MLQP_CYCLIC needs equal n_nodes on every interface");
+  }
   c->k.assign(k, k + 2 * (I + 1));
   for (int j = 0; j <= I; ++j) {
     if (!(c->k[2 * j] > 0) || !(c->k[2 * j + 1] >= 0) || !std::isfinite(c->k[2 * j]) ||
@@ -436,6 +444,8 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
     take(cur, c->r_ZXA, d8 * nt * (size_t)c->L * q.P);
     take(cur, c->r_Y32, f8 * nt * c->n_den);
     take(cur, c->r_RNRM, d8 * nt * RNRM_W);
+    if (q.block_solver == MLQP_CYCLIC)
+      take(cur, c->r_CRSAVE, sizeof(float2) * nt * (size_t)cr_slots(I) * 2 * c->maxn * c->maxn);
     take(cur, c->r_PERMV, sizeof(int) * nt * c->n_den);
   }
   take(cur, c->r_ETA, z16 * nt * c->n_den);
@@ -543,6 +553,10 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
     D.ZXA = at<double>(c, c->r_ZXA);
     D.Y32 = at<float2>(c, c->r_Y32);
     D.RNRM = at<double>(c, c->r_RNRM);
+    if (q.block_solver == MLQP_CYCLIC) {
+      D.CRSAVE = at<float2>(c, c->r_CRSAVE);
+      D.crsave_stride = (size_t)cr_slots(c->I) * 2 * c->maxn * c->maxn;
+    }
   }
   D.ETA = at<double2>(c, c->r_ETA);
   D.eta_stride = c->n_den;
@@ -581,6 +595,8 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   if ((e = lsq_configure(c->max_m, c->max_p)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
   if (q.precision == MLQP_MIXED && (e = mixed_configure(c->maxn)) != cudaSuccess)
     return cuda_fail(c, e, "kernel configuration");
+  if (q.block_solver == MLQP_CYCLIC && (e = cr_configure(c->maxn)) != cudaSuccess)
+    return cuda_fail(c, e, "kernel configuration");
   if ((e = make_angle_streams(c)) != cudaSuccess) return cuda_fail(c, e, "sweep streams");
   c->bound = true;
   return MLQP_OK;
@@ -606,7 +622,7 @@ static cudaError_t enqueue_stage(mlqp_ctx* c, int stage, cudaStream_t st) {
     case MLQP_STAGE_SWEEP:
       e = (c->prm.precision == MLQP_MIXED)
               ? launch_mixed_solve(c->D, c->n_host.data(), c->maxn, c->n_den, c->prm.max_refine, c->prm.refine_tol,
-                                   at<int>(c, c->r_PERMV), A)
+                                   at<int>(c, c->r_PERMV), A, c->prm.block_solver == MLQP_CYCLIC)
               : launch_sweep(c->D, c->n_host.data(), A);
       break;
     case MLQP_STAGE_RECOVER: e = launch_recover(c->D, st); break;

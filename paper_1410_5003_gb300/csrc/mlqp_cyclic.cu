@@ -1,0 +1,591 @@
+// Block cyclic reduction over the interfaces: the parallel block solve that
+// the paper's closing remarks name for deep stacks, used for the FP32
+// factorisation of the mixed-precision form when every interface has the
+// same node count.
+//
+// Level k (s = 2^k) eliminates the interfaces i = s, 3s, 5s, ... (i < I):
+//   G_i = A~_i^{-1} A_{i,i-s},  H_i = A~_i^{-1} A_{i,i+s}   (LU of A~_i, row pivoting)
+// and updates the survivors e = 0, 2s, 4s, ...:
+//   A~_e       -= A_{e,e-s} H_{e-s} + A_{e,e+s} G_{e+s},
+//   A_{e,e-2s}  = -A_{e,e-s} G_{e-s},   A_{e,e+2s} = -A_{e,e+s} H_{e+s},
+// until interface 0 alone remains; its LU closes the factorisation.  The
+// couplings A_{e,e+-s} consumed at each level are saved: the solve needs them.
+// Solve of A' y = r (y holds r on entry):
+//   forward,  k = 0..K-1: y_i <- A~_i^{-1} y_i (eliminated at level k),
+//                         y_e -= A_{e,e-s} y_{e-s} + A_{e,e+s} y_{e+s} (survivors);
+//   root:                 y_0 <- A~_0^{-1} y_0;
+//   backward, k = K-1..0: y_i -= G_i y_{i-s} + H_i y_{i+s}.
+// The block rows R32_i = [left | A~_i | right] (n x n blocks, leading
+// dimension n) hold the current couplings, then G_i (left), H_i (right) and
+// the LU factors with their pivots (LUPIV) and reciprocal pivots (UDINV32).
+#include <algorithm>
+
+#include "mlqp_internal.h"
+#include "mlqp_math.cuh"
+#include "mlqp_trsv.cuh"
+
+namespace mlqp {
+
+extern thread_local long g_launches;
+constexpr int CR_THREADS = 256;
+constexpr int CRB = 16;   // LU panel width
+constexpr int CRT = 64;   // trailing-update column tile
+constexpr int MLQP_ESINGULAR_CR = 4;
+
+__device__ __forceinline__ bool cr_angle_done(const Dev& D, int a) {
+  return reinterpret_cast<const unsigned long long*>(D.RNRM + (size_t)a * RNRM_W)[4] != 0ull;
+}
+__device__ __forceinline__ float2* cr_row(const Dev& D, int i, int a) {
+  return D.ROW32 + a * D.r_stride + D.ifc[i].row_off;
+}
+// blocks of row i: left at column 0, diagonal at nl, right at nl + n
+__device__ __forceinline__ float2* cr_left(const Dev& D, int i, int a) { return cr_row(D, i, a); }
+__device__ __forceinline__ float2* cr_diag(const Dev& D, int i, int a) {
+  return cr_row(D, i, a) + (size_t)D.ifc[i].nl * D.ifc[i].n;
+}
+__device__ __forceinline__ float2* cr_right(const Dev& D, int i, int a) {
+  return cr_row(D, i, a) + (size_t)(D.ifc[i].nl + D.ifc[i].n) * D.ifc[i].n;
+}
+__device__ __forceinline__ float2* cr_save(const Dev& D, int slot, int side, int a) {
+  const size_t nn = (size_t)D.maxn * D.maxn;
+  return D.CRSAVE + (size_t)a * D.crsave_stride + ((size_t)slot * 2 + side) * nn;
+}
+
+// ---------------------------------------------------------------------------
+// LU with row pivoting of the diagonal block of interface i = s + 2s x
+// (blockIdx.x; i = 0 for the root), in place, one CTA per (interface, angle):
+// panels of CRB columns factored in shared memory (pivot: largest
+// |re| + |im|, smallest row on ties), their swaps applied to the other
+// columns, U12 by forward substitution, trailing update in CRT-column tiles.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(CR_THREADS) k_cr_lu(Dev D, int s, int root) {
+  const int i = root ? 0 : s + 2 * s * blockIdx.x;
+  const int a = blockIdx.y;
+  if (i >= D.I) return;
+  const IfaceDesc f = D.ifc[i];
+  const int n = f.n, ld = n;
+  float2* A = cr_diag(D, i, a);
+  int* piv = D.LUPIV + a * D.piv_stride + f.eta_off;
+  float2* udinv = D.UDINV32 + a * D.piv_stride + f.eta_off;
+  extern __shared__ __align__(16) unsigned char cr_raw[];
+  float2* pan = reinterpret_cast<float2*>(cr_raw);  // m x CRB, column-major, leading dimension m
+  __shared__ float2 su[CRB][CRT + 1];
+  __shared__ unsigned s_key[CR_THREADS / 32], s_pos[CR_THREADS / 32];
+  __shared__ int s_piv[CRB];
+  __shared__ float2 s_rinv;
+  __shared__ int s_sing;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_sing = 0;
+  for (int k0 = 0; k0 < n; k0 += CRB) {
+    const int w = min(CRB, n - k0), m = n - k0;
+    for (int e = tid; e < m * w; e += CR_THREADS) {
+      const int r = e % m, c = e / m;
+      pan[c * m + r] = A[(size_t)(k0 + c) * ld + k0 + r];
+    }
+    __syncthreads();
+    for (int c = 0; c < w; ++c) {
+      unsigned kb = 0, pb = 0xffffffffu;
+      for (int r = c + tid; r < m; r += CR_THREADS) {
+        const unsigned kk = pivot_key32(ldv<float>(&pan[c * m + r]));
+        if (kk > kb || pb == 0xffffffffu) {
+          kb = kk;
+          pb = (unsigned)r;
+        }
+      }
+      const unsigned km = __reduce_max_sync(0xffffffffu, (pb != 0xffffffffu) ? kb : 0u);
+      const unsigned pm = __reduce_min_sync(0xffffffffu, (pb != 0xffffffffu && kb == km) ? pb : 0xffffffffu);
+      if (lane == 0) {
+        s_key[warp] = km;
+        s_pos[warp] = pm;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        const bool ok = lane < CR_THREADS / 32 && s_pos[lane] != 0xffffffffu;
+        const unsigned k2 = ok ? s_key[lane] : 0u;
+        const unsigned kx = __reduce_max_sync(0xffffffffu, k2);
+        const unsigned px = __reduce_min_sync(0xffffffffu, (ok && k2 == kx) ? s_pos[lane] : 0xffffffffu);
+        const int p = (int)px;
+        if (lane < w && p != c) {
+          const float2 t = pan[lane * m + c];
+          pan[lane * m + c] = pan[lane * m + p];
+          pan[lane * m + p] = t;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          s_piv[c] = k0 + p;
+          const cpx<float> ri = inv_fast_t(ldv<float>(&pan[c * m + c]));
+          s_rinv = make_float2(ri.re, ri.im);
+          if (!pivot_ok32(kx, 0.0f)) s_sing = 1;
+        }
+      }
+      __syncthreads();
+      const cpx<float> ip = ldv<float>(&s_rinv);
+      for (int r = c + 1 + tid; r < m; r += CR_THREADS) {
+        const cpx<float> l = ldv<float>(&pan[c * m + r]) * ip;
+        stv<float>(&pan[c * m + r], l);
+        for (int cc = c + 1; cc < w; ++cc) {
+          float2* x = &pan[cc * m + r];
+          stv<float>(x, cfms(l, ldv<float>(&pan[cc * m + c]), ldv<float>(x)));
+        }
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < m * w; e += CR_THREADS) {
+      const int r = e % m, c = e / m;
+      A[(size_t)(k0 + c) * ld + k0 + r] = pan[c * m + r];
+    }
+    if (tid < w) {
+      piv[k0 + tid] = s_piv[tid];
+      const cpx<float> ri = inv_fast_t(ldv<float>(&pan[tid * m + tid]));
+      udinv[k0 + tid] = make_float2(ri.re, ri.im);
+    }
+    // the panel's swaps on every other column; U12 on the columns to its right
+    for (int j = tid; j < n; j += CR_THREADS) {
+      if (j >= k0 && j < k0 + w) continue;
+      float2* col = A + (size_t)j * ld;
+      for (int t = 0; t < w; ++t) {
+        const int p = s_piv[t];
+        if (p != k0 + t) {
+          const float2 x = col[k0 + t];
+          col[k0 + t] = col[p];
+          col[p] = x;
+        }
+      }
+      if (j >= k0 + w) {
+        cpx<float> x[CRB];
+#pragma unroll
+        for (int t = 0; t < CRB; ++t) x[t] = (t < w) ? ldv<float>(&col[k0 + t]) : mkc<float>(0.f);
+#pragma unroll
+        for (int t = 1; t < CRB; ++t)
+#pragma unroll
+          for (int q = 0; q < t; ++q)
+            if (t < w) x[t] = cfms(ldv<float>(&pan[q * m + t]), x[q], x[t]);
+#pragma unroll
+        for (int t = 0; t < CRB; ++t)
+          if (t < w) stv<float>(&col[k0 + t], x[t]);
+      }
+    }
+    __syncthreads();
+    // trailing update A22 -= L21 U12 (rows and columns k0 + w .. n-1)
+    const int tr = n - k0 - w;
+    const int tx = tid % 64, ty = tid / 64;  // 64 rows x 4 groups of CRT/4 columns
+    for (int j0 = 0; j0 < tr; j0 += CRT) {
+      for (int e = tid; e < CRB * CRT; e += CR_THREADS) {  // rows t >= w zero-filled
+        const int t = e / CRT, jj = e % CRT;
+        su[t][jj] = (t < w && j0 + jj < tr) ? A[(size_t)(k0 + w + j0 + jj) * ld + k0 + t] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      for (int r0 = 0; r0 < tr; r0 += 64) {
+        const int r = r0 + tx;
+        if (r < tr) {
+          cpx<float> l[CRB];
+#pragma unroll
+          for (int t = 0; t < CRB; ++t) l[t] = (t < w) ? ldv<float>(&pan[t * m + w + r]) : mkc<float>(0.f);
+          for (int jj = ty * (CRT / 4); jj < (ty + 1) * (CRT / 4) && j0 + jj < tr; ++jj) {
+            float2* x = &A[(size_t)(k0 + w + j0 + jj) * ld + k0 + w + r];
+            cpx<float> acc = ldv<float>(x);
+#pragma unroll
+            for (int t = 0; t < CRB; ++t) acc = cfms(l[t], ldv<float>(&su[t][jj]), acc);
+            stv<float>(x, acc);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0 && s_sing) atomicExch(D.STATUS, MLQP_ESINGULAR_CR);
+}
+
+// Composed row permutation of the LU of interface i (PERMV[j] = source row of
+// row j after the sequential swaps j <-> piv[j]), one thread per (i, angle).
+__global__ void k_cr_perm(Dev D, int s, int root, int n_int, int* permv) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (q >= n_int) return;
+  const int i = root ? 0 : s + 2 * s * q;
+  if (i >= D.I) return;
+  const IfaceDesc f = D.ifc[i];
+  const int* piv = D.LUPIV + a * D.piv_stride + f.eta_off;
+  int* pv = permv + a * D.piv_stride + f.eta_off;
+  for (int j = 0; j < f.n; ++j) pv[j] = j;
+  for (int j = 0; j < f.n; ++j) {
+    const int p = piv[j];
+    const int t = pv[j];
+    pv[j] = pv[p];
+    pv[p] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// G_i, H_i: A~_i^{-1} applied to the couplings of row i, in place, by chunks
+// of CW columns (blockIdx.x over the chunks of [left | right], blockIdx.y over
+// the eliminated interfaces).  The chunk sits in shared memory with its rows
+// permuted; forward substitution with L, then backward with U, both by
+// 32-row blocks: one warp per column solves the diagonal block, every thread
+// then updates the rows beyond it for all the chunk's columns.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(CR_THREADS) k_cr_trsm(Dev D, int s, int cw, const int* permv) {
+  const int i = s + 2 * s * blockIdx.y;
+  const int a = blockIdx.z;
+  if (i >= D.I) return;
+  const IfaceDesc f = D.ifc[i];
+  const int n = f.n, ld = n;
+  const bool has_right = i + s < D.I;
+  const int ncols = has_right ? 2 * n : n;
+  const int c0 = blockIdx.x * cw;
+  if (c0 >= ncols) return;
+  const int cwn = min(cw, ncols - c0);
+  const float2* LU = cr_diag(D, i, a);
+  const float2* ud = D.UDINV32 + a * D.piv_stride + f.eta_off;
+  const int* pv = permv + a * D.piv_stride + f.eta_off;
+  extern __shared__ __align__(16) unsigned char cr_raw[];
+  float2* X = reinterpret_cast<float2*>(cr_raw);  // n x cw, row-major in the chunk: X[r * cw + c]
+  auto colptr = [&](int c) -> float2* {
+    const int g = c0 + c;
+    return (g < n) ? cr_left(D, i, a) + (size_t)g * ld : cr_right(D, i, a) + (size_t)(g - n) * ld;
+  };
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < n * cwn; e += CR_THREADS) {
+    const int r = e % n, c = e / n;
+    X[r * cw + c] = colptr(c)[pv[r]];
+  }
+  __syncthreads();
+  const int nblk = (n + 31) / 32;
+  // forward: unit lower L
+  for (int b = 0; b < nblk; ++b) {
+    const int i0 = 32 * b, wb = min(32, n - i0);
+    for (int c = warp; c < cwn; c += CR_THREADS / 32) {
+      cpx<float> v = (lane < wb) ? ldv<float>(&X[(i0 + lane) * cw + c]) : mkc<float>(0.f);
+      for (int j = 0; j + 1 < wb; ++j) {
+        const float xr = __shfl_sync(0xffffffffu, v.re, j), xi = __shfl_sync(0xffffffffu, v.im, j);
+        if (lane > j && lane < wb) v = cfms(ldv<float>(&LU[(size_t)(i0 + j) * ld + i0 + lane]), mkc<float>(xr, xi), v);
+      }
+      if (lane < wb) stv<float>(&X[(i0 + lane) * cw + c], v);
+    }
+    __syncthreads();
+    for (int r = i0 + wb + tid; r < n; r += CR_THREADS) {
+      float2 lv[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) lv[q] = (q < wb) ? LU[(size_t)(i0 + q) * ld + r] : make_float2(0.f, 0.f);
+      for (int c = 0; c < cwn; ++c) {
+        cpx<float> acc = ldv<float>(&X[r * cw + c]);
+#pragma unroll
+        for (int q = 0; q < 32; ++q)  // rows i0 + q >= n lie outside the chunk: never read them
+          if (q < wb) acc = cfms(mkc<float>(lv[q].x, lv[q].y), ldv<float>(&X[(i0 + q) * cw + c]), acc);
+        stv<float>(&X[r * cw + c], acc);
+      }
+    }
+    __syncthreads();
+  }
+  // backward: upper U (pivot reciprocals in ud)
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int i0 = 32 * b, wb = min(32, n - i0);
+    for (int c = warp; c < cwn; c += CR_THREADS / 32) {
+      cpx<float> v = (lane < wb) ? ldv<float>(&X[(i0 + lane) * cw + c]) : mkc<float>(0.f);
+      for (int j = wb - 1; j >= 0; --j) {
+        if (lane == j) v = v * ldv<float>(&ud[i0 + j]);
+        const float xr = __shfl_sync(0xffffffffu, v.re, j), xi = __shfl_sync(0xffffffffu, v.im, j);
+        if (lane < j) v = cfms(ldv<float>(&LU[(size_t)(i0 + j) * ld + i0 + lane]), mkc<float>(xr, xi), v);
+      }
+      if (lane < wb) stv<float>(&X[(i0 + lane) * cw + c], v);
+    }
+    __syncthreads();
+    for (int r = tid; r < i0; r += CR_THREADS) {
+      float2 uv[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) uv[q] = (q < wb) ? LU[(size_t)(i0 + q) * ld + r] : make_float2(0.f, 0.f);
+      for (int c = 0; c < cwn; ++c) {
+        cpx<float> acc = ldv<float>(&X[r * cw + c]);
+#pragma unroll
+        for (int q = 0; q < 32; ++q)  // rows i0 + q >= n lie outside the chunk: never read them
+          if (q < wb) acc = cfms(mkc<float>(uv[q].x, uv[q].y), ldv<float>(&X[(i0 + q) * cw + c]), acc);
+        stv<float>(&X[r * cw + c], acc);
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < n * cwn; e += CR_THREADS) {
+    const int r = e % n, c = e / n;
+    colptr(c)[r] = X[r * cw + c];
+  }
+}
+
+// Save the couplings A_{e,e-s}, A_{e,e+s} of the survivors e = 2s q.
+__global__ void k_cr_save(Dev D, int s, int slot_base) {
+  const int e = 2 * s * blockIdx.y, a = blockIdx.z;
+  if (e >= D.I) return;
+  const int n = D.ifc[e].n;
+  const size_t nn = (size_t)n * n;
+  const int slot = slot_base + blockIdx.y;
+  const bool hl = e - s >= 0, hr = e + s < D.I;
+  const float2* L = hl ? cr_left(D, e, a) : nullptr;
+  const float2* Rr = hr ? cr_right(D, e, a) : nullptr;
+  float2* SL = cr_save(D, slot, 0, a);
+  float2* SR = cr_save(D, slot, 1, a);
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < nn; x += (size_t)gridDim.x * blockDim.x) {
+    if (hl) SL[x] = L[x];
+    if (hr) SR[x] = Rr[x];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Survivor updates, 64 x 64 output tiles with FP32 accumulation (the complex
+// products as three real ones): blockIdx.y = 3 x (survivor index) + block
+// (0: diagonal -= SL H_{e-s} + SR G_{e+s}; 1: left = -SL G_{e-s};
+// 2: right = -SR H_{e+s}), SL/SR the saved couplings.
+// ---------------------------------------------------------------------------
+constexpr int UT32 = 64, UK32 = 16;
+
+__global__ void __launch_bounds__(256) k_cr_update(Dev D, int s, int slot_base) {
+  const int q = blockIdx.y / 3, kind = blockIdx.y % 3;
+  const int e = 2 * s * q, a = blockIdx.z;
+  if (e >= D.I) return;
+  const int n = D.ifc[e].n;
+  const bool hl = e - s >= 0, hr = e + s < D.I;
+  if (kind == 1 && !hl) return;
+  if (kind == 2 && !(hr && e + 2 * s < D.I)) return;
+  if (kind == 0 && !hl && !hr) return;
+  const int tiles = (n + UT32 - 1) / UT32;
+  const int row0 = (blockIdx.x / tiles) * UT32, col0 = (blockIdx.x % tiles) * UT32;
+  if (row0 >= n) return;
+  const int slot = slot_base + q;
+  const float2* T1A = nullptr;
+  const float2* T1B = nullptr;
+  const float2* T2A = nullptr;
+  const float2* T2B = nullptr;
+  float2* C;
+  if (kind == 0) {
+    C = cr_diag(D, e, a);
+    if (hl) { T1A = cr_save(D, slot, 0, a); T1B = cr_right(D, e - s, a); }
+    if (hr) { T2A = cr_save(D, slot, 1, a); T2B = cr_left(D, e + s, a); }
+  } else if (kind == 1) {
+    C = cr_left(D, e, a);
+    T1A = cr_save(D, slot, 0, a);
+    T1B = cr_left(D, e - s, a);
+  } else {
+    C = cr_right(D, e, a);
+    T1A = cr_save(D, slot, 1, a);
+    T1B = cr_right(D, e + s, a);
+  }
+  __shared__ float As[UK32][3][UT32];
+  __shared__ float Bs[UK32][3][UT32];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // 4 x 4 outputs per thread
+  float t1[4][4] = {}, t2[4][4] = {}, t3[4][4] = {};
+  for (int term = 0; term < 2; ++term) {
+    const float2* Am = term ? T2A : T1A;
+    const float2* Bm = term ? T2B : T1B;
+    if (!Am) continue;
+    for (int k0 = 0; k0 < n; k0 += UK32) {
+      for (int x = tid; x < UT32 * UK32; x += 256) {
+        const int r = x % UT32, kk = x / UT32;
+        float2 v = make_float2(0.f, 0.f);
+        if (row0 + r < n && k0 + kk < n) v = Am[(size_t)(k0 + kk) * n + row0 + r];
+        As[kk][0][r] = v.x;
+        As[kk][1][r] = v.y;
+        As[kk][2][r] = v.x + v.y;
+      }
+      for (int x = tid; x < UT32 * UK32; x += 256) {
+        const int kk = x % UK32, c = x / UK32;
+        float2 v = make_float2(0.f, 0.f);
+        if (col0 + c < n && k0 + kk < n) v = Bm[(size_t)(col0 + c) * n + k0 + kk];
+        Bs[kk][0][c] = v.x;
+        Bs[kk][1][c] = v.y;
+        Bs[kk][2][c] = v.x + v.y;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < UK32; ++kk) {
+        float ar[4], ai[4], as[4], br[4], bi[4], bs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ar[u] = As[kk][0][ty * 4 + u];
+          ai[u] = As[kk][1][ty * 4 + u];
+          as[u] = As[kk][2][ty * 4 + u];
+          br[u] = Bs[kk][0][tx * 4 + u];
+          bi[u] = Bs[kk][1][tx * 4 + u];
+          bs[u] = Bs[kk][2][tx * 4 + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            t1[u][v] = fmaf(ar[u], br[v], t1[u][v]);
+            t2[u][v] = fmaf(ai[u], bi[v], t2[u][v]);
+            t3[u][v] = fmaf(as[u], bs[v], t3[u][v]);
+          }
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int r = row0 + ty * 4 + u, c = col0 + tx * 4 + v;
+      if (r < n && c < n) {
+        const float pr = t1[u][v] - t2[u][v], pi = t3[u][v] - t1[u][v] - t2[u][v];
+        float2* p = &C[(size_t)c * n + r];
+        if (kind == 0) {
+          const float2 x = *p;
+          *p = make_float2(x.x - pr, x.y - pi);
+        } else {
+          *p = make_float2(-pr, -pi);
+        }
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Solve kernels (per refinement step, on the FP32 vector Y32)
+// ---------------------------------------------------------------------------
+__global__ void k_cr_res32(Dev D, long n_den) {
+  const int a = blockIdx.y;
+  if (cr_angle_done(D, a)) return;
+  for (long r = (long)blockIdx.x * blockDim.x + threadIdx.x; r < n_den; r += (long)gridDim.x * blockDim.x) {
+    const double2 x = D.RES[a * D.eta_stride + r];
+    D.Y32[a * D.eta_stride + r] = make_float2((float)x.x, (float)x.y);
+  }
+}
+
+// y_i <- A~_i^{-1} y_i for the interfaces eliminated at level s (or the root)
+__global__ void __launch_bounds__(TRSV_THREADS) k_cr_tri(Dev D, int s, int root, const int* permv) {
+  const int i = root ? 0 : s + 2 * s * blockIdx.x;
+  const int a = blockIdx.y;
+  if (i >= D.I || cr_angle_done(D, a)) return;
+  const IfaceDesc f = D.ifc[i];
+  extern __shared__ __align__(16) unsigned char trsv_raw[];
+  float2* ys = reinterpret_cast<float2*>(trsv_raw);
+  float2* y = D.Y32 + a * D.eta_stride + f.eta_off;
+  const float2* LU = cr_diag(D, i, a);
+  unit_lower_solve<float>(LU, f.n, y, ys, permv + a * D.piv_stride + f.eta_off);
+  __syncthreads();
+  upper_solve<float>(LU, f.n, D.UDINV32 + a * D.piv_stride + f.eta_off, y, ys);
+}
+
+// y_t -= M1 y_{t-s} + M2 y_{t+s}: mode 0 the survivors t = 2s q with the saved
+// couplings (forward), mode 1 the eliminated t = s + 2s q with G_t, H_t
+// (backward).  32 rows per CTA, warp w sums columns w, w+8, ...
+__global__ void __launch_bounds__(256) k_cr_mv(Dev D, int s, int mode, int slot_base) {
+  const int q = blockIdx.y, a = blockIdx.z;
+  const int t = (mode == 0) ? 2 * s * q : s + 2 * s * q;
+  if (t >= D.I || cr_angle_done(D, a)) return;
+  const IfaceDesc f = D.ifc[t];
+  const int n = f.n;
+  const bool hl = t - s >= 0, hr = t + s < D.I;
+  const float2* M1 = nullptr;
+  const float2* M2 = nullptr;
+  if (mode == 0) {
+    if (hl) M1 = cr_save(D, slot_base + q, 0, a);
+    if (hr) M2 = cr_save(D, slot_base + q, 1, a);
+  } else {
+    M1 = cr_left(D, t, a);
+    if (hr) M2 = cr_right(D, t, a);
+  }
+  const float2* y1 = hl ? D.Y32 + a * D.eta_stride + D.ifc[t - s].eta_off : nullptr;
+  const float2* y2 = hr ? D.Y32 + a * D.eta_stride + D.ifc[t + s].eta_off : nullptr;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + lane;
+  float sr = 0.f, si = 0.f;
+  if (r < n) {
+    for (int term = 0; term < 2; ++term) {
+      const float2* M = term ? M2 : M1;
+      const float2* x = term ? y2 : y1;
+      if (!M) continue;
+      for (int c = warp; c < n; c += 8) {
+        const float2 u = M[(size_t)c * n + r], xv = x[c];
+        sr = fmaf(u.x, xv.x, fmaf(-u.y, xv.y, sr));
+        si = fmaf(u.x, xv.y, fmaf(u.y, xv.x, si));
+      }
+    }
+  }
+  __shared__ float2 part[8][32];
+  part[warp][lane] = make_float2(sr, si);
+  __syncthreads();
+  if (warp == 0 && r < n) {
+    float tr = 0.f, ti = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      tr += part[w][lane].x;
+      ti += part[w][lane].y;
+    }
+    float2* y = D.Y32 + a * D.eta_stride + f.eta_off;
+    const float2 v = y[r];
+    y[r] = make_float2(v.x - tr, v.y - ti);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+static int cr_count(int start, int step, int I) { return (start < I) ? (I - 1 - start) / step + 1 : 0; }
+
+static int cr_chunk(int n) { return (n <= 512) ? 32 : 16; }
+
+cudaError_t cr_configure(int maxn) {
+  const int pan = maxn * CRB * (int)sizeof(float2);
+  const int tr = maxn * cr_chunk(maxn) * (int)sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_cr_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, pan);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cr_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, tr);
+  return e;
+}
+
+// Number of saved-coupling slots the factorisation of I interfaces uses.
+int cr_slots(int I) {
+  int slots = 0;
+  for (int s = 1; s < I; s *= 2) slots += cr_count(0, 2 * s, I);
+  return slots;
+}
+
+cudaError_t launch_cr_factor(const Dev& D, int n, int* permv, cudaStream_t st) {
+  const int I = D.I, nt = D.n_theta;
+  const size_t pan = (size_t)n * CRB * sizeof(float2);
+  const int cw = cr_chunk(n);
+  const size_t trs = (size_t)n * cw * sizeof(float2);
+  int slot_base = 0;
+  for (int s = 1; s < I; s *= 2) {
+    const int nE = cr_count(s, 2 * s, I), nS = cr_count(0, 2 * s, I);
+    g_launches += 5;
+    k_cr_lu<<<dim3(nE, nt), CR_THREADS, pan, st>>>(D, s, 0);
+    k_cr_perm<<<dim3((nE + 63) / 64, nt), 64, 0, st>>>(D, s, 0, nE, permv);
+    k_cr_trsm<<<dim3((2 * n + cw - 1) / cw, nE, nt), CR_THREADS, trs, st>>>(D, s, cw, permv);
+    k_cr_save<<<dim3(std::max(1, (n * n + 255) / 256 / 4), nS, nt), 256, 0, st>>>(D, s, slot_base);
+    const int tiles = ((n + UT32 - 1) / UT32) * ((n + UT32 - 1) / UT32);
+    k_cr_update<<<dim3(tiles, 3 * nS, nt), 256, 0, st>>>(D, s, slot_base);
+    slot_base += nS;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  g_launches += 2;
+  k_cr_lu<<<dim3(1, nt), CR_THREADS, pan, st>>>(D, 0, 1);
+  k_cr_perm<<<dim3(1, nt), 64, 0, st>>>(D, 0, 1, 1, permv);
+  return cudaGetLastError();
+}
+
+// y = A'^{-1} r on Y32 (r converted from the FP64 residual RES).
+cudaError_t launch_cr_solve(const Dev& D, int n, long n_den, const int* permv, cudaStream_t st) {
+  const int I = D.I, nt = D.n_theta;
+  const size_t ys = (size_t)n * sizeof(float2);
+  ++g_launches;
+  k_cr_res32<<<dim3(std::max(1L, std::min(1024L, (n_den + 255) / 256)), nt), 256, 0, st>>>(D, n_den);
+  int slot_base = 0;
+  for (int s = 1; s < I; s *= 2) {
+    const int nE = cr_count(s, 2 * s, I), nS = cr_count(0, 2 * s, I);
+    g_launches += 2;
+    k_cr_tri<<<dim3(nE, nt), TRSV_THREADS, ys, st>>>(D, s, 0, permv);
+    k_cr_mv<<<dim3((n + 31) / 32, nS, nt), 256, 0, st>>>(D, s, 0, slot_base);
+    slot_base += nS;
+  }
+  ++g_launches;
+  k_cr_tri<<<dim3(1, nt), TRSV_THREADS, ys, st>>>(D, 0, 1, permv);
+  int s = 1;
+  while (2 * s < I) s *= 2;  // the last level
+  for (; s >= 1; s /= 2) {
+    const int nE = cr_count(s, 2 * s, I);
+    if (nE == 0) continue;
+    ++g_launches;
+    k_cr_mv<<<dim3((n + 31) / 32, nE, nt), 256, 0, st>>>(D, s, 1, 0);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mlqp

@@ -125,6 +125,7 @@ struct Dev {
   double2* ZX;   // per angle, sum_j P entries: X_j[:P] eta
   double* ZXA;   // per angle, like ZX: |X_j[:P]| |eta| (|re| + |im|), the rounding scale of ZX
   float2* Y32;   // per angle, indexed like eta: forward / backward solve vector
+  float2* CRSAVE; size_t crsave_stride;  // cyclic reduction: couplings saved per level (2 n x n per slot)
   double* RNRM;  // per angle RNRM_W slots: backward error, corrections applied,
                  // max |r| and max scale (bit patterns, atomic max), done flag
   double2* ETA; size_t eta_stride;

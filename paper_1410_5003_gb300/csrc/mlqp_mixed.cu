@@ -347,14 +347,24 @@ cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s) {
 // Factorise A'_32 and refine eta in FP64: up to max_refine corrections,
 // each preceded by a residual and its backward error; a final residual
 // checks the last one.
+cudaError_t launch_cr_factor(const Dev& D, int n, int* permv, cudaStream_t st);
+cudaError_t launch_cr_solve(const Dev& D, int n, long n_den, const int* permv, cudaStream_t st);
+
 cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n_den, int max_refine, double tol,
-                               int* permv, const AngleStreams& A) {
+                               int* permv, const AngleStreams& A, bool cyclic) {
   cudaStream_t s = A.main;
   cudaError_t e = cudaMemsetAsync(D.F32, 0, sizeof(float2) * D.f_stride * D.n_theta, s);
-  if (e == cudaSuccess) e = launch_factor32(D, n_host, A);
   if (e != cudaSuccess) return e;
-  ++g_launches;
-  k_compose_perm<<<dim3((D.I + 63) / 64, D.n_theta), 64, 0, s>>>(D, permv);
+  if (cyclic) {
+    e = launch_cr_factor(D, n_host[0], permv, s);
+  } else {
+    e = launch_factor32(D, n_host, A);
+    if (e == cudaSuccess) {
+      ++g_launches;
+      k_compose_perm<<<dim3((D.I + 63) / 64, D.n_theta), 64, 0, s>>>(D, permv);
+    }
+  }
+  if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(D.ETA, 0, sizeof(double2) * D.eta_stride * D.n_theta, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(D.RNRM, 0, sizeof(double) * RNRM_W * D.n_theta, s);
   if (e != cudaSuccess) return e;
@@ -367,18 +377,22 @@ cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n
     ++g_launches;
     k_refine_ctl<<<1, 32, 0, s>>>(D, last, tol);
     if (last) break;
-    for (int t = 0; t < D.I; ++t) {
-      g_launches += 2;
-      k_mv32<<<dim3((n_host[t] + 31) / 32, D.n_theta), 256, 0, s>>>(D, t, 0, permv);
-      k_lower32<<<D.n_theta, TRSV_THREADS, sizeof(float2) * n_host[t], s>>>(D, t);
-    }
-    for (int t = D.I - 1; t >= 0; --t) {
-      if (t + 1 < D.I) {
-        ++g_launches;
-        k_mv32<<<dim3((n_host[t] + 31) / 32, D.n_theta), 256, 0, s>>>(D, t, 1, permv);
+    if (cyclic) {
+      if ((e = launch_cr_solve(D, n_host[0], n_den, permv, s)) != cudaSuccess) return e;
+    } else {
+      for (int t = 0; t < D.I; ++t) {
+        g_launches += 2;
+        k_mv32<<<dim3((n_host[t] + 31) / 32, D.n_theta), 256, 0, s>>>(D, t, 0, permv);
+        k_lower32<<<D.n_theta, TRSV_THREADS, sizeof(float2) * n_host[t], s>>>(D, t);
       }
-      ++g_launches;
-      k_upper32<<<D.n_theta, TRSV_THREADS, sizeof(float2) * n_host[t], s>>>(D, t);
+      for (int t = D.I - 1; t >= 0; --t) {
+        if (t + 1 < D.I) {
+          ++g_launches;
+          k_mv32<<<dim3((n_host[t] + 31) / 32, D.n_theta), 256, 0, s>>>(D, t, 1, permv);
+        }
+        ++g_launches;
+        k_upper32<<<D.n_theta, TRSV_THREADS, sizeof(float2) * n_host[t], s>>>(D, t);
+      }
     }
     ++g_launches;
     k_eta_update<<<D.n_theta, 256, 0, s>>>(D, (int)n_den);

@@ -99,13 +99,15 @@ __device__ void upper_solve(const vec2<R>* U, int n, const vec2<R>* udinv, vec2<
 }
 
 // L y = b in place, L the unit lower triangle of the n x n column-major block
-// at L (leading dimension n).
+// at L (leading dimension n).  With perm, the right-hand side is b_r = y[perm[r]]
+// (a row permutation applied on the way in).
 template <typename R>
-__device__ void unit_lower_solve(const vec2<R>* L, int n, vec2<R>* y, vec2<R>* ys) {
+__device__ void unit_lower_solve(const vec2<R>* L, int n, vec2<R>* y, vec2<R>* ys, const int* perm = nullptr) {
   __shared__ vec2<R> blk[32][33];
   __shared__ vec2<R> xb[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int r = tid; r < n; r += TRSV_THREADS) ys[r] = y[r];
+  for (int r = tid; r < n; r += TRSV_THREADS) ys[r] = y[perm ? perm[r] : r];
+  __syncthreads();  // every read of y completes before any write-back
   const int nblk = (n + 31) / 32;
   DiagPrefetch<R> dp;
   dp.load(L, n, 0, min(32, n), nullptr);

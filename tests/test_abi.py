@@ -126,3 +126,25 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in txt.replace("oracle_", ""), f
+
+
+def test_cyclic_solver_validation(M):
+    """MLQP_CYCLIC belongs to the mixed form and needs equal node counts."""
+    lib = M.load()
+    from workloads import small_stack
+    import ctypes as ct
+    def st(prob, precision, solver):
+        try:
+            ctx, _ = M.mlqp_setup(prob, precision, 5 if precision == M.MLQP_MIXED else 0,
+                                  1e-15 if precision == M.MLQP_MIXED else 0.0, solver)
+        except M.MlqpError as e:
+            return e.status
+        lib.mlqp_destroy(ctx)
+        return M.MLQP_OK
+    even = small_stack(I=3)
+    assert st(even, M.MLQP_MIXED, M.MLQP_CYCLIC) == M.MLQP_OK
+    assert st(even, M.MLQP_FP64, M.MLQP_CYCLIC) == M.MLQP_EINVAL
+    ragged = small_stack(I=3)
+    ragged.ifaces[1].N = 72
+    assert st(ragged, M.MLQP_MIXED, M.MLQP_CYCLIC) == M.MLQP_EINVAL
+    assert st(ragged, M.MLQP_MIXED, M.MLQP_SWEEP) == M.MLQP_OK

@@ -358,3 +358,37 @@ def test_mixed_precision_reports_unreached_tolerance(M):
     for a in range(prob.n_theta):
         assert rel(np.concatenate([out["aU"][a], out["aD"][a]]), np.concatenate([ref["aU"][a], ref["aD"][a]])) < 1e-12
     ok.close()
+
+
+@pytest.mark.parametrize("name", ["config1", "small3", "corner2", "five"])
+def test_cyclic_reduction_matches_oracle(M, name):
+    """Mixed form with the block cyclic-reduction solver: FP32 LU, G/H
+    triangular solves and Schur updates level by level, refined in FP64.
+    Amplitudes agree with the oracle to 1e-9 and with the sweep to 1e-12.
+    `five` (I = 5) has levels that eliminate 2, 1 and 1 interfaces."""
+    prob = small_stack(I=5, N=64, P=50, Mw=30, K=20, M=45) if name == "five" else PROBLEMS[name]()
+    cr = M.Context(prob, precision=M.MLQP_MIXED, block_solver=M.MLQP_CYCLIC)
+    out = cr.solve_host()
+    steps = [cr.block(M.BLK_REFINE, 1, a).cpu().numpy()[1] for a in range(prob.n_theta)]
+    cr.close()
+    sw = M.Context(prob, precision=M.MLQP_MIXED)
+    ref = sw.solve_host()
+    sw.close()
+    asm = O.Assembler(prob)
+    for a in range(prob.n_theta):
+        ag = np.concatenate([out["aU"][a], out["aD"][a]])
+        assert rel(ag, np.concatenate([ref["aU"][a], ref["aD"][a]])) < 1e-12
+        r = O.solve(prob, a, asm)
+        assert rel(ag, np.concatenate([r["aU"], r["aD"]])) < AMP_TOL, (name, a)
+    assert max(steps) <= 8, steps
+
+
+def test_cyclic_reduction_on_benchmark_stack(M):
+    prob = config2()
+    cr = M.Context(prob, precision=M.MLQP_MIXED, block_solver=M.MLQP_CYCLIC)
+    out = cr.solve_host()
+    cr.close()
+    asm = O.Assembler(prob)
+    for a in range(prob.n_theta):
+        r = O.solve(prob, a, asm)
+        assert rel(np.concatenate([out["aU"][a], out["aD"][a]]), np.concatenate([r["aU"], r["aD"]])) < AMP_TOL
