@@ -219,8 +219,8 @@ __global__ void k_cr_perm(Dev D, int s, int root, int n_int, int* permv) {
 // ---------------------------------------------------------------------------
 // G_i, H_i: A~_i^{-1} applied to the couplings of row i, in place, by chunks
 // of CW columns (blockIdx.x over the chunks of [left | right], blockIdx.y over
-// the eliminated interfaces).  The chunk sits in shared memory with its rows
-// permuted; forward substitution with L, then backward with U, both by
+// the eliminated interfaces).  The chunk sits in shared memory, column-major
+// (so row-parallel updates are free of bank conflicts), with its rows permuted; forward substitution with L, then backward with U, both by
 // 32-row blocks: one warp per column solves the diagonal block, every thread
 // then updates the rows beyond it for all the chunk's columns.
 // ---------------------------------------------------------------------------
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_trsm(Dev D, int s, int cw, co
   const float2* ud = D.UDINV32 + a * D.piv_stride + f.eta_off;
   const int* pv = permv + a * D.piv_stride + f.eta_off;
   extern __shared__ __align__(16) unsigned char cr_raw[];
-  float2* X = reinterpret_cast<float2*>(cr_raw);  // n x cw, row-major in the chunk: X[r * cw + c]
+  float2* X = reinterpret_cast<float2*>(cr_raw);  // n x cw chunk, column-major: X[c * n + r]
   auto colptr = [&](int c) -> float2* {
     const int g = c0 + c;
     return (g < n) ? cr_left(D, i, a) + (size_t)g * ld : cr_right(D, i, a) + (size_t)(g - n) * ld;
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_trsm(Dev D, int s, int cw, co
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < n * cwn; e += CR_THREADS) {
     const int r = e % n, c = e / n;
-    X[r * cw + c] = colptr(c)[pv[r]];
+    X[c * n + r] = colptr(c)[pv[r]];
   }
   __syncthreads();
   const int nblk = (n + 31) / 32;
@@ -255,12 +255,12 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_trsm(Dev D, int s, int cw, co
   for (int b = 0; b < nblk; ++b) {
     const int i0 = 32 * b, wb = min(32, n - i0);
     for (int c = warp; c < cwn; c += CR_THREADS / 32) {
-      cpx<float> v = (lane < wb) ? ldv<float>(&X[(i0 + lane) * cw + c]) : mkc<float>(0.f);
+      cpx<float> v = (lane < wb) ? ldv<float>(&X[c * n + i0 + lane]) : mkc<float>(0.f);
       for (int j = 0; j + 1 < wb; ++j) {
         const float xr = __shfl_sync(0xffffffffu, v.re, j), xi = __shfl_sync(0xffffffffu, v.im, j);
         if (lane > j && lane < wb) v = cfms(ldv<float>(&LU[(size_t)(i0 + j) * ld + i0 + lane]), mkc<float>(xr, xi), v);
       }
-      if (lane < wb) stv<float>(&X[(i0 + lane) * cw + c], v);
+      if (lane < wb) stv<float>(&X[c * n + i0 + lane], v);
     }
     __syncthreads();
     for (int r = i0 + wb + tid; r < n; r += CR_THREADS) {
@@ -268,11 +268,11 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_trsm(Dev D, int s, int cw, co
 #pragma unroll
       for (int q = 0; q < 32; ++q) lv[q] = (q < wb) ? LU[(size_t)(i0 + q) * ld + r] : make_float2(0.f, 0.f);
       for (int c = 0; c < cwn; ++c) {
-        cpx<float> acc = ldv<float>(&X[r * cw + c]);
+        cpx<float> acc = ldv<float>(&X[c * n + r]);
 #pragma unroll
         for (int q = 0; q < 32; ++q)  // rows i0 + q >= n lie outside the chunk: never read them
-          if (q < wb) acc = cfms(mkc<float>(lv[q].x, lv[q].y), ldv<float>(&X[(i0 + q) * cw + c]), acc);
-        stv<float>(&X[r * cw + c], acc);
+          if (q < wb) acc = cfms(mkc<float>(lv[q].x, lv[q].y), ldv<float>(&X[c * n + i0 + q]), acc);
+        stv<float>(&X[c * n + r], acc);
       }
     }
     __syncthreads();
@@ -281,13 +281,13 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_trsm(Dev D, int s, int cw, co
   for (int b = nblk - 1; b >= 0; --b) {
     const int i0 = 32 * b, wb = min(32, n - i0);
     for (int c = warp; c < cwn; c += CR_THREADS / 32) {
-      cpx<float> v = (lane < wb) ? ldv<float>(&X[(i0 + lane) * cw + c]) : mkc<float>(0.f);
+      cpx<float> v = (lane < wb) ? ldv<float>(&X[c * n + i0 + lane]) : mkc<float>(0.f);
       for (int j = wb - 1; j >= 0; --j) {
         if (lane == j) v = v * ldv<float>(&ud[i0 + j]);
         const float xr = __shfl_sync(0xffffffffu, v.re, j), xi = __shfl_sync(0xffffffffu, v.im, j);
         if (lane < j) v = cfms(ldv<float>(&LU[(size_t)(i0 + j) * ld + i0 + lane]), mkc<float>(xr, xi), v);
       }
-      if (lane < wb) stv<float>(&X[(i0 + lane) * cw + c], v);
+      if (lane < wb) stv<float>(&X[c * n + i0 + lane], v);
     }
     __syncthreads();
     for (int r = tid; r < i0; r += CR_THREADS) {
@@ -295,18 +295,18 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_trsm(Dev D, int s, int cw, co
 #pragma unroll
       for (int q = 0; q < 32; ++q) uv[q] = (q < wb) ? LU[(size_t)(i0 + q) * ld + r] : make_float2(0.f, 0.f);
       for (int c = 0; c < cwn; ++c) {
-        cpx<float> acc = ldv<float>(&X[r * cw + c]);
+        cpx<float> acc = ldv<float>(&X[c * n + r]);
 #pragma unroll
         for (int q = 0; q < 32; ++q)  // rows i0 + q >= n lie outside the chunk: never read them
-          if (q < wb) acc = cfms(mkc<float>(uv[q].x, uv[q].y), ldv<float>(&X[(i0 + q) * cw + c]), acc);
-        stv<float>(&X[r * cw + c], acc);
+          if (q < wb) acc = cfms(mkc<float>(uv[q].x, uv[q].y), ldv<float>(&X[c * n + i0 + q]), acc);
+        stv<float>(&X[c * n + r], acc);
       }
     }
     __syncthreads();
   }
   for (int e = tid; e < n * cwn; e += CR_THREADS) {
     const int r = e % n, c = e / n;
-    colptr(c)[r] = X[r * cw + c];
+    colptr(c)[r] = X[c * n + r];
   }
 }
 

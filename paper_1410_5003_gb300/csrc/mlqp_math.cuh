@@ -178,6 +178,13 @@ constexpr double EULER_GAMMA = 0.57721566490153286061;
 constexpr double SQRT_HALF = 0.70710678118654752440;
 constexpr double INV_4PI = 0.07957747154594766788;
 
+// Small integers k and their reciprocals 1/k (k < 64) as doubles: in the
+// recurrences below, sgn * RK[k] equals the correctly rounded sgn / k and
+// DK[n] * t equals n * t, without an FP64 division or an int-to-double
+// conversion (each a multi-cycle FP64-pipe operation) per step.
+static __device__ const double DK[64] = {0.0, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0, 8.0, 9.0, 10.0, 11.0, 12.0, 13.0, 14.0, 15.0, 16.0, 17.0, 18.0, 19.0, 20.0, 21.0, 22.0, 23.0, 24.0, 25.0, 26.0, 27.0, 28.0, 29.0, 30.0, 31.0, 32.0, 33.0, 34.0, 35.0, 36.0, 37.0, 38.0, 39.0, 40.0, 41.0, 42.0, 43.0, 44.0, 45.0, 46.0, 47.0, 48.0, 49.0, 50.0, 51.0, 52.0, 53.0, 54.0, 55.0, 56.0, 57.0, 58.0, 59.0, 60.0, 61.0, 62.0, 63.0};
+static __device__ const double RK[64] = {0.0, 1.0 / 1, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31, 1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39, 1.0 / 40, 1.0 / 41, 1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47, 1.0 / 48, 1.0 / 49, 1.0 / 50, 1.0 / 51, 1.0 / 52, 1.0 / 53, 1.0 / 54, 1.0 / 55, 1.0 / 56, 1.0 / 57, 1.0 / 58, 1.0 / 59, 1.0 / 60, 1.0 / 61, 1.0 / 62, 1.0 / 63};
+
 // ---------------------------------------------------------------------------
 // Real argument x > 0
 // ---------------------------------------------------------------------------
@@ -223,16 +230,16 @@ static __device__ __noinline__ Hank hankel_real(double x) {
         const int k = n >> 1;
         norm += 2.0 * jn;
         const double sgn = (k & 1) ? -1.0 : 1.0;
-        sy0 = fma(sgn / k, jn, sy0);
+        sy0 = fma(sgn * RK[k], jn, sy0);
       } else {
         // odd n = 2m+1: + (-1)^{m+1}/(m+1) J_n  (term k=m+1), - (-1)^m/m J_n (term k=m, m>=1)
         const int m = n >> 1;
         const double sgn = (m & 1) ? -1.0 : 1.0;  // (-1)^m
-        double c = -sgn / (m + 1);
-        if (m >= 1) c -= sgn / m;
+        double c = -sgn * RK[m + 1];
+        if (m >= 1) c -= sgn * RK[m];
         sy1 = fma(c, jn, sy1);
       }
-      const double jm1 = fma(n * tx, jn, -jn1);
+      const double jm1 = fma(DK[n] * tx, jn, -jn1);
       jn1 = jn;
       jn = jm1;
       if (n == 1) j1 = jn1;
@@ -252,8 +259,8 @@ static __device__ __noinline__ Hank hankel_real(double x) {
     double t0 = 1.0, t1 = 1.0;
     for (int k = 1; k <= 40; ++k) {
       const double o = (double)(2 * k - 1) * (2 * k - 1);
-      t0 *= (0.0 - o) * r8 / k;
-      t1 *= (4.0 - o) * r8 / k;
+      t0 *= (0.0 - o) * r8 * RK[k];
+      t1 *= (4.0 - o) * r8 * RK[k];
       const int ph = k & 3;  // k mod 4: 1 -> +Q, 2 -> -P, 3 -> -Q, 0 -> +P
       if (ph == 1) { Q0 += t0; Q1 += t1; }
       else if (ph == 2) { P0 -= t0; P1 -= t1; }
@@ -322,15 +329,15 @@ static __device__ __noinline__ Hank hankel_cplx(cplx z) {
       if ((n & 1) == 0) {
         const int k = n >> 1;
         const double sgn = (k & 1) ? -1.0 : 1.0;
-        sy0 = sy0 + (sgn / k) * jn;
+        sy0 = sy0 + (sgn * RK[k]) * jn;
       } else {
         const int m = n >> 1;
         const double sgn = (m & 1) ? -1.0 : 1.0;
-        double c = -sgn / (m + 1);
-        if (m >= 1) c -= sgn / m;
+        double c = -sgn * RK[m + 1];
+        if (m >= 1) c -= sgn * RK[m];
         sy1 = sy1 + c * jn;
       }
-      const cplx jm1 = ((double)n * tz) * jn - jn1;
+      const cplx jm1 = (DK[n] * tz) * jn - jn1;
       jn1 = jn;
       jn = jm1;
       if (n == 1) j1 = jn1;
@@ -353,8 +360,8 @@ static __device__ __noinline__ Hank hankel_cplx(cplx z) {
     cplx t0 = C(1.0), t1 = C(1.0);
     for (int k = 1; k <= 40; ++k) {
       const double o = (double)(2 * k - 1) * (2 * k - 1);
-      t0 = ((0.0 - o) / k) * (t0 * r8);
-      t1 = ((4.0 - o) / k) * (t1 * r8);
+      t0 = ((0.0 - o) * RK[k]) * (t0 * r8);
+      t1 = ((4.0 - o) * RK[k]) * (t1 * r8);
       const int ph = k & 3;
       if (ph == 1) { Q0 = Q0 + t0; Q1 = Q1 + t1; }
       else if (ph == 2) { P0 = P0 - t0; P1 = P1 - t1; }
