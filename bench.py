@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--config3", action="store_true",
                     help="also time the 1000-interface corner grating (one solve per form, after a warm-up)")
     ap.add_argument("--corner-levels", type=int, default=2)
+    ap.add_argument("--config4", action="store_true",
+                    help="also time the 256-angle sweep of the 100-interface uneven stack, in chunks of 128 angles")
     return ap.parse_args()
 
 
@@ -226,6 +228,67 @@ def corner_grating(mlqp, dev, levels):
     return out
 
 
+def angle_sweep(mlqp, dev, chunk=128):
+    """The batched angle sweep: 256 angles of the 100-interface stack with
+    uneven node counts, solved in chunks of `chunk` angles through one
+    context (mlqp_set_angles; every stage a replayed graph), in FP64 and in
+    the mixed form; beside it, the plain FP64 solve of single angles."""
+    import numpy as np
+    import torch
+    from workloads import config4
+    prob = config4()
+    th = np.asarray(prob.theta)
+    out = {"workload": "100 interfaces, N_i in {80,...,320}, 256 angles in [-pi+0.1, -0.1]", "unit": "angles/s",
+           "chunk": chunk}
+    def checked(ctx, prec, omegas):
+        """Status check; in the mixed form an unreached refine_tol is recorded
+        (per-angle backward errors), not raised."""
+        try:
+            ctx.check()
+        except mlqp.MlqpError as e:
+            if not (prec == mlqp.MLQP_MIXED and e.status == mlqp.MLQP_ENOTCONV):
+                raise
+        if prec == mlqp.MLQP_MIXED and omegas is not None:
+            omegas += [float(ctx.block(mlqp.BLK_REFINE, 1, a)[0]) for a in range(ctx.n_theta)]
+
+    for name, prec in (("fp64", mlqp.MLQP_FP64), ("mixed", mlqp.MLQP_MIXED)):
+        ctx = mlqp.Context(prob.with_angles(th[:chunk]), device=dev, precision=prec, max_refine=20)
+        ctx.solve_device()
+        checked(ctx, prec, None)
+        torch.cuda.synchronize()
+        omegas = []
+        t0 = time.perf_counter()
+        for c0 in range(0, len(th), chunk):
+            ctx.set_angles(th[c0:c0 + chunk])
+            ctx.solve_device()
+            checked(ctx, prec, omegas)
+        el = time.perf_counter() - t0
+        out[name] = {"seconds": el, "value": len(th) / el, "workspace_gb": ctx.ws_bytes / 1e9}
+        if omegas:
+            out[name]["backward_error_max"] = max(omegas)
+            out[name]["angles_above_refine_tol"] = int(sum(w > 1e-15 for w in omegas))
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+    # per-angle plain FP64: one-angle contexts, a sample of 4 angles
+    ctx = mlqp.Context(prob.with_angles(th[:1]), device=dev)
+    ctx.solve_device()
+    ctx.check()
+    torch.cuda.synchronize()
+    sample = th[::64][:4]
+    t0 = time.perf_counter()
+    for a in sample:
+        ctx.set_angles([a])
+        ctx.solve_device()
+        ctx.check()
+    el = (time.perf_counter() - t0) / len(sample)
+    ctx.close()
+    out["per_angle_fp64"] = {"seconds_per_angle": el, "value": 1.0 / el, "sample": f"{len(sample)} of 256 angles"}
+    for name in ("fp64", "mixed"):
+        out[name]["speedup_vs_per_angle_fp64"] = out[name]["value"] * el
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -399,6 +462,8 @@ def main():
                            "d2h_bytes_per_step": d2h}
     if args.config3 and rank == 0:
         line["config3"] = corner_grating(mlqp, dev, args.corner_levels)
+    if args.config4 and rank == 0:
+        line["config4"] = angle_sweep(mlqp, dev)
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(1)

@@ -172,6 +172,13 @@ enum { MLQP_STAGE_GEOM = 0, MLQP_STAGE_FILL = 1, MLQP_STAGE_LSQ = 2,
        MLQP_STAGE_SCHUR = 3, MLQP_STAGE_SWEEP = 4, MLQP_STAGE_RECOVER = 5 };
 mlqp_status mlqp_run_stage(mlqp_ctx* ctx, int stage);
 
+/* Replaces the incidence angles of a bound context by n_theta new ones (the
+ * count given at setup, each in (-pi, 0)) and re-uploads them on the bound
+ * stream.  A sweep over many angles (Sec. 3.4) then runs in chunks through
+ * one workspace and one set of captured stage graphs.  Errors: MLQP_EINVAL
+ * (count or range), MLQP_ESTATE (not bound). */
+mlqp_status mlqp_set_angles(mlqp_ctx* ctx, const double* theta, int n_theta);
+
 /* Location of a workspace block (for inspection by tests):
  *   MLQP_BLK_ROW    interface i (1..I), angle a: the block row
  *                   [A_{i,i-1} | A_{i,i} | A_{i,i+1}] (A' after the Schur

@@ -631,6 +631,17 @@ static cudaError_t enqueue_stage(mlqp_ctx* c, int stage, cudaStream_t st) {
   return e;
 }
 
+mlqp_status mlqp_set_angles(mlqp_ctx* c, const double* theta, int n_theta) {
+  if (!c) return MLQP_EINVAL;
+  if (!theta || n_theta != c->n_theta) return fail(c, MLQP_EINVAL, "set_angles needs the n_theta given at setup");
+  for (int a = 0; a < n_theta; ++a)
+    if (!(theta[a] > -M_PI && theta[a] < 0)) return fail(c, MLQP_EINVAL, "incidence angles must lie in (-pi, 0)");
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  c->theta.assign(theta, theta + n_theta);
+  // same workspace and stream: re-uploads the descriptors, keeps the stage graphs
+  return mlqp_bind(c, c->ws, c->ws_bytes, c->stream);
+}
+
 mlqp_status mlqp_run_stage(mlqp_ctx* c, int stage) {
   if (!c) return MLQP_EINVAL;
   if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");

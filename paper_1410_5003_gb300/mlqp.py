@@ -64,6 +64,8 @@ def load(path: str = LIB_PATH):
     lib.mlqp_workspace_bytes.restype = Z
     lib.mlqp_bind.argtypes = [P, V, Z, V]
     lib.mlqp_bind.restype = I
+    lib.mlqp_set_angles.argtypes = [P, ct.POINTER(D), I]
+    lib.mlqp_set_angles.restype = I
     lib.mlqp_solve_device.argtypes = [P, V, V, V, V]
     lib.mlqp_solve_device.restype = I
     lib.mlqp_check_device.argtypes = [P]
@@ -90,7 +92,7 @@ def load(path: str = LIB_PATH):
     return lib
 
 
-EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_solve_device",
+EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_set_angles", "mlqp_solve_device",
             "mlqp_check_device", "mlqp_solve", "mlqp_run_stage", "mlqp_block_info", "mlqp_last_error",
             "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes",
             "mlqp_lsq_solve_noalloc"]
@@ -177,6 +179,11 @@ class Context:
     def bind(self):
         _check(self.ctx, self.lib.mlqp_bind(self.ctx, ct.c_void_p(self.ws.data_ptr() + self.ws_off),
                                             self.ws_bytes, ct.c_void_p(self.stream.cuda_stream)))
+
+    def set_angles(self, theta):
+        """New incidence angles (as many as at setup) for the next solves."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        _check(self.ctx, self.lib.mlqp_set_angles(self.ctx, _dptr(th), len(th)))
 
     def close(self):
         if self.ctx:

@@ -148,3 +148,19 @@ def test_cyclic_solver_validation(M):
     ragged.ifaces[1].N = 72
     assert st(ragged, M.MLQP_MIXED, M.MLQP_CYCLIC) == M.MLQP_EINVAL
     assert st(ragged, M.MLQP_MIXED, M.MLQP_SWEEP) == M.MLQP_OK
+
+
+def test_set_angles_validation_without_a_device(M):
+    """mlqp_set_angles checks count and range before anything else, and needs
+    a bound context (none exists here, so no device work is reached)."""
+    import ctypes as ct
+    from workloads import small_stack
+    lib = M.load()
+    prob = small_stack(I=2, n_angles=2)
+    ctx, _ = M.mlqp_setup(prob)
+    th = np.ascontiguousarray([-0.5, -1.0])
+    assert lib.mlqp_set_angles(ctx, M._dptr(th), 3) == M.MLQP_EINVAL
+    bad = np.ascontiguousarray([-0.5, 0.2])
+    assert lib.mlqp_set_angles(ctx, M._dptr(bad), 2) == M.MLQP_EINVAL
+    assert lib.mlqp_set_angles(ctx, M._dptr(th), 2) == M.MLQP_ESTATE
+    lib.mlqp_destroy(ctx)

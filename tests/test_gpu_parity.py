@@ -392,3 +392,21 @@ def test_cyclic_reduction_on_benchmark_stack(M):
     for a in range(prob.n_theta):
         r = O.solve(prob, a, asm)
         assert rel(np.concatenate([out["aU"][a], out["aD"][a]]), np.concatenate([r["aU"], r["aD"]])) < AMP_TOL
+
+
+def test_set_angles_sweeps_in_chunks(M):
+    """An angle sweep in chunks through one context (mlqp_set_angles) gives,
+    bit for bit, what a context set up with those angles gives."""
+    prob = small_stack(I=2, N=48, P=40, Mw=30, K=20, M=45, n_angles=2)
+    th2 = np.asarray(prob.theta) - 0.07
+    ctx = M.Context(prob)
+    o1 = ctx.solve_host()
+    a1 = o1["aU"].copy()
+    ctx.set_angles(th2)
+    o2 = ctx.solve_host()
+    ctx.close()
+    fresh = M.Context(prob.with_angles(th2))
+    o3 = fresh.solve_host()
+    fresh.close()
+    assert np.array_equal(o2["aU"], o3["aU"]) and np.array_equal(o2["aD"], o3["aD"])
+    assert not np.allclose(a1, o2["aU"])
