@@ -232,7 +232,9 @@ def angle_sweep(mlqp, dev, chunk=128):
     """The batched angle sweep: 256 angles of the 100-interface stack with
     uneven node counts, solved in chunks of `chunk` angles through one
     context (mlqp_set_angles; every stage a replayed graph), in FP64 and in
-    the mixed form; beside it, the plain FP64 solve of single angles."""
+    the mixed form (plain and GMRES refinement), with each mixed leg's
+    backward errors and amplitude deviation from the FP64 leg; beside it, the
+    plain FP64 solve of single angles."""
     import numpy as np
     import torch
     from workloads import config4
@@ -251,24 +253,34 @@ def angle_sweep(mlqp, dev, chunk=128):
         if prec == mlqp.MLQP_MIXED and omegas is not None:
             omegas += [float(ctx.block(mlqp.BLK_REFINE, 1, a)[0]) for a in range(ctx.n_theta)]
 
-    for name, prec in (("fp64", mlqp.MLQP_FP64), ("mixed", mlqp.MLQP_MIXED)):
-        ctx = mlqp.Context(prob.with_angles(th[:chunk]), device=dev, precision=prec, max_refine=20)
-        ctx.solve_device()
+    legs = (("fp64", mlqp.MLQP_FP64, {}),
+            ("mixed", mlqp.MLQP_MIXED, dict(max_refine=20)),
+            ("mixed_gmres", mlqp.MLQP_MIXED, dict(max_refine=4, refine_method=mlqp.MLQP_GMRES_IR)))
+    amps = {}
+    for name, prec, kw in legs:
+        ctx = mlqp.Context(prob.with_angles(th[:chunk]), device=dev, precision=prec, **kw)
+        res = ctx.outputs()
+        ctx.solve_device(res)
         checked(ctx, prec, None)
         torch.cuda.synchronize()
-        omegas = []
+        omegas, amps[name] = [], []
         t0 = time.perf_counter()
         for c0 in range(0, len(th), chunk):
             ctx.set_angles(th[c0:c0 + chunk])
-            ctx.solve_device()
+            ctx.solve_device(res)
             checked(ctx, prec, omegas)
+            amps[name].append(torch.cat([res["aU"], res["aD"]], 1).cpu())
         el = time.perf_counter() - t0
         out[name] = {"seconds": el, "value": len(th) / el, "workspace_gb": ctx.ws_bytes / 1e9}
         if omegas:
             out[name]["backward_error_max"] = max(omegas)
             out[name]["angles_above_refine_tol"] = int(sum(w > 1e-15 for w in omegas))
+            dev_a = torch.cat(amps[name]) - torch.cat(amps["fp64"])
+            rel = (dev_a.abs().amax(1) / torch.cat(amps["fp64"]).abs().amax(1)).numpy()
+            out[name]["amp_rel_diff_vs_fp64"] = {"median": float(np.median(rel)), "max": float(rel.max()),
+                                                 "angles_above_1e-9": int((rel > 1e-9).sum())}
         ctx.close()
-        del ctx
+        del ctx, res
         torch.cuda.empty_cache()
     # per-angle plain FP64: one-angle contexts, a sample of 4 angles
     ctx = mlqp.Context(prob.with_angles(th[:1]), device=dev)
@@ -284,7 +296,7 @@ def angle_sweep(mlqp, dev, chunk=128):
     el = (time.perf_counter() - t0) / len(sample)
     ctx.close()
     out["per_angle_fp64"] = {"seconds_per_angle": el, "value": 1.0 / el, "sample": f"{len(sample)} of 256 angles"}
-    for name in ("fp64", "mixed"):
+    for name, _, _ in legs:
         out[name]["speedup_vs_per_angle_fp64"] = out[name]["value"] * el
     return out
 

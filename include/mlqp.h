@@ -50,6 +50,7 @@ typedef enum {
 
 enum { MLQP_FP64 = 0, MLQP_MIXED = 1 };
 enum { MLQP_SWEEP = 0, MLQP_CYCLIC = 1 };
+enum { MLQP_IR = 0, MLQP_GMRES_IR = 1 };
 
 typedef struct mlqp_ctx mlqp_ctx;
 
@@ -96,7 +97,13 @@ typedef struct {
  * interfaces) or, for MLQP_MIXED with equal n_nodes on every interface,
  * MLQP_CYCLIC (block cyclic reduction over the interfaces: log2 I levels of
  * batched FP32 LU, triangular solves and Schur updates, the parallel block
- * solve the paper's closing remarks name for deep stacks). */
+ * solve the paper's closing remarks name for deep stacks).  refine_method
+ * (MLQP_MIXED): MLQP_IR (each correction is one FP32 block solve of the
+ * residual) or MLQP_GMRES_IR (each correction is a flexible GMRES solve in
+ * FP64, at most 12 steps, right-preconditioned by the same FP32 block
+ * factors; it converges where kappa(A') eps_32 is near 1 and plain
+ * refinement stalls, at up to 12 block solves and FP64 operator products per
+ * correction). */
 typedef struct {
   int P;
   double R;
@@ -112,6 +119,7 @@ typedef struct {
   int max_refine;
   double refine_tol;
   int block_solver;
+  int refine_method;
 } mlqp_params;
 
 /* Validates the problem and records it on the host (no device work).
@@ -193,7 +201,10 @@ mlqp_status mlqp_set_angles(mlqp_ctx* ctx, const double* theta, int n_theta);
  *   MLQP_BLK_AMP    index 1, angle a: [a^U; a^D] after recovery (2(2K+1) x 1)
  *   MLQP_BLK_REFINE index 1, angle a (MLQP_MIXED only): 2 doubles, the
  *                   normwise backward error omega of the returned eta (below)
- *                   and the number of FP64 corrections applied
+ *                   and the number of FP64 corrections applied;
+ *                   index 2 (MLQP_GMRES_IR only): 2 doubles, the GMRES steps
+ *                   taken over all corrections and |r - A' d| / |r| of the
+ *                   last inner solve
  * Complex blocks are interleaved complex128.  Offsets are in bytes from the
  * workspace base; ld is the leading dimension in elements. */
 enum { MLQP_BLK_ROW = 0, MLQP_BLK_B = 1, MLQP_BLK_QP = 2, MLQP_BLK_CP = 3,

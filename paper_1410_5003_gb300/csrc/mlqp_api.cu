@@ -24,7 +24,7 @@ cudaError_t sweep_configure(int maxn);
 cudaError_t mixed_configure(int maxn);
 cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s);
 cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n_den, int max_refine, double tol,
-                               int* permv, const AngleStreams& A, bool cyclic);
+                               int* permv, const AngleStreams& A, bool cyclic, bool gmres);
 cudaError_t cr_configure(int maxn);
 int cr_slots(int I);
 cudaError_t lsq_configure(int max_m, int max_p);
@@ -57,7 +57,7 @@ struct mlqp_ctx {
          t_stride = 0;
   // layout
   Region r_ifc, r_lay, r_tasks, r_k, r_ca, r_cb, r_theta, r_scal, r_geo[8], r_pan[4], r_gl16, r_nidx, r_nw, r_wy, r_gl, r_ux, r_alpha, r_kappa,
-      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ROW32, r_F32, r_UDINV32, r_RES, r_ZX, r_ZXA, r_Y32, r_RNRM, r_CRSAVE, r_PERMV, r_ETA, r_AMP, r_FLUX, r_STATUS;
+      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ROW32, r_F32, r_UDINV32, r_RES, r_ZX, r_ZXA, r_Y32, r_RNRM, r_CRSAVE, r_GV, r_GZ, r_GW, r_GH, r_GPART, r_PERMV, r_ETA, r_AMP, r_FLUX, r_STATUS;
   size_t ws_bytes = 0;
   // binding
   char* ws = nullptr;
@@ -204,6 +204,10 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   if (q.precision == MLQP_MIXED && (q.max_refine < 1 || q.max_refine > 50 || !(q.refine_tol > 0)))
     return bad("MLQP_MIXED needs 1 <= max_refine <= 50 and refine_tol > 0");
   if (q.block_solver != MLQP_SWEEP && q.block_solver != MLQP_CYCLIC) return bad("block_solver must be MLQP_SWEEP or MLQP_CYCLIC");
+  if (q.refine_method != MLQP_IR && q.refine_method != MLQP_GMRES_IR)
+    return bad("refine_method must be MLQP_IR or MLQP_GMRES_IR");
+  if (q.refine_method == MLQP_GMRES_IR && q.precision != MLQP_MIXED)
+    return bad("MLQP_GMRES_IR is a refinement of the MLQP_MIXED form");
   if (q.block_solver == MLQP_CYCLIC) {
     if (q.precision != MLQP_MIXED) return bad("MLQP_CYCLIC is the block solver of the MLQP_MIXED form");
     for (int i = 1; i < I; ++i)
@@ -446,6 +450,13 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
     take(cur, c->r_RNRM, d8 * nt * RNRM_W);
     if (q.block_solver == MLQP_CYCLIC)
       take(cur, c->r_CRSAVE, sizeof(float2) * nt * (size_t)cr_slots(I) * 2 * c->maxn * c->maxn);
+    if (q.refine_method == MLQP_GMRES_IR) {
+      take(cur, c->r_GV, z16 * nt * (GM_M + 1) * c->n_den);
+      take(cur, c->r_GZ, z16 * nt * GM_M * c->n_den);
+      take(cur, c->r_GW, z16 * nt * c->n_den);
+      take(cur, c->r_GH, d8 * nt * GM_HW);
+      take(cur, c->r_GPART, z16 * nt * GM_NB * (GM_M + 1));
+    }
     take(cur, c->r_PERMV, sizeof(int) * nt * c->n_den);
   }
   take(cur, c->r_ETA, z16 * nt * c->n_den);
@@ -557,6 +568,13 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
       D.CRSAVE = at<float2>(c, c->r_CRSAVE);
       D.crsave_stride = (size_t)cr_slots(c->I) * 2 * c->maxn * c->maxn;
     }
+    if (q.refine_method == MLQP_GMRES_IR) {
+      D.GV = at<double2>(c, c->r_GV);
+      D.GZ = at<double2>(c, c->r_GZ);
+      D.GW = at<double2>(c, c->r_GW);
+      D.GH = at<double>(c, c->r_GH);
+      D.GPART = at<double2>(c, c->r_GPART);
+    }
   }
   D.ETA = at<double2>(c, c->r_ETA);
   D.eta_stride = c->n_den;
@@ -622,7 +640,8 @@ static cudaError_t enqueue_stage(mlqp_ctx* c, int stage, cudaStream_t st) {
     case MLQP_STAGE_SWEEP:
       e = (c->prm.precision == MLQP_MIXED)
               ? launch_mixed_solve(c->D, c->n_host.data(), c->maxn, c->n_den, c->prm.max_refine, c->prm.refine_tol,
-                                   at<int>(c, c->r_PERMV), A, c->prm.block_solver == MLQP_CYCLIC)
+                                   at<int>(c, c->r_PERMV), A, c->prm.block_solver == MLQP_CYCLIC,
+                                   c->prm.refine_method == MLQP_GMRES_IR)
               : launch_sweep(c->D, c->n_host.data(), A);
       break;
     case MLQP_STAGE_RECOVER: e = launch_recover(c->D, st); break;
@@ -735,8 +754,9 @@ mlqp_status mlqp_block_info(const mlqp_ctx* c, int kind, int index, int angle, s
   const size_t z = sizeof(double2);
   const size_t a = angle;
   if (kind == MLQP_BLK_REFINE) {
-    if (index != 1 || c->prm.precision != MLQP_MIXED) return MLQP_EINVAL;
-    *offset_bytes = c->r_RNRM.off + sizeof(double) * RNRM_W * a;
+    if (c->prm.precision != MLQP_MIXED) return MLQP_EINVAL;
+    if (index != 1 && !(index == 2 && c->prm.refine_method == MLQP_GMRES_IR)) return MLQP_EINVAL;
+    *offset_bytes = c->r_RNRM.off + sizeof(double) * (RNRM_W * a + (index == 2 ? 5 : 0));
     *rows = 2; *cols = 1; *ld = 2;
     return MLQP_OK;
   }

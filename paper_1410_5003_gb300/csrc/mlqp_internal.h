@@ -71,6 +71,10 @@ struct AngleStreams {
 constexpr int RNRM_W = 8;  // doubles per angle of the refinement control block
 constexpr int PANEL_P = 16;  // Gauss-Legendre nodes per corner panel
 constexpr int NEAR_MAX = 12; // near-panel slots per node of a corner interface
+constexpr int GM_M = 40;     // GMRES steps per refinement step
+constexpr int GM_NB = 64;    // CTAs of the batched reductions (per angle)
+constexpr int GM_HW = 4096;  // doubles of per-angle GMRES data
+constexpr double GM_TOL = 1e-10;  // inner GMRES stop: |r - A' d| <= GM_TOL |r|
 
 struct Dev {
   int I, L, n_theta, P, Mw, M, K, nK;
@@ -126,8 +130,17 @@ struct Dev {
   double* ZXA;   // per angle, like ZX: |X_j[:P]| |eta| (|re| + |im|), the rounding scale of ZX
   float2* Y32;   // per angle, indexed like eta: forward / backward solve vector
   float2* CRSAVE; size_t crsave_stride;  // cyclic reduction: couplings saved per level (2 n x n per slot)
+  // GMRES refinement: Krylov basis V (GM_M + 1 vectors) and preconditioned
+  // basis Z (GM_M vectors), vector i of all angles stored as one block indexed
+  // like eta; work vector, per-angle small data, reduction partials
+  double2* GV;
+  double2* GZ;
+  double2* GW;
+  double* GH;
+  double2* GPART;
   double* RNRM;  // per angle RNRM_W slots: backward error, corrections applied,
-                 // max |r| and max scale (bit patterns, atomic max), done flag
+                 // max |r| and max scale (bit patterns, atomic max), done flag,
+                 // GMRES steps over all corrections, last inner relative residual
   double2* ETA; size_t eta_stride;
   double2* AMP;                        // n_theta x 2 nK
   double* FLUX;                        // n_theta

@@ -9,6 +9,8 @@
 // least-squares solves stay FP64.
 #include <math_constants.h>
 
+#include <algorithm>
+
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
 #include "mlqp_trsv.cuh"
@@ -140,8 +142,10 @@ __device__ __forceinline__ bool angle_done(const Dev& D, int a) { return ctl(D, 
 
 __device__ __forceinline__ double cabs1(double2 z) { return fabs(z.x) + fabs(z.y); }
 
-// ZX_j = X_j[:P] eta and ZXA_j = |X_j[:P]| |eta| (one warp per row of X).
-__global__ void __launch_bounds__(256) k_xeta(Dev D) {
+// ZX_j = X_j[:P] v and (SCALE) ZXA_j = |X_j[:P]| |v| for the vector v = vin
+// (indexed like eta; eta itself for the residual), one warp per row of X.
+template <bool SCALE>
+__global__ void __launch_bounds__(256) k_xeta(Dev D, const double2* vin) {
   const int a = blockIdx.y;
   if (angle_done(D, a)) return;
   const int lane = threadIdx.x & 31;
@@ -150,28 +154,30 @@ __global__ void __launch_bounds__(256) k_xeta(Dev D) {
   const int j = row / D.P, p = row % D.P;
   const LayerDesc L = D.lay[j];
   const int first = (L.if0 >= 0) ? L.if0 : L.if1;
-  const double2* eta = D.ETA + a * D.eta_stride + D.ifc[first].eta_off;
+  const double2* eta = vin + a * D.eta_stride + D.ifc[first].eta_off;
   const double2* X = D.Xb + a * D.x_stride + L.x_off;
   double sr = 0.0, si = 0.0, sa = 0.0;
   for (int c = lane; c < L.c; c += 32) {
     const double2 x = X[(size_t)c * L.p + p], e = eta[c];
     sr = fma(x.x, e.x, fma(-x.y, e.y, sr));
     si = fma(x.x, e.y, fma(x.y, e.x, si));
-    sa = fma(cabs1(x), cabs1(e), sa);
+    if (SCALE) sa = fma(cabs1(x), cabs1(e), sa);
   }
   sr = warp_sum_dd(sr);
   si = warp_sum_dd(si);
-  sa = warp_sum_dd(sa);
+  if (SCALE) sa = warp_sum_dd(sa);
   if (lane == 0) {
     D.ZX[(size_t)a * D.L * D.P + row] = make_double2(sr, si);
-    D.ZXA[(size_t)a * D.L * D.P + row] = sa;
+    if (SCALE) D.ZXA[(size_t)a * D.L * D.P + row] = sa;
   }
 }
 
-// r_i = f_i - [A_{i,i-1} A_{i,i} A_{i,i+1}] eta + [B_{i,i} B_{i,i+1}] [ZX_i; ZX_{i+1}]
-// (one warp per row, lanes over columns), with its scale s; per-angle maxima
-// of |r| and s by atomic max.
-__global__ void __launch_bounds__(256) k_resid(Dev D) {
+// MODE 0: r_i = f_i - [A_{i,i-1} A_{i,i} A_{i,i+1}] v + [B_{i,i} B_{i,i+1}] [ZX_i; ZX_{i+1}]
+// with its scale s and per-angle maxima of |r| and s by atomic max (the
+// residual, v = eta); MODE 1: A' v = A v - B (X v) (the operator applied to
+// v, ZX from k_xeta<false>).  One warp per row, lanes over columns.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_resid(Dev D, const double2* vin, double2* vout) {
   const int i = blockIdx.y, a = blockIdx.z;
   if (angle_done(D, a)) return;
   const IfaceDesc f = D.ifc[i];
@@ -179,7 +185,7 @@ __global__ void __launch_bounds__(256) k_resid(Dev D) {
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (r >= f.n) return;
   const double2* A = D.ROW + a * D.r_stride + f.row_off;
-  const double2* eta = D.ETA + a * D.eta_stride + f.eta_off - f.nl;  // eta_{i-1}, eta_i, eta_{i+1} are contiguous
+  const double2* eta = vin + a * D.eta_stride + f.eta_off - f.nl;  // v_{i-1}, v_i, v_{i+1} are contiguous
   const double2* Bm = D.B + f.b_off;
   const size_t zo = (size_t)a * D.L * D.P + (size_t)i * D.P;  // [ZX_i; ZX_{i+1}]
   const double2* z = D.ZX + zo;
@@ -189,21 +195,22 @@ __global__ void __launch_bounds__(256) k_resid(Dev D) {
     const double2 x = A[(size_t)c * f.n + r], e = eta[c];
     sr = fma(x.x, e.x, fma(-x.y, e.y, sr));
     si = fma(x.x, e.y, fma(x.y, e.x, si));
-    sa = fma(cabs1(x), cabs1(e), sa);
+    if (MODE == 0) sa = fma(cabs1(x), cabs1(e), sa);
   }
   for (int c = lane; c < 2 * D.P; c += 32) {
     const double2 x = Bm[(size_t)c * f.n + r], e = z[c];
     sr = fma(-x.x, e.x, fma(x.y, e.y, sr));
     si = fma(-x.x, e.y, fma(-x.y, e.x, si));
-    sa = fma(cabs1(x), za[c], sa);
+    if (MODE == 0) sa = fma(cabs1(x), za[c], sa);
   }
   sr = warp_sum_dd(sr);
   si = warp_sum_dd(si);
-  sa = warp_sum_dd(sa);
-  if (lane == 0) {
+  if (MODE == 0) sa = warp_sum_dd(sa);
+  if (lane == 0 && MODE == 1) vout[a * D.eta_stride + f.eta_off + r] = make_double2(sr, si);
+  if (lane == 0 && MODE == 0) {
     const double2 fv = D.F[a * D.f_stride + f.rhs_off + r];
     const double2 rv = make_double2(fv.x - sr, fv.y - si);
-    D.RES[a * D.eta_stride + f.eta_off + r] = rv;
+    vout[a * D.eta_stride + f.eta_off + r] = rv;
     unsigned long long* c = ctl(D, a);
     atomicMax(c + 2, (unsigned long long)__double_as_longlong(cabs1(rv)));
     atomicMax(c + 3, (unsigned long long)__double_as_longlong(sa + cabs1(fv)));
@@ -344,14 +351,85 @@ cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Factorise A'_32 and refine eta in FP64: up to max_refine corrections,
-// each preceded by a residual and its backward error; a final residual
-// checks the last one.
 cudaError_t launch_cr_factor(const Dev& D, int n, int* permv, cudaStream_t st);
 cudaError_t launch_cr_solve(const Dev& D, int n, long n_den, const int* permv, cudaStream_t st);
 
+// GMRES refinement kernels (defined below)
+__global__ void k_gm_to64(Dev D, int j, int n_den);
+__global__ void k_gm_dot(Dev D, int j, int mode, int n_den);
+__global__ void k_gm_sum(Dev D, int j, int mode);
+__global__ void k_gm_orth(Dev D, int j, int n_den);
+__global__ void k_gm_scale(Dev D, int j, int n_den);
+__global__ void k_gm_begin(Dev D);
+__global__ void k_gm_givens(Dev D, int j, double tol_inner);
+__global__ void k_gm_solve(Dev D);
+__global__ void k_gm_update(Dev D, int n_den);
+
+// M^{-1} applied to RES (FP64), result in Y32 (FP32): the block substitution
+// with the FP32 factors, by the sweep's per-interface kernels or cyclic reduction.
+static cudaError_t launch_precond(const Dev& D, const int* n_host, long n_den, int* permv, bool cyclic, cudaStream_t s) {
+  if (cyclic) return launch_cr_solve(D, n_host[0], n_den, permv, s);
+  for (int t = 0; t < D.I; ++t) {
+    g_launches += 2;
+    k_mv32<<<dim3((n_host[t] + 31) / 32, D.n_theta), 256, 0, s>>>(D, t, 0, permv);
+    k_lower32<<<D.n_theta, TRSV_THREADS, sizeof(float2) * n_host[t], s>>>(D, t);
+  }
+  for (int t = D.I - 1; t >= 0; --t) {
+    if (t + 1 < D.I) {
+      ++g_launches;
+      k_mv32<<<dim3((n_host[t] + 31) / 32, D.n_theta), 256, 0, s>>>(D, t, 1, permv);
+    }
+    ++g_launches;
+    k_upper32<<<D.n_theta, TRSV_THREADS, sizeof(float2) * n_host[t], s>>>(D, t);
+  }
+  return cudaGetLastError();
+}
+
+// One inner flexible GMRES(GM_M) solve of A' d = r (r in RES), eta += d.
+// Angles whose outer test has passed are skipped.
+static cudaError_t launch_gmres(const Dev& D, const int* n_host, int maxn, long n_den, int* permv, bool cyclic,
+                                cudaStream_t s) {
+  const int nt = D.n_theta, nd = (int)n_den;
+  const dim3 vec((unsigned)std::max(1L, std::min(512L, (n_den + 255) / 256)), nt);
+  const dim3 red(GM_NB, nt);
+  cudaError_t e;
+  g_launches += 4;
+  k_gm_begin<<<nt, 256, 0, s>>>(D);
+  k_gm_dot<<<red, 256, 0, s>>>(D, -1, 1, nd);
+  k_gm_sum<<<nt, 64, 0, s>>>(D, -1, 1);
+  k_gm_scale<<<vec, 256, 0, s>>>(D, -1, nd);
+  const size_t vstride = (size_t)nt * D.eta_stride;
+  for (int j = 0; j < GM_M; ++j) {
+    if ((e = launch_precond(D, n_host, n_den, permv, cyclic, s)) != cudaSuccess) return e;
+    const double2* zj = D.GZ + (size_t)j * vstride;
+    g_launches += 3;
+    k_gm_to64<<<vec, 256, 0, s>>>(D, j, nd);
+    k_xeta<false><<<dim3((D.L * D.P + 7) / 8, nt), 256, 0, s>>>(D, zj);
+    k_resid<1><<<dim3((maxn + 7) / 8, D.I, nt), 256, 0, s>>>(D, zj, D.GW);
+    for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+      g_launches += 3;
+      k_gm_dot<<<dim3(GM_NB, nt, (j + 8) / 8), 256, 0, s>>>(D, j, 0, nd);
+      k_gm_sum<<<nt, 64, 0, s>>>(D, j, 0);
+      k_gm_orth<<<vec, 256, 0, s>>>(D, j, nd);
+    }
+    g_launches += 4;
+    k_gm_dot<<<red, 256, 0, s>>>(D, j, 1, nd);
+    k_gm_sum<<<nt, 64, 0, s>>>(D, j, 1);
+    k_gm_scale<<<vec, 256, 0, s>>>(D, j, nd);
+    k_gm_givens<<<1, 128, 0, s>>>(D, j, GM_TOL);
+  }
+  g_launches += 2;
+  k_gm_solve<<<1, 128, 0, s>>>(D);
+  k_gm_update<<<vec, 256, 0, s>>>(D, nd);
+  return cudaGetLastError();
+}
+
+// Factorise A'_32 and refine eta in FP64: up to max_refine corrections (one
+// FP32 block solve each, or with gmres one flexible GMRES solve), each
+// preceded by a residual and its backward error; a final residual checks the
+// last one.
 cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n_den, int max_refine, double tol,
-                               int* permv, const AngleStreams& A, bool cyclic) {
+                               int* permv, const AngleStreams& A, bool cyclic, bool gmres) {
   cudaStream_t s = A.main;
   cudaError_t e = cudaMemsetAsync(D.F32, 0, sizeof(float2) * D.f_stride * D.n_theta, s);
   if (e != cudaSuccess) return e;
@@ -371,36 +449,303 @@ cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n
   for (int it = 0; it <= max_refine; ++it) {
     const int last = (it == max_refine);
     ++g_launches;
-    k_xeta<<<dim3((D.L * D.P + 7) / 8, D.n_theta), 256, 0, s>>>(D);
+    k_xeta<true><<<dim3((D.L * D.P + 7) / 8, D.n_theta), 256, 0, s>>>(D, D.ETA);
     ++g_launches;
-    k_resid<<<dim3((maxn + 7) / 8, D.I, D.n_theta), 256, 0, s>>>(D);
+    k_resid<0><<<dim3((maxn + 7) / 8, D.I, D.n_theta), 256, 0, s>>>(D, D.ETA, D.RES);
     ++g_launches;
     k_refine_ctl<<<1, 32, 0, s>>>(D, last, tol);
     if (last) break;
-    if (cyclic) {
-      if ((e = launch_cr_solve(D, n_host[0], n_den, permv, s)) != cudaSuccess) return e;
+    if (gmres) {
+      if ((e = launch_gmres(D, n_host, maxn, n_den, permv, cyclic, s)) != cudaSuccess) return e;
     } else {
-      for (int t = 0; t < D.I; ++t) {
-        g_launches += 2;
-        k_mv32<<<dim3((n_host[t] + 31) / 32, D.n_theta), 256, 0, s>>>(D, t, 0, permv);
-        k_lower32<<<D.n_theta, TRSV_THREADS, sizeof(float2) * n_host[t], s>>>(D, t);
-      }
-      for (int t = D.I - 1; t >= 0; --t) {
-        if (t + 1 < D.I) {
-          ++g_launches;
-          k_mv32<<<dim3((n_host[t] + 31) / 32, D.n_theta), 256, 0, s>>>(D, t, 1, permv);
-        }
-        ++g_launches;
-        k_upper32<<<D.n_theta, TRSV_THREADS, sizeof(float2) * n_host[t], s>>>(D, t);
-      }
+      if ((e = launch_precond(D, n_host, n_den, permv, cyclic, s)) != cudaSuccess) return e;
+      ++g_launches;
+      k_eta_update<<<D.n_theta, 256, 0, s>>>(D, (int)n_den);
     }
-    ++g_launches;
-    k_eta_update<<<D.n_theta, 256, 0, s>>>(D, (int)n_den);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
 
 cudaError_t mixed_configure(int) { return cudaSuccess; }
+
+}  // namespace mlqp
+
+namespace mlqp {
+
+// ---------------------------------------------------------------------------
+// GMRES-based refinement.  Where plain refinement stalls (kappa(A') eps32
+// near 1), each correction equation A' d = r is solved by flexible GMRES in
+// FP64, right-preconditioned by the FP32 block factorisation M:
+//   z_j = M^{-1} v_j (FP32 solve),  w = A' z_j (FP64),  Arnoldi on w,
+//   d = Z y  with  y = argmin || beta e_1 - H y ||,
+// so the minimised quantity is the true FP64 residual || r - A' d || whatever
+// the rounding of the FP32 solves; then eta += d and the outer backward-error
+// test decides (refine_tol).  Arnoldi with classical Gram-Schmidt applied
+// twice; complex Givens rotations on the Hessenberg matrix.  Reductions are
+// two-pass (GM_NB partial sums per angle, then a fixed-order sum):
+// deterministic.  Per-angle data (GM_HW doubles): H (GM_M+1) x GM_M complex
+// at 0, cos at HC, sin (complex) at HS, g (GM_M+1 complex) at HG, y at HY,
+// CGS coefficients at HT, then [active, steps, beta].  Vector i of all angles
+// is one eta-indexed block: V_i at GV + i nt eta_stride, Z_i likewise at GZ.
+// ---------------------------------------------------------------------------
+constexpr int HH = 0;
+constexpr int HC = HH + 2 * (GM_M + 1) * GM_M;
+constexpr int HS = HC + GM_M;
+constexpr int HG = HS + 2 * GM_M;
+constexpr int HY = HG + 2 * (GM_M + 1);
+constexpr int HT = HY + 2 * GM_M;
+constexpr int HF = HT + 2 * (GM_M + 1);
+static_assert(HF + 3 <= GM_HW, "per-angle GMRES data");
+
+__device__ __forceinline__ double* gmh(const Dev& D, int a) { return D.GH + (size_t)a * GM_HW; }
+__device__ __forceinline__ bool gm_active(const Dev& D, int a) { return !angle_done(D, a) && gmh(D, a)[HF] != 0.0; }
+__device__ __forceinline__ double2* gvec(const Dev& D, double2* base, int a, int i) {
+  return base + ((size_t)i * D.n_theta + a) * D.eta_stride;
+}
+
+// Z_j (FP64) <- Y32 = M^{-1} v_j
+__global__ void k_gm_to64(Dev D, int j, int n_den) {
+  const int a = blockIdx.y;
+  if (!gm_active(D, a)) return;
+  const float2* y = D.Y32 + a * D.eta_stride;
+  double2* z = gvec(D, D.GZ, a, j);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_den; r += gridDim.x * blockDim.x) {
+    const float2 q = y[r];
+    z[r] = make_double2((double)q.x, (double)q.y);
+  }
+}
+
+// partial sums over rows: mode 0: conj(V_i) . w for i <= j, vectors
+// 8 z .. 8 z + 7 in grid slice z;  mode 1: |w|^2 (j < 0: w = RES, the start
+// residual; else w = GW)
+__global__ void __launch_bounds__(256) k_gm_dot(Dev D, int j, int mode, int n_den) {
+  constexpr int C = 8;
+  const int a = blockIdx.y;
+  if (!gm_active(D, a)) return;
+  const double2* w = ((j < 0) ? D.RES : D.GW) + a * D.eta_stride;
+  const int i0 = C * blockIdx.z;
+  const int ni = (mode == 0) ? min(C, j + 1 - i0) : 1;
+  double sr[C], si[C];
+#pragma unroll
+  for (int i = 0; i < C; ++i) sr[i] = si[i] = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_den; r += gridDim.x * blockDim.x) {
+    const double2 x = w[r];
+    if (mode == 1) {
+      sr[0] = fma(x.x, x.x, fma(x.y, x.y, sr[0]));
+    } else {
+#pragma unroll
+      for (int i = 0; i < C; ++i)
+        if (i < ni) {
+          const double2 v = gvec(D, D.GV, a, i0 + i)[r];
+          sr[i] = fma(v.x, x.x, fma(v.y, x.y, sr[i]));  // conj(v) x
+          si[i] = fma(v.x, x.y, fma(-v.y, x.x, si[i]));
+        }
+    }
+  }
+  __shared__ double red[8][2 * C];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < C; ++i) {
+    if (i < ni) {
+      double vr = sr[i], vi = si[i];
+      for (int o = 16; o > 0; o >>= 1) {
+        vr += __shfl_xor_sync(0xffffffffu, vr, o);
+        vi += __shfl_xor_sync(0xffffffffu, vi, o);
+      }
+      if (lane == 0) {
+        red[warp][2 * i] = vr;
+        red[warp][2 * i + 1] = vi;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < ni) {
+    const int i = threadIdx.x;
+    double vr = 0.0, vi = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      vr += red[q][2 * i];
+      vi += red[q][2 * i + 1];
+    }
+    D.GPART[((size_t)a * GM_NB + blockIdx.x) * (GM_M + 1) + i0 + i] = make_double2(vr, vi);
+  }
+}
+
+// fixed-order sum of the partials.  mode 0: CGS coefficients c_i (added to
+// H[:, j] and kept in HT for k_gm_orth); mode 1: h_{j+1,j} = |w|, or with
+// j < 0 beta = |r| and g = (beta, 0, ...), a zero beta ending the angle.
+__global__ void k_gm_sum(Dev D, int j, int mode) {
+  const int a = blockIdx.x;
+  if (!gm_active(D, a)) return;
+  double* h = gmh(D, a);
+  const int ni = (mode == 0) ? j + 1 : 1;
+  for (int i = threadIdx.x; i < ni; i += blockDim.x) {
+    double vr = 0.0, vi = 0.0;
+    for (int b = 0; b < GM_NB; ++b) {
+      const double2 p = D.GPART[((size_t)a * GM_NB + b) * (GM_M + 1) + i];
+      vr += p.x;
+      vi += p.y;
+    }
+    if (mode == 0) {
+      h[HT + 2 * i] = vr;
+      h[HT + 2 * i + 1] = vi;
+      h[HH + 2 * (i * GM_M + j)] += vr;
+      h[HH + 2 * (i * GM_M + j) + 1] += vi;
+    } else if (j < 0) {
+      const double beta = sqrt(vr);
+      h[HF + 2] = beta;
+      h[HG] = beta;
+      if (!(beta > 0.0)) h[HF] = 0.0;
+    } else {
+      h[HH + 2 * ((j + 1) * GM_M + j)] = sqrt(vr);
+      h[HH + 2 * ((j + 1) * GM_M + j) + 1] = 0.0;
+    }
+  }
+}
+
+// w -= sum_{i<=j} c_i V_i  (c from HT)
+__global__ void k_gm_orth(Dev D, int j, int n_den) {
+  const int a = blockIdx.y;
+  if (!gm_active(D, a)) return;
+  const double* h = gmh(D, a);
+  double2* w = D.GW + a * D.eta_stride;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_den; r += gridDim.x * blockDim.x) {
+    double2 x = w[r];
+    for (int i = 0; i <= j; ++i) {
+      const double cr = h[HT + 2 * i], ci = h[HT + 2 * i + 1];
+      const double2 v = gvec(D, D.GV, a, i)[r];
+      x.x = fma(-cr, v.x, fma(ci, v.y, x.x));
+      x.y = fma(-cr, v.y, fma(-ci, v.x, x.y));
+    }
+    w[r] = x;
+  }
+}
+
+// V_{j+1} = w / h_{j+1,j}  (j < 0: V_0 = r / beta), also written to RES, the
+// input of the next FP32 solve.  A zero norm leaves the angle to k_gm_givens.
+__global__ void k_gm_scale(Dev D, int j, int n_den) {
+  const int a = blockIdx.y;
+  if (!gm_active(D, a)) return;
+  const double* h = gmh(D, a);
+  const double nrm = (j < 0) ? h[HF + 2] : h[HH + 2 * ((j + 1) * GM_M + j)];
+  if (!(nrm > 0.0)) return;
+  const double inv = 1.0 / nrm;
+  double2* res = D.RES + a * D.eta_stride;
+  const double2* w = (j < 0) ? res : D.GW + a * D.eta_stride;
+  double2* v = gvec(D, D.GV, a, j + 1);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_den; r += gridDim.x * blockDim.x) {
+    const double2 x = w[r];
+    const double2 q = make_double2(x.x * inv, x.y * inv);
+    v[r] = q;
+    res[r] = q;
+  }
+}
+
+// start of an inner solve: clear the per-angle data, activate the angles not
+// yet converged.  One CTA per angle.
+__global__ void k_gm_begin(Dev D) {
+  const int a = blockIdx.x;
+  double* h = gmh(D, a);
+  for (int q = threadIdx.x; q < GM_HW; q += blockDim.x) h[q] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) h[HF] = angle_done(D, a) ? 0.0 : 1.0;
+}
+
+// Givens step j: apply the earlier rotations to column j of H, form the
+// rotation that zeroes H[j+1][j], update g; stop the angle when |g_{j+1}| <=
+// tol_inner beta or the Arnoldi vector vanished.  Rotation (c real, s complex):
+//   (x, y) -> (c x + s y, -conj(s) x + c y).
+__global__ void k_gm_givens(Dev D, int j, double tol_inner) {
+  for (int a = threadIdx.x; a < D.n_theta; a += blockDim.x) {
+    if (!gm_active(D, a)) continue;
+    double* h = gmh(D, a);
+    auto H = [&](int r, int c) -> double* { return h + HH + 2 * (r * GM_M + c); };
+    for (int i = 0; i < j; ++i) {
+      const double c = h[HC + i], sr = h[HS + 2 * i], si = h[HS + 2 * i + 1];
+      double* x = H(i, j);
+      double* y = H(i + 1, j);
+      const double xr = x[0], xi = x[1], yr = y[0], yi = y[1];
+      x[0] = c * xr + sr * yr - si * yi;
+      x[1] = c * xi + sr * yi + si * yr;
+      y[0] = -(sr * xr + si * xi) + c * yr;
+      y[1] = -(sr * xi - si * xr) + c * yi;
+    }
+    double* x = H(j, j);
+    const double ay = H(j + 1, j)[0];  // real, >= 0
+    const double ax = hypot(x[0], x[1]);
+    const double den = hypot(ax, ay);
+    double c = 1.0, sr = 0.0, si = 0.0;
+    if (den > 0.0) {
+      if (ax > 0.0) {  // s = (x / |x|) y / den
+        c = ax / den;
+        sr = (x[0] / ax) * ay / den;
+        si = (x[1] / ax) * ay / den;
+      } else {
+        c = 0.0;
+        sr = 1.0;
+      }
+    }
+    h[HC + j] = c;
+    h[HS + 2 * j] = sr;
+    h[HS + 2 * j + 1] = si;
+    const double nr = c * x[0] + sr * ay, ni = c * x[1] + si * ay;
+    x[0] = nr;
+    x[1] = ni;
+    H(j + 1, j)[0] = 0.0;
+    const double gr = h[HG + 2 * j], gi = h[HG + 2 * j + 1];
+    h[HG + 2 * j] = c * gr;
+    h[HG + 2 * j + 1] = c * gi;
+    h[HG + 2 * (j + 1)] = -(sr * gr + si * gi);
+    h[HG + 2 * (j + 1) + 1] = -(sr * gi - si * gr);
+    h[HF + 1] = j + 1;  // steps taken
+    const double res = hypot(h[HG + 2 * (j + 1)], h[HG + 2 * (j + 1) + 1]);
+    double* rn = D.RNRM + (size_t)a * RNRM_W;
+    rn[5] += 1.0;                // GMRES steps, all corrections
+    rn[6] = res / h[HF + 2];     // relative residual of this inner solve
+    if (!(res > tol_inner * h[HF + 2]) || !(ay > 0.0)) h[HF] = 0.0;
+  }
+}
+
+// y = R^{-1} g over the steps taken (R the rotated H)
+__global__ void k_gm_solve(Dev D) {
+  for (int a = threadIdx.x; a < D.n_theta; a += blockDim.x) {
+    if (angle_done(D, a)) continue;
+    double* h = gmh(D, a);
+    const int k = (int)h[HF + 1];
+    for (int i = k - 1; i >= 0; --i) {
+      double sr = h[HG + 2 * i], si = h[HG + 2 * i + 1];
+      for (int c = i + 1; c < k; ++c) {
+        const double* R = h + HH + 2 * (i * GM_M + c);
+        const double yr = h[HY + 2 * c], yi = h[HY + 2 * c + 1];
+        sr -= R[0] * yr - R[1] * yi;
+        si -= R[0] * yi + R[1] * yr;
+      }
+      const double* R = h + HH + 2 * (i * GM_M + i);
+      const double d = R[0] * R[0] + R[1] * R[1];
+      h[HY + 2 * i] = (d > 0.0) ? (sr * R[0] + si * R[1]) / d : 0.0;
+      h[HY + 2 * i + 1] = (d > 0.0) ? (si * R[0] - sr * R[1]) / d : 0.0;
+    }
+  }
+}
+
+// eta += Z y
+__global__ void k_gm_update(Dev D, int n_den) {
+  const int a = blockIdx.y;
+  if (angle_done(D, a)) return;
+  const double* h = gmh(D, a);
+  const int k = (int)h[HF + 1];
+  double2* eta = D.ETA + a * D.eta_stride;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_den; r += gridDim.x * blockDim.x) {
+    double2 x = eta[r];
+    for (int i = 0; i < k; ++i) {
+      const double yr = h[HY + 2 * i], yi = h[HY + 2 * i + 1];
+      const double2 z = gvec(D, D.GZ, a, i)[r];
+      x.x = fma(yr, z.x, fma(-yi, z.y, x.x));
+      x.y = fma(yr, z.y, fma(yi, z.x, x.y));
+    }
+    eta[r] = x;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) D.RNRM[(size_t)a * RNRM_W + 1] += 1.0;
+}
 
 }  // namespace mlqp

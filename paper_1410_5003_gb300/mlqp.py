@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmlqp.so")
 MLQP_OK, MLQP_EINVAL, MLQP_ENOMEM, MLQP_ECUDA, MLQP_ESINGULAR, MLQP_ETIMEOUT, MLQP_ENOTCONV, MLQP_ESTATE = range(8)
 MLQP_FP64, MLQP_MIXED = 0, 1
 MLQP_SWEEP, MLQP_CYCLIC = 0, 1
+MLQP_IR, MLQP_GMRES_IR = 0, 1
 STAGE_GEOM, STAGE_FILL, STAGE_LSQ, STAGE_SCHUR, STAGE_SWEEP, STAGE_RECOVER = range(6)
 BLK_ROW, BLK_B, BLK_QP, BLK_CP, BLK_X, BLK_RHS, BLK_NODES, BLK_ETA, BLK_AMP, BLK_REFINE = range(10)
 
@@ -33,7 +34,8 @@ class mlqp_params(ct.Structure):
     _fields_ = [("P", ct.c_int), ("R", ct.c_double), ("Mw", ct.c_int), ("M", ct.c_int), ("K", ct.c_int),
                 ("gap_U", ct.c_double), ("gap_D", ct.c_double), ("cut_a", ct.c_double), ("cut_b", ct.c_double),
                 ("lsq_rcond", ct.c_double), ("precision", ct.c_int), ("max_refine", ct.c_int),
-                ("refine_tol", ct.c_double), ("block_solver", ct.c_int)]
+                ("refine_tol", ct.c_double), ("block_solver", ct.c_int),
+                ("refine_method", ct.c_int)]
 
 
 class MlqpError(RuntimeError):
@@ -108,13 +110,15 @@ def _dptr(a):
     return ct.cast(a.ctypes.data, ct.POINTER(ct.c_double))
 
 
-def make_params(p, precision=MLQP_FP64, max_refine=0, refine_tol=0.0, block_solver=MLQP_SWEEP):
+def make_params(p, precision=MLQP_FP64, max_refine=0, refine_tol=0.0, block_solver=MLQP_SWEEP,
+                refine_method=MLQP_IR):
     return mlqp_params(int(p.P), float(p.R), int(p.Mw), int(p.M), int(p.K), float(p.gap_U), float(p.gap_D),
                        float(p.cut_a), float(p.cut_b), float(p.lsq_rcond), int(precision), int(max_refine),
-                       float(refine_tol), int(block_solver))
+                       float(refine_tol), int(block_solver), int(refine_method))
 
 
-def mlqp_setup(prob, precision=MLQP_FP64, max_refine=0, refine_tol=0.0, block_solver=MLQP_SWEEP):
+def mlqp_setup(prob, precision=MLQP_FP64, max_refine=0, refine_tol=0.0, block_solver=MLQP_SWEEP,
+               refine_method=MLQP_IR):
     """prob: an object with .ifaces (y0, a, b, N; or y0, vx, vy, levels for a
     corner interface), .k (complex, I+1), .d,
     .theta, .params (P, R, Mw, M, K, gap_U, gap_D, cut_a, cut_b, lsq_rcond).
@@ -140,7 +144,7 @@ def mlqp_setup(prob, precision=MLQP_FP64, max_refine=0, refine_tol=0.0, block_so
     k = np.ascontiguousarray(np.stack([np.real(prob.k), np.imag(prob.k)], axis=1).ravel(), dtype=np.float64)
     th = np.ascontiguousarray(prob.theta, dtype=np.float64)
     keep += [k, th]
-    prm = make_params(prob.params, precision, max_refine, refine_tol, block_solver)
+    prm = make_params(prob.params, precision, max_refine, refine_tol, block_solver, refine_method)
     ctx = ct.c_void_p()
     st = lib.mlqp_setup(arr, I, _dptr(k), float(prob.d), _dptr(th), len(th), ct.byref(prm), ct.byref(ctx))
     if st != MLQP_OK:
@@ -155,14 +159,15 @@ class Context:
     """One problem on one device: owns the host context and a torch workspace."""
 
     def __init__(self, prob, device="cuda", stream=None, precision=MLQP_FP64, max_refine=10, refine_tol=1e-15,
-                 block_solver=MLQP_SWEEP):
+                 block_solver=MLQP_SWEEP, refine_method=MLQP_IR):
         import torch
         self.torch = torch
         self.lib = load()
         self.prob = prob
         self.precision = precision
         self.ctx, self._keep = mlqp_setup(prob, precision, max_refine if precision == MLQP_MIXED else 0,
-                                          refine_tol if precision == MLQP_MIXED else 0.0, block_solver)
+                                          refine_tol if precision == MLQP_MIXED else 0.0, block_solver,
+                                          refine_method)
         n_den = ct.c_long()
         n_modes = ct.c_int()
         _check(self.ctx, self.lib.mlqp_sizes(self.ctx, ct.byref(n_den), ct.byref(n_modes)))

@@ -150,6 +150,24 @@ def test_cyclic_solver_validation(M):
     assert st(ragged, M.MLQP_MIXED, M.MLQP_SWEEP) == M.MLQP_OK
 
 
+def test_refine_method_validation(M):
+    """MLQP_GMRES_IR refines the mixed form only; unknown methods are refused."""
+    lib = M.load()
+    from workloads import small_stack
+    def st(precision, method, solver=0):
+        try:
+            ctx, _ = M.mlqp_setup(small_stack(I=3), precision, 5 if precision == M.MLQP_MIXED else 0,
+                                  1e-15 if precision == M.MLQP_MIXED else 0.0, solver, method)
+        except M.MlqpError as e:
+            return e.status
+        lib.mlqp_destroy(ctx)
+        return M.MLQP_OK
+    assert st(M.MLQP_MIXED, M.MLQP_GMRES_IR) == M.MLQP_OK
+    assert st(M.MLQP_MIXED, M.MLQP_GMRES_IR, M.MLQP_CYCLIC) == M.MLQP_OK
+    assert st(M.MLQP_FP64, M.MLQP_GMRES_IR) == M.MLQP_EINVAL
+    assert st(M.MLQP_MIXED, 2) == M.MLQP_EINVAL
+
+
 def test_set_angles_validation_without_a_device(M):
     """mlqp_set_angles checks count and range before anything else, and needs
     a bound context (none exists here, so no device work is reached)."""

@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 from scipy.special import hankel1, jv  # noqa: E402
 
 from oracle import mlqp_oracle as O  # noqa: E402
-from workloads import config1, config2, corner_stack, small_stack, flat_stack  # noqa: E402
+from workloads import config1, config2, config4, corner_stack, small_stack, flat_stack  # noqa: E402
 from workloads.problems import Interface, Params, Problem  # noqa: E402
 from tests.closed_forms import fresnel  # noqa: E402
 
@@ -392,6 +392,53 @@ def test_cyclic_reduction_on_benchmark_stack(M):
     for a in range(prob.n_theta):
         r = O.solve(prob, a, asm)
         assert rel(np.concatenate([out["aU"][a], out["aD"][a]]), np.concatenate([r["aU"], r["aD"]])) < AMP_TOL
+
+
+@pytest.mark.parametrize("name,solver", [("config1", 0), ("small3_lossy", 0), ("corner2", 0), ("uneven", 0),
+                                         ("small3", 1)])
+def test_gmres_refinement_matches_oracle(M, name, solver):
+    """Mixed form refined by flexible GMRES (FP64 Arnoldi, FP32 block solves
+    as the right preconditioner), with the sweep (0) or cyclic reduction (1)
+    as the block solver: amplitudes agree with the oracle to 1e-9 and the
+    backward error reaches 1e-15 within two corrections."""
+    prob = PROBLEMS[name]()
+    ctx = M.Context(prob, precision=M.MLQP_MIXED, block_solver=solver, refine_method=M.MLQP_GMRES_IR)
+    out = ctx.solve_host()
+    asm = O.Assembler(prob)
+    for a in range(prob.n_theta):
+        r = O.solve(prob, a, asm)
+        ag = np.concatenate([out["aU"][a], out["aD"][a]])
+        assert rel(ag, np.concatenate([r["aU"], r["aD"]])) < AMP_TOL, (name, a)
+        omega, steps = ctx.block(M.BLK_REFINE, 1, a).cpu().numpy()
+        assert omega <= 1e-15 and 1 <= steps <= 2, (omega, steps)
+    ctx.close()
+
+
+def test_gmres_refinement_where_plain_refinement_stalls(M):
+    """100-interface angle-sweep stack, three of its angles where plain
+    refinement stalls (omega 5e-10 to 3e-9 after 20 corrections):
+    kappa(A') eps_32 is near 1 there.  Flexible GMRES refinement brings the
+    backward error below 1e-15 in at most two corrections.  At the first two
+    angles the amplitudes then agree with the plain FP64 path to 1e-9.  The
+    third angle is ill-conditioned: two backward-stable FP64 solutions differ
+    there by about 1e-5 (below the discretisation's flux-balance error at that
+    angle, 3e-6), so only the backward error is checked."""
+    th = np.asarray(config4().theta)
+    prob = config4().with_angles(th[[64, 192, 224]])
+    plain = M.Context(prob)
+    ref = plain.solve_host()
+    plain.close()
+    ctx = M.Context(prob, precision=M.MLQP_MIXED, max_refine=4, refine_method=M.MLQP_GMRES_IR)
+    out = ctx.solve_host()
+    for a in range(prob.n_theta):
+        omega, steps = ctx.block(M.BLK_REFINE, 1, a).cpu().numpy()
+        inner, inner_res = ctx.block(M.BLK_REFINE, 2, a).cpu().numpy()
+        assert omega <= 1e-15 and steps <= 2, (a, omega, steps)
+        assert 1 <= inner <= 2 * 40 and inner_res < 1e-9, (a, inner, inner_res)
+        if a < 2:
+            ag = np.concatenate([out["aU"][a], out["aD"][a]])
+            assert rel(ag, np.concatenate([ref["aU"][a], ref["aD"][a]])) < AMP_TOL, a
+    ctx.close()
 
 
 def test_set_angles_sweeps_in_chunks(M):
