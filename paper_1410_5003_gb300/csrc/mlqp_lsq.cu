@@ -10,10 +10,14 @@
 // obtained by a blocked back substitution (rows x columns parallel).
 // The Schur updates are batched complex GEMM tiles with 3M products
 // (three real products per complex product), in FP64.
+#include <cooperative_groups.h>
+
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
 
 namespace mlqp {
+
+namespace cg = cooperative_groups;
 
 extern thread_local long g_launches;
 
@@ -32,8 +36,21 @@ __device__ __forceinline__ double warp_sum(double v) {
 // lam I, lam = rcond * max_c ||Q'_j[:, c]||.  Reflector j acts on rows j..m+j
 // only: below row m+j column j is still zero (the rows m+j'+1.. of the lam I
 // block are untouched by the earlier reflectors j' < j).
-__global__ void __launch_bounds__(QR_THREADS) k_lsq_qr(Dev D) {
-  const int jl = blockIdx.x, a = blockIdx.y;
+//
+// A cluster of QCL CTAs factors one (layer, angle): column c belongs to CTA
+// c mod QCL, which alone writes it.  Per column j the owner forms reflector j
+// from its own (already updated) column and publishes beta, v0 and 1/R_jj in
+// LAUX; one cluster barrier; then every CTA applies the reflector to its own
+// columns c > j, reading column j through L2 (__ldcg).  Each column's
+// arithmetic is that of a single-CTA factorisation, warp for warp, so the
+// result does not depend on QCL.  The end layers ([Q'; lam I] of about
+// 400 x 111) were FP64-bound on one SM; QCL SMs share them now.
+constexpr int QCL = 8;
+
+__global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QR_THREADS) k_lsq_qr(Dev D) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank();
+  const int jl = blockIdx.x / QCL, a = blockIdx.y;
   const LayerDesc L = D.lay[jl];
   const int m = L.m, p = L.p, ld = L.ldq;
   double2* A = D.QP + a * D.qp_stride + L.qp_off;
@@ -41,76 +58,83 @@ __global__ void __launch_bounds__(QR_THREADS) k_lsq_qr(Dev D) {
   double2* rdg = reinterpret_cast<double2*>(aux);
   double2* v0s = reinterpret_cast<double2*>(aux + 2 * p);
   double* beta = aux + 4 * p;
-  extern __shared__ double sm[];
-  double* norms = sm;  // p
-  __shared__ double s_beta, s_lam, s_nx2;
-  __shared__ double2 s_v0;
+  __shared__ double s_part, s_lam, s_nx2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = QR_THREADS / 32;
-  // 1. column norms of Q'_j and lam
-  for (int c = warp; c < p; c += nw) {
+  // 1. squared column norms of the own columns; cluster-wide maximum -> lam
+  __shared__ double s_wmax[QR_THREADS / 32];
+  double wmax = 0.0;
+  for (int c = q + QCL * warp; c < p; c += QCL * nw) {
     const double2* col = A + (size_t)c * ld;
     double s = 0.0;
     for (int r = lane; r < m; r += 32) {
       const double2 x = col[r];
       s = fma(x.x, x.x, fma(x.y, x.y, s));
     }
-    s = warp_sum(s);
-    if (lane == 0) norms[c] = s;
+    wmax = fmax(wmax, warp_sum(s));
   }
+  if (lane == 0) s_wmax[warp] = wmax;
   __syncthreads();
   if (tid == 0) {
     double mx = 0.0;
-    for (int c = 0; c < p; ++c) mx = fmax(mx, norms[c]);
+    for (int w = 0; w < nw; ++w) mx = fmax(mx, s_wmax[w]);
+    s_part = mx;
+  }
+  cl.sync();
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int r = 0; r < QCL; ++r) mx = fmax(mx, *cl.map_shared_rank(&s_part, r));
     s_lam = D.rcond * sqrt(mx);
   }
   __syncthreads();
-  // 2. the lam I rows
-  for (int e = tid; e < p * p; e += QR_THREADS) {
-    const int r = e % p, c = e / p;
-    A[(size_t)c * ld + m + r] = make_double2(r == c ? s_lam : 0.0, 0.0);
+  // 2. the lam I rows of the own columns
+  for (int c = q; c < p; c += QCL) {
+    double2* col = A + (size_t)c * ld + m;
+    for (int r = tid; r < p; r += QR_THREADS) col[r] = make_double2(r == c ? s_lam : 0.0, 0.0);
   }
   __syncthreads();
   for (int j = 0; j < p; ++j) {
     const int r1 = m + j;  // last nonzero row of column j
-    double2* cj = A + (size_t)j * ld;
-    // 3. reflector of x = A[j..r1, j]: v = x - alpha e1, alpha = -e^{i arg x0} |x|
-    if (warp == 0) {
-      double s = 0.0;
-      for (int r = j + lane; r <= r1; r += 32) {
-        const double2 x = cj[r];
-        s = fma(x.x, x.x, fma(x.y, x.y, s));
+    const double2* cj = A + (size_t)j * ld;
+    // 3. the owner forms the reflector of x = A[j..r1, j]: v = x - alpha e1,
+    //    alpha = -e^{i arg x0} |x|
+    if (j % QCL == q) {
+      if (warp == 0) {
+        double s = 0.0;
+        for (int r = j + lane; r <= r1; r += 32) {
+          const double2 x = cj[r];
+          s = fma(x.x, x.x, fma(x.y, x.y, s));
+        }
+        s = warp_sum(s);
+        if (lane == 0) s_nx2 = s;
       }
-      s = warp_sum(s);
-      if (lane == 0) s_nx2 = s;
+      __syncthreads();
+      if (tid == 0) {
+        const double nx2 = s_nx2;
+        const double nx = sqrt(nx2);
+        const cplx x0 = ld2(&cj[j]);
+        const double ax0 = cabs(x0);
+        const cplx ph = (ax0 != 0.0) ? (1.0 / ax0) * x0 : C(1.0);
+        const cplx alpha = -(nx * ph);
+        const cplx v0 = x0 - alpha;
+        const double vv = abs2(v0) + (nx2 - ax0 * ax0);
+        beta[j] = (nx == 0.0) ? 0.0 : 2.0 / vv;
+        v0s[j] = make_double2(v0.re, v0.im);
+        const cplx ra = inv(alpha);
+        rdg[j] = make_double2(ra.re, ra.im);
+      }
     }
-    __syncthreads();
-    if (tid == 0) {
-      const double nx2 = s_nx2;
-      const double nx = sqrt(nx2);
-      const cplx x0 = ld2(&cj[j]);
-      const double ax0 = cabs(x0);
-      const cplx ph = (ax0 != 0.0) ? (1.0 / ax0) * x0 : C(1.0);
-      const cplx alpha = -(nx * ph);
-      const cplx v0 = x0 - alpha;
-      const double vv = abs2(v0) + (nx2 - ax0 * ax0);
-      const double b = (nx == 0.0) ? 0.0 : 2.0 / vv;
-      s_beta = b;
-      s_v0 = make_double2(v0.re, v0.im);
-      beta[j] = b;
-      v0s[j] = s_v0;
-      const cplx ra = inv(alpha);
-      rdg[j] = make_double2(ra.re, ra.im);
-    }
-    __syncthreads();
-    // 4. apply (I - beta v v^H) to columns j+1..p-1, rows j..r1
-    const double b = s_beta;
-    const cplx v0 = C(s_v0.x, s_v0.y);
+    cl.sync();  // reflector j published; column j final
+    // 4. apply (I - beta v v^H) to the own columns c > j, rows j..r1
+    const double b = __ldcg(&beta[j]);
+    const double2 v0d = __ldcg(&v0s[j]);
     if (b != 0.0) {
-      for (int c = j + 1 + warp; c < p; c += nw) {
+      const int c0 = j + 1 + ((q - (j + 1)) % QCL + QCL) % QCL;  // first own column > j
+      for (int c = c0 + QCL * warp; c < p; c += QCL * nw) {
         double2* col = A + (size_t)c * ld;
         double sr = 0.0, si = 0.0;
         for (int r = j + lane; r <= r1; r += 32) {
-          const cplx v = (r == j) ? v0 : ld2(&cj[r]);
+          const double2 vr = (r == j) ? v0d : __ldcg(&cj[r]);
+          const cplx v = C(vr.x, vr.y);
           const cplx x = ld2(&col[r]);
           sr = fma(v.re, x.re, fma(v.im, x.im, sr));  // conj(v) x
           si = fma(v.re, x.im, fma(-v.im, x.re, si));
@@ -119,12 +143,13 @@ __global__ void __launch_bounds__(QR_THREADS) k_lsq_qr(Dev D) {
         si = warp_sum(si);
         const cplx w = C(b * sr, b * si);
         for (int r = j + lane; r <= r1; r += 32) {
-          const cplx v = (r == j) ? v0 : ld2(&cj[r]);
+          const double2 vr = (r == j) ? v0d : __ldcg(&cj[r]);
+          const cplx v = C(vr.x, vr.y);
           st2(&col[r], ld2(&col[r]) - v * w);
         }
       }
     }
-    __syncthreads();
+    __syncthreads();  // own columns updated before this CTA forms the next reflector
   }
 }
 
@@ -401,9 +426,8 @@ __global__ void __launch_bounds__(256) k_schur(Dev D) {
 }
 
 cudaError_t launch_lsq(const Dev& D, int max_m, int max_p, int max_c, cudaStream_t s) {
-  const size_t smem = (size_t)max_p * sizeof(double);
   ++g_launches;
-  k_lsq_qr<<<dim3(D.L, D.n_theta), QR_THREADS, smem, s>>>(D);
+  k_lsq_qr<<<dim3(D.L * QCL, D.n_theta), QR_THREADS, 0, s>>>(D);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nbmax = (max_p + WYB - 1) / WYB;
