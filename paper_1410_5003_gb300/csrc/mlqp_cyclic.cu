@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_lu(Dev D, int s, int root) {
   __shared__ int s_piv[CRB];
   __shared__ float2 s_rinv;
   __shared__ int s_sing;
+  __shared__ int s_mpos[32], s_msrc[32], s_mn;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_sing = 0;
   for (int k0 = 0; k0 < n; k0 += CRB) {
@@ -139,22 +140,29 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_lu(Dev D, int s, int root) {
       const cpx<float> ri = inv_fast_t(ldv<float>(&pan[tid * m + tid]));
       udinv[k0 + tid] = make_float2(ri.re, ri.im);
     }
-    // the panel's swaps on every other column; U12 on the columns to its right
+    // the panel's swaps on every other column, as one gather per column from
+    // the composed row map (all loads in flight together); U12 on the columns
+    // to its right
+    if (warp == 0) {
+      int mp, ms;
+      const int nm = compose_row_swaps(k0, w, s_piv, lane, mp, ms);
+      s_mpos[lane] = mp;
+      s_msrc[lane] = ms;
+      if (lane == 0) s_mn = nm;
+    }
+    __syncthreads();
+    const int nmap = s_mn;
     for (int j = tid; j < n; j += CR_THREADS) {
       if (j >= k0 && j < k0 + w) continue;
       float2* col = A + (size_t)j * ld;
-      for (int t = 0; t < w; ++t) {
-        const int p = s_piv[t];
-        if (p != k0 + t) {
-          const float2 x = col[k0 + t];
-          col[k0 + t] = col[p];
-          col[p] = x;
-        }
-      }
+      float2 v[2 * CRB];
+#pragma unroll
+      for (int e = 0; e < 2 * CRB; ++e)
+        if (e < nmap) v[e] = col[s_msrc[e]];
       if (j >= k0 + w) {
         cpx<float> x[CRB];
 #pragma unroll
-        for (int t = 0; t < CRB; ++t) x[t] = (t < w) ? ldv<float>(&col[k0 + t]) : mkc<float>(0.f);
+        for (int t = 0; t < CRB; ++t) x[t] = (t < w) ? mkc<float>(v[t].x, v[t].y) : mkc<float>(0.f);
 #pragma unroll
         for (int t = 1; t < CRB; ++t)
 #pragma unroll
@@ -163,10 +171,18 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_lu(Dev D, int s, int root) {
 #pragma unroll
         for (int t = 0; t < CRB; ++t)
           if (t < w) stv<float>(&col[k0 + t], x[t]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < CRB; ++t)
+          if (t < w) col[k0 + t] = v[t];
       }
+#pragma unroll
+      for (int e = 0; e < 2 * CRB; ++e)  // the displaced rows, slots w .. nmap-1
+        if (e >= w && e < nmap) col[s_mpos[e]] = v[e];
     }
     __syncthreads();
-    // trailing update A22 -= L21 U12 (rows and columns k0 + w .. n-1)
+    // trailing update A22 -= L21 U12 (rows and columns k0 + w .. n-1); each
+    // thread loads its CRT/4 outputs before the products
     const int tr = n - k0 - w;
     const int tx = tid % 64, ty = tid / 64;  // 64 rows x 4 groups of CRT/4 columns
     for (int j0 = 0; j0 < tr; j0 += CRT) {
@@ -175,19 +191,25 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_lu(Dev D, int s, int root) {
         su[t][jj] = (t < w && j0 + jj < tr) ? A[(size_t)(k0 + w + j0 + jj) * ld + k0 + t] : make_float2(0.f, 0.f);
       }
       __syncthreads();
+      const int jb = ty * (CRT / 4);
       for (int r0 = 0; r0 < tr; r0 += 64) {
         const int r = r0 + tx;
         if (r < tr) {
           cpx<float> l[CRB];
 #pragma unroll
           for (int t = 0; t < CRB; ++t) l[t] = (t < w) ? ldv<float>(&pan[t * m + w + r]) : mkc<float>(0.f);
-          for (int jj = ty * (CRT / 4); jj < (ty + 1) * (CRT / 4) && j0 + jj < tr; ++jj) {
-            float2* x = &A[(size_t)(k0 + w + j0 + jj) * ld + k0 + w + r];
-            cpx<float> acc = ldv<float>(x);
+          float2* xb = &A[(size_t)(k0 + w + j0 + jb) * ld + k0 + w + r];
+          cpx<float> acc[CRT / 4];
 #pragma unroll
-            for (int t = 0; t < CRB; ++t) acc = cfms(l[t], ldv<float>(&su[t][jj]), acc);
-            stv<float>(x, acc);
-          }
+          for (int u = 0; u < CRT / 4; ++u)
+            acc[u] = (j0 + jb + u < tr) ? ldv<float>(xb + (size_t)u * ld) : mkc<float>(0.f);
+#pragma unroll
+          for (int u = 0; u < CRT / 4; ++u)
+#pragma unroll
+            for (int t = 0; t < CRB; ++t) acc[u] = cfms(l[t], ldv<float>(&su[t][jb + u]), acc[u]);
+#pragma unroll
+          for (int u = 0; u < CRT / 4; ++u)
+            if (j0 + jb + u < tr) stv<float>(xb + (size_t)u * ld, acc[u]);
         }
       }
       __syncthreads();

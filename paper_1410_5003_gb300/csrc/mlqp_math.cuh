@@ -456,4 +456,34 @@ __device__ __forceinline__ KernL kernels_log(cplx k, const Geo& g, const Hank& h
   return o;
 }
 
+// Row map of w sequential row swaps (row k+r <-> piv[r], r = 0..w-1, piv
+// holding absolute rows >= k+r), as new[pos] = old[src]: slots 0..w-1 are
+// rows k..k+w-1 in order, then the rows displaced from below the block.  One
+// full warp, w <= 16: lane i holds slot i; each swap finds its slot by a
+// ballot.  Returns the number of slots (w <= n <= 2w); lanes >= n hold pos -1.
+__device__ __forceinline__ int compose_row_swaps(int k, int w, const int* piv, int lane, int& pos, int& src) {
+  pos = (lane < w) ? k + lane : -1;
+  src = pos;
+  int n = w;
+  for (int r = 0; r < w; ++r) {
+    const int p2 = piv[r];
+    const unsigned m = __ballot_sync(0xffffffffu, pos == p2);
+    int f;
+    if (m) {
+      f = __ffs(m) - 1;
+    } else {
+      f = n;
+      if (lane == n) {
+        pos = p2;
+        src = p2;
+      }
+      ++n;
+    }
+    const int sr = __shfl_sync(0xffffffffu, src, r), sf = __shfl_sync(0xffffffffu, src, f);
+    if (lane == r) src = sf;
+    if (lane == f) src = sr;
+  }
+  return n;
+}
+
 }  // namespace mlqp

@@ -80,32 +80,11 @@ __device__ __forceinline__ void argmax_merge(unsigned long long& key, int& idx, 
   }
 }
 
-// Row map of the w sequential swaps (row k+r <-> piv[k+r]): new[pos] = old[src],
-// rows k..k+w-1 first (in order), then the displaced rows below the block.
-// One warp: lane i holds slot i (position, source row); each swap finds its
-// slot by a ballot.  Written to PERM (80 ints per angle) for k_lu_prep.
+// Row map of the panel's w swaps (compose_row_swaps), written to PERM (80
+// ints per angle) for k_lu_prep.
 __device__ void write_row_map(const Dev& D, int a, int k, int w, const int* s_piv, int lane) {
-  int mypos = (lane < w) ? k + lane : -1;
-  int mysrc = mypos;
-  int n = w;
-  for (int r = 0; r < w; ++r) {
-    const int p2 = s_piv[r];
-    const unsigned m = __ballot_sync(0xffffffffu, mypos == p2);
-    int f;
-    if (m) {
-      f = __ffs(m) - 1;
-    } else {
-      f = n;
-      if (lane == n) {
-        mypos = p2;
-        mysrc = p2;
-      }
-      ++n;
-    }
-    const int sr = __shfl_sync(0xffffffffu, mysrc, r), sf = __shfl_sync(0xffffffffu, mysrc, f);
-    if (lane == r) mysrc = sf;
-    if (lane == f) mysrc = sr;
-  }
+  int mypos, mysrc;
+  const int n = compose_row_swaps(k, w, s_piv, lane, mypos, mysrc);
   int* pm = D.PERM + 80 * a;
   if (lane == 0) pm[0] = n;
   if (lane < n) {
