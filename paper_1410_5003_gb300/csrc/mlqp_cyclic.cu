@@ -19,6 +19,7 @@
 // dimension n) hold the current couplings, then G_i (left), H_i (right) and
 // the LU factors with their pivots (LUPIV) and reciprocal pivots (UDINV32).
 #include <algorithm>
+#include <cooperative_groups.h>
 
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
@@ -26,6 +27,7 @@
 
 namespace mlqp {
 
+namespace cg = cooperative_groups;
 extern thread_local long g_launches;
 constexpr int CR_THREADS = 256;
 constexpr int CRB = 16;   // LU panel width
@@ -53,25 +55,43 @@ __device__ __forceinline__ float2* cr_save(const Dev& D, int slot, int side, int
 
 // ---------------------------------------------------------------------------
 // LU with row pivoting of the diagonal block of interface i = s + 2s x
-// (blockIdx.x; i = 0 for the root), in place, one CTA per (interface, angle):
-// panels of CRB columns factored in shared memory (pivot: largest
-// |re| + |im|, smallest row on ties), their swaps applied to the other
-// columns, U12 by forward substitution, trailing update in CRT-column tiles.
+// (x = blockIdx.x / cluster size; i = 0 for the root), in place, one thread-
+// block cluster of 1..8 CTAs per (interface, angle), blocked by panels of CRB
+// columns:
+//  - CTA 0 loads the panel into shared memory and factors it (pivot: largest
+//    |re| + |im|, smallest row on ties; one thread per row), then writes it
+//    back with its pivots and reciprocal pivots;
+//  - cluster barrier; every CTA composes the panel's swaps into a row map and
+//    applies it, as one gather per column, to its own columns (j mod CL = q),
+//    with U12 by forward substitution on those right of the panel;
+//  - cluster barrier; the trailing update in 64 x 64 tiles, tile t to CTA
+//    t mod CL, each thread loading its outputs before the products;
+//  - cluster barrier.
+// Data written by another CTA of the cluster is read through L2 (__ldcg).
+// The arithmetic per element is that of a one-CTA factorisation.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ cpx<float> ldcg_c(const float2* p) {
+  const float2 v = __ldcg(p);
+  return mkc<float>(v.x, v.y);
+}
+
 __global__ void __launch_bounds__(CR_THREADS) k_cr_lu(Dev D, int s, int root) {
-  const int i = root ? 0 : s + 2 * s * blockIdx.x;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  const int i = root ? 0 : s + 2 * s * (int)(blockIdx.x / CL);
   const int a = blockIdx.y;
-  if (i >= D.I) return;
+  if (i >= D.I) return;  // whole clusters only: x / CL is uniform in a cluster
   const IfaceDesc f = D.ifc[i];
   const int n = f.n, ld = n;
   float2* A = cr_diag(D, i, a);
   int* piv = D.LUPIV + a * D.piv_stride + f.eta_off;
   float2* udinv = D.UDINV32 + a * D.piv_stride + f.eta_off;
   extern __shared__ __align__(16) unsigned char cr_raw[];
-  float2* pan = reinterpret_cast<float2*>(cr_raw);  // m x CRB, column-major, leading dimension m
+  float2* pan = reinterpret_cast<float2*>(cr_raw);  // m x CRB, column-major, leading dimension m (CTA 0)
   __shared__ float2 su[CRB][CRT + 1];
-  __shared__ unsigned s_key[CR_THREADS / 32], s_pos[CR_THREADS / 32];
+  __shared__ float2 s_l11[CRB][CRB];
   __shared__ int s_piv[CRB];
+  __shared__ unsigned s_key[CR_THREADS / 32], s_pos[CR_THREADS / 32];
   __shared__ float2 s_rinv;
   __shared__ int s_sing;
   __shared__ int s_mpos[32], s_msrc[32], s_mn;
@@ -79,86 +99,96 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_lu(Dev D, int s, int root) {
   if (tid == 0) s_sing = 0;
   for (int k0 = 0; k0 < n; k0 += CRB) {
     const int w = min(CRB, n - k0), m = n - k0;
-    for (int e = tid; e < m * w; e += CR_THREADS) {
-      const int r = e % m, c = e / m;
-      pan[c * m + r] = A[(size_t)(k0 + c) * ld + k0 + r];
-    }
-    __syncthreads();
-    for (int c = 0; c < w; ++c) {
-      unsigned kb = 0, pb = 0xffffffffu;
-      for (int r = c + tid; r < m; r += CR_THREADS) {
-        const unsigned kk = pivot_key32(ldv<float>(&pan[c * m + r]));
-        if (kk > kb || pb == 0xffffffffu) {
-          kb = kk;
-          pb = (unsigned)r;
-        }
-      }
-      const unsigned km = __reduce_max_sync(0xffffffffu, (pb != 0xffffffffu) ? kb : 0u);
-      const unsigned pm = __reduce_min_sync(0xffffffffu, (pb != 0xffffffffu && kb == km) ? pb : 0xffffffffu);
-      if (lane == 0) {
-        s_key[warp] = km;
-        s_pos[warp] = pm;
+    if (q == 0) {
+      for (int e = tid; e < m * w; e += CR_THREADS) {
+        const int r = e % m, c = e / m;
+        pan[c * m + r] = __ldcg(&A[(size_t)(k0 + c) * ld + k0 + r]);
       }
       __syncthreads();
-      if (warp == 0) {
-        const bool ok = lane < CR_THREADS / 32 && s_pos[lane] != 0xffffffffu;
-        const unsigned k2 = ok ? s_key[lane] : 0u;
-        const unsigned kx = __reduce_max_sync(0xffffffffu, k2);
-        const unsigned px = __reduce_min_sync(0xffffffffu, (ok && k2 == kx) ? s_pos[lane] : 0xffffffffu);
-        const int p = (int)px;
-        if (lane < w && p != c) {
-          const float2 t = pan[lane * m + c];
-          pan[lane * m + c] = pan[lane * m + p];
-          pan[lane * m + p] = t;
+      for (int c = 0; c < w; ++c) {
+        unsigned kb = 0, pb = 0xffffffffu;
+        for (int r = c + tid; r < m; r += CR_THREADS) {
+          const unsigned kk = pivot_key32(ldv<float>(&pan[c * m + r]));
+          if (kk > kb || pb == 0xffffffffu) {
+            kb = kk;
+            pb = (unsigned)r;
+          }
         }
-        __syncwarp();
+        const unsigned km = __reduce_max_sync(0xffffffffu, (pb != 0xffffffffu) ? kb : 0u);
+        const unsigned pm = __reduce_min_sync(0xffffffffu, (pb != 0xffffffffu && kb == km) ? pb : 0xffffffffu);
         if (lane == 0) {
-          s_piv[c] = k0 + p;
-          const cpx<float> ri = inv_fast_t(ldv<float>(&pan[c * m + c]));
-          s_rinv = make_float2(ri.re, ri.im);
-          if (!pivot_ok32(kx, 0.0f)) s_sing = 1;
+          s_key[warp] = km;
+          s_pos[warp] = pm;
         }
-      }
-      __syncthreads();
-      const cpx<float> ip = ldv<float>(&s_rinv);
-      for (int r = c + 1 + tid; r < m; r += CR_THREADS) {
-        const cpx<float> l = ldv<float>(&pan[c * m + r]) * ip;
-        stv<float>(&pan[c * m + r], l);
-        for (int cc = c + 1; cc < w; ++cc) {
-          float2* x = &pan[cc * m + r];
-          stv<float>(x, cfms(l, ldv<float>(&pan[cc * m + c]), ldv<float>(x)));
+        __syncthreads();
+        if (warp == 0) {
+          const bool ok = lane < CR_THREADS / 32 && s_pos[lane] != 0xffffffffu;
+          const unsigned k2 = ok ? s_key[lane] : 0u;
+          const unsigned kx = __reduce_max_sync(0xffffffffu, k2);
+          const unsigned px = __reduce_min_sync(0xffffffffu, (ok && k2 == kx) ? s_pos[lane] : 0xffffffffu);
+          const int p = (int)px;
+          if (lane < w && p != c) {
+            const float2 t = pan[lane * m + c];
+            pan[lane * m + c] = pan[lane * m + p];
+            pan[lane * m + p] = t;
+          }
+          __syncwarp();
+          if (lane == 0) {
+            s_piv[c] = k0 + p;
+            const cpx<float> ri = inv_fast_t(ldv<float>(&pan[c * m + c]));
+            s_rinv = make_float2(ri.re, ri.im);
+            if (!pivot_ok32(kx, 0.0f)) s_sing = 1;
+          }
         }
+        __syncthreads();
+        const cpx<float> ip = ldv<float>(&s_rinv);
+        for (int r = c + 1 + tid; r < m; r += CR_THREADS) {
+          const cpx<float> l = ldv<float>(&pan[c * m + r]) * ip;
+          stv<float>(&pan[c * m + r], l);
+          for (int cc = c + 1; cc < w; ++cc) {
+            float2* x = &pan[cc * m + r];
+            stv<float>(x, cfms(l, ldv<float>(&pan[cc * m + c]), ldv<float>(x)));
+          }
+        }
+        __syncthreads();
       }
-      __syncthreads();
+      for (int e = tid; e < m * w; e += CR_THREADS) {
+        const int r = e % m, c = e / m;
+        A[(size_t)(k0 + c) * ld + k0 + r] = pan[c * m + r];
+      }
+      if (tid < w) {
+        piv[k0 + tid] = s_piv[tid];
+        const cpx<float> ri = inv_fast_t(ldv<float>(&pan[tid * m + tid]));
+        udinv[k0 + tid] = make_float2(ri.re, ri.im);
+      }
     }
-    for (int e = tid; e < m * w; e += CR_THREADS) {
-      const int r = e % m, c = e / m;
-      A[(size_t)(k0 + c) * ld + k0 + r] = pan[c * m + r];
-    }
-    if (tid < w) {
-      piv[k0 + tid] = s_piv[tid];
-      const cpx<float> ri = inv_fast_t(ldv<float>(&pan[tid * m + tid]));
-      udinv[k0 + tid] = make_float2(ri.re, ri.im);
-    }
-    // the panel's swaps on every other column, as one gather per column from
+    cl.sync();  // panel, pivots in place
+    // the panel's swaps on the other columns, as one gather per column from
     // the composed row map (all loads in flight together); U12 on the columns
-    // to its right
+    // right of the panel
     if (warp == 0) {
+      const int pv = (lane < w) ? __ldcg(&piv[k0 + lane]) : 0;
+      if (lane < CRB) s_piv[lane] = pv;
+      __syncwarp();
       int mp, ms;
       const int nm = compose_row_swaps(k0, w, s_piv, lane, mp, ms);
       s_mpos[lane] = mp;
       s_msrc[lane] = ms;
       if (lane == 0) s_mn = nm;
     }
+    for (int e = tid; e < CRB * CRB; e += CR_THREADS) {  // unit-lower L11 (row t, column q2)
+      const int t = e % CRB, q2 = e / CRB;
+      s_l11[q2][t] = (t < w && q2 < w) ? __ldcg(&A[(size_t)(k0 + q2) * ld + k0 + t]) : make_float2(0.f, 0.f);
+    }
     __syncthreads();
     const int nmap = s_mn;
-    for (int j = tid; j < n; j += CR_THREADS) {
+    for (int j = q + CL * tid; j < n; j += CL * CR_THREADS) {
       if (j >= k0 && j < k0 + w) continue;
       float2* col = A + (size_t)j * ld;
       float2 v[2 * CRB];
 #pragma unroll
       for (int e = 0; e < 2 * CRB; ++e)
-        if (e < nmap) v[e] = col[s_msrc[e]];
+        if (e < nmap) v[e] = __ldcg(&col[s_msrc[e]]);
       if (j >= k0 + w) {
         cpx<float> x[CRB];
 #pragma unroll
@@ -166,8 +196,8 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_lu(Dev D, int s, int root) {
 #pragma unroll
         for (int t = 1; t < CRB; ++t)
 #pragma unroll
-          for (int q = 0; q < t; ++q)
-            if (t < w) x[t] = cfms(ldv<float>(&pan[q * m + t]), x[q], x[t]);
+          for (int q2 = 0; q2 < t; ++q2)
+            if (t < w) x[t] = cfms(ldv<float>(&s_l11[q2][t]), x[q2], x[t]);
 #pragma unroll
         for (int t = 0; t < CRB; ++t)
           if (t < w) stv<float>(&col[k0 + t], x[t]);
@@ -180,42 +210,44 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_lu(Dev D, int s, int root) {
       for (int e = 0; e < 2 * CRB; ++e)  // the displaced rows, slots w .. nmap-1
         if (e >= w && e < nmap) col[s_mpos[e]] = v[e];
     }
-    __syncthreads();
-    // trailing update A22 -= L21 U12 (rows and columns k0 + w .. n-1); each
-    // thread loads its CRT/4 outputs before the products
+    cl.sync();  // swaps and U12 in place
+    // trailing update A22 -= L21 U12 (rows and columns k0 + w .. n-1)
     const int tr = n - k0 - w;
+    const int nrt = (tr + 63) / 64, nct = (tr + CRT - 1) / CRT;
     const int tx = tid % 64, ty = tid / 64;  // 64 rows x 4 groups of CRT/4 columns
-    for (int j0 = 0; j0 < tr; j0 += CRT) {
+    const int jb = ty * (CRT / 4);
+    for (int tile = q; tile < nrt * nct; tile += CL) {
+      const int r0 = 64 * (tile % nrt), j0 = CRT * (tile / nrt);
       for (int e = tid; e < CRB * CRT; e += CR_THREADS) {  // rows t >= w zero-filled
         const int t = e / CRT, jj = e % CRT;
-        su[t][jj] = (t < w && j0 + jj < tr) ? A[(size_t)(k0 + w + j0 + jj) * ld + k0 + t] : make_float2(0.f, 0.f);
+        su[t][jj] = (t < w && j0 + jj < tr) ? __ldcg(&A[(size_t)(k0 + w + j0 + jj) * ld + k0 + t])
+                                            : make_float2(0.f, 0.f);
       }
       __syncthreads();
-      const int jb = ty * (CRT / 4);
-      for (int r0 = 0; r0 < tr; r0 += 64) {
-        const int r = r0 + tx;
-        if (r < tr) {
-          cpx<float> l[CRB];
+      const int r = r0 + tx;
+      if (r < tr) {
+        cpx<float> l[CRB];
 #pragma unroll
-          for (int t = 0; t < CRB; ++t) l[t] = (t < w) ? ldv<float>(&pan[t * m + w + r]) : mkc<float>(0.f);
-          float2* xb = &A[(size_t)(k0 + w + j0 + jb) * ld + k0 + w + r];
-          cpx<float> acc[CRT / 4];
+        for (int t = 0; t < CRB; ++t)
+          l[t] = (t < w) ? ldcg_c(&A[(size_t)(k0 + t) * ld + k0 + w + r]) : mkc<float>(0.f);
+        float2* xb = &A[(size_t)(k0 + w + j0 + jb) * ld + k0 + w + r];
+        cpx<float> acc[CRT / 4];
 #pragma unroll
-          for (int u = 0; u < CRT / 4; ++u)
-            acc[u] = (j0 + jb + u < tr) ? ldv<float>(xb + (size_t)u * ld) : mkc<float>(0.f);
+        for (int u = 0; u < CRT / 4; ++u)
+          acc[u] = (j0 + jb + u < tr) ? ldcg_c(xb + (size_t)u * ld) : mkc<float>(0.f);
 #pragma unroll
-          for (int u = 0; u < CRT / 4; ++u)
+        for (int u = 0; u < CRT / 4; ++u)
 #pragma unroll
-            for (int t = 0; t < CRB; ++t) acc[u] = cfms(l[t], ldv<float>(&su[t][jb + u]), acc[u]);
+          for (int t = 0; t < CRB; ++t) acc[u] = cfms(l[t], ldv<float>(&su[t][jb + u]), acc[u]);
 #pragma unroll
-          for (int u = 0; u < CRT / 4; ++u)
-            if (j0 + jb + u < tr) stv<float>(xb + (size_t)u * ld, acc[u]);
-        }
+        for (int u = 0; u < CRT / 4; ++u)
+          if (j0 + jb + u < tr) stv<float>(xb + (size_t)u * ld, acc[u]);
       }
       __syncthreads();
     }
+    cl.sync();  // trailing block updated
   }
-  if (tid == 0 && s_sing) atomicExch(D.STATUS, MLQP_ESINGULAR_CR);
+  if (q == 0 && tid == 0 && s_sing) atomicExch(D.STATUS, MLQP_ESINGULAR_CR);
 }
 
 // Composed row permutation of the LU of interface i (PERMV[j] = source row of
@@ -558,6 +590,32 @@ int cr_slots(int I) {
   return slots;
 }
 
+// k_cr_lu on clusters of CL CTAs per block: as many SMs per block as the
+// level leaves free (at most 8, the portable cluster size), one CTA per SM.
+static cudaError_t launch_cr_lu(const Dev& D, int s, int root, int nblk, int nt, size_t pan, cudaStream_t st) {
+  static int n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
+  }
+  int cl = n_sm / std::max(1, nblk * nt);
+  cl = cl >= 8 ? 8 : cl >= 4 ? 4 : cl >= 2 ? 2 : 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblk * cl, nt);
+  cfg.blockDim = dim3(CR_THREADS);
+  cfg.dynamicSmemBytes = pan;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_cr_lu, D, s, root);
+}
+
 cudaError_t launch_cr_factor(const Dev& D, int n, int* permv, cudaStream_t st) {
   const int I = D.I, nt = D.n_theta;
   const size_t pan = (size_t)n * CRB * sizeof(float2);
@@ -567,18 +625,18 @@ cudaError_t launch_cr_factor(const Dev& D, int n, int* permv, cudaStream_t st) {
   for (int s = 1; s < I; s *= 2) {
     const int nE = cr_count(s, 2 * s, I), nS = cr_count(0, 2 * s, I);
     g_launches += 5;
-    k_cr_lu<<<dim3(nE, nt), CR_THREADS, pan, st>>>(D, s, 0);
+    cudaError_t e = launch_cr_lu(D, s, 0, nE, nt, pan, st);
+    if (e != cudaSuccess) return e;
     k_cr_perm<<<dim3((nE + 63) / 64, nt), 64, 0, st>>>(D, s, 0, nE, permv);
     k_cr_trsm<<<dim3((2 * n + cw - 1) / cw, nE, nt), CR_THREADS, trs, st>>>(D, s, cw, permv);
     k_cr_save<<<dim3(std::max(1, (n * n + 255) / 256 / 4), nS, nt), 256, 0, st>>>(D, s, slot_base);
     const int tiles = ((n + UT32 - 1) / UT32) * ((n + UT32 - 1) / UT32);
     k_cr_update<<<dim3(tiles, 3 * nS, nt), 256, 0, st>>>(D, s, slot_base);
     slot_base += nS;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   g_launches += 2;
-  k_cr_lu<<<dim3(1, nt), CR_THREADS, pan, st>>>(D, 0, 1);
+  if (cudaError_t e = launch_cr_lu(D, 0, 1, 1, nt, pan, st); e != cudaSuccess) return e;
   k_cr_perm<<<dim3(1, nt), 64, 0, st>>>(D, 0, 1, 1, permv);
   return cudaGetLastError();
 }
