@@ -323,6 +323,7 @@ def main():
 
     prob = problem(rank)
     ctx = mlqp.Context(prob, device=dev)
+    tuned = ctx.autotune()  # launch shapes timed on this problem (untimed setup)
     stream = ctx.stream
     out = ctx.outputs()
     n = [2 * f.N for f in prob.ifaces]
@@ -392,7 +393,9 @@ def main():
                 "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "interfaces": prob.I, "angles": nth, "nodes_per_interface": 120,
-                           "unknowns_per_angle": int(sum(n)), "l2": "flushed between steps (256 MB write)"},
+                           "unknowns_per_angle": int(sum(n)), "l2": "flushed between steps (256 MB write)",
+                           "launch_shapes": {"qr_cluster": int(tuned["qr_cluster"]),
+                                             "angle_groups": int(tuned["angle_groups"]), "source": "mlqp_autotune"}},
                 "stage_ms": stage_ms, "dominant_stage": dominant,
                 "roofline": {"bound": "alu", "kernel": "block-tridiagonal sweep (k_lu_panel/k_lu_prep/k_lu_update)",
                              "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
@@ -408,6 +411,7 @@ def main():
     def time_mixed(solver):
         mctx = mlqp.Context(prob, device=dev, precision=mlqp.MLQP_MIXED, max_refine=10, refine_tol=1e-15,
                             block_solver=solver)
+        mtuned = mctx.autotune()
         mout = mctx.outputs()
         for _ in range(args.warmup):
             mctx.solve_device(mout)
@@ -442,6 +446,8 @@ def main():
                "backward_error": max(float(mctx.block(mlqp.BLK_REFINE, 1, a)[0]) for a in range(nth)),
                "max_rel_amp_diff_vs_fp64": diff,
                "block_solver": "sweep" if solver == mlqp.MLQP_SWEEP else "cyclic reduction",
+               "launch_shapes": {k: (None if v != v else int(v)) for k, v in mtuned.items()
+                                 if k in ("qr_cluster", "angle_groups", "cr_cluster_cap")},
                "dtype": "f32 Schur/LU + f64 refinement (fill, least squares, residuals in f64)"}
         mctx.close()
         return res

@@ -187,6 +187,23 @@ mlqp_status mlqp_run_stage(mlqp_ctx* ctx, int stage);
  * (count or range), MLQP_ESTATE (not bound). */
 mlqp_status mlqp_set_angles(mlqp_ctx* ctx, const double* theta, int n_theta);
 
+/* Chooses the launch shapes of a bound context by timing candidates on its
+ * own problem (each timed stage preceded by the stages it depends on, so
+ * this costs several solves): the CTAs per least-squares QR cluster (1, 2,
+ * 4, 8), the number of angle groups (streams) of the block solve (1 to
+ * min(n_theta, 4)) and, with MLQP_CYCLIC, the largest cluster of the
+ * cyclic-reduction LU (1, 2, 4, 8).  The fastest of each is kept for later
+ * solves.  None of them changes the arithmetic: results are bitwise those of
+ * the default shapes.  report (may be NULL) receives MLQP_TUNE_REPORT
+ * doubles: [QR cluster chosen, LSQ-stage ms for 1, 2, 4, 8; angle groups
+ * chosen, block-solve ms for 1, 2, 3, 4 groups; CR cluster cap chosen,
+ * block-solve ms for 1, 2, 4, 8], NaN where a candidate does not apply.  Sec. 3.4's angle
+ * sweep is the intended use: tune on the first chunk, then mlqp_set_angles.
+ * Errors: MLQP_ESTATE (not bound), MLQP_EINVAL (report too short),
+ * MLQP_ECUDA. */
+enum { MLQP_TUNE_REPORT = 15 };
+mlqp_status mlqp_autotune(mlqp_ctx* ctx, double* report, int report_len);
+
 /* Location of a workspace block (for inspection by tests):
  *   MLQP_BLK_ROW    interface i (1..I), angle a: the block row
  *                   [A_{i,i-1} | A_{i,i} | A_{i,i+1}] (A' after the Schur

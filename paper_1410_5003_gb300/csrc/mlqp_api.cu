@@ -2,6 +2,7 @@
 // descriptor upload and the ordered launches of the device path.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -77,6 +78,9 @@ struct mlqp_ctx {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec[MLQP_STAGE_RECOVER + 1] = {};
   long glaunches[MLQP_STAGE_RECOVER + 1] = {};
+  // launch shapes (mlqp_autotune): QR cluster size, cyclic-reduction LU
+  // cluster cap, angle groups of the sweep (0: min(n_theta, MAX_ANGLE_STREAMS))
+  int qr_cl = 8, cr_cl_max = 8, angle_groups = 0;
 };
 
 static void drop_graphs(mlqp_ctx* c) {
@@ -132,7 +136,8 @@ static cudaError_t make_angle_streams(mlqp_ctx* c) {
     c->astr_dev = dev;
   }
   A.main = c->stream;
-  A.n = c->n_theta < MAX_ANGLE_STREAMS ? c->n_theta : MAX_ANGLE_STREAMS;
+  const int gmax = c->angle_groups > 0 ? std::min(c->angle_groups, MAX_ANGLE_STREAMS) : MAX_ANGLE_STREAMS;
+  A.n = c->n_theta < gmax ? c->n_theta : gmax;
   for (int g = 0, a = 0; g < A.n; ++g) {
     A.a0[g] = a;
     A.na[g] = c->n_theta / A.n + (g < c->n_theta % A.n ? 1 : 0);
@@ -502,6 +507,8 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   D.cut_a = q.cut_a;
   D.cut_b = q.cut_b;
   D.rcond = q.lsq_rcond;
+  D.qr_cl = c->qr_cl;
+  D.cr_cl_max = c->cr_cl_max;
   D.yU = q.gap_U;  // the geometry kernel turns the gaps into y_U, y_D (stored in scal)
   D.yD = q.gap_D;
   D.maxN = c->maxN;
@@ -688,6 +695,100 @@ mlqp_status mlqp_run_stage(mlqp_ctx* c, int stage) {
   if ((e = cudaGraphLaunch(c->gexec[stage], c->stream)) != cudaSuccess) return cuda_fail(c, e, "stage launch");
   c->launches += c->glaunches[stage];
   return MLQP_OK;
+}
+
+// Device time of `stage` (best of reps), each run preceded by the stages
+// before it (untimed) so that it sees the inputs of a solve.
+static mlqp_status time_stage(mlqp_ctx* c, int stage, int reps, double* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  mlqp_status st = MLQP_OK;
+  double best = INFINITY;
+  for (int r = 0; r < reps && st == MLQP_OK && e == cudaSuccess; ++r) {
+    for (int s0 = MLQP_STAGE_GEOM; s0 < stage && st == MLQP_OK; ++s0) st = mlqp_run_stage(c, s0);
+    if (st != MLQP_OK) break;
+    if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) break;
+    if ((st = mlqp_run_stage(c, stage)) != MLQP_OK) break;
+    if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float t = 0.f;
+    if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
+    if (r > 0 || reps == 1) best = std::min(best, (double)t);  // the first run also captures the graph
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st != MLQP_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune timing");
+  *ms = best;
+  return MLQP_OK;
+}
+
+// Applies the context's launch shapes: re-binds in place and drops the
+// captured graphs, which hold the old shapes.
+static mlqp_status apply_shapes(mlqp_ctx* c) {
+  drop_graphs(c);
+  return mlqp_bind(c, c->ws, c->ws_bytes, c->stream);
+}
+
+mlqp_status mlqp_autotune(mlqp_ctx* c, double* report, int report_len) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  if (report && report_len < MLQP_TUNE_REPORT) return fail(c, MLQP_EINVAL, "report needs %d doubles", MLQP_TUNE_REPORT);
+  double rep[MLQP_TUNE_REPORT];
+  for (double& x : rep) x = NAN;
+  mlqp_status st = MLQP_OK;
+  // 1. least-squares QR cluster size
+  {
+    const int cand[4] = {1, 2, 4, 8};
+    int best = c->qr_cl;
+    double tb = INFINITY;
+    for (int q = 0; q < 4 && st == MLQP_OK; ++q) {
+      c->qr_cl = cand[q];
+      double t = 0;
+      if ((st = apply_shapes(c)) == MLQP_OK && (st = time_stage(c, MLQP_STAGE_LSQ, 3, &t)) == MLQP_OK) {
+        rep[1 + q] = t;
+        if (t < tb) tb = t, best = cand[q];
+      }
+    }
+    c->qr_cl = best;
+    rep[0] = best;
+  }
+  // 2. angle groups of the sweep: every count from 1 to min(n_theta, MAX_ANGLE_STREAMS)
+  if (st == MLQP_OK) {
+    int best = c->angle_groups;
+    double tb = INFINITY;
+    for (int g = 1; g <= std::min(c->n_theta, MAX_ANGLE_STREAMS) && st == MLQP_OK; ++g) {
+      c->angle_groups = g;
+      double t = 0;
+      if ((st = apply_shapes(c)) == MLQP_OK && (st = time_stage(c, MLQP_STAGE_SWEEP, 3, &t)) == MLQP_OK) {
+        rep[5 + g] = t;
+        if (t < tb) tb = t, best = g;
+      }
+    }
+    c->angle_groups = best;
+    rep[5] = best;
+  }
+  // 3. cluster cap of the cyclic-reduction LU
+  if (st == MLQP_OK && c->prm.block_solver == MLQP_CYCLIC) {
+    const int cand[4] = {1, 2, 4, 8};
+    int best = c->cr_cl_max;
+    double tb = INFINITY;
+    for (int q = 0; q < 4 && st == MLQP_OK; ++q) {
+      c->cr_cl_max = cand[q];
+      double t = 0;
+      if ((st = apply_shapes(c)) == MLQP_OK && (st = time_stage(c, MLQP_STAGE_SWEEP, 3, &t)) == MLQP_OK) {
+        rep[11 + q] = t;
+        if (t < tb) tb = t, best = cand[q];
+      }
+    }
+    c->cr_cl_max = best;
+    rep[10] = best;
+  }
+  const mlqp_status sa = apply_shapes(c);
+  if (st == MLQP_OK) st = sa;
+  if (st == MLQP_OK && report) std::copy(rep, rep + MLQP_TUNE_REPORT, report);
+  return st;
 }
 
 mlqp_status mlqp_solve_device(mlqp_ctx* c, void* d_eta, void* d_aU, void* d_aD, void* d_flux) {

@@ -591,7 +591,8 @@ int cr_slots(int I) {
 }
 
 // k_cr_lu on clusters of CL CTAs per block: as many SMs per block as the
-// level leaves free (at most 8, the portable cluster size), one CTA per SM.
+// level leaves free, up to D.cr_cl_max (at most 8, the portable cluster
+// size), rounded down to a power of two.
 static cudaError_t launch_cr_lu(const Dev& D, int s, int root, int nblk, int nt, size_t pan, cudaStream_t st) {
   static int n_sm = 0;
   if (n_sm == 0) {
@@ -599,7 +600,7 @@ static cudaError_t launch_cr_lu(const Dev& D, int s, int root, int nblk, int nt,
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
   }
-  int cl = n_sm / std::max(1, nblk * nt);
+  int cl = std::min(n_sm / std::max(1, nblk * nt), std::max(1, D.cr_cl_max));
   cl = cl >= 8 ? 8 : cl >= 4 ? 4 : cl >= 2 ? 2 : 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nblk * cl, nt);

@@ -146,6 +146,9 @@ struct Dev {
   double* FLUX;                        // n_theta
   int* STATUS;
   const SchurTask* tasks; int n_tasks;
+  // launch shapes (host side; set by mlqp_autotune, defaults at bind)
+  int qr_cl;      // CTAs per least-squares QR cluster (1..8)
+  int cr_cl_max;  // largest cluster of the cyclic-reduction LU (1..8)
 };
 
 }  // namespace mlqp

@@ -10,6 +10,7 @@
 // obtained by a blocked back substitution (rows x columns parallel).
 // The Schur updates are batched complex GEMM tiles with 3M products
 // (three real products per complex product), in FP64.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "mlqp_internal.h"
@@ -37,19 +38,17 @@ __device__ __forceinline__ double warp_sum(double v) {
 // only: below row m+j column j is still zero (the rows m+j'+1.. of the lam I
 // block are untouched by the earlier reflectors j' < j).
 //
-// A cluster of QCL CTAs factors one (layer, angle): column c belongs to CTA
-// c mod QCL, which alone writes it.  Per column j the owner forms reflector j
+// A cluster of CL CTAs (1..8, D.qr_cl) factors one (layer, angle): column c
+// belongs to CTA c mod CL, which alone writes it.  Per column j the owner forms reflector j
 // from its own (already updated) column and publishes beta, v0 and 1/R_jj in
 // LAUX; one cluster barrier; then every CTA applies the reflector to its own
 // columns c > j, reading column j through L2 (__ldcg).  Each column's
 // arithmetic is that of a single-CTA factorisation, warp for warp, so the
-// result does not depend on QCL.  The end layers ([Q'; lam I] of about
-// 400 x 111) were FP64-bound on one SM; QCL SMs share them now.
-constexpr int QCL = 8;
-
-__global__ void __cluster_dims__(QCL, 1, 1) __launch_bounds__(QR_THREADS) k_lsq_qr(Dev D) {
+// result does not depend on CL.  The end layers ([Q'; lam I] of about
+// 400 x 111) were FP64-bound on one SM; CL SMs share them now.
+__global__ void __launch_bounds__(QR_THREADS) k_lsq_qr(Dev D) {
   cg::cluster_group cl = cg::this_cluster();
-  const int q = (int)cl.block_rank();
+  const int QCL = (int)cl.num_blocks(), q = (int)cl.block_rank();
   const int jl = blockIdx.x / QCL, a = blockIdx.y;
   const LayerDesc L = D.lay[jl];
   const int m = L.m, p = L.p, ld = L.ldq;
@@ -427,7 +426,22 @@ __global__ void __launch_bounds__(256) k_schur(Dev D) {
 
 cudaError_t launch_lsq(const Dev& D, int max_m, int max_p, int max_c, cudaStream_t s) {
   ++g_launches;
-  k_lsq_qr<<<dim3(D.L * QCL, D.n_theta), QR_THREADS, 0, s>>>(D);
+  {
+    const int ql = std::min(8, std::max(1, D.qr_cl));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(D.L * ql, D.n_theta);
+    cfg.blockDim = dim3(QR_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = ql;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_lsq_qr, D);
+    if (e != cudaSuccess) return e;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nbmax = (max_p + WYB - 1) / WYB;

@@ -68,6 +68,8 @@ def load(path: str = LIB_PATH):
     lib.mlqp_bind.restype = I
     lib.mlqp_set_angles.argtypes = [P, ct.POINTER(D), I]
     lib.mlqp_set_angles.restype = I
+    lib.mlqp_autotune.argtypes = [P, ct.POINTER(D), I]
+    lib.mlqp_autotune.restype = I
     lib.mlqp_solve_device.argtypes = [P, V, V, V, V]
     lib.mlqp_solve_device.restype = I
     lib.mlqp_check_device.argtypes = [P]
@@ -94,7 +96,8 @@ def load(path: str = LIB_PATH):
     return lib
 
 
-EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_set_angles", "mlqp_solve_device",
+EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_set_angles", "mlqp_autotune",
+            "mlqp_solve_device",
             "mlqp_check_device", "mlqp_solve", "mlqp_run_stage", "mlqp_block_info", "mlqp_last_error",
             "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes",
             "mlqp_lsq_solve_noalloc"]
@@ -189,6 +192,18 @@ class Context:
         """New incidence angles (as many as at setup) for the next solves."""
         th = np.ascontiguousarray(theta, dtype=np.float64)
         _check(self.ctx, self.lib.mlqp_set_angles(self.ctx, _dptr(th), len(th)))
+
+    TUNE_REPORT = 15
+
+    def autotune(self):
+        """mlqp_autotune: times candidate launch shapes on this problem and
+        keeps the fastest; returns the chosen shapes and the timings (ms)."""
+        rep = (ct.c_double * self.TUNE_REPORT)()
+        _check(self.ctx, self.lib.mlqp_autotune(self.ctx, rep, self.TUNE_REPORT))
+        r = list(rep)
+        return {"qr_cluster": r[0], "lsq_ms": dict(zip((1, 2, 4, 8), r[1:5])),
+                "angle_groups": r[5], "sweep_ms_by_groups": dict(zip((1, 2, 3, 4), r[6:10])),
+                "cr_cluster_cap": r[10], "sweep_ms_by_cr_cluster": dict(zip((1, 2, 4, 8), r[11:15]))}
 
     def close(self):
         if self.ctx:

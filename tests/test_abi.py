@@ -168,6 +168,18 @@ def test_refine_method_validation(M):
     assert st(M.MLQP_MIXED, 2) == M.MLQP_EINVAL
 
 
+def test_autotune_needs_a_bound_context(M):
+    """mlqp_autotune refuses an unbound context before any device work."""
+    lib = M.load()
+    from workloads import small_stack
+    import ctypes as ct
+    ctx, _ = M.mlqp_setup(small_stack(I=2))
+    rep = (ct.c_double * 15)()
+    assert lib.mlqp_autotune(ctx, rep, 15) == M.MLQP_ESTATE
+    assert lib.mlqp_autotune(None, rep, 15) == M.MLQP_EINVAL
+    lib.mlqp_destroy(ctx)
+
+
 def test_set_angles_validation_without_a_device(M):
     """mlqp_set_angles checks count and range before anything else, and needs
     a bound context (none exists here, so no device work is reached)."""

@@ -441,6 +441,31 @@ def test_gmres_refinement_where_plain_refinement_stalls(M):
     ctx.close()
 
 
+@pytest.mark.parametrize("form", ["fp64", "mixed_cyclic"])
+def test_autotune_keeps_results_bitwise(M, form):
+    """mlqp_autotune times its candidate launch shapes (QR cluster size,
+    angle groups, cyclic-reduction cluster cap) and keeps the fastest; the
+    shapes do not change the arithmetic, so the amplitudes are bitwise those
+    of an untuned context."""
+    prob = config1() if form == "fp64" else small_stack(I=3, N=64, P=50, Mw=30, K=20, M=45, n_angles=2)
+    kw = {} if form == "fp64" else dict(precision=M.MLQP_MIXED, block_solver=M.MLQP_CYCLIC)
+    ref = M.Context(prob, **kw)
+    r0 = ref.solve_host()
+    ref.close()
+    ctx = M.Context(prob, **kw)
+    rep = ctx.autotune()
+    assert rep["qr_cluster"] in (1, 2, 4, 8)
+    assert all(t > 0 for t in rep["lsq_ms"].values())
+    assert 1 <= rep["angle_groups"] <= min(4, prob.n_theta)
+    if form == "mixed_cyclic":
+        assert rep["cr_cluster_cap"] in (1, 2, 4, 8)
+    else:
+        assert math.isnan(rep["cr_cluster_cap"])
+    r1 = ctx.solve_host()
+    ctx.close()
+    assert np.array_equal(r0["aU"], r1["aU"]) and np.array_equal(r0["aD"], r1["aD"])
+
+
 def test_set_angles_sweeps_in_chunks(M):
     """An angle sweep in chunks through one context (mlqp_set_angles) gives,
     bit for bit, what a context set up with those angles gives."""
