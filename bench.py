@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (fixed launch sequence, e.g. for ncu launch skips)")
     ap.add_argument("--config3", action="store_true",
                     help="also time the 1000-interface corner grating (one solve per form, after a warm-up)")
     ap.add_argument("--corner-levels", type=int, default=2)
@@ -301,6 +303,13 @@ def angle_sweep(mlqp, dev, chunk=128):
     return out
 
 
+# DRAM bytes (read + write) of the sweep kernels (k_lu_panel_cl, k_lu_prep,
+# k_lu_update, k_back_*) in one step of the 20-interface 3-angle grating, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over the
+# step's 2817 sweep launches, L2 warm between launches as in the bench).
+SWEEP_TRAFFIC_BYTES = 472.3e6
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -323,7 +332,8 @@ def main():
 
     prob = problem(rank)
     ctx = mlqp.Context(prob, device=dev)
-    tuned = ctx.autotune()  # launch shapes timed on this problem (untimed setup)
+    # launch shapes timed on this problem (untimed setup)
+    tuned = ctx.autotune() if not args.no_autotune else {"qr_cluster": 8, "angle_groups": min(4, prob.n_theta)}
     stream = ctx.stream
     out = ctx.outputs()
     n = [2 * f.N for f in prob.ifaces]
@@ -395,11 +405,14 @@ def main():
                 "config": {"workload": WORKLOAD, "interfaces": prob.I, "angles": nth, "nodes_per_interface": 120,
                            "unknowns_per_angle": int(sum(n)), "l2": "flushed between steps (256 MB write)",
                            "launch_shapes": {"qr_cluster": int(tuned["qr_cluster"]),
-                                             "angle_groups": int(tuned["angle_groups"]), "source": "mlqp_autotune"}},
+                                             "angle_groups": int(tuned["angle_groups"]),
+                                             "source": "defaults" if args.no_autotune else "mlqp_autotune"}},
                 "stage_ms": stage_ms, "dominant_stage": dominant,
                 "roofline": {"bound": "alu", "kernel": "block-tridiagonal sweep (k_lu_panel/k_lu_prep/k_lu_update)",
                              "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                             "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
+                             "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": SWEEP_TRAFFIC_BYTES,
+                             "traffic_note": "DRAM bytes read + written by the sweep kernels per step (3 angles), "
+                                             "one ncu capture of this workload",
                              "algorithmic_flops_per_step": sw_flops,
                              "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived; 1.20 measured at 1995 MHz)"},
                 "gpu_launches": launches, "outputs_finite": ok,
@@ -411,7 +424,7 @@ def main():
     def time_mixed(solver):
         mctx = mlqp.Context(prob, device=dev, precision=mlqp.MLQP_MIXED, max_refine=10, refine_tol=1e-15,
                             block_solver=solver)
-        mtuned = mctx.autotune()
+        mtuned = mctx.autotune() if not args.no_autotune else {}
         mout = mctx.outputs()
         for _ in range(args.warmup):
             mctx.solve_device(mout)

@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 from scipy.special import hankel1, jv  # noqa: E402
 
 from oracle import mlqp_oracle as O  # noqa: E402
-from workloads import config1, config2, config4, corner_stack, small_stack, flat_stack  # noqa: E402
+from workloads import config1, config2, config3, config4, corner_stack, small_stack, flat_stack  # noqa: E402
 from workloads.problems import Interface, Params, Problem  # noqa: E402
 from tests.closed_forms import fresnel  # noqa: E402
 
@@ -464,6 +464,49 @@ def test_autotune_keeps_results_bitwise(M, form):
     r1 = ctx.solve_host()
     ctx.close()
     assert np.array_equal(r0["aU"], r1["aU"]) and np.array_equal(r0["aD"], r1["aD"])
+
+
+def test_corner_grating_at_full_size(M):
+    """The 1000-interface corner grating at full size (256 nodes per
+    interface, 512 000 unknowns, one angle), in the launch configuration the
+    bench times.  Sampled blocks (interfaces 1, 500, 1000 with their
+    neighbours; layers 1, 500, 1001) equal the oracle's.  The mixed form with
+    cyclic reduction reaches omega <= 1e-15 and the plain FP64 amplitudes to
+    1e-9.  The flux error is that of the configuration's node budget (about
+    7e-5 at two panel levels per corner side), below 1e-4."""
+    prob = config3()
+    I, P = prob.I, prob.params.P
+    ctx = M.Context(prob)
+    ctx.run_stage(M.STAGE_GEOM)
+    ctx.run_stage(M.STAGE_FILL)
+    torch.cuda.synchronize()
+    asm = O.Assembler(prob)
+    bl = O.bloch(prob, prob.theta[0])
+    al = bl["alpha"]
+    for i in (1, 500, I):
+        row = ctx.block(M.BLK_ROW, i, 0).cpu().numpy()
+        n = 2 * prob.ifaces[i - 1].N
+        nl = 2 * prob.ifaces[i - 2].N if i > 1 else 0
+        assert rel(row[:, nl:nl + n], asm.A(i, i, al)) < BLOCK_TOL, i
+        if i < I:
+            assert rel(row[:, nl + n:], asm.A(i, i + 1, al)) < BLOCK_TOL, i
+        if i > 1:
+            assert rel(row[:, :nl], asm.A(i, i - 1, al)) < BLOCK_TOL, i
+        B = ctx.block(M.BLK_B, i).cpu().numpy()
+        assert rel(B[:, :P], asm.B(i, i)) < BLOCK_TOL and rel(B[:, P:], asm.B(i, i + 1)) < BLOCK_TOL
+    for j in (1, 500, I + 1):
+        assert rel(ctx.block(M.BLK_QP, j, 0).cpu().numpy(), asm.Qp(j, al, bl)) < BLOCK_TOL, j
+        assert rel(ctx.block(M.BLK_CP, j, 0).cpu().numpy(), asm.Cp(j, al)) < BLOCK_TOL, j
+    ref = ctx.solve_host()
+    ctx.close()
+    assert abs(ref["flux"][0]) < 1e-4
+    mixed = M.Context(prob, precision=M.MLQP_MIXED, block_solver=M.MLQP_CYCLIC)
+    out = mixed.solve_host()
+    omega, steps = mixed.block(M.BLK_REFINE, 1, 0).cpu().numpy()
+    mixed.close()
+    assert omega <= 1e-15, (omega, steps)
+    ag = np.concatenate([out["aU"][0], out["aD"][0]])
+    assert rel(ag, np.concatenate([ref["aU"][0], ref["aD"][0]])) < AMP_TOL
 
 
 def test_set_angles_sweeps_in_chunks(M):
