@@ -333,7 +333,8 @@ def main():
     prob = problem(rank)
     ctx = mlqp.Context(prob, device=dev)
     # launch shapes timed on this problem (untimed setup)
-    tuned = ctx.autotune() if not args.no_autotune else {"qr_cluster": 8, "angle_groups": min(4, prob.n_theta)}
+    tuned = ctx.autotune() if not args.no_autotune else {"qr_cluster": 8, "angle_groups": min(4, prob.n_theta),
+                                                         "update_tile": 32}
     stream = ctx.stream
     out = ctx.outputs()
     n = [2 * f.N for f in prob.ifaces]
@@ -406,6 +407,7 @@ def main():
                            "unknowns_per_angle": int(sum(n)), "l2": "flushed between steps (256 MB write)",
                            "launch_shapes": {"qr_cluster": int(tuned["qr_cluster"]),
                                              "angle_groups": int(tuned["angle_groups"]),
+                                             "update_tile": int(tuned.get("update_tile", 32)),
                                              "source": "defaults" if args.no_autotune else "mlqp_autotune"}},
                 "stage_ms": stage_ms, "dominant_stage": dominant,
                 "roofline": {"bound": "alu", "kernel": "block-tridiagonal sweep (k_lu_panel/k_lu_prep/k_lu_update)",
@@ -460,7 +462,7 @@ def main():
                "max_rel_amp_diff_vs_fp64": diff,
                "block_solver": "sweep" if solver == mlqp.MLQP_SWEEP else "cyclic reduction",
                "launch_shapes": {k: (None if v != v else int(v)) for k, v in mtuned.items()
-                                 if k in ("qr_cluster", "angle_groups", "cr_cluster_cap")},
+                                 if k in ("qr_cluster", "angle_groups", "cr_cluster_cap", "update_tile")},
                "dtype": "f32 Schur/LU + f64 refinement (fill, least squares, residuals in f64)"}
         mctx.close()
         return res

@@ -191,17 +191,19 @@ mlqp_status mlqp_set_angles(mlqp_ctx* ctx, const double* theta, int n_theta);
  * own problem (each timed stage preceded by the stages it depends on, so
  * this costs several solves): the CTAs per least-squares QR cluster (1, 2,
  * 4, 8), the number of angle groups (streams) of the block solve (1 to
- * min(n_theta, 4)) and, with MLQP_CYCLIC, the largest cluster of the
- * cyclic-reduction LU (1, 2, 4, 8).  The fastest of each is kept for later
+ * min(n_theta, 4)), the tile edge of the block LU's trailing update (16 or
+ * 32; not with MLQP_CYCLIC) and, with MLQP_CYCLIC, the largest cluster of
+ * the cyclic-reduction LU (1, 2, 4, 8).  The fastest of each is kept for later
  * solves.  None of them changes the arithmetic: results are bitwise those of
  * the default shapes.  report (may be NULL) receives MLQP_TUNE_REPORT
  * doubles: [QR cluster chosen, LSQ-stage ms for 1, 2, 4, 8; angle groups
  * chosen, block-solve ms for 1, 2, 3, 4 groups; CR cluster cap chosen,
- * block-solve ms for 1, 2, 4, 8], NaN where a candidate does not apply.  Sec. 3.4's angle
+ * block-solve ms for 1, 2, 4, 8; update tile chosen, block-solve ms for 16,
+ * 32], NaN where a candidate does not apply.  Sec. 3.4's angle
  * sweep is the intended use: tune on the first chunk, then mlqp_set_angles.
  * Errors: MLQP_ESTATE (not bound), MLQP_EINVAL (report too short),
  * MLQP_ECUDA. */
-enum { MLQP_TUNE_REPORT = 15 };
+enum { MLQP_TUNE_REPORT = 18 };
 mlqp_status mlqp_autotune(mlqp_ctx* ctx, double* report, int report_len);
 
 /* Location of a workspace block (for inspection by tests):

@@ -79,8 +79,9 @@ struct mlqp_ctx {
   cudaGraphExec_t gexec[MLQP_STAGE_RECOVER + 1] = {};
   long glaunches[MLQP_STAGE_RECOVER + 1] = {};
   // launch shapes (mlqp_autotune): QR cluster size, cyclic-reduction LU
-  // cluster cap, angle groups of the sweep (0: min(n_theta, MAX_ANGLE_STREAMS))
-  int qr_cl = 8, cr_cl_max = 8, angle_groups = 0;
+  // cluster cap, angle groups of the sweep (0: min(n_theta, MAX_ANGLE_STREAMS)),
+  // tile edge of the block LU's trailing update
+  int qr_cl = 8, cr_cl_max = 8, angle_groups = 0, upd_tile = 32;
 };
 
 static void drop_graphs(mlqp_ctx* c) {
@@ -509,6 +510,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   D.rcond = q.lsq_rcond;
   D.qr_cl = c->qr_cl;
   D.cr_cl_max = c->cr_cl_max;
+  D.upd_tile = c->upd_tile;
   D.yU = q.gap_U;  // the geometry kernel turns the gaps into y_U, y_D (stored in scal)
   D.yD = q.gap_D;
   D.maxN = c->maxN;
@@ -754,7 +756,24 @@ mlqp_status mlqp_autotune(mlqp_ctx* c, double* report, int report_len) {
     c->qr_cl = best;
     rep[0] = best;
   }
-  // 2. angle groups of the sweep: every count from 1 to min(n_theta, MAX_ANGLE_STREAMS)
+  // 2. tile edge of the block LU's trailing update (the sweep's, or the FP32
+  //    factorisation's in the mixed form)
+  if (st == MLQP_OK && !(c->prm.precision == MLQP_MIXED && c->prm.block_solver == MLQP_CYCLIC)) {
+    const int cand[2] = {16, 32};
+    int best = c->upd_tile;
+    double tb = INFINITY;
+    for (int q = 0; q < 2 && st == MLQP_OK; ++q) {
+      c->upd_tile = cand[q];
+      double t = 0;
+      if ((st = apply_shapes(c)) == MLQP_OK && (st = time_stage(c, MLQP_STAGE_SWEEP, 3, &t)) == MLQP_OK) {
+        rep[16 + q] = t;
+        if (t < tb) tb = t, best = cand[q];
+      }
+    }
+    c->upd_tile = best;
+    rep[15] = best;
+  }
+  // 3. angle groups of the sweep: every count from 1 to min(n_theta, MAX_ANGLE_STREAMS)
   if (st == MLQP_OK) {
     int best = c->angle_groups;
     double tb = INFINITY;
@@ -769,7 +788,7 @@ mlqp_status mlqp_autotune(mlqp_ctx* c, double* report, int report_len) {
     c->angle_groups = best;
     rep[5] = best;
   }
-  // 3. cluster cap of the cyclic-reduction LU
+  // 4. cluster cap of the cyclic-reduction LU
   if (st == MLQP_OK && c->prm.block_solver == MLQP_CYCLIC) {
     const int cand[4] = {1, 2, 4, 8};
     int best = c->cr_cl_max;

@@ -149,6 +149,7 @@ struct Dev {
   // launch shapes (host side; set by mlqp_autotune, defaults at bind)
   int qr_cl;      // CTAs per least-squares QR cluster (1..8)
   int cr_cl_max;  // largest cluster of the cyclic-reduction LU (1..8)
+  int upd_tile;   // tile edge of the block LU's trailing update (16 or 32)
 };
 
 }  // namespace mlqp

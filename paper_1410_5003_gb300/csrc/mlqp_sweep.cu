@@ -401,11 +401,19 @@ __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, i
 
 // ---------------------------------------------------------------------------
 // Trailing update: rows  v in [0, nt-k-w) (top rows k+w..) then [0, nb) (bottom),
-// columns u in [0, nt-k-w) (E), [0, nb) (T), then the rhs.  32 x 32 tiles,
-// 64 threads, 4 x 4 outputs per thread, complex 3M products.
-// ---------------------------------------------------------------------------
-constexpr int UT = 32;
-constexpr int UPD_THREADS = 128;
+// columns u in [0, nt-k-w) (E), [0, nb) (T), then the rhs.  Square tiles,
+// complex 3M products.  Tile edge UTT (32: 128 threads, 2 x 4 outputs each; 16: 64 threads, 2 x 2),
+// chosen per context (D.upd_tile, mlqp_autotune).  A tile is UTT^2 K complex
+// MACs on one SM, which sets the latency floor of an update with few tiles
+// (about 12 us for 32 x 32, K = 16, at GB300's 2 FP64 FMA per clock per SM).
+template <int UTT>
+struct UpdShape {
+  static constexpr int TH = (UTT == 32) ? 128 : 64;
+  static constexpr int RQ = 2;                          // rows per thread
+  static constexpr int CZ = UTT * UTT / TH / RQ;        // columns per thread
+  static constexpr int TXN = UTT / CZ;                  // column groups
+  static_assert(RQ * CZ * TH == UTT * UTT && TXN * CZ == UTT && (TH / TXN) * RQ == UTT, "update tile shape");
+};
 
 template <typename V>
 __device__ __forceinline__ V* row_col_ptr(V* top, int ldt, V* ftop, V* bot, int ldb, V* fbot, const Step& S, int k,
@@ -423,8 +431,10 @@ __device__ __forceinline__ V* row_col_ptr(V* top, int ldt, V* ftop, V* bot, int 
   return fbot + row;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k, int a0, int mode, int wn) {
+template <typename R, int UTT>
+__global__ void __launch_bounds__(UpdShape<UTT>::TH) k_lu_update(Dev D, int t, int k, int a0, int mode, int wn) {
+  constexpr int UT = UTT, UPD_THREADS = UpdShape<UTT>::TH, RQ = UpdShape<UTT>::RQ, CZ = UpdShape<UTT>::CZ,
+                TXN = UpdShape<UTT>::TXN;
   // mode 0: the whole trailing block.  Look-ahead split: mode 1 updates only
   // the next panel's columns u < wn of the top rows v < tr (so that panel can
   // be factored), mode 2 everything else.
@@ -482,36 +492,36 @@ __global__ void __launch_bounds__(UPD_THREADS) k_lu_update(Dev D, int t, int k, 
     Bs[kk][2][c] = x.x + x.y;
   }
   __syncthreads();
-  const int tx = tid & 7, ty = tid >> 3;  // 2 rows x 4 columns per thread
-  R t1[2][4] = {}, t2[2][4] = {}, t3[2][4] = {};
+  const int tx = tid % TXN, ty = tid / TXN;  // RQ rows x CZ columns per thread
+  R t1[RQ][CZ] = {}, t2[RQ][CZ] = {}, t3[RQ][CZ] = {};
   for (int kk = 0; kk < w; ++kk) {
-    R ar[2], ai[2], as[2], br[4], bi[4], bs[4];
+    R ar[RQ], ai[RQ], as[RQ], br[CZ], bi[CZ], bs[CZ];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      ar[q] = As[kk][0][ty * 2 + q];
-      ai[q] = As[kk][1][ty * 2 + q];
-      as[q] = As[kk][2][ty * 2 + q];
+    for (int q = 0; q < RQ; ++q) {
+      ar[q] = As[kk][0][ty * RQ + q];
+      ai[q] = As[kk][1][ty * RQ + q];
+      as[q] = As[kk][2][ty * RQ + q];
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      br[q] = Bs[kk][0][tx * 4 + q];
-      bi[q] = Bs[kk][1][tx * 4 + q];
-      bs[q] = Bs[kk][2][tx * 4 + q];
+    for (int q = 0; q < CZ; ++q) {
+      br[q] = Bs[kk][0][tx * CZ + q];
+      bi[q] = Bs[kk][1][tx * CZ + q];
+      bs[q] = Bs[kk][2][tx * CZ + q];
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < RQ; ++q)
 #pragma unroll
-      for (int z = 0; z < 4; ++z) {
+      for (int z = 0; z < CZ; ++z) {
         t1[q][z] = fma(ar[q], br[z], t1[q][z]);
         t2[q][z] = fma(ai[q], bi[z], t2[q][z]);
         t3[q][z] = fma(as[q], bs[z], t3[q][z]);
       }
   }
 #pragma unroll
-  for (int q = 0; q < 2; ++q)
+  for (int q = 0; q < RQ; ++q)
 #pragma unroll
-    for (int z = 0; z < 4; ++z) {
-      const int v = row0 + ty * 2 + q, u = col0 + tx * 4 + z;
+    for (int z = 0; z < CZ; ++z) {
+      const int v = row0 + ty * RQ + q, u = col0 + tx * CZ + z;
       const bool next_block = v < tr && u < wn;
       if (v < nrows && u < ncols && (mode == 0 || (mode == 1) == next_block)) {
         vec2<R>* p = row_col_ptr(top, ldt, ftop, bot, ldb, fbot, S, k, w, v, u);
@@ -612,6 +622,14 @@ __global__ void __launch_bounds__(128) k_recover(Dev D) {
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+template <typename R>
+static void launch_update(const Dev& D, int ut, dim3 grid, cudaStream_t s, int t, int k, int a0, int mode, int wn) {
+  if (ut == 16)
+    k_lu_update<R, 16><<<grid, UpdShape<16>::TH, 0, s>>>(D, t, k, a0, mode, wn);
+  else
+    k_lu_update<R, 32><<<grid, UpdShape<32>::TH, 0, s>>>(D, t, k, a0, mode, wn);
+}
+
 // The block LU of the forward sweep, in precision R (FP64: plain path on ROW/F;
 // FP32: factorisation of the mixed path on ROW32/F32), for angles a0..a0+na-1.
 template <typename R>
@@ -641,6 +659,7 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
       k_lu_prep<R><<<dim3(n_col_ctas + n_row_ctas, na), PREP_THREADS, 0, s>>>(D, t, k, n_col_ctas, a0);
       const int tr = nt - k - w;
       const int nrows = tr + nb, ncols = tr + nb + 1;
+      const int UT = (D.upd_tile == 16) ? 16 : 32;
       const int tiles = ((nrows + UT - 1) / UT) * ((ncols + UT - 1) / UT);
       const int k2 = k + w;
       if (LOOKAHEAD && k2 < nt) {
@@ -648,18 +667,18 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
         // the panel stream beside the rest of this update
         const int wn = (nt - k2 < NB) ? nt - k2 : NB;
         ++g_launches;
-        k_lu_update<R><<<dim3((tr + UT - 1) / UT, na), UPD_THREADS, 0, s>>>(D, t, k, a0, 1, wn);
+        launch_update<R>(D, UT, dim3((tr + UT - 1) / UT, na), s, t, k, a0, 1, wn);
         if ((e = cudaEventRecord(ev_next, s)) != cudaSuccess) break;
         if ((e = cudaStreamWaitEvent(ps, ev_next, 0)) != cudaSuccess) break;
         panel(k2, ps);
         if ((e = cudaEventRecord(ev_panel, ps)) != cudaSuccess) break;
         ++g_launches;
-        k_lu_update<R><<<dim3(tiles, na), UPD_THREADS, 0, s>>>(D, t, k, a0, 2, wn);
+        launch_update<R>(D, UT, dim3(tiles, na), s, t, k, a0, 2, wn);
         e = cudaStreamWaitEvent(s, ev_panel, 0);
       } else {
         if (nrows > 0) {
           ++g_launches;
-          k_lu_update<R><<<dim3(tiles, na), UPD_THREADS, 0, s>>>(D, t, k, a0, 0, 0);
+          launch_update<R>(D, UT, dim3(tiles, na), s, t, k, a0, 0, 0);
         }
         if (k2 < nt) panel(k2, s);
       }

@@ -193,7 +193,7 @@ class Context:
         th = np.ascontiguousarray(theta, dtype=np.float64)
         _check(self.ctx, self.lib.mlqp_set_angles(self.ctx, _dptr(th), len(th)))
 
-    TUNE_REPORT = 15
+    TUNE_REPORT = 18
 
     def autotune(self):
         """mlqp_autotune: times candidate launch shapes on this problem and
@@ -203,7 +203,8 @@ class Context:
         r = list(rep)
         return {"qr_cluster": r[0], "lsq_ms": dict(zip((1, 2, 4, 8), r[1:5])),
                 "angle_groups": r[5], "sweep_ms_by_groups": dict(zip((1, 2, 3, 4), r[6:10])),
-                "cr_cluster_cap": r[10], "sweep_ms_by_cr_cluster": dict(zip((1, 2, 4, 8), r[11:15]))}
+                "cr_cluster_cap": r[10], "sweep_ms_by_cr_cluster": dict(zip((1, 2, 4, 8), r[11:15])),
+                "update_tile": r[15], "sweep_ms_by_update_tile": dict(zip((16, 32), r[16:18]))}
 
     def close(self):
         if self.ctx:

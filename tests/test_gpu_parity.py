@@ -444,7 +444,7 @@ def test_gmres_refinement_where_plain_refinement_stalls(M):
 @pytest.mark.parametrize("form", ["fp64", "mixed_cyclic"])
 def test_autotune_keeps_results_bitwise(M, form):
     """mlqp_autotune times its candidate launch shapes (QR cluster size,
-    angle groups, cyclic-reduction cluster cap) and keeps the fastest; the
+    update tile, angle groups, cyclic-reduction cluster cap) and keeps the fastest; the
     shapes do not change the arithmetic, so the amplitudes are bitwise those
     of an untuned context."""
     prob = config1() if form == "fp64" else small_stack(I=3, N=64, P=50, Mw=30, K=20, M=45, n_angles=2)
@@ -458,9 +458,9 @@ def test_autotune_keeps_results_bitwise(M, form):
     assert all(t > 0 for t in rep["lsq_ms"].values())
     assert 1 <= rep["angle_groups"] <= min(4, prob.n_theta)
     if form == "mixed_cyclic":
-        assert rep["cr_cluster_cap"] in (1, 2, 4, 8)
+        assert rep["cr_cluster_cap"] in (1, 2, 4, 8) and math.isnan(rep["update_tile"])
     else:
-        assert math.isnan(rep["cr_cluster_cap"])
+        assert math.isnan(rep["cr_cluster_cap"]) and rep["update_tile"] in (16, 32)
     r1 = ctx.solve_host()
     ctx.close()
     assert np.array_equal(r0["aU"], r1["aU"]) and np.array_equal(r0["aD"], r1["aD"])
