@@ -59,6 +59,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, device):
+    """The job's time: the largest of the ranks' times (all_reduce MAX; any
+    backend, the tensor on `device`)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world_size, steps, total_ms):
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return units_per_rank * world_size * steps / (total_ms / 1e3)
+
+
 def problem(rank=0):
     from workloads import config2
     prob = config2()
@@ -377,13 +394,9 @@ def main():
         per_step.append(evs[0].elapsed_time(evs[-1]))
         for q in range(len(stages)):
             per_stage[q] += evs[q].elapsed_time(evs[q + 1])
-    total_ms = sum(per_step)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(per_step), dev)
     K = args.steps
-    value = units * ws * K / (total_ms / 1e3)
+    value = job_value(units, ws, K, total_ms)
     ctx.check()
 
     # correctness of the timed outputs: finite amplitudes
@@ -446,11 +459,7 @@ def main():
                 e1.record(mctx.stream)
                 mtimes.append((e0, e1))
         torch.cuda.synchronize()
-        mms = sum(a.elapsed_time(b) for a, b in mtimes)
-        if ws > 1:
-            t = torch.tensor([mms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            mms = float(t.item())
+        mms = max_over_ranks(sum(a.elapsed_time(b) for a, b in mtimes), dev)
         mctx.solve_device(mout)
         mctx.check()
         ref = torch.cat([out["aU"], out["aD"]], 1)
@@ -484,14 +493,10 @@ def main():
         for _ in range(K):
             ctx.bind()
             ctx.solve_host(out=hout)
-        el = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([el], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks((time.perf_counter() - t0) * 1e3, dev)
         if rank == 0:
             d2h = sum(v.numel() * v.element_size() for v in hout.values() if v is not None) + 4
-            line["e2e"] = {"value": units * ws * K / el, "unit": METRIC, "h2d_bytes_per_step": ctx.upload_bytes(),
+            line["e2e"] = {"value": job_value(units, ws, K, el), "unit": METRIC, "h2d_bytes_per_step": ctx.upload_bytes(),
                            "d2h_bytes_per_step": d2h}
     if args.config3 and rank == 0:
         line["config3"] = corner_grating(mlqp, dev, args.corner_levels)

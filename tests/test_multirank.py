@@ -1,0 +1,69 @@
+"""The multi-GPU path of bench.py (angle sharding, weak scaling) on CPU:
+world-size-2 gloo ranks run the host logic (each rank's problem, the job
+time as the maximum over ranks, the whole-job value), and the reference arm
+under torchrun prints one line from rank 0 only.  No GPU is involved."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, results):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        prob = bench.problem(rank)
+        ms = 100.0 + 25.0 * rank  # this rank's (made-up) device time
+        job_ms = bench.max_over_ranks(ms, torch.device("cpu"))
+        value = bench.job_value(prob.I * prob.n_theta, world, 3, job_ms)
+        results[rank] = (list(map(float, prob.theta)), prob.I, [f.N for f in prob.ifaces], job_ms, value)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_angles_and_take_the_slowest_time():
+    world, port = 2, _free_port()
+    with mp.Manager() as man:
+        results = man.dict()
+        mp.start_processes(_rank, args=(world, port, results), nprocs=world, start_method="spawn")
+        r = dict(results)
+    th0, I0, N0, ms0, v0 = r[0]
+    th1, I1, N1, ms1, v1 = r[1]
+    # weak scaling: the same stack per rank, its own angles (shifted by 1e-3 per rank)
+    assert (I0, N0) == (I1, N1)
+    assert all(abs((b - a) - 1e-3) < 1e-15 for a, b in zip(th0, th1))
+    # the job's time is the slowest rank's; the value counts every rank's units
+    assert ms0 == ms1 == 125.0
+    assert v0 == v1 == pytest.approx(I0 * len(th0) * 2 * 3 / 0.125)
+
+
+def test_reference_arm_under_torchrun_prints_from_rank_zero_only():
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1"]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
