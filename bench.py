@@ -278,6 +278,7 @@ def angle_sweep(mlqp, dev, chunk=128):
     amps = {}
     for name, prec, kw in legs:
         ctx = mlqp.Context(prob.with_angles(th[:chunk]), device=dev, precision=prec, **kw)
+        tuned = ctx.autotune(mlqp.TUNE_QR)  # the QR cluster size only: tuning the block solve costs minutes here
         res = ctx.outputs()
         ctx.solve_device(res)
         checked(ctx, prec, None)
@@ -290,7 +291,8 @@ def angle_sweep(mlqp, dev, chunk=128):
             checked(ctx, prec, omegas)
             amps[name].append(torch.cat([res["aU"], res["aD"]], 1).cpu())
         el = time.perf_counter() - t0
-        out[name] = {"seconds": el, "value": len(th) / el, "workspace_gb": ctx.ws_bytes / 1e9}
+        out[name] = {"seconds": el, "value": len(th) / el, "workspace_gb": ctx.ws_bytes / 1e9,
+                     "launch_shapes": {"qr_cluster": int(tuned["qr_cluster"]), "source": "mlqp_autotune"}}
         if omegas:
             out[name]["backward_error_max"] = max(omegas)
             out[name]["angles_above_refine_tol"] = int(sum(w > 1e-15 for w in omegas))

@@ -153,7 +153,12 @@ mlqp_status mlqp_bind(mlqp_ctx* ctx, void* dev_workspace, size_t bytes, void* st
  * interleaved re/im, may be NULL), d_aU and d_aD (n_theta x (2K+1)
  * complex128), d_flux (n_theta doubles, may be NULL).  Returns after the
  * launches; errors detected on the device (MLQP_ESINGULAR) are reported by
- * mlqp_check_device. */
+ * mlqp_check_device.  In the MLQP_MIXED form the refinement is driven from
+ * the host: after each correction (and each block of 8 GMRES steps) it reads
+ * the number of angles still active, synchronising the bound stream, and
+ * stops launching once none is; so this call returns when the refinement has
+ * ended and only the recovery is still in flight.  The results are those of
+ * running every correction. */
 mlqp_status mlqp_solve_device(mlqp_ctx* ctx, void* d_eta, void* d_aU, void* d_aD, void* d_flux);
 
 /* Synchronises the bound stream and returns the device-side status word. */
@@ -193,7 +198,8 @@ mlqp_status mlqp_set_angles(mlqp_ctx* ctx, const double* theta, int n_theta);
  * 4, 8), the number of angle groups (streams) of the block solve (1 to
  * min(n_theta, 4)), the tile edge of the block LU's trailing update (16 or
  * 32; not with MLQP_CYCLIC) and, with MLQP_CYCLIC, the largest cluster of
- * the cyclic-reduction LU (1, 2, 4, 8).  The fastest of each is kept for later
+ * the cyclic-reduction LU (1, 2, 4, 8).  which selects them (MLQP_TUNE_*
+ * bits; MLQP_TUNE_ALL or 0 for all); the fastest of each is kept for later
  * solves.  None of them changes the arithmetic: results are bitwise those of
  * the default shapes.  report (may be NULL) receives MLQP_TUNE_REPORT
  * doubles: [QR cluster chosen, LSQ-stage ms for 1, 2, 4, 8; angle groups
@@ -204,7 +210,8 @@ mlqp_status mlqp_set_angles(mlqp_ctx* ctx, const double* theta, int n_theta);
  * Errors: MLQP_ESTATE (not bound), MLQP_EINVAL (report too short),
  * MLQP_ECUDA. */
 enum { MLQP_TUNE_REPORT = 18 };
-mlqp_status mlqp_autotune(mlqp_ctx* ctx, double* report, int report_len);
+enum { MLQP_TUNE_QR = 1, MLQP_TUNE_TILE = 2, MLQP_TUNE_GROUPS = 4, MLQP_TUNE_CR = 8, MLQP_TUNE_ALL = 15 };
+mlqp_status mlqp_autotune(mlqp_ctx* ctx, int which, double* report, int report_len);
 
 /* Location of a workspace block (for inspection by tests):
  *   MLQP_BLK_ROW    interface i (1..I), angle a: the block row

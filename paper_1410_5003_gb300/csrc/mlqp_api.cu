@@ -24,8 +24,8 @@ cudaError_t launch_recover(const Dev& D, cudaStream_t s);
 cudaError_t sweep_configure(int maxn);
 cudaError_t mixed_configure(int maxn);
 cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s);
-cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n_den, int max_refine, double tol,
-                               int* permv, const AngleStreams& A, bool cyclic, bool gmres);
+cudaError_t launch_mixed_piece(const Dev& D, const int* n_host, int maxn, long n_den, double tol, int* permv,
+                               const AngleStreams& A, bool cyclic, int piece);
 cudaError_t cr_configure(int maxn);
 int cr_slots(int I);
 cudaError_t lsq_configure(int max_m, int max_p);
@@ -82,10 +82,19 @@ struct mlqp_ctx {
   // cluster cap, angle groups of the sweep (0: min(n_theta, MAX_ANGLE_STREAMS)),
   // tile edge of the block LU's trailing update
   int qr_cl = 8, cr_cl_max = 8, angle_groups = 0, upd_tile = 32;
+  // the mixed block solve: one graph per piece (launch_mixed_piece), replayed by
+  // a host loop that reads the active-angle counts into hflag (pinned)
+  cudaGraphExec_t pexec[MP_COUNT] = {};
+  long plaunches[MP_COUNT] = {};
+  int* hflag = nullptr;
 };
 
 static void drop_graphs(mlqp_ctx* c) {
   for (auto& g : c->gexec) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+  for (auto& g : c->pexec) {
     if (g) cudaGraphExecDestroy(g);
     g = nullptr;
   }
@@ -646,12 +655,8 @@ static cudaError_t enqueue_stage(mlqp_ctx* c, int stage, cudaStream_t st) {
       e = (c->prm.precision == MLQP_MIXED) ? launch_schur32(c->D, c->max_tiles, st)
                                            : launch_schur(c->D, c->max_tiles, st);
       break;
-    case MLQP_STAGE_SWEEP:
-      e = (c->prm.precision == MLQP_MIXED)
-              ? launch_mixed_solve(c->D, c->n_host.data(), c->maxn, c->n_den, c->prm.max_refine, c->prm.refine_tol,
-                                   at<int>(c, c->r_PERMV), A, c->prm.block_solver == MLQP_CYCLIC,
-                                   c->prm.refine_method == MLQP_GMRES_IR)
-              : launch_sweep(c->D, c->n_host.data(), A);
+    case MLQP_STAGE_SWEEP:  // the mixed form runs in pieces (run_mixed_sweep)
+      e = (c->prm.precision == MLQP_MIXED) ? cudaErrorInvalidValue : launch_sweep(c->D, c->n_host.data(), A);
       break;
     case MLQP_STAGE_RECOVER: e = launch_recover(c->D, st); break;
     default: e = cudaErrorInvalidValue;
@@ -670,33 +675,91 @@ mlqp_status mlqp_set_angles(mlqp_ctx* c, const double* theta, int n_theta) {
   return mlqp_bind(c, c->ws, c->ws_bytes, c->stream);
 }
 
-mlqp_status mlqp_run_stage(mlqp_ctx* c, int stage) {
-  if (!c) return MLQP_EINVAL;
-  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
-  if (stage < MLQP_STAGE_GEOM || stage > MLQP_STAGE_RECOVER) return fail(c, MLQP_EINVAL, "unknown stage %d", stage);
+extern "C++" {
+// Captures fn(stream) once into gx (on the internal stream c->cap) and
+// replays it on the bound stream.
+template <typename F>
+static mlqp_status replay(mlqp_ctx* c, cudaGraphExec_t& gx, long& gl, F&& fn, const char* what) {
   cudaError_t e = cudaSuccess;
-  if (!c->gexec[stage]) {
+  if (!gx) {
     g_launches = 0;
     e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return cuda_fail(c, e, "stage capture");
-    const cudaError_t el = enqueue_stage(c, stage, c->cap);
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    const cudaError_t el = fn(c->cap);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(c->cap, &graph);
     if (el != cudaSuccess || e != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
-      return cuda_fail(c, el != cudaSuccess ? el : e, "stage capture");
+      return cuda_fail(c, el != cudaSuccess ? el : e, what);
     }
-    e = cudaGraphInstantiate(&c->gexec[stage], graph, 0);
+    e = cudaGraphInstantiate(&gx, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-      c->gexec[stage] = nullptr;
-      return cuda_fail(c, e, "stage graph");
+      gx = nullptr;
+      return cuda_fail(c, e, what);
     }
-    c->glaunches[stage] = g_launches;
+    gl = g_launches;
   }
-  if ((e = cudaGraphLaunch(c->gexec[stage], c->stream)) != cudaSuccess) return cuda_fail(c, e, "stage launch");
-  c->launches += c->glaunches[stage];
+  if ((e = cudaGraphLaunch(gx, c->stream)) != cudaSuccess) return cuda_fail(c, e, what);
+  c->launches += gl;
   return MLQP_OK;
+}
+
+// The mixed block solve: FP32 factorisation, then refinement corrections
+// until every angle meets refine_tol (or max_refine); with GMRES, blocks of
+// GM_BLK Arnoldi steps until every angle's inner solve has stopped.  The
+// counts read between pieces only skip launches that no angle needs, so the
+// results are those of running every piece.
+static mlqp_status run_mixed_sweep(mlqp_ctx* c) {
+  AngleStreams A = c->astr;
+  auto piece = [&](int p) {
+    return replay(c, c->pexec[p], c->plaunches[p], [&](cudaStream_t st) {
+      AngleStreams B = A;
+      B.main = st;
+      return launch_mixed_piece(c->D, c->n_host.data(), c->maxn, c->n_den, c->prm.refine_tol,
+                                at<int>(c, c->r_PERMV), B, c->prm.block_solver == MLQP_CYCLIC, p);
+    }, "mixed solve");
+  };
+  auto count = [&](int which, int* out) -> mlqp_status {
+    cudaError_t e = cudaSuccess;
+    if (!c->hflag && (e = cudaMallocHost(&c->hflag, 4 * sizeof(int))) != cudaSuccess) return cuda_fail(c, e, "flag");
+    e = cudaMemcpyAsync(c->hflag + which, c->D.STATUS + 1 + which, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "flag");
+    *out = c->hflag[which];
+    return MLQP_OK;
+  };
+  const bool gm = c->prm.refine_method == MLQP_GMRES_IR;
+  mlqp_status st = piece(MP_FACTOR);
+  for (int it = 0; it <= c->prm.max_refine && st == MLQP_OK; ++it) {
+    const bool last = (it == c->prm.max_refine);
+    int active = 0;
+    if ((st = piece(last ? MP_RESID_LAST : MP_RESID)) != MLQP_OK || (st = count(0, &active)) != MLQP_OK) break;
+    if (last || active == 0) break;
+    if (!gm) {
+      st = piece(MP_IR);
+      continue;
+    }
+    if ((st = piece(MP_GM_START)) != MLQP_OK) break;
+    for (int b = 0; b < GM_M / GM_BLK && st == MLQP_OK; ++b) {
+      int inner = 0;
+      if ((st = piece(MP_GM_BLOCK + b)) != MLQP_OK || (st = count(1, &inner)) != MLQP_OK) break;
+      if (inner == 0) break;
+    }
+    if (st == MLQP_OK) st = piece(MP_GM_END);
+  }
+  return st;
+}
+
+}  // extern "C++"
+
+mlqp_status mlqp_run_stage(mlqp_ctx* c, int stage) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  if (stage < MLQP_STAGE_GEOM || stage > MLQP_STAGE_RECOVER) return fail(c, MLQP_EINVAL, "unknown stage %d", stage);
+  if (stage == MLQP_STAGE_SWEEP && c->prm.precision == MLQP_MIXED) return run_mixed_sweep(c);
+  return replay(c, c->gexec[stage], c->glaunches[stage], [&](cudaStream_t st) { return enqueue_stage(c, stage, st); },
+                "stage");
 }
 
 // Device time of `stage` (best of reps), each run preceded by the stages
@@ -733,15 +796,17 @@ static mlqp_status apply_shapes(mlqp_ctx* c) {
   return mlqp_bind(c, c->ws, c->ws_bytes, c->stream);
 }
 
-mlqp_status mlqp_autotune(mlqp_ctx* c, double* report, int report_len) {
+mlqp_status mlqp_autotune(mlqp_ctx* c, int which, double* report, int report_len) {
   if (!c) return MLQP_EINVAL;
+  if (which == 0) which = MLQP_TUNE_ALL;
+  if (which & ~MLQP_TUNE_ALL) return fail(c, MLQP_EINVAL, "unknown autotune selection %d", which);
   if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
   if (report && report_len < MLQP_TUNE_REPORT) return fail(c, MLQP_EINVAL, "report needs %d doubles", MLQP_TUNE_REPORT);
   double rep[MLQP_TUNE_REPORT];
   for (double& x : rep) x = NAN;
   mlqp_status st = MLQP_OK;
   // 1. least-squares QR cluster size
-  {
+  if (which & MLQP_TUNE_QR) {
     const int cand[4] = {1, 2, 4, 8};
     int best = c->qr_cl;
     double tb = INFINITY;
@@ -758,7 +823,8 @@ mlqp_status mlqp_autotune(mlqp_ctx* c, double* report, int report_len) {
   }
   // 2. tile edge of the block LU's trailing update (the sweep's, or the FP32
   //    factorisation's in the mixed form)
-  if (st == MLQP_OK && !(c->prm.precision == MLQP_MIXED && c->prm.block_solver == MLQP_CYCLIC)) {
+  if (st == MLQP_OK && (which & MLQP_TUNE_TILE) &&
+      !(c->prm.precision == MLQP_MIXED && c->prm.block_solver == MLQP_CYCLIC)) {
     const int cand[2] = {16, 32};
     int best = c->upd_tile;
     double tb = INFINITY;
@@ -774,7 +840,7 @@ mlqp_status mlqp_autotune(mlqp_ctx* c, double* report, int report_len) {
     rep[15] = best;
   }
   // 3. angle groups of the sweep: every count from 1 to min(n_theta, MAX_ANGLE_STREAMS)
-  if (st == MLQP_OK) {
+  if (st == MLQP_OK && (which & MLQP_TUNE_GROUPS)) {
     int best = c->angle_groups;
     double tb = INFINITY;
     for (int g = 1; g <= std::min(c->n_theta, MAX_ANGLE_STREAMS) && st == MLQP_OK; ++g) {
@@ -789,7 +855,7 @@ mlqp_status mlqp_autotune(mlqp_ctx* c, double* report, int report_len) {
     rep[5] = best;
   }
   // 4. cluster cap of the cyclic-reduction LU
-  if (st == MLQP_OK && c->prm.block_solver == MLQP_CYCLIC) {
+  if (st == MLQP_OK && (which & MLQP_TUNE_CR) && c->prm.block_solver == MLQP_CYCLIC) {
     const int cand[4] = {1, 2, 4, 8};
     int best = c->cr_cl_max;
     double tb = INFINITY;
@@ -941,6 +1007,7 @@ void mlqp_destroy(mlqp_ctx* c) {
   if (!c) return;
   if (c->bound) cudaStreamSynchronize(c->stream);
   if (c->staging) cudaFreeHost(c->staging);
+  if (c->hflag) cudaFreeHost(c->hflag);
   destroy_angle_streams(c);
   delete c;
 }

@@ -75,6 +75,11 @@ constexpr int GM_M = 40;     // GMRES steps per refinement step
 constexpr int GM_NB = 64;    // CTAs of the batched reductions (per angle)
 constexpr int GM_HW = 4096;  // doubles of per-angle GMRES data
 constexpr double GM_TOL = 1e-10;  // inner GMRES stop: |r - A' d| <= GM_TOL |r|
+constexpr int GM_BLK = 8;         // Arnoldi steps per replayed piece of the mixed solve
+static_assert(GM_M % GM_BLK == 0, "GMRES pieces");
+// pieces of the mixed block solve (launch_mixed_piece)
+enum { MP_FACTOR = 0, MP_RESID = 1, MP_RESID_LAST = 2, MP_IR = 3, MP_GM_START = 4, MP_GM_BLOCK = 5,
+       MP_GM_END = MP_GM_BLOCK + GM_M / GM_BLK, MP_COUNT = MP_GM_END + 1 };
 
 struct Dev {
   int I, L, n_theta, P, Mw, M, K, nK;

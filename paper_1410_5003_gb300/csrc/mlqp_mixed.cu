@@ -385,85 +385,89 @@ static cudaError_t launch_precond(const Dev& D, const int* n_host, long n_den, i
   return cudaGetLastError();
 }
 
-// One inner flexible GMRES(GM_M) solve of A' d = r (r in RES), eta += d.
-// Angles whose outer test has passed are skipped.
-static cudaError_t launch_gmres(const Dev& D, const int* n_host, int maxn, long n_den, int* permv, bool cyclic,
-                                cudaStream_t s) {
+// Counts into STATUS[1 + which] the angles not yet converged (which 0) or,
+// of those, the ones whose inner GMRES is still running (which 1).  One CTA.
+__global__ void k_count_active(Dev D, int which);
+
+// The mixed block solve in pieces, each captured once as a graph and
+// replayed by a host loop that reads the active-angle counts between them
+// (so no piece is launched once no angle needs it):
+//   MP_FACTOR     FP32 factorisation (sweep or cyclic reduction), eta = 0
+//   MP_RESID[_LAST] residual, backward error, convergence test (the last one
+//                 flags angles that missed refine_tol), count -> STATUS[1]
+//   MP_IR         one plain correction: d = M^{-1} r, eta += d
+//   MP_GM_START   start of a flexible GMRES correction: beta, v_0
+//   MP_GM_BLOCK+b Arnoldi steps GM_BLK b .. GM_BLK (b+1) - 1, count -> STATUS[2]
+//   MP_GM_END     y = R^{-1} g, eta += Z y
+cudaError_t launch_mixed_piece(const Dev& D, const int* n_host, int maxn, long n_den, double tol, int* permv,
+                               const AngleStreams& A, bool cyclic, int piece) {
+  cudaStream_t s = A.main;
   const int nt = D.n_theta, nd = (int)n_den;
   const dim3 vec((unsigned)std::max(1L, std::min(512L, (n_den + 255) / 256)), nt);
   const dim3 red(GM_NB, nt);
-  cudaError_t e;
-  g_launches += 4;
-  k_gm_begin<<<nt, 256, 0, s>>>(D);
-  k_gm_dot<<<red, 256, 0, s>>>(D, -1, 1, nd);
-  k_gm_sum<<<nt, 64, 0, s>>>(D, -1, 1);
-  k_gm_scale<<<vec, 256, 0, s>>>(D, -1, nd);
   const size_t vstride = (size_t)nt * D.eta_stride;
-  for (int j = 0; j < GM_M; ++j) {
-    if ((e = launch_precond(D, n_host, n_den, permv, cyclic, s)) != cudaSuccess) return e;
-    const double2* zj = D.GZ + (size_t)j * vstride;
-    g_launches += 3;
-    k_gm_to64<<<vec, 256, 0, s>>>(D, j, nd);
-    k_xeta<false><<<dim3((D.L * D.P + 7) / 8, nt), 256, 0, s>>>(D, zj);
-    k_resid<1><<<dim3((maxn + 7) / 8, D.I, nt), 256, 0, s>>>(D, zj, D.GW);
-    for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-      g_launches += 3;
-      k_gm_dot<<<dim3(GM_NB, nt, (j + 8) / 8), 256, 0, s>>>(D, j, 0, nd);
-      k_gm_sum<<<nt, 64, 0, s>>>(D, j, 0);
-      k_gm_orth<<<vec, 256, 0, s>>>(D, j, nd);
-    }
-    g_launches += 4;
-    k_gm_dot<<<red, 256, 0, s>>>(D, j, 1, nd);
-    k_gm_sum<<<nt, 64, 0, s>>>(D, j, 1);
-    k_gm_scale<<<vec, 256, 0, s>>>(D, j, nd);
-    k_gm_givens<<<1, 128, 0, s>>>(D, j, GM_TOL);
-  }
-  g_launches += 2;
-  k_gm_solve<<<1, 128, 0, s>>>(D);
-  k_gm_update<<<vec, 256, 0, s>>>(D, nd);
-  return cudaGetLastError();
-}
-
-// Factorise A'_32 and refine eta in FP64: up to max_refine corrections (one
-// FP32 block solve each, or with gmres one flexible GMRES solve), each
-// preceded by a residual and its backward error; a final residual checks the
-// last one.
-cudaError_t launch_mixed_solve(const Dev& D, const int* n_host, int maxn, long n_den, int max_refine, double tol,
-                               int* permv, const AngleStreams& A, bool cyclic, bool gmres) {
-  cudaStream_t s = A.main;
-  cudaError_t e = cudaMemsetAsync(D.F32, 0, sizeof(float2) * D.f_stride * D.n_theta, s);
-  if (e != cudaSuccess) return e;
-  if (cyclic) {
-    e = launch_cr_factor(D, n_host[0], permv, s);
-  } else {
-    e = launch_factor32(D, n_host, A);
-    if (e == cudaSuccess) {
-      ++g_launches;
-      k_compose_perm<<<dim3((D.I + 63) / 64, D.n_theta), 64, 0, s>>>(D, permv);
-    }
-  }
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(D.ETA, 0, sizeof(double2) * D.eta_stride * D.n_theta, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(D.RNRM, 0, sizeof(double) * RNRM_W * D.n_theta, s);
-  if (e != cudaSuccess) return e;
-  for (int it = 0; it <= max_refine; ++it) {
-    const int last = (it == max_refine);
-    ++g_launches;
-    k_xeta<true><<<dim3((D.L * D.P + 7) / 8, D.n_theta), 256, 0, s>>>(D, D.ETA);
-    ++g_launches;
-    k_resid<0><<<dim3((maxn + 7) / 8, D.I, D.n_theta), 256, 0, s>>>(D, D.ETA, D.RES);
-    ++g_launches;
-    k_refine_ctl<<<1, 32, 0, s>>>(D, last, tol);
-    if (last) break;
-    if (gmres) {
-      if ((e = launch_gmres(D, n_host, maxn, n_den, permv, cyclic, s)) != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (piece == MP_FACTOR) {
+    e = cudaMemsetAsync(D.F32, 0, sizeof(float2) * D.f_stride * nt, s);
+    if (e != cudaSuccess) return e;
+    if (cyclic) {
+      e = launch_cr_factor(D, n_host[0], permv, s);
     } else {
-      if ((e = launch_precond(D, n_host, n_den, permv, cyclic, s)) != cudaSuccess) return e;
-      ++g_launches;
-      k_eta_update<<<D.n_theta, 256, 0, s>>>(D, (int)n_den);
+      e = launch_factor32(D, n_host, A);
+      if (e == cudaSuccess) {
+        ++g_launches;
+        k_compose_perm<<<dim3((D.I + 63) / 64, nt), 64, 0, s>>>(D, permv);
+      }
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.ETA, 0, sizeof(double2) * D.eta_stride * nt, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.RNRM, 0, sizeof(double) * RNRM_W * nt, s);
+  } else if (piece == MP_RESID || piece == MP_RESID_LAST) {
+    g_launches += 4;
+    k_xeta<true><<<dim3((D.L * D.P + 7) / 8, nt), 256, 0, s>>>(D, D.ETA);
+    k_resid<0><<<dim3((maxn + 7) / 8, D.I, nt), 256, 0, s>>>(D, D.ETA, D.RES);
+    k_refine_ctl<<<1, 32, 0, s>>>(D, piece == MP_RESID_LAST, tol);
+    k_count_active<<<1, 256, 0, s>>>(D, 0);
+  } else if (piece == MP_IR) {
+    if ((e = launch_precond(D, n_host, n_den, permv, cyclic, s)) != cudaSuccess) return e;
+    ++g_launches;
+    k_eta_update<<<nt, 256, 0, s>>>(D, nd);
+  } else if (piece == MP_GM_START) {
+    g_launches += 4;
+    k_gm_begin<<<nt, 256, 0, s>>>(D);
+    k_gm_dot<<<red, 256, 0, s>>>(D, -1, 1, nd);
+    k_gm_sum<<<nt, 64, 0, s>>>(D, -1, 1);
+    k_gm_scale<<<vec, 256, 0, s>>>(D, -1, nd);
+  } else if (piece >= MP_GM_BLOCK && piece < MP_GM_BLOCK + GM_M / GM_BLK) {
+    const int j0 = GM_BLK * (piece - MP_GM_BLOCK);
+    for (int j = j0; j < j0 + GM_BLK; ++j) {
+      if ((e = launch_precond(D, n_host, n_den, permv, cyclic, s)) != cudaSuccess) return e;
+      const double2* zj = D.GZ + (size_t)j * vstride;
+      g_launches += 3;
+      k_gm_to64<<<vec, 256, 0, s>>>(D, j, nd);
+      k_xeta<false><<<dim3((D.L * D.P + 7) / 8, nt), 256, 0, s>>>(D, zj);
+      k_resid<1><<<dim3((maxn + 7) / 8, D.I, nt), 256, 0, s>>>(D, zj, D.GW);
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        g_launches += 3;
+        k_gm_dot<<<dim3(GM_NB, nt, (j + 8) / 8), 256, 0, s>>>(D, j, 0, nd);
+        k_gm_sum<<<nt, 64, 0, s>>>(D, j, 0);
+        k_gm_orth<<<vec, 256, 0, s>>>(D, j, nd);
+      }
+      g_launches += 4;
+      k_gm_dot<<<red, 256, 0, s>>>(D, j, 1, nd);
+      k_gm_sum<<<nt, 64, 0, s>>>(D, j, 1);
+      k_gm_scale<<<vec, 256, 0, s>>>(D, j, nd);
+      k_gm_givens<<<1, 128, 0, s>>>(D, j, GM_TOL);
+    }
+    ++g_launches;
+    k_count_active<<<1, 256, 0, s>>>(D, 1);
+  } else if (piece == MP_GM_END) {
+    g_launches += 2;
+    k_gm_solve<<<1, 128, 0, s>>>(D);
+    k_gm_update<<<vec, 256, 0, s>>>(D, nd);
+  } else {
+    return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -746,6 +750,21 @@ __global__ void k_gm_update(Dev D, int n_den) {
     eta[r] = x;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) D.RNRM[(size_t)a * RNRM_W + 1] += 1.0;
+}
+
+__global__ void k_count_active(Dev D, int which) {
+  __shared__ int part[8];
+  int cnt = 0;
+  for (int a = threadIdx.x; a < D.n_theta; a += blockDim.x)
+    cnt += (which == 0) ? !angle_done(D, a) : gm_active(D, a);
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    D.STATUS[1 + which] = t;
+  }
 }
 
 }  // namespace mlqp

@@ -20,6 +20,7 @@ MLQP_OK, MLQP_EINVAL, MLQP_ENOMEM, MLQP_ECUDA, MLQP_ESINGULAR, MLQP_ETIMEOUT, ML
 MLQP_FP64, MLQP_MIXED = 0, 1
 MLQP_SWEEP, MLQP_CYCLIC = 0, 1
 MLQP_IR, MLQP_GMRES_IR = 0, 1
+TUNE_QR, TUNE_TILE, TUNE_GROUPS, TUNE_CR, TUNE_ALL = 1, 2, 4, 8, 15
 STAGE_GEOM, STAGE_FILL, STAGE_LSQ, STAGE_SCHUR, STAGE_SWEEP, STAGE_RECOVER = range(6)
 BLK_ROW, BLK_B, BLK_QP, BLK_CP, BLK_X, BLK_RHS, BLK_NODES, BLK_ETA, BLK_AMP, BLK_REFINE = range(10)
 
@@ -68,7 +69,7 @@ def load(path: str = LIB_PATH):
     lib.mlqp_bind.restype = I
     lib.mlqp_set_angles.argtypes = [P, ct.POINTER(D), I]
     lib.mlqp_set_angles.restype = I
-    lib.mlqp_autotune.argtypes = [P, ct.POINTER(D), I]
+    lib.mlqp_autotune.argtypes = [P, I, ct.POINTER(D), I]
     lib.mlqp_autotune.restype = I
     lib.mlqp_solve_device.argtypes = [P, V, V, V, V]
     lib.mlqp_solve_device.restype = I
@@ -195,11 +196,12 @@ class Context:
 
     TUNE_REPORT = 18
 
-    def autotune(self):
-        """mlqp_autotune: times candidate launch shapes on this problem and
-        keeps the fastest; returns the chosen shapes and the timings (ms)."""
+    def autotune(self, which=TUNE_ALL):
+        """mlqp_autotune: times candidate launch shapes (the TUNE_* bits of
+        `which`) on this problem and keeps the fastest; returns the chosen
+        shapes and the timings (ms), NaN for those not tuned."""
         rep = (ct.c_double * self.TUNE_REPORT)()
-        _check(self.ctx, self.lib.mlqp_autotune(self.ctx, rep, self.TUNE_REPORT))
+        _check(self.ctx, self.lib.mlqp_autotune(self.ctx, int(which), rep, self.TUNE_REPORT))
         r = list(rep)
         return {"qr_cluster": r[0], "lsq_ms": dict(zip((1, 2, 4, 8), r[1:5])),
                 "angle_groups": r[5], "sweep_ms_by_groups": dict(zip((1, 2, 3, 4), r[6:10])),

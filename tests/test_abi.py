@@ -175,8 +175,8 @@ def test_autotune_needs_a_bound_context(M):
     import ctypes as ct
     ctx, _ = M.mlqp_setup(small_stack(I=2))
     rep = (ct.c_double * 18)()
-    assert lib.mlqp_autotune(ctx, rep, 18) == M.MLQP_ESTATE
-    assert lib.mlqp_autotune(None, rep, 18) == M.MLQP_EINVAL
+    assert lib.mlqp_autotune(ctx, 0, rep, 18) == M.MLQP_ESTATE
+    assert lib.mlqp_autotune(None, 0, rep, 18) == M.MLQP_EINVAL
     lib.mlqp_destroy(ctx)
 
 

@@ -317,6 +317,25 @@ def test_mixed_precision_matches_oracle(M, name):
     ctx.close()
 
 
+def test_refinement_stops_launching_once_converged(M):
+    """The mixed solve is driven from the host: once every angle meets
+    refine_tol no further correction is launched, so max_refine = 10 and 50
+    issue the same kernels and give bitwise the same amplitudes."""
+    prob = PROBLEMS["small3"]()
+    runs = []
+    for mr in (10, 50):
+        ctx = M.Context(prob, precision=M.MLQP_MIXED, max_refine=mr)
+        ctx.solve_host()
+        n0 = ctx.launch_count()
+        out = ctx.solve_host()
+        runs.append((ctx.launch_count() - n0, out["aU"].copy(), out["aD"].copy()))
+        steps = ctx.block(M.BLK_REFINE, 1, 0).cpu().numpy()[1]
+        ctx.close()
+        assert steps < 10
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][2], runs[1][2])
+
+
 def test_mixed_precision_on_benchmark_stack(M):
     """Mixed form on the 20-interface, 3-angle stack: amplitudes agree with
     the plain FP64 GPU path and with the oracle to 1e-9."""
