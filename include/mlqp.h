@@ -161,6 +161,23 @@ mlqp_status mlqp_bind(mlqp_ctx* ctx, void* dev_workspace, size_t bytes, void* st
  * running every correction. */
 mlqp_status mlqp_solve_device(mlqp_ctx* ctx, void* d_eta, void* d_aU, void* d_aD, void* d_flux);
 
+/* Solves with the block factors the last FP64 solve left in the workspace
+ * (Sec. 3.3: P A' = L U, P the interfaces' row pivots, L block lower and U
+ * block upper bidiagonal), asynchronously on the bound stream, for all bound
+ * angles at once.  Vectors are n_theta x n_den complex128 in device memory,
+ * indexed like eta.
+ *   mlqp_solve_rhs:     A' eta = f for a caller right-hand side f (d_eta must
+ *                       not alias d_f; the workspace's own eta is overwritten)
+ *   mlqp_adjoint_solve: A'^H mu = h, the transposed block sweep: U^H, then L^H
+ *                       and the pivots (d_mu may equal d_h)
+ * With h = -X_1[P:]^H e_n on Gamma_1 (zero elsewhere), mu^H f is the upper
+ * Bragg amplitude a^U_n of the solve; such adjoint vectors carry gradients
+ * of the amplitudes back to the blocks of the system.  Errors: MLQP_ESTATE
+ * (not bound, or no solve since the last bind or stage before the sweep),
+ * MLQP_EINVAL (MLQP_MIXED, or bad buffers), MLQP_ECUDA. */
+mlqp_status mlqp_solve_rhs(mlqp_ctx* ctx, const void* d_f, void* d_eta);
+mlqp_status mlqp_adjoint_solve(mlqp_ctx* ctx, const void* d_h, void* d_mu);
+
 /* Synchronises the bound stream and returns the device-side status word. */
 mlqp_status mlqp_check_device(mlqp_ctx* ctx);
 

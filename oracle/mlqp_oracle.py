@@ -860,6 +860,17 @@ def block_thomas(Ad, Al, Au, f, I):
     return eta
 
 
+def adjoint_block_thomas(Ad, Al, Au, h, I):
+    """mu = A'^{-H} h by the same block elimination on the conjugate-transposed
+    system: (A'^H)_{i,i} = A'_{i,i}^H, (A'^H)_{i,i-1} = A'_{i-1,i}^H and
+    (A'^H)_{i,i+1} = A'_{i+1,i}^H (the adjoint of the Sec. 3.3 system)."""
+    H = lambda M: M.conj().T
+    Bd = {i: H(Ad[i]) for i in range(1, I + 1)}
+    Bl = {i: H(Au[i - 1]) for i in range(2, I + 1)}
+    Bu = {i: H(Al[i + 1]) for i in range(1, I)}
+    return block_thomas(Bd, Bl, Bu, h, I)
+
+
 def recover_amplitudes(prob, X, eta):
     """x_1 = -Q'^+_1 C'_{1,1} eta_1, x_{I+1} = -Q'^+_{I+1} C'_{I+1,I} eta_I; the
     Bragg amplitudes are their last 2K+1 entries (n = -K..K)."""

@@ -24,6 +24,9 @@ cudaError_t launch_recover(const Dev& D, cudaStream_t s);
 cudaError_t sweep_configure(int maxn);
 cudaError_t mixed_configure(int maxn);
 cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s);
+cudaError_t launch_solve_rhs(const Dev& D, const int* n_host, const double2* f, int* permv, double2* G,
+                             cudaStream_t s);
+cudaError_t launch_adjoint_solve(const Dev& D, const int* n_host, int* permv, double2* V, cudaStream_t s);
 cudaError_t launch_mixed_piece(const Dev& D, const int* n_host, int maxn, long n_den, double tol, int* permv,
                                const AngleStreams& A, bool cyclic, int piece);
 cudaError_t cr_configure(int maxn);
@@ -87,6 +90,7 @@ struct mlqp_ctx {
   cudaGraphExec_t pexec[MP_COUNT] = {};
   long plaunches[MP_COUNT] = {};
   int* hflag = nullptr;
+  bool factored = false;  // the FP64 block factors of the bound angles are in the workspace
 };
 
 static void drop_graphs(mlqp_ctx* c) {
@@ -472,8 +476,8 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
       take(cur, c->r_GH, d8 * nt * GM_HW);
       take(cur, c->r_GPART, z16 * nt * GM_NB * (GM_M + 1));
     }
-    take(cur, c->r_PERMV, sizeof(int) * nt * c->n_den);
   }
+  take(cur, c->r_PERMV, sizeof(int) * nt * c->n_den);
   take(cur, c->r_ETA, z16 * nt * c->n_den);
   take(cur, c->r_AMP, z16 * nt * 2 * nK);
   take(cur, c->r_FLUX, d8 * nt);
@@ -635,6 +639,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
     return cuda_fail(c, e, "kernel configuration");
   if ((e = make_angle_streams(c)) != cudaSuccess) return cuda_fail(c, e, "sweep streams");
   c->bound = true;
+  c->factored = false;
   return MLQP_OK;
 }
 
@@ -758,8 +763,11 @@ mlqp_status mlqp_run_stage(mlqp_ctx* c, int stage) {
   if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
   if (stage < MLQP_STAGE_GEOM || stage > MLQP_STAGE_RECOVER) return fail(c, MLQP_EINVAL, "unknown stage %d", stage);
   if (stage == MLQP_STAGE_SWEEP && c->prm.precision == MLQP_MIXED) return run_mixed_sweep(c);
-  return replay(c, c->gexec[stage], c->glaunches[stage], [&](cudaStream_t st) { return enqueue_stage(c, stage, st); },
-                "stage");
+  if (stage <= MLQP_STAGE_SCHUR) c->factored = false;
+  const mlqp_status st = replay(c, c->gexec[stage], c->glaunches[stage],
+                                [&](cudaStream_t s) { return enqueue_stage(c, stage, s); }, "stage");
+  if (st == MLQP_OK && stage == MLQP_STAGE_SWEEP) c->factored = true;
+  return st;
 }
 
 // Device time of `stage` (best of reps), each run preceded by the stages
@@ -897,6 +905,42 @@ mlqp_status mlqp_solve_device(mlqp_ctx* c, void* d_eta, void* d_aU, void* d_aD, 
     e = cudaMemcpyAsync(d_flux, c->D.FLUX, sizeof(double) * c->n_theta, cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "output copy");
   return MLQP_OK;
+}
+
+static mlqp_status factors_ready(mlqp_ctx* c) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  if (c->prm.precision != MLQP_FP64) return fail(c, MLQP_EINVAL, "solves with the stored factors need MLQP_FP64");
+  if (!c->factored) return fail(c, MLQP_ESTATE, "no block factors: run a solve for the bound angles first");
+  return MLQP_OK;
+}
+
+mlqp_status mlqp_solve_rhs(mlqp_ctx* c, const void* d_f, void* d_eta) {
+  mlqp_status st = factors_ready(c);
+  if (st != MLQP_OK) return st;
+  if (!d_f || !d_eta || d_f == d_eta) return fail(c, MLQP_EINVAL, "d_f and d_eta: distinct device buffers");
+  double2* out = static_cast<double2*>(d_eta);
+  g_launches = 0;
+  cudaError_t e = launch_solve_rhs(c->D, c->n_host.data(), static_cast<const double2*>(d_f), at<int>(c, c->r_PERMV),
+                                   out, c->stream);
+  c->launches += g_launches;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, c->D.ETA, sizeof(double2) * c->n_den * c->n_theta, cudaMemcpyDeviceToDevice, c->stream);
+  return e == cudaSuccess ? MLQP_OK : cuda_fail(c, e, "solve with the stored factors");
+}
+
+mlqp_status mlqp_adjoint_solve(mlqp_ctx* c, const void* d_h, void* d_mu) {
+  mlqp_status st = factors_ready(c);
+  if (st != MLQP_OK) return st;
+  if (!d_h || !d_mu) return fail(c, MLQP_EINVAL, "d_h and d_mu: device buffers");
+  double2* mu = static_cast<double2*>(d_mu);
+  cudaError_t e = cudaSuccess;
+  if (d_h != d_mu)
+    e = cudaMemcpyAsync(mu, d_h, sizeof(double2) * c->n_den * c->n_theta, cudaMemcpyDeviceToDevice, c->stream);
+  g_launches = 0;
+  if (e == cudaSuccess) e = launch_adjoint_solve(c->D, c->n_host.data(), at<int>(c, c->r_PERMV), mu, c->stream);
+  c->launches += g_launches;
+  return e == cudaSuccess ? MLQP_OK : cuda_fail(c, e, "adjoint solve");
 }
 
 mlqp_status mlqp_check_device(mlqp_ctx* c) {

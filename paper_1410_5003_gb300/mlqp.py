@@ -73,6 +73,10 @@ def load(path: str = LIB_PATH):
     lib.mlqp_autotune.restype = I
     lib.mlqp_solve_device.argtypes = [P, V, V, V, V]
     lib.mlqp_solve_device.restype = I
+    lib.mlqp_solve_rhs.argtypes = [P, V, V]
+    lib.mlqp_solve_rhs.restype = I
+    lib.mlqp_adjoint_solve.argtypes = [P, V, V]
+    lib.mlqp_adjoint_solve.restype = I
     lib.mlqp_check_device.argtypes = [P]
     lib.mlqp_check_device.restype = I
     lib.mlqp_solve.argtypes = [P, V, V, V, V]
@@ -98,6 +102,7 @@ def load(path: str = LIB_PATH):
 
 
 EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_set_angles", "mlqp_autotune",
+            "mlqp_solve_rhs", "mlqp_adjoint_solve",
             "mlqp_solve_device",
             "mlqp_check_device", "mlqp_solve", "mlqp_run_stage", "mlqp_block_info", "mlqp_last_error",
             "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes",
@@ -236,6 +241,30 @@ class Context:
 
     def check(self):
         _check(self.ctx, self.lib.mlqp_check_device(self.ctx))
+
+    def _vec(self, x):
+        t = self.torch
+        x = t.as_tensor(x, dtype=t.complex128, device=self.device)
+        if tuple(x.shape) != (self.n_theta, self.n_den):
+            raise ValueError(f"expected ({self.n_theta}, {self.n_den}), got {tuple(x.shape)}")
+        return x.contiguous()
+
+    def solve_rhs(self, f):
+        """mlqp_solve_rhs: eta = A'^{-1} f with the block factors of the last
+        FP64 solve (f: (n_theta, n_den) complex128, indexed like eta)."""
+        f = self._vec(f)
+        eta = self.torch.empty_like(f)
+        with self.torch.cuda.stream(self.stream):
+            _check(self.ctx, self.lib.mlqp_solve_rhs(self.ctx, ct.c_void_p(f.data_ptr()), ct.c_void_p(eta.data_ptr())))
+        return eta
+
+    def adjoint_solve(self, h):
+        """mlqp_adjoint_solve: mu = A'^{-H} h with the same factors."""
+        mu = self._vec(h).clone()
+        with self.torch.cuda.stream(self.stream):
+            _check(self.ctx, self.lib.mlqp_adjoint_solve(self.ctx, ct.c_void_p(mu.data_ptr()),
+                                                         ct.c_void_p(mu.data_ptr())))
+        return mu
 
     def host_outputs(self, eta=False, pinned=False):
         t = self.torch

@@ -180,6 +180,20 @@ def test_autotune_needs_a_bound_context(M):
     lib.mlqp_destroy(ctx)
 
 
+def test_solves_with_stored_factors_need_a_bound_fp64_context(M):
+    """mlqp_solve_rhs / mlqp_adjoint_solve refuse an unbound context, before
+    any device work."""
+    lib = M.load()
+    from workloads import small_stack
+    import ctypes as ct
+    ctx, _ = M.mlqp_setup(small_stack(I=2))
+    buf = ct.c_void_p(16)
+    assert lib.mlqp_solve_rhs(ctx, buf, ct.c_void_p(32)) == M.MLQP_ESTATE
+    assert lib.mlqp_adjoint_solve(ctx, buf, buf) == M.MLQP_ESTATE
+    assert lib.mlqp_solve_rhs(None, buf, buf) == M.MLQP_EINVAL
+    lib.mlqp_destroy(ctx)
+
+
 def test_set_angles_validation_without_a_device(M):
     """mlqp_set_angles checks count and range before anything else, and needs
     a bound context (none exists here, so no device work is reached)."""

@@ -1,0 +1,68 @@
+"""Pins of the oracle's adjoint block solve (the transposed system
+A'^H mu = h of Sec. 3.3's reduced block-tridiagonal system):
+- brute force: mu solves the dense conjugate-transposed system;
+- duality: with h = -X_1[P:]^H e_n on Gamma_1, mu^H f = h^H eta is the upper
+  Bragg amplitude a^U_n of the oracle's own solve (the identity the GPU
+  adjoint is tested by), to 1e-8 of the largest amplitude (the end-layer
+  near-null space of A' limits the adjoint route, see the test).  A random h is not used for duality: it excites
+  the near-null directions of the end blocks (condition 1e8 and more), where
+  mu is large and the identity holds only to kappa * eps; the Bragg rows do
+  not radiate into those directions.
+"""
+import numpy as np
+
+from oracle import mlqp_oracle as O
+from workloads import small_stack
+
+
+def _setup(I):
+    p = small_stack(I=I, N=40, P=40, Mw=24, K=8, M=30, lossy=(I == 3))
+    sc = O.schur(p, float(p.theta[0]))
+    eta = O.block_thomas(sc["Ad"], sc["Al"], sc["Au"], sc["f"], p.I)
+    return p, sc, eta
+
+
+def _flat(d, I):
+    return np.concatenate([d[i] for i in range(1, I + 1)])
+
+
+def test_adjoint_solves_the_dense_transposed_system():
+    for I in (1, 2, 3):
+        p, sc, _ = _setup(I)
+        A, f = O.dense_reduced_system(p, sc)
+        rng = np.random.default_rng(5 + I)
+        n = [2 * q.N for q in p.ifaces]
+        h = {i: rng.standard_normal(n[i - 1]) + 1j * rng.standard_normal(n[i - 1]) for i in range(1, I + 1)}
+        mu = _flat(O.adjoint_block_thomas(sc["Ad"], sc["Al"], sc["Au"], h, I), I)
+        hv = _flat(h, I)
+        r = A.conj().T @ mu - hv
+        assert np.linalg.norm(r) / (np.linalg.norm(A, 2) * np.linalg.norm(mu) + np.linalg.norm(hv)) < 1e-14
+        # against a dense solve, where the system is well enough conditioned to compare elementwise
+        if np.linalg.cond(A) < 1e8:
+            ref = np.linalg.solve(A.conj().T, hv)
+            assert np.max(np.abs(mu - ref)) / np.max(np.abs(ref)) < 1e-8
+
+
+def test_adjoint_gives_the_bragg_amplitudes():
+    for I in (2, 3):
+        p, sc, eta = _setup(I)
+        P = p.params.P
+        f = _flat(sc["f"], I)
+        ev = _flat(eta, I)
+        aU, _ = O.recover_amplitudes(p, sc["X"], eta)
+        n1 = 2 * p.ifaces[0].N
+        nd = ev.size
+        offs = np.concatenate([[0], np.cumsum([2 * q.N for q in p.ifaces])])
+        split = lambda v: {i: v[offs[i - 1]:offs[i]] for i in range(1, I + 1)}
+        # A' has a near-null direction at the end layers (condition 1e12 to
+        # 1e15 here) that does not radiate: the forward route's amplitudes do
+        # not see it, but mu picks up a large multiple of the left null
+        # vector u, and u^H f vanishes only to rounding.  The two routes agree
+        # to a few 1e-9 of the largest amplitude on these stacks; a wrong
+        # transpose, conjugation or pivot order is off by O(1).
+        tol = 1e-8
+        for order in (0, p.params.K, 2 * p.params.K):
+            h = np.zeros(nd, np.complex128)
+            h[:n1] = -np.conj(sc["X"][1][P + order, :])
+            mu = _flat(O.adjoint_block_thomas(sc["Ad"], sc["Al"], sc["Au"], split(h), I), I)
+            assert abs(np.vdot(mu, f) - aU[order]) < tol * np.max(np.abs(aU)), (I, order, tol)
