@@ -84,7 +84,7 @@ struct mlqp_ctx {
   // launch shapes (mlqp_autotune): QR cluster size, cyclic-reduction LU
   // cluster cap, angle groups of the sweep (0: min(n_theta, MAX_ANGLE_STREAMS)),
   // tile edge of the block LU's trailing update
-  int qr_cl = 8, cr_cl_max = 8, angle_groups = 0, upd_tile = 32;
+  int qr_cl = 8, cr_cl_max = 8, angle_groups = 0, upd_tile = 16;
   // the mixed block solve: one graph per piece (launch_mixed_piece), replayed by
   // a host loop that reads the active-angle counts into hflag (pinned)
   cudaGraphExec_t pexec[MP_COUNT] = {};
