@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(256) k_adj_mv(Dev D, int t, int dir, double2* 
 
 // U^H z = b (U upper, column-major, leading dimension n; udinv = 1/U_jj), in
 // place on y, vector in ys (shared).  Row i of U^H is column i of U.
-__device__ void upper_conj_trans_solve(const double2* U, int n, const double2* udinv, double2* y, double2* ys) {
-  __shared__ double2 blk[32][33];  // blk[j][l] = U[i0 + j, i0 + l]
+__device__ void upper_conj_trans_solve(const double2* U, int n, const double2* udinv, double2* y, double2* ys,
+                                       double2 (*blk)[33]) {  // blk[j][l] = U[i0 + j, i0 + l]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TRSV_THREADS / 32;
   for (int r = tid; r < n; r += TRSV_THREADS) ys[r] = y[r];
   for (int i0 = 0; i0 < n; i0 += 32) {
@@ -175,8 +175,8 @@ __device__ void upper_conj_trans_solve(const double2* U, int n, const double2* u
 
 // L^H w = b (L unit lower, column-major, leading dimension n), in place on
 // y, vector in ys (shared).  Row i of L^H is column i of L below the diagonal.
-__device__ void unit_lower_conj_trans_solve(const double2* L, int n, double2* y, double2* ys) {
-  __shared__ double2 blk[32][33];  // blk[j][l] = L[i0 + j, i0 + l]
+__device__ void unit_lower_conj_trans_solve(const double2* L, int n, double2* y, double2* ys,
+                                            double2 (*blk)[33]) {  // blk[j][l] = L[i0 + j, i0 + l]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = TRSV_THREADS / 32;
   for (int r = tid; r < n; r += TRSV_THREADS) ys[r] = y[r];
   const int nblk = (n + 31) / 32;
@@ -220,12 +220,13 @@ __global__ void __launch_bounds__(TRSV_THREADS) k_adj_trsv(Dev D, int t, int dir
   const IfaceDesc f = D.ifc[t];
   extern __shared__ __align__(16) unsigned char adj_raw[];
   double2* ys = reinterpret_cast<double2*>(adj_raw);
+  __shared__ double2 blk[32][33];  // the staged 32 x 32 diagonal block (16.9 KB; n <= 1024 adds 16 KB)
   double2* v = V + (size_t)a * D.eta_stride + f.eta_off;
-  const double2* blk = D.ROW + a * D.r_stride + f.row_off + (size_t)f.nl * f.n;
+  const double2* dblk = D.ROW + a * D.r_stride + f.row_off + (size_t)f.nl * f.n;
   if (dir == 0) {
-    upper_conj_trans_solve(blk, f.n, D.UDINV + a * D.piv_stride + f.eta_off, v, ys);
+    upper_conj_trans_solve(dblk, f.n, D.UDINV + a * D.piv_stride + f.eta_off, v, ys, blk);
   } else {
-    unit_lower_conj_trans_solve(blk, f.n, v, ys);
+    unit_lower_conj_trans_solve(dblk, f.n, v, ys, blk);
     __syncthreads();
     // mu = P^T w: (P x)_r = x[pv_r], so mu[pv_r] = w_r
     const int* pv = permv + a * D.piv_stride + f.eta_off;

@@ -22,7 +22,6 @@ cudaError_t launch_schur(const Dev& D, int max_tiles, cudaStream_t s);
 cudaError_t launch_sweep(const Dev& D, const int* n_host, const AngleStreams& A);
 cudaError_t launch_recover(const Dev& D, cudaStream_t s);
 cudaError_t sweep_configure(int maxn);
-cudaError_t mixed_configure(int maxn);
 cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s);
 cudaError_t launch_solve_rhs(const Dev& D, const int* n_host, const double2* f, int* permv, double2* G,
                              cudaStream_t s);
@@ -633,8 +632,6 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   if (e != cudaSuccess) return cuda_fail(c, e, "descriptor upload");
   if ((e = sweep_configure(c->maxn)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
   if ((e = lsq_configure(c->max_m, c->max_p)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
-  if (q.precision == MLQP_MIXED && (e = mixed_configure(c->maxn)) != cudaSuccess)
-    return cuda_fail(c, e, "kernel configuration");
   if (q.block_solver == MLQP_CYCLIC && (e = cr_configure(c->maxn)) != cudaSuccess)
     return cuda_fail(c, e, "kernel configuration");
   if ((e = make_angle_streams(c)) != cudaSuccess) return cuda_fail(c, e, "sweep streams");

@@ -471,8 +471,6 @@ cudaError_t launch_mixed_piece(const Dev& D, const int* n_host, int maxn, long n
   return cudaGetLastError();
 }
 
-cudaError_t mixed_configure(int) { return cudaSuccess; }
-
 }  // namespace mlqp
 
 namespace mlqp {

@@ -16,9 +16,10 @@
 // Each panel of NB columns takes three kernels: the panel factorisation (a
 // cluster of PCL CTAs per angle, panel rows split over their shared memory),
 // the row swaps / U12 rows / bottom multipliers (column- and row-parallel),
-// and the trailing update (32 x 32 tiles, complex 3M products).  With
-// look-ahead, the update first finishes the next panel's columns, and that
-// panel is factored on a second stream while the rest of the update runs.
+// and the trailing update (16 x 16 or 32 x 32 tiles, complex 3M products).
+// With look-ahead (compiled out, see LOOKAHEAD), the update first finishes
+// the next panel's columns, and that panel is factored on a second stream
+// while the rest of the update runs.
 // Angle groups run on streams of their own.  The kernels are templates on the
 // real type: FP64 for the plain path, FP32 for the factorisation of the
 // mixed-precision path (whose solves are refined in FP64, mlqp_mixed.cu).
