@@ -305,14 +305,22 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_trsm(Dev D, int s, int cw, co
   }
   __syncthreads();
   const int nblk = (n + 31) / 32;
+  // the 32 x 32 diagonal block of the current row block, staged once for all
+  // warps' recurrences: dblk[j][l] = LU[i0 + l, i0 + j]
+  __shared__ float2 dblk[32][33];
   // forward: unit lower L
   for (int b = 0; b < nblk; ++b) {
     const int i0 = 32 * b, wb = min(32, n - i0);
+    for (int e = tid; e < wb * wb; e += CR_THREADS) {
+      const int j = e / wb, l = e % wb;
+      dblk[j][l] = LU[(size_t)(i0 + j) * ld + i0 + l];
+    }
+    __syncthreads();
     for (int c = warp; c < cwn; c += CR_THREADS / 32) {
       cpx<float> v = (lane < wb) ? ldv<float>(&X[c * n + i0 + lane]) : mkc<float>(0.f);
       for (int j = 0; j + 1 < wb; ++j) {
         const float xr = __shfl_sync(0xffffffffu, v.re, j), xi = __shfl_sync(0xffffffffu, v.im, j);
-        if (lane > j && lane < wb) v = cfms(ldv<float>(&LU[(size_t)(i0 + j) * ld + i0 + lane]), mkc<float>(xr, xi), v);
+        if (lane > j && lane < wb) v = cfms(ldv<float>(&dblk[j][lane]), mkc<float>(xr, xi), v);
       }
       if (lane < wb) stv<float>(&X[c * n + i0 + lane], v);
     }
@@ -334,12 +342,17 @@ __global__ void __launch_bounds__(CR_THREADS) k_cr_trsm(Dev D, int s, int cw, co
   // backward: upper U (pivot reciprocals in ud)
   for (int b = nblk - 1; b >= 0; --b) {
     const int i0 = 32 * b, wb = min(32, n - i0);
+    for (int e = tid; e < wb * wb; e += CR_THREADS) {
+      const int j = e / wb, l = e % wb;
+      dblk[j][l] = LU[(size_t)(i0 + j) * ld + i0 + l];
+    }
+    __syncthreads();
     for (int c = warp; c < cwn; c += CR_THREADS / 32) {
       cpx<float> v = (lane < wb) ? ldv<float>(&X[c * n + i0 + lane]) : mkc<float>(0.f);
       for (int j = wb - 1; j >= 0; --j) {
         if (lane == j) v = v * ldv<float>(&ud[i0 + j]);
         const float xr = __shfl_sync(0xffffffffu, v.re, j), xi = __shfl_sync(0xffffffffu, v.im, j);
-        if (lane < j) v = cfms(ldv<float>(&LU[(size_t)(i0 + j) * ld + i0 + lane]), mkc<float>(xr, xi), v);
+        if (lane < j) v = cfms(ldv<float>(&dblk[j][lane]), mkc<float>(xr, xi), v);
       }
       if (lane < wb) stv<float>(&X[c * n + i0 + lane], v);
     }
