@@ -3,11 +3,14 @@
 //
 // Bessel/Hankel evaluation (own code, from the published formulas):
 //   |z| < 4        ascending series (Abramowitz & Stegun 9.1.10, 9.1.11)
-//   4 <= |z| < 20  Miller's backward recurrence J_{n-1} = (2n/z) J_n - J_{n+1}
-//                  (A&S 9.12), normalised by e^{-iz} = J_0 + 2 sum (-i)^n J_n
-//                  (real z: 1 = J_0 + 2 sum J_{2k}); Y_0 from Neumann's series
-//                  Y_0 = (2/pi)(ln(z/2)+gamma) J_0 - (4/pi) sum (-1)^k J_{2k}/k
-//                  (A&S 9.1.88) and Y_1 = -Y_0' from the same J_n
+//   4 <= |z| < 20  complex z: Miller's backward recurrence J_{n-1} = (2n/z) J_n
+//                  - J_{n+1} (A&S 9.12), normalised by e^{-iz} = J_0 + 2 sum
+//                  (-i)^n J_n; Y_0 from Neumann's series Y_0 = (2/pi)(ln(z/2)
+//                  + gamma) J_0 - (4/pi) sum (-1)^k J_{2k}/k (A&S 9.1.88) and
+//                  Y_1 = -Y_0' from the same J_n.  Real z: degree-16 Taylor
+//                  expansions about the centres of half-unit intervals
+//                  (coefficients from 30-digit derivatives, generated by
+//                  gen_bessel_taylor.py into mlqp_bessel_taylor.inc)
 //   |z| >= 20      Hankel's asymptotic expansion H_nu = sqrt(2/(pi z)) (P + iQ)
 //                  e^{i(z - (nu/2 + 1/4) pi)} (A&S 9.2.5-9.2.10)
 // Returned: H_0, H_1 and J_0, J_1 (the latter are the coefficients of the
@@ -185,6 +188,8 @@ constexpr double INV_4PI = 0.07957747154594766788;
 static __device__ const double DK[64] = {0.0, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0, 8.0, 9.0, 10.0, 11.0, 12.0, 13.0, 14.0, 15.0, 16.0, 17.0, 18.0, 19.0, 20.0, 21.0, 22.0, 23.0, 24.0, 25.0, 26.0, 27.0, 28.0, 29.0, 30.0, 31.0, 32.0, 33.0, 34.0, 35.0, 36.0, 37.0, 38.0, 39.0, 40.0, 41.0, 42.0, 43.0, 44.0, 45.0, 46.0, 47.0, 48.0, 49.0, 50.0, 51.0, 52.0, 53.0, 54.0, 55.0, 56.0, 57.0, 58.0, 59.0, 60.0, 61.0, 62.0, 63.0};
 static __device__ const double RK[64] = {0.0, 1.0 / 1, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31, 1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39, 1.0 / 40, 1.0 / 41, 1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47, 1.0 / 48, 1.0 / 49, 1.0 / 50, 1.0 / 51, 1.0 / 52, 1.0 / 53, 1.0 / 54, 1.0 / 55, 1.0 / 56, 1.0 / 57, 1.0 / 58, 1.0 / 59, 1.0 / 60, 1.0 / 61, 1.0 / 62, 1.0 / 63};
 
+#include "mlqp_bessel_taylor.inc"
+
 // ---------------------------------------------------------------------------
 // Real argument x > 0
 // ---------------------------------------------------------------------------
@@ -205,6 +210,8 @@ static __device__ __noinline__ Hank hankel_real(double x) {
     double s0 = 1.0, s1 = 1.0, sy0 = 0.0, sy1 = 1.0;
 #pragma unroll
     for (int k = 1; k <= 18; ++k) {
+      // the quotients 1/k^2, 1/(k(k+1)), 1/k, 1/(k+1) are compile-time
+      // constants (k is unrolled): no FP64 division in the loop
       t0 *= -q * (1.0 / ((double)k * k));
       t1 *= -q * (1.0 / ((double)k * (k + 1)));
       Hk += 1.0 / k;
@@ -219,39 +226,24 @@ static __device__ __noinline__ Hank hankel_real(double x) {
     Y0 = TWO_OVER_PI * (L * J0 - sy0);
     Y1 = -TWO_OVER_PI / x + TWO_OVER_PI * L * J1 - 0.5 * INV_PI * x * sy1;
   } else if (x < 20.0) {
-    const int N = 2 * (((int)(x + 36.0)) / 2);
-    const double tx = 2.0 / x;
-    double jn1 = 0.0, jn = 1e-30;  // J_{n+1}, J_n (unnormalised), n = N
-    double norm = 0.0, sy0 = 0.0, sy1 = 0.0;
-    double j1 = 0.0;
-    for (int n = N; n >= 1; --n) {
-      // accumulate the contributions of J_n
-      if ((n & 1) == 0) {
-        const int k = n >> 1;
-        norm += 2.0 * jn;
-        const double sgn = (k & 1) ? -1.0 : 1.0;
-        sy0 = fma(sgn * RK[k], jn, sy0);
-      } else {
-        // odd n = 2m+1: + (-1)^{m+1}/(m+1) J_n  (term k=m+1), - (-1)^m/m J_n (term k=m, m>=1)
-        const int m = n >> 1;
-        const double sgn = (m & 1) ? -1.0 : 1.0;  // (-1)^m
-        double c = -sgn * RK[m + 1];
-        if (m >= 1) c -= sgn * RK[m];
-        sy1 = fma(c, jn, sy1);
-      }
-      const double jm1 = fma(DK[n] * tx, jn, -jn1);
-      jn1 = jn;
-      jn = jm1;
-      if (n == 1) j1 = jn1;
+    // local Taylor expansions of J0, J1, Y0, Y1 about the centre of x's
+    // half-unit interval (mlqp_bessel_taylor.inc), Horner in four independent
+    // chains: 64 FMAs instead of a Miller recurrence of 40-56 dependent steps
+    const int m = min((int)((x - 4.0) * 2.0), 31);
+    const double t = x - (4.25 + 0.5 * m);
+    const double* c = BESSEL_TAYLOR + m * 68;
+    double a0 = __ldg(c + 16), a1 = __ldg(c + 33), a2 = __ldg(c + 50), a3 = __ldg(c + 67);
+#pragma unroll
+    for (int k = 15; k >= 0; --k) {
+      a0 = fma(a0, t, __ldg(c + k));
+      a1 = fma(a1, t, __ldg(c + 17 + k));
+      a2 = fma(a2, t, __ldg(c + 34 + k));
+      a3 = fma(a3, t, __ldg(c + 51 + k));
     }
-    // now jn = J_0 (unnormalised), j1 = J_1
-    norm += jn;
-    const double sc = 1.0 / norm;
-    J0 = jn * sc;
-    J1 = j1 * sc;
-    const double L = log(0.5 * x) + EULER_GAMMA;
-    Y0 = TWO_OVER_PI * (L * J0 - 2.0 * sy0 * sc);
-    Y1 = TWO_OVER_PI * (L * J1 - J0 / x + sy1 * sc);
+    J0 = a0;
+    J1 = a1;
+    Y0 = a2;
+    Y1 = a3;
   } else {
     // Hankel's expansion: t_k = prod_{i<=k} (mu - (2i-1)^2) / (k! (8x)^k)
     const double r8 = 0.125 / x;
