@@ -1,6 +1,6 @@
 """Writes mlqp_bessel_taylor.inc: Taylor coefficients f^(k)(c)/k!, k = 0..16,
-of J0, J1, Y0, Y1 at the centres c = 4.25 + 0.5 m (m = 0..31) of the
-half-unit intervals covering [4, 20), from 30-digit mpmath derivatives,
+of J0, J1, Y0, Y1 at the centres c = 4.25 + 0.5 m (m = 0..119) of the
+half-unit intervals covering [4, 64), from 30-digit mpmath derivatives,
 rounded to double.  The nearest singularity of these functions is the
 logarithm at 0, at distance c >= 4.25, and |x - c| <= 0.25, so the dropped
 terms are below 1e-17 of the functions' scale.  Run from this directory:
@@ -8,7 +8,7 @@ terms are below 1e-17 of the functions' scale.  Run from this directory:
 import mpmath as mp
 
 mp.mp.dps = 30
-DEG, M, X0, H = 16, 32, 4.0, 0.5
+DEG, M, X0, H = 16, 120, 4.0, 0.5
 
 
 def coeffs(fn, n, c):

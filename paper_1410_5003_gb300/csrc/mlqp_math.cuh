@@ -7,11 +7,11 @@
 //                  - J_{n+1} (A&S 9.12), normalised by e^{-iz} = J_0 + 2 sum
 //                  (-i)^n J_n; Y_0 from Neumann's series Y_0 = (2/pi)(ln(z/2)
 //                  + gamma) J_0 - (4/pi) sum (-1)^k J_{2k}/k (A&S 9.1.88) and
-//                  Y_1 = -Y_0' from the same J_n.  Real z: degree-16 Taylor
-//                  expansions about the centres of half-unit intervals
+//                  Y_1 = -Y_0' from the same J_n.  Real z < 64: degree-16
+//                  Taylor expansions about the centres of half-unit intervals
 //                  (coefficients from 30-digit derivatives, generated by
 //                  gen_bessel_taylor.py into mlqp_bessel_taylor.inc)
-//   |z| >= 20      Hankel's asymptotic expansion H_nu = sqrt(2/(pi z)) (P + iQ)
+//   |z| >= 20      (real z: >= 64) Hankel's asymptotic expansion H_nu = sqrt(2/(pi z)) (P + iQ)
 //                  e^{i(z - (nu/2 + 1/4) pi)} (A&S 9.2.5-9.2.10)
 // Returned: H_0, H_1 and J_0, J_1 (the latter are the coefficients of the
 // logarithmic singularity used by the log-split quadrature).
@@ -225,11 +225,12 @@ static __device__ __noinline__ Hank hankel_real(double x) {
     J1 = 0.5 * x * s1;
     Y0 = TWO_OVER_PI * (L * J0 - sy0);
     Y1 = -TWO_OVER_PI / x + TWO_OVER_PI * L * J1 - 0.5 * INV_PI * x * sy1;
-  } else if (x < 20.0) {
+  } else if (x < 64.0) {
     // local Taylor expansions of J0, J1, Y0, Y1 about the centre of x's
     // half-unit interval (mlqp_bessel_taylor.inc), Horner in four independent
     // chains: 64 FMAs instead of a Miller recurrence of 40-56 dependent steps
-    const int m = min((int)((x - 4.0) * 2.0), 31);
+    // (x < 20) or up to 40 asymptotic terms with a sincos (x >= 20)
+    const int m = min((int)((x - 4.0) * 2.0), 119);
     const double t = x - (4.25 + 0.5 * m);
     const double* c = BESSEL_TAYLOR + m * 68;
     double a0 = __ldg(c + 16), a1 = __ldg(c + 33), a2 = __ldg(c + 50), a3 = __ldg(c + 67);

@@ -57,12 +57,14 @@ def uneven_stack():
 
 # ---------------------------------------------------------------------------
 def test_hankel_functions_match_scipy(M):
-    """FP64 H0, H1, J0, J1 (series / Miller-Neumann / asymptotic regimes and
-    their switch points) against SciPy's AMOS routines, for real wavenumbers
-    and absorbing ones with Im k / Re k up to 0.1."""
+    """FP64 H0, H1, J0, J1 (series / Taylor tables (real) or Miller-Neumann
+    (complex) / asymptotic regimes and their switch points) against SciPy's
+    AMOS routines, for real wavenumbers and absorbing ones with Im k / Re k
+    up to 0.1."""
     for k in (1.0, 12.0 + 0.5j, 3.0 + 0.3j):
-        z_abs = np.concatenate([np.linspace(1e-3, 60, 6001), [3.9999999, 4.0, 4.0000001, 19.9999999, 20.0,
-                                                               20.0000001, 250.0, 1000.0]])
+        z_abs = np.concatenate([np.linspace(1e-3, 80, 8001), [3.9999999, 4.0, 4.0000001, 19.9999999, 20.0,
+                                                               20.0000001, 63.9999999, 64.0, 64.0000001,
+                                                               250.0, 1000.0]])
         rho = z_abs / abs(k)
         out = M.hankel_eval(k, rho)
         z = k * rho
