@@ -178,6 +178,20 @@ mlqp_status mlqp_solve_device(mlqp_ctx* ctx, void* d_eta, void* d_aU, void* d_aD
 mlqp_status mlqp_solve_rhs(mlqp_ctx* ctx, const void* d_f, void* d_eta);
 mlqp_status mlqp_adjoint_solve(mlqp_ctx* ctx, const void* d_h, void* d_mu);
 
+/* Adjoint of the per-layer regularised least squares (Sec. 3.2):
+ * Y_j = (Q'_j^H Q'_j + lam^2 I)^{-1} G_j for every layer j and angle, with the
+ * triangular factor R of [Q'_j; lam I] that the LSQ stage left in the
+ * workspace (Y = R^{-1} R^{-H} G).  If G_j is the sensitivity of a real
+ * functional to X_j, its sensitivity to C'_j is Q'_j Y_j and to Q'_j is
+ * (C'_j - Q'_j X_j) Y_j^H - Q'_j Y_j X_j^H (lam held fixed).  G and Y are
+ * device buffers of mlqp_x_elements complex128, laid out like the X blocks
+ * (MLQP_BLK_X offsets relative to layer 1, angle 0).  Asynchronous on the
+ * bound stream.  Errors: MLQP_ESTATE (not bound, or no LSQ stage since the
+ * last bind or fill), MLQP_EINVAL, MLQP_ECUDA. */
+mlqp_status mlqp_lsq_adjoint(mlqp_ctx* ctx, const void* d_G, void* d_Y);
+/* Complex entries of the X blocks of all layers and angles. */
+size_t mlqp_x_elements(const mlqp_ctx* ctx);
+
 /* Synchronises the bound stream and returns the device-side status word. */
 mlqp_status mlqp_check_device(mlqp_ctx* ctx);
 

@@ -797,6 +797,17 @@ def lsq(Q, C, rcond):
     return sla.solve_triangular(r, q.conj().T @ B, lower=False)
 
 
+def lsq_adjoint(Q, G, rcond):
+    """Y = (Q^H Q + lam^2 I)^{-1} G, lam as in lsq(): the adjoint of the
+    regularised least squares (a functional with sensitivity G to X has
+    sensitivity Q Y to C), by two triangular solves with the R of [Q; lam I]."""
+    m, p = Q.shape
+    lam = rcond * np.max(np.sqrt(np.sum(np.abs(Q) ** 2, axis=0)))
+    _, r = np.linalg.qr(np.vstack([Q, lam * np.eye(p)]))
+    z = sla.solve_triangular(r.conj().T, G, lower=True)
+    return sla.solve_triangular(r, z, lower=False)
+
+
 # ----------------------------------------------------------------------------
 # Sec. 3.2: Schur complements (eqs. Schur1 - Schuri)
 # ----------------------------------------------------------------------------

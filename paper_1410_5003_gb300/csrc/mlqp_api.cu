@@ -26,6 +26,7 @@ cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s);
 cudaError_t launch_solve_rhs(const Dev& D, const int* n_host, const double2* f, int* permv, double2* G,
                              cudaStream_t s);
 cudaError_t launch_adjoint_solve(const Dev& D, const int* n_host, int* permv, double2* V, cudaStream_t s);
+cudaError_t launch_lsq_adjoint(const Dev& D, int max_p, int max_c, const double2* G, double2* Y, cudaStream_t s);
 cudaError_t launch_mixed_piece(const Dev& D, const int* n_host, int maxn, long n_den, double tol, int* permv,
                                const AngleStreams& A, bool cyclic, int piece);
 cudaError_t cr_configure(int maxn);
@@ -90,6 +91,7 @@ struct mlqp_ctx {
   long plaunches[MP_COUNT] = {};
   int* hflag = nullptr;
   bool factored = false;  // the FP64 block factors of the bound angles are in the workspace
+  bool lsq_ready = false;  // the least-squares factors R of the bound angles are in the workspace
 };
 
 static void drop_graphs(mlqp_ctx* c) {
@@ -637,6 +639,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   if ((e = make_angle_streams(c)) != cudaSuccess) return cuda_fail(c, e, "sweep streams");
   c->bound = true;
   c->factored = false;
+  c->lsq_ready = false;
   return MLQP_OK;
 }
 
@@ -761,9 +764,11 @@ mlqp_status mlqp_run_stage(mlqp_ctx* c, int stage) {
   if (stage < MLQP_STAGE_GEOM || stage > MLQP_STAGE_RECOVER) return fail(c, MLQP_EINVAL, "unknown stage %d", stage);
   if (stage == MLQP_STAGE_SWEEP && c->prm.precision == MLQP_MIXED) return run_mixed_sweep(c);
   if (stage <= MLQP_STAGE_SCHUR) c->factored = false;
+  if (stage <= MLQP_STAGE_LSQ) c->lsq_ready = false;
   const mlqp_status st = replay(c, c->gexec[stage], c->glaunches[stage],
                                 [&](cudaStream_t s) { return enqueue_stage(c, stage, s); }, "stage");
   if (st == MLQP_OK && stage == MLQP_STAGE_SWEEP) c->factored = true;
+  if (st == MLQP_OK && stage == MLQP_STAGE_LSQ) c->lsq_ready = true;
   return st;
 }
 
@@ -925,6 +930,20 @@ mlqp_status mlqp_solve_rhs(mlqp_ctx* c, const void* d_f, void* d_eta) {
     e = cudaMemcpyAsync(out, c->D.ETA, sizeof(double2) * c->n_den * c->n_theta, cudaMemcpyDeviceToDevice, c->stream);
   return e == cudaSuccess ? MLQP_OK : cuda_fail(c, e, "solve with the stored factors");
 }
+
+mlqp_status mlqp_lsq_adjoint(mlqp_ctx* c, const void* d_G, void* d_Y) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  if (!c->lsq_ready) return fail(c, MLQP_ESTATE, "no least-squares factors: run the LSQ stage (or a solve) first");
+  if (!d_G || !d_Y || d_G == d_Y) return fail(c, MLQP_EINVAL, "d_G and d_Y: distinct device buffers");
+  g_launches = 0;
+  const cudaError_t e = launch_lsq_adjoint(c->D, c->max_p, c->max_c, static_cast<const double2*>(d_G),
+                                           static_cast<double2*>(d_Y), c->stream);
+  c->launches += g_launches;
+  return e == cudaSuccess ? MLQP_OK : cuda_fail(c, e, "least-squares adjoint");
+}
+
+size_t mlqp_x_elements(const mlqp_ctx* c) { return (c && c->valid) ? c->x_stride * (size_t)c->n_theta : 0; }
 
 mlqp_status mlqp_adjoint_solve(mlqp_ctx* c, const void* d_h, void* d_mu) {
   mlqp_status st = factors_ready(c);

@@ -424,6 +424,74 @@ __global__ void __launch_bounds__(256) k_schur(Dev D) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the regularised least squares (Sec. 3.2): Y_j = (Q'^H Q' +
+// lam^2 I)^{-1} G_j = R^{-1} R^{-H} G_j, with R the triangular factor of
+// [Q'_j; lam I] the QR kernel left in place (strict upper part in QP, 1/R_kk
+// in LAUX).  A functional of X_j = (Q'^H Q' + lam^2)^{-1} Q'^H C'_j with
+// sensitivity G_j to X_j has sensitivity Q'_j Y_j to C'_j and
+// (C'_j - Q'_j X_j) Y_j^H - Q'_j Y_j X_j^H to Q'_j.  G and Y are laid out
+// like X.  One warp per column: R^H z = g forward (column dots of R,
+// contiguous), then R y = z backward (row dots), vector in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int LADJ_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * LADJ_WARPS) k_lsq_adj(Dev D, const double2* G, double2* Y) {
+  const int jl = blockIdx.y, a = blockIdx.z;
+  const LayerDesc L = D.lay[jl];
+  const int p = L.p, ld = L.ldq;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * LADJ_WARPS + warp;
+  if (col >= L.c) return;
+  const double2* R = D.QP + a * D.qp_stride + L.qp_off;
+  const double2* rinv = reinterpret_cast<const double2*>(D.LAUX + a * D.laux_stride + 6 * L.aux_off);
+  extern __shared__ double2 ladj_sm[];
+  double2* z = ladj_sm + (size_t)warp * p;
+  const double2* g = G + a * D.x_stride + L.x_off + (size_t)col * p;
+  for (int i = lane; i < p; i += 32) z[i] = g[i];
+  __syncwarp();
+  for (int i = 0; i < p; ++i) {  // z_i = (g_i - sum_{r<i} conj(R_ri) z_r) / conj(R_ii)
+    const double2* ci = R + (size_t)i * ld;
+    double sr = 0.0, si = 0.0;
+    for (int r = lane; r < i; r += 32) {
+      const double2 m = ci[r], v = z[r];
+      sr = fma(m.x, v.x, fma(m.y, v.y, sr));
+      si = fma(m.x, v.y, fma(-m.y, v.x, si));
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) {
+      const cplx v = C(z[i].x - sr, z[i].y - si) * conj(ld2(&rinv[i]));
+      st2(&z[i], v);
+    }
+    __syncwarp();
+  }
+  for (int i = p - 1; i >= 0; --i) {  // y_i = (z_i - sum_{l>i} R_il y_l) / R_ii
+    double sr = 0.0, si = 0.0;
+    for (int l = i + 1 + lane; l < p; l += 32) {
+      const double2 m = R[(size_t)l * ld + i], v = z[l];
+      sr = fma(m.x, v.x, fma(-m.y, v.y, sr));
+      si = fma(m.x, v.y, fma(m.y, v.x, si));
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) {
+      const cplx v = C(z[i].x - sr, z[i].y - si) * ld2(&rinv[i]);
+      st2(&z[i], v);
+    }
+    __syncwarp();
+  }
+  double2* y = Y + a * D.x_stride + L.x_off + (size_t)col * p;
+  for (int i = lane; i < p; i += 32) y[i] = z[i];
+}
+
+cudaError_t launch_lsq_adjoint(const Dev& D, int max_p, int max_c, const double2* G, double2* Y, cudaStream_t s) {
+  ++g_launches;
+  k_lsq_adj<<<dim3((max_c + LADJ_WARPS - 1) / LADJ_WARPS, D.L, D.n_theta), 32 * LADJ_WARPS,
+              sizeof(double2) * LADJ_WARPS * max_p, s>>>(D, G, Y);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_lsq(const Dev& D, int max_m, int max_p, int max_c, cudaStream_t s) {
   ++g_launches;
   {

@@ -77,6 +77,10 @@ def load(path: str = LIB_PATH):
     lib.mlqp_solve_rhs.restype = I
     lib.mlqp_adjoint_solve.argtypes = [P, V, V]
     lib.mlqp_adjoint_solve.restype = I
+    lib.mlqp_lsq_adjoint.argtypes = [P, V, V]
+    lib.mlqp_lsq_adjoint.restype = I
+    lib.mlqp_x_elements.argtypes = [P]
+    lib.mlqp_x_elements.restype = Z
     lib.mlqp_check_device.argtypes = [P]
     lib.mlqp_check_device.restype = I
     lib.mlqp_solve.argtypes = [P, V, V, V, V]
@@ -102,7 +106,7 @@ def load(path: str = LIB_PATH):
 
 
 EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_set_angles", "mlqp_autotune",
-            "mlqp_solve_rhs", "mlqp_adjoint_solve",
+            "mlqp_solve_rhs", "mlqp_adjoint_solve", "mlqp_lsq_adjoint", "mlqp_x_elements",
             "mlqp_solve_device",
             "mlqp_check_device", "mlqp_solve", "mlqp_run_stage", "mlqp_block_info", "mlqp_last_error",
             "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes",
@@ -257,6 +261,36 @@ class Context:
         with self.torch.cuda.stream(self.stream):
             _check(self.ctx, self.lib.mlqp_solve_rhs(self.ctx, ct.c_void_p(f.data_ptr()), ct.c_void_p(eta.data_ptr())))
         return eta
+
+    def x_layout(self):
+        """{(layer j, angle a): (offset in complex entries, p_j, c_j)} of the X
+        blocks within an mlqp_x_elements-long buffer."""
+        base = None
+        out = {}
+        for a in range(self.n_theta):
+            for j in range(1, self.prob.I + 2):
+                off = ct.c_size_t()
+                r, c, ld = ct.c_int(), ct.c_int(), ct.c_int()
+                _check(self.ctx, self.lib.mlqp_block_info(self.ctx, BLK_X, j, a, ct.byref(off), ct.byref(r),
+                                                          ct.byref(c), ct.byref(ld)))
+                base = off.value if base is None else base
+                out[(j, a)] = ((off.value - base) // 16, r.value, c.value)
+        return out
+
+    def lsq_adjoint(self, G):
+        """mlqp_lsq_adjoint: {(j, a): Y_j} = (Q'^H Q' + lam^2)^{-1} G_j for the
+        given {(j, a): G_j} (p_j x c_j complex; missing blocks are zero)."""
+        t = self.torch
+        lay = self.x_layout()
+        n = int(self.lib.mlqp_x_elements(self.ctx))
+        g = t.zeros(n, dtype=t.complex128, device=self.device)
+        for key, (off, p, c) in lay.items():
+            if key in G:
+                g[off:off + p * c] = t.as_tensor(G[key], dtype=t.complex128, device=self.device).T.reshape(-1)
+        y = t.empty_like(g)
+        with t.cuda.stream(self.stream):
+            _check(self.ctx, self.lib.mlqp_lsq_adjoint(self.ctx, ct.c_void_p(g.data_ptr()), ct.c_void_p(y.data_ptr())))
+        return {key: y[off:off + p * c].reshape(c, p).T for key, (off, p, c) in lay.items()}
 
     def adjoint_solve(self, h):
         """mlqp_adjoint_solve: mu = A'^{-H} h with the same factors."""

@@ -191,6 +191,8 @@ def test_solves_with_stored_factors_need_a_bound_fp64_context(M):
     assert lib.mlqp_solve_rhs(ctx, buf, ct.c_void_p(32)) == M.MLQP_ESTATE
     assert lib.mlqp_adjoint_solve(ctx, buf, buf) == M.MLQP_ESTATE
     assert lib.mlqp_solve_rhs(None, buf, buf) == M.MLQP_EINVAL
+    assert lib.mlqp_lsq_adjoint(ctx, buf, ct.c_void_p(32)) == M.MLQP_ESTATE
+    assert lib.mlqp_x_elements(ctx) > 0
     lib.mlqp_destroy(ctx)
 
 

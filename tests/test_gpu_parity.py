@@ -653,3 +653,53 @@ def test_block_solve_is_differentiable(M):
     lin = torch.real(torch.sum(torch.conj(g) * d))
     ctx.close()
     assert abs(float(fd - lin)) < 1e-9 * max(1.0, abs(float(lin)))
+
+
+def test_lsq_adjoint_against_the_gpu_factors(M):
+    """mlqp_lsq_adjoint: Y_j = (Q'^H Q' + lam^2)^{-1} G_j with the R factors
+    the LSQ stage left in the workspace.  Backward error below 1e-13 against
+    Q'_j read before the stage, for every layer and angle.  And for layer 2,
+    central differences of Re<S, X_2> through the GPU least squares along a
+    random dC (added to the workspace's C'_2 after the fill) equal
+    Re<Q'_2 Y_2, dC>; the regularised problem has condition about
+    1/rcond = 1e10, so they agree to 1e-4 (as in the oracle's pin)."""
+    prob = PROBLEMS["small3"]()
+    ctx = M.Context(prob)
+    ctx.run_stage(M.STAGE_GEOM)
+    ctx.run_stage(M.STAGE_FILL)
+    torch.cuda.synchronize()
+    keys = [(j, a) for a in range(prob.n_theta) for j in range(1, prob.I + 2)]
+    Q = {k: ctx.block(M.BLK_QP, *k).cpu().numpy().copy() for k in keys}
+    ctx.run_stage(M.STAGE_LSQ)
+    rng = np.random.default_rng(8)
+    S = {}
+    for k in keys:
+        p_, c_ = ctx.block(M.BLK_X, *k).shape
+        S[k] = rng.standard_normal((p_, c_)) + 1j * rng.standard_normal((p_, c_))
+    Y = {k: v.cpu().numpy() for k, v in ctx.lsq_adjoint(S).items()}
+    rc = prob.params.lsq_rcond
+    for k in keys:
+        q = Q[k]
+        lam = rc * np.max(np.linalg.norm(q, axis=0))
+        Mx = q.conj().T @ q + lam ** 2 * np.eye(q.shape[1])
+        nq = np.linalg.norm(q, 2)
+        r = np.linalg.norm(Mx @ Y[k] - S[k]) / ((nq ** 2 + lam ** 2) * np.linalg.norm(Y[k]) + np.linalg.norm(S[k]))
+        assert r < 1e-13, (k, r)
+    k = (2, 0)
+    dC = None
+    eps = 1e-3
+
+    def phi(sign):
+        nonlocal dC
+        ctx.run_stage(M.STAGE_GEOM)
+        ctx.run_stage(M.STAGE_FILL)
+        blk = ctx.block(M.BLK_CP, *k)
+        if dC is None:
+            dC = rng.standard_normal(tuple(blk.shape)) + 1j * rng.standard_normal(tuple(blk.shape))
+        blk += sign * eps * torch.tensor(dC, device=blk.device)
+        ctx.run_stage(M.STAGE_LSQ)
+        return float(np.real(np.vdot(S[k], ctx.block(M.BLK_X, *k).cpu().numpy())))
+    fd = (phi(1.0) - phi(-1.0)) / (2 * eps)
+    an = float(np.real(np.vdot(Q[k] @ Y[k], dC)))
+    ctx.close()
+    assert abs(fd - an) < 1e-4 * max(1.0, abs(an)), (fd, an)

@@ -66,3 +66,32 @@ def test_adjoint_gives_the_bragg_amplitudes():
             h[:n1] = -np.conj(sc["X"][1][P + order, :])
             mu = _flat(O.adjoint_block_thomas(sc["Ad"], sc["Al"], sc["Au"], split(h), I), I)
             assert abs(np.vdot(mu, f) - aU[order]) < tol * np.max(np.abs(aU)), (I, order, tol)
+
+
+def test_lsq_adjoint_solves_the_regularised_normal_equations_and_gives_dC():
+    """Y = (Q^H Q + lam^2)^{-1} G: small backward error; and for the
+    functional Phi(C) = Re<S, X(C)> (linear in C), central differences along
+    a random dC equal Re<Q Y, dC> with Y from G = S."""
+    p = small_stack(I=2, N=40, P=40, Mw=24, K=8, M=30)
+    al = O.bloch(p, float(p.theta[0]))
+    asm = O.Assembler(p)
+    rng = np.random.default_rng(4)
+    for j in (1, 2, 3):
+        Q = asm.Qp(j, al["alpha"], al)
+        Cm = asm.Cp(j, al["alpha"])
+        rc = p.params.lsq_rcond
+        lam = rc * np.max(np.linalg.norm(Q, axis=0))
+        S = rng.standard_normal((Q.shape[1], Cm.shape[1])) + 1j * rng.standard_normal((Q.shape[1], Cm.shape[1]))
+        Y = O.lsq_adjoint(Q, S, rc)
+        Mx = Q.conj().T @ Q + lam ** 2 * np.eye(Q.shape[1])
+        nQ = np.linalg.norm(Q, 2)
+        assert np.linalg.norm(Mx @ Y - S) / ((nQ ** 2 + lam ** 2) * np.linalg.norm(Y) + np.linalg.norm(S)) < 1e-13
+        dC = rng.standard_normal(Cm.shape) + 1j * rng.standard_normal(Cm.shape)
+        eps = 1e-3
+        phi = lambda Cx: np.real(np.vdot(S, O.lsq(Q, Cx, rc)))
+        fd = (phi(Cm + eps * dC) - phi(Cm - eps * dC)) / (2 * eps)
+        an = np.real(np.vdot(Q @ Y, dC))
+        # [Q; lam I] has condition about 1/rcond = 1e10, so X(C) itself carries
+        # rounding errors of about 1e-6 relative in its near-null directions,
+        # where a random S makes Phi large: the differences agree to that
+        assert abs(fd - an) < 1e-4 * max(1.0, abs(an)), (j, fd, an)
