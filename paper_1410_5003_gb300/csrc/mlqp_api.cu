@@ -90,6 +90,9 @@ struct mlqp_ctx {
   cudaGraphExec_t pexec[MP_COUNT] = {};
   long plaunches[MP_COUNT] = {};
   int* hflag = nullptr;
+  // the FP64 solve as one graph (all stages), replayed by mlqp_solve_device
+  cudaGraphExec_t solve_exec = nullptr;
+  long solve_launches = 0;
   bool factored = false;  // the FP64 block factors of the bound angles are in the workspace
   bool lsq_ready = false;  // the least-squares factors R of the bound angles are in the workspace
 };
@@ -103,6 +106,8 @@ static void drop_graphs(mlqp_ctx* c) {
     if (g) cudaGraphExecDestroy(g);
     g = nullptr;
   }
+  if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+  c->solve_exec = nullptr;
 }
 
 static void destroy_angle_streams(mlqp_ctx* c) {
@@ -889,9 +894,21 @@ mlqp_status mlqp_autotune(mlqp_ctx* c, int which, double* report, int report_len
 mlqp_status mlqp_solve_device(mlqp_ctx* c, void* d_eta, void* d_aU, void* d_aD, void* d_flux) {
   if (!c) return MLQP_EINVAL;
   if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
-  for (int s = MLQP_STAGE_GEOM; s <= MLQP_STAGE_RECOVER; ++s) {
-    mlqp_status st = mlqp_run_stage(c, s);
+  if (c->prm.precision == MLQP_FP64) {
+    // every stage in one captured graph: one launch per solve
+    const mlqp_status st = replay(c, c->solve_exec, c->solve_launches, [&](cudaStream_t s) {
+      cudaError_t e = cudaSuccess;
+      for (int q = MLQP_STAGE_GEOM; q <= MLQP_STAGE_RECOVER && e == cudaSuccess; ++q) e = enqueue_stage(c, q, s);
+      return e;
+    }, "solve");
     if (st != MLQP_OK) return st;
+    c->factored = true;
+    c->lsq_ready = true;
+  } else {
+    for (int s = MLQP_STAGE_GEOM; s <= MLQP_STAGE_RECOVER; ++s) {
+      mlqp_status st = mlqp_run_stage(c, s);
+      if (st != MLQP_OK) return st;
+    }
   }
   const int nK = 2 * c->prm.K + 1;
   cudaError_t e = cudaSuccess;

@@ -278,6 +278,21 @@ def test_repeated_solves_are_bitwise_identical(M):
     o2 = ctx.solve_host(eta=True)
     assert np.array_equal(o1["eta"], o2["eta"])
     assert np.array_equal(o1["aU"], o2["aU"]) and np.array_equal(o1["aD"], o2["aD"])
+    # the FP64 solve is one captured graph of every stage: one replay, the same
+    # kernels as running the stages one by one, and bitwise the same results
+    for s_ in (M.STAGE_GEOM, M.STAGE_FILL, M.STAGE_LSQ, M.STAGE_SCHUR, M.STAGE_SWEEP, M.STAGE_RECOVER):
+        ctx.run_stage(s_)
+    n0 = ctx.launch_count()
+    for s_ in (M.STAGE_GEOM, M.STAGE_FILL, M.STAGE_LSQ, M.STAGE_SCHUR, M.STAGE_SWEEP, M.STAGE_RECOVER):
+        ctx.run_stage(s_)
+    per_stage = ctx.launch_count() - n0
+    a_stages = np.stack([ctx.block(M.BLK_AMP, 1, a).cpu().numpy()[:, 0] for a in range(prob.n_theta)])
+    n0 = ctx.launch_count()
+    out = ctx.outputs()
+    ctx.solve_device(out)
+    assert ctx.launch_count() - n0 == per_stage
+    a_graph = np.stack([ctx.block(M.BLK_AMP, 1, a).cpu().numpy()[:, 0] for a in range(prob.n_theta)])
+    assert np.array_equal(a_stages, a_graph)
     ctx.close()
 
 
