@@ -918,6 +918,111 @@ def solve(prob, itheta=0, asm=None, keep=False):
     return res
 
 
+# ----------------------------------------------------------------------------
+# Adjoint gradient of a Bragg-efficiency objective (the differentiation form:
+# transposed block solve, least-squares adjoint, block sensitivities).  The
+# derivatives of the blocks with respect to a parameter are taken by central
+# differences of this module's own assembly ("numeric kernel-derivative
+# pass"); everything else is the adjoint of the solve.
+# ----------------------------------------------------------------------------
+def reflected_weights(prob, theta, bl, orders=(0, -1)):
+    """w_n = k^U_n / (k_1 |sin theta|) for the propagating orders among
+    `orders` (0 otherwise): the reflected efficiency of order n is w_n |a^U_n|^2."""
+    K = prob.params.K
+    inc = prob.k[0].real * abs(math.sin(theta))
+    w = np.zeros(2 * K + 1)
+    for n in orders:
+        kv = bl["kU"][K + n]
+        if kv.imag == 0 and kv.real > 0:
+            w[K + n] = kv.real / inc
+    return w
+
+
+def bragg_objective(prob, asm=None, orders=(0, -1)):
+    """J = sum over the angles of the reflected efficiencies of `orders`."""
+    asm = asm or Assembler(prob)
+    J = 0.0
+    for a in range(prob.n_theta):
+        th = float(prob.theta[a])
+        r = solve(prob, a, asm)
+        w = reflected_weights(prob, th, bloch(prob, th), orders)
+        J += float(np.sum(w * np.abs(r["aU"]) ** 2))
+    return J
+
+
+def _blocks(prob, theta):
+    """The parameter-dependent blocks of one angle: A (unreduced), B, Q', C', f."""
+    asm = Assembler(prob)
+    bl = bloch(prob, theta)
+    al = bl["alpha"]
+    I = prob.I
+    A = {}
+    for i in range(1, I + 1):
+        for j in (i - 1, i, i + 1):
+            if 1 <= j <= I:
+                A[(i, j)] = asm.A(i, j, al)
+    B = {(i, j): asm.B(i, j) for i in range(1, I + 1) for j in (i, i + 1)}
+    Qp = {j: asm.Qp(j, al, bl) for j in range(1, I + 2)}
+    Cp = {j: asm.Cp(j, al) for j in range(1, I + 2)}
+    return dict(A=A, B=B, Qp=Qp, Cp=Cp, f=rhs(prob, theta), w=reflected_weights(prob, theta, bl))
+
+
+def adjoint_gradient(prob, shifted, step, orders=(0, -1)):
+    """dJ/dp for J = bragg_objective(prob) and each parameter p given by
+    shifted[p](t) -> the problem with p moved by t.  Per angle: the forward
+    solve; g = w a^U; the adjoint block solve A'^H mu = h, h = -X_1[P:]^H g on
+    Gamma_1; Psi_j = sum B_{i,j}^H mu_i (proxy rows) and -g (Rayleigh rows of
+    layer 1); Y_j = (Q'^H Q' + lam^2)^{-1} Psi_j eta_j^H; then
+        dJ = 2 Re[ mu^H df - <mu eta^H, dA> + <mu (X eta)^H, dB>
+                   + <Q' Y, dC'> + <(C' - Q' X) Y^H - Q' Y X^H, dQ'> ] + dw |a|^2,
+    with the block derivatives by fourth-order central differences of the
+    assembly (steps step[p], 2 step[p]); lam is held fixed."""
+    I, P, K = prob.I, prob.params.P, prob.params.K
+    rc = prob.params.lsq_rcond
+    grad = {p: 0.0 for p in shifted}
+    for a in range(prob.n_theta):
+        th = float(prob.theta[a])
+        sc = schur(prob, th)
+        eta = block_thomas(sc["Ad"], sc["Al"], sc["Au"], sc["f"], I)
+        X = sc["X"]
+        aU = -(X[1][P:, :] @ eta[1])
+        w = reflected_weights(prob, th, sc["bloch"], orders)
+        g = w * aU
+        h = {i: np.zeros_like(eta[i]) for i in range(1, I + 1)}
+        h[1] = -(X[1][P:, :].conj().T @ g)
+        mu = adjoint_block_thomas(sc["Ad"], sc["Al"], sc["Au"], h, I)
+        etaL = {j: np.concatenate([eta[i] for i in layer_columns(prob, j)]) for j in range(1, I + 2)}
+        asm = Assembler(prob)
+        Bb = {(i, j): asm.B(i, j) for i in range(1, I + 1) for j in (i, i + 1)}
+        SC, SQ, SB = {}, {}, {}
+        for j in range(1, I + 2):
+            Psi = np.zeros(X[j].shape[0], np.complex128)
+            for i in (j - 1, j):  # interfaces whose A' uses X_j[:P] through B_{i,j}
+                if 1 <= i <= I:
+                    Psi[:P] += Bb[(i, j)].conj().T @ mu[i]
+            if j == 1:
+                Psi[P:] = -g
+            Y = lsq_adjoint(sc["Qp"][j], np.outer(Psi, etaL[j].conj()), rc)
+            SC[j] = sc["Qp"][j] @ Y
+            SQ[j] = (sc["Cp"][j] - sc["Qp"][j] @ X[j]) @ Y.conj().T - sc["Qp"][j] @ Y @ X[j].conj().T
+        for i in range(1, I + 1):
+            for j in (i, i + 1):
+                SB[(i, j)] = np.outer(mu[i], (X[j][:P, :] @ etaL[j]).conj())
+        for p, make in shifted.items():
+            t = step[p]
+            Bk = {s_: _blocks(make(s_ * t), th) for s_ in (-2, -1, 1, 2)}
+            d = lambda get: (-get(Bk[2]) + 8 * get(Bk[1]) - 8 * get(Bk[-1]) + get(Bk[-2])) / (12 * t)
+            acc = np.vdot(mu[1], d(lambda b: b["f"]))
+            for (i, j) in Bk[1]["A"]:
+                acc -= np.vdot(mu[i], d(lambda b: b["A"][(i, j)]) @ eta[j])
+            for key in SB:
+                acc += np.vdot(SB[key], d(lambda b: b["B"][key]))
+            for j in range(1, I + 2):
+                acc += np.vdot(SC[j], d(lambda b: b["Cp"][j])) + np.vdot(SQ[j], d(lambda b: b["Qp"][j]))
+            grad[p] += 2.0 * acc.real + float(np.sum(d(lambda b: b["w"]) * np.abs(aU) ** 2))
+    return grad
+
+
 def solve_all(prob):
     asm = Assembler(prob)
     return [solve(prob, t, asm) for t in range(prob.n_theta)]

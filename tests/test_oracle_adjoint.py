@@ -95,3 +95,45 @@ def test_lsq_adjoint_solves_the_regularised_normal_equations_and_gives_dC():
         # rounding errors of about 1e-6 relative in its near-null directions,
         # where a random S makes Phi large: the differences agree to that
         assert abs(fd - an) < 1e-4 * max(1.0, abs(an)), (j, fd, an)
+
+
+def test_adjoint_gradient_matches_central_differences():
+    """Gradient of J = sum over angles of the reflected 0th and -1st order
+    efficiencies, with respect to layer wavenumbers and interface Fourier
+    coefficients: the oracle's adjoint (transposed block solve, least-squares
+    adjoint, block sensitivities contracted with block derivatives by central
+    differences of the assembly) against central differences of J itself
+    (h = 1e-6), to 1e-6 relative.  The stack uses lsq_rcond = 1e-6: the
+    per-block terms of the end layers are of order 0.3 and cancel to 1e-2,
+    and at the default 1e-10 the regularisation's 1/lam ~ 1e10 amplifies the
+    1e-13 error of difference-quotient block derivatives past that (the
+    adjoint then misses by O(1); at 1e-8 it agrees to 2e-6, at 1e-6 to 1e-9)."""
+    from dataclasses import replace
+    from workloads.problems import Interface
+    base = small_stack(I=2, N=40, P=40, Mw=24, K=8, M=30, n_angles=2)
+    prob = replace(base, params=replace(base.params, lsq_rcond=1e-6)).with_angles([-0.9, -2.1])
+
+    def shift_k(j):
+        def make(t):
+            k = prob.k.copy()
+            k[j] += t
+            return replace(prob, k=k)
+        return make
+
+    def shift_shape(i, which, m):
+        def make(t):
+            ifs = list(prob.ifaces)
+            f = ifs[i]
+            a, b = f.a.copy(), f.b.copy()
+            (a if which == "a" else b)[m] += t
+            ifs[i] = Interface(f.y0, a, b, f.N)
+            return replace(prob, ifaces=ifs)
+        return make
+
+    shifted = {"k1": shift_k(0), "k2": shift_k(1), "k3": shift_k(2),
+               "a1[1]": shift_shape(0, "a", 0), "b2[2]": shift_shape(1, "b", 1)}
+    grad = O.adjoint_gradient(prob, shifted, {p: 1e-3 for p in shifted})
+    for p, make in shifted.items():
+        hfd = 1e-6
+        fd = (O.bragg_objective(make(hfd)) - O.bragg_objective(make(-hfd))) / (2 * hfd)
+        assert abs(grad[p] - fd) < 1e-6 * max(abs(fd), 1e-3), (p, grad[p], fd)
