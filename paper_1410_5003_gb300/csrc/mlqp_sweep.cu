@@ -645,8 +645,11 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
     auto panel = [&](int k, cudaStream_t st) {
       const int w = (nt - k < NB) ? nt - k : NB;
       const size_t rc = (size_t)((nt - k + PCL - 1) / PCL);
-      // at least PANEL_SMEM_MIN, so that no two panel CTAs share an SM's FP64 pipes
-      const size_t smem = std::max(rc * (w + 1) * sizeof(vec2<R>) + rc * sizeof(unsigned), PANEL_SMEM_MIN);
+      // FP64: at least PANEL_SMEM_MIN, so that no two panel CTAs share an SM's
+      // FP64 pipes.  FP32 (the mixed form's factorisation) is not FP64-bound:
+      // its panels may share SMs, which lets large angle batches run in one wave.
+      const size_t smem = std::max(rc * (w + 1) * sizeof(vec2<R>) + rc * sizeof(unsigned),
+                                   sizeof(R) == 8 ? PANEL_SMEM_MIN : size_t(0));
       ++g_launches;
       k_lu_panel_cl<R><<<dim3(PCL, na), PCL_THREADS, smem, st>>>(D, t, k, a0);
     };
