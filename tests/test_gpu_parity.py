@@ -545,6 +545,36 @@ def test_corner_grating_at_full_size(M):
     assert rel(ag, np.concatenate([ref["aU"][0], ref["aD"][0]])) < AMP_TOL
 
 
+def test_angle_sweep_stack_blocks_at_full_size(M):
+    """The 100-interface angle-sweep stack at full size (N_i from 80 to 320,
+    uneven), two of its angles: sampled blocks (interfaces 1, 50, 100 with
+    their neighbours; layers 1, 50, 101) equal the oracle's."""
+    th = np.asarray(config4().theta)
+    prob = config4().with_angles(th[[0, 200]])
+    I, P = prob.I, prob.params.P
+    ctx = M.Context(prob)
+    ctx.run_stage(M.STAGE_GEOM)
+    ctx.run_stage(M.STAGE_FILL)
+    torch.cuda.synchronize()
+    asm = O.Assembler(prob)
+    for a in range(prob.n_theta):
+        bl = O.bloch(prob, prob.theta[a])
+        al = bl["alpha"]
+        for i in (1, 50, I):
+            row = ctx.block(M.BLK_ROW, i, a).cpu().numpy()
+            n = 2 * prob.ifaces[i - 1].N
+            nl = 2 * prob.ifaces[i - 2].N if i > 1 else 0
+            assert rel(row[:, nl:nl + n], asm.A(i, i, al)) < BLOCK_TOL, (a, i)
+            if i < I:
+                assert rel(row[:, nl + n:], asm.A(i, i + 1, al)) < BLOCK_TOL, (a, i)
+            if i > 1:
+                assert rel(row[:, :nl], asm.A(i, i - 1, al)) < BLOCK_TOL, (a, i)
+        for j in (1, 50, I + 1):
+            assert rel(ctx.block(M.BLK_QP, j, a).cpu().numpy(), asm.Qp(j, al, bl)) < BLOCK_TOL, (a, j)
+            assert rel(ctx.block(M.BLK_CP, j, a).cpu().numpy(), asm.Cp(j, al)) < BLOCK_TOL, (a, j)
+    ctx.close()
+
+
 def test_set_angles_sweeps_in_chunks(M):
     """An angle sweep in chunks through one context (mlqp_set_angles) gives,
     bit for bit, what a context set up with those angles gives."""
@@ -592,14 +622,16 @@ def _factored(M, prob):
     return ctx, f0, rows, X1
 
 
-@pytest.mark.parametrize("name", ["small3", "uneven", "corner2"])
+@pytest.mark.parametrize("name", ["small3", "uneven", "corner2", "corner2_deep"])
 def test_solves_with_stored_factors(M, name):
     """mlqp_solve_rhs (A' eta = f) and mlqp_adjoint_solve (A'^H mu = h, the
     transposed block sweep) with the factors of the FP64 solve: normwise
     backward error below 1e-13 against the A' blocks read before the sweep,
     and solve_rhs of the solve's own right-hand side reproduces its
     amplitudes to 1e-9."""
-    prob = PROBLEMS[name]()
+    # corner2_deep: 512 nodes per interface (4 panel levels), n = 1024, the largest block the
+    # library accepts
+    prob = corner_stack(I=2, levels=4, K=24, M=50) if name == "corner2_deep" else PROBLEMS[name]()
     ctx, f0, rows, X1 = _factored(M, prob)
     out = ctx.outputs()
     ctx.run_stage(M.STAGE_RECOVER)
