@@ -102,6 +102,13 @@ __device__ void legendre_upto(double x, double* P) {  // P_0..P_{PANEL_P-1}(x)
   P[1] = x;
   for (int n = 1; n + 1 < PANEL_P; ++n) P[n + 1] = ((2 * n + 1) * x * P[n] - n * P[n - 1]) / (n + 1);
 }
+// the same recurrence with 1/(n+1) from the RK table: no FP64 division
+__device__ __forceinline__ void legendre_upto_mul(double x, double* P) {
+  P[0] = 1.0;
+  P[1] = x;
+#pragma unroll
+  for (int n = 1; n + 1 < PANEL_P; ++n) P[n + 1] = ((2 * n + 1) * x * P[n] - n * P[n - 1]) * RK[n + 1];
+}
 
 __global__ void k_geom_panels(Dev D) {
   if (blockIdx.x == 0 && threadIdx.x < PANEL_P) {
@@ -218,8 +225,6 @@ __global__ void __launch_bounds__(128) k_geom_near(Dev D) {
     const int code = s_code[s], l = code / npan - 1, q = code % npan, pq = f.pan_off + q;
     const double xa = D.PXA[pq] + l * D.d, ya = D.PYA[pq], xb = D.PXB[pq] + l * D.d, yb = D.PYB[pq];
     const double dx = xb - xa, dy = yb - ya, h = sqrt(dx * dx + dy * dy), half = 0.5 * h;
-    double acc[PANEL_P];
-    for (int j = 0; j < PANEL_P; ++j) acc[j] = 0.0;
     if (l == 0 && q == own) {
       if (lane < PANEL_P) {
         const double t = D.GL16[m % PANEL_P];
@@ -242,7 +247,13 @@ __global__ void __launch_bounds__(128) k_geom_near(Dev D) {
     ss = fmin(1.0, fmax(-1.0, ss));
     const double qx = cx + ss * 0.5 * dx, qy = cy + ss * 0.5 * dy;
     const double dist = fmax(sqrt((x - qx) * (x - qx) + (y - qy) * (y - qy)) / half, 1e-14);
-    // pieces: [ss - 2^k dist, ...] on both sides, clipped to [-1, 1]
+    // pieces: [ss - 2^k dist, ...] on both sides, clipped to [-1, 1].  The
+    // Legendre moments sum fw P_n(su) are accumulated per point (16 FMAs) and
+    // turned into the 16 Lagrange weights once per panel (W_j = sum_n c_jn mom_n,
+    // the basis l_j = sum_n c_jn P_n being linear).
+    double mom[PANEL_P];
+#pragma unroll
+    for (int n = 0; n < PANEL_P; ++n) mom[n] = 0.0;
     for (int side = 0; side < 2; ++side) {
       double lo = ss, step = dist;
       const double end = side ? 1.0 : -1.0;
@@ -254,25 +265,27 @@ __global__ void __launch_bounds__(128) k_geom_near(Dev D) {
           const double su = 0.5 * (u0 + u1) + 0.5 * (u1 - u0) * D.GL16[lane];
           const double wu = 0.5 * (u1 - u0) * D.GL16[PANEL_P + lane];
           const double yx = cx + su * 0.5 * dx, yy = cy + su * 0.5 * dy;
-          const double fw = wu * log(sqrt((x - yx) * (x - yx) + (y - yy) * (y - yy)));
+          const double fw = wu * 0.5 * log((x - yx) * (x - yx) + (y - yy) * (y - yy));
           double P[PANEL_P];
-          legendre_upto(su, P);
+          legendre_upto_mul(su, P);
 #pragma unroll
-          for (int j = 0; j < PANEL_P; ++j) {
-            double lj = 0.0;
-            for (int n = 0; n < PANEL_P; ++n) lj = fma(cjn[j * PANEL_P + n], P[n], lj);
-            acc[j] = fma(lj, fw, acc[j]);
-          }
+          for (int n = 0; n < PANEL_P; ++n) mom[n] = fma(P[n], fw, mom[n]);
         }
         lo = hi;
         step *= 2.0;
       }
     }
 #pragma unroll
-    for (int j = 0; j < PANEL_P; ++j) {
-      double v = (lane < PANEL_P) ? acc[j] : 0.0;
+    for (int n = 0; n < PANEL_P; ++n) {
+      double v = (lane < PANEL_P) ? mom[n] : 0.0;
       for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if (lane == 0) W[s * PANEL_P + j] = half * v;
+      mom[n] = v;  // every lane holds the panel's moments
+    }
+    if (lane < PANEL_P) {
+      double w = 0.0;
+#pragma unroll
+      for (int n = 0; n < PANEL_P; ++n) w = fma(cjn[lane * PANEL_P + n], mom[n], w);
+      W[s * PANEL_P + lane] = half * w;
     }
   }
 }
