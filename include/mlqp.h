@@ -192,6 +192,41 @@ mlqp_status mlqp_lsq_adjoint(mlqp_ctx* ctx, const void* d_G, void* d_Y);
 /* Complex entries of the X blocks of all layers and angles. */
 size_t mlqp_x_elements(const mlqp_ctx* ctx);
 
+/* Gradient of a real functional of the upper Bragg amplitudes (Sec. 3.3 and
+ * 3.2, the adjoints of the block sweep and of the least squares),
+ * J = sum_a sum_n w_n |a^U_n|^2, along one parameter p of the problem
+ * (a wavenumber, an interface coefficient, ...), at fixed w and lam:
+ *     grad[a] = 2 Re dF_a/dp,
+ * with F_a the contraction of the rank-one block sensitivities of angle a
+ * (-mu eta^H to A, mu (X eta)[:P]^H to B, mu to f, (Q'y) eta^H to C',
+ * r y^H - (Q'y)(X eta)^H to Q', where A'^H mu = -X_1[P:]^H g on Gamma_1 and
+ * y = (Q'^H Q' + lam^2)^{-1} Psi) with the blocks, and dF/dp its
+ * fourth-order central difference over the blocks of the problem moved along
+ * p by -2t, -t, t, 2t:  (F(-2t) - 8 F(-t) + 8 F(t) - F(2t)) / (12 t).
+ * The caller adds the dw/dp |a^U|^2 term of its own weights.
+ *   ctx:    an MLQP_FP64 context solved for its bound angles (mlqp_solve or
+ *           the stages through the sweep); its eta is the one in the
+ *           workspace.  On return the workspace holds the filled, unreduced
+ *           blocks at t = 0 (the factors are gone: solve again before
+ *           mlqp_solve_rhs, mlqp_adjoint_solve or another gradient).
+ *   moved:  4 bound MLQP_FP64 contexts of the problem moved by -2t, -t, t,
+ *           2t (same discretisation, angles and layout as ctx, each its own
+ *           workspace); their geometry and fill stages run here, on their
+ *           streams, and the base stream waits for them.
+ *   d_g:    device, n_theta x (2K+1) complex128: g = w a^U per angle.
+ *   d_work: device, 256-byte aligned, >= mlqp_gradient_work_bytes(ctx)
+ *           bytes of caller-owned scratch.
+ *   grad:   host, n_theta doubles (one term per angle; J's gradient is
+ *           their sum plus the weights' term).
+ * Synchronous: returns after the result is on the host.  Errors: MLQP_ESTATE
+ * (no solve), MLQP_EINVAL (a moved context that differs from ctx, shares a
+ * workspace or is not FP64; t zero or not finite; bad buffers), MLQP_ENOMEM
+ * (work buffer too small), MLQP_ECUDA, and the device status of any of the
+ * five contexts. */
+size_t mlqp_gradient_work_bytes(const mlqp_ctx* ctx);
+mlqp_status mlqp_fd_gradient(mlqp_ctx* ctx, mlqp_ctx* const* moved, double t, const void* d_g, void* d_work,
+                             size_t work_bytes, double* grad);
+
 /* Synchronises the bound stream and returns the device-side status word. */
 mlqp_status mlqp_check_device(mlqp_ctx* ctx);
 

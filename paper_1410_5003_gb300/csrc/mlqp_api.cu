@@ -27,6 +27,11 @@ cudaError_t launch_solve_rhs(const Dev& D, const int* n_host, const double2* f, 
                              cudaStream_t s);
 cudaError_t launch_adjoint_solve(const Dev& D, const int* n_host, int* permv, double2* V, cudaStream_t s);
 cudaError_t launch_lsq_adjoint(const Dev& D, int max_p, int max_c, const double2* G, double2* Y, cudaStream_t s);
+cudaError_t launch_grad_adjoint(const Dev& D, const int* n_host, int* permv, int max_p, const GradVecs& V,
+                                cudaStream_t s);
+cudaError_t launch_grad_base_lsq(const Dev& D, const GradVecs& V, cudaStream_t s);
+cudaError_t launch_grad_form(const Dev& Dm, const GradVecs& V, int slot, cudaStream_t s);
+cudaError_t launch_grad_combine(const Dev& D, const GradVecs& V, double t, cudaStream_t s);
 cudaError_t launch_mixed_piece(const Dev& D, const int* n_host, int maxn, long n_den, double tol, int* permv,
                                const AngleStreams& A, bool cyclic, int piece);
 cudaError_t cr_configure(int maxn);
@@ -974,6 +979,128 @@ mlqp_status mlqp_adjoint_solve(mlqp_ctx* c, const void* d_h, void* d_mu) {
   if (e == cudaSuccess) e = launch_adjoint_solve(c->D, c->n_host.data(), at<int>(c, c->r_PERMV), mu, c->stream);
   c->launches += g_launches;
   return e == cudaSuccess ? MLQP_OK : cuda_fail(c, e, "adjoint solve");
+}
+
+// The gradient's work buffer: regions of 256-byte-aligned bytes, in the
+// order of GradVecs.  Returns the total; fills V when base is given.
+static size_t grad_layout(const mlqp_ctx* c, char* base, GradVecs* V) {
+  const size_t nt = c->n_theta, nd = c->n_den, sp = c->sum_p, vm = (size_t)c->L * c->max_m;
+  const size_t bytes[10] = {16 * nt * nd, 16 * nt * nd, 16 * nt * sp, 16 * nt * sp, 16 * nt * sp,
+                            16 * nt * vm, 16 * nt * vm, 16 * nt * (c->I + c->L), 16 * nt * 4, 8 * nt};
+  size_t off[10], cur = 0;
+  for (int q = 0; q < 10; ++q) {
+    off[q] = cur;
+    cur += (bytes[q] + 255) / 256 * 256;
+  }
+  if (base && V) {
+    auto p2 = [&](int q) { return reinterpret_cast<double2*>(base + off[q]); };
+    V->eta = p2(0);
+    V->mu = p2(1);
+    V->psi = p2(2);
+    V->y = p2(3);
+    V->xi = p2(4);
+    V->qy = p2(5);
+    V->rv = p2(6);
+    V->part = p2(7);
+    V->fs = p2(8);
+    V->grad = reinterpret_cast<double*>(base + off[9]);
+    V->n_den = nd;
+    V->sum_p = sp;
+    V->max_m = c->max_m;
+  }
+  return cur;
+}
+
+size_t mlqp_gradient_work_bytes(const mlqp_ctx* c) { return (c && c->valid) ? grad_layout(c, nullptr, nullptr) : 0; }
+
+// A moved context must hold the same discretisation as the base: every size
+// and offset of the blocks, and the angles.
+static bool same_layout(const mlqp_ctx* c, const mlqp_ctx* m) {
+  if (m->I != c->I || m->L != c->L || m->n_theta != c->n_theta || m->n_den != c->n_den) return false;
+  if (m->prm.P != c->prm.P || m->prm.Mw != c->prm.Mw || m->prm.K != c->prm.K || m->prm.M != c->prm.M) return false;
+  if (m->theta != c->theta || m->n_host != c->n_host || m->sum_p != c->sum_p) return false;
+  if (m->D.r_stride != c->D.r_stride || m->D.f_stride != c->D.f_stride || m->D.qp_stride != c->D.qp_stride ||
+      m->D.cp_stride != c->D.cp_stride)
+    return false;
+  for (int i = 0; i < c->I; ++i) {
+    const IfaceDesc &a = c->ifc[i], &b = m->ifc[i];
+    if (a.n != b.n || a.nl != b.nl || a.nr != b.nr || a.row_off != b.row_off || a.row_cols != b.row_cols ||
+        a.rhs_off != b.rhs_off || a.b_off != b.b_off || a.eta_off != b.eta_off)
+      return false;
+  }
+  for (int j = 0; j < c->L; ++j) {
+    const LayerDesc &a = c->lay[j], &b = m->lay[j];
+    if (a.m != b.m || a.p != b.p || a.c != b.c || a.ldq != b.ldq || a.qp_off != b.qp_off || a.cp_off != b.cp_off ||
+        a.aux_off != b.aux_off || a.if0 != b.if0 || a.if1 != b.if1)
+      return false;
+  }
+  return true;
+}
+
+mlqp_status mlqp_fd_gradient(mlqp_ctx* c, mlqp_ctx* const* moved, double t, const void* d_g, void* d_work,
+                             size_t work_bytes, double* grad) {
+  mlqp_status st = factors_ready(c);
+  if (st != MLQP_OK) return st;
+  if (!c->lsq_ready) return fail(c, MLQP_ESTATE, "no least-squares factors: run a solve first");
+  if (!(std::isfinite(t) && t != 0.0)) return fail(c, MLQP_EINVAL, "t: a finite nonzero step");
+  if (!moved || !d_g || !d_work || !grad) return fail(c, MLQP_EINVAL, "moved, d_g, d_work and grad are required");
+  if (reinterpret_cast<uintptr_t>(d_work) % 256 != 0 || reinterpret_cast<uintptr_t>(d_g) % 16 != 0)
+    return fail(c, MLQP_EINVAL, "d_work must be 256-byte and d_g 16-byte aligned");
+  if (work_bytes < grad_layout(c, nullptr, nullptr)) return fail(c, MLQP_ENOMEM, "work buffer too small");
+  for (int s = 0; s < 4; ++s) {
+    mlqp_ctx* m = moved[s];
+    if (!m || m == c || !m->valid || !m->bound) return fail(c, MLQP_EINVAL, "moved[%d]: a bound context", s);
+    if (m->prm.precision != MLQP_FP64) return fail(c, MLQP_EINVAL, "moved[%d]: MLQP_FP64", s);
+    if (!same_layout(c, m)) return fail(c, MLQP_EINVAL, "moved[%d]: not the base's discretisation and angles", s);
+    if (m->ws == c->ws) return fail(c, MLQP_EINVAL, "moved[%d] shares the base's workspace", s);
+    for (int q = 0; q < s; ++q)
+      if (moved[q] == m || moved[q]->ws == m->ws) return fail(c, MLQP_EINVAL, "moved[%d] repeats moved[%d]", s, q);
+  }
+  GradVecs V{};
+  grad_layout(c, static_cast<char*>(d_work), &V);
+  V.g = static_cast<const double2*>(d_g);
+  g_launches = 0;
+  cudaError_t e = launch_grad_adjoint(c->D, c->n_host.data(), at<int>(c, c->r_PERMV), c->max_p, V, c->stream);
+  c->launches += g_launches;
+  if (e != cudaSuccess) return cuda_fail(c, e, "gradient: adjoint pieces");
+  // Q' and C' at t = 0 (the least squares factored them in place)
+  for (int q = MLQP_STAGE_GEOM; q <= MLQP_STAGE_FILL; ++q)
+    if ((st = mlqp_run_stage(c, q)) != MLQP_OK) return st;
+  g_launches = 0;
+  e = launch_grad_base_lsq(c->D, V, c->stream);
+  c->launches += g_launches;
+  if (e != cudaSuccess) return cuda_fail(c, e, "gradient: base least-squares vectors");
+  cudaEvent_t ev = nullptr;
+  if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(c, e, "event");
+  int bad = -1;
+  for (int s = 0; s < 4 && st == MLQP_OK && e == cudaSuccess; ++s) {
+    mlqp_ctx* m = moved[s];
+    for (int q = MLQP_STAGE_GEOM; q <= MLQP_STAGE_FILL && st == MLQP_OK; ++q) st = mlqp_run_stage(m, q);
+    if (st != MLQP_OK) {
+      bad = s;
+      break;
+    }
+    if ((e = cudaEventRecord(ev, m->stream)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(c->stream, ev, 0)) != cudaSuccess) break;
+    g_launches = 0;
+    e = launch_grad_form(m->D, V, s, c->stream);
+    c->launches += g_launches;
+  }
+  if (st == MLQP_OK && e == cudaSuccess) {
+    g_launches = 0;
+    e = launch_grad_combine(c->D, V, t, c->stream);
+    c->launches += g_launches;
+  }
+  if (st == MLQP_OK && e == cudaSuccess)
+    e = cudaMemcpyAsync(grad, V.grad, sizeof(double) * c->n_theta, cudaMemcpyDeviceToHost, c->stream);
+  if (st == MLQP_OK && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaEventDestroy(ev);
+  if (st != MLQP_OK) return fail(c, st, "gradient: moved[%d]'s fill failed: %s", bad, mlqp_last_error(moved[bad]));
+  if (e != cudaSuccess) return cuda_fail(c, e, "gradient");
+  for (int s = 0; s < 4; ++s)
+    if ((st = mlqp_check_device(moved[s])) != MLQP_OK)
+      return fail(c, st, "gradient: moved[%d]: %s", s, mlqp_last_error(moved[s]));
+  return mlqp_check_device(c);
 }
 
 mlqp_status mlqp_check_device(mlqp_ctx* c) {

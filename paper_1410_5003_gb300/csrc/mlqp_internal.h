@@ -157,4 +157,21 @@ struct Dev {
   int upd_tile;   // tile edge of the block LU's trailing update (16 or 32)
 };
 
+// Per-angle vectors of the gradient, carved from the caller's work buffer.
+struct GradVecs {
+  double2* eta;   // n_theta x n_den: the base solution
+  double2* mu;    // n_theta x n_den: adjoint solution
+  double2* psi;   // n_theta x sum_p: sensitivities to X_j (one vector per layer, at aux_off_j)
+  double2* y;     // n_theta x sum_p: (Q'^H Q' + lam^2)^{-1} psi
+  double2* xi;    // n_theta x sum_p: X_j eta^_j
+  double2* qy;    // n_theta x L x max_m: Q'_j y_j (layer j at j max_m)
+  double2* rv;    // n_theta x L x max_m: C'_j eta^_j - Q'_j xi_j
+  double2* part;  // n_theta x (I + L): per interface and per layer parts of F
+  double2* fs;    // n_theta x 4: F at -2t, -t, t, 2t
+  double* grad;   // n_theta
+  const double2* g;  // n_theta x (2K + 1), caller's
+  size_t n_den, sum_p;
+  int max_m;
+};
+
 }  // namespace mlqp

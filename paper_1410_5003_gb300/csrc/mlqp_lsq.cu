@@ -431,23 +431,26 @@ __global__ void __launch_bounds__(256) k_schur(Dev D) {
 // in LAUX).  A functional of X_j = (Q'^H Q' + lam^2)^{-1} Q'^H C'_j with
 // sensitivity G_j to X_j has sensitivity Q'_j Y_j to C'_j and
 // (C'_j - Q'_j X_j) Y_j^H - Q'_j Y_j X_j^H to Q'_j.  G and Y are laid out
-// like X.  One warp per column: R^H z = g forward (column dots of R,
-// contiguous), then R y = z backward (row dots), vector in shared memory.
+// like X (VEC: one column per layer, layer j at aux_off_j of a sum_p-long
+// vector per angle).  One warp per column: R^H z = g forward (column dots of
+// R, contiguous), then R y = z backward (row dots), vector in shared memory.
 // ---------------------------------------------------------------------------
 constexpr int LADJ_WARPS = 4;
 
-__global__ void __launch_bounds__(32 * LADJ_WARPS) k_lsq_adj(Dev D, const double2* G, double2* Y) {
+template <bool VEC>
+__global__ void __launch_bounds__(32 * LADJ_WARPS) k_lsq_adj(Dev D, const double2* G, double2* Y, size_t sum_p) {
   const int jl = blockIdx.y, a = blockIdx.z;
   const LayerDesc L = D.lay[jl];
   const int p = L.p, ld = L.ldq;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.x * LADJ_WARPS + warp;
-  if (col >= L.c) return;
+  if (col >= (VEC ? 1 : L.c)) return;
+  const size_t off = VEC ? a * sum_p + L.aux_off : a * D.x_stride + L.x_off + (size_t)col * p;
   const double2* R = D.QP + a * D.qp_stride + L.qp_off;
   const double2* rinv = reinterpret_cast<const double2*>(D.LAUX + a * D.laux_stride + 6 * L.aux_off);
   extern __shared__ double2 ladj_sm[];
   double2* z = ladj_sm + (size_t)warp * p;
-  const double2* g = G + a * D.x_stride + L.x_off + (size_t)col * p;
+  const double2* g = G + off;
   for (int i = lane; i < p; i += 32) z[i] = g[i];
   __syncwarp();
   for (int i = 0; i < p; ++i) {  // z_i = (g_i - sum_{r<i} conj(R_ri) z_r) / conj(R_ii)
@@ -481,14 +484,23 @@ __global__ void __launch_bounds__(32 * LADJ_WARPS) k_lsq_adj(Dev D, const double
     }
     __syncwarp();
   }
-  double2* y = Y + a * D.x_stride + L.x_off + (size_t)col * p;
+  double2* y = Y + off;
   for (int i = lane; i < p; i += 32) y[i] = z[i];
 }
 
 cudaError_t launch_lsq_adjoint(const Dev& D, int max_p, int max_c, const double2* G, double2* Y, cudaStream_t s) {
   ++g_launches;
-  k_lsq_adj<<<dim3((max_c + LADJ_WARPS - 1) / LADJ_WARPS, D.L, D.n_theta), 32 * LADJ_WARPS,
-              sizeof(double2) * LADJ_WARPS * max_p, s>>>(D, G, Y);
+  k_lsq_adj<false><<<dim3((max_c + LADJ_WARPS - 1) / LADJ_WARPS, D.L, D.n_theta), 32 * LADJ_WARPS,
+                     sizeof(double2) * LADJ_WARPS * max_p, s>>>(D, G, Y, 0);
+  return cudaGetLastError();
+}
+
+// one vector per layer and angle (G, Y: n_theta x sum_p, layer j at aux_off_j)
+cudaError_t launch_lsq_adjoint_vec(const Dev& D, int max_p, size_t sum_p, const double2* G, double2* Y,
+                                   cudaStream_t s) {
+  ++g_launches;
+  k_lsq_adj<true><<<dim3(1, D.L, D.n_theta), 32 * LADJ_WARPS, sizeof(double2) * LADJ_WARPS * max_p, s>>>(D, G, Y,
+                                                                                                       sum_p);
   return cudaGetLastError();
 }
 

@@ -81,6 +81,10 @@ def load(path: str = LIB_PATH):
     lib.mlqp_lsq_adjoint.restype = I
     lib.mlqp_x_elements.argtypes = [P]
     lib.mlqp_x_elements.restype = Z
+    lib.mlqp_gradient_work_bytes.argtypes = [P]
+    lib.mlqp_gradient_work_bytes.restype = Z
+    lib.mlqp_fd_gradient.argtypes = [P, ct.POINTER(P), D, V, V, Z, ct.POINTER(D)]
+    lib.mlqp_fd_gradient.restype = I
     lib.mlqp_check_device.argtypes = [P]
     lib.mlqp_check_device.restype = I
     lib.mlqp_solve.argtypes = [P, V, V, V, V]
@@ -107,6 +111,7 @@ def load(path: str = LIB_PATH):
 
 EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_set_angles", "mlqp_autotune",
             "mlqp_solve_rhs", "mlqp_adjoint_solve", "mlqp_lsq_adjoint", "mlqp_x_elements",
+            "mlqp_gradient_work_bytes", "mlqp_fd_gradient",
             "mlqp_solve_device",
             "mlqp_check_device", "mlqp_solve", "mlqp_run_stage", "mlqp_block_info", "mlqp_last_error",
             "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes",
@@ -299,6 +304,29 @@ class Context:
             _check(self.ctx, self.lib.mlqp_adjoint_solve(self.ctx, ct.c_void_p(mu.data_ptr()),
                                                          ct.c_void_p(mu.data_ptr())))
         return mu
+
+    def fd_gradient(self, moved, t, g):
+        """mlqp_fd_gradient: per angle, 2 Re dF/dp for J = sum w |a^U|^2 along
+        a parameter p, from this solved context and `moved`, the 4 contexts of
+        the problem moved along p by -2t, -t, t, 2t (g = w a^U: (n_theta,
+        2K+1) complex).  Returns a numpy array of n_theta doubles; the caller
+        adds the weights' own term.  The context's factors are used up."""
+        import numpy as np
+        t_ = self.torch
+        if len(moved) != 4:
+            raise ValueError("moved: the contexts at -2t, -t, t, 2t")
+        g = t_.as_tensor(g, dtype=t_.complex128, device=self.device).contiguous()
+        if tuple(g.shape) != (self.n_theta, self.n_modes):
+            raise ValueError(f"g: expected ({self.n_theta}, {self.n_modes}), got {tuple(g.shape)}")
+        nb = int(self.lib.mlqp_gradient_work_bytes(self.ctx))
+        work = t_.empty(nb + 256, dtype=t_.uint8, device=self.device)
+        wp = (work.data_ptr() + 255) // 256 * 256
+        arr = (ct.c_void_p * 4)(*[m.ctx for m in moved])
+        out = np.zeros(self.n_theta)
+        with t_.cuda.stream(self.stream):
+            _check(self.ctx, self.lib.mlqp_fd_gradient(self.ctx, ct.cast(arr, ct.POINTER(ct.c_void_p)), float(t),
+                                                       ct.c_void_p(g.data_ptr()), ct.c_void_p(wp), nb, _dptr(out)))
+        return out
 
     def host_outputs(self, eta=False, pinned=False):
         t = self.torch

@@ -196,6 +196,27 @@ def test_solves_with_stored_factors_need_a_bound_fp64_context(M):
     lib.mlqp_destroy(ctx)
 
 
+def test_gradient_needs_a_solved_fp64_context(M):
+    """mlqp_fd_gradient refuses an unbound (unsolved) context before any
+    device work; its work size covers eta, mu and the per-layer vectors."""
+    lib = M.load()
+    from workloads import small_stack
+    import ctypes as ct
+    prob = small_stack(I=2)
+    ctx, _ = M.mlqp_setup(prob)
+    arr = (ct.c_void_p * 4)(ct.c_void_p(16), ct.c_void_p(32), ct.c_void_p(48), ct.c_void_p(64))
+    out = (ct.c_double * prob.n_theta)()
+    mv = ct.cast(arr, ct.POINTER(ct.c_void_p))
+    assert lib.mlqp_fd_gradient(ctx, mv, 1e-3, ct.c_void_p(256), ct.c_void_p(256), 1 << 30, out) == M.MLQP_ESTATE
+    assert lib.mlqp_fd_gradient(None, mv, 1e-3, ct.c_void_p(256), ct.c_void_p(256), 1 << 30, out) == M.MLQP_EINVAL
+    n_den, n_modes = ct.c_long(), ct.c_int()
+    assert lib.mlqp_sizes(ctx, ct.byref(n_den), ct.byref(n_modes)) == M.MLQP_OK
+    need = lib.mlqp_gradient_work_bytes(ctx)
+    assert need >= 2 * 16 * prob.n_theta * n_den.value
+    assert lib.mlqp_gradient_work_bytes(None) == 0
+    lib.mlqp_destroy(ctx)
+
+
 def test_set_angles_validation_without_a_device(M):
     """mlqp_set_angles checks count and range before anything else, and needs
     a bound context (none exists here, so no device work is reached)."""

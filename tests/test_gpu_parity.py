@@ -677,6 +677,67 @@ def test_adjoint_route_to_bragg_amplitudes(M, name):
     ctx.close()
 
 
+def _gradient_stack():
+    """The oracle's own gradient pin: 2 interfaces, 2 angles, lsq_rcond 1e-6
+    (at the default 1e-10 the regularisation amplifies the rounding of the
+    difference-quotient block derivatives past the gradient itself)."""
+    from dataclasses import replace
+    base = small_stack(I=2, N=40, P=40, Mw=24, K=8, M=30, n_angles=2)
+    prob = replace(base, params=replace(base.params, lsq_rcond=1e-6)).with_angles([-0.9, -2.1])
+
+    def shift_k(j):
+        def make(t):
+            k = prob.k.copy()
+            k[j] += t
+            return replace(prob, k=k)
+        return make
+
+    def shift_shape(i, which, m):
+        def make(t):
+            ifs = list(prob.ifaces)
+            f = ifs[i]
+            a, b = f.a.copy(), f.b.copy()
+            (a if which == "a" else b)[m] += t
+            ifs[i] = Interface(f.y0, a, b, f.N)
+            return replace(prob, ifaces=ifs)
+        return make
+
+    # parameters that leave the top layer (and so the weights w) unchanged
+    return prob, {"k2": shift_k(1), "k3": shift_k(2), "a1[1]": shift_shape(0, "a", 0),
+                  "b2[2]": shift_shape(1, "b", 1)}
+
+
+def test_fd_gradient_against_the_oracle(M):
+    """mlqp_fd_gradient: dJ/dp for J = the reflected 0th and -1st order
+    efficiencies summed over the angles, with respect to two layer
+    wavenumbers and two interface Fourier coefficients, from the solved base
+    context and the four contexts moved by -2t, -t, t, 2t (t = 1e-3), against
+    the oracle's adjoint gradient (transposed block solve, least-squares
+    adjoint, block derivatives by the same fourth-order central differences),
+    to 1e-8 relative (the two agree to 3e-11 when the forms are evaluated on
+    the oracle's own blocks)."""
+    prob, shifted = _gradient_stack()
+    t = 1e-3
+    ref = O.adjoint_gradient(prob, shifted, {p: t for p in shifted})
+    K = prob.params.K
+    ctx = M.Context(prob)
+    for p, make in shifted.items():
+        res = ctx.solve_host()
+        g = np.zeros((prob.n_theta, 2 * K + 1), np.complex128)
+        for a in range(prob.n_theta):
+            th = float(prob.theta[a])
+            g[a] = O.reflected_weights(prob, th, O.bloch(prob, th)) * res["aU"][a]
+        moved = [M.Context(make(s_ * t)) for s_ in (-2, -1, 1, 2)]
+        gr = ctx.fd_gradient(moved, t, g)
+        for m in moved:
+            m.close()
+        assert gr.shape == (prob.n_theta,)
+        assert abs(gr.sum() - ref[p]) < 1e-8 * max(abs(ref[p]), 1e-3), (p, gr.sum(), ref[p])
+    with pytest.raises(M.MlqpError):  # the gradient used up the factors
+        ctx.fd_gradient(moved, t, g)
+    ctx.close()
+
+
 def test_block_solve_is_differentiable(M):
     """paper_1410_5003_gb300.diff.block_solve: eta = A'^{-1} f with
     torch autograd; the gradient of L = Re(c^H eta) agrees with central
