@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--config3", action="store_true",
                     help="also time the 1000-interface corner grating (one solve per form, after a warm-up)")
     ap.add_argument("--corner-levels", type=int, default=2)
+    ap.add_argument("--gradient", action="store_true",
+                    help="also time mlqp_fd_gradient on the 20-interface stack (one shape parameter)")
     ap.add_argument("--config4", action="store_true",
                     help="also time the 256-angle sweep of the 100-interface uneven stack, in chunks of 128 angles")
     return ap.parse_args()
@@ -244,6 +246,50 @@ def corner_grating(mlqp, dev, levels):
                      "flux_error": float(res["flux"][0]), "unknowns": int(sum(2 * f.N for f in prob.ifaces)),
                      "workspace_gb": ctx.ws_bytes / 1e9}
         ctx.close()
+    return out
+
+
+def gradient_leg(mlqp, dev, reps=3):
+    """mlqp_fd_gradient on the 20-interface, 3-angle stack: dJ/dp for
+    J = sum over angles and orders of |a^U_n|^2 (w = 1), p = the first cosine
+    coefficient of interface 10, t = 1e-3; the base context re-solved
+    (untimed) before each call; wall-clock of the synchronous call (adjoint
+    pieces, base refill, four moved fills and forms), best of `reps` after a
+    warm-up that captures the stage graphs."""
+    import time
+    from dataclasses import replace
+    import numpy as np
+    from workloads import config2
+    from workloads.problems import Interface
+    prob = config2()
+    t = 1e-3
+
+    def moved_problem(s_):
+        ifs = list(prob.ifaces)
+        f = ifs[9]
+        a = f.a.copy()
+        a[0] += s_ * t
+        ifs[9] = Interface(f.y0, a, f.b.copy(), f.N)
+        return replace(prob, ifaces=ifs)
+
+    ctx = mlqp.Context(prob, device=dev)
+    moved = [mlqp.Context(moved_problem(s_), device=dev) for s_ in (-2, -1, 1, 2)]
+    best, solve_best, grad = float("inf"), float("inf"), None
+    for r in range(reps + 1):
+        t0 = time.perf_counter()
+        res = ctx.solve_host()
+        ts = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        grad = ctx.fd_gradient(moved, t, np.asarray(res["aU"]))
+        tg = (time.perf_counter() - t0) * 1e3
+        if r > 0:
+            best, solve_best = min(best, tg), min(solve_best, ts)
+    out = {"workload": "20-interface random grating, 3 angles, d J / d a_10[1] with J = sum |a^U_n|^2",
+           "ms_per_gradient": best, "ms_per_solve_host": solve_best, "dJ_dp": float(np.sum(grad)),
+           "moved_contexts": 4, "step": t}
+    for m in moved:
+        m.close()
+    ctx.close()
     return out
 
 
@@ -510,6 +556,8 @@ def main():
         line["config3"] = corner_grating(mlqp, dev, args.corner_levels)
     if args.config4 and rank == 0:
         line["config4"] = angle_sweep(mlqp, dev)
+    if args.gradient and rank == 0:
+        line["gradient"] = gradient_leg(mlqp, dev)
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(1)
