@@ -23,7 +23,7 @@ the paper's order:
   Sec. 3.3      block-tridiagonal LU sweep, recovery of a^U, a^D
   Remark r:flux flux error
 
-Readings of the paper that this oracle fixes (each is listed in the design doc):
+Readings of the paper that this oracle fixes:
   * Self-interaction quadrature: instead of Alpert's corrections the paper
     also names Kress' periodic log-split with cut-off functions (Remark
     phasewrap).  The three Bloch-phased copies are one integral over the
