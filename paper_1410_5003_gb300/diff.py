@@ -20,3 +20,90 @@ class BlockSolve(torch.autograd.Function):
 def block_solve(ctx, f):
     """eta = A'^{-1} f, differentiable in f (ctx: a Context after an FP64 solve)."""
     return BlockSolve.apply(f, ctx)
+
+
+def reflected_weights(prob, orders=(0, -1)):
+    """(n_theta, 2K+1) weights w with w_n |a^U_n|^2 the reflected efficiency
+    of order n (the vertical energy flux of the reflected Rayleigh-Bloch mode
+    over the incident one, Sec. 2): k^U_n / (k_1 |sin theta|) for the
+    propagating orders among `orders`, with kappa_n = k_1 cos theta + 2 pi n/d
+    and k^U_n = sqrt(k_1^2 - kappa_n^2) > 0; 0 for the other orders."""
+    import math
+    import numpy as np
+    K = prob.params.K
+    k1 = float(np.real(prob.k[0]))
+    w = np.zeros((prob.n_theta, 2 * K + 1))
+    for a, th in enumerate(np.asarray(prob.theta, dtype=float)):
+        for n in orders:
+            kap = k1 * math.cos(th) + 2.0 * math.pi * n / prob.d
+            q = k1 * k1 - kap * kap
+            if q > 0.0:
+                w[a, K + n] = math.sqrt(q) / (k1 * abs(math.sin(th)))
+    return w
+
+
+class BraggEfficiency(torch.autograd.Function):
+    """J(p) = sum over the angles and `orders` of the reflected efficiencies
+    of make_problem(p).  Forward: one solve (mlqp_solve); backward, per
+    parameter p_q: mlqp_fd_gradient from the solved context and the contexts
+    of make_problem(p + s t e_q), s = -2, -1, 1, 2, plus the weights' own
+    fourth-order difference times |a^U|^2.  make_problem must keep the
+    discretisation and the angles; backward runs once (no retain_graph)."""
+
+    @staticmethod
+    def forward(fctx, p, make_problem, orders, step, new_context):
+        import numpy as np
+        pv = p.detach().to("cpu", torch.float64).numpy().copy()
+        prob = make_problem(pv)
+        ctx = new_context(prob)
+        aU = np.asarray(ctx.solve_host()["aU"])
+        w = reflected_weights(prob, orders)
+        fctx.p_meta = (p.dtype, p.device)
+        if fctx.needs_input_grad[0]:
+            fctx.state = (pv, make_problem, orders, step, new_context, ctx, aU, w)
+        else:
+            fctx.state = None
+            ctx.close()
+        return torch.tensor(float(np.sum(w * np.abs(aU) ** 2)), dtype=torch.float64)
+
+    @staticmethod
+    def backward(fctx, gJ):
+        import numpy as np
+        if fctx.state is None:
+            raise RuntimeError("BraggEfficiency.backward runs once")
+        pv, make_problem, orders, step, new_context, ctx, aU, w = fctx.state
+        fctx.state = None
+        grad = np.zeros_like(pv)
+        try:
+            for q in range(pv.size):
+                if q > 0:
+                    ctx.solve_host()  # the previous gradient used up the factors
+                probs = []
+                for s_ in (-2, -1, 1, 2):
+                    pm = pv.copy()
+                    pm[q] += s_ * step
+                    probs.append(make_problem(pm))
+                moved = [new_context(mp) for mp in probs]
+                try:
+                    gq = float(np.sum(ctx.fd_gradient(moved, step, w * aU)))
+                finally:
+                    for m in moved:
+                        m.close()
+                wm = [reflected_weights(mp, orders) for mp in probs]
+                dw = (wm[0] - 8.0 * wm[1] + 8.0 * wm[2] - wm[3]) / (12.0 * step)
+                grad[q] = gq + float(np.sum(dw * np.abs(aU) ** 2))
+        finally:
+            ctx.close()
+        dtype, device = fctx.p_meta
+        return torch.as_tensor(float(gJ) * grad).to(dtype=dtype, device=device), None, None, None, None
+
+
+def bragg_efficiency(p, make_problem, orders=(0, -1), step=1e-3, device="cuda", new_context=None):
+    """J(p) as a torch scalar, differentiable in the 1-D parameter tensor p
+    (wavenumbers, interface coefficients, anything make_problem maps it to).
+    new_context(prob) makes the solver context (default: an FP64 Context on
+    `device`)."""
+    if new_context is None:
+        from . import mlqp
+        new_context = lambda prob: mlqp.Context(prob, device=device)  # noqa: E731
+    return BraggEfficiency.apply(p, make_problem, tuple(orders), float(step), new_context)

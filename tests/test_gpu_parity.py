@@ -738,6 +738,33 @@ def test_fd_gradient_against_the_oracle(M):
     ctx.close()
 
 
+def test_bragg_efficiency_autograd(M):
+    """paper_1410_5003_gb300.diff.bragg_efficiency on the GPU: the autograd
+    gradient of the reflected 0th and -1st order efficiencies in five
+    parameters (three layer wavenumbers, the top layer's among them, whose
+    weights move too, and two interface Fourier coefficients) against the
+    oracle's adjoint gradient to 1e-8 relative, and against fourth-order
+    central differences of J through GPU forward solves (h = 1e-3) to 1e-6."""
+    from paper_1410_5003_gb300.diff import bragg_efficiency
+    from tests.adjoint_forms import gradient_family
+    prob, make_problem, shifted, names = gradient_family()
+    p = torch.zeros(5, dtype=torch.float64, requires_grad=True)
+    J = bragg_efficiency(p, make_problem)
+    J.backward()
+    g = p.grad.numpy()
+    ref = O.adjoint_gradient(prob, shifted, {nm: 1e-3 for nm in names})
+    h = 1e-3
+    for q, nm in enumerate(names):
+        assert abs(g[q] - ref[nm]) < 1e-8 * max(abs(ref[nm]), 1e-3), (nm, g[q], ref[nm])
+        Js = []
+        for s_ in (-2, -1, 1, 2):
+            pv = torch.zeros(5, dtype=torch.float64)
+            pv[q] = s_ * h
+            Js.append(bragg_efficiency(pv, make_problem).item())
+        fd = (Js[0] - 8 * Js[1] + 8 * Js[2] - Js[3]) / (12 * h)
+        assert abs(g[q] - fd) < 1e-6 * max(abs(fd), 1e-3), (nm, g[q], fd)
+
+
 def test_block_solve_is_differentiable(M):
     """paper_1410_5003_gb300.diff.block_solve: eta = A'^{-1} f with
     torch autograd; the gradient of L = Re(c^H eta) agrees with central

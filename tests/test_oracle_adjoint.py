@@ -12,6 +12,7 @@ A'^H mu = h of Sec. 3.3's reduced block-tridiagonal system):
 import numpy as np
 
 from oracle import mlqp_oracle as O
+from tests.adjoint_forms import forms_gradient
 from workloads import small_stack
 
 
@@ -163,44 +164,13 @@ def test_block_sensitivities_are_rank_one_forms():
     shifted = {"k2": shift_k(1), "k3": shift_k(2)}
     t = 1e-3
     ref = O.adjoint_gradient(prob, shifted, {p: t for p in shifted})
-    I, P, rc = prob.I, prob.params.P, prob.params.lsq_rcond
     mine = {p: 0.0 for p in shifted}
     for a in range(prob.n_theta):
         th = float(prob.theta[a])
         sc = O.schur(prob, th)
-        eta = O.block_thomas(sc["Ad"], sc["Al"], sc["Au"], sc["f"], I)
-        X = sc["X"]
-        g = O.reflected_weights(prob, th, sc["bloch"]) * -(X[1][P:, :] @ eta[1])
-        h = {i: np.zeros_like(eta[i]) for i in range(1, I + 1)}
-        h[1] = -(X[1][P:, :].conj().T @ g)
-        mu = O.adjoint_block_thomas(sc["Ad"], sc["Al"], sc["Au"], h, I)
-        etaL = {j: np.concatenate([eta[i] for i in O.layer_columns(prob, j)]) for j in range(1, I + 2)}
-        asm = O.Assembler(prob)
-        xi, y, qy, rv = {}, {}, {}, {}
-        for j in range(1, I + 2):
-            psi = np.zeros(X[j].shape[0], np.complex128)
-            for i in (j - 1, j):
-                if 1 <= i <= I:
-                    psi[:P] += asm.B(i, j).conj().T @ mu[i]
-            if j == 1:
-                psi[P:] = -g
-            y[j] = O.lsq_adjoint(sc["Qp"][j], psi[:, None], rc)[:, 0]
-            xi[j] = X[j] @ etaL[j]
-            qy[j] = sc["Qp"][j] @ y[j]
-            rv[j] = sc["Cp"][j] @ etaL[j] - sc["Qp"][j] @ xi[j]
-
-        def F(b):
-            s = np.vdot(mu[1], b["f"])
-            for (i, j), A in b["A"].items():
-                s -= np.vdot(mu[i], A @ eta[j])
-            for (i, j), B in b["B"].items():
-                s += np.vdot(mu[i], B @ xi[j][:P])
-            for j in range(1, I + 2):
-                s += np.vdot(qy[j], b["Cp"][j] @ etaL[j] - b["Qp"][j] @ xi[j]) + np.vdot(rv[j], b["Qp"][j] @ y[j])
-            return s
-
+        eta1 = O.block_thomas(sc["Ad"], sc["Al"], sc["Au"], sc["f"], prob.I)[1]
+        g = O.reflected_weights(prob, th, sc["bloch"]) * -(sc["X"][1][prob.params.P:, :] @ eta1)
         for p, make in shifted.items():
-            Fs = [F(O._blocks(make(s_ * t), th)) for s_ in (-2, -1, 1, 2)]
-            mine[p] += 2.0 * ((Fs[0] - 8 * Fs[1] + 8 * Fs[2] - Fs[3]) / (12 * t)).real
+            mine[p] += forms_gradient(prob, a, g, [make(s_ * t) for s_ in (-2, -1, 1, 2)], t)
     for p in shifted:
         assert abs(mine[p] - ref[p]) < 1e-9 * max(abs(ref[p]), 1e-3), (p, mine[p], ref[p])
