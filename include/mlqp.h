@@ -43,7 +43,7 @@ typedef enum {
   MLQP_ENOMEM = 2,     /* host allocation failed or workspace too small */
   MLQP_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
   MLQP_ESINGULAR = 4,  /* a block-LU pivot was zero or not finite */
-  MLQP_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+  MLQP_ETIMEOUT = 5,   /* reserved for a bounded device-side wait that gave up (no kernel waits today) */
   MLQP_ENOTCONV = 6,   /* iterative refinement missed its tolerance */
   MLQP_ESTATE = 7      /* call out of order (e.g. solve before bind) */
 } mlqp_status;
