@@ -100,10 +100,10 @@ typedef struct {
  * solve the paper's closing remarks name for deep stacks).  refine_method
  * (MLQP_MIXED): MLQP_IR (each correction is one FP32 block solve of the
  * residual) or MLQP_GMRES_IR (each correction is a flexible GMRES solve in
- * FP64, at most 12 steps, right-preconditioned by the same FP32 block
- * factors; it converges where kappa(A') eps_32 is near 1 and plain
- * refinement stalls, at up to 12 block solves and FP64 operator products per
- * correction). */
+ * FP64, at most 40 steps, right-preconditioned by the same FP32 block
+ * factors, stopped when its residual falls by 1e-10; it converges where
+ * kappa(A') eps_32 is near 1 and plain refinement stalls, at up to 40 block
+ * solves and FP64 operator products per correction). */
 typedef struct {
   int P;
   double R;
