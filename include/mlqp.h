@@ -258,6 +258,18 @@ mlqp_status mlqp_run_stage(mlqp_ctx* ctx, int stage);
  * (count or range), MLQP_ESTATE (not bound). */
 mlqp_status mlqp_set_angles(mlqp_ctx* ctx, const double* theta, int n_theta);
 
+/* Replaces the problem's values in a bound context: the wavenumbers k (as in
+ * mlqp_setup) and each interface's y0 and Fourier coefficients (or corner
+ * vertices), keeping the period, the angles, the parameters and every size
+ * (I, node counts, modes, corners, levels).  The new description is
+ * validated like mlqp_setup's and re-uploaded on the bound stream; the
+ * workspace and the captured stage graphs are kept, the solve state is
+ * dropped (run a solve again).  For a sequence of problems of one family,
+ * e.g. the moved problems of a parameter gradient (Sec. 3.3 adjoint).
+ * Errors: MLQP_ESTATE (not bound), MLQP_EINVAL (invalid description, or a
+ * size that differs from the context's), MLQP_ENOMEM, MLQP_ECUDA. */
+mlqp_status mlqp_set_problem(mlqp_ctx* ctx, const mlqp_interface* ifaces, int I, const double* k);
+
 /* Chooses the launch shapes of a bound context by timing candidates on its
  * own problem (each timed stage preceded by the stages it depends on, so
  * this costs several solves): the CTAs per least-squares QR cluster (1, 2,

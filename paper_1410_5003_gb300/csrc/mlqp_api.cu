@@ -690,6 +690,70 @@ mlqp_status mlqp_set_angles(mlqp_ctx* c, const double* theta, int n_theta) {
   return mlqp_bind(c, c->ws, c->ws_bytes, c->stream);
 }
 
+// The layout a problem gives a context: every size, offset and region, all
+// but the problem's values (wavenumbers, coefficients or vertices, y0).
+static bool same_problem_layout(const mlqp_ctx* a, const mlqp_ctx* b) {
+  if (a->I != b->I || a->L != b->L || a->n_theta != b->n_theta || a->n_den != b->n_den || a->ws_bytes != b->ws_bytes)
+    return false;
+  if (a->n_host != b->n_host || a->maxN != b->maxN || a->total_nodes != b->total_nodes ||
+      a->total_panels != b->total_panels || a->max_m != b->max_m || a->max_p != b->max_p || a->max_c != b->max_c ||
+      a->max_tiles != b->max_tiles || a->any_poly != b->any_poly || a->coef_a.size() != b->coef_a.size())
+    return false;
+  if (a->r_stride != b->r_stride || a->f_stride != b->f_stride || a->b_total != b->b_total ||
+      a->qp_stride != b->qp_stride || a->cp_stride != b->cp_stride || a->x_stride != b->x_stride ||
+      a->sum_p != b->sum_p || a->t_stride != b->t_stride)
+    return false;
+  for (int i = 0; i < a->I; ++i) {
+    const IfaceDesc &x = a->ifc[i], &y = b->ifc[i];
+    if (x.N != y.N || x.n != y.n || x.node_off != y.node_off || x.n_modes != y.n_modes || x.coef_off != y.coef_off ||
+        x.nl != y.nl || x.nr != y.nr || x.n_corners != y.n_corners || x.levels != y.levels ||
+        x.pan_off != y.pan_off || x.row_off != y.row_off || x.row_cols != y.row_cols || x.rhs_off != y.rhs_off ||
+        x.b_off != y.b_off || x.eta_off != y.eta_off)
+      return false;
+  }
+  for (int j = 0; j < a->L; ++j) {
+    const LayerDesc &x = a->lay[j], &y = b->lay[j];
+    if (x.m != y.m || x.p != y.p || x.ldq != y.ldq || x.c != y.c || x.if0 != y.if0 || x.if1 != y.if1 ||
+        x.c0 != y.c0 || x.c1 != y.c1 || x.end != y.end || x.qp_off != y.qp_off || x.cp_off != y.cp_off ||
+        x.x_off != y.x_off || x.aux_off != y.aux_off || x.t_off != y.t_off)
+      return false;
+  }
+  if (a->tasks.size() != b->tasks.size()) return false;
+  for (size_t q = 0; q < a->tasks.size(); ++q) {
+    const SchurTask &x = a->tasks[q], &y = b->tasks[q];
+    if (x.c_off != y.c_off || x.ldc != y.ldc || x.rows != y.rows || x.cols != y.cols || x.a1_off != y.a1_off ||
+        x.a2_off != y.a2_off || x.lda1 != y.lda1 || x.lda2 != y.lda2 || x.b1_off != y.b1_off ||
+        x.b2_off != y.b2_off || x.ldb1 != y.ldb1 || x.ldb2 != y.ldb2 || x.k1 != y.k1 || x.k2 != y.k2)
+      return false;
+  }
+  return true;
+}
+
+mlqp_status mlqp_set_problem(mlqp_ctx* c, const mlqp_interface* ifaces, int I, const double* k) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  mlqp_ctx* t = nullptr;
+  mlqp_status st = mlqp_setup(ifaces, I, k, c->d, c->theta.data(), c->n_theta, &c->prm, &t);
+  if (st != MLQP_OK) {
+    const std::string msg = t ? t->err : std::string("setup failed");
+    mlqp_destroy(t);
+    return fail(c, st, "set_problem: %s", msg.c_str());
+  }
+  if (!same_problem_layout(c, t)) {
+    mlqp_destroy(t);
+    return fail(c, MLQP_EINVAL, "set_problem keeps every size: node counts, modes, corners and levels");
+  }
+  c->k = t->k;
+  c->coef_a = t->coef_a;
+  c->coef_b = t->coef_b;
+  c->ifc = t->ifc;
+  c->lay = t->lay;
+  mlqp_destroy(t);
+  // same workspace, stream, period and parameters: the kernels' arguments are
+  // unchanged, so re-uploading the descriptors keeps the stage graphs valid
+  return mlqp_bind(c, c->ws, c->ws_bytes, c->stream);
+}
+
 extern "C++" {
 // Captures fn(stream) once into gx (on the internal stream c->cap) and
 // replays it on the bound stream.

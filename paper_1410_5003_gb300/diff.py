@@ -47,7 +47,8 @@ class BraggEfficiency(torch.autograd.Function):
     of make_problem(p).  Forward: one solve (mlqp_solve); backward, per
     parameter p_q: mlqp_fd_gradient from the solved context and the contexts
     of make_problem(p + s t e_q), s = -2, -1, 1, 2, plus the weights' own
-    fourth-order difference times |a^U|^2.  make_problem must keep the
+    fourth-order difference times |a^U|^2.  The four moved contexts are made
+    once and moved to each parameter's problems by mlqp_set_problem.  make_problem must keep the
     discretisation and the angles; backward runs once (no retain_graph)."""
 
     @staticmethod
@@ -74,6 +75,7 @@ class BraggEfficiency(torch.autograd.Function):
         pv, make_problem, orders, step, new_context, ctx, aU, w = fctx.state
         fctx.state = None
         grad = np.zeros_like(pv)
+        moved = []
         try:
             for q in range(pv.size):
                 if q > 0:
@@ -83,16 +85,22 @@ class BraggEfficiency(torch.autograd.Function):
                     pm = pv.copy()
                     pm[q] += s_ * step
                     probs.append(make_problem(pm))
-                moved = [new_context(mp) for mp in probs]
-                try:
-                    gq = float(np.sum(ctx.fd_gradient(moved, step, w * aU)))
-                finally:
+                if moved and all(hasattr(m, "set_problem") for m in moved):
+                    for m, mp in zip(moved, probs):  # same sizes: reuse the workspaces and graphs
+                        m.set_problem(mp)
+                else:
                     for m in moved:
                         m.close()
+                    moved = []
+                    for mp in probs:
+                        moved.append(new_context(mp))
+                gq = float(np.sum(ctx.fd_gradient(moved, step, w * aU)))
                 wm = [reflected_weights(mp, orders) for mp in probs]
                 dw = (wm[0] - 8.0 * wm[1] + 8.0 * wm[2] - wm[3]) / (12.0 * step)
                 grad[q] = gq + float(np.sum(dw * np.abs(aU) ** 2))
         finally:
+            for m in moved:
+                m.close()
             ctx.close()
         dtype, device = fctx.p_meta
         return torch.as_tensor(float(gJ) * grad).to(dtype=dtype, device=device), None, None, None, None

@@ -69,6 +69,8 @@ def load(path: str = LIB_PATH):
     lib.mlqp_bind.restype = I
     lib.mlqp_set_angles.argtypes = [P, ct.POINTER(D), I]
     lib.mlqp_set_angles.restype = I
+    lib.mlqp_set_problem.argtypes = [P, ct.POINTER(mlqp_interface), I, ct.POINTER(D)]
+    lib.mlqp_set_problem.restype = I
     lib.mlqp_autotune.argtypes = [P, I, ct.POINTER(D), I]
     lib.mlqp_autotune.restype = I
     lib.mlqp_solve_device.argtypes = [P, V, V, V, V]
@@ -109,7 +111,8 @@ def load(path: str = LIB_PATH):
     return lib
 
 
-EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_set_angles", "mlqp_autotune",
+EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_set_angles", "mlqp_set_problem",
+            "mlqp_autotune",
             "mlqp_solve_rhs", "mlqp_adjoint_solve", "mlqp_lsq_adjoint", "mlqp_x_elements",
             "mlqp_gradient_work_bytes", "mlqp_fd_gradient",
             "mlqp_solve_device",
@@ -142,6 +145,23 @@ def mlqp_setup(prob, precision=MLQP_FP64, max_refine=0, refine_tol=0.0, block_so
     .theta, .params (P, R, Mw, M, K, gap_U, gap_D, cut_a, cut_b, lsq_rcond).
     Returns (ctx handle, keep-alive list)."""
     lib = load()
+    arr, I, k, keep = _marshal(prob)
+    th = np.ascontiguousarray(prob.theta, dtype=np.float64)
+    keep.append(th)
+    prm = make_params(prob.params, precision, max_refine, refine_tol, block_solver, refine_method)
+    ctx = ct.c_void_p()
+    st = lib.mlqp_setup(arr, I, _dptr(k), float(prob.d), _dptr(th), len(th), ct.byref(prm), ct.byref(ctx))
+    if st != MLQP_OK:
+        msg = lib.mlqp_last_error(ctx).decode() if ctx.value else ""
+        if ctx.value:
+            lib.mlqp_destroy(ctx)
+        raise MlqpError(st, msg)
+    return ctx, keep
+
+
+def _marshal(prob):
+    """The interfaces and wavenumbers of prob as mlqp_setup takes them:
+    (mlqp_interface array, I, k array, keep-alive list)."""
     I = len(prob.ifaces)
     keep = []
     arr = (mlqp_interface * I)()
@@ -160,17 +180,8 @@ def mlqp_setup(prob, precision=MLQP_FP64, max_refine=0, refine_tol=0.0, block_so
             keep += [a, b]
             arr[i] = mlqp_interface(float(f.y0), len(a), _dptr(a), _dptr(b), int(f.N), 0, None, None, 0)
     k = np.ascontiguousarray(np.stack([np.real(prob.k), np.imag(prob.k)], axis=1).ravel(), dtype=np.float64)
-    th = np.ascontiguousarray(prob.theta, dtype=np.float64)
-    keep += [k, th]
-    prm = make_params(prob.params, precision, max_refine, refine_tol, block_solver, refine_method)
-    ctx = ct.c_void_p()
-    st = lib.mlqp_setup(arr, I, _dptr(k), float(prob.d), _dptr(th), len(th), ct.byref(prm), ct.byref(ctx))
-    if st != MLQP_OK:
-        msg = lib.mlqp_last_error(ctx).decode() if ctx.value else ""
-        if ctx.value:
-            lib.mlqp_destroy(ctx)
-        raise MlqpError(st, msg)
-    return ctx, keep
+    keep.append(k)
+    return arr, I, k, keep
 
 
 class Context:
@@ -207,6 +218,16 @@ class Context:
         """New incidence angles (as many as at setup) for the next solves."""
         th = np.ascontiguousarray(theta, dtype=np.float64)
         _check(self.ctx, self.lib.mlqp_set_angles(self.ctx, _dptr(th), len(th)))
+
+    def set_problem(self, prob):
+        """mlqp_set_problem: prob's wavenumbers, y0 and coefficients (or
+        vertices) replace the context's, with every size, the period, the
+        parameters and the context's angles kept; the workspace and the
+        stage graphs are reused."""
+        arr, I, k, keep = _marshal(prob)
+        _check(self.ctx, self.lib.mlqp_set_problem(self.ctx, arr, I, _dptr(k)))
+        self.prob = prob
+        self._keep = keep
 
     TUNE_REPORT = 18
 

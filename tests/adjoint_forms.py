@@ -73,6 +73,11 @@ class OracleContext:
         probs = [m.prob for m in moved]
         return np.array([forms_gradient(self.prob, a, g[a], probs, t) for a in range(self.prob.n_theta)])
 
+    def set_problem(self, prob):
+        self.prob = prob
+        self.factored = False
+        self.moves = getattr(self, "moves", 0) + 1
+
     def close(self):
         self.closed = True
 

@@ -197,8 +197,9 @@ def test_solves_with_stored_factors_need_a_bound_fp64_context(M):
 
 
 def test_gradient_needs_a_solved_fp64_context(M):
-    """mlqp_fd_gradient refuses an unbound (unsolved) context before any
-    device work; its work size covers eta, mu and the per-layer vectors."""
+    """mlqp_fd_gradient and mlqp_set_problem refuse an unbound context before
+    any device work; the gradient's work size covers eta, mu and the
+    per-layer vectors."""
     lib = M.load()
     from workloads import small_stack
     import ctypes as ct
@@ -214,6 +215,9 @@ def test_gradient_needs_a_solved_fp64_context(M):
     need = lib.mlqp_gradient_work_bytes(ctx)
     assert need >= 2 * 16 * prob.n_theta * n_den.value
     assert lib.mlqp_gradient_work_bytes(None) == 0
+    arr, I, k, keep = M._marshal(prob)
+    assert lib.mlqp_set_problem(ctx, arr, I, M._dptr(k)) == M.MLQP_ESTATE
+    assert lib.mlqp_set_problem(None, arr, I, M._dptr(k)) == M.MLQP_EINVAL
     lib.mlqp_destroy(ctx)
 
 

@@ -738,6 +738,41 @@ def test_fd_gradient_against_the_oracle(M):
     ctx.close()
 
 
+def test_set_problem_matches_a_fresh_context(M):
+    """mlqp_set_problem: a context moved to another problem of the same
+    family (new wavenumbers, y0 and Fourier coefficients; for a corner stack
+    new vertices) solves it bitwise like a fresh context of that problem; a
+    different node count is refused."""
+    from dataclasses import replace
+    from tests.adjoint_forms import gradient_family
+    from workloads.problems import PolyInterface
+    prob, make_problem, _, _ = gradient_family()
+    moved = make_problem(np.array([0.01, -0.02, 0.03, 0.004, -0.005]))
+    ifs = list(moved.ifaces)
+    ifs[1] = Interface(ifs[1].y0 - 0.01, ifs[1].a, ifs[1].b, ifs[1].N)
+    moved = replace(moved, ifaces=ifs)
+    cs = corner_stack(I=2, levels=2, K=24, M=50)
+    cifs = [PolyInterface(f.y0, f.vx.copy(), f.vy + 0.01 * (i + 1), f.levels) for i, f in enumerate(cs.ifaces)]
+    cmoved = replace(cs, ifaces=cifs, k=cs.k * 1.01)
+    for base, other in ((prob, moved), (cs, cmoved)):
+        ctx = M.Context(base)
+        ctx.solve_host()
+        ctx.set_problem(other)
+        got = ctx.solve_host()
+        fresh = M.Context(other)
+        ref = fresh.solve_host()
+        for key in ("aU", "aD"):
+            assert np.array_equal(got[key], ref[key]), key
+        fresh.close()
+        ctx.close()
+    ctx = M.Context(prob)
+    ifs = list(prob.ifaces)
+    ifs[0] = Interface(ifs[0].y0, ifs[0].a, ifs[0].b, ifs[0].N + 2)
+    with pytest.raises(M.MlqpError):
+        ctx.set_problem(replace(prob, ifaces=ifs))
+    ctx.close()
+
+
 def test_bragg_efficiency_autograd(M):
     """paper_1410_5003_gb300.diff.bragg_efficiency on the GPU: the autograd
     gradient of the reflected 0th and -1st order efficiencies in five
