@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--corner-levels", type=int, default=2)
     ap.add_argument("--gradient", action="store_true",
                     help="also time mlqp_fd_gradient on the 20-interface stack (one shape parameter)")
+    ap.add_argument("--config5", action="store_true",
+                    help="also time the design gradient of the 50-interface, 16-angle stack (a few parameters)")
     ap.add_argument("--config4", action="store_true",
                     help="also time the 256-angle sweep of the 100-interface uneven stack, in chunks of 128 angles")
     return ap.parse_args()
@@ -291,6 +293,71 @@ def gradient_leg(mlqp, dev, reps=3):
         m.close()
     ctx.close()
     return out
+
+
+def design_gradient(mlqp, dev, n_params=4):
+    """The design-gradient stack (50 interfaces with 4 Fourier modes, 51
+    wavenumbers, 120 nodes, 16 angles; 451 parameters in all), along
+    `n_params` of its parameters (wavenumbers and coefficients of the middle
+    of the stack), J = sum over angles and orders of |a^U_n|^2, t = 1e-3:
+    wall-clock of the solve, of forming the sensitivities once
+    (mlqp_gradient_prepare), of the first parameter (making the four moved
+    contexts and capturing their graphs) and of each later one (moving them by
+    mlqp_set_problem, fills and forms: mlqp_gradient_eval)."""
+    import time
+    from dataclasses import replace
+    import numpy as np
+    import torch
+    from workloads import config5
+    from workloads.problems import Interface
+    prob = config5()
+    mid = prob.I // 2
+    t = 1e-3
+
+    def moved_problem(q, s_):
+        k = np.asarray(prob.k, dtype=np.complex128).copy()
+        ifs = list(prob.ifaces)
+        f = ifs[mid - 1 + q // 2]
+        a, b = f.a.copy(), f.b.copy()
+        if q % 2 == 0:
+            k[mid + q // 2] += s_ * t
+        else:
+            a[q // 2 % len(a)] += s_ * t
+        ifs[mid - 1 + q // 2] = Interface(f.y0, a, b, f.N)
+        return replace(prob, k=k, ifaces=ifs)
+
+    ctx = mlqp.Context(prob, device=dev)
+    ctx.solve_host()  # captures the graphs
+    t0 = time.perf_counter()
+    res = ctx.solve_host()
+    solve_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    work = ctx.gradient_prepare(np.asarray(res["aU"]))
+    torch.cuda.synchronize()
+    prep_ms = (time.perf_counter() - t0) * 1e3
+    moved, per, first, total = [], [], None, 0.0
+    for q in range(n_params):
+        t0 = time.perf_counter()
+        probs = [moved_problem(q, s_) for s_ in (-2, -1, 1, 2)]
+        if not moved:
+            moved = [mlqp.Context(mp, device=dev) for mp in probs]
+        else:
+            for m, mp in zip(moved, probs):
+                m.set_problem(mp)
+        total += float(np.sum(ctx.gradient_eval(moved, t, work)))
+        ms = (time.perf_counter() - t0) * 1e3
+        if q == 0:
+            first = ms
+        else:
+            per.append(ms)
+    for m in moved:
+        m.close()
+    ctx.close()
+    n_all = prob.I * 2 * len(prob.ifaces[0].a) + prob.I + 1
+    return {"workload": "50 interfaces x 4 Fourier modes, 51 wavenumbers, 120 nodes, 16 angles",
+            "parameters_total": n_all, "parameters_timed": n_params, "ms_solve_host": solve_ms,
+            "ms_prepare": prep_ms, "ms_first_parameter": first,
+            "ms_per_parameter": float(np.median(per)) if per else None, "sum_dJ": total}
 
 
 def angle_sweep(mlqp, dev, chunk=128):
@@ -558,6 +625,8 @@ def main():
         line["config4"] = angle_sweep(mlqp, dev)
     if args.gradient and rank == 0:
         line["gradient"] = gradient_leg(mlqp, dev)
+    if args.config5 and rank == 0:
+        line["config5"] = design_gradient(mlqp, dev)
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(1)

@@ -227,6 +227,20 @@ size_t mlqp_gradient_work_bytes(const mlqp_ctx* ctx);
 mlqp_status mlqp_fd_gradient(mlqp_ctx* ctx, mlqp_ctx* const* moved, double t, const void* d_g, void* d_work,
                              size_t work_bytes, double* grad);
 
+/* The two halves of mlqp_fd_gradient, for many parameters of one solve: the
+ * sensitivities (mu, psi, y, X eta, Q'y, r) depend on the solution and g
+ * only, so they are formed once, and each parameter costs the four moved
+ * fills and their forms.
+ *   mlqp_gradient_prepare: from the solved ctx and g into d_work (same
+ *       arguments and state rules as above; the factors are used up).
+ *   mlqp_gradient_eval: grad[a] for one parameter from the four moved
+ *       contexts and the d_work that mlqp_gradient_prepare filled for this
+ *       context's problem and angles (MLQP_ESTATE otherwise, e.g. after
+ *       mlqp_set_angles or mlqp_set_problem on ctx).  Synchronous. */
+mlqp_status mlqp_gradient_prepare(mlqp_ctx* ctx, const void* d_g, void* d_work, size_t work_bytes);
+mlqp_status mlqp_gradient_eval(mlqp_ctx* ctx, mlqp_ctx* const* moved, double t, void* d_work, size_t work_bytes,
+                               double* grad);
+
 /* Synchronises the bound stream and returns the device-side status word. */
 mlqp_status mlqp_check_device(mlqp_ctx* ctx);
 

@@ -100,6 +100,7 @@ struct mlqp_ctx {
   long solve_launches = 0;
   bool factored = false;  // the FP64 block factors of the bound angles are in the workspace
   bool lsq_ready = false;  // the least-squares factors R of the bound angles are in the workspace
+  const void* grad_work = nullptr;  // the work buffer mlqp_gradient_prepare filled for the bound problem
 };
 
 static void drop_graphs(mlqp_ctx* c) {
@@ -650,6 +651,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   c->bound = true;
   c->factored = false;
   c->lsq_ready = false;
+  c->grad_work = nullptr;  // new angles or problem values: the sensitivities no longer apply
   return MLQP_OK;
 }
 
@@ -1101,16 +1103,8 @@ static bool same_layout(const mlqp_ctx* c, const mlqp_ctx* m) {
   return true;
 }
 
-mlqp_status mlqp_fd_gradient(mlqp_ctx* c, mlqp_ctx* const* moved, double t, const void* d_g, void* d_work,
-                             size_t work_bytes, double* grad) {
-  mlqp_status st = factors_ready(c);
-  if (st != MLQP_OK) return st;
-  if (!c->lsq_ready) return fail(c, MLQP_ESTATE, "no least-squares factors: run a solve first");
-  if (!(std::isfinite(t) && t != 0.0)) return fail(c, MLQP_EINVAL, "t: a finite nonzero step");
-  if (!moved || !d_g || !d_work || !grad) return fail(c, MLQP_EINVAL, "moved, d_g, d_work and grad are required");
-  if (reinterpret_cast<uintptr_t>(d_work) % 256 != 0 || reinterpret_cast<uintptr_t>(d_g) % 16 != 0)
-    return fail(c, MLQP_EINVAL, "d_work must be 256-byte and d_g 16-byte aligned");
-  if (work_bytes < grad_layout(c, nullptr, nullptr)) return fail(c, MLQP_ENOMEM, "work buffer too small");
+static mlqp_status check_moved(mlqp_ctx* c, mlqp_ctx* const* moved) {
+  if (!moved) return fail(c, MLQP_EINVAL, "moved: 4 contexts");
   for (int s = 0; s < 4; ++s) {
     mlqp_ctx* m = moved[s];
     if (!m || m == c || !m->valid || !m->bound) return fail(c, MLQP_EINVAL, "moved[%d]: a bound context", s);
@@ -1120,6 +1114,23 @@ mlqp_status mlqp_fd_gradient(mlqp_ctx* c, mlqp_ctx* const* moved, double t, cons
     for (int q = 0; q < s; ++q)
       if (moved[q] == m || moved[q]->ws == m->ws) return fail(c, MLQP_EINVAL, "moved[%d] repeats moved[%d]", s, q);
   }
+  return MLQP_OK;
+}
+
+static mlqp_status check_work(mlqp_ctx* c, const void* d_work, size_t work_bytes) {
+  if (!d_work) return fail(c, MLQP_EINVAL, "d_work is required");
+  if (reinterpret_cast<uintptr_t>(d_work) % 256 != 0) return fail(c, MLQP_EINVAL, "d_work must be 256-byte aligned");
+  if (work_bytes < grad_layout(c, nullptr, nullptr)) return fail(c, MLQP_ENOMEM, "work buffer too small");
+  return MLQP_OK;
+}
+
+mlqp_status mlqp_gradient_prepare(mlqp_ctx* c, const void* d_g, void* d_work, size_t work_bytes) {
+  mlqp_status st = factors_ready(c);
+  if (st != MLQP_OK) return st;
+  if (!c->lsq_ready) return fail(c, MLQP_ESTATE, "no least-squares factors: run a solve first");
+  if ((st = check_work(c, d_work, work_bytes)) != MLQP_OK) return st;
+  if (!d_g || reinterpret_cast<uintptr_t>(d_g) % 16 != 0) return fail(c, MLQP_EINVAL, "d_g: a 16-byte aligned buffer");
+  c->grad_work = nullptr;  // set again only once every sensitivity is in place
   GradVecs V{};
   grad_layout(c, static_cast<char*>(d_work), &V);
   V.g = static_cast<const double2*>(d_g);
@@ -1134,8 +1145,26 @@ mlqp_status mlqp_fd_gradient(mlqp_ctx* c, mlqp_ctx* const* moved, double t, cons
   e = launch_grad_base_lsq(c->D, V, c->stream);
   c->launches += g_launches;
   if (e != cudaSuccess) return cuda_fail(c, e, "gradient: base least-squares vectors");
+  c->grad_work = d_work;
+  return MLQP_OK;
+}
+
+mlqp_status mlqp_gradient_eval(mlqp_ctx* c, mlqp_ctx* const* moved, double t, void* d_work, size_t work_bytes,
+                               double* grad) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  mlqp_status st = check_work(c, d_work, work_bytes);
+  if (st != MLQP_OK) return st;
+  if (c->grad_work != d_work)
+    return fail(c, MLQP_ESTATE, "d_work holds no sensitivities of this problem: mlqp_gradient_prepare first");
+  if (!(std::isfinite(t) && t != 0.0)) return fail(c, MLQP_EINVAL, "t: a finite nonzero step");
+  if (!grad) return fail(c, MLQP_EINVAL, "grad is required");
+  if ((st = check_moved(c, moved)) != MLQP_OK) return st;
+  GradVecs V{};
+  grad_layout(c, static_cast<char*>(d_work), &V);
   cudaEvent_t ev = nullptr;
-  if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(c, e, "event");
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(c, e, "event");
   int bad = -1;
   for (int s = 0; s < 4 && st == MLQP_OK && e == cudaSuccess; ++s) {
     mlqp_ctx* m = moved[s];
@@ -1165,6 +1194,19 @@ mlqp_status mlqp_fd_gradient(mlqp_ctx* c, mlqp_ctx* const* moved, double t, cons
     if ((st = mlqp_check_device(moved[s])) != MLQP_OK)
       return fail(c, st, "gradient: moved[%d]: %s", s, mlqp_last_error(moved[s]));
   return mlqp_check_device(c);
+}
+
+mlqp_status mlqp_fd_gradient(mlqp_ctx* c, mlqp_ctx* const* moved, double t, const void* d_g, void* d_work,
+                             size_t work_bytes, double* grad) {
+  mlqp_status st = factors_ready(c);
+  if (st != MLQP_OK) return st;
+  if (!c->lsq_ready) return fail(c, MLQP_ESTATE, "no least-squares factors: run a solve first");
+  if (!(std::isfinite(t) && t != 0.0)) return fail(c, MLQP_EINVAL, "t: a finite nonzero step");
+  if (!d_g || !grad) return fail(c, MLQP_EINVAL, "d_g and grad are required");
+  if ((st = check_work(c, d_work, work_bytes)) != MLQP_OK) return st;
+  if ((st = check_moved(c, moved)) != MLQP_OK) return st;  // before the factors are used up
+  if ((st = mlqp_gradient_prepare(c, d_g, d_work, work_bytes)) != MLQP_OK) return st;
+  return mlqp_gradient_eval(c, moved, t, d_work, work_bytes, grad);
 }
 
 mlqp_status mlqp_check_device(mlqp_ctx* c) {

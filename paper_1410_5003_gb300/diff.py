@@ -45,8 +45,9 @@ def reflected_weights(prob, orders=(0, -1)):
 class BraggEfficiency(torch.autograd.Function):
     """J(p) = sum over the angles and `orders` of the reflected efficiencies
     of make_problem(p).  Forward: one solve (mlqp_solve); backward, per
-    parameter p_q: mlqp_fd_gradient from the solved context and the contexts
-    of make_problem(p + s t e_q), s = -2, -1, 1, 2, plus the weights' own
+    parameter p_q: the sensitivities of the solve, formed once
+    (mlqp_gradient_prepare), contracted with the blocks of make_problem(p +
+    s t e_q), s = -2, -1, 1, 2 (mlqp_gradient_eval), plus the weights' own
     fourth-order difference times |a^U|^2.  The four moved contexts are made
     once and moved to each parameter's problems by mlqp_set_problem.  make_problem must keep the
     discretisation and the angles; backward runs once (no retain_graph)."""
@@ -77,9 +78,8 @@ class BraggEfficiency(torch.autograd.Function):
         grad = np.zeros_like(pv)
         moved = []
         try:
+            work = ctx.gradient_prepare(w * aU)  # the sensitivities, once for every parameter
             for q in range(pv.size):
-                if q > 0:
-                    ctx.solve_host()  # the previous gradient used up the factors
                 probs = []
                 for s_ in (-2, -1, 1, 2):
                     pm = pv.copy()
@@ -94,7 +94,7 @@ class BraggEfficiency(torch.autograd.Function):
                     moved = []
                     for mp in probs:
                         moved.append(new_context(mp))
-                gq = float(np.sum(ctx.fd_gradient(moved, step, w * aU)))
+                gq = float(np.sum(ctx.gradient_eval(moved, step, work)))
                 wm = [reflected_weights(mp, orders) for mp in probs]
                 dw = (wm[0] - 8.0 * wm[1] + 8.0 * wm[2] - wm[3]) / (12.0 * step)
                 grad[q] = gq + float(np.sum(dw * np.abs(aU) ** 2))

@@ -87,6 +87,10 @@ def load(path: str = LIB_PATH):
     lib.mlqp_gradient_work_bytes.restype = Z
     lib.mlqp_fd_gradient.argtypes = [P, ct.POINTER(P), D, V, V, Z, ct.POINTER(D)]
     lib.mlqp_fd_gradient.restype = I
+    lib.mlqp_gradient_prepare.argtypes = [P, V, V, Z]
+    lib.mlqp_gradient_prepare.restype = I
+    lib.mlqp_gradient_eval.argtypes = [P, ct.POINTER(P), D, V, Z, ct.POINTER(D)]
+    lib.mlqp_gradient_eval.restype = I
     lib.mlqp_check_device.argtypes = [P]
     lib.mlqp_check_device.restype = I
     lib.mlqp_solve.argtypes = [P, V, V, V, V]
@@ -114,7 +118,7 @@ def load(path: str = LIB_PATH):
 EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_set_angles", "mlqp_set_problem",
             "mlqp_autotune",
             "mlqp_solve_rhs", "mlqp_adjoint_solve", "mlqp_lsq_adjoint", "mlqp_x_elements",
-            "mlqp_gradient_work_bytes", "mlqp_fd_gradient",
+            "mlqp_gradient_work_bytes", "mlqp_fd_gradient", "mlqp_gradient_prepare", "mlqp_gradient_eval",
             "mlqp_solve_device",
             "mlqp_check_device", "mlqp_solve", "mlqp_run_stage", "mlqp_block_info", "mlqp_last_error",
             "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes",
@@ -347,6 +351,38 @@ class Context:
         with t_.cuda.stream(self.stream):
             _check(self.ctx, self.lib.mlqp_fd_gradient(self.ctx, ct.cast(arr, ct.POINTER(ct.c_void_p)), float(t),
                                                        ct.c_void_p(g.data_ptr()), ct.c_void_p(wp), nb, _dptr(out)))
+        return out
+
+    def _grad_args(self, g):
+        t_ = self.torch
+        g = t_.as_tensor(g, dtype=t_.complex128, device=self.device).contiguous()
+        if tuple(g.shape) != (self.n_theta, self.n_modes):
+            raise ValueError(f"g: expected ({self.n_theta}, {self.n_modes}), got {tuple(g.shape)}")
+        nb = int(self.lib.mlqp_gradient_work_bytes(self.ctx))
+        work = t_.empty(nb + 256, dtype=t_.uint8, device=self.device)
+        return g, work, (work.data_ptr() + 255) // 256 * 256, nb
+
+    def gradient_prepare(self, g):
+        """mlqp_gradient_prepare: the sensitivities of this solved context for
+        g = w a^U, formed once for many parameters; returns the work buffer
+        to pass to gradient_eval (the factors are used up)."""
+        g, work, wp, nb = self._grad_args(g)
+        with self.torch.cuda.stream(self.stream):
+            _check(self.ctx, self.lib.mlqp_gradient_prepare(self.ctx, ct.c_void_p(g.data_ptr()), ct.c_void_p(wp), nb))
+        return (work, wp, nb, g)
+
+    def gradient_eval(self, moved, t, work):
+        """mlqp_gradient_eval: per angle, 2 Re dF/dp for the parameter along
+        which `moved` (the contexts at -2t, -t, t, 2t) are moved."""
+        import numpy as np
+        if len(moved) != 4:
+            raise ValueError("moved: the contexts at -2t, -t, t, 2t")
+        _, wp, nb, _ = work
+        arr = (ct.c_void_p * 4)(*[m.ctx for m in moved])
+        out = np.zeros(self.n_theta)
+        with self.torch.cuda.stream(self.stream):
+            _check(self.ctx, self.lib.mlqp_gradient_eval(self.ctx, ct.cast(arr, ct.POINTER(ct.c_void_p)), float(t),
+                                                         ct.c_void_p(wp), nb, _dptr(out)))
         return out
 
     def host_outputs(self, eta=False, pinned=False):

@@ -73,6 +73,17 @@ class OracleContext:
         probs = [m.prob for m in moved]
         return np.array([forms_gradient(self.prob, a, g[a], probs, t) for a in range(self.prob.n_theta)])
 
+    def gradient_prepare(self, g):
+        if not self.factored:
+            raise RuntimeError("no factors: solve first")
+        self.factored = False
+        self.prepares = getattr(self, "prepares", 0) + 1
+        return np.array(g)
+
+    def gradient_eval(self, moved, t, work):
+        probs = [m.prob for m in moved]
+        return np.array([forms_gradient(self.prob, a, work[a], probs, t) for a in range(self.prob.n_theta)])
+
     def set_problem(self, prob):
         self.prob = prob
         self.factored = False

@@ -217,6 +217,8 @@ def test_gradient_needs_a_solved_fp64_context(M):
     assert lib.mlqp_gradient_work_bytes(None) == 0
     arr, I, k, keep = M._marshal(prob)
     assert lib.mlqp_set_problem(ctx, arr, I, M._dptr(k)) == M.MLQP_ESTATE
+    assert lib.mlqp_gradient_prepare(ctx, ct.c_void_p(256), ct.c_void_p(256), 1 << 30) == M.MLQP_ESTATE
+    assert lib.mlqp_gradient_eval(ctx, mv, 1e-3, ct.c_void_p(256), 1 << 30, out) == M.MLQP_ESTATE
     assert lib.mlqp_set_problem(None, arr, I, M._dptr(k)) == M.MLQP_EINVAL
     lib.mlqp_destroy(ctx)
 

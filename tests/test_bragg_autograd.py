@@ -42,6 +42,7 @@ def test_bragg_efficiency_value_and_gradient_on_the_oracle():
     # the base context and four moved ones, moved on to each later parameter
     assert len(made) == 5 and all(c.closed for c in made)
     assert all(getattr(c, "moves", 0) == len(names) - 1 for c in made[1:])
+    assert made[0].prepares == 1  # one solve and one set of sensitivities for all five parameters
     # a forward pass that needs no gradient releases its context at once
     made.clear()
     with torch.no_grad():

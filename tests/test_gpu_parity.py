@@ -735,6 +735,24 @@ def test_fd_gradient_against_the_oracle(M):
         assert abs(gr.sum() - ref[p]) < 1e-8 * max(abs(ref[p]), 1e-3), (p, gr.sum(), ref[p])
     with pytest.raises(M.MlqpError):  # the gradient used up the factors
         ctx.fd_gradient(moved, t, g)
+    # the sensitivities formed once, then one evaluation per parameter
+    ctx.solve_host()
+    work = ctx.gradient_prepare(g)
+    moved = None
+    for p, make in shifted.items():
+        probs = [make(s_ * t) for s_ in (-2, -1, 1, 2)]
+        if moved is None:
+            moved = [M.Context(mp) for mp in probs]
+        else:
+            for m, mp in zip(moved, probs):
+                m.set_problem(mp)
+        gr = ctx.gradient_eval(moved, t, work)
+        assert abs(gr.sum() - ref[p]) < 1e-8 * max(abs(ref[p]), 1e-3), (p, gr.sum(), ref[p])
+    ctx.set_angles(prob.theta)  # new angles: the prepared sensitivities no longer apply
+    with pytest.raises(M.MlqpError):
+        ctx.gradient_eval(moved, t, work)
+    for m in moved:
+        m.close()
     ctx.close()
 
 
