@@ -48,3 +48,43 @@ def test_bragg_efficiency_value_and_gradient_on_the_oracle():
     with torch.no_grad():
         bragg_efficiency(torch.zeros(5, dtype=torch.float64), make_problem, new_context=new_context)
     assert len(made) == 1 and made[0].closed
+
+
+def test_bragg_efficiency_edge_cases_on_the_oracle():
+    """No parameters: an empty gradient (one solve, the sensitivities still
+    formed); a second backward through the same graph is refused (the
+    solver context was released by the first)."""
+    from workloads import small_stack
+    prob = small_stack(I=1, N=40, P=40, Mw=24, K=8, M=30)
+
+    def make_problem(pv):
+        return prob
+
+    p = torch.zeros(0, dtype=torch.float64, requires_grad=True)
+    J = bragg_efficiency(p, make_problem, new_context=OracleContext)
+    J.backward()
+    assert p.grad.shape == (0,)
+    p = torch.zeros(1, dtype=torch.float64, requires_grad=True)
+    J = bragg_efficiency(p, make_problem, new_context=OracleContext)
+    J.backward(retain_graph=True)
+    assert abs(p.grad.item()) < 1e-9  # make_problem ignores p: dJ/dp = 0 up to the difference's rounding
+    with pytest.raises(RuntimeError):
+        J.backward()
+
+
+def test_reflected_weights_vanish_for_evanescent_and_grazing_orders():
+    """w_n = 0 where k^U_n is imaginary or zero (a Wood anomaly), and the
+    specular weight is 1 (k^U_0 = k_1 |sin theta|)."""
+    import math
+    from dataclasses import replace
+    from workloads import small_stack
+    prob = small_stack(I=1, N=40, P=40, Mw=24, K=8, M=30)
+    k1, d = float(np.real(prob.k[0])), prob.d
+    th_w = -math.acos(1.0 - 2.0 * math.pi / (d * k1))  # order +1 grazing: kappa_1 = k_1
+    pr = replace(prob).with_angles([th_w, -0.9])
+    w = reflected_weights(pr, orders=(0, 1, -8, 8))
+    K = pr.params.K
+    assert abs(w[0, K] - 1.0) < 1e-14 and abs(w[1, K] - 1.0) < 1e-14
+    kap = k1 * math.cos(th_w) + 2 * math.pi / d
+    assert w[0, K + 1] == 0.0 or k1 * k1 - kap * kap <= 1e-12 * k1 * k1
+    assert w[1, K + 8] == 0.0 and w[1, K - 8] == 0.0  # evanescent at |n| = 8
