@@ -53,7 +53,7 @@ class BraggEfficiency(torch.autograd.Function):
     discretisation and the angles; backward runs once (no retain_graph)."""
 
     @staticmethod
-    def forward(fctx, p, make_problem, orders, step, new_context):
+    def forward(fctx, p, make_problem, orders, step, new_context, distributed=False):
         import numpy as np
         pv = p.detach().to("cpu", torch.float64).numpy().copy()
         prob = make_problem(pv)
@@ -61,6 +61,7 @@ class BraggEfficiency(torch.autograd.Function):
         aU = np.asarray(ctx.solve_host()["aU"])
         w = reflected_weights(prob, orders)
         fctx.p_meta = (p.dtype, p.device)
+        fctx.distributed = distributed
         if fctx.needs_input_grad[0]:
             fctx.state = (pv, make_problem, orders, step, new_context, ctx, aU, w)
         else:
@@ -76,10 +77,13 @@ class BraggEfficiency(torch.autograd.Function):
         pv, make_problem, orders, step, new_context, ctx, aU, w = fctx.state
         fctx.state = None
         grad = np.zeros_like(pv)
+        rank, world = _shard()
+        if not fctx.distributed:
+            rank, world = 0, 1
         moved = []
         try:
             work = ctx.gradient_prepare(w * aU)  # the sensitivities, once for every parameter
-            for q in range(pv.size):
+            for q in range(rank, pv.size, world):  # this rank's share of the parameters
                 probs = []
                 for s_ in (-2, -1, 1, 2):
                     pm = pv.copy()
@@ -102,16 +106,36 @@ class BraggEfficiency(torch.autograd.Function):
             for m in moved:
                 m.close()
             ctx.close()
+        if world > 1:  # every rank solved the same problem: the shares add up to the gradient
+            import torch.distributed as dist
+            dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+            tot = torch.as_tensor(grad, dtype=torch.float64, device=dev)
+            dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+            grad = tot.cpu().numpy()
         dtype, device = fctx.p_meta
-        return torch.as_tensor(float(gJ) * grad).to(dtype=dtype, device=device), None, None, None, None
+        return torch.as_tensor(float(gJ) * grad).to(dtype=dtype, device=device), None, None, None, None, None
 
 
-def bragg_efficiency(p, make_problem, orders=(0, -1), step=1e-3, device="cuda", new_context=None):
+def _shard():
+    """(rank, world size) of the default process group, (0, 1) without one."""
+    try:
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            return dist.get_rank(), dist.get_world_size()
+    except ImportError:
+        pass
+    return 0, 1
+
+
+def bragg_efficiency(p, make_problem, orders=(0, -1), step=1e-3, device="cuda", new_context=None,
+                     distributed=False):
     """J(p) as a torch scalar, differentiable in the 1-D parameter tensor p
     (wavenumbers, interface coefficients, anything make_problem maps it to).
     new_context(prob) makes the solver context (default: an FP64 Context on
-    `device`)."""
+    `device`).  distributed=True, under an initialised process group whose
+    ranks all call this with the same p: each rank evaluates the parameters
+    q = rank, rank + world, ... and one all_reduce sums the shares."""
     if new_context is None:
         from . import mlqp
         new_context = lambda prob: mlqp.Context(prob, device=device)  # noqa: E731
-    return BraggEfficiency.apply(p, make_problem, tuple(orders), float(step), new_context)
+    return BraggEfficiency.apply(p, make_problem, tuple(orders), float(step), new_context, bool(distributed))

@@ -81,6 +81,7 @@ class OracleContext:
         return np.array(g)
 
     def gradient_eval(self, moved, t, work):
+        self.evals = getattr(self, "evals", 0) + 1
         probs = [m.prob for m in moved]
         return np.array([forms_gradient(self.prob, a, work[a], probs, t) for a in range(self.prob.n_theta)])
 

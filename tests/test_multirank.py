@@ -1,7 +1,9 @@
-"""The multi-GPU path of bench.py (angle sharding, weak scaling) on CPU:
-world-size-2 gloo ranks run the host logic (each rank's problem, the job
-time as the maximum over ranks, the whole-job value), and the reference arm
-under torchrun prints one line from rank 0 only.  No GPU is involved."""
+"""The multi-GPU paths on CPU: world-size-2 gloo ranks run the host logic of
+bench.py's angle sharding (each rank's problem, the job time as the maximum
+over ranks, the whole-job value) and of the gradient's parameter sharding
+(each rank's share of the parameters, one all_reduce of the shares), and the
+reference arm under torchrun prints one line from rank 0 only.  No GPU is
+involved."""
 import json
 import os
 import socket
@@ -52,6 +54,50 @@ def test_two_gloo_ranks_shard_angles_and_take_the_slowest_time():
     # the job's time is the slowest rank's; the value counts every rank's units
     assert ms0 == ms1 == 125.0
     assert v0 == v1 == pytest.approx(I0 * len(th0) * 2 * 3 / 0.125)
+
+
+def _grad_rank(rank, world, port, results):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1410_5003_gb300.diff import bragg_efficiency
+        from tests.adjoint_forms import OracleContext, gradient_family
+        prob, make_problem, _, _ = gradient_family()
+        made = []
+
+        def new_context(pr):
+            made.append(OracleContext(pr))
+            return made[-1]
+
+        p = torch.zeros(5, dtype=torch.float64, requires_grad=True)
+        J = bragg_efficiency(p, make_problem, new_context=new_context, distributed=True)
+        J.backward()
+        results[rank] = (float(J), p.grad.tolist(), getattr(made[0], "evals", 0))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gradient_parameters_shard_over_two_gloo_ranks():
+    """bragg_efficiency(distributed=True): rank r evaluates the parameters
+    r, r + 2, ..., and one all_reduce sums the shares; both ranks end with
+    the whole gradient, equal to the oracle's adjoint gradient (the ranks'
+    contexts are oracle-backed stand-ins; no GPU is involved)."""
+    sys.path.insert(0, ROOT)
+    from oracle import mlqp_oracle as O
+    from tests.adjoint_forms import gradient_family
+    world, port = 2, _free_port()
+    with mp.Manager() as man:
+        results = man.dict()
+        mp.start_processes(_grad_rank, args=(world, port, results), nprocs=world, start_method="spawn")
+        r = dict(results)
+    prob, _, shifted, names = gradient_family()
+    ref = O.adjoint_gradient(prob, shifted, {nm: 1e-3 for nm in names})
+    (J0, g0, e0), (J1, g1, e1) = r[0], r[1]
+    assert J0 == J1 and g0 == g1
+    assert (e0, e1) == (3, 2)  # parameters 0, 2, 4 and 1, 3
+    for q, nm in enumerate(names):
+        assert abs(g0[q] - ref[nm]) < 1e-9 * max(abs(ref[nm]), 1e-3), (nm, g0[q], ref[nm])
 
 
 def test_reference_arm_under_torchrun_prints_from_rank_zero_only():
