@@ -174,3 +174,45 @@ def test_block_sensitivities_are_rank_one_forms():
             mine[p] += forms_gradient(prob, a, g, [make(s_ * t) for s_ in (-2, -1, 1, 2)], t)
     for p in shifted:
         assert abs(mine[p] - ref[p]) < 1e-9 * max(abs(ref[p]), 1e-3), (p, mine[p], ref[p])
+
+
+def test_parameter_blocks_are_local():
+    """Which blocks a parameter moves (the locality a restricted gradient
+    fill would use), on a 4-interface stack: a Fourier coefficient of
+    interface 2 moves the A blocks that touch interface 2, B_{i,j} (layer j's
+    proxies to interface i) with i = 2 or j in {2, 3} (the proxy circles of
+    layers 2 and 3 sit at their walls' mid-height) and Q', C' of layers 2
+    and 3; the wavenumber of layer 3 moves
+    the A blocks of interfaces 2 and 3, B_{2,3}, B_{3,3} and Q', C' of layer
+    3.  Every other block is bitwise unchanged."""
+    from dataclasses import replace
+    from workloads.problems import Interface
+    prob = small_stack(I=4, N=40, P=40, Mw=24, K=8, M=30)
+    th = float(prob.theta[0])
+
+    def shape(t):
+        ifs = list(prob.ifaces)
+        f = ifs[1]
+        a = f.a.copy()
+        a[0] += t
+        ifs[1] = Interface(f.y0, a, f.b.copy(), f.N)
+        return replace(prob, ifaces=ifs)
+
+    def wavenumber(t):
+        k = prob.k.copy()
+        k[2] += t
+        return replace(prob, k=k)
+
+    cases = {
+        "shape": (shape, {"A": {(i, j) for (i, j) in [(1, 2), (2, 1), (2, 2), (2, 3), (3, 2)]},
+                          "B": {(1, 2), (2, 2), (2, 3), (3, 3)},
+                          "Qp": {2, 3}, "Cp": {2, 3}}),
+        "wavenumber": (wavenumber, {"A": {(2, 2), (2, 3), (3, 2), (3, 3)},
+                                    "B": {(2, 3), (3, 3)}, "Qp": {3}, "Cp": {3}}),
+    }
+    for name, (make, moved) in cases.items():
+        lo, hi = O._blocks(make(-1e-3), th), O._blocks(make(1e-3), th)
+        for kind in ("A", "B", "Qp", "Cp"):
+            for key in lo[kind]:
+                same = np.array_equal(lo[kind][key], hi[kind][key])
+                assert same == (key not in moved[kind]), (name, kind, key, same)
