@@ -7,13 +7,14 @@ import numpy as np
 from oracle import mlqp_oracle as O
 
 
-def forms_gradient(prob, a, g, moved_probs, t):
+def forms_gradient(prob, a, g, moved_probs, t, only=None):
     """2 Re[(F(-2t) - 8 F(-t) + 8 F(t) - F(2t)) / (12 t)] for angle a: the
     sensitivities of prob's solve with g = w a^U of that angle (mu from
     A'^H mu = -X_1[P:]^H g; xi = X eta^; y = (Q'^H Q' + lam^2)^{-1} Psi;
     Q'y and r = C' eta^ - Q' xi), and F(M) = mu^H (f - A eta + B xi[:P]) +
     sum_j [(Q'y)_j^H (C'_j eta^_j - Q'_j xi_j) + r_j^H Q'_j y_j] over the
-    oracle blocks of each moved problem."""
+    oracle blocks of each moved problem.  only: None (every block) or
+    {"f": bool, "A": keys, "B": keys, "layers": layers}, the terms kept."""
     I, P, rc = prob.I, prob.params.P, prob.params.lsq_rcond
     th = float(prob.theta[a])
     sc = O.schur(prob, th)
@@ -37,14 +38,19 @@ def forms_gradient(prob, a, g, moved_probs, t):
         qy[j] = sc["Qp"][j] @ y[j]
         rv[j] = sc["Cp"][j] @ etaL[j] - sc["Qp"][j] @ xi[j]
 
+    keep = (lambda kind, key: True) if only is None else (lambda kind, key: key in only[kind])
+
     def F(b):
-        s = np.vdot(mu[1], b["f"])
+        s = np.vdot(mu[1], b["f"]) if only is None or only["f"] else 0.0
         for (i, j), A in b["A"].items():
-            s -= np.vdot(mu[i], A @ eta[j])
+            if keep("A", (i, j)):
+                s -= np.vdot(mu[i], A @ eta[j])
         for (i, j), B in b["B"].items():
-            s += np.vdot(mu[i], B @ xi[j][:P])
+            if keep("B", (i, j)):
+                s += np.vdot(mu[i], B @ xi[j][:P])
         for j in range(1, I + 2):
-            s += np.vdot(qy[j], b["Cp"][j] @ etaL[j] - b["Qp"][j] @ xi[j]) + np.vdot(rv[j], b["Qp"][j] @ y[j])
+            if keep("layers", j):
+                s += np.vdot(qy[j], b["Cp"][j] @ etaL[j] - b["Qp"][j] @ xi[j]) + np.vdot(rv[j], b["Qp"][j] @ y[j])
         return s
 
     Fs = [F(O._blocks(mp, th)) for mp in moved_probs]

@@ -216,3 +216,42 @@ def test_parameter_blocks_are_local():
             for key in lo[kind]:
                 same = np.array_equal(lo[kind][key], hi[kind][key])
                 assert same == (key not in moved[kind]), (name, kind, key, same)
+
+
+def test_gradient_forms_restricted_to_the_moved_blocks():
+    """The difference of F over only the blocks a parameter moves equals the
+    difference over every block (the others' terms are identical in the four
+    moved problems and cancel), to 1e-9 of the gradient: a shape coefficient
+    of interface 2 and the wavenumber of layer 3 on a 4-interface stack."""
+    from dataclasses import replace
+    from workloads.problems import Interface
+    base = small_stack(I=4, N=40, P=40, Mw=24, K=8, M=30)
+    prob = replace(base, params=replace(base.params, lsq_rcond=1e-6))
+    P, t, a = prob.params.P, 1e-3, 0
+    th = float(prob.theta[a])
+
+    def shape(s_):
+        ifs = list(prob.ifaces)
+        f = ifs[1]
+        av = f.a.copy()
+        av[0] += s_
+        ifs[1] = Interface(f.y0, av, f.b.copy(), f.N)
+        return replace(prob, ifaces=ifs)
+
+    def wavenumber(s_):
+        k = prob.k.copy()
+        k[2] += s_
+        return replace(prob, k=k)
+
+    cases = [(shape, {"f": False, "A": {(1, 2), (2, 1), (2, 2), (2, 3), (3, 2)},
+                      "B": {(1, 2), (2, 2), (2, 3), (3, 3)}, "layers": {2, 3}}),
+             (wavenumber, {"f": False, "A": {(2, 2), (2, 3), (3, 2), (3, 3)},
+                           "B": {(2, 3), (3, 3)}, "layers": {3}})]
+    sc = O.schur(prob, th)
+    eta1 = O.block_thomas(sc["Ad"], sc["Al"], sc["Au"], sc["f"], prob.I)[1]
+    g = O.reflected_weights(prob, th, sc["bloch"]) * -(sc["X"][1][P:, :] @ eta1)
+    for make, only in cases:
+        probs = [make(s_ * t) for s_ in (-2, -1, 1, 2)]
+        full = forms_gradient(prob, a, g, probs, t)
+        local = forms_gradient(prob, a, g, probs, t, only=only)
+        assert abs(local - full) < 1e-9 * max(abs(full), 1e-3), (local, full)
