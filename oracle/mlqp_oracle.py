@@ -1023,6 +1023,76 @@ def adjoint_gradient(prob, shifted, step, orders=(0, -1)):
     return grad
 
 
+def solve_streaming(prob, itheta=0):
+    """solve() without holding every block at once, for stacks whose blocks
+    do not fit in host memory together (the 1000-interface corner grating:
+    about 25 GB of A, A' and per-copy terms).  Each quantity is formed by the
+    same expression as in schur() and block_thomas(), in the order the
+    forward sweep of Sec. 3.3 first needs it: X_j (Sec. 3.2) when interface
+    j-1 or j is reached, A'_{i,i-1}, A'_{i,i}, A'_{i,i+1} (eqs. Schur1 -
+    Schuri) at step i, then A~_i and f~_i.  Blocks are dropped once used; the
+    LU factors of A~_i and A'_{i,i+1} are kept for the backward sweep.  The
+    results are bitwise those of solve()."""
+    theta = float(prob.theta[itheta])
+    I, P = prob.I, prob.params.P
+    bl = bloch(prob, theta)
+    al = bl["alpha"]
+    n = [2 * f.N for f in prob.ifaces]
+    asm = Assembler(prob)
+    X = {}
+
+    def x_of(j):
+        if j not in X:
+            X[j] = lsq(asm.Qp(j, al, bl), asm.Cp(j, al), prob.params.lsq_rcond)
+        return X[j]
+
+    def xcols(j, i):
+        off = 0
+        for ii in layer_columns(prob, j):
+            if ii == i:
+                return x_of(j)[:P, off:off + n[i - 1]]
+            off += n[ii - 1]
+        raise KeyError
+
+    def evict(below):
+        """Drop cached per-copy terms and X blocks of interfaces and layers
+        that no later step reads (all indices < below; X_1 stays for the
+        amplitudes)."""
+        for key in list(asm._c):
+            idx = [v for v in key[1:] if isinstance(v, int)]
+            if idx and max(idx) < below:
+                del asm._c[key]
+        for j in list(X):
+            if 1 < j < below:
+                del X[j]
+
+    lu, Au, ft = {}, {}, {}
+    f1 = rhs(prob, theta)
+    for i in range(1, I + 1):
+        Ad = asm.A(i, i, al) - asm.B(i, i) @ xcols(i, i) - asm.B(i, i + 1) @ xcols(i + 1, i)
+        if i < I:
+            Au[i] = asm.A(i, i + 1, al) - asm.B(i, i + 1) @ xcols(i + 1, i + 1)
+        if i == 1:
+            At, ft[1] = Ad, f1
+        else:
+            Al = asm.A(i, i - 1, al) - asm.B(i, i) @ xcols(i, i - 1)
+            Y = sla.lu_solve(lu[i - 1], Au[i - 1])
+            At = Ad - Al @ Y
+            fi = np.zeros(n[i - 1], np.complex128)
+            ft[i] = fi - Al @ sla.lu_solve(lu[i - 1], ft[i - 1])
+            del Al, Y
+        lu[i] = sla.lu_factor(At)
+        del Ad, At
+        evict(i)
+    eta = {I: sla.lu_solve(lu[I], ft[I])}
+    for i in range(I - 1, 0, -1):
+        eta[i] = sla.lu_solve(lu[i], ft[i] - Au[i] @ eta[i + 1])
+    aU = -(x_of(1)[P:, :] @ eta[1])
+    aD = -(x_of(I + 1)[P:, :] @ eta[I])
+    return dict(theta=theta, aU=aU, aD=aD, eta=np.concatenate([eta[i] for i in range(1, I + 1)]),
+                flux=flux_error(prob, theta, bl, aU, aD), bloch=bl)
+
+
 def solve_all(prob):
     asm = Assembler(prob)
     return [solve(prob, t, asm) for t in range(prob.n_theta)]

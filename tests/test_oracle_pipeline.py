@@ -211,3 +211,17 @@ def test_regularised_and_pivoted_lsq_agree_on_amplitudes():
             O.lsq = orig
         scale = np.max(np.abs(_amps(r)))
         assert np.max(np.abs(_amps(r) - _amps(rp))) < 1e-9 * scale
+
+
+def test_streaming_solve_is_the_plain_solve():
+    """solve_streaming (blocks formed when the forward sweep needs them and
+    dropped after) gives bitwise the amplitudes and densities of solve() on a
+    smooth stack and on a corner stack with a lossy layer."""
+    from workloads import corner_stack
+    for prob in (small_stack(I=4, N=40, P=40, Mw=24, K=6, M=20),
+                 corner_stack(I=3, levels=1, K=6, M=20, lossy=True)):
+        a = O.solve(prob, 0)
+        b = O.solve_streaming(prob, 0)
+        assert np.array_equal(a["aU"], b["aU"]) and np.array_equal(a["aD"], b["aD"])
+        assert np.array_equal(a["eta"], b["eta"])
+        assert (math.isnan(a["flux"]) and math.isnan(b["flux"])) or a["flux"] == b["flux"]
