@@ -56,10 +56,17 @@ class BraggEfficiency(torch.autograd.Function):
     def forward(fctx, p, make_problem, orders, step, new_context, distributed=False):
         import numpy as np
         pv = p.detach().to("cpu", torch.float64).numpy().copy()
-        prob = make_problem(pv)
-        ctx = new_context(prob)
-        aU = np.asarray(ctx.solve_host()["aU"])
-        w = reflected_weights(prob, orders)
+        ctx, err = None, None
+        try:
+            prob = make_problem(pv)
+            ctx = new_context(prob)
+            aU = np.asarray(ctx.solve_host()["aU"])
+            w = reflected_weights(prob, orders)
+        except Exception as e:  # noqa: BLE001 -- re-raised below, on every rank
+            err = e
+            if ctx is not None:
+                ctx.close()
+        _agree(distributed, err, "forward solve")
         fctx.p_meta = (p.dtype, p.device)
         fctx.distributed = distributed
         if fctx.needs_input_grad[0]:
@@ -80,7 +87,7 @@ class BraggEfficiency(torch.autograd.Function):
         rank, world = _shard()
         if not fctx.distributed:
             rank, world = 0, 1
-        moved = []
+        moved, err = [], None
         try:
             work = ctx.gradient_prepare(w * aU)  # the sensitivities, once for every parameter
             for q in range(rank, pv.size, world):  # this rank's share of the parameters
@@ -102,18 +109,44 @@ class BraggEfficiency(torch.autograd.Function):
                 wm = [reflected_weights(mp, orders) for mp in probs]
                 dw = (wm[0] - 8.0 * wm[1] + 8.0 * wm[2] - wm[3]) / (12.0 * step)
                 grad[q] = gq + float(np.sum(dw * np.abs(aU) ** 2))
+        except Exception as e:  # noqa: BLE001 -- re-raised below, after the ranks agree
+            err = e
         finally:
             for m in moved:
                 m.close()
             ctx.close()
         if world > 1:  # every rank solved the same problem: the shares add up to the gradient
+            # One all_reduce carries the shares and a failure count, so that a
+            # rank whose share failed still takes part and every rank learns of it.
             import torch.distributed as dist
             dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
-            tot = torch.as_tensor(grad, dtype=torch.float64, device=dev)
+            tot = torch.as_tensor(np.append(grad, 1.0 if err is not None else 0.0), dtype=torch.float64,
+                                  device=dev)
             dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-            grad = tot.cpu().numpy()
+            tot = tot.cpu().numpy()
+            if tot[-1] > 0:
+                raise RuntimeError(f"parameter gradient failed on {int(tot[-1])} of {world} ranks") from err
+            grad = tot[:-1]
+        elif err is not None:
+            raise err
         dtype, device = fctx.p_meta
         return torch.as_tensor(float(gJ) * grad).to(dtype=dtype, device=device), None, None, None, None, None
+
+
+def _agree(distributed, err, what):
+    """Raises on every rank if `what` failed on any rank (one all_reduce of a
+    failure count under an initialised process group with distributed=True;
+    otherwise re-raises the local error)."""
+    rank, world = _shard()
+    if distributed and world > 1:
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        flag = torch.tensor([1.0 if err is not None else 0.0], dtype=torch.float64, device=dev)
+        dist.all_reduce(flag, op=dist.ReduceOp.SUM)
+        if float(flag.item()) > 0:
+            raise RuntimeError(f"{what} failed on {int(flag.item())} of {world} ranks") from err
+    elif err is not None:
+        raise err
 
 
 def _shard():

@@ -113,3 +113,46 @@ def test_reference_arm_under_torchrun_prints_from_rank_zero_only():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def _failing_grad_rank(rank, world, port, results, fail_in):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1410_5003_gb300.diff import bragg_efficiency
+        from tests.adjoint_forms import OracleContext, gradient_family
+        prob, make_problem, _, _ = gradient_family()
+        calls = []
+
+        def flaky_problem(pv):
+            calls.append(1)
+            # rank 1 fails on its first problem (forward) or on a moved one (backward)
+            if rank == 1 and (fail_in == "forward" or len(calls) > 1):
+                raise ValueError("make_problem failed on rank 1")
+            return make_problem(pv)
+
+        p = torch.zeros(5, dtype=torch.float64, requires_grad=True)
+        try:
+            J = bragg_efficiency(p, flaky_problem, new_context=OracleContext, distributed=True)
+            J.backward()
+            results[rank] = "ok"
+        except RuntimeError as e:
+            results[rank] = str(e)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("fail_in", ["forward", "backward"])
+def test_gradient_failure_on_one_rank_reaches_every_rank(fail_in):
+    """If one rank's problem cannot be made (an exception in make_problem, in
+    the forward solve or in its share of the parameters), that rank still
+    takes part in the collective, and every rank raises instead of waiting."""
+    world, port = 2, _free_port()
+    with mp.Manager() as man:
+        results = man.dict()
+        mp.start_processes(_failing_grad_rank, args=(world, port, results, fail_in), nprocs=world,
+                           start_method="spawn")
+        r = dict(results)
+    assert "failed on 1 of 2 ranks" in r[0], r
+    assert "failed on 1 of 2 ranks" in r[1], r
