@@ -50,7 +50,7 @@ typedef enum {
 
 enum { MLQP_FP64 = 0, MLQP_MIXED = 1 };
 enum { MLQP_SWEEP = 0, MLQP_CYCLIC = 1 };
-enum { MLQP_IR = 0, MLQP_GMRES_IR = 1 };
+enum { MLQP_IR = 0, MLQP_GMRES_IR = 1, MLQP_IR_GMRES = 2 };
 
 typedef struct mlqp_ctx mlqp_ctx;
 
@@ -103,7 +103,11 @@ typedef struct {
  * FP64, at most 40 steps, right-preconditioned by the same FP32 block
  * factors, stopped when its residual falls by 1e-10; it converges where
  * kappa(A') eps_32 is near 1 and plain refinement stalls, at up to 40 block
- * solves and FP64 operator products per correction). */
+ * solves and FP64 operator products per correction) or MLQP_IR_GMRES (plain
+ * corrections while each of them divides every unconverged angle's omega by
+ * at least 4; from the first one that does not, GMRES corrections for all
+ * angles still unconverged; the form that is cheap where plain refinement
+ * converges and safe where it stalls). */
 typedef struct {
   int P;
   double R;
@@ -289,21 +293,33 @@ mlqp_status mlqp_set_problem(mlqp_ctx* ctx, const mlqp_interface* ifaces, int I,
  * this costs several solves): the CTAs per least-squares QR cluster (1, 2,
  * 4, 8), the number of angle groups (streams) of the block solve (1 to
  * min(n_theta, 4)), the tile edge of the block LU's trailing update (16 or
- * 32; not with MLQP_CYCLIC) and, with MLQP_CYCLIC, the largest cluster of
- * the cyclic-reduction LU (1, 2, 4, 8).  which selects them (MLQP_TUNE_*
+ * 32; not with MLQP_CYCLIC), look-ahead in the block LU (off or on: the
+ * next panel factored on a second stream beside the rest of each trailing
+ * update, its CTAs reserving their SMs; not with MLQP_CYCLIC) and, with
+ * MLQP_CYCLIC, the largest cluster of the cyclic-reduction LU (1, 2, 4, 8).  which selects them (MLQP_TUNE_*
  * bits; MLQP_TUNE_ALL or 0 for all); the fastest of each is kept for later
  * solves.  None of them changes the arithmetic: results are bitwise those of
  * the default shapes.  report (may be NULL) receives MLQP_TUNE_REPORT
  * doubles: [QR cluster chosen, LSQ-stage ms for 1, 2, 4, 8; angle groups
  * chosen, block-solve ms for 1, 2, 3, 4 groups; CR cluster cap chosen,
  * block-solve ms for 1, 2, 4, 8; update tile chosen, block-solve ms for 16,
- * 32], NaN where a candidate does not apply.  Sec. 3.4's angle
+ * 32; look-ahead chosen (0 or 1), block-solve ms without and with it], NaN
+ * where a candidate does not apply.  Sec. 3.4's angle
  * sweep is the intended use: tune on the first chunk, then mlqp_set_angles.
  * Errors: MLQP_ESTATE (not bound), MLQP_EINVAL (report too short),
  * MLQP_ECUDA. */
-enum { MLQP_TUNE_REPORT = 18 };
-enum { MLQP_TUNE_QR = 1, MLQP_TUNE_TILE = 2, MLQP_TUNE_GROUPS = 4, MLQP_TUNE_CR = 8, MLQP_TUNE_ALL = 15 };
+enum { MLQP_TUNE_REPORT = 21 };
+enum { MLQP_TUNE_QR = 1, MLQP_TUNE_TILE = 2, MLQP_TUNE_GROUPS = 4, MLQP_TUNE_CR = 8, MLQP_TUNE_LOOKAHEAD = 16,
+       MLQP_TUNE_ALL = 31 };
 mlqp_status mlqp_autotune(mlqp_ctx* ctx, int which, double* report, int report_len);
+
+/* Sets one launch shape of a bound context by hand (which: one MLQP_TUNE_*
+ * bit; value: a candidate mlqp_autotune would try: QR cluster 1, 2, 4, 8;
+ * update tile 16, 32; angle groups 1..min(n_theta, 4); cyclic-reduction
+ * cluster cap 1, 2, 4, 8; look-ahead 0, 1).  The stage graphs are re-captured
+ * at the next solve; the arithmetic, and so every result, is unchanged.
+ * Errors: MLQP_ESTATE (not bound), MLQP_EINVAL, MLQP_ECUDA. */
+mlqp_status mlqp_set_shape(mlqp_ctx* ctx, int which, int value);
 
 /* Location of a workspace block (for inspection by tests):
  *   MLQP_BLK_ROW    interface i (1..I), angle a: the block row
@@ -364,9 +380,12 @@ long mlqp_launch_count(const mlqp_ctx* ctx);
  * serialised by the caller.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  No cudaMalloc, cudaFree
- * or allocating library routine is called.
+ * or allocating library routine is called.  d_Q, d_C and d_X must be
+ * 16-byte aligned (each complex entry is moved as one 16-byte access).  If
+ * every column of Q is zero, lam is 0, R has a zero diagonal and X is not
+ * finite: this call does not detect it (it returns before the kernels run).
  * Errors: MLQP_EINVAL (sizes, leading dimensions, rcond not in (0, 1), null
- * pointers), MLQP_ENOMEM (beyond the fixed scratch), MLQP_ECUDA. */
+ * or misaligned pointers), MLQP_ENOMEM (beyond the fixed scratch), MLQP_ECUDA. */
 mlqp_status mlqp_lsq_solve_noalloc(const void* d_Q, int m, int p, int ldq, const void* d_C, int nc, int ldc,
                                    double rcond, void* d_X, int ldx, void* stream);
 

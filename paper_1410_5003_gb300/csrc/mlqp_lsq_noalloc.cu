@@ -14,6 +14,7 @@
 // whose kernels overlap on the GPU (e.g. on two streams) race on it.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/mlqp.h"
@@ -198,6 +199,8 @@ extern "C" mlqp_status mlqp_lsq_solve_noalloc(const void* d_Q, int m, int p, int
   if (m < 1 || p < 1 || nc < 0 || ldq < m || ldc < m || ldx < p || !(rcond > 0.0 && rcond < 1.0))
     return MLQP_EINVAL;
   if (!d_Q || (nc > 0 && (!d_C || !d_X))) return MLQP_EINVAL;
+  // both kernels move complex entries as 16-byte double2 loads and stores
+  if (((uintptr_t)d_Q | (uintptr_t)d_C | (uintptr_t)d_X) & 15u) return MLQP_EINVAL;
   const size_t need = (size_t)(m + p) * (size_t)(p + nc) + 3 * (size_t)p;
   if (need > NOALLOC_ENTRIES) return MLQP_ENOMEM;  // beyond the fixed scratch
   if ((size_t)p * sizeof(double) > 48 * 1024) return MLQP_ENOMEM;

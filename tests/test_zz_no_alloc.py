@@ -5,9 +5,13 @@ give the library the workspace mlqp_bind needs): it solves one regularised
 least-squares problem with scratch held in a fixed array inside the library.
 Here it is called through the C ABI, twice in a row, on the same blocks the
 workspace path solves in its least-squares stage, and its X is compared with
-that path's X: within 1e-11 relative on well-conditioned synthetic blocks,
+that path's X and with the FP64 CPU oracle's regularised least squares
+(oracle.lsq): within 1e-11 relative on well-conditioned synthetic blocks,
 and on the physical wall/radiation blocks with the tolerances of the stage
-test (fitted values Q X to 1e-9, X to 1e-5).  This file is collected last.
+test (fitted values Q X to 1e-9, X to 1e-5).  One case fills the fixed
+scratch exactly ((m + p)(p + nc) + 3p = 262144), so that the last columns
+of the right-hand side reach the array's last entry.  This file is collected
+last.
 """
 import ctypes as ct
 
@@ -18,6 +22,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+from oracle import mlqp_oracle as O  # noqa: E402
 from workloads import small_stack  # noqa: E402
 
 
@@ -74,13 +79,33 @@ def test_noalloc_lsq_matches_workspace_path(M, synthetic):
         for j, (Q, C) in inputs.items():
             X_ref = ctx.block(M.BLK_X, j, 0).cpu().numpy()
             X = _noalloc(M, Q, C, rcond)
+            X_ora = O.lsq(Q.cpu().numpy(), C.cpu().numpy(), rcond)
             if synthetic:
                 assert rel(X, X_ref) < 1e-11, (call, j)
+                assert rel(X, X_ora) < 1e-11, (call, j)
             else:
                 q = Q.cpu().numpy()
                 assert rel(q @ X, q @ X_ref) < 1e-9, (call, j)
                 assert rel(X, X_ref) < 1e-5, (call, j)
+                assert rel(q @ X, q @ X_ora) < 1e-9, (call, j)
+                assert rel(X, X_ora) < 1e-5, (call, j)
     ctx.close()
+
+
+def test_noalloc_at_the_largest_accepted_size(M):
+    """m = 241, p = 12, nc = 1024: (m + p)(p + nc) + 3p = 262144, the whole
+    fixed array; X equals the oracle's regularised least squares."""
+    m, p, nc = 241, 12, 1024
+    assert (m + p) * (p + nc) + 3 * p == 262144
+    rng = np.random.default_rng(5)
+    Qh = rng.standard_normal((m, p)) + 1j * rng.standard_normal((m, p))
+    Ch = rng.standard_normal((m, nc)) + 1j * rng.standard_normal((m, nc))
+    Q = torch.from_numpy(Qh).cuda()
+    C = torch.from_numpy(Ch).cuda()
+    ref = O.lsq(Qh, Ch, 1e-10)
+    for call in range(2):
+        X = _noalloc(M, Q, C, 1e-10)
+        assert rel(X, ref) < 1e-11, call
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(M):
@@ -89,5 +114,12 @@ def test_noalloc_rejects_problems_beyond_its_scratch(M):
     ptr = ct.c_void_p(dummy.data_ptr())
     # (m + p)(p + nc) + 3p > 262144: refused before any device work
     assert lib.mlqp_lsq_solve_noalloc(ptr, 400, 200, 400, ptr, 600, 400, 1e-10, ptr, 200, None) == M.MLQP_ENOMEM
+    # one entry beyond the array: (208 + 13)(13 + 1173) + 39 = 262145
+    assert lib.mlqp_lsq_solve_noalloc(ptr, 208, 13, 208, ptr, 1173, 208, 1e-10, ptr, 13, None) == M.MLQP_ENOMEM
+    # buffers off the 16-byte boundary of a complex entry are refused
+    odd = ct.c_void_p(dummy.data_ptr() + 8)
+    assert lib.mlqp_lsq_solve_noalloc(odd, 10, 5, 10, ptr, 3, 10, 1e-10, ptr, 5, None) == M.MLQP_EINVAL
+    assert lib.mlqp_lsq_solve_noalloc(ptr, 10, 5, 10, odd, 3, 10, 1e-10, ptr, 5, None) == M.MLQP_EINVAL
+    assert lib.mlqp_lsq_solve_noalloc(ptr, 10, 5, 10, ptr, 3, 10, 1e-10, odd, 5, None) == M.MLQP_EINVAL
     assert lib.mlqp_lsq_solve_noalloc(ptr, 10, 5, 4, ptr, 3, 10, 1e-10, ptr, 5, None) == M.MLQP_EINVAL
     assert lib.mlqp_lsq_solve_noalloc(ptr, 10, 5, 10, ptr, 3, 10, 0.0, ptr, 5, None) == M.MLQP_EINVAL
