@@ -2,16 +2,21 @@
 
 Metric: layer*angle solves per second (interfaces x incidence angles solved
 per second, from the first fill kernel to the Bragg amplitudes).  Workload:
-the 20-interface grating (5-mode random Fourier profiles 1.5 apart, period
-2 pi, layer wavenumbers U[5, 20] with one lossy layer, 120 nodes per
-interface, 30 wall nodes, 60 proxies, K = 25, 3 angles one of them 1e-8 past
-a Wood anomaly), plain FP64.  A step is one solve of all three angles.
+the paper-scale corner grating -- 1000 trapezoidal interfaces 1 apart
+(period 1, height 0.4, corners at x = +-0.3, +-0.1), 256 nodes per
+interface (16-node Gauss-Legendre panels, 2 dyadic levels per corner side),
+512 000 unknowns, layer wavenumbers alternating 10 and 20 with +-5 % jitter,
+one angle theta = -pi/4, P = 60, M_w = 30, K = 20 -- solved in plain FP64
+(`value`), beside the mixed form with the block sweep and with block cyclic
+reduction (FP32 Schur / LU, FP64 refinement).  A step is one solve.  Small
+leg: the 20-interface, 3-angle grating.  Optional legs: the 256-angle sweep of
+the 100-interface stack at its resolved discretisation, gradients.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun every rank solves the same stack for its own three angles
-(shifted by 1e-3 rank), so per-GPU work is fixed (weak scaling); the only
-collective is the max over ranks of the timing.
+Under torchrun every rank solves the same stack at its own angle (shifted by
+1e-3 rank), so per-GPU work is fixed (weak scaling); the only collective is
+the max over ranks of the timing.
 """
 from __future__ import annotations
 
@@ -29,7 +34,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "layer*angle solves/s"
-WORKLOAD = "20-interface random grating, 120 nodes/interface, 3 angles (Wood + 2), lossy layer 11, plain FP64"
+WORKLOAD = ("1000-interface trapezoidal corner grating, d = 1, 256 nodes/interface (16-node Gauss-Legendre panels, "
+            "2 dyadic levels per corner side), k alternating 10/20 +-5 %, theta = -pi/4, P = 60, M_w = 30, K = 20; "
+            "512 000 unknowns; plain FP64")
+CPU_SAMPLE_INTERFACES = 8      # the oracle's bounded sample: the first 8 interfaces of the same grating
+REFERENCE_STEP_INTERFACES = 4  # one --impl reference step: the first 4 interfaces
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # SMs x FP64 FMA/clk/SM x 2 flop x GHz (max SM clock) = 1258.6
 
 
@@ -44,15 +53,19 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (fixed launch sequence, e.g. for ncu launch skips)")
-    ap.add_argument("--config3", action="store_true",
-                    help="also time the 1000-interface corner grating (one solve per form, after a warm-up)")
-    ap.add_argument("--corner-levels", type=int, default=2)
+    ap.add_argument("--interfaces", type=int, default=1000,
+                    help="interfaces of the corner grating (the first ones of the 1000; smaller stacks are for "
+                         "profiling captures only)")
+    ap.add_argument("--leg-steps", type=int, default=5,
+                    help="timed steps of the mixed legs, e2e and the small leg (at most --steps)")
+    ap.add_argument("--no-small", action="store_true", help="skip the 20-interface leg")
     ap.add_argument("--gradient", action="store_true",
                     help="also time mlqp_fd_gradient on the 20-interface stack (one shape parameter)")
     ap.add_argument("--config5", action="store_true",
                     help="also time the design gradient of the 50-interface, 16-angle stack (a few parameters)")
     ap.add_argument("--config4", action="store_true",
-                    help="also time the 256-angle sweep of the 100-interface uneven stack, in chunks of 128 angles")
+                    help="also time the 256-angle sweep of the 100-interface uneven stack (resolved "
+                         "discretisation), in chunks of angles")
     return ap.parse_args()
 
 
@@ -80,9 +93,9 @@ def job_value(units_per_rank, world_size, steps, total_ms):
     return units_per_rank * world_size * steps / (total_ms / 1e3)
 
 
-def problem(rank=0):
-    from workloads import config2
-    prob = config2()
+def problem(rank=0, interfaces=1000):
+    from workloads import config3
+    prob = config3(I=interfaces)
     if rank:
         prob = prob.with_angles(prob.theta + 1e-3 * rank)
     return prob
@@ -165,90 +178,84 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(angles=1):
-    """The oracle, as it stands, on one angle of the same stack, single-threaded
-    BLAS, in a child process."""
+def _oracle_child(interfaces, reps, threads):
+    """Runs the oracle (as it stands: oracle.mlqp_oracle.solve) on the first
+    `interfaces` interfaces of the corner grating, `reps` times, in a child
+    process with `threads` BLAS threads; returns the per-solve seconds."""
     code = (
         "import sys, time, json; sys.path.insert(0, %r)\n"
-        "from workloads import config2\n"
+        "from workloads import config3\n"
         "from oracle import mlqp_oracle as O\n"
-        "p = config2(); asm = O.Assembler(p); t = time.perf_counter()\n"
-        "for a in range(%d): O.solve(p, a, asm)\n"
-        "dt = time.perf_counter() - t\n"
-        "print(json.dumps({'seconds': dt, 'units': p.I * %d}))\n" % (ROOT, angles, angles))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+        "p = config3(I=%d); ts = []\n"
+        "for s in range(%d):\n"
+        "    t = time.perf_counter(); O.solve(p, 0, O.Assembler(p)); ts.append(time.perf_counter() - t)\n"
+        "print(json.dumps(ts))\n" % (ROOT, interfaces, reps))
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
     if r.returncode != 0:
-        return {"error": r.stderr[-300:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["units"] / d["seconds"], "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{angles} of 3 angles of the same stack (all 20 interfaces), {d['seconds']:.1f} s"}
+        raise RuntimeError(r.stderr[-300:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline():
+    """The oracle, as it stands, on a bounded sample of the same workload: the
+    first CPU_SAMPLE_INTERFACES interfaces of the corner grating (same
+    geometry, wavenumbers, discretisation and angle), one solve with BLAS on
+    all host cores and one with a single BLAS thread."""
+    cores = os.cpu_count() or 1
+    try:
+        t_all = _oracle_child(CPU_SAMPLE_INTERFACES, 1, cores)[0]
+        t_one = _oracle_child(CPU_SAMPLE_INTERFACES, 1, 1)[0]
+    except Exception as e:  # the baseline is reported, never required
+        return {"error": str(e)[-300:]}
+    return {"value": CPU_SAMPLE_INTERFACES / t_all, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"oracle solve of the first {CPU_SAMPLE_INTERFACES} of the 1000 interfaces (same geometry, "
+                      f"wavenumbers, discretisation, angle): {t_all:.1f} s with BLAS on {cores} threads",
+            "cpu_model": cpu_model(),
+            "single_thread": {"value": CPU_SAMPLE_INTERFACES / t_one, "unit": METRIC, "cores": 1,
+                              "seconds": t_one}}
 
 
 def run_reference(args):
+    """The reference arm: the oracle (there is no reference implementation of
+    the paper) on the host cores, each step one solve of the first
+    REFERENCE_STEP_INTERFACES interfaces of the corner grating.  Under
+    torchrun only rank 0 runs it."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     K, W = args.steps, args.warmup
-    code = (
-        "import sys, time, json; sys.path.insert(0, %r)\n"
-        "from workloads import config2\n"
-        "from oracle import mlqp_oracle as O\n"
-        "p = config2(); ts = []\n"
-        "for s in range(%d):\n"
-        "    asm = O.Assembler(p); t = time.perf_counter(); O.solve(p, s %% 3, asm); ts.append(time.perf_counter() - t)\n"
-        "print(json.dumps(ts))\n" % (ROOT, K + W))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
-    if r.returncode != 0:
-        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + r.stderr[-200:]}))
+    cores = os.cpu_count() or 1
+    try:
+        ts = _oracle_child(REFERENCE_STEP_INTERFACES, K + W, cores)[W:]
+    except Exception as e:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + str(e)[-200:]}))
         return
-    ts = json.loads(r.stdout.strip().splitlines()[-1])[W:]
     total = sum(ts)
-    value = 20 * K / total
+    value = REFERENCE_STEP_INTERFACES * K / total
+    sample = (f"oracle solve of the first {REFERENCE_STEP_INTERFACES} of the 1000 interfaces per step "
+              f"(same geometry, wavenumbers, discretisation, angle)")
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus, "steps": K, "warmup": W,
             "ms_per_step": 1e3 * total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD + " (one angle per step)", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": "one angle of the stack per step, all 20 interfaces"},
+            "config": {"workload": WORKLOAD + f" (oracle: first {REFERENCE_STEP_INTERFACES} interfaces per step)",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
-
-
-def corner_grating(mlqp, dev, levels):
-    """The paper-scale corner stack (1000 trapezoidal interfaces, d = 1, graded
-    panels): one timed solve per form after a warm-up, per-stage CUDA events."""
-    import torch
-    from workloads import config3
-    out = {"workload": f"1000 trapezoidal interfaces, {levels} panel levels per corner side, one angle",
-           "unit": METRIC}
-    for name, prec, solver in (("fp64", mlqp.MLQP_FP64, mlqp.MLQP_SWEEP), ("mixed", mlqp.MLQP_MIXED, mlqp.MLQP_SWEEP),
-                               ("mixed_cyclic", mlqp.MLQP_MIXED, mlqp.MLQP_CYCLIC)):
-        prob = config3(levels=levels)
-        ctx = mlqp.Context(prob, device=dev, precision=prec, block_solver=solver)
-        st = [mlqp.STAGE_GEOM, mlqp.STAGE_FILL, mlqp.STAGE_LSQ, mlqp.STAGE_SCHUR, mlqp.STAGE_SWEEP,
-              mlqp.STAGE_RECOVER]
-        for s_ in st:
-            ctx.run_stage(s_)
-        ctx.check()
-        torch.cuda.synchronize()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(st) + 1)]
-        with torch.cuda.stream(ctx.stream):
-            for q, s_ in enumerate(st):
-                evs[q].record(ctx.stream)
-                ctx.run_stage(s_)
-            evs[-1].record(ctx.stream)
-        torch.cuda.synchronize()
-        ctx.check()
-        ms = [evs[q].elapsed_time(evs[q + 1]) for q in range(len(st))]
-        res = ctx.solve_host()
-        out[name] = {"value": prob.I / (sum(ms) / 1e3), "ms_per_solve": sum(ms),
-                     "stage_ms": dict(zip(["geometry", "fill", "lsq", "schur", "sweep", "recover"], ms)),
-                     "flux_error": float(res["flux"][0]), "unknowns": int(sum(2 * f.N for f in prob.ifaces)),
-                     "workspace_gb": ctx.ws_bytes / 1e9}
-        ctx.close()
-    return out
 
 
 def gradient_leg(mlqp, dev, reps=3):
@@ -360,9 +367,10 @@ def design_gradient(mlqp, dev, n_params=4):
             "ms_per_parameter": float(np.median(per)) if per else None, "sum_dJ": total}
 
 
-def angle_sweep(mlqp, dev, chunk=128):
+def angle_sweep(mlqp, dev, chunk=32):
     """The batched angle sweep: 256 angles of the 100-interface stack with
-    uneven node counts, solved in chunks of `chunk` angles through one
+    uneven node counts at its resolved discretisation (node counts doubled,
+    P = 100, M_w = 50, K = 40, M = 90), solved in chunks of `chunk` angles through one
     context (mlqp_set_angles; every stage a replayed graph), in FP64 and in
     the mixed form (plain and GMRES refinement), with each mixed leg's
     backward errors and amplitude deviation from the FP64 leg; beside it, the
@@ -370,9 +378,10 @@ def angle_sweep(mlqp, dev, chunk=128):
     import numpy as np
     import torch
     from workloads import config4
-    prob = config4()
+    prob = config4(resolved=True)
     th = np.asarray(prob.theta)
-    out = {"workload": "100 interfaces, N_i in {80,...,320}, 256 angles in [-pi+0.1, -0.1]", "unit": "angles/s",
+    out = {"workload": "100 interfaces, N_i in {160,...,512} (the drawn {80,...,320} doubled, at most 512), "
+                       "P = 100, M_w = 50, K = 40, M = 90, 256 angles in [-pi+0.1, -0.1]", "unit": "angles/s",
            "chunk": chunk}
     def checked(ctx, prec, omegas):
         """Status check; in the mixed form an unreached refine_tol is recorded
@@ -386,7 +395,7 @@ def angle_sweep(mlqp, dev, chunk=128):
             omegas += [float(ctx.block(mlqp.BLK_REFINE, 1, a)[0]) for a in range(ctx.n_theta)]
 
     legs = (("fp64", mlqp.MLQP_FP64, {}),
-            ("mixed", mlqp.MLQP_MIXED, dict(max_refine=20)),
+            ("mixed", mlqp.MLQP_MIXED, dict(max_refine=10)),  # default refinement: plain, GMRES once it stalls
             ("mixed_gmres", mlqp.MLQP_MIXED, dict(max_refine=4, refine_method=mlqp.MLQP_GMRES_IR)))
     amps = {}
     for name, prec, kw in legs:
@@ -396,15 +405,19 @@ def angle_sweep(mlqp, dev, chunk=128):
         ctx.solve_device(res)
         checked(ctx, prec, None)
         torch.cuda.synchronize()
-        omegas, amps[name] = [], []
+        omegas, amps[name], fluxes = [], [], []
         t0 = time.perf_counter()
         for c0 in range(0, len(th), chunk):
             ctx.set_angles(th[c0:c0 + chunk])
             ctx.solve_device(res)
             checked(ctx, prec, omegas)
             amps[name].append(torch.cat([res["aU"], res["aD"]], 1).cpu())
+            fluxes.append(res["flux"].abs().cpu())
         el = time.perf_counter() - t0
-        out[name] = {"seconds": el, "value": len(th) / el, "workspace_gb": ctx.ws_bytes / 1e9,
+        fl = torch.cat(fluxes)
+        out[name] = {"seconds": el, "value": len(th) / el, "layer_angle_solves_per_s": prob.I * len(th) / el,
+                     "flux_error_max": float(fl.max()), "angles_flux_above_1e-9": int((fl > 1e-9).sum()),
+                     "workspace_gb": ctx.ws_bytes / 1e9,
                      "launch_shapes": {"qr_cluster": int(tuned["qr_cluster"]), "source": "mlqp_autotune"}}
         if omegas:
             out[name]["backward_error_max"] = max(omegas)
@@ -436,12 +449,86 @@ def angle_sweep(mlqp, dev, chunk=128):
 
 
 # DRAM bytes (read + write) of the sweep kernels (k_lu_panel_cl, k_lu_prep,
-# k_lu_update, k_back_*) in one step of the 20-interface 3-angle grating, from
-# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over the
-# step's sweep launches, L2 warm between launches as in the bench), with the
-# launch shapes SWEEP_TRAFFIC_SHAPES.
-SWEEP_TRAFFIC_BYTES = 484.9e6
-SWEEP_TRAFFIC_SHAPES = {"qr_cluster": 8, "angle_groups": 3, "update_tile": 16}
+# k_lu_update, k_back_*) per interface of the corner grating, from one ncu
+# capture of a shorter stack of the same interfaces (traffic grows in
+# proportion to the interfaces: every interface's sweep step touches the same
+# sizes); None until captured for the current kernels.
+SWEEP_TRAFFIC_BYTES_PER_INTERFACE = None
+SWEEP_TRAFFIC_NOTE = "null: no ncu capture of the current sweep kernels on this workload"
+
+
+def timed_solves(mlqp, ctx, steps, flush, stages):
+    """`steps` solves of a bound context, each after an L2 flush (outside the
+    events), with CUDA events on the library's stream around every stage.
+    Returns (ms per step list, ms per stage summed over steps, launches)."""
+    import torch
+    stream = ctx.stream
+    launches0 = ctx.launch_count()
+    all_evs = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            flush.fill_(1)
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
+            for q, s_ in enumerate(stages):
+                evs[q].record(stream)
+                ctx.run_stage(s_)
+            evs[-1].record(stream)
+            all_evs.append(evs)
+    torch.cuda.synchronize()
+    launches = ctx.launch_count() - launches0
+    per_step, per_stage = [], [0.0] * len(stages)
+    for evs in all_evs:
+        per_step.append(evs[0].elapsed_time(evs[-1]))
+        for q in range(len(stages)):
+            per_stage[q] += evs[q].elapsed_time(evs[q + 1])
+    return per_step, per_stage, launches
+
+
+def refine_info(mlqp, ctx):
+    nth = ctx.n_theta
+    r = [ctx.block(mlqp.BLK_REFINE, 1, a).cpu().numpy() for a in range(nth)]
+    return {"refine_steps": [int(x[1]) for x in r], "backward_error": float(max(x[0] for x in r))}
+
+
+def rel_amp_diff(out, ref):
+    import torch
+    a = torch.cat([out["aU"], out["aD"]], 1)
+    b = torch.cat([ref["aU"], ref["aD"]], 1)
+    return float(torch.max((a - b).abs().amax(1) / b.abs().amax(1)))
+
+
+def small_leg(mlqp, dev, steps, warmup, flush, stages, autotune):
+    """The 20-interface random grating (120 nodes per interface, 3 angles one
+    of them 1e-8 past a Wood anomaly, a lossy layer): FP64 and the mixed form
+    with cyclic reduction, device-timed like the headline."""
+    import torch
+    from workloads import config2
+    prob = config2()
+    out = {"workload": "20-interface random grating, 120 nodes/interface, 3 angles (Wood + 2), lossy layer 11",
+           "unit": METRIC, "steps": steps, "flux_error": "undefined (lossy layer; Remark r:flux)"}
+    ref = None
+    for name, prec, solver in (("fp64", mlqp.MLQP_FP64, mlqp.MLQP_SWEEP),
+                               ("mixed_cyclic", mlqp.MLQP_MIXED, mlqp.MLQP_CYCLIC)):
+        ctx = mlqp.Context(prob, device=dev, precision=prec, block_solver=solver)
+        if autotune:
+            ctx.autotune()
+        res = ctx.outputs()
+        for _ in range(warmup):
+            ctx.solve_device(res)
+        ctx.check()
+        per_step, _, _ = timed_solves(mlqp, ctx, steps, flush, stages)
+        ctx.solve_device(res)
+        ctx.check()
+        torch.cuda.synchronize()
+        ms = sum(per_step) / steps
+        out[name] = {"value": prob.I * prob.n_theta / (ms / 1e3), "ms_per_step": ms}
+        if ref is None:
+            ref = {k: v.clone() for k, v in res.items()}
+        else:
+            out[name].update(refine_info(mlqp, ctx))
+            out[name]["max_rel_amp_diff_vs_fp64"] = rel_amp_diff(res, ref)
+        ctx.close()
+    return out
 
 
 def main():
@@ -464,136 +551,106 @@ def main():
     from paper_1410_5003_gb300 import mlqp
     mlqp.load()
 
-    prob = problem(rank)
-    ctx = mlqp.Context(prob, device=dev)
-    # launch shapes timed on this problem (untimed setup)
-    tuned = ctx.autotune() if not args.no_autotune else {"qr_cluster": 8, "angle_groups": min(4, prob.n_theta),
-                                                         "update_tile": 16}
-    stream = ctx.stream
-    out = ctx.outputs()
+    prob = problem(rank, args.interfaces)
+    K, W = args.steps, args.warmup
+    K_leg = min(K, args.leg_steps)
+    stages = [mlqp.STAGE_GEOM, mlqp.STAGE_FILL, mlqp.STAGE_LSQ, mlqp.STAGE_SCHUR, mlqp.STAGE_SWEEP,
+              mlqp.STAGE_RECOVER]
+    names = ["geometry", "fill", "lsq", "schur", "sweep", "recover"]
     n = [2 * f.N for f in prob.ifaces]
     nth = prob.n_theta
     units = prob.I * nth
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    stages = [mlqp.STAGE_GEOM, mlqp.STAGE_FILL, mlqp.STAGE_LSQ, mlqp.STAGE_SCHUR, mlqp.STAGE_SWEEP,
-              mlqp.STAGE_RECOVER]
 
-    def step(evs=None):
-        for q, s in enumerate(stages):
-            if evs is not None:
-                evs[q].record(stream)
-            ctx.run_stage(s)
-        if evs is not None:
-            evs[len(stages)].record(stream)
-
-    for _ in range(args.warmup):
+    ctx = mlqp.Context(prob, device=dev)
+    # launch shapes timed on this problem (untimed setup)
+    tuned = ctx.autotune() if not args.no_autotune else {"qr_cluster": 8, "angle_groups": 1, "update_tile": 16}
+    out = ctx.outputs()
+    for _ in range(W):
         ctx.solve_device(out)
     ctx.check()
-    launches0 = ctx.launch_count()
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk = Clocks(local)
-    per_step, per_stage = [], [0.0] * len(stages)
-    all_evs = []
-    with torch.cuda.stream(stream):
-        for _ in range(args.steps):
-            flush.fill_(1)  # evicts the 129 MB L2 between steps (outside the events)
-            evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
-            step(evs)
-            all_evs.append(evs)
-    torch.cuda.synchronize()
+    per_step, per_stage, launches = timed_solves(mlqp, ctx, K, flush, stages)
     if ws > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
-    launches = ctx.launch_count() - launches0
-    for evs in all_evs:
-        per_step.append(evs[0].elapsed_time(evs[-1]))
-        for q in range(len(stages)):
-            per_stage[q] += evs[q].elapsed_time(evs[q + 1])
     total_ms = max_over_ranks(sum(per_step), dev)
-    K = args.steps
     value = job_value(units, ws, K, total_ms)
     ctx.check()
-
-    # correctness of the timed outputs: finite amplitudes
+    # the outputs of the timed solves (the last one): finite, flux error
     ctx.solve_device(out)
     ctx.check()
+    torch.cuda.synchronize()
     ok = bool(torch.isfinite(out["aU"].real).all() and torch.isfinite(out["aD"].real).all())
+    flux = float(out["flux"].abs().max())
 
     line = None
     if rank == 0:
-        names = ["geometry", "fill", "lsq", "schur", "sweep", "recover"]
         stage_ms = {nm: per_stage[q] / K for q, nm in enumerate(names)}
         # dominant kernel group: the block-tridiagonal sweep (FP64 pipe)
         sw_flops = nth * sweep_flops(n)
-        sw_s = stage_ms["sweep"] / 1e3
-        achieved = sw_flops / sw_s / 1e12
-        dominant = max(stage_ms, key=stage_ms.get)
-        shapes_as_captured = all(int(tuned.get(k, -1)) == v for k, v in SWEEP_TRAFFIC_SHAPES.items())
+        achieved = sw_flops / (stage_ms["sweep"] / 1e3) / 1e12
+        peak = FP64_PEAK_GFLOPS / 1e3
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K,
-                "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+                "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "interfaces": prob.I, "angles": nth, "nodes_per_interface": 120,
-                           "unknowns_per_angle": int(sum(n)), "l2": "flushed between steps (256 MB write)",
+                "config": {"workload": WORKLOAD if prob.I == 1000 else WORKLOAD + f" (first {prob.I} interfaces)",
+                           "interfaces": prob.I, "angles": nth,
+                           "nodes_per_interface": int(prob.ifaces[0].N), "unknowns_per_angle": int(sum(n)),
+                           "l2": "flushed between steps (256 MB write); the working set (about 25 GB of blocks) "
+                                 "is far larger than L2",
                            "launch_shapes": {"qr_cluster": int(tuned["qr_cluster"]),
                                              "angle_groups": int(tuned["angle_groups"]),
-                                             "update_tile": int(tuned.get("update_tile", 32)),
+                                             "update_tile": int(tuned.get("update_tile", 16)),
                                              "source": "defaults" if args.no_autotune else "mlqp_autotune"}},
-                "stage_ms": stage_ms, "dominant_stage": dominant,
-                "roofline": {"bound": "alu", "kernel": "block-tridiagonal sweep (k_lu_panel/k_lu_prep/k_lu_update)",
-                             "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                             "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
-                             "traffic": SWEEP_TRAFFIC_BYTES if shapes_as_captured else None,
-                             "traffic_note": ("DRAM bytes read + written by the sweep kernels per step (3 angles), "
-                                              "one ncu capture of this workload with the same launch shapes"
-                                              if shapes_as_captured else
-                                              "null: the tuned launch shapes differ from the ncu capture's"),
+                "flux_error": flux, "meets_flux_gate_1e-9": flux <= 1e-9,
+                "stage_ms": stage_ms, "dominant_stage": max(stage_ms, key=stage_ms.get),
+                "roofline": {"bound": "alu", "kernel": "block-tridiagonal sweep (k_lu_panel_cl, k_lu_prep, "
+                                                      "k_lu_update, k_back_*), one stage of the step",
+                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                             "traffic": SWEEP_TRAFFIC_BYTES_PER_INTERFACE * prob.I * nth
+                             if SWEEP_TRAFFIC_BYTES_PER_INTERFACE else None,
+                             "traffic_note": SWEEP_TRAFFIC_NOTE,
                              "algorithmic_flops_per_step": sw_flops,
-                             "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived; 1.20 measured at 1995 MHz)"},
+                             "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived from the "
+                                          "unit counts and the maximum SM clock; MEASURED_PEAKS.json has no FP64 "
+                                          "figure; a probe measured 1.20 TFLOP/s at 1995 MHz)"},
                 "gpu_launches": launches, "outputs_finite": ok,
                 "schur_tflops": nth * schur_flops(n, prob.params.P) / (stage_ms["schur"] / 1e3) / 1e12}
         if clocks:
             line["clocks"] = clocks
-    # the mixed-precision form on the same stack: FP32 Schur / block LU (sweep, then
-    # block cyclic reduction), FP64 refinement
+
+    # the mixed-precision form on the same stack: FP32 Schur / block LU (sweep,
+    # then block cyclic reduction), FP64 refinement against the FP64 operator
     def time_mixed(solver):
         mctx = mlqp.Context(prob, device=dev, precision=mlqp.MLQP_MIXED, max_refine=10, refine_tol=1e-15,
                             block_solver=solver)
         mtuned = mctx.autotune() if not args.no_autotune else {}
         mout = mctx.outputs()
-        for _ in range(args.warmup):
+        for _ in range(W):
             mctx.solve_device(mout)
         mctx.check()
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        mtimes = []
-        with torch.cuda.stream(mctx.stream):
-            for _ in range(K):
-                flush.fill_(1)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(mctx.stream)
-                for s_ in stages:
-                    mctx.run_stage(s_)
-                e1.record(mctx.stream)
-                mtimes.append((e0, e1))
-        torch.cuda.synchronize()
-        mms = max_over_ranks(sum(a.elapsed_time(b) for a, b in mtimes), dev)
+        mper, mstage, mlaunch = timed_solves(mlqp, mctx, K_leg, flush, stages)
+        mms = max_over_ranks(sum(mper), dev)
         mctx.solve_device(mout)
         mctx.check()
-        ref = torch.cat([out["aU"], out["aD"]], 1)
-        diff = float(torch.max(torch.abs(torch.cat([mout["aU"], mout["aD"]], 1) - ref)) / torch.max(torch.abs(ref)))
-        res = {"value": units * ws * K / (mms / 1e3), "unit": METRIC, "ms_per_step": mms / K,
-               "speedup_vs_fp64": (total_ms / K) / (mms / K),
-               "refine_steps": [int(mctx.block(mlqp.BLK_REFINE, 1, a)[1]) for a in range(nth)],
-               "backward_error": max(float(mctx.block(mlqp.BLK_REFINE, 1, a)[0]) for a in range(nth)),
-               "max_rel_amp_diff_vs_fp64": diff,
+        torch.cuda.synchronize()
+        res = {"value": job_value(units, ws, K_leg, mms), "unit": METRIC, "steps": K_leg,
+               "ms_per_step": mms / K_leg, "speedup_vs_fp64": (total_ms / K) / (mms / K_leg),
+               "stage_ms": {nm: mstage[q] / K_leg for q, nm in enumerate(names)},
+               "flux_error": float(mout["flux"].abs().max()),
+               "max_rel_amp_diff_vs_fp64": rel_amp_diff(mout, out), "gpu_launches": mlaunch,
                "block_solver": "sweep" if solver == mlqp.MLQP_SWEEP else "cyclic reduction",
                "launch_shapes": {k: (None if v != v else int(v)) for k, v in mtuned.items()
                                  if k in ("qr_cluster", "angle_groups", "cr_cluster_cap", "update_tile")},
                "dtype": "f32 Schur/LU + f64 refinement (fill, least squares, residuals in f64)"}
+        res.update(refine_info(mlqp, mctx))
         mctx.close()
         return res
 
@@ -602,25 +659,35 @@ def main():
             res = time_mixed(solver)
             if rank == 0:
                 line[key] = res
-    # e2e through the C ABI with host buffers: bind (H2D of the problem) + solve (D2H of amplitudes)
+    # e2e through the C ABI with host buffers: bind (H2D of the problem) + solve
+    # (D2H of amplitudes and flux), wall clock, each step after an L2 flush
     if not args.no_e2e:
         hout = ctx.host_outputs(eta=False, pinned=True)
-        for _ in range(2):
-            ctx.bind()
-            ctx.solve_host(out=hout)
+        ctx.bind()
+        ctx.solve_host(out=hout)
         if ws > 1:
             torch.distributed.barrier()
-        t0 = time.perf_counter()
-        for _ in range(K):
+        el = 0.0
+        for _ in range(K_leg):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             ctx.bind()
             ctx.solve_host(out=hout)
-        el = max_over_ranks((time.perf_counter() - t0) * 1e3, dev)
+            el += time.perf_counter() - t0
+        el = max_over_ranks(el * 1e3, dev)
         if rank == 0:
             d2h = sum(v.numel() * v.element_size() for v in hout.values() if v is not None) + 4
-            line["e2e"] = {"value": job_value(units, ws, K, el), "unit": METRIC, "h2d_bytes_per_step": ctx.upload_bytes(),
-                           "d2h_bytes_per_step": d2h}
-    if args.config3 and rank == 0:
-        line["config3"] = corner_grating(mlqp, dev, args.corner_levels)
+            line["e2e"] = {"value": job_value(units, ws, K_leg, el), "unit": METRIC, "steps": K_leg,
+                           "h2d_bytes_per_step": ctx.upload_bytes(), "d2h_bytes_per_step": d2h,
+                           "how": "wall clock of mlqp_bind (problem upload from pinned memory) + mlqp_solve "
+                                  "(one replayed graph of every stage, amplitudes copied to pinned host "
+                                  "buffers) per step, L2 flushed before each step as in the device-timed loop"}
+    ctx.close()
+    del ctx, out
+    torch.cuda.empty_cache()
+    if not args.no_small and rank == 0:
+        line["config2"] = small_leg(mlqp, dev, K_leg, W, flush, stages, not args.no_autotune)
     if args.config4 and rank == 0:
         line["config4"] = angle_sweep(mlqp, dev)
     if args.gradient and rank == 0:
@@ -629,9 +696,8 @@ def main():
         line["config5"] = design_gradient(mlqp, dev)
     if rank == 0:
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(1)
+            line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
-    ctx.close()
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()

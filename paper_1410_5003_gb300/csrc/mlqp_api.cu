@@ -89,7 +89,7 @@ struct mlqp_ctx {
   // launch shapes (mlqp_autotune): QR cluster size, cyclic-reduction LU
   // cluster cap, angle groups of the sweep (0: min(n_theta, MAX_ANGLE_STREAMS)),
   // tile edge of the block LU's trailing update
-  int qr_cl = 8, cr_cl_max = 8, angle_groups = 0, upd_tile = 16;
+  int qr_cl = 8, cr_cl_max = 8, angle_groups = 0, upd_tile = 16, lookahead = 0;
   // the mixed block solve: one graph per piece (launch_mixed_piece), replayed by
   // a host loop that reads the active-angle counts into hflag (pinned)
   cudaGraphExec_t pexec[MP_COUNT] = {};
@@ -235,10 +235,10 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   if (q.precision == MLQP_MIXED && (q.max_refine < 1 || q.max_refine > 50 || !(q.refine_tol > 0)))
     return bad("MLQP_MIXED needs 1 <= max_refine <= 50 and refine_tol > 0");
   if (q.block_solver != MLQP_SWEEP && q.block_solver != MLQP_CYCLIC) return bad("block_solver must be MLQP_SWEEP or MLQP_CYCLIC");
-  if (q.refine_method != MLQP_IR && q.refine_method != MLQP_GMRES_IR)
-    return bad("refine_method must be MLQP_IR or MLQP_GMRES_IR");
-  if (q.refine_method == MLQP_GMRES_IR && q.precision != MLQP_MIXED)
-    return bad("MLQP_GMRES_IR is a refinement of the MLQP_MIXED form");
+  if (q.refine_method != MLQP_IR && q.refine_method != MLQP_GMRES_IR && q.refine_method != MLQP_IR_GMRES)
+    return bad("refine_method must be MLQP_IR, MLQP_GMRES_IR or MLQP_IR_GMRES");
+  if (q.refine_method != MLQP_IR && q.precision != MLQP_MIXED)
+    return bad("MLQP_GMRES_IR and MLQP_IR_GMRES are refinements of the MLQP_MIXED form");
   if (q.block_solver == MLQP_CYCLIC) {
     if (q.precision != MLQP_MIXED) return bad("MLQP_CYCLIC is the block solver of the MLQP_MIXED form");
     for (int i = 1; i < I; ++i)
@@ -481,7 +481,7 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
     take(cur, c->r_RNRM, d8 * nt * RNRM_W);
     if (q.block_solver == MLQP_CYCLIC)
       take(cur, c->r_CRSAVE, sizeof(float2) * nt * (size_t)cr_slots(I) * 2 * c->maxn * c->maxn);
-    if (q.refine_method == MLQP_GMRES_IR) {
+    if (q.refine_method != MLQP_IR) {
       take(cur, c->r_GV, z16 * nt * (GM_M + 1) * c->n_den);
       take(cur, c->r_GZ, z16 * nt * GM_M * c->n_den);
       take(cur, c->r_GW, z16 * nt * c->n_den);
@@ -536,6 +536,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   D.qr_cl = c->qr_cl;
   D.cr_cl_max = c->cr_cl_max;
   D.upd_tile = c->upd_tile;
+  D.lookahead = c->lookahead;
   D.yU = q.gap_U;  // the geometry kernel turns the gaps into y_U, y_D (stored in scal)
   D.yD = q.gap_D;
   D.maxN = c->maxN;
@@ -602,7 +603,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
       D.CRSAVE = at<float2>(c, c->r_CRSAVE);
       D.crsave_stride = (size_t)cr_slots(c->I) * 2 * c->maxn * c->maxn;
     }
-    if (q.refine_method == MLQP_GMRES_IR) {
+    if (q.refine_method != MLQP_IR) {
       D.GV = at<double2>(c, c->r_GV);
       D.GZ = at<double2>(c, c->r_GZ);
       D.GW = at<double2>(c, c->r_GW);
@@ -810,13 +811,21 @@ static mlqp_status run_mixed_sweep(mlqp_ctx* c) {
     *out = c->hflag[which];
     return MLQP_OK;
   };
-  const bool gm = c->prm.refine_method == MLQP_GMRES_IR;
+  // MLQP_IR_GMRES: plain corrections until one of them leaves some angle's
+  // omega above REFINE_STALL of its previous value, GMRES corrections after
+  bool gm = c->prm.refine_method == MLQP_GMRES_IR;
+  const bool may_switch = c->prm.refine_method == MLQP_IR_GMRES;
   mlqp_status st = piece(MP_FACTOR);
   for (int it = 0; it <= c->prm.max_refine && st == MLQP_OK; ++it) {
     const bool last = (it == c->prm.max_refine);
     int active = 0;
     if ((st = piece(last ? MP_RESID_LAST : MP_RESID)) != MLQP_OK || (st = count(0, &active)) != MLQP_OK) break;
     if (last || active == 0) break;
+    if (may_switch && !gm) {
+      int stalled = 0;
+      if ((st = count(2, &stalled)) != MLQP_OK) break;
+      gm = stalled > 0;
+    }
     if (!gm) {
       st = piece(MP_IR);
       continue;
@@ -882,6 +891,38 @@ static mlqp_status apply_shapes(mlqp_ctx* c) {
   return mlqp_bind(c, c->ws, c->ws_bytes, c->stream);
 }
 
+mlqp_status mlqp_set_shape(mlqp_ctx* c, int which, int value) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  const bool p2 = value == 1 || value == 2 || value == 4 || value == 8;
+  switch (which) {
+    case MLQP_TUNE_QR:
+      if (!p2) return fail(c, MLQP_EINVAL, "QR cluster size must be 1, 2, 4 or 8");
+      c->qr_cl = value;
+      break;
+    case MLQP_TUNE_TILE:
+      if (value != 16 && value != 32) return fail(c, MLQP_EINVAL, "update tile must be 16 or 32");
+      c->upd_tile = value;
+      break;
+    case MLQP_TUNE_GROUPS:
+      if (value < 1 || value > std::min(c->n_theta, MAX_ANGLE_STREAMS))
+        return fail(c, MLQP_EINVAL, "angle groups must be 1..min(n_theta, %d)", MAX_ANGLE_STREAMS);
+      c->angle_groups = value;
+      break;
+    case MLQP_TUNE_CR:
+      if (!p2) return fail(c, MLQP_EINVAL, "cyclic-reduction cluster cap must be 1, 2, 4 or 8");
+      c->cr_cl_max = value;
+      break;
+    case MLQP_TUNE_LOOKAHEAD:
+      if (value != 0 && value != 1) return fail(c, MLQP_EINVAL, "look-ahead must be 0 or 1");
+      c->lookahead = value;
+      break;
+    default:
+      return fail(c, MLQP_EINVAL, "unknown launch shape %d", which);
+  }
+  return apply_shapes(c);
+}
+
 mlqp_status mlqp_autotune(mlqp_ctx* c, int which, double* report, int report_len) {
   if (!c) return MLQP_EINVAL;
   if (which == 0) which = MLQP_TUNE_ALL;
@@ -940,7 +981,23 @@ mlqp_status mlqp_autotune(mlqp_ctx* c, int which, double* report, int report_len
     c->angle_groups = best;
     rep[5] = best;
   }
-  // 4. cluster cap of the cyclic-reduction LU
+  // 4. look-ahead of the block LU (the sweep's, or the FP32 factorisation's)
+  if (st == MLQP_OK && (which & MLQP_TUNE_LOOKAHEAD) &&
+      !(c->prm.precision == MLQP_MIXED && c->prm.block_solver == MLQP_CYCLIC)) {
+    int best = c->lookahead;
+    double tb = INFINITY;
+    for (int q = 0; q < 2 && st == MLQP_OK; ++q) {
+      c->lookahead = q;
+      double t = 0;
+      if ((st = apply_shapes(c)) == MLQP_OK && (st = time_stage(c, MLQP_STAGE_SWEEP, 3, &t)) == MLQP_OK) {
+        rep[19 + q] = t;
+        if (t < tb) tb = t, best = q;
+      }
+    }
+    c->lookahead = best;
+    rep[18] = best;
+  }
+  // 5. cluster cap of the cyclic-reduction LU
   if (st == MLQP_OK && (which & MLQP_TUNE_CR) && c->prm.block_solver == MLQP_CYCLIC) {
     const int cand[4] = {1, 2, 4, 8};
     int best = c->cr_cl_max;
@@ -1251,7 +1308,7 @@ mlqp_status mlqp_block_info(const mlqp_ctx* c, int kind, int index, int angle, s
   const size_t a = angle;
   if (kind == MLQP_BLK_REFINE) {
     if (c->prm.precision != MLQP_MIXED) return MLQP_EINVAL;
-    if (index != 1 && !(index == 2 && c->prm.refine_method == MLQP_GMRES_IR)) return MLQP_EINVAL;
+    if (index != 1 && !(index == 2 && c->prm.refine_method != MLQP_IR)) return MLQP_EINVAL;
     *offset_bytes = c->r_RNRM.off + sizeof(double) * (RNRM_W * a + (index == 2 ? 5 : 0));
     *rows = 2; *cols = 1; *ld = 2;
     return MLQP_OK;

@@ -71,6 +71,8 @@ struct AngleStreams {
 constexpr int RNRM_W = 8;  // doubles per angle of the refinement control block
 constexpr int PANEL_P = 16;  // Gauss-Legendre nodes per corner panel
 constexpr int NEAR_MAX = 12; // near-panel slots per node of a corner interface
+constexpr double REFINE_STALL = 0.25;  // MLQP_IR_GMRES: a plain correction that leaves omega above
+                                       // this fraction of its previous value counts as stalled
 constexpr int GM_M = 40;     // GMRES steps per refinement step
 constexpr int GM_NB = 64;    // CTAs of the batched reductions (per angle)
 constexpr int GM_HW = 4096;  // doubles of per-angle GMRES data
@@ -155,6 +157,7 @@ struct Dev {
   int qr_cl;      // CTAs per least-squares QR cluster (1..8)
   int cr_cl_max;  // largest cluster of the cyclic-reduction LU (1..8)
   int upd_tile;   // tile edge of the block LU's trailing update (16 or 32)
+  int lookahead;  // 1: the next panel factored beside the rest of each trailing update
 };
 
 // Per-angle vectors of the gradient, carved from the caller's work buffer.

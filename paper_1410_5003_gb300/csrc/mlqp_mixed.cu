@@ -130,7 +130,8 @@ __global__ void k_compose_perm(Dev D, int* permv) {
 //           s_r = |f_r| + sum_c |A_rc| |eta_c| + sum_c |B_rc| (|X| |eta|)_c
 //       (|z| taken as |re| + |im| throughout);
 //   [1] corrections applied;  [2], [3] max |r|, max s (bit patterns of
-//   non-negative doubles, so an unsigned atomic max orders them);  [4] done.
+//   non-negative doubles, so an unsigned atomic max orders them);  [4] done;
+//   [5], [6] GMRES steps and last inner residual;  [7] the previous omega.
 // An angle whose omega reaches tol is done: every later kernel of the
 // refinement returns at once for it, so the launch sequence is fixed and
 // the work is not.
@@ -219,7 +220,12 @@ __global__ void __launch_bounds__(256) k_resid(Dev D, const double2* vin, double
 
 // omega of the residual just formed; marks converged angles done; on the
 // final check an angle above tol sets MLQP_ENOTCONV.  One thread per angle.
+// One warp.  Besides the convergence test it counts, into STATUS[3], the
+// angles whose omega fell by less than REFINE_STALL over the last correction
+// (slot [7] keeps the previous omega): MLQP_IR_GMRES switches to GMRES
+// corrections when that count is not zero.
 __global__ void k_refine_ctl(Dev D, int last, double tol) {
+  int stalled = 0;
   for (int a = threadIdx.x; a < D.n_theta; a += blockDim.x) {
     unsigned long long* c = ctl(D, a);
     double* cd = D.RNRM + (size_t)a * RNRM_W;
@@ -227,13 +233,18 @@ __global__ void k_refine_ctl(Dev D, int last, double tol) {
       const double rmax = __longlong_as_double((long long)c[2]);
       const double smax = __longlong_as_double((long long)c[3]);
       const double w = (smax > 0.0) ? rmax / smax : (rmax > 0.0 ? CUDART_INF : 0.0);
+      const double prev = cd[7];
       cd[0] = w;
+      cd[7] = w;
       if (w <= tol) c[4] = 1ull;
+      else if (cd[1] >= 1.0 && prev > 0.0 && !(w <= REFINE_STALL * prev)) ++stalled;
     }
     c[2] = 0ull;
     c[3] = 0ull;
     if (last && !(cd[0] <= tol)) atomicExch(D.STATUS, MLQP_ENOTCONV_CODE);
   }
+  for (int o = 16; o > 0; o >>= 1) stalled += __shfl_xor_sync(0xffffffffu, stalled, o);
+  if (threadIdx.x == 0) D.STATUS[3] = stalled;
 }
 
 // ---------------------------------------------------------------------------

@@ -17,9 +17,11 @@
 // cluster of PCL CTAs per angle, panel rows split over their shared memory),
 // the row swaps / U12 rows / bottom multipliers (column- and row-parallel),
 // and the trailing update (16 x 16 or 32 x 32 tiles, complex 3M products).
-// With look-ahead (compiled out, see LOOKAHEAD), the update first finishes
-// the next panel's columns, and that panel is factored on a second stream
-// while the rest of the update runs.
+// With look-ahead (a launch shape, D.lookahead, chosen by mlqp_autotune), the
+// update first finishes the next panel's columns, and that panel is factored
+// on a second stream while the rest of the update runs; the panel CTAs then
+// reserve nearly all of their SMs' shared memory, so that no update CTA shares
+// an SM (and its FP64 pipes) with the latency-bound panel.
 // Angle groups run on streams of their own.  The kernels are templates on the
 // real type: FP64 for the plain path, FP32 for the factorisation of the
 // mixed-precision path (whose solves are refined in FP64, mlqp_mixed.cu).
@@ -35,10 +37,6 @@ namespace mlqp {
 extern thread_local long g_launches;
 
 constexpr int NB = 16;        // panel width
-// Look-ahead (panel k+1 factored on a second stream beside the rest of update
-// k) is off: measured on GB300, the latency-bound panel slows down more from
-// sharing the SMs' FP64 pipes with the update than the overlap saves.
-constexpr bool LOOKAHEAD = false;
 constexpr int MLQP_ESINGULAR_CODE = 4;
 
 struct Step {
@@ -123,6 +121,7 @@ constexpr int PCL_THREADS = 128;
 constexpr int PCL_SLOTS = 4;  // rows per lane: RC <= 32 PCL_SLOTS, so n_i <= 1024
 constexpr int PCL_WARPS = PCL_THREADS / 32;
 constexpr size_t PANEL_SMEM_MIN = 116 * 1024;  // more than half of an SM's shared memory
+constexpr size_t PANEL_SMEM_RESERVE = 216 * 1024;  // look-ahead: leaves less than an update CTA's 12 KB
 
 template <typename R>
 __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
@@ -649,7 +648,8 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
       // FP64 pipes.  FP32 (the mixed form's factorisation) is not FP64-bound:
       // its panels may share SMs, which lets large angle batches run in one wave.
       const size_t smem = std::max(rc * (w + 1) * sizeof(vec2<R>) + rc * sizeof(unsigned),
-                                   sizeof(R) == 8 ? PANEL_SMEM_MIN : size_t(0));
+                                   D.lookahead ? PANEL_SMEM_RESERVE
+                                               : (sizeof(R) == 8 ? PANEL_SMEM_MIN : size_t(0)));
       ++g_launches;
       k_lu_panel_cl<R><<<dim3(PCL, na), PCL_THREADS, smem, st>>>(D, t, k, a0);
     };
@@ -666,7 +666,7 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
       const int UT = (D.upd_tile == 16) ? 16 : 32;
       const int tiles = ((nrows + UT - 1) / UT) * ((ncols + UT - 1) / UT);
       const int k2 = k + w;
-      if (LOOKAHEAD && k2 < nt) {
+      if (D.lookahead && k2 < nt) {
         // look-ahead: the next panel's columns first, then its factorisation on
         // the panel stream beside the rest of this update
         const int wn = (nt - k2 < NB) ? nt - k2 : NB;
@@ -744,7 +744,7 @@ cudaError_t launch_recover(const Dev& D, cudaStream_t s) {
 
 size_t sweep_panel_smem_max(int maxn) {
   const size_t rc = (size_t)((maxn + PCL - 1) / PCL);
-  return std::max(rc * (NB + 1) * sizeof(double2) + rc * sizeof(unsigned), PANEL_SMEM_MIN);
+  return std::max(rc * (NB + 1) * sizeof(double2) + rc * sizeof(unsigned), PANEL_SMEM_RESERVE);
 }
 
 cudaError_t sweep_configure(int maxn) {

@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmlqp.so")
 MLQP_OK, MLQP_EINVAL, MLQP_ENOMEM, MLQP_ECUDA, MLQP_ESINGULAR, MLQP_ETIMEOUT, MLQP_ENOTCONV, MLQP_ESTATE = range(8)
 MLQP_FP64, MLQP_MIXED = 0, 1
 MLQP_SWEEP, MLQP_CYCLIC = 0, 1
-MLQP_IR, MLQP_GMRES_IR = 0, 1
-TUNE_QR, TUNE_TILE, TUNE_GROUPS, TUNE_CR, TUNE_ALL = 1, 2, 4, 8, 15
+MLQP_IR, MLQP_GMRES_IR, MLQP_IR_GMRES = 0, 1, 2
+TUNE_QR, TUNE_TILE, TUNE_GROUPS, TUNE_CR, TUNE_LOOKAHEAD, TUNE_ALL = 1, 2, 4, 8, 16, 31
 STAGE_GEOM, STAGE_FILL, STAGE_LSQ, STAGE_SCHUR, STAGE_SWEEP, STAGE_RECOVER = range(6)
 BLK_ROW, BLK_B, BLK_QP, BLK_CP, BLK_X, BLK_RHS, BLK_NODES, BLK_ETA, BLK_AMP, BLK_REFINE = range(10)
 
@@ -73,6 +73,8 @@ def load(path: str = LIB_PATH):
     lib.mlqp_set_problem.restype = I
     lib.mlqp_autotune.argtypes = [P, I, ct.POINTER(D), I]
     lib.mlqp_autotune.restype = I
+    lib.mlqp_set_shape.argtypes = [P, I, I]
+    lib.mlqp_set_shape.restype = I
     lib.mlqp_solve_device.argtypes = [P, V, V, V, V]
     lib.mlqp_solve_device.restype = I
     lib.mlqp_solve_rhs.argtypes = [P, V, V]
@@ -116,7 +118,7 @@ def load(path: str = LIB_PATH):
 
 
 EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "mlqp_set_angles", "mlqp_set_problem",
-            "mlqp_autotune",
+            "mlqp_autotune", "mlqp_set_shape",
             "mlqp_solve_rhs", "mlqp_adjoint_solve", "mlqp_lsq_adjoint", "mlqp_x_elements",
             "mlqp_gradient_work_bytes", "mlqp_fd_gradient", "mlqp_gradient_prepare", "mlqp_gradient_eval",
             "mlqp_solve_device",
@@ -192,7 +194,7 @@ class Context:
     """One problem on one device: owns the host context and a torch workspace."""
 
     def __init__(self, prob, device="cuda", stream=None, precision=MLQP_FP64, max_refine=10, refine_tol=1e-15,
-                 block_solver=MLQP_SWEEP, refine_method=MLQP_IR):
+                 block_solver=MLQP_SWEEP, refine_method=MLQP_IR_GMRES):
         import torch
         self.torch = torch
         self.lib = load()
@@ -200,7 +202,7 @@ class Context:
         self.precision = precision
         self.ctx, self._keep = mlqp_setup(prob, precision, max_refine if precision == MLQP_MIXED else 0,
                                           refine_tol if precision == MLQP_MIXED else 0.0, block_solver,
-                                          refine_method)
+                                          refine_method if precision == MLQP_MIXED else MLQP_IR)
         n_den = ct.c_long()
         n_modes = ct.c_int()
         _check(self.ctx, self.lib.mlqp_sizes(self.ctx, ct.byref(n_den), ct.byref(n_modes)))
@@ -233,7 +235,7 @@ class Context:
         self.prob = prob
         self._keep = keep
 
-    TUNE_REPORT = 18
+    TUNE_REPORT = 21
 
     def autotune(self, which=TUNE_ALL):
         """mlqp_autotune: times candidate launch shapes (the TUNE_* bits of
@@ -245,7 +247,12 @@ class Context:
         return {"qr_cluster": r[0], "lsq_ms": dict(zip((1, 2, 4, 8), r[1:5])),
                 "angle_groups": r[5], "sweep_ms_by_groups": dict(zip((1, 2, 3, 4), r[6:10])),
                 "cr_cluster_cap": r[10], "sweep_ms_by_cr_cluster": dict(zip((1, 2, 4, 8), r[11:15])),
-                "update_tile": r[15], "sweep_ms_by_update_tile": dict(zip((16, 32), r[16:18]))}
+                "update_tile": r[15], "sweep_ms_by_update_tile": dict(zip((16, 32), r[16:18])),
+                "lookahead": r[18], "sweep_ms_by_lookahead": dict(zip((0, 1), r[19:21]))}
+
+    def set_shape(self, which, value):
+        """mlqp_set_shape: one launch shape (a TUNE_* bit) set by hand."""
+        _check(self.ctx, self.lib.mlqp_set_shape(self.ctx, int(which), int(value)))
 
     def close(self):
         if self.ctx:

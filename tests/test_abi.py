@@ -151,7 +151,8 @@ def test_cyclic_solver_validation(M):
 
 
 def test_refine_method_validation(M):
-    """MLQP_GMRES_IR refines the mixed form only; unknown methods are refused."""
+    """MLQP_GMRES_IR and MLQP_IR_GMRES refine the mixed form only; unknown
+    methods are refused."""
     lib = M.load()
     from workloads import small_stack
     def st(precision, method, solver=0):
@@ -165,7 +166,10 @@ def test_refine_method_validation(M):
     assert st(M.MLQP_MIXED, M.MLQP_GMRES_IR) == M.MLQP_OK
     assert st(M.MLQP_MIXED, M.MLQP_GMRES_IR, M.MLQP_CYCLIC) == M.MLQP_OK
     assert st(M.MLQP_FP64, M.MLQP_GMRES_IR) == M.MLQP_EINVAL
-    assert st(M.MLQP_MIXED, 2) == M.MLQP_EINVAL
+    assert st(M.MLQP_MIXED, M.MLQP_IR_GMRES) == M.MLQP_OK
+    assert st(M.MLQP_MIXED, M.MLQP_IR_GMRES, M.MLQP_CYCLIC) == M.MLQP_OK
+    assert st(M.MLQP_FP64, M.MLQP_IR_GMRES) == M.MLQP_EINVAL
+    assert st(M.MLQP_MIXED, 3) == M.MLQP_EINVAL
 
 
 def test_autotune_needs_a_bound_context(M):
@@ -174,9 +178,11 @@ def test_autotune_needs_a_bound_context(M):
     from workloads import small_stack
     import ctypes as ct
     ctx, _ = M.mlqp_setup(small_stack(I=2))
-    rep = (ct.c_double * 18)()
-    assert lib.mlqp_autotune(ctx, 0, rep, 18) == M.MLQP_ESTATE
-    assert lib.mlqp_autotune(None, 0, rep, 18) == M.MLQP_EINVAL
+    rep = (ct.c_double * 21)()
+    assert lib.mlqp_autotune(ctx, 0, rep, 21) == M.MLQP_ESTATE
+    assert lib.mlqp_autotune(None, 0, rep, 21) == M.MLQP_EINVAL
+    assert lib.mlqp_set_shape(ctx, M.TUNE_LOOKAHEAD, 1) == M.MLQP_ESTATE
+    assert lib.mlqp_set_shape(None, M.TUNE_LOOKAHEAD, 1) == M.MLQP_EINVAL
     lib.mlqp_destroy(ctx)
 
 

@@ -475,6 +475,37 @@ def test_gmres_refinement_where_plain_refinement_stalls(M):
             ag = np.concatenate([out["aU"][a], out["aD"][a]])
             assert rel(ag, np.concatenate([ref["aU"][a], ref["aD"][a]])) < AMP_TOL, a
     ctx.close()
+    # the default refinement (MLQP_IR_GMRES) starts plain, sees the stall and
+    # finishes with GMRES corrections
+    auto = M.Context(prob, precision=M.MLQP_MIXED, max_refine=10)
+    out = auto.solve_host()
+    for a in range(prob.n_theta):
+        omega, steps = auto.block(M.BLK_REFINE, 1, a).cpu().numpy()
+        inner, _ = auto.block(M.BLK_REFINE, 2, a).cpu().numpy()
+        assert omega <= 1e-15 and inner >= 1, (a, omega, steps, inner)
+        if a < 2:
+            ag = np.concatenate([out["aU"][a], out["aD"][a]])
+            assert rel(ag, np.concatenate([ref["aU"][a], ref["aD"][a]])) < AMP_TOL, a
+    auto.close()
+
+
+@pytest.mark.parametrize("name", ["small3", "corner2"])
+def test_default_refinement_is_plain_where_it_converges(M, name):
+    """Where every plain correction divides the backward error by more than
+    4, the default MLQP_IR_GMRES takes no GMRES step and gives bitwise the
+    amplitudes of MLQP_IR."""
+    prob = PROBLEMS[name]()
+    outs = {}
+    for method in (M.MLQP_IR, M.MLQP_IR_GMRES):
+        ctx = M.Context(prob, precision=M.MLQP_MIXED, refine_method=method)
+        outs[method] = ctx.solve_host()
+        if method == M.MLQP_IR_GMRES:
+            for a in range(prob.n_theta):
+                inner, _ = ctx.block(M.BLK_REFINE, 2, a).cpu().numpy()
+                assert inner == 0, (a, inner)
+        ctx.close()
+    for k in ("aU", "aD"):
+        assert np.array_equal(outs[M.MLQP_IR][k], outs[M.MLQP_IR_GMRES][k])
 
 
 @pytest.mark.parametrize("form", ["fp64", "mixed_cyclic"])
@@ -495,11 +526,32 @@ def test_autotune_keeps_results_bitwise(M, form):
     assert 1 <= rep["angle_groups"] <= min(4, prob.n_theta)
     if form == "mixed_cyclic":
         assert rep["cr_cluster_cap"] in (1, 2, 4, 8) and math.isnan(rep["update_tile"])
+        assert math.isnan(rep["lookahead"])
     else:
         assert math.isnan(rep["cr_cluster_cap"]) and rep["update_tile"] in (16, 32)
+        assert rep["lookahead"] in (0, 1) and all(t > 0 for t in rep["sweep_ms_by_lookahead"].values())
     r1 = ctx.solve_host()
     ctx.close()
     assert np.array_equal(r0["aU"], r1["aU"]) and np.array_equal(r0["aD"], r1["aD"])
+
+
+@pytest.mark.parametrize("name,precision", [("uneven", 0), ("corner2", 0), ("small3", 1)])
+def test_lookahead_keeps_results_bitwise(M, name, precision):
+    """The block LU with look-ahead (the next panel factored on a second
+    stream beside the rest of each trailing update, mlqp_set_shape) gives
+    bitwise the amplitudes of the LU without it, in FP64 and in the mixed
+    form's FP32 factorisation, with one angle group and with two."""
+    prob = PROBLEMS[name]()
+    kw = dict(precision=M.MLQP_MIXED) if precision else {}
+    outs = []
+    for la, groups in ((0, 1), (1, 1), (1, min(2, prob.n_theta))):
+        ctx = M.Context(prob, **kw)
+        ctx.set_shape(M.TUNE_LOOKAHEAD, la)
+        ctx.set_shape(M.TUNE_GROUPS, groups)
+        outs.append(ctx.solve_host())
+        ctx.close()
+    for o in outs[1:]:
+        assert np.array_equal(outs[0]["aU"], o["aU"]) and np.array_equal(outs[0]["aD"], o["aD"])
 
 
 def test_corner_grating_at_full_size(M):
