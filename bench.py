@@ -564,7 +564,8 @@ def main():
 
     ctx = mlqp.Context(prob, device=dev)
     # launch shapes timed on this problem (untimed setup)
-    tuned = ctx.autotune() if not args.no_autotune else {"qr_cluster": 8, "angle_groups": 1, "update_tile": 16}
+    tuned = ctx.autotune() if not args.no_autotune else {"qr_cluster": 8, "angle_groups": 1, "update_tile": 16,
+                                                         "lookahead": 0}
     out = ctx.outputs()
     for _ in range(W):
         ctx.solve_device(out)
@@ -605,6 +606,7 @@ def main():
                            "launch_shapes": {"qr_cluster": int(tuned["qr_cluster"]),
                                              "angle_groups": int(tuned["angle_groups"]),
                                              "update_tile": int(tuned.get("update_tile", 16)),
+                                             "lookahead": int(tuned.get("lookahead", 0)),
                                              "source": "defaults" if args.no_autotune else "mlqp_autotune"}},
                 "flux_error": flux, "meets_flux_gate_1e-9": flux <= 1e-9,
                 "stage_ms": stage_ms, "dominant_stage": max(stage_ms, key=stage_ms.get),
@@ -648,7 +650,8 @@ def main():
                "max_rel_amp_diff_vs_fp64": rel_amp_diff(mout, out), "gpu_launches": mlaunch,
                "block_solver": "sweep" if solver == mlqp.MLQP_SWEEP else "cyclic reduction",
                "launch_shapes": {k: (None if v != v else int(v)) for k, v in mtuned.items()
-                                 if k in ("qr_cluster", "angle_groups", "cr_cluster_cap", "update_tile")},
+                                 if k in ("qr_cluster", "angle_groups", "cr_cluster_cap", "update_tile",
+                                          "lookahead")},
                "dtype": "f32 Schur/LU + f64 refinement (fill, least squares, residuals in f64)"}
         res.update(refine_info(mlqp, mctx))
         mctx.close()
