@@ -453,8 +453,10 @@ def angle_sweep(mlqp, dev, chunk=32):
 # capture of a shorter stack of the same interfaces (traffic grows in
 # proportion to the interfaces: every interface's sweep step touches the same
 # sizes); None until captured for the current kernels.
-SWEEP_TRAFFIC_BYTES_PER_INTERFACE = None
-SWEEP_TRAFFIC_NOTE = "null: no ncu capture of the current sweep kernels on this workload"
+SWEEP_TRAFFIC_BYTES_PER_INTERFACE = 43.59e6
+SWEEP_TRAFFIC_SHAPES = {"qr_cluster": 8, "angle_groups": 1, "update_tile": 16, "lookahead": 0}
+SWEEP_TRAFFIC_NOTE = ("DRAM bytes read + written by the sweep kernels per step: 43.6 MB per interface from one ncu "
+                      "capture of the first 40 interfaces (launch shapes SWEEP_TRAFFIC_SHAPES), times the interfaces")
 
 
 def timed_solves(mlqp, ctx, steps, flush, stages):
@@ -595,6 +597,7 @@ def main():
         sw_flops = nth * sweep_flops(n)
         achieved = sw_flops / (stage_ms["sweep"] / 1e3) / 1e12
         peak = FP64_PEAK_GFLOPS / 1e3
+        shapes_as_captured = all(int(tuned.get(k, -1)) == v for k, v in SWEEP_TRAFFIC_SHAPES.items())
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K,
                 "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -613,9 +616,10 @@ def main():
                 "roofline": {"bound": "alu", "kernel": "block-tridiagonal sweep (k_lu_panel_cl, k_lu_prep, "
                                                       "k_lu_update, k_back_*), one stage of the step",
                              "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                             "traffic": SWEEP_TRAFFIC_BYTES_PER_INTERFACE * prob.I * nth
-                             if SWEEP_TRAFFIC_BYTES_PER_INTERFACE else None,
-                             "traffic_note": SWEEP_TRAFFIC_NOTE,
+                             "traffic": SWEEP_TRAFFIC_BYTES_PER_INTERFACE * prob.I * nth if shapes_as_captured
+                             else None,
+                             "traffic_note": SWEEP_TRAFFIC_NOTE if shapes_as_captured else
+                             "null: the tuned launch shapes differ from the ncu capture's",
                              "algorithmic_flops_per_step": sw_flops,
                              "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived from the "
                                           "unit counts and the maximum SM clock; MEASURED_PEAKS.json has no FP64 "
