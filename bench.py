@@ -302,69 +302,104 @@ def gradient_leg(mlqp, dev, reps=3):
     return out
 
 
-def design_gradient(mlqp, dev, n_params=4):
+def design_gradient(mlqp, dev, n_check=20, h=1e-6, rcond=1e-8):
     """The design-gradient stack (50 interfaces with 4 Fourier modes, 51
-    wavenumbers, 120 nodes, 16 angles; 451 parameters in all), along
-    `n_params` of its parameters (wavenumbers and coefficients of the middle
-    of the stack), J = sum over angles and orders of |a^U_n|^2, t = 1e-3:
-    wall-clock of the solve, of forming the sensitivities once
-    (mlqp_gradient_prepare), of the first parameter (making the four moved
-    contexts and capturing their graphs) and of each later one (moving them by
-    mlqp_set_problem, fills and forms: mlqp_gradient_eval)."""
-    import time
+    wavenumbers, 120 nodes, 16 angles; 451 parameters): the gradient of
+    J = sum over the angles of the reflected 0th and -1st order efficiencies
+    with respect to every parameter.  One gradient = the solve, the
+    sensitivities formed once (mlqp_gradient_prepare), and per parameter the
+    four moved contexts (mlqp_set_problem) filled and contracted over the
+    blocks that parameter moves (mlqp_gradient_eval_local, t = 1e-3), plus
+    the weights' own term.  Checked against central differences of J through
+    GPU solves (step h) on n_check parameters spread over the stack.  The
+    least squares use lsq_rcond = rcond: at 1e-10, J itself is rough at the
+    1e-5 level under parameter steps (its central differences at h = 1e-6,
+    1e-5, 1e-4 disagree by that much), so no gradient can be checked to
+    1e-6 there."""
     from dataclasses import replace
     import numpy as np
     import torch
+    from paper_1410_5003_gb300.diff import reflected_weights
     from workloads import config5
     from workloads.problems import Interface
-    prob = config5()
-    mid = prob.I // 2
+    base = config5()
+    prob = replace(base, params=replace(base.params, lsq_rcond=rcond))
+    I, nm = prob.I, len(prob.ifaces[0].a)
     t = 1e-3
+    # parameters: k_1..k_{I+1}, then a_m, b_m of each interface
+    plist = [("k", j, 0) for j in range(I + 1)] + [(ab, i, m) for i in range(I) for ab in ("a", "b")
+                                                    for m in range(nm)]
 
-    def moved_problem(q, s_):
-        k = np.asarray(prob.k, dtype=np.complex128).copy()
+    def moved_problem(q, delta):
+        kind, i, m = plist[q]
+        if kind == "k":
+            k = np.asarray(prob.k, dtype=np.complex128).copy()
+            k[i] += delta
+            return replace(prob, k=k)
         ifs = list(prob.ifaces)
-        f = ifs[mid - 1 + q // 2]
+        f = ifs[i]
         a, b = f.a.copy(), f.b.copy()
-        if q % 2 == 0:
-            k[mid + q // 2] += s_ * t
-        else:
-            a[q // 2 % len(a)] += s_ * t
-        ifs[mid - 1 + q // 2] = Interface(f.y0, a, b, f.N)
-        return replace(prob, k=k, ifaces=ifs)
+        (a if kind == "a" else b)[m] += delta
+        ifs[i] = Interface(f.y0, a, b, f.N)
+        return replace(prob, ifaces=ifs)
+
+    def where(q):
+        kind, i, _ = plist[q]
+        return (mlqp.PARAM_LAYER, i + 1) if kind == "k" else (mlqp.PARAM_INTERFACE, i + 1)
+
+    def objective(ctx_, pr):
+        res = ctx_.solve_host()
+        w = reflected_weights(pr)
+        return float(np.sum(w * np.abs(np.asarray(res["aU"])) ** 2)), res
 
     ctx = mlqp.Context(prob, device=dev)
-    ctx.solve_host()  # captures the graphs
-    t0 = time.perf_counter()
-    res = ctx.solve_host()
-    solve_ms = (time.perf_counter() - t0) * 1e3
-    t0 = time.perf_counter()
-    work = ctx.gradient_prepare(np.asarray(res["aU"]))
-    torch.cuda.synchronize()
-    prep_ms = (time.perf_counter() - t0) * 1e3
-    moved, per, first, total = [], [], None, 0.0
-    for q in range(n_params):
-        t0 = time.perf_counter()
-        probs = [moved_problem(q, s_) for s_ in (-2, -1, 1, 2)]
-        if not moved:
-            moved = [mlqp.Context(mp, device=dev) for mp in probs]
-        else:
+    moved = [mlqp.Context(moved_problem(0, s_ * t), device=dev) for s_ in (-2, -1, 1, 2)]
+    objective(ctx, prob)  # captures the graphs
+    w0 = reflected_weights(prob)
+
+    def gradient():
+        J, res = objective(ctx, prob)
+        aU = np.asarray(res["aU"])
+        work = ctx.gradient_prepare(w0 * aU)
+        grad = np.zeros(len(plist))
+        for q in range(len(plist)):
+            probs = [moved_problem(q, s_ * t) for s_ in (-2, -1, 1, 2)]
             for m, mp in zip(moved, probs):
                 m.set_problem(mp)
-        total += float(np.sum(ctx.gradient_eval(moved, t, work)))
-        ms = (time.perf_counter() - t0) * 1e3
-        if q == 0:
-            first = ms
-        else:
-            per.append(ms)
+            gq = float(np.sum(ctx.gradient_eval_local(moved, t, work, *where(q))))
+            wm = [reflected_weights(mp) for mp in probs]
+            dw = (wm[0] - 8.0 * wm[1] + 8.0 * wm[2] - wm[3]) / (12.0 * t)
+            grad[q] = gq + float(np.sum(dw * np.abs(aU) ** 2))
+        return J, grad
+
+    gradient()  # warm-up: the moved contexts' graphs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, grad = gradient()
+    el = time.perf_counter() - t0
+    # central differences of J through GPU solves on a spread of parameters
+    check = sorted(set(np.linspace(0, len(plist) - 1, n_check).round().astype(int).tolist()))
+    fdc = mlqp.Context(prob, device=dev)
+    errs = []
+    for q in check:
+        vals = []
+        for sgn in (1, -1):
+            mp = moved_problem(q, sgn * h)
+            fdc.set_problem(mp)
+            vals.append(objective(fdc, mp)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        errs.append(abs(grad[q] - fd) / max(abs(fd), 1e-3 * float(np.max(np.abs(grad)))))
+    fdc.close()
     for m in moved:
         m.close()
     ctx.close()
-    n_all = prob.I * 2 * len(prob.ifaces[0].a) + prob.I + 1
-    return {"workload": "50 interfaces x 4 Fourier modes, 51 wavenumbers, 120 nodes, 16 angles",
-            "parameters_total": n_all, "parameters_timed": n_params, "ms_solve_host": solve_ms,
-            "ms_prepare": prep_ms, "ms_first_parameter": first,
-            "ms_per_parameter": float(np.median(per)) if per else None, "sum_dJ": total}
+    return {"workload": "50 interfaces x 4 Fourier modes, 51 wavenumbers, 120 nodes, 16 angles; J = sum over angles "
+                        "of the reflected 0th and -1st order efficiencies",
+            "parameters": len(plist), "lsq_rcond": rcond, "J": J, "seconds_per_gradient": el,
+            "grads_per_s": 1.0 / el, "ms_per_parameter": 1e3 * el / len(plist),
+            "fd_check": {"parameters": len(check), "h": h, "max_rel_err": float(max(errs)),
+                         "median_rel_err": float(np.median(errs)),
+                         "scale": "|adjoint - FD| / max(|FD|, 1e-3 max|grad|)"}}
 
 
 def angle_sweep(mlqp, dev, chunk=32):
@@ -569,8 +604,9 @@ def main():
     tuned = ctx.autotune() if not args.no_autotune else {"qr_cluster": 8, "angle_groups": 1, "update_tile": 16,
                                                          "lookahead": 0}
     out = ctx.outputs()
-    for _ in range(W):
-        ctx.solve_device(out)
+    ctx.solve_device(out)  # the one-graph solve (e2e below) captured outside the timed region
+    # warm-up in the timed loop's own form: the stage graphs are captured here, not in a timed step
+    timed_solves(mlqp, ctx, W, flush, stages)
     ctx.check()
     if ws > 1:
         torch.distributed.barrier()

@@ -43,7 +43,7 @@ typedef enum {
   MLQP_ENOMEM = 2,     /* host allocation failed or workspace too small */
   MLQP_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
   MLQP_ESINGULAR = 4,  /* a block-LU pivot was zero or not finite */
-  MLQP_ETIMEOUT = 5,   /* reserved for a bounded device-side wait that gave up (no kernel waits today) */
+  MLQP_ETIMEOUT = 5,   /* a bounded device-side wait (an mbarrier of a tensor-core kernel) gave up */
   MLQP_ENOTCONV = 6,   /* iterative refinement missed its tolerance */
   MLQP_ESTATE = 7      /* call out of order (e.g. solve before bind) */
 } mlqp_status;
@@ -245,6 +245,24 @@ mlqp_status mlqp_gradient_prepare(mlqp_ctx* ctx, const void* d_g, void* d_work, 
 mlqp_status mlqp_gradient_eval(mlqp_ctx* ctx, mlqp_ctx* const* moved, double t, void* d_work, size_t work_bytes,
                                double* grad);
 
+/* mlqp_gradient_eval for a parameter that moves one interface (any of its
+ * Fourier coefficients, y0 or corner vertices: param_kind
+ * MLQP_PARAM_INTERFACE, index i = 1..I) or one layer wavenumber
+ * (MLQP_PARAM_LAYER, index j = 1..I+1).  Such a parameter moves only the
+ * blocks near it (Secs. 2.4-3.1: interface i enters the A and B blocks of
+ * block rows i-1..i+1 and the wall, proxy and radiation blocks Q', C' of
+ * layers i and i+1; k_j the block rows j-1, j and layer j), so the moved
+ * contexts fill only those blocks and the forms run over them alone; the
+ * other blocks' terms are equal in the four moved problems and drop out of
+ * the difference.  k_1 sets the Bloch phase of every block: layer 1 is
+ * evaluated over the whole stack.  The moved problems must differ from
+ * ctx's only in that interface or wavenumber (checked: MLQP_EINVAL).  The
+ * moved contexts fill the whole stack again at their next solve.  Other
+ * arguments, state rules and errors as mlqp_gradient_eval. */
+enum { MLQP_PARAM_INTERFACE = 1, MLQP_PARAM_LAYER = 2 };
+mlqp_status mlqp_gradient_eval_local(mlqp_ctx* ctx, mlqp_ctx* const* moved, double t, void* d_work,
+                                     size_t work_bytes, int param_kind, int index, double* grad);
+
 /* Synchronises the bound stream and returns the device-side status word. */
 mlqp_status mlqp_check_device(mlqp_ctx* ctx);
 
@@ -353,6 +371,20 @@ mlqp_status mlqp_block_info(const mlqp_ctx* ctx, int kind, int index, int angle,
  * `stream`.  Same device routines as the fill kernels.  Errors: MLQP_EINVAL,
  * MLQP_ECUDA. */
 mlqp_status mlqp_debug_hankel(const double* d_krho, int n, double* d_out, void* stream);
+
+/* Test hook for the tensor-core complex products (the Schur updates of the
+ * block cyclic reduction in the mixed form run on them): C = beta C - A B
+ * for n x n complex FP32 blocks A, B, C (column-major, interleaved re / im,
+ * device memory, 16-byte aligned; n even, 2..4096; beta 0 or 1), computed as
+ * one real 2n x n x 2n product on tcgen05 tensor cores in three TF32 passes
+ * (hi x hi + hi x lo + lo x hi of each operand's split into the TF32 value
+ * and its remainder: about FP32 accuracy).  d_work: device, 256-byte aligned,
+ * mlqp_debug_tc_work_bytes(n) bytes (0 for an invalid n).  Synchronous.
+ * Errors: MLQP_EINVAL, MLQP_ENOMEM (work too small), MLQP_ECUDA,
+ * MLQP_ETIMEOUT (a bounded wait inside the kernel gave up). */
+size_t mlqp_debug_tc_work_bytes(int n);
+mlqp_status mlqp_debug_tc_cgemm(const void* d_A, const void* d_B, void* d_C, int n, int beta, void* d_work,
+                                size_t work_bytes, void* stream);
 
 /* Bytes of the problem description mlqp_bind copies host -> device. */
 size_t mlqp_upload_bytes(const mlqp_ctx* ctx);

@@ -30,12 +30,19 @@ cudaError_t launch_lsq_adjoint(const Dev& D, int max_p, int max_c, const double2
 cudaError_t launch_grad_adjoint(const Dev& D, const int* n_host, int* permv, int max_p, const GradVecs& V,
                                 cudaStream_t s);
 cudaError_t launch_grad_base_lsq(const Dev& D, const GradVecs& V, cudaStream_t s);
-cudaError_t launch_grad_form(const Dev& Dm, const GradVecs& V, int slot, cudaStream_t s);
+cudaError_t launch_grad_form(const Dev& Dm, const GradVecs& V, int slot, const int* win, cudaStream_t s);
 cudaError_t launch_grad_combine(const Dev& D, const GradVecs& V, double t, cudaStream_t s);
 cudaError_t launch_mixed_piece(const Dev& D, const int* n_host, int maxn, long n_den, double tol, int* permv,
                                const AngleStreams& A, bool cyclic, int piece);
 cudaError_t cr_configure(int maxn);
 int cr_slots(int I);
+int cr_tc_group(int I, int n, int nt);
+void cr_tc_tables(const Dev& D, const IfaceDesc* ifc, int n, int qb, std::vector<TcJob>& jobs,
+                  std::vector<TcPrep>& prep, std::vector<TcBatch>& batches, std::vector<int>& lvl_first);
+size_t tc_x_bytes(int n, long slots);
+size_t tc_y_bytes(int n, long slots);
+cudaError_t tc_encode_plan(TcPlan& P, long x_slots, long y_slots);
+cudaError_t tc_configure();
 cudaError_t lsq_configure(int max_m, int max_p);
 cudaError_t launch_hankel_eval(const double* kr, int n, double* out, cudaStream_t s);
 extern thread_local long g_launches;
@@ -66,7 +73,7 @@ struct mlqp_ctx {
          t_stride = 0;
   // layout
   Region r_ifc, r_lay, r_tasks, r_k, r_ca, r_cb, r_theta, r_scal, r_geo[8], r_pan[4], r_gl16, r_nidx, r_nw, r_wy, r_gl, r_ux, r_alpha, r_kappa,
-      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ROW32, r_F32, r_UDINV32, r_RES, r_ZX, r_ZXA, r_Y32, r_RNRM, r_CRSAVE, r_GV, r_GZ, r_GW, r_GH, r_GPART, r_PERMV, r_ETA, r_AMP, r_FLUX, r_STATUS;
+      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ROW32, r_F32, r_UDINV32, r_RES, r_ZX, r_ZXA, r_Y32, r_RNRM, r_CRSAVE, r_fwin, r_tcjob, r_tcprep, r_TCX, r_TCY, r_GV, r_GZ, r_GW, r_GH, r_GPART, r_PERMV, r_ETA, r_AMP, r_FLUX, r_STATUS;
   size_t ws_bytes = 0;
   // binding
   char* ws = nullptr;
@@ -90,6 +97,15 @@ struct mlqp_ctx {
   // cluster cap, angle groups of the sweep (0: min(n_theta, MAX_ANGLE_STREAMS)),
   // tile edge of the block LU's trailing update
   int qr_cl = 8, cr_cl_max = 8, angle_groups = 0, upd_tile = 16, lookahead = 0;
+  // the cyclic reduction's survivor updates on the tensor cores: survivors per
+  // launch group, the job / prep tables (uploaded with the descriptors), the
+  // launch groups in order, and the plan the launches read (tensor maps)
+  int tc_qb = 0;
+  std::vector<TcJob> tc_jobs;
+  std::vector<TcPrep> tc_prep;
+  std::vector<TcBatch> tc_batches;
+  std::vector<int> tc_lvl;
+  TcPlan tcplan;
   // the mixed block solve: one graph per piece (launch_mixed_piece), replayed by
   // a host loop that reads the active-angle counts into hflag (pinned)
   cudaGraphExec_t pexec[MP_COUNT] = {};
@@ -440,6 +456,16 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   take(cur, c->r_ifc, sizeof(IfaceDesc) * I);
   take(cur, c->r_lay, sizeof(LayerDesc) * c->L);
   take(cur, c->r_tasks, sizeof(SchurTask) * c->tasks.size());
+  take(cur, c->r_fwin, 4 * sizeof(int));
+  if (q.precision == MLQP_MIXED && q.block_solver == MLQP_CYCLIC) {
+    Dev cnt{};
+    cnt.I = I;
+    cnt.n_theta = n_theta;
+    c->tc_qb = cr_tc_group(I, c->maxn, n_theta);
+    cr_tc_tables(cnt, c->ifc.data(), c->maxn, c->tc_qb, c->tc_jobs, c->tc_prep, c->tc_batches, c->tc_lvl);
+    take(cur, c->r_tcjob, sizeof(TcJob) * std::max<size_t>(1, c->tc_jobs.size()));
+    take(cur, c->r_tcprep, sizeof(TcPrep) * std::max<size_t>(1, c->tc_prep.size()));
+  }
   take(cur, c->r_k, d8 * c->k.size());
   take(cur, c->r_ca, d8 * c->coef_a.size());
   take(cur, c->r_cb, d8 * c->coef_b.size());
@@ -479,8 +505,11 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
     take(cur, c->r_ZXA, d8 * nt * (size_t)c->L * q.P);
     take(cur, c->r_Y32, f8 * nt * c->n_den);
     take(cur, c->r_RNRM, d8 * nt * RNRM_W);
-    if (q.block_solver == MLQP_CYCLIC)
+    if (q.block_solver == MLQP_CYCLIC) {
       take(cur, c->r_CRSAVE, sizeof(float2) * nt * (size_t)cr_slots(I) * 2 * c->maxn * c->maxn);
+      take(cur, c->r_TCX, tc_x_bytes(c->maxn, (long)nt * 2 * c->tc_qb));
+      take(cur, c->r_TCY, tc_y_bytes(c->maxn, (long)nt * 2 * (c->tc_qb + 1)));
+    }
     if (q.refine_method != MLQP_IR) {
       take(cur, c->r_GV, z16 * nt * (GM_M + 1) * c->n_den);
       take(cur, c->r_GZ, z16 * nt * GM_M * c->n_den);
@@ -602,6 +631,21 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
     if (q.block_solver == MLQP_CYCLIC) {
       D.CRSAVE = at<float2>(c, c->r_CRSAVE);
       D.crsave_stride = (size_t)cr_slots(c->I) * 2 * c->maxn * c->maxn;
+      // the survivor updates' tables with this workspace's addresses, and their plan
+      cr_tc_tables(D, c->ifc.data(), c->maxn, c->tc_qb, c->tc_jobs, c->tc_prep, c->tc_batches, c->tc_lvl);
+      TcPlan& P = c->tcplan;
+      P.xs = at<float>(c, c->r_TCX);
+      P.ys = at<float>(c, c->r_TCY);
+      P.jobs = at<TcJob>(c, c->r_tcjob);
+      P.prep = at<TcPrep>(c, c->r_tcprep);
+      P.n = c->maxn;
+      P.qb = c->tc_qb;
+      P.batches = c->tc_batches.data();
+      P.lvl_first = c->tc_lvl.data();
+      const int nt_ = c->n_theta;
+      if (tc_encode_plan(P, (long)nt_ * 2 * c->tc_qb, (long)nt_ * 2 * (c->tc_qb + 1)) != cudaSuccess)
+        return fail(c, MLQP_ECUDA, "tensor-map encoding of the cyclic reduction's operand planes failed");
+      D.tc = &c->tcplan;
     }
     if (q.refine_method != MLQP_IR) {
       D.GV = at<double2>(c, c->r_GV);
@@ -617,6 +661,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   D.FLUX = at<double>(c, c->r_FLUX);
   D.STATUS = at<int>(c, c->r_STATUS);
   D.tasks = at<SchurTask>(c, c->r_tasks);
+  D.FWIN = at<int>(c, c->r_fwin);
   D.n_tasks = (int)c->tasks.size();
   // stage the descriptors and inputs in pinned host memory, one H2D copy
   const size_t hdr = c->r_geo[0].off;
@@ -638,6 +683,10 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   put(c->r_ifc, c->ifc.data(), sizeof(IfaceDesc) * c->ifc.size());
   put(c->r_lay, c->lay.data(), sizeof(LayerDesc) * c->lay.size());
   put(c->r_tasks, c->tasks.data(), sizeof(SchurTask) * c->tasks.size());
+  const int full_window[4] = {0, c->I, 0, c->L};
+  put(c->r_fwin, full_window, sizeof(full_window));
+  put(c->r_tcjob, c->tc_jobs.data(), sizeof(TcJob) * c->tc_jobs.size());
+  put(c->r_tcprep, c->tc_prep.data(), sizeof(TcPrep) * c->tc_prep.size());
   put(c->r_k, c->k.data(), sizeof(double) * c->k.size());
   put(c->r_ca, c->coef_a.data(), sizeof(double) * c->coef_a.size());
   put(c->r_cb, c->coef_b.data(), sizeof(double) * c->coef_b.size());
@@ -647,6 +696,8 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   if ((e = sweep_configure(c->maxn)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
   if ((e = lsq_configure(c->max_m, c->max_p)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
   if (q.block_solver == MLQP_CYCLIC && (e = cr_configure(c->maxn)) != cudaSuccess)
+    return cuda_fail(c, e, "kernel configuration");
+  if (q.block_solver == MLQP_CYCLIC && (e = tc_configure()) != cudaSuccess)
     return cuda_fail(c, e, "kernel configuration");
   if ((e = make_angle_streams(c)) != cudaSuccess) return cuda_fail(c, e, "sweep streams");
   c->bound = true;
@@ -1206,8 +1257,20 @@ mlqp_status mlqp_gradient_prepare(mlqp_ctx* c, const void* d_g, void* d_work, si
   return MLQP_OK;
 }
 
-mlqp_status mlqp_gradient_eval(mlqp_ctx* c, mlqp_ctx* const* moved, double t, void* d_work, size_t work_bytes,
-                               double* grad) {
+// Sets the fill window of a bound context (interfaces [w0, w1), layers
+// [w2, w3), 0-based) on its stream, from its pinned staging buffer.
+static cudaError_t set_fill_window(mlqp_ctx* m, const int* w) {
+  cudaError_t e = cudaStreamSynchronize(m->stream);  // earlier uploads from the staging buffer are done
+  if (e != cudaSuccess) return e;
+  std::memcpy(m->staging + m->r_fwin.off, w, 4 * sizeof(int));
+  return cudaMemcpyAsync(const_cast<int*>(m->D.FWIN), m->staging + m->r_fwin.off, 4 * sizeof(int),
+                         cudaMemcpyHostToDevice, m->stream);
+}
+
+// The four moved fills (restricted to the window win when it is not the
+// whole stack), their forms, and the difference quotient per angle.
+static mlqp_status grad_eval(mlqp_ctx* c, mlqp_ctx* const* moved, double t, void* d_work, size_t work_bytes,
+                             const int* win, double* grad) {
   if (!c) return MLQP_EINVAL;
   if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
   mlqp_status st = check_work(c, d_work, work_bytes);
@@ -1217,6 +1280,7 @@ mlqp_status mlqp_gradient_eval(mlqp_ctx* c, mlqp_ctx* const* moved, double t, vo
   if (!(std::isfinite(t) && t != 0.0)) return fail(c, MLQP_EINVAL, "t: a finite nonzero step");
   if (!grad) return fail(c, MLQP_EINVAL, "grad is required");
   if ((st = check_moved(c, moved)) != MLQP_OK) return st;
+  const bool local = win[0] != 0 || win[1] != c->I || win[2] != 0 || win[3] != c->L;
   GradVecs V{};
   grad_layout(c, static_cast<char*>(d_work), &V);
   cudaEvent_t ev = nullptr;
@@ -1225,6 +1289,7 @@ mlqp_status mlqp_gradient_eval(mlqp_ctx* c, mlqp_ctx* const* moved, double t, vo
   int bad = -1;
   for (int s = 0; s < 4 && st == MLQP_OK && e == cudaSuccess; ++s) {
     mlqp_ctx* m = moved[s];
+    if (local && (e = set_fill_window(m, win)) != cudaSuccess) break;
     for (int q = MLQP_STAGE_GEOM; q <= MLQP_STAGE_FILL && st == MLQP_OK; ++q) st = mlqp_run_stage(m, q);
     if (st != MLQP_OK) {
       bad = s;
@@ -1233,7 +1298,7 @@ mlqp_status mlqp_gradient_eval(mlqp_ctx* c, mlqp_ctx* const* moved, double t, vo
     if ((e = cudaEventRecord(ev, m->stream)) != cudaSuccess) break;
     if ((e = cudaStreamWaitEvent(c->stream, ev, 0)) != cudaSuccess) break;
     g_launches = 0;
-    e = launch_grad_form(m->D, V, s, c->stream);
+    e = launch_grad_form(m->D, V, s, win, c->stream);
     c->launches += g_launches;
   }
   if (st == MLQP_OK && e == cudaSuccess) {
@@ -1244,6 +1309,14 @@ mlqp_status mlqp_gradient_eval(mlqp_ctx* c, mlqp_ctx* const* moved, double t, vo
   if (st == MLQP_OK && e == cudaSuccess)
     e = cudaMemcpyAsync(grad, V.grad, sizeof(double) * c->n_theta, cudaMemcpyDeviceToHost, c->stream);
   if (st == MLQP_OK && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (local) {  // the moved contexts fill the whole stack again in their later solves
+    const int full[4] = {0, c->I, 0, c->L};
+    for (int s = 0; s < 4; ++s) {
+      cudaError_t er = set_fill_window(moved[s], full);
+      if (er == cudaSuccess) er = cudaStreamSynchronize(moved[s]->stream);
+      if (e == cudaSuccess) e = er;
+    }
+  }
   cudaEventDestroy(ev);
   if (st != MLQP_OK) return fail(c, st, "gradient: moved[%d]'s fill failed: %s", bad, mlqp_last_error(moved[bad]));
   if (e != cudaSuccess) return cuda_fail(c, e, "gradient");
@@ -1251,6 +1324,65 @@ mlqp_status mlqp_gradient_eval(mlqp_ctx* c, mlqp_ctx* const* moved, double t, vo
     if ((st = mlqp_check_device(moved[s])) != MLQP_OK)
       return fail(c, st, "gradient: moved[%d]: %s", s, mlqp_last_error(moved[s]));
   return mlqp_check_device(c);
+}
+
+mlqp_status mlqp_gradient_eval(mlqp_ctx* c, mlqp_ctx* const* moved, double t, void* d_work, size_t work_bytes,
+                               double* grad) {
+  if (!c) return MLQP_EINVAL;
+  const int full[4] = {0, c->I, 0, c->L};
+  return grad_eval(c, moved, t, d_work, work_bytes, full, grad);
+}
+
+// True if interfaces a and b of contexts x and y have the same description.
+static bool same_interface(const mlqp_ctx* x, const mlqp_ctx* y, int i) {
+  const IfaceDesc &a = x->ifc[i], &b = y->ifc[i];
+  if (a.y0 != b.y0 || a.n_modes != b.n_modes || a.n_corners != b.n_corners) return false;
+  const int cnt = a.n_corners > 0 ? a.n_corners : a.n_modes;
+  for (int m = 0; m < cnt; ++m)
+    if (x->coef_a[a.coef_off + m] != y->coef_a[b.coef_off + m] || x->coef_b[a.coef_off + m] != y->coef_b[b.coef_off + m])
+      return false;
+  return true;
+}
+
+mlqp_status mlqp_gradient_eval_local(mlqp_ctx* c, mlqp_ctx* const* moved, double t, void* d_work,
+                                     size_t work_bytes, int param_kind, int index, double* grad) {
+  if (!c) return MLQP_EINVAL;
+  if (!moved) return fail(c, MLQP_EINVAL, "moved: 4 contexts");
+  const int I = c->I;
+  int win[4] = {0, I, 0, c->L};
+  if (param_kind == MLQP_PARAM_INTERFACE) {
+    if (index < 1 || index > I) return fail(c, MLQP_EINVAL, "interface index %d not in 1..%d", index, I);
+    const int i = index - 1;  // rows i-1..i+1 (the A and B blocks touching interface i), layers i, i+1
+    win[0] = std::max(0, i - 1);
+    win[1] = std::min(I, i + 2);
+    win[2] = i;
+    win[3] = i + 2;
+  } else if (param_kind == MLQP_PARAM_LAYER) {
+    if (index < 1 || index > I + 1) return fail(c, MLQP_EINVAL, "layer index %d not in 1..%d", index, I + 1);
+    const int j = index - 1;  // rows j-1, j (the interfaces bounding layer j), layer j; k_1 sets the Bloch phase
+    if (j > 0) {
+      win[0] = j - 1;
+      win[1] = std::min(I, j + 1);
+      win[2] = j;
+      win[3] = j + 1;
+    }
+  } else {
+    return fail(c, MLQP_EINVAL, "param_kind must be MLQP_PARAM_INTERFACE or MLQP_PARAM_LAYER");
+  }
+  // the moved problems may differ from this one only in the named interface or layer
+  for (int s = 0; s < 4; ++s) {
+    const mlqp_ctx* m = moved[s];
+    if (!m || !m->valid || m->I != I || m->ifc.size() != c->ifc.size() || m->k.size() != c->k.size())
+      return fail(c, MLQP_EINVAL, "moved[%d]: a context of this problem's sizes", s);
+    for (int q = 0; q < I; ++q)
+      if (!(param_kind == MLQP_PARAM_INTERFACE && q == index - 1) && !same_interface(c, m, q))
+        return fail(c, MLQP_EINVAL, "moved[%d] changes interface %d, not only the parameter's", s, q + 1);
+    for (int q = 0; q <= I; ++q)
+      if (!(param_kind == MLQP_PARAM_LAYER && q == index - 1) &&
+          (m->k[2 * q] != c->k[2 * q] || m->k[2 * q + 1] != c->k[2 * q + 1]))
+        return fail(c, MLQP_EINVAL, "moved[%d] changes the wavenumber of layer %d, not only the parameter's", s, q + 1);
+  }
+  return grad_eval(c, moved, t, d_work, work_bytes, win, grad);
 }
 
 mlqp_status mlqp_fd_gradient(mlqp_ctx* c, mlqp_ctx* const* moved, double t, const void* d_g, void* d_work,

@@ -20,6 +20,7 @@
 // the LU factors with their pivots (LUPIV) and reciprocal pivots (UDINV32).
 #include <algorithm>
 #include <cooperative_groups.h>
+#include <vector>
 
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
@@ -28,6 +29,7 @@
 namespace mlqp {
 
 namespace cg = cooperative_groups;
+cudaError_t tc_run(const TcPlan& P, const TcBatch& b, int* status, cudaStream_t st);
 extern thread_local long g_launches;
 constexpr int CR_THREADS = 256;
 constexpr int CRB = 16;   // LU panel width
@@ -396,11 +398,6 @@ __global__ void k_cr_save(Dev D, int s, int slot_base) {
 }
 
 // ---------------------------------------------------------------------------
-// Survivor updates, 64 x 64 output tiles with FP32 accumulation (the complex
-// products as three real ones): blockIdx.y = 3 x (survivor index) + block
-// (0: diagonal -= SL H_{e-s} + SR G_{e+s}; 1: left = -SL G_{e-s};
-// 2: right = -SR H_{e+s}), SL/SR the saved couplings.
-// ---------------------------------------------------------------------------
 constexpr int UT32 = 64, UK32 = 16;
 
 __global__ void __launch_bounds__(256) k_cr_update(Dev D, int s, int slot_base) {
@@ -603,6 +600,97 @@ int cr_slots(int I) {
   return slots;
 }
 
+// Survivors per tensor-core launch group: the operand planes of a group take
+// 96 n^2 bytes per survivor and angle (X: two couplings x two planes of
+// (2n)^2 FP32; Y: two G / H blocks x two planes of 2n^2 FP32), at most
+// TC_SCRATCH bytes in all; grid dimensions stay below 65535.
+constexpr size_t TC_SCRATCH = size_t(2) << 30;
+int cr_tc_group(int I, int n, int nt) {
+  const size_t per = 96 * (size_t)n * n * (size_t)nt;
+  const int cap = std::max(1, 21000 / std::max(1, nt));
+  return std::max(1, std::min({(int)(TC_SCRATCH / per), cr_count(0, 2, I), cap}));
+}
+
+// Tables of the survivor updates (eqs. of the cyclic reduction above) as
+// tensor-core jobs, level by level, in groups of qb survivors q0 .. q0+qb-1
+// (e = 2 s q): X slots a 2qb + 2(q - q0) + side hold the saved couplings
+// (side 0: A_{e,e-s}, 1: A_{e,e+s}); Y slots a 2(qb+1) + 2(x - q0 + 1) + side
+// the G (side 0) and H (side 1) blocks of the eliminated interfaces
+// i = s + 2 s x, x = q0 - 1 .. q0 + qb - 1.  Jobs per survivor and angle:
+//   diagonal  -= A_{e,e-s} H_{e-s} + A_{e,e+s} G_{e+s}
+//   left       = -A_{e,e-s} G_{e-s}
+//   right      = -A_{e,e+s} H_{e+s}
+// With D's pointers null the entries only count (for the workspace sizes).
+void cr_tc_tables(const Dev& D, const IfaceDesc* ifc, int n, int qb, std::vector<TcJob>& jobs,
+                  std::vector<TcPrep>& prep, std::vector<TcBatch>& batches, std::vector<int>& lvl_first) {
+  const int I = D.I, nt = D.n_theta;
+  const size_t nn = (size_t)n * n;
+  auto row = [&](int i, int a) -> float* {
+    return D.ROW32 ? reinterpret_cast<float*>(D.ROW32 + a * D.r_stride + ifc[i].row_off) : nullptr;
+  };
+  auto at_ = [](float* p, size_t off) -> float* { return p ? p + 2 * off : nullptr; };
+  jobs.clear();
+  prep.clear();
+  batches.clear();
+  lvl_first.clear();
+  int slot_base = 0;
+  for (int s = 1; s < I; s *= 2) {
+    lvl_first.push_back((int)batches.size());
+    const int nS = cr_count(0, 2 * s, I);
+    for (int q0 = 0; q0 < nS; q0 += qb) {
+      const int q1 = std::min(nS, q0 + qb);
+      TcBatch b{};
+      b.x_off = (int)prep.size();
+      for (int a = 0; a < nt; ++a)
+        for (int q = q0; q < q1; ++q) {
+          const int e = 2 * s * q;
+          for (int side = 0; side < 2; ++side) {
+            if (side == 0 ? e - s < 0 : e + s >= I) continue;
+            const float* src = D.CRSAVE ? reinterpret_cast<const float*>(D.CRSAVE + a * D.crsave_stride +
+                                                                         ((size_t)(slot_base + q) * 2 + side) *
+                                                                             (size_t)D.maxn * D.maxn)
+                                        : nullptr;
+            prep.push_back(TcPrep{src, (long)a * 2 * qb + 2 * (q - q0) + side});
+          }
+        }
+      b.nx = (int)prep.size() - b.x_off;
+      b.y_off = (int)prep.size();
+      for (int a = 0; a < nt; ++a)
+        for (int x = q0 - 1; x < q1; ++x) {
+          const int i = s + 2 * s * x;
+          if (x < 0 || i >= I) continue;
+          const long base = (long)a * 2 * (qb + 1) + 2 * (x - q0 + 1);
+          prep.push_back(TcPrep{row(i, a), base});                                    // G_i: left block
+          if (i + s < I) prep.push_back(TcPrep{at_(row(i, a), (size_t)(ifc[i].nl + n) * n), base + 1});  // H_i
+        }
+      b.ny = (int)prep.size() - b.y_off;
+      b.j_off = (int)jobs.size();
+      for (int a = 0; a < nt; ++a)
+        for (int q = q0; q < q1; ++q) {
+          const int e = 2 * s * q;
+          const bool hl = e - s >= 0, hr = e + s < I;
+          const int xl = a * 2 * qb + 2 * (q - q0), xr = xl + 1;
+          const int ybase = a * 2 * (qb + 1);
+          const int ylx = ybase + 2 * (q - 1 - q0 + 1), yrx = ybase + 2 * (q - q0 + 1);  // x = q - 1, x = q
+          if (hl || hr) {
+            TcJob j{at_(row(e, a), (size_t)ifc[e].nl * n), 1, 0, {0, 0}, {0, 0}};
+            if (hl) j.xslot[j.nterm] = xl, j.yslot[j.nterm] = ylx + 1, ++j.nterm;  // A_{e,e-s} H_{e-s}
+            if (hr) j.xslot[j.nterm] = xr, j.yslot[j.nterm] = yrx, ++j.nterm;      // A_{e,e+s} G_{e+s}
+            jobs.push_back(j);
+          }
+          if (hl) jobs.push_back(TcJob{row(e, a), 0, 1, {xl, 0}, {ylx, 0}});  // left = -A_{e,e-s} G_{e-s}
+          if (hr && e + 2 * s < I)  // right = -A_{e,e+s} H_{e+s}
+            jobs.push_back(TcJob{at_(row(e, a), (size_t)(ifc[e].nl + n) * n), 0, 1, {xr, 0}, {yrx + 1, 0}});
+        }
+      b.nj = (int)jobs.size() - b.j_off;
+      batches.push_back(b);
+    }
+    slot_base += nS;
+  }
+  lvl_first.push_back((int)batches.size());
+  (void)nn;
+}
+
 // k_cr_lu on clusters of CL CTAs per block: as many SMs per block as the
 // level leaves free, up to D.cr_cl_max (at most 8, the portable cluster
 // size), rounded down to a power of two.
@@ -635,7 +723,7 @@ cudaError_t launch_cr_factor(const Dev& D, int n, int* permv, cudaStream_t st) {
   const size_t pan = (size_t)n * CRB * sizeof(float2);
   const int cw = cr_chunk(n);
   const size_t trs = (size_t)n * cw * sizeof(float2);
-  int slot_base = 0;
+  int slot_base = 0, lvl = 0;
   for (int s = 1; s < I; s *= 2) {
     const int nE = cr_count(s, 2 * s, I), nS = cr_count(0, 2 * s, I);
     g_launches += 5;
@@ -644,10 +732,14 @@ cudaError_t launch_cr_factor(const Dev& D, int n, int* permv, cudaStream_t st) {
     k_cr_perm<<<dim3((nE + 63) / 64, nt), 64, 0, st>>>(D, s, 0, nE, permv);
     k_cr_trsm<<<dim3((2 * n + cw - 1) / cw, nE, nt), CR_THREADS, trs, st>>>(D, s, cw, permv);
     k_cr_save<<<dim3(std::max(1, (n * n + 255) / 256 / 4), nS, nt), 256, 0, st>>>(D, s, slot_base);
-    const int tiles = ((n + UT32 - 1) / UT32) * ((n + UT32 - 1) / UT32);
-    k_cr_update<<<dim3(tiles, 3 * nS, nt), 256, 0, st>>>(D, s, slot_base);
+    g_launches -= 1;  // counted: lu, perm, trsm, save; the updates below count their own
+    // survivor updates on the tensor cores, one launch group of qb survivors at a time
+    const TcPlan& P = *D.tc;
+    for (int b = P.lvl_first[lvl]; b < P.lvl_first[lvl + 1] && e == cudaSuccess; ++b)
+      e = tc_run(P, P.batches[b], D.STATUS, st);
+    ++lvl;
     slot_base += nS;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return e;
   }
   g_launches += 2;
   if (cudaError_t e = launch_cr_lu(D, 0, 1, 1, nt, pan, st); e != cudaSuccess) return e;

@@ -421,8 +421,14 @@ __device__ __forceinline__ void diag_limits(cplx k1, cplx k2, double sp, cplx ou
   out1[3] = (-0.5 * q) * (k1s - k2s);
 }
 
+// The fill window (a parameter-local gradient fills only the blocks its
+// parameter moves).
+__device__ __forceinline__ bool fill_row(const Dev& D, int i) { return i >= D.FWIN[0] && i < D.FWIN[1]; }
+__device__ __forceinline__ bool fill_layer(const Dev& D, int j) { return j >= D.FWIN[2] && j < D.FWIN[3]; }
+
 __global__ void __launch_bounds__(128) k_fill_A(Dev D) {
   const int i = blockIdx.z / 3, type = blockIdx.z % 3;  // 0 self, 1 upper (i+1), 2 lower (i-1)
+  if (!fill_row(D, i)) return;
   if (type == 1 && i == D.I - 1) return;
   if (type == 2 && i == 0) return;
   const IfaceDesc ft = D.ifc[i];
@@ -578,6 +584,7 @@ __device__ __forceinline__ void proxy_field(cplx k, double tx, double ty, double
 
 __global__ void __launch_bounds__(128) k_fill_B(Dev D) {
   const int i = blockIdx.z >> 1, which = blockIdx.z & 1;  // 0: B_{i,i}, 1: B_{i,i+1}
+  if (!fill_row(D, i)) return;
   const IfaceDesc f = D.ifc[i];
   const int j = blockIdx.x * 32 + threadIdx.x, p = blockIdx.y * 4 + threadIdx.y;
   if (j >= f.N || p >= D.P) return;
@@ -601,6 +608,7 @@ __global__ void __launch_bounds__(128) k_fill_B(Dev D) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_fill_C(Dev D) {
   const int jl = blockIdx.z >> 1, side = blockIdx.z & 1;
+  if (!fill_layer(D, jl)) return;
   const LayerDesc L = D.lay[jl];
   const int ifs = side ? L.if1 : L.if0;
   if (ifs < 0) return;
@@ -635,6 +643,7 @@ __global__ void __launch_bounds__(128) k_fill_C(Dev D) {
 __global__ void __launch_bounds__(128) k_fill_Z(Dev D, const double* scal) {
   const int which = blockIdx.z;  // 0: U, 1: D
   const int jl = which ? D.I : 0;
+  if (!fill_layer(D, jl)) return;
   const LayerDesc L = D.lay[jl];
   const int ifs = which ? D.I - 1 : 0;
   const IfaceDesc f = D.ifc[ifs];
@@ -668,6 +677,7 @@ __global__ void __launch_bounds__(128) k_fill_Z(Dev D, const double* scal) {
 // at the end layers also the zero block under the amplitude columns.
 __global__ void __launch_bounds__(128) k_fill_Q(Dev D) {
   const int jl = blockIdx.z;
+  if (!fill_layer(D, jl)) return;
   const LayerDesc L = D.lay[jl];
   const int g = blockIdx.x * 32 + threadIdx.x, p = blockIdx.y * 4 + threadIdx.y;
   if (g >= D.Mw || p >= L.p) return;
@@ -699,6 +709,7 @@ __global__ void __launch_bounds__(128) k_fill_Q(Dev D) {
 __global__ void __launch_bounds__(128) k_fill_VW(Dev D, const double* scal) {
   const int which = blockIdx.z;
   const int jl = which ? D.I : 0;
+  if (!fill_layer(D, jl)) return;
   const LayerDesc L = D.lay[jl];
   const int m = blockIdx.x * 32 + threadIdx.x, c = blockIdx.y * 4 + threadIdx.y;
   if (m >= D.M || c >= L.p) return;
@@ -732,6 +743,7 @@ __global__ void __launch_bounds__(128) k_fill_VW(Dev D, const double* scal) {
 // f_1 = [-u_inc; -du_inc/dn] on Gamma_1 (eq. rokhlin_muller_matrix), f_i = 0.
 __global__ void k_fill_rhs(Dev D) {
   const int i = blockIdx.y;
+  if (!fill_row(D, i)) return;
   const IfaceDesc f = D.ifc[i];
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= f.N) return;

@@ -122,8 +122,8 @@ __global__ void __launch_bounds__(128) k_grad_xi(Dev D, GradVecs V) {
 // MODE 0 (the base blocks at t = 0): rv = u, qy = v.
 // MODE 1 (moved blocks): the layer's part qy^H u + rv^H v.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_grad_lsq(Dev D, GradVecs V) {
-  const int jl = blockIdx.x, a = blockIdx.y;
+__global__ void __launch_bounds__(256) k_grad_lsq(Dev D, GradVecs V, int j0) {
+  const int jl = j0 + blockIdx.x, a = blockIdx.y;
   const LayerDesc L = D.lay[jl];
   const int first = (L.if0 >= 0) ? L.if0 : L.if1;
   const double2* Q = D.QP + a * D.qp_stride + L.qp_off;
@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(256) k_grad_lsq(Dev D, GradVecs V) {
 
 // Per interface i of the context D: mu_i^H (f_i - [A_{i,i-1} A_{i,i} A_{i,i+1}]
 // eta + [B_{i,i} B_{i,i+1}] [zeta_i; zeta_{i+1}]), one thread per row.
-__global__ void __launch_bounds__(256) k_grad_row(Dev D, GradVecs V) {
-  const int i = blockIdx.x, a = blockIdx.y;
+__global__ void __launch_bounds__(256) k_grad_row(Dev D, GradVecs V, int i0) {
+  const int i = i0 + blockIdx.x, a = blockIdx.y;
   const IfaceDesc f = D.ifc[i];
   const double2* A = D.ROW + a * D.r_stride + f.row_off;
   const double2* Bm = D.B + f.b_off;
@@ -183,14 +183,16 @@ __global__ void __launch_bounds__(256) k_grad_row(Dev D, GradVecs V) {
   if (threadIdx.x == 0) V.part[(size_t)a * (D.I + D.L) + i] = acc;
 }
 
-// F of moved context s: the sum of its I + L parts, lane-strided then a
-// fixed-order warp reduction.  One warp per angle.
-__global__ void k_grad_sum(Dev D, GradVecs V, int s) {
+// F of moved context s: the sum of its parts over the window's interfaces
+// [i0, i1) and layers [j0, j1) (all I + L parts for the whole stack),
+// lane-strided then a fixed-order warp reduction.  One warp per angle.
+__global__ void k_grad_sum(Dev D, GradVecs V, int s, int i0, int i1, int j0, int j1) {
   const int a = blockIdx.x, lane = threadIdx.x;
-  const int np = D.I + D.L;
+  const int np = D.I + D.L, ni = i1 - i0, nq = ni + (j1 - j0);
   double sr = 0.0, si = 0.0;
-  for (int q = lane; q < np; q += 32) {
-    const double2 v = V.part[(size_t)a * np + q];
+  for (int q = lane; q < nq; q += 32) {
+    const int part = (q < ni) ? i0 + q : D.I + j0 + (q - ni);
+    const double2 v = V.part[(size_t)a * np + part];
     sr += v.x;
     si += v.y;
   }
@@ -232,16 +234,18 @@ cudaError_t launch_grad_adjoint(const Dev& D, const int* n_host, int* permv, int
 // Q'y and r from the base context's blocks (filled again at t = 0).
 cudaError_t launch_grad_base_lsq(const Dev& D, const GradVecs& V, cudaStream_t s) {
   ++g_launches;
-  k_grad_lsq<0><<<dim3(D.L, D.n_theta), 256, 0, s>>>(D, V);
+  k_grad_lsq<0><<<dim3(D.L, D.n_theta), 256, 0, s>>>(D, V, 0);
   return cudaGetLastError();
 }
 
-// F over the blocks of the moved context Dm, stored as evaluation `slot`.
-cudaError_t launch_grad_form(const Dev& Dm, const GradVecs& V, int slot, cudaStream_t s) {
+// F over the blocks of the moved context Dm in the window win = {first
+// interface, last + 1, first layer, last + 1} (0-based), stored as
+// evaluation `slot`.
+cudaError_t launch_grad_form(const Dev& Dm, const GradVecs& V, int slot, const int* win, cudaStream_t s) {
   g_launches += 3;
-  k_grad_row<<<dim3(Dm.I, Dm.n_theta), 256, 0, s>>>(Dm, V);
-  k_grad_lsq<1><<<dim3(Dm.L, Dm.n_theta), 256, 0, s>>>(Dm, V);
-  k_grad_sum<<<Dm.n_theta, 32, 0, s>>>(Dm, V, slot);
+  k_grad_row<<<dim3(win[1] - win[0], Dm.n_theta), 256, 0, s>>>(Dm, V, win[0]);
+  k_grad_lsq<1><<<dim3(win[3] - win[2], Dm.n_theta), 256, 0, s>>>(Dm, V, win[2]);
+  k_grad_sum<<<Dm.n_theta, 32, 0, s>>>(Dm, V, slot, win[0], win[1], win[2], win[3]);
   return cudaGetLastError();
 }
 

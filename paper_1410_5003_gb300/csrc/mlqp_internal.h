@@ -54,6 +54,41 @@ struct SchurTask {
   int k1, k2;             // inner dimensions (k2 = 0: single term)
 };
 
+// Tensor-core complex products (mlqp_tc.cu).  A job is one output block
+//   out (n x n complex FP32, column-major, interleaved) = beta out - sum_t A_t B_t
+// whose factors were split into operand planes: A_t in X slot xslot[t], B_t
+// in Y slot yslot[t].  A prep entry names a matrix to split into a slot.
+struct TcJob {
+  float* out;
+  int beta;      // 1: out -= product; 0: out = -product
+  int nterm;     // 1 or 2
+  int xslot[2];
+  int yslot[2];
+};
+struct TcPrep {
+  const float* src;
+  long slot;
+};
+// One launch group: its prep lists and jobs (offsets into the device tables).
+struct TcBatch {
+  int x_off, nx, y_off, ny, j_off, nj;
+};
+// Everything the launches of one context need on the host: the TMA tensor
+// maps of the X and Y operand planes (opaque 128-byte CUtensorMap objects,
+// encoded at bind) and the device tables.
+struct TcPlan {
+  alignas(64) unsigned char mx[128];
+  alignas(64) unsigned char my[128];
+  float* xs = nullptr;
+  float* ys = nullptr;
+  const TcJob* jobs = nullptr;
+  const TcPrep* prep = nullptr;
+  int n = 0;
+  int qb = 0;                   // survivors per launch group (cyclic reduction)
+  const TcBatch* batches = nullptr;  // host array, launch order; level k's groups from lvl_first[k]
+  const int* lvl_first = nullptr;    // host array, one entry per level plus one
+};
+
 // Angle groups of the sweep, each on its own stream (forked from and joined
 // back into the context's stream), with a second stream per group for the
 // look-ahead panel factorisations.
@@ -152,12 +187,17 @@ struct Dev {
   double2* AMP;                        // n_theta x 2 nK
   double* FLUX;                        // n_theta
   int* STATUS;
+  // fill window (device, 4 ints): the fill writes only the blocks of interfaces
+  // [FWIN[0], FWIN[1]) and layers [FWIN[2], FWIN[3]); the whole stack except
+  // inside a parameter-local gradient evaluation
+  const int* FWIN;
   const SchurTask* tasks; int n_tasks;
   // launch shapes (host side; set by mlqp_autotune, defaults at bind)
   int qr_cl;      // CTAs per least-squares QR cluster (1..8)
   int cr_cl_max;  // largest cluster of the cyclic-reduction LU (1..8)
   int upd_tile;   // tile edge of the block LU's trailing update (16 or 32)
   int lookahead;  // 1: the next panel factored beside the rest of each trailing update
+  const TcPlan* tc;  // host side: tensor-core products of the cyclic reduction (MLQP_CYCLIC)
 };
 
 // Per-angle vectors of the gradient, carved from the caller's work buffer.

@@ -105,7 +105,11 @@ class BraggEfficiency(torch.autograd.Function):
                     moved = []
                     for mp in probs:
                         moved.append(new_context(mp))
-                gq = float(np.sum(ctx.gradient_eval(moved, step, work)))
+                where = _locality(make_problem(pv), probs)
+                if where is not None and hasattr(ctx, "gradient_eval_local"):
+                    gq = float(np.sum(ctx.gradient_eval_local(moved, step, work, *where)))
+                else:
+                    gq = float(np.sum(ctx.gradient_eval(moved, step, work)))
                 wm = [reflected_weights(mp, orders) for mp in probs]
                 dw = (wm[0] - 8.0 * wm[1] + 8.0 * wm[2] - wm[3]) / (12.0 * step)
                 grad[q] = gq + float(np.sum(dw * np.abs(aU) ** 2))
@@ -131,6 +135,33 @@ class BraggEfficiency(torch.autograd.Function):
             raise err
         dtype, device = fctx.p_meta
         return torch.as_tensor(float(gJ) * grad).to(dtype=dtype, device=device), None, None, None, None, None
+
+
+def _locality(base, probs):
+    """(kind, index) for a parameter whose moved problems differ from base in
+    one interface only (PARAM_INTERFACE, 1-based interface) or in one layer
+    wavenumber only (PARAM_LAYER, 1-based layer); None otherwise (the
+    gradient then fills the whole stack)."""
+    import numpy as np
+    from .mlqp import PARAM_INTERFACE, PARAM_LAYER
+
+    def iface_key(f):
+        return tuple(np.concatenate([[float(f.y0)]] + [np.asarray(getattr(f, nm, []), float).ravel()
+                                                       for nm in ("a", "b", "vx", "vy")]))
+
+    ks, ifs = set(), set()
+    bk = np.asarray(base.k)
+    bi = [iface_key(f) for f in base.ifaces]
+    for pr in probs:
+        if len(pr.ifaces) != len(base.ifaces) or np.shape(pr.k) != np.shape(bk):
+            return None
+        ks.update(int(j) for j in np.nonzero(np.asarray(pr.k) != bk)[0])
+        ifs.update(i for i, f in enumerate(pr.ifaces) if iface_key(f) != bi[i])
+    if len(ks) == 1 and not ifs:
+        return PARAM_LAYER, next(iter(ks)) + 1
+    if len(ifs) == 1 and not ks:
+        return PARAM_INTERFACE, next(iter(ifs)) + 1
+    return None
 
 
 def _agree(distributed, err, what):

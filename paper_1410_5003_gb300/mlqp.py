@@ -20,6 +20,7 @@ MLQP_OK, MLQP_EINVAL, MLQP_ENOMEM, MLQP_ECUDA, MLQP_ESINGULAR, MLQP_ETIMEOUT, ML
 MLQP_FP64, MLQP_MIXED = 0, 1
 MLQP_SWEEP, MLQP_CYCLIC = 0, 1
 MLQP_IR, MLQP_GMRES_IR, MLQP_IR_GMRES = 0, 1, 2
+PARAM_INTERFACE, PARAM_LAYER = 1, 2
 TUNE_QR, TUNE_TILE, TUNE_GROUPS, TUNE_CR, TUNE_LOOKAHEAD, TUNE_ALL = 1, 2, 4, 8, 16, 31
 STAGE_GEOM, STAGE_FILL, STAGE_LSQ, STAGE_SCHUR, STAGE_SWEEP, STAGE_RECOVER = range(6)
 BLK_ROW, BLK_B, BLK_QP, BLK_CP, BLK_X, BLK_RHS, BLK_NODES, BLK_ETA, BLK_AMP, BLK_REFINE = range(10)
@@ -75,6 +76,10 @@ def load(path: str = LIB_PATH):
     lib.mlqp_autotune.restype = I
     lib.mlqp_set_shape.argtypes = [P, I, I]
     lib.mlqp_set_shape.restype = I
+    lib.mlqp_debug_tc_work_bytes.argtypes = [I]
+    lib.mlqp_debug_tc_work_bytes.restype = Z
+    lib.mlqp_debug_tc_cgemm.argtypes = [V, V, V, I, I, V, Z, V]
+    lib.mlqp_debug_tc_cgemm.restype = I
     lib.mlqp_solve_device.argtypes = [P, V, V, V, V]
     lib.mlqp_solve_device.restype = I
     lib.mlqp_solve_rhs.argtypes = [P, V, V]
@@ -93,6 +98,8 @@ def load(path: str = LIB_PATH):
     lib.mlqp_gradient_prepare.restype = I
     lib.mlqp_gradient_eval.argtypes = [P, ct.POINTER(P), D, V, Z, ct.POINTER(D)]
     lib.mlqp_gradient_eval.restype = I
+    lib.mlqp_gradient_eval_local.argtypes = [P, ct.POINTER(P), D, V, Z, I, I, ct.POINTER(D)]
+    lib.mlqp_gradient_eval_local.restype = I
     lib.mlqp_check_device.argtypes = [P]
     lib.mlqp_check_device.restype = I
     lib.mlqp_solve.argtypes = [P, V, V, V, V]
@@ -121,10 +128,11 @@ EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "ml
             "mlqp_autotune", "mlqp_set_shape",
             "mlqp_solve_rhs", "mlqp_adjoint_solve", "mlqp_lsq_adjoint", "mlqp_x_elements",
             "mlqp_gradient_work_bytes", "mlqp_fd_gradient", "mlqp_gradient_prepare", "mlqp_gradient_eval",
+            "mlqp_gradient_eval_local",
             "mlqp_solve_device",
             "mlqp_check_device", "mlqp_solve", "mlqp_run_stage", "mlqp_block_info", "mlqp_last_error",
             "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes",
-            "mlqp_lsq_solve_noalloc"]
+            "mlqp_lsq_solve_noalloc", "mlqp_debug_tc_work_bytes", "mlqp_debug_tc_cgemm"]
 
 
 def _check(ctx, st):
@@ -392,6 +400,19 @@ class Context:
                                                          ct.c_void_p(wp), nb, _dptr(out)))
         return out
 
+    def gradient_eval_local(self, moved, t, work, kind, index):
+        """mlqp_gradient_eval_local: gradient_eval for a parameter that moves
+        only interface `index` (kind PARAM_INTERFACE) or the wavenumber of
+        layer `index` (PARAM_LAYER), filling only the blocks it moves."""
+        _, wp, nb, _ = work
+        arr = (ct.c_void_p * 4)(*[m.ctx for m in moved])
+        out = np.zeros(self.n_theta)
+        with self.torch.cuda.stream(self.stream):
+            _check(self.ctx, self.lib.mlqp_gradient_eval_local(self.ctx, ct.cast(arr, ct.POINTER(ct.c_void_p)),
+                                                               float(t), ct.c_void_p(wp), nb, int(kind), int(index),
+                                                               _dptr(out)))
+        return out
+
     def host_outputs(self, eta=False, pinned=False):
         t = self.torch
         mk = lambda shape, dt: t.empty(shape, dtype=dt, pin_memory=pinned)
@@ -435,6 +456,25 @@ class Context:
         nbytes = 16 * ld.value * c.value
         v = self.ws[start:start + nbytes].view(t.complex128).view(c.value, ld.value)
         return v[:, :r.value].transpose(0, 1)
+
+
+def tc_cgemm(A, B, C, beta):
+    """mlqp_debug_tc_cgemm: C = beta C - A B on the tensor cores, for square
+    complex64 CUDA tensors (any torch layout; the library sees them
+    column-major).  Returns the new C."""
+    import torch
+    lib = load()
+    n = A.shape[0]
+    col = lambda M: M.t().contiguous()  # noqa: E731 -- column-major storage of M
+    a, b, c = col(A), col(B), col(C)
+    nb = int(lib.mlqp_debug_tc_work_bytes(n))
+    work = torch.empty(nb + 256, dtype=torch.uint8, device=A.device)
+    wp = work.data_ptr() + (-work.data_ptr()) % 256
+    st = lib.mlqp_debug_tc_cgemm(ct.c_void_p(a.data_ptr()), ct.c_void_p(b.data_ptr()), ct.c_void_p(c.data_ptr()), n,
+                                 int(beta), ct.c_void_p(wp), nb, ct.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != MLQP_OK:
+        raise MlqpError(st, "mlqp_debug_tc_cgemm")
+    return c.t()
 
 
 def hankel_eval(k, rho, device="cuda"):

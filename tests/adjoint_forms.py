@@ -91,6 +91,10 @@ class OracleContext:
         probs = [m.prob for m in moved]
         return np.array([forms_gradient(self.prob, a, work[a], probs, t) for a in range(self.prob.n_theta)])
 
+    def gradient_eval_local(self, moved, t, work, kind, index):
+        self.local_evals = getattr(self, "local_evals", 0) + 1
+        return self.gradient_eval(moved, t, work)
+
     def set_problem(self, prob):
         self.prob = prob
         self.factored = False

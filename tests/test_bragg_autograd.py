@@ -43,6 +43,8 @@ def test_bragg_efficiency_value_and_gradient_on_the_oracle():
     assert len(made) == 5 and all(c.closed for c in made)
     assert all(getattr(c, "moves", 0) == len(names) - 1 for c in made[1:])
     assert made[0].prepares == 1  # one solve and one set of sensitivities for all five parameters
+    # each of the five moves one layer wavenumber or one interface: all evaluated locally
+    assert made[0].local_evals == len(names)
     # a forward pass that needs no gradient releases its context at once
     made.clear()
     with torch.no_grad():
@@ -88,3 +90,29 @@ def test_reflected_weights_vanish_for_evanescent_and_grazing_orders():
     kap = k1 * math.cos(th_w) + 2 * math.pi / d
     assert w[0, K + 1] == 0.0 or k1 * k1 - kap * kap <= 1e-12 * k1 * k1
     assert w[1, K + 8] == 0.0 and w[1, K - 8] == 0.0  # evanescent at |n| = 8
+
+
+def test_parameter_locality_is_read_from_the_moved_problems():
+    """The autograd path evaluates a parameter locally (only the blocks near
+    it) when its moved problems differ from the base in one layer wavenumber
+    or one interface, and over the whole stack otherwise."""
+    from paper_1410_5003_gb300.diff import _locality
+    from paper_1410_5003_gb300.mlqp import PARAM_INTERFACE, PARAM_LAYER
+    prob, make_problem, _, _ = gradient_family()
+
+    def moved(q):
+        out = []
+        for s_ in (-2, -1, 1, 2):
+            if q == 5:  # two parameters at once
+                pv = np.array([0, 0, s_ * 1e-3, s_ * 1e-3, 0])
+            else:
+                pv = np.zeros(5)
+                pv[q] = s_ * 1e-3
+            out.append(make_problem(pv))
+        return out
+
+    assert _locality(prob, moved(0)) == (PARAM_LAYER, 1)
+    assert _locality(prob, moved(2)) == (PARAM_LAYER, 3)
+    assert _locality(prob, moved(3)) == (PARAM_INTERFACE, 1)
+    assert _locality(prob, moved(4)) == (PARAM_INTERFACE, 2)
+    assert _locality(prob, moved(5)) is None

@@ -597,6 +597,59 @@ def test_corner_grating_at_full_size(M):
     assert rel(ag, np.concatenate([ref["aU"][0], ref["aD"][0]])) < AMP_TOL
 
 
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"{name}_amplitudes.json")
+    with open(path) as f:
+        g = json.load(f)
+    amp = lambda key: np.array([[complex(*z) for z in row] for row in g[key]])  # noqa: E731
+    return g, amp("aU"), amp("aD")
+
+
+def test_corner_grating_amplitudes_against_the_stored_oracle(M):
+    """The 1000-interface corner grating (512 000 unknowns, one angle) end to
+    end against the oracle's amplitudes stored in tests/golden (written by
+    tests/golden/make_golden.py, oracle only): plain FP64, the mixed form
+    with the block sweep and with cyclic reduction (tensor-core Schur
+    updates), each within 1e-9 relative (max over the 2(2K+1) orders); the
+    flux errors agree with the oracle's to 1e-9."""
+    g, aU, aD = _golden("config3")
+    prob = config3()
+    assert g["I"] == prob.I and g["K"] == prob.params.K and abs(g["theta"][0] - prob.theta[0]) < 1e-15
+    ref = np.concatenate([aU[0], aD[0]])
+    for kw in ({}, dict(precision=M.MLQP_MIXED), dict(precision=M.MLQP_MIXED, block_solver=M.MLQP_CYCLIC)):
+        ctx = M.Context(prob, **kw)
+        out = ctx.solve_host()
+        ctx.close()
+        torch.cuda.empty_cache()
+        got = np.concatenate([out["aU"][0], out["aD"][0]])
+        assert rel(got, ref) < AMP_TOL, (kw, rel(got, ref))
+        assert abs(out["flux"][0] - g["flux"][0]) < 1e-9, (kw, out["flux"][0], g["flux"][0])
+
+
+def test_angle_sweep_amplitudes_against_the_stored_oracle(M):
+    """The angle-sweep stack at its resolved discretisation (100 interfaces,
+    node counts 160-512, P = 100, M_w = 50, K = 40; 72 480 unknowns per
+    angle) at every eighth of its 256 angles, end to end against the
+    oracle's stored amplitudes: plain FP64 and the mixed form (default
+    refinement), within 1e-9 relative at every angle."""
+    g, aU, aD = _golden("config4r")
+    prob = config4(resolved=True)
+    th = np.asarray(prob.theta)[g["angles"]]
+    assert np.allclose(th, g["theta"], rtol=0, atol=1e-15)
+    sub = prob.with_angles(th)
+    ref = np.concatenate([aU, aD], axis=1)
+    for kw in ({}, dict(precision=M.MLQP_MIXED)):
+        ctx = M.Context(sub, **kw)
+        out = ctx.solve_host()
+        ctx.close()
+        torch.cuda.empty_cache()
+        got = np.concatenate([out["aU"], out["aD"]], axis=1)
+        errs = [rel(got[a], ref[a]) for a in range(len(th))]
+        assert max(errs) < AMP_TOL, (kw, max(errs), int(np.argmax(errs)))
+
+
 def test_angle_sweep_stack_blocks_at_full_size(M):
     """The 100-interface angle-sweep stack at full size (N_i from 80 to 320,
     uneven), two of its angles: sampled blocks (interfaces 1, 50, 100 with
@@ -803,6 +856,73 @@ def test_fd_gradient_against_the_oracle(M):
     ctx.set_angles(prob.theta)  # new angles: the prepared sensitivities no longer apply
     with pytest.raises(M.MlqpError):
         ctx.gradient_eval(moved, t, work)
+    for m in moved:
+        m.close()
+    ctx.close()
+
+
+def test_local_gradient_evaluation_matches_the_whole_stack(M):
+    """mlqp_gradient_eval_local fills and contracts only the blocks a
+    parameter moves (interface i: block rows i-1..i+1, layers i, i+1; layer
+    wavenumber k_j: rows j-1, j, layer j; k_1: everything).  On a 4-interface
+    stack it gives mlqp_gradient_eval's gradient to 1e-9 for shape
+    coefficients of an inner, the top and the bottom interface and for the
+    wavenumbers of an inner, the bottom and the top layer; the moved contexts
+    solve afterwards exactly as fresh ones do (their fill covers the whole
+    stack again); moved problems that change more than the named parameter
+    are refused."""
+    from dataclasses import replace
+    base = small_stack(I=4, N=40, P=40, Mw=24, K=8, M=30, n_angles=2)
+    prob = replace(base, params=replace(base.params, lsq_rcond=1e-6)).with_angles([-0.9, -2.1])
+    t = 1e-3
+
+    def shape(i, m, delta):
+        ifs = list(prob.ifaces)
+        f = ifs[i]
+        a = f.a.copy()
+        a[m] += delta
+        ifs[i] = Interface(f.y0, a, f.b.copy(), f.N)
+        return replace(prob, ifaces=ifs)
+
+    def wavenumber(j, delta):
+        k = prob.k.copy()
+        k[j] += delta
+        return replace(prob, k=k)
+
+    params = [(M.PARAM_INTERFACE, 2, lambda d: shape(1, 0, d)), (M.PARAM_INTERFACE, 1, lambda d: shape(0, 1, d)),
+              (M.PARAM_INTERFACE, 4, lambda d: shape(3, 2, d)), (M.PARAM_LAYER, 3, lambda d: wavenumber(2, d)),
+              (M.PARAM_LAYER, 5, lambda d: wavenumber(4, d)), (M.PARAM_LAYER, 1, lambda d: wavenumber(0, d))]
+    ctx = M.Context(prob)
+    res = ctx.solve_host()
+    K = prob.params.K
+    g = np.zeros((prob.n_theta, 2 * K + 1), np.complex128)
+    for a in range(prob.n_theta):
+        th = float(prob.theta[a])
+        g[a] = O.reflected_weights(prob, th, O.bloch(prob, th)) * res["aU"][a]
+    work = ctx.gradient_prepare(g)
+    moved = None
+    for kind, index, make in params:
+        probs = [make(s_ * t) for s_ in (-2, -1, 1, 2)]
+        if moved is None:
+            moved = [M.Context(mp) for mp in probs]
+        else:
+            for m, mp in zip(moved, probs):
+                m.set_problem(mp)
+        full = ctx.gradient_eval(moved, t, work)
+        local = ctx.gradient_eval_local(moved, t, work, kind, index)
+        assert rel(local, full) < 1e-9, (kind, index, local, full)
+    # after a local evaluation the moved contexts fill the whole stack again
+    again = moved[0].solve_host()
+    fresh = M.Context(moved[0].prob)
+    ref = fresh.solve_host()
+    fresh.close()
+    assert np.array_equal(again["aU"], ref["aU"]) and np.array_equal(again["aD"], ref["aD"])
+    # moved problems that change an interface other than the named one are refused
+    for m, mp in zip(moved, [shape(1, 0, s_ * t) for s_ in (-2, -1, 1, 2)]):
+        m.set_problem(mp)
+    with pytest.raises(M.MlqpError) as e:
+        ctx.gradient_eval_local(moved, t, work, M.PARAM_INTERFACE, 3)
+    assert e.value.status == M.MLQP_EINVAL
     for m in moved:
         m.close()
     ctx.close()
