@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--leg-steps", type=int, default=5,
                     help="timed steps of the mixed legs, e2e and the small leg (at most --steps)")
     ap.add_argument("--no-small", action="store_true", help="skip the 20-interface leg")
+    ap.add_argument("--lookahead", type=int, choices=[0, 1], default=None,
+                    help="with --no-autotune: the block LU's look-ahead shape (default 0)")
     ap.add_argument("--gradient", action="store_true",
                     help="also time mlqp_fd_gradient on the 20-interface stack (one shape parameter)")
     ap.add_argument("--config5", action="store_true",
@@ -489,7 +491,7 @@ def angle_sweep(mlqp, dev, chunk=32):
 # proportion to the interfaces: every interface's sweep step touches the same
 # sizes); None until captured for the current kernels.
 SWEEP_TRAFFIC_BYTES_PER_INTERFACE = 43.59e6
-SWEEP_TRAFFIC_SHAPES = {"qr_cluster": 8, "angle_groups": 1, "update_tile": 16, "lookahead": 0}
+SWEEP_TRAFFIC_SHAPES = {"angle_groups": 1, "update_tile": 16, "lookahead": 0}  # the shapes the sweep depends on
 SWEEP_TRAFFIC_NOTE = ("DRAM bytes read + written by the sweep kernels per step: 43.6 MB per interface from one ncu "
                       "capture of the first 40 interfaces (launch shapes SWEEP_TRAFFIC_SHAPES), times the interfaces")
 
@@ -601,8 +603,11 @@ def main():
 
     ctx = mlqp.Context(prob, device=dev)
     # launch shapes timed on this problem (untimed setup)
-    tuned = ctx.autotune() if not args.no_autotune else {"qr_cluster": 8, "angle_groups": 1, "update_tile": 16,
-                                                         "lookahead": 0}
+    if args.no_autotune:
+        tuned = {"qr_cluster": 8, "angle_groups": 1, "update_tile": 16, "lookahead": args.lookahead or 0}
+        ctx.set_shape(mlqp.TUNE_LOOKAHEAD, tuned["lookahead"])
+    else:
+        tuned = ctx.autotune()
     out = ctx.outputs()
     ctx.solve_device(out)  # the one-graph solve (e2e below) captured outside the timed region
     # warm-up in the timed loop's own form: the stage graphs are captured here, not in a timed step
