@@ -17,8 +17,9 @@
 // row-major so that K is contiguous; k_tc_prep_y: Y_hi, Y_lo) and then read
 // by TMA.  k_tc_cgemm is warp-specialised: warp 0 issues the TMA loads of a
 // stage (four 128 x 32 tiles), warp 1 the 12 tcgen05.mma of a stage into one
-// 128 x 128 FP32 accumulator in tensor memory, warps 2-5 read the accumulator
-// (tcgen05.ld) and update C.  A three-stage mbarrier ring couples them.
+// of four 128 x 128 FP32 accumulators in tensor memory (stage s into s mod
+// 4), warps 2-5 read and sum the accumulators (tcgen05.ld) and update C.  A
+// three-stage mbarrier ring couples them.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -38,6 +39,7 @@ constexpr int TC_BN = 128;   // columns of Out per tile
 constexpr int TC_BK = 32;    // FP32 values of K per stage (one 128-byte row)
 constexpr int TC_STAGES = 3;
 constexpr int TC_THREADS = 192;
+constexpr int TC_NACC = 4;  // accumulators in tensor memory (stage s into s mod 4), summed in the epilogue
 constexpr uint32_t TC_TILE = TC_BM * TC_BK * 4;  // 16 KB (X and Y tiles alike: TC_BN == TC_BM)
 constexpr uint32_t TC_STAGE = 4 * TC_TILE;       // X_hi, X_lo, Y_hi, Y_lo
 constexpr size_t TC_SMEM = TC_STAGES * TC_STAGE + 1024 + 256;
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_prefetch_tmap(&my);
   }
   if (warp == 1) {
-    tc_tmem_alloc(tslot, TC_BN);
+    tc_tmem_alloc(tslot, TC_NACC * TC_BN);
     tc_tmem_relinquish();
   }
   tc_fence_before();
@@ -170,14 +172,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t sa = tc_smem(base + (size_t)s * TC_STAGE);
+        // stage it accumulates into accumulator it mod TC_NACC: shorter sums per
+        // accumulator, whose rounding inside the tensor core then grows less
+        const uint32_t acc = tmem + static_cast<uint32_t>((it % TC_NACC) * TC_BN);
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 8; ++kk) {
           const uint64_t xh = tc_desc_sw128(sa + kk * 32), xl = tc_desc_sw128(sa + TC_TILE + kk * 32);
           const uint64_t yh = tc_desc_sw128(sa + 2 * TC_TILE + kk * 32);
           const uint64_t yl = tc_desc_sw128(sa + 3 * TC_TILE + kk * 32);
-          tc_mma_tf32(tmem, xh, yh, idesc, (it > 0 || kk > 0) ? 1u : 0u);
-          tc_mma_tf32(tmem, xh, yl, idesc, 1u);
-          tc_mma_tf32(tmem, xl, yh, idesc, 1u);
+          tc_mma_tf32(acc, xh, yh, idesc, (it >= TC_NACC || kk > 0) ? 1u : 0u);
+          tc_mma_tf32(acc, xh, yl, idesc, 1u);
+          tc_mma_tf32(acc, xl, yh, idesc, 1u);
         }
         tc_commit(&empty[s]);  // the stage's shared memory is free once these products are done
       }
@@ -191,10 +196,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int q = warp & 3;
       const int m = m0 + 32 * q + lane;
       float* out = job.out;
+      const int nacc = iters < TC_NACC ? iters : TC_NACC;  // accumulators written
 #pragma unroll 1
       for (int ch = 0; ch < TC_BN / 16; ++ch) {
-        float v[16];
-        tc_tmem_ld16(tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(ch * 16), v);
+        float v[16], w[16];
+        const uint32_t ta = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(ch * 16);
+        tc_tmem_ld16(ta, v);
+        for (int x = 1; x < nacc; ++x) {
+          tc_tmem_ld16(ta + static_cast<uint32_t>(x * TC_BN), w);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] += w[j];
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int c = c0 + ch * 16 + j;
@@ -211,7 +223,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tc_tmem_dealloc(tmem, TC_BN);
+    tc_tmem_dealloc(tmem, TC_NACC * TC_BN);
   }
 }
 
