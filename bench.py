@@ -491,9 +491,14 @@ def angle_sweep(mlqp, dev, chunk=32):
 # proportion to the interfaces: every interface's sweep step touches the same
 # sizes); None until captured for the current kernels.
 SWEEP_TRAFFIC_BYTES_PER_INTERFACE = 43.59e6
-SWEEP_TRAFFIC_SHAPES = {"angle_groups": 1, "update_tile": 16, "lookahead": 0}  # the shapes the sweep depends on
+SWEEP_TRAFFIC_SHAPES = {"angle_groups": 1, "lookahead": 0}  # the shapes the FP64 sweep depends on
 SWEEP_TRAFFIC_NOTE = ("DRAM bytes read + written by the sweep kernels per step: 43.6 MB per interface from one ncu "
                       "capture of the first 40 interfaces (launch shapes SWEEP_TRAFFIC_SHAPES), times the interfaces")
+
+
+def shape(v):
+    """A launch shape as an int, None where it does not apply (NaN)."""
+    return None if v is None or v != v else int(v)
 
 
 def timed_solves(mlqp, ctx, steps, flush, stages):
@@ -604,7 +609,7 @@ def main():
     ctx = mlqp.Context(prob, device=dev)
     # launch shapes timed on this problem (untimed setup)
     if args.no_autotune:
-        tuned = {"qr_cluster": 8, "angle_groups": 1, "update_tile": 16, "lookahead": args.lookahead or 0}
+        tuned = {"qr_cluster": 8, "angle_groups": 1, "update_tile": None, "lookahead": args.lookahead or 0}
         ctx.set_shape(mlqp.TUNE_LOOKAHEAD, tuned["lookahead"])
     else:
         tuned = ctx.autotune()
@@ -638,7 +643,7 @@ def main():
         sw_flops = nth * sweep_flops(n)
         achieved = sw_flops / (stage_ms["sweep"] / 1e3) / 1e12
         peak = FP64_PEAK_GFLOPS / 1e3
-        shapes_as_captured = all(int(tuned.get(k, -1)) == v for k, v in SWEEP_TRAFFIC_SHAPES.items())
+        shapes_as_captured = all(shape(tuned.get(k)) == v for k, v in SWEEP_TRAFFIC_SHAPES.items())
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K,
                 "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -647,10 +652,10 @@ def main():
                            "nodes_per_interface": int(prob.ifaces[0].N), "unknowns_per_angle": int(sum(n)),
                            "l2": "flushed between steps (256 MB write); the working set (about 25 GB of blocks) "
                                  "is far larger than L2",
-                           "launch_shapes": {"qr_cluster": int(tuned["qr_cluster"]),
-                                             "angle_groups": int(tuned["angle_groups"]),
-                                             "update_tile": int(tuned.get("update_tile", 16)),
-                                             "lookahead": int(tuned.get("lookahead", 0)),
+                           "launch_shapes": {"qr_cluster": shape(tuned["qr_cluster"]),
+                                             "angle_groups": shape(tuned["angle_groups"]),
+                                             "update_tile": shape(tuned.get("update_tile")),
+                                             "lookahead": shape(tuned.get("lookahead")),
                                              "source": "defaults" if args.no_autotune else "mlqp_autotune"}},
                 "flux_error": flux, "meets_flux_gate_1e-9": flux <= 1e-9,
                 "stage_ms": stage_ms, "dominant_stage": max(stage_ms, key=stage_ms.get),
@@ -694,7 +699,7 @@ def main():
                "flux_error": float(mout["flux"].abs().max()),
                "max_rel_amp_diff_vs_fp64": rel_amp_diff(mout, out), "gpu_launches": mlaunch,
                "block_solver": "sweep" if solver == mlqp.MLQP_SWEEP else "cyclic reduction",
-               "launch_shapes": {k: (None if v != v else int(v)) for k, v in mtuned.items()
+               "launch_shapes": {k: shape(v) for k, v in mtuned.items()
                                  if k in ("qr_cluster", "angle_groups", "cr_cluster_cap", "update_tile",
                                           "lookahead")},
                "dtype": "f32 Schur/LU + f64 refinement (fill, least squares, residuals in f64)"}

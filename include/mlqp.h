@@ -310,8 +310,9 @@ mlqp_status mlqp_set_problem(mlqp_ctx* ctx, const mlqp_interface* ifaces, int I,
  * own problem (each timed stage preceded by the stages it depends on, so
  * this costs several solves): the CTAs per least-squares QR cluster (1, 2,
  * 4, 8), the number of angle groups (streams) of the block solve (1 to
- * min(n_theta, 4)), the tile edge of the block LU's trailing update (16 or
- * 32; not with MLQP_CYCLIC), look-ahead in the block LU (off or on: the
+ * min(n_theta, 4)), the tile edge of the FP32 block LU's trailing update
+ * (16 or 32; MLQP_MIXED with MLQP_SWEEP only: the FP64 update runs on the
+ * tensor cores in fixed 64 x 64 tiles), look-ahead in the block LU (off or on: the
  * next panel factored on a second stream beside the rest of each trailing
  * update, its CTAs reserving their SMs; not with MLQP_CYCLIC) and, with
  * MLQP_CYCLIC, the largest cluster of the cyclic-reduction LU (1, 2, 4, 8).  which selects them (MLQP_TUNE_*
@@ -385,6 +386,17 @@ mlqp_status mlqp_debug_hankel(const double* d_krho, int n, double* d_out, void* 
 size_t mlqp_debug_tc_work_bytes(int n);
 mlqp_status mlqp_debug_tc_cgemm(const void* d_A, const void* d_B, void* d_C, int n, int beta, void* d_work,
                                 size_t work_bytes, void* stream);
+
+/* Test hook for the FP64 tensor-core update of the block LU (the error-free
+ * split of each operand row / column into seven 8-bit digit slices of Ozaki
+ * et al., Numer. Algorithms 59 (2012), multiplied as BF16 on tcgen05 tensor
+ * cores with exact FP32 sums, recombined in integers and FP64):
+ * C -= A B for complex128 column-major device blocks A (rows x K, lda),
+ * B (K x cols, ldb), C (rows x cols, ldc), 1 <= K <= 16, all 16-byte aligned.
+ * d_work: 16 bytes of device memory (status).  Synchronous.  Errors:
+ * MLQP_EINVAL, MLQP_ECUDA, MLQP_ETIMEOUT. */
+mlqp_status mlqp_debug_oz_update(const void* d_A, int lda, const void* d_B, int ldb, void* d_C, int ldc, int rows,
+                                 int cols, int K, void* d_work, void* stream);
 
 /* Bytes of the problem description mlqp_bind copies host -> device. */
 size_t mlqp_upload_bytes(const mlqp_ctx* ctx);

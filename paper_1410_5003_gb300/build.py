@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libmlqp.so")
 SOURCES = ["mlqp_api.cu", "mlqp_fill.cu", "mlqp_lsq.cu", "mlqp_sweep.cu", "mlqp_mixed.cu", "mlqp_cyclic.cu", "mlqp_lsq_noalloc.cu",
-           "mlqp_adjoint.cu", "mlqp_grad.cu", "mlqp_tc.cu"]
+           "mlqp_adjoint.cu", "mlqp_grad.cu", "mlqp_tc.cu", "mlqp_oz.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -999,10 +999,10 @@ mlqp_status mlqp_autotune(mlqp_ctx* c, int which, double* report, int report_len
     c->qr_cl = best;
     rep[0] = best;
   }
-  // 2. tile edge of the block LU's trailing update (the sweep's, or the FP32
-  //    factorisation's in the mixed form)
-  if (st == MLQP_OK && (which & MLQP_TUNE_TILE) &&
-      !(c->prm.precision == MLQP_MIXED && c->prm.block_solver == MLQP_CYCLIC)) {
+  // 2. tile edge of the FP32 block LU's trailing update (the mixed form's
+  //    factorisation; the FP64 sweep's update runs on the tensor cores)
+  if (st == MLQP_OK && (which & MLQP_TUNE_TILE) && c->prm.precision == MLQP_MIXED &&
+      c->prm.block_solver != MLQP_CYCLIC) {  // the FP64 update runs on the tensor cores in fixed tiles
     const int cand[2] = {16, 32};
     int best = c->upd_tile;
     double tb = INFINITY;

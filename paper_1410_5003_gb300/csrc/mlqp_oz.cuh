@@ -1,0 +1,299 @@
+// FP64 complex rank-K updates (K <= 16) on the tensor cores by an error-free
+// split of the operands into 8-bit integer digits (the splitting of Ozaki,
+// Ogita, Oishi and Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59 (2012)), with BF16 tcgen05 products.
+//
+//   C[v, u] -= sum_k L[v, k] U[k, u]      (complex FP64; v, u over a 64 x 64 tile)
+//
+// The complex product is one real product Out = X Y of the 2 x 2 real
+// embedding X of L (X[2v, 2k] = Re L, X[2v, 2k+1] = -Im L, X[2v+1, 2k] = Im L,
+// X[2v+1, 2k+1] = Re L) and Y[2k + q, u] = (Re U, Im U)[q], so Out[2v + p, u]
+// is the real (p = 0) or imaginary (p = 1) part of (L U)[v, u]; K' = 2K <= 32.
+//
+// Each row m of X is written as 2^(e_m - 56) sum_s d_s 2^(56 - 8 s), s = 1..7,
+// with integer digits |d_s| <= 255 (e_m: |X[m, :]| < 2^e_m), and each column u
+// of Y likewise with f_u and digits d'_t.  A digit is exact in BF16, a digit
+// product (< 2^16) and a sum over K' <= 32 of them (< 2^21) exact in FP32, and
+// so is the sum of the up to 8 products of one level l = s + t - 2 (< 2^24):
+// one FP32 accumulator in tensor memory per level, l = 0..7 (s + t <= 9; the
+// dropped pairs weigh at most 2^-53 of the largest term).  The epilogue turns
+// each accumulator into an integer, combines the levels in 64-bit integers
+// (unit 2^(e_m + f_u - 48)), rounds the result into a double and applies it
+// with one FP64 subtraction per real entry of C, where a direct complex
+// rank-16 update does about 24 FP64 operations.  The split keeps 56 bits of every entry
+// relative to its row's (column's) largest, so the result carries FP64
+// accuracy relative to sum_k |L||U|.
+//
+// One CTA (256 threads) per 64 x 64 complex tile: threads 0..127 split one
+// row of X each and threads 128..191 one column of Y each into shared memory,
+// in the 128-byte-swizzled K-major layout (two slices per 128-byte row);
+// thread 0 issues the 72 tcgen05.mma kind::f16 (BF16) products into the eight
+// accumulators (8 x 64 columns of tensor memory); then every thread reads
+// half of its TMEM lane (Out row m, 32 columns) and updates those entries of
+// C, whose loads it issues before the accumulator reads.  The combination
+// runs in integers and the scaling into a double by integer operations: the
+// FP64 pipe does one subtraction per real entry.  The geometry G maps
+// (v, k), (k, u), (v, u) to the operands and C, and filters the outputs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mlqp_tc.cuh"
+
+namespace mlqp {
+
+constexpr int OZ_TILE = 64;       // complex rows and columns of C per CTA
+constexpr int OZ_THREADS = 256;   // two per row of Out (2 x 64 rows, 2 halves of the columns)
+constexpr int OZ_SLICES = 7;
+constexpr int OZ_LEVELS = 8;      // l = s + t - 2 for s + t <= 9
+constexpr uint32_t OZ_XTILE = 128 * 128;   // bytes of one pair of X slices (128 rows x 128 bytes)
+constexpr uint32_t OZ_YTILE = 64 * 128;    // bytes of one pair of Y slices (64 rows x 128 bytes)
+constexpr size_t OZ_SMEM = 4 * OZ_XTILE + 4 * OZ_YTILE + 1024 + 1024;
+// 120 KB of dynamic shared memory keeps one CTA per SM: its 512 tensor-memory
+// columns are then never contended.
+constexpr size_t OZ_SMEM_LAUNCH = 120 * 1024;
+constexpr int OZ_TIMEOUT_CODE = 5;  // MLQP_ETIMEOUT
+
+// Instruction descriptor of tcgen05.mma kind::f16 with BF16 A and B (bits
+// 7-9, 10-12 = 1), FP32 accumulator (bits 4-5 = 1), both K-major, N / 8 in
+// bits 17-22, M / 16 in bits 24-28.
+__host__ __device__ constexpr uint32_t oz_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void oz_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Generic-proxy writes to shared memory, made visible to the tensor core.
+__device__ __forceinline__ void oz_fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Biased exponent field of x (0 for zero and subnormals).
+__device__ __forceinline__ int oz_expo(double x) {
+  return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7FF);
+}
+
+// |x| 2^(56 - e) as an integer, e = emax - 1022 where emax is the largest
+// biased exponent of the row: the 53-bit significand shifted by
+// (biased exponent - emax + 3) <= 3 bits (entries far below the row's largest
+// lose their bits under 2^(e - 56)).
+__device__ __forceinline__ unsigned long long oz_fixed(double x, int emax) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = static_cast<int>((b >> 52) & 0x7FF);
+  if (E == 0) return 0ull;
+  const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const int sh = E - emax + 3;
+  if (sh >= 0) return M << sh;
+  return (sh <= -53) ? 0ull : (M >> (-sh));
+}
+
+// Writes the 7 digit slices of 32 values (one row of X or column of Y) into
+// the slice-pair tiles at `base` (row r of tiles of `tile_bytes`), 128-byte
+// swizzle: 16-byte chunk c of row r at chunk c ^ (r mod 8).
+__device__ __forceinline__ void oz_store_digits(unsigned char* base, uint32_t tile_bytes, int r, const double* val,
+                                                int emax) {
+  unsigned long long q[32];
+  uint32_t neg = 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    q[i] = oz_fixed(val[i], emax);
+    neg |= static_cast<uint32_t>(static_cast<unsigned long long>(__double_as_longlong(val[i])) >> 63) << i;
+  }
+#pragma unroll
+  for (int s = 1; s <= OZ_SLICES; ++s) {
+    const int idx = s - 1, tile = idx >> 1, half = idx & 1;
+    unsigned char* row = base + (size_t)tile * tile_bytes + (size_t)r * 128;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {  // 4 chunks of 8 BF16 (K' = 8c .. 8c + 7)
+      uint32_t w[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        uint32_t pair = 0;
+#pragma unroll
+        for (int e2 = 0; e2 < 2; ++e2) {
+          const int i = 8 * c + 2 * h + e2;
+          const int d = static_cast<int>((q[i] >> (56 - 8 * s)) & 0xFFull);
+          const float f = static_cast<float>((neg >> i) & 1u ? -d : d);  // exact: |d| <= 255
+          pair |= (__float_as_uint(f) >> 16) << (16 * e2);
+        }
+        w[h] = pair;
+      }
+      const int chunk = (half * 4 + c) ^ (r & 7);
+      *reinterpret_cast<uint4*>(row + chunk * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// tot 2^sc as the nearest double (ties to even) by integer operations only
+// (normalise, round the 64-bit magnitude to 53 bits, set the exponent field);
+// ok = false if the result would leave the normal range (the caller then
+// takes the FP64 route).
+__device__ __forceinline__ double oz_i2d(long long tot, int sc, bool& ok) {
+  if (tot == 0) return 0.0;
+  const unsigned long long neg = tot < 0 ? 1ull : 0ull;
+  const unsigned long long a = neg ? static_cast<unsigned long long>(-tot) : static_cast<unsigned long long>(tot);
+  const int lz = __clzll(static_cast<long long>(a));
+  const unsigned long long an = a << lz;
+  unsigned long long mant = an >> 11;
+  const unsigned long long rem = an & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;
+  int e = (63 - lz) + sc + 1023;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++e;
+  }
+  if (e <= 0 || e >= 2047) {
+    ok = false;
+    return 0.0;
+  }
+  return __longlong_as_double(
+      static_cast<long long>((neg << 63) | (static_cast<unsigned long long>(e) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+__device__ __forceinline__ double oz_neg(double x) {  // sign flip without the FP64 pipe
+  return __longlong_as_double(__double_as_longlong(x) ^ static_cast<long long>(0x8000000000000000ull));
+}
+
+template <class G>
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(G g, int* status) {
+  extern __shared__ unsigned char oz_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  unsigned char* xs = base;
+  unsigned char* ys = base + 4 * OZ_XTILE;
+  int* fexp = reinterpret_cast<int*>(ys + 4 * OZ_YTILE);   // 64 column exponents
+  int* eexp = fexp + OZ_TILE;                               // 128 row exponents
+  uint64_t* done = reinterpret_cast<uint64_t*>(eexp + 2 * OZ_TILE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (!g.setup()) return;  // uniform: the whole tile lies outside the block
+  const int v0 = g.v0(), u0 = g.u0();
+  if (tid == 0) {
+    tc_bar_init(done, 1);
+    tc_fence_bar_init();
+  }
+  if (warp == 0) {
+    tc_tmem_alloc(tslot, OZ_LEVELS * OZ_TILE);
+    tc_tmem_relinquish();
+  }
+  const int m = tid & 127, vl = m >> 1, p = m & 1, half = tid >> 7;
+  if (half == 0) {  // one row of X: Out row m = 2 (v - v0) + p
+    double val[32];
+    const int v = v0 + vl;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const double2 a = g.a(v, k);
+      val[2 * k] = p ? a.y : a.x;
+      val[2 * k + 1] = p ? a.x : oz_neg(a.y);
+    }
+    int emax = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) emax = max(emax, oz_expo(val[i]));
+    oz_store_digits(xs, OZ_XTILE, m, val, emax);
+    eexp[m] = emax;
+  } else if (m < OZ_TILE) {  // one column of Y
+    double val[32];
+    const int u = u0 + m;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const double2 b = g.b(k, u);
+      val[2 * k] = b.x;
+      val[2 * k + 1] = b.y;
+    }
+    int emax = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) emax = max(emax, oz_expo(val[i]));
+    oz_store_digits(ys, OZ_YTILE, m, val, emax);
+    fexp[m] = emax;
+  }
+  oz_fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    const uint32_t idesc = oz_idesc_bf16(2 * OZ_TILE, OZ_TILE);
+    const uint32_t xa = tc_smem(xs), ya = tc_smem(ys);
+    uint32_t started = 0;
+    for (int s = 1; s <= OZ_SLICES; ++s)
+      for (int t = 1; t <= OZ_SLICES && s + t <= 9; ++t) {
+        const int l = s + t - 2;
+        const uint32_t xo = xa + ((s - 1) >> 1) * OZ_XTILE + ((s - 1) & 1) * 64;
+        const uint32_t yo = ya + ((t - 1) >> 1) * OZ_YTILE + ((t - 1) & 1) * 64;
+        const uint32_t acc = tmem + static_cast<uint32_t>(l * OZ_TILE);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {  // K' = 32 as two K = 16 steps, 32 bytes apart
+          oz_mma_bf16(acc, tc_desc_sw128(xo + ks * 32), tc_desc_sw128(yo + ks * 32), idesc,
+                      ((started >> l) & 1u) ? 1u : 0u);
+          started |= 1u << l;
+        }
+      }
+    tc_commit(done);
+  }
+  // the epilogue: Out row m (TMEM lane m), columns half * 32 .. half * 32 + 31
+  const int v = v0 + vl;
+  const int emax_x = eexp[m];
+  bool ok = tc_wait(done, 0);
+  ok = __all_sync(0xffffffffu, ok);
+  tc_fence_after();
+  if (ok) {
+    const uint32_t lane_addr = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+#pragma unroll 1
+    for (int ch = 0; ch < 2; ++ch) {
+      const int c0 = half * 32 + ch * 16;  // local column of this chunk
+      // the chunk's entries of C first: their latency overlaps the accumulator reads
+      double cv[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) cv[j] = g.keep(v, u0 + c0 + j) ? *g.ptr(v, u0 + c0 + j, p) : 0.0;
+      long long V[16], T[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) V[j] = T[j] = 0;
+#pragma unroll 1
+      for (int l = 0; l < OZ_LEVELS; ++l) {
+        float a[16];
+        tc_tmem_ld16(lane_addr + static_cast<uint32_t>(l * OZ_TILE + c0), a);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const long long iv = static_cast<long long>(__float2int_rn(a[j]));
+          if (l <= 4) V[j] += iv * (1LL << (32 - 8 * l));
+          else T[j] += iv * (1LL << (8 * (7 - l)));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int u = u0 + c0 + j;
+        if (!g.keep(v, u)) continue;
+        // unit 2^(e + f - 48) with e = emax_x - 1022, f = fexp - 1022
+        const int sc = emax_x + fexp[c0 + j] - 2044 - 48;
+        const long long tot = V[j] + (T[j] >> 24);
+        bool fine = true;
+        double d = oz_i2d(tot, sc, fine);
+        if (!fine) {  // outside one power of two's normal range: two factors
+          const int h1 = sc / 2, h2 = sc - h1;
+          d = (static_cast<double>(tot) * __longlong_as_double((long long)(h1 + 1023) << 52)) *
+              __longlong_as_double((long long)(h2 + 1023) << 52);
+        }
+        *g.ptr(v, u, p) = cv[j] - d;
+      }
+    }
+  }
+  if (!ok && tid == 0) atomicExch(status, OZ_TIMEOUT_CODE);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tc_tmem_dealloc(tmem, OZ_LEVELS * OZ_TILE);
+  }
+}
+
+}  // namespace mlqp

@@ -31,6 +31,7 @@
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
 #include "mlqp_trsv.cuh"
+#include "mlqp_oz.cuh"
 
 namespace mlqp {
 
@@ -534,6 +535,77 @@ __global__ void __launch_bounds__(UpdShape<UTT>::TH) k_lu_update(Dev D, int t, i
 }
 
 // ---------------------------------------------------------------------------
+// The FP64 trailing update on the tensor cores (mlqp_oz.cuh): the same rows,
+// columns, operands and look-ahead modes as k_lu_update, in 64 x 64 tiles.
+// ---------------------------------------------------------------------------
+struct OzSweep {
+  Dev D;
+  int t, k, a0, mode, wn;
+  double2 *top, *ftop, *bot;
+  double2* fbot;
+  int ldt, ldb, nlt, nt, nb, w, tr, nrows, ncols, v0_, u0_;
+  __device__ bool setup() {
+    const int a = a0 + blockIdx.y;
+    const Step S = make_step(D, t);
+    const IfaceDesc ft = D.ifc[t];
+    nt = S.nt;
+    nb = S.nb;
+    nlt = S.nlt;
+    w = min(NB, nt - k);
+    tr = nt - k - w;
+    nrows = (mode == 1) ? tr : tr + nb;
+    ncols = tr + nb + 1;
+    const int tiles_c = (mode == 1) ? 1 : (ncols + OZ_TILE - 1) / OZ_TILE;
+    v0_ = (blockIdx.x / tiles_c) * OZ_TILE;
+    u0_ = (blockIdx.x % tiles_c) * OZ_TILE;
+    if (v0_ >= nrows) return false;
+    top = D.ROW + a * D.r_stride + ft.row_off;
+    ftop = D.F + a * D.f_stride + ft.rhs_off;
+    bot = fbot = nullptr;
+    if (S.b >= 0) {
+      const IfaceDesc fb = D.ifc[S.b];
+      bot = D.ROW + a * D.r_stride + fb.row_off;
+      fbot = D.F + a * D.f_stride + fb.rhs_off;
+    }
+    ldt = nt;
+    ldb = nb;
+    return true;
+  }
+  __device__ int v0() const { return v0_; }
+  __device__ int u0() const { return u0_; }
+  __device__ double2 a(int v, int kk) const {
+    if (v >= nrows || kk >= w) return make_double2(0.0, 0.0);
+    if (v < tr) return top[(size_t)(nlt + k + kk) * ldt + k + w + v];
+    return bot[(size_t)(k + kk) * ldb + (v - tr)];
+  }
+  __device__ double2 b(int kk, int u) const {
+    if (u >= ncols || kk >= w) return make_double2(0.0, 0.0);
+    const int row = k + kk;
+    if (u < tr) return top[(size_t)(nlt + k + w + u) * ldt + row];
+    if (u < tr + nb) return top[(size_t)(nlt + nt + (u - tr)) * ldt + row];
+    return ftop[row];
+  }
+  __device__ bool keep(int v, int u) const {
+    if (v >= nrows || u >= ncols) return false;
+    const bool next_block = v < tr && u < wn;
+    return mode == 0 || (mode == 1) == next_block;
+  }
+  __device__ double* ptr(int v, int u, int p) const {
+    double2* c;
+    if (v < tr) {
+      const int row = k + w + v;
+      c = (u < tr) ? top + (size_t)(nlt + k + w + u) * ldt + row
+                   : (u < tr + nb) ? top + (size_t)(nlt + nt + (u - tr)) * ldt + row : ftop + row;
+    } else {
+      const int row = v - tr;
+      c = (u < tr) ? bot + (size_t)(k + w + u) * ldb + row
+                   : (u < tr + nb) ? bot + (size_t)(nt + (u - tr)) * ldb + row : fbot + row;
+    }
+    return reinterpret_cast<double*>(c) + p;
+  }
+};
+
+// ---------------------------------------------------------------------------
 // Backward sweep: y = g_t - U12_t eta_{t+1} (one row per warp, lanes over the
 // columns, shuffle reduction); U_t eta_t = y by blocks of 32 rows from the
 // bottom: one warp solves the 32 x 32 diagonal block (lane = row, pivot
@@ -622,12 +694,34 @@ __global__ void __launch_bounds__(128) k_recover(Dev D) {
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+// Trailing update of panel k (mode 0: everything; look-ahead: mode 1 the next
+// panel's columns of the top rows, mode 2 the rest), tr trailing top rows,
+// nb bottom rows, na angles from a0.  FP32 (the mixed form's factorisation):
+// k_lu_update's square tiles of edge ut.  FP64: the tensor-core update
+// (k_oz_update) in 64 x 64 tiles.
 template <typename R>
-static void launch_update(const Dev& D, int ut, dim3 grid, cudaStream_t s, int t, int k, int a0, int mode, int wn) {
-  if (ut == 16)
-    k_lu_update<R, 16><<<grid, UpdShape<16>::TH, 0, s>>>(D, t, k, a0, mode, wn);
-  else
-    k_lu_update<R, 32><<<grid, UpdShape<32>::TH, 0, s>>>(D, t, k, a0, mode, wn);
+static void launch_update(const Dev& D, int ut, int tr, int nb, int na, cudaStream_t s, int t, int k, int a0,
+                          int mode, int wn) {
+  const int nrows = (mode == 1) ? tr : tr + nb, ncols = tr + nb + 1;
+  if constexpr (sizeof(R) == 8) {
+    const int tc = (mode == 1) ? 1 : (ncols + OZ_TILE - 1) / OZ_TILE;
+    OzSweep g{};
+    g.D = D;
+    g.t = t;
+    g.k = k;
+    g.a0 = a0;
+    g.mode = mode;
+    g.wn = wn;
+    k_oz_update<OzSweep><<<dim3(((nrows + OZ_TILE - 1) / OZ_TILE) * tc, na), OZ_THREADS, OZ_SMEM_LAUNCH, s>>>(
+        g, D.STATUS);
+  } else {
+    const int tc = (mode == 1) ? 1 : (ncols + ut - 1) / ut;
+    const dim3 grid(((nrows + ut - 1) / ut) * tc, na);
+    if (ut == 16)
+      k_lu_update<R, 16><<<grid, UpdShape<16>::TH, 0, s>>>(D, t, k, a0, mode, wn);
+    else
+      k_lu_update<R, 32><<<grid, UpdShape<32>::TH, 0, s>>>(D, t, k, a0, mode, wn);
+  }
 }
 
 // The block LU of the forward sweep, in precision R (FP64: plain path on ROW/F;
@@ -671,18 +765,18 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
         // the panel stream beside the rest of this update
         const int wn = (nt - k2 < NB) ? nt - k2 : NB;
         ++g_launches;
-        launch_update<R>(D, UT, dim3((tr + UT - 1) / UT, na), s, t, k, a0, 1, wn);
+        launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 1, wn);
         if ((e = cudaEventRecord(ev_next, s)) != cudaSuccess) break;
         if ((e = cudaStreamWaitEvent(ps, ev_next, 0)) != cudaSuccess) break;
         panel(k2, ps);
         if ((e = cudaEventRecord(ev_panel, ps)) != cudaSuccess) break;
         ++g_launches;
-        launch_update<R>(D, UT, dim3(tiles, na), s, t, k, a0, 2, wn);
+        launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 2, wn);
         e = cudaStreamWaitEvent(s, ev_panel, 0);
       } else {
         if (nrows > 0) {
           ++g_launches;
-          launch_update<R>(D, UT, dim3(tiles, na), s, t, k, a0, 0, 0);
+          launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 0, 0);
         }
         if (k2 < nt) panel(k2, s);
       }
@@ -752,6 +846,8 @@ cudaError_t sweep_configure(int maxn) {
   cudaError_t e = cudaFuncSetAttribute(k_lu_panel_cl<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_lu_panel_cl<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_oz_update<OzSweep>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM_LAUNCH);
   return e;
 }
 

@@ -80,6 +80,8 @@ def load(path: str = LIB_PATH):
     lib.mlqp_debug_tc_work_bytes.restype = Z
     lib.mlqp_debug_tc_cgemm.argtypes = [V, V, V, I, I, V, Z, V]
     lib.mlqp_debug_tc_cgemm.restype = I
+    lib.mlqp_debug_oz_update.argtypes = [V, I, V, I, V, I, I, I, I, V, V]
+    lib.mlqp_debug_oz_update.restype = I
     lib.mlqp_solve_device.argtypes = [P, V, V, V, V]
     lib.mlqp_solve_device.restype = I
     lib.mlqp_solve_rhs.argtypes = [P, V, V]
@@ -132,7 +134,8 @@ EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "ml
             "mlqp_solve_device",
             "mlqp_check_device", "mlqp_solve", "mlqp_run_stage", "mlqp_block_info", "mlqp_last_error",
             "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes",
-            "mlqp_lsq_solve_noalloc", "mlqp_debug_tc_work_bytes", "mlqp_debug_tc_cgemm"]
+            "mlqp_lsq_solve_noalloc", "mlqp_debug_tc_work_bytes", "mlqp_debug_tc_cgemm",
+            "mlqp_debug_oz_update"]
 
 
 def _check(ctx, st):
@@ -474,6 +477,24 @@ def tc_cgemm(A, B, C, beta):
                                  int(beta), ct.c_void_p(wp), nb, ct.c_void_p(torch.cuda.current_stream().cuda_stream))
     if st != MLQP_OK:
         raise MlqpError(st, "mlqp_debug_tc_cgemm")
+    return c.t()
+
+
+def oz_update(A, B, C):
+    """mlqp_debug_oz_update: C - A B (complex128 CUDA tensors; A rows x K,
+    B K x cols, K <= 16) by the FP64 tensor-core update of the block LU."""
+    import torch
+    lib = load()
+    rows, K = A.shape
+    cols = B.shape[1]
+    col = lambda M: M.t().contiguous()  # noqa: E731 -- column-major storage of M
+    a, b, c = col(A), col(B), col(C)
+    work = torch.zeros(4, dtype=torch.int32, device=A.device)
+    st = lib.mlqp_debug_oz_update(ct.c_void_p(a.data_ptr()), rows, ct.c_void_p(b.data_ptr()), K,
+                                  ct.c_void_p(c.data_ptr()), rows, rows, cols, K, ct.c_void_p(work.data_ptr()),
+                                  ct.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != MLQP_OK:
+        raise MlqpError(st, "mlqp_debug_oz_update")
     return c.t()
 
 

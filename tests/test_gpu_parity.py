@@ -528,7 +528,7 @@ def test_autotune_keeps_results_bitwise(M, form):
         assert rep["cr_cluster_cap"] in (1, 2, 4, 8) and math.isnan(rep["update_tile"])
         assert math.isnan(rep["lookahead"])
     else:
-        assert math.isnan(rep["cr_cluster_cap"]) and rep["update_tile"] in (16, 32)
+        assert math.isnan(rep["cr_cluster_cap"]) and math.isnan(rep["update_tile"])  # FP64: tensor-core update
         assert rep["lookahead"] in (0, 1) and all(t > 0 for t in rep["sweep_ms_by_lookahead"].values())
     r1 = ctx.solve_host()
     ctx.close()

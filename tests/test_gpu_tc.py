@@ -35,3 +35,24 @@ def test_tc_complex_product_matches_complex128(M, n, beta):
         scale = float((A.abs().to(torch.float64) @ B.abs().to(torch.float64)).max())
         err = float((out - ref).abs().max()) / scale
         assert err < 3e-7 * np.sqrt(2 * n), (n, beta, call, err)
+
+
+@pytest.mark.parametrize("rows,cols,K", [(64, 64, 16), (100, 130, 16), (700, 513, 16), (257, 65, 5)])
+def test_fp64_tensor_core_update_matches_complex128(M, rows, cols, K):
+    """The block LU's FP64 trailing update on the tensor cores (seven 8-bit
+    digit slices per operand row / column, BF16 products with exact FP32
+    sums): C - A B against complex128, to 4e-16 of max (|A||B|) times the
+    inner dimension, the size of FP64 rounding over the sum.  One row of A
+    spans 1e-12 .. 1 and one column of B contains zeros, and the tiles are
+    ragged against the 64 x 64 output tiles."""
+    g = torch.Generator(device="cpu").manual_seed(rows + cols + K)
+    mk = lambda r, c: torch.complex(torch.randn(r, c, generator=g, dtype=torch.float64),  # noqa: E731
+                                    torch.randn(r, c, generator=g, dtype=torch.float64))
+    A, B, C = mk(rows, K), mk(K, cols), mk(rows, cols)
+    A[3] *= torch.logspace(-12, 0, K, dtype=torch.float64)
+    B[:, 2] = 0
+    ref = C - A @ B
+    out = M.oz_update(A.cuda(), B.cuda(), C.cuda()).cpu()
+    scale = float((A.abs() @ B.abs()).max())
+    err = float((out - ref).abs().max()) / scale
+    assert err < 4e-16 * 2 * K, (rows, cols, K, err)
