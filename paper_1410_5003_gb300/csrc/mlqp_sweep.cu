@@ -698,11 +698,18 @@ __global__ void __launch_bounds__(128) k_recover(Dev D) {
 // panel's columns of the top rows, mode 2 the rest), tr trailing top rows,
 // nb bottom rows, na angles from a0.  FP32 (the mixed form's factorisation):
 // k_lu_update's square tiles of edge ut.  FP64: the tensor-core update
-// (k_oz_update) in 64 x 64 tiles.
+// (k_oz_update) in 64 x 64 tiles, except the next panel's columns (mode 1),
+// which k_lu_update does in FP64 on the SIMT pipe: a narrow update whose
+// latency, not its work, matters, on the critical path to the next panel.
 template <typename R>
 static void launch_update(const Dev& D, int ut, int tr, int nb, int na, cudaStream_t s, int t, int k, int a0,
                           int mode, int wn) {
   const int nrows = (mode == 1) ? tr : tr + nb, ncols = tr + nb + 1;
+  if (sizeof(R) == 8 && mode == 1) {  // the next panel's columns: a narrow update, FP64 on the SIMT pipe
+    const dim3 grid((tr + 15) / 16, na);
+    k_lu_update<R, 16><<<grid, UpdShape<16>::TH, 0, s>>>(D, t, k, a0, 1, wn);
+    return;
+  }
   if constexpr (sizeof(R) == 8) {
     const int tc = (mode == 1) ? 1 : (ncols + OZ_TILE - 1) / OZ_TILE;
     OzSweep g{};
@@ -775,8 +782,17 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
         e = cudaStreamWaitEvent(s, ev_panel, 0);
       } else {
         if (nrows > 0) {
-          ++g_launches;
-          launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 0, 0);
+          if (sizeof(R) == 8 && k2 < nt) {
+            // FP64: the next panel's columns by the narrow update, the rest on the
+            // tensor cores, as with look-ahead (so both give the same bits)
+            const int wn = (nt - k2 < NB) ? nt - k2 : NB;
+            g_launches += 2;
+            launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 1, wn);
+            launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 2, wn);
+          } else {
+            ++g_launches;
+            launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 0, 0);
+          }
         }
         if (k2 < nt) panel(k2, s);
       }
