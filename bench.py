@@ -486,13 +486,13 @@ def angle_sweep(mlqp, dev, chunk=32):
 
 
 # DRAM bytes (read + write) of the sweep kernels (k_lu_panel_cl, k_lu_prep,
-# k_lu_update, k_back_*) per interface of the corner grating, from one ncu
+# k_oz_update, k_lu_update, k_back_*) per interface of the corner grating, from one ncu
 # capture of a shorter stack of the same interfaces (traffic grows in
 # proportion to the interfaces: every interface's sweep step touches the same
 # sizes); None until captured for the current kernels.
-SWEEP_TRAFFIC_BYTES_PER_INTERFACE = 43.59e6
-SWEEP_TRAFFIC_SHAPES = {"angle_groups": 1, "lookahead": 0}  # the shapes the FP64 sweep depends on
-SWEEP_TRAFFIC_NOTE = ("DRAM bytes read + written by the sweep kernels per step: 43.6 MB per interface from one ncu "
+SWEEP_TRAFFIC_BYTES_PER_INTERFACE = 37.45e6
+SWEEP_TRAFFIC_SHAPES = {"angle_groups": 1, "lookahead": 1}  # the shapes the FP64 sweep depends on
+SWEEP_TRAFFIC_NOTE = ("DRAM bytes read + written by the sweep kernels per step: 37.4 MB per interface from one ncu "
                       "capture of the first 40 interfaces (launch shapes SWEEP_TRAFFIC_SHAPES), times the interfaces")
 
 
@@ -660,7 +660,7 @@ def main():
                 "flux_error": flux, "meets_flux_gate_1e-9": flux <= 1e-9,
                 "stage_ms": stage_ms, "dominant_stage": max(stage_ms, key=stage_ms.get),
                 "roofline": {"bound": "alu", "kernel": "block-tridiagonal sweep (k_lu_panel_cl, k_lu_prep, "
-                                                      "k_lu_update, k_back_*), one stage of the step",
+                                                      "k_oz_update, k_lu_update, k_back_*), one stage of the step",
                              "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                              "traffic": SWEEP_TRAFFIC_BYTES_PER_INTERFACE * prob.I * nth if shapes_as_captured
                              else None,
@@ -669,7 +669,10 @@ def main():
                              "algorithmic_flops_per_step": sw_flops,
                              "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived from the "
                                           "unit counts and the maximum SM clock; MEASURED_PEAKS.json has no FP64 "
-                                          "figure; a probe measured 1.20 TFLOP/s at 1995 MHz)"},
+                                          "figure; a probe measured 1.20 TFLOP/s at 1995 MHz). achieved counts the FP64 "
+                                          "flops of the complex block LU, including the trailing updates that "
+                                          "k_oz_update runs on the BF16 tensor cores by the error-free digit split: "
+                                          "an FP64-equivalent rate"},
                 "gpu_launches": launches, "outputs_finite": ok,
                 "schur_tflops": nth * schur_flops(n, prob.params.P) / (stage_ms["schur"] / 1e3) / 1e12}
         if clocks:

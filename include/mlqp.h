@@ -392,7 +392,9 @@ mlqp_status mlqp_debug_tc_cgemm(const void* d_A, const void* d_B, void* d_C, int
  * et al., Numer. Algorithms 59 (2012), multiplied as BF16 on tcgen05 tensor
  * cores with exact FP32 sums, recombined in integers and FP64):
  * C -= A B for complex128 column-major device blocks A (rows x K, lda),
- * B (K x cols, ldb), C (rows x cols, ldc), 1 <= K <= 16, all 16-byte aligned.
+ * B (K x cols, ldb), C (rows x cols, ldc), all 16-byte aligned; 1 <= K <= 16
+ * by the block LU's update kernel, 16 < K <= 128 by the chunked kernel of
+ * the Schur updates.
  * d_work: 16 bytes of device memory (status).  Synchronous.  Errors:
  * MLQP_EINVAL, MLQP_ECUDA, MLQP_ETIMEOUT. */
 mlqp_status mlqp_debug_oz_update(const void* d_A, int lda, const void* d_B, int ldb, void* d_C, int ldc, int rows,

@@ -15,6 +15,7 @@
 
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
+#include "mlqp_oz.cuh"
 
 namespace mlqp {
 
@@ -335,94 +336,43 @@ __global__ void __launch_bounds__(WY_THREADS) k_lsq_trsm(Dev D) {
 }
 
 // ---------------------------------------------------------------------------
-// Batched Schur updates C -= A1 B1 (+ A2 B2), complex FP64 with 3M products:
-//   Cr -= (Ar Br - Ai Bi),  Ci -= ((Ar + Ai)(Br + Bi) - Ar Br - Ai Bi)
-// 64 x 64 output tile per CTA, inner chunks of 16, 4 x 4 outputs per thread.
+// Batched Schur updates C -= A1 B1 (+ A2 B2) (eqs. Schur1-Schuri), complex
+// FP64 on the tensor cores (k_oz_gemm, mlqp_oz.cuh: the error-free 8-bit
+// digit split, one scale per row of A over both terms and per column of B):
+// one 64 x 64 output tile per CTA; blockIdx.y = task, blockIdx.z = angle.
 // ---------------------------------------------------------------------------
-constexpr int GT = 64, GK = 16;
+constexpr int GT = 64;
+static_assert(GT == OZ_TILE, "Schur tiles are the tensor-core tiles");
 
-__device__ __forceinline__ void gemm3m_accumulate(const double2* __restrict__ A, int lda,
-                                                  const double2* __restrict__ B, int ldb, int K,
-                                                  int row0, int col0, int rows, int cols,
-                                                  double t1[4][4], double t2[4][4], double t3[4][4],
-                                                  double (*As)[3][GT], double (*Bs)[3][GT]) {
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    // A tile: GT rows x GK k
-    for (int e = tid; e < GT * GK; e += 256) {
-      const int r = e % GT, kk = e / GT;
-      double2 v = make_double2(0.0, 0.0);
-      if (row0 + r < rows && k0 + kk < K) v = A[(size_t)(k0 + kk) * lda + row0 + r];
-      As[kk][0][r] = v.x;
-      As[kk][1][r] = v.y;
-      As[kk][2][r] = v.x + v.y;
-    }
-    // B tile: GK k x GT cols
-    for (int e = tid; e < GT * GK; e += 256) {
-      const int kk = e % GK, c = e / GK;
-      double2 v = make_double2(0.0, 0.0);
-      if (col0 + c < cols && k0 + kk < K) v = B[(size_t)(col0 + c) * ldb + k0 + kk];
-      Bs[kk][0][c] = v.x;
-      Bs[kk][1][c] = v.y;
-      Bs[kk][2][c] = v.x + v.y;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < GK; ++kk) {
-      double ar[4], ai[4], as[4], br[4], bi[4], bs[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        ar[u] = As[kk][0][ty * 4 + u];
-        ai[u] = As[kk][1][ty * 4 + u];
-        as[u] = As[kk][2][ty * 4 + u];
-        br[u] = Bs[kk][0][tx * 4 + u];
-        bi[u] = Bs[kk][1][tx * 4 + u];
-        bs[u] = Bs[kk][2][tx * 4 + u];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          t1[u][w] = fma(ar[u], br[w], t1[u][w]);
-          t2[u][w] = fma(ai[u], bi[w], t2[u][w]);
-          t3[u][w] = fma(as[u], bs[w], t3[u][w]);
-        }
-    }
-    __syncthreads();
+struct OzSchur {
+  Dev D;
+  SchurTask T;
+  int ang, v0_, u0_;
+  __device__ bool setup() {
+    T = D.tasks[blockIdx.y];
+    ang = blockIdx.z;
+    const int tiles_c = (T.cols + GT - 1) / GT;
+    v0_ = (blockIdx.x / tiles_c) * GT;
+    u0_ = (blockIdx.x % tiles_c) * GT;
+    return v0_ < T.rows;
   }
-}
-
-__global__ void __launch_bounds__(256) k_schur(Dev D) {
-  const SchurTask T = D.tasks[blockIdx.y];
-  const int a = blockIdx.z;
-  const int tiles_c = (T.cols + GT - 1) / GT;
-  const int tr = blockIdx.x / tiles_c, tc = blockIdx.x % tiles_c;
-  if (tr * GT >= T.rows) return;
-  __shared__ double As[GK][3][GT];
-  __shared__ double Bs[GK][3][GT];
-  double t1[4][4] = {}, t2[4][4] = {}, t3[4][4] = {};
-  const int row0 = tr * GT, col0 = tc * GT;
-  gemm3m_accumulate(D.B + T.a1_off, T.lda1, D.Xb + a * D.x_stride + T.b1_off, T.ldb1, T.k1, row0, col0,
-                    T.rows, T.cols, t1, t2, t3, As, Bs);
-  if (T.k2 > 0)
-    gemm3m_accumulate(D.B + T.a2_off, T.lda2, D.Xb + a * D.x_stride + T.b2_off, T.ldb2, T.k2, row0, col0,
-                      T.rows, T.cols, t1, t2, t3, As, Bs);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double2* Cb = D.ROW + a * D.r_stride + T.c_off;
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const int r = row0 + ty * 4 + u, c = col0 + tx * 4 + w;
-      if (r < T.rows && c < T.cols) {
-        double2* p = Cb + (size_t)c * T.ldc + r;
-        double2 v = *p;
-        v.x -= t1[u][w] - t2[u][w];
-        v.y -= t3[u][w] - t1[u][w] - t2[u][w];
-        *p = v;
-      }
-    }
-}
+  __device__ int v0() const { return v0_; }
+  __device__ int u0() const { return u0_; }
+  __device__ int nk() const { return T.k1 + T.k2; }
+  __device__ double2 a(int v, int k) const {
+    if (v >= T.rows) return make_double2(0.0, 0.0);
+    return (k < T.k1) ? D.B[T.a1_off + (size_t)k * T.lda1 + v] : D.B[T.a2_off + (size_t)(k - T.k1) * T.lda2 + v];
+  }
+  __device__ double2 b(int k, int u) const {
+    if (u >= T.cols) return make_double2(0.0, 0.0);
+    const double2* X = D.Xb + ang * D.x_stride;
+    return (k < T.k1) ? X[T.b1_off + (size_t)u * T.ldb1 + k] : X[T.b2_off + (size_t)u * T.ldb2 + (k - T.k1)];
+  }
+  __device__ bool keep(int v, int u) const { return v < T.rows && u < T.cols; }
+  __device__ double* ptr(int v, int u, int p) const {
+    return reinterpret_cast<double*>(D.ROW + ang * D.r_stride + T.c_off + (size_t)u * T.ldc + v) + p;
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Adjoint of the regularised least squares (Sec. 3.2): Y_j = (Q'^H Q' +
@@ -546,13 +496,17 @@ cudaError_t lsq_configure(int max_m, int max_p) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_lsq_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((size_t)max_p * WYB * sizeof(double2)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_oz_gemm<OzSchur>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM_LAUNCH);
   return e;
 }
 
 cudaError_t launch_schur(const Dev& D, int max_tiles, cudaStream_t s) {
   if (D.n_tasks == 0) return cudaSuccess;
   ++g_launches;
-  k_schur<<<dim3(max_tiles, D.n_tasks, D.n_theta), 256, 0, s>>>(D);
+  OzSchur g{};
+  g.D = D;
+  k_oz_gemm<OzSchur><<<dim3(max_tiles, D.n_tasks, D.n_theta), OZ_THREADS, OZ_SMEM_LAUNCH, s>>>(g, D.STATUS);
   return cudaGetLastError();
 }
 

@@ -296,4 +296,160 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(G g, int* status) {
   }
 }
 
+// The same product over a longer inner dimension, C -= sum_k A[v, k] B[k, u]
+// with K = G::nk() complex (two terms of the Schur updates, up to 2 x 64):
+// every row of the embedding of A and every column of B gets one scale over
+// the whole K, the digits of each chunk of 16 complex k (K' = 32) are
+// multiplied into the eight level accumulators as in k_oz_update, and after
+// each chunk every thread adds its lane's levels, as integers in the common
+// unit, into 64-bit sums; C is read and written once at the end.
+template <class G>
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(G g, int* status) {
+  extern __shared__ unsigned char oz_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  unsigned char* xs = base;
+  unsigned char* ys = base + 4 * OZ_XTILE;
+  int* fexp = reinterpret_cast<int*>(ys + 4 * OZ_YTILE);
+  int* eexp = fexp + OZ_TILE;
+  uint64_t* done = reinterpret_cast<uint64_t*>(eexp + 2 * OZ_TILE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (!g.setup()) return;
+  const int v0 = g.v0(), u0 = g.u0(), nk = g.nk(), nch = (nk + 15) / 16;
+  if (tid == 0) {
+    tc_bar_init(done, 1);
+    tc_fence_bar_init();
+  }
+  if (warp == 0) {
+    tc_tmem_alloc(tslot, OZ_LEVELS * OZ_TILE);
+    tc_tmem_relinquish();
+  }
+  const int m = tid & 127, vl = m >> 1, p = m & 1, half = tid >> 7;
+  const int v = v0 + vl;
+  // the scales: largest exponent of each row (column) over the whole K
+  if (half == 0) {
+    int emax = 0;
+    for (int k = 0; k < nk; ++k) {
+      const double2 a = g.a(v, k);
+      emax = max(emax, max(oz_expo(a.x), oz_expo(a.y)));
+    }
+    eexp[m] = emax;
+  } else if (m < OZ_TILE) {
+    int emax = 0;
+    for (int k = 0; k < nk; ++k) {
+      const double2 b = g.b(k, u0 + m);
+      emax = max(emax, max(oz_expo(b.x), oz_expo(b.y)));
+    }
+    fexp[m] = emax;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int emax_x = eexp[m];
+  long long V[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) V[j] = 0;
+  bool ok = true;
+  for (int ch = 0; ch < nch && ok; ++ch) {
+    const int kc = 16 * ch;
+    if (half == 0) {
+      double val[32];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const double2 a = (kc + k < nk) ? g.a(v, kc + k) : make_double2(0.0, 0.0);
+        val[2 * k] = p ? a.y : a.x;
+        val[2 * k + 1] = p ? a.x : oz_neg(a.y);
+      }
+      oz_store_digits(xs, OZ_XTILE, m, val, emax_x);
+    } else if (m < OZ_TILE) {
+      double val[32];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const double2 b = (kc + k < nk) ? g.b(kc + k, u0 + m) : make_double2(0.0, 0.0);
+        val[2 * k] = b.x;
+        val[2 * k + 1] = b.y;
+      }
+      oz_store_digits(ys, OZ_YTILE, m, val, fexp[m]);
+    }
+    oz_fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      const uint32_t idesc = oz_idesc_bf16(2 * OZ_TILE, OZ_TILE);
+      const uint32_t xa = tc_smem(xs), ya = tc_smem(ys);
+      uint32_t started = 0;
+      for (int s = 1; s <= OZ_SLICES; ++s)
+        for (int t = 1; t <= OZ_SLICES && s + t <= 9; ++t) {
+          const int l = s + t - 2;
+          const uint32_t xo = xa + ((s - 1) >> 1) * OZ_XTILE + ((s - 1) & 1) * 64;
+          const uint32_t yo = ya + ((t - 1) >> 1) * OZ_YTILE + ((t - 1) & 1) * 64;
+          const uint32_t acc = tmem + static_cast<uint32_t>(l * OZ_TILE);
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            oz_mma_bf16(acc, tc_desc_sw128(xo + ks * 32), tc_desc_sw128(yo + ks * 32), idesc,
+                        ((started >> l) & 1u) ? 1u : 0u);
+            started |= 1u << l;
+          }
+        }
+      tc_commit(done);
+    }
+    ok = tc_wait(done, static_cast<uint32_t>(ch & 1));
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    if (ok) {
+      const uint32_t lane_addr = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+#pragma unroll
+      for (int sub = 0; sub < 2; ++sub) {
+        long long T[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) T[j] = 0;
+#pragma unroll 1
+        for (int l = 0; l < OZ_LEVELS; ++l) {
+          float a[16];
+          tc_tmem_ld16(lane_addr + static_cast<uint32_t>(l * OZ_TILE + half * 32 + sub * 16), a);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const long long iv = static_cast<long long>(__float2int_rn(a[j]));
+            if (l <= 4) V[sub * 16 + j] += iv * (1LL << (32 - 8 * l));
+            else T[j] += iv * (1LL << (8 * (7 - l)));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) V[sub * 16 + j] += T[j] >> 24;
+      }
+    }
+    // the accumulators and the operand tiles are reused by the next chunk
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  if (ok) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int u = u0 + half * 32 + j;
+      if (!g.keep(v, u)) continue;
+      const int sc = emax_x + fexp[half * 32 + j] - 2044 - 48;
+      bool fine = true;
+      double d = oz_i2d(V[j], sc, fine);
+      if (!fine) {
+        const int h1 = sc / 2, h2 = sc - h1;
+        d = (static_cast<double>(V[j]) * __longlong_as_double((long long)(h1 + 1023) << 52)) *
+            __longlong_as_double((long long)(h2 + 1023) << 52);
+      }
+      double* c = g.ptr(v, u, p);
+      *c = *c - d;
+    }
+  }
+  if (!ok && tid == 0) atomicExch(status, OZ_TIMEOUT_CODE);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tc_tmem_dealloc(tmem, OZ_LEVELS * OZ_TILE);
+  }
+}
+
 }  // namespace mlqp

@@ -37,12 +37,15 @@ def test_tc_complex_product_matches_complex128(M, n, beta):
         assert err < 3e-7 * np.sqrt(2 * n), (n, beta, call, err)
 
 
-@pytest.mark.parametrize("rows,cols,K", [(64, 64, 16), (100, 130, 16), (700, 513, 16), (257, 65, 5)])
+@pytest.mark.parametrize("rows,cols,K", [(64, 64, 16), (100, 130, 16), (700, 513, 16), (257, 65, 5),
+                                         (512, 512, 60), (300, 170, 120)])
 def test_fp64_tensor_core_update_matches_complex128(M, rows, cols, K):
-    """The block LU's FP64 trailing update on the tensor cores (seven 8-bit
-    digit slices per operand row / column, BF16 products with exact FP32
-    sums): C - A B against complex128, to 4e-16 of max (|A||B|) times the
-    inner dimension, the size of FP64 rounding over the sum.  One row of A
+    """The FP64 products on the tensor cores (seven 8-bit digit slices per
+    operand row / column, BF16 products with exact FP32 sums): the block
+    LU's rank-16 update (K <= 16) and the Schur updates' chunked product
+    (K = 60 and 120, one scale per row and column over all of K): C - A B
+    against complex128, to 4e-16 of max (|A||B|) times the inner dimension,
+    the size of FP64 rounding over the sum.  One row of A
     spans 1e-12 .. 1 and one column of B contains zeros, and the tiles are
     ragged against the 64 x 64 output tiles."""
     g = torch.Generator(device="cpu").manual_seed(rows + cols + K)
