@@ -321,7 +321,6 @@ def design_gradient(mlqp, dev, n_check=20, h=1e-6, rcond=1e-8):
     from dataclasses import replace
     import numpy as np
     import torch
-    from paper_1410_5003_gb300.diff import reflected_weights
     from workloads import config5
     from workloads.problems import Interface
     base = config5()
@@ -351,13 +350,13 @@ def design_gradient(mlqp, dev, n_check=20, h=1e-6, rcond=1e-8):
 
     def objective(ctx_, pr):
         res = ctx_.solve_host()
-        w = reflected_weights(pr)
+        w = ctx_.efficiency_weights()
         return float(np.sum(w * np.abs(np.asarray(res["aU"])) ** 2)), res
 
     ctx = mlqp.Context(prob, device=dev)
     moved = [mlqp.Context(moved_problem(0, s_ * t), device=dev) for s_ in (-2, -1, 1, 2)]
     objective(ctx, prob)  # captures the graphs
-    w0 = reflected_weights(prob)
+    w0 = ctx.efficiency_weights()
 
     def gradient():
         J, res = objective(ctx, prob)
@@ -369,9 +368,7 @@ def design_gradient(mlqp, dev, n_check=20, h=1e-6, rcond=1e-8):
             for m, mp in zip(moved, probs):
                 m.set_problem(mp)
             gq = float(np.sum(ctx.gradient_eval_local(moved, t, work, *where(q))))
-            wm = [reflected_weights(mp) for mp in probs]
-            dw = (wm[0] - 8.0 * wm[1] + 8.0 * wm[2] - wm[3]) / (12.0 * t)
-            grad[q] = gq + float(np.sum(dw * np.abs(aU) ** 2))
+            grad[q] = gq + float(np.sum(ctx.efficiency_weight_gradient(moved, t)))
         return J, grad
 
     gradient()  # warm-up: the moved contexts' graphs

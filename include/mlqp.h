@@ -263,6 +263,39 @@ enum { MLQP_PARAM_INTERFACE = 1, MLQP_PARAM_LAYER = 2 };
 mlqp_status mlqp_gradient_eval_local(mlqp_ctx* ctx, mlqp_ctx* const* moved, double t, void* d_work,
                                      size_t work_bytes, int param_kind, int index, double* grad);
 
+/* Reflected efficiency weights (Remark r:flux, eq. fluxerror: the vertical
+ * energy flux of reflected order n over the incident one is
+ * w_n |a^U_n|^2):
+ *     w[a, K + n] = k^U_n / (k_1 |sin theta_a|)  for n in orders with
+ *                   k^U_n = sqrt(k_1^2 - kappa_n^2) real and > 0
+ *                   (kappa_n = k_1 cos theta_a + 2 pi n / d),
+ *     w[a, K + n] = 0  for evanescent and grazing orders and the orders not
+ *                   listed,
+ * computed on the device from the bound problem (k_1 = Re of the top layer's
+ * wavenumber) and angles.
+ *   orders:   host, n_orders ints in [-K, K] (repeats count once);
+ *             0 <= n_orders <= MLQP_MAX_ORDERS.
+ *   w:        host, n_theta x (2K+1) doubles, row-major (angle, K + n).
+ * Synchronous.  Errors: MLQP_ESTATE (not bound), MLQP_EINVAL (an order out
+ * of range, too many orders, w or orders missing), MLQP_ECUDA. */
+enum { MLQP_MAX_ORDERS = 64 };
+mlqp_status mlqp_efficiency_weights(mlqp_ctx* ctx, const int* orders, int n_orders, double* w);
+
+/* The weights' own term of the gradient of J = sum_a sum_n w_n |a^U_n|^2
+ * along one parameter p: grad[a] = sum_{n in orders} dw_n/dp |a^U_n|^2, with
+ * a^U from ctx's last solve and dw/dp the fourth-order central difference
+ * ((w(-2t) - w(2t)) + 8 (w(t) - w(-t))) / (12 t) (grouped so that a
+ * parameter that does not move the weights gives exactly 0) of the four
+ * moved contexts' problems (the same moved contexts and step as
+ * mlqp_gradient_eval, whose grad[a] this term completes).
+ *   moved:  4 bound MLQP_FP64 contexts (rules as mlqp_gradient_eval).
+ *   grad:   host, n_theta doubles.
+ * Synchronous.  Errors: MLQP_ESTATE (ctx has no amplitudes: no solve since
+ * its last bind), MLQP_EINVAL (moved contexts, t zero or not finite, orders
+ * as mlqp_efficiency_weights), MLQP_ECUDA. */
+mlqp_status mlqp_efficiency_weight_gradient(mlqp_ctx* ctx, mlqp_ctx* const* moved, double t, const int* orders,
+                                            int n_orders, double* grad);
+
 /* Synchronises the bound stream and returns the device-side status word. */
 mlqp_status mlqp_check_device(mlqp_ctx* ctx);
 

@@ -32,6 +32,10 @@ cudaError_t launch_grad_adjoint(const Dev& D, const int* n_host, int* permv, int
 cudaError_t launch_grad_base_lsq(const Dev& D, const GradVecs& V, cudaStream_t s);
 cudaError_t launch_grad_form(const Dev& Dm, const GradVecs& V, int slot, const int* win, cudaStream_t s);
 cudaError_t launch_grad_combine(const Dev& D, const GradVecs& V, double t, cudaStream_t s);
+cudaError_t launch_eff_weights(int n_theta, int K, const WeightSrc& src, const OrderSet& o, double* w,
+                               cudaStream_t s);
+cudaError_t launch_eff_weight_grad(int n_theta, int K, const double2* amp, const WeightSrc* m, const OrderSet& o,
+                                   double t, double* grad, cudaStream_t s);
 cudaError_t launch_mixed_piece(const Dev& D, const int* n_host, int maxn, long n_den, double tol, int* permv,
                                const AngleStreams& A, bool cyclic, int piece);
 cudaError_t cr_configure(int maxn);
@@ -73,7 +77,7 @@ struct mlqp_ctx {
          t_stride = 0;
   // layout
   Region r_ifc, r_lay, r_tasks, r_k, r_ca, r_cb, r_theta, r_scal, r_geo[8], r_pan[4], r_gl16, r_nidx, r_nw, r_wy, r_gl, r_ux, r_alpha, r_kappa,
-      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ROW32, r_F32, r_UDINV32, r_RES, r_ZX, r_ZXA, r_Y32, r_RNRM, r_CRSAVE, r_fwin, r_tcjob, r_tcprep, r_TCX, r_TCY, r_GV, r_GZ, r_GW, r_GH, r_GPART, r_PERMV, r_ETA, r_AMP, r_FLUX, r_STATUS;
+      r_ku, r_kd, r_R, r_F, r_B, r_QP, r_CP, r_X, r_LAUX, r_LT, r_LUPIV, r_UDINV, r_PERM, r_ROW32, r_F32, r_UDINV32, r_RES, r_ZX, r_ZXA, r_Y32, r_RNRM, r_CRSAVE, r_fwin, r_tcjob, r_tcprep, r_TCX, r_TCY, r_GV, r_GZ, r_GW, r_GH, r_GPART, r_PERMV, r_ETA, r_AMP, r_FLUX, r_WEFF, r_STATUS;
   size_t ws_bytes = 0;
   // binding
   char* ws = nullptr;
@@ -116,6 +120,7 @@ struct mlqp_ctx {
   long solve_launches = 0;
   bool factored = false;  // the FP64 block factors of the bound angles are in the workspace
   bool lsq_ready = false;  // the least-squares factors R of the bound angles are in the workspace
+  bool amps_ready = false;  // AMP holds the amplitudes of a solve of the bound problem and angles
   const void* grad_work = nullptr;  // the work buffer mlqp_gradient_prepare filled for the bound problem
 };
 
@@ -522,6 +527,7 @@ mlqp_status mlqp_setup(const mlqp_interface* ifaces, int I, const double* k, dou
   take(cur, c->r_ETA, z16 * nt * c->n_den);
   take(cur, c->r_AMP, z16 * nt * 2 * nK);
   take(cur, c->r_FLUX, d8 * nt);
+  take(cur, c->r_WEFF, d8 * nt * nK);
   take(cur, c->r_STATUS, 256);
   c->ws_bytes = cur;
   c->valid = true;
@@ -692,6 +698,8 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   put(c->r_cb, c->coef_b.data(), sizeof(double) * c->coef_b.size());
   put(c->r_theta, c->theta.data(), sizeof(double) * c->theta.size());
   cudaError_t e = cudaMemcpyAsync(c->ws, c->staging, hdr, cudaMemcpyHostToDevice, c->stream);
+  // a fresh binding carries no device-side error (the workspace is the caller's uninitialised memory)
+  if (e == cudaSuccess) e = cudaMemsetAsync(D.STATUS, 0, 256, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "descriptor upload");
   if ((e = sweep_configure(c->maxn)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
   if ((e = lsq_configure(c->max_m, c->max_p)) != cudaSuccess) return cuda_fail(c, e, "kernel configuration");
@@ -703,6 +711,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   c->bound = true;
   c->factored = false;
   c->lsq_ready = false;
+  c->amps_ready = false;
   c->grad_work = nullptr;  // new angles or problem values: the sensitivities no longer apply
   return MLQP_OK;
 }
@@ -905,6 +914,7 @@ mlqp_status mlqp_run_stage(mlqp_ctx* c, int stage) {
                                 [&](cudaStream_t s) { return enqueue_stage(c, stage, s); }, "stage");
   if (st == MLQP_OK && stage == MLQP_STAGE_SWEEP) c->factored = true;
   if (st == MLQP_OK && stage == MLQP_STAGE_LSQ) c->lsq_ready = true;
+  if (st == MLQP_OK && stage == MLQP_STAGE_RECOVER) c->amps_ready = true;
   return st;
 }
 
@@ -1083,6 +1093,7 @@ mlqp_status mlqp_solve_device(mlqp_ctx* c, void* d_eta, void* d_aU, void* d_aD, 
     if (st != MLQP_OK) return st;
     c->factored = true;
     c->lsq_ready = true;
+    c->amps_ready = true;
   } else {
     for (int s = MLQP_STAGE_GEOM; s <= MLQP_STAGE_RECOVER; ++s) {
       mlqp_status st = mlqp_run_stage(c, s);
@@ -1383,6 +1394,73 @@ mlqp_status mlqp_gradient_eval_local(mlqp_ctx* c, mlqp_ctx* const* moved, double
         return fail(c, MLQP_EINVAL, "moved[%d] changes the wavenumber of layer %d, not only the parameter's", s, q + 1);
   }
   return grad_eval(c, moved, t, d_work, work_bytes, win, grad);
+}
+
+static mlqp_status order_set(mlqp_ctx* c, const int* orders, int n_orders, OrderSet* o) {
+  static_assert(MAX_ORDERS == MLQP_MAX_ORDERS, "order set size");
+  if (n_orders < 0 || n_orders > MLQP_MAX_ORDERS)
+    return fail(c, MLQP_EINVAL, "n_orders %d not in 0..%d", n_orders, (int)MLQP_MAX_ORDERS);
+  if (n_orders > 0 && !orders) return fail(c, MLQP_EINVAL, "orders is required");
+  o->n = n_orders;
+  for (int q = 0; q < n_orders; ++q) {
+    if (orders[q] < -c->prm.K || orders[q] > c->prm.K)
+      return fail(c, MLQP_EINVAL, "order %d outside -K..K (K = %d)", orders[q], c->prm.K);
+    o->v[q] = orders[q];
+  }
+  return MLQP_OK;
+}
+
+static WeightSrc weight_src(const mlqp_ctx* c) {
+  WeightSrc w;
+  w.k1 = c->k[0];
+  w.d = c->d;
+  w.theta = c->D.theta;
+  return w;
+}
+
+mlqp_status mlqp_efficiency_weights(mlqp_ctx* c, const int* orders, int n_orders, double* w) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  if (!w) return fail(c, MLQP_EINVAL, "w is required");
+  OrderSet o{};
+  mlqp_status st = order_set(c, orders, n_orders, &o);
+  if (st != MLQP_OK) return st;
+  const int nK = 2 * c->prm.K + 1;
+  double* dw = at<double>(c, c->r_WEFF);
+  g_launches = 0;
+  cudaError_t e = launch_eff_weights(c->n_theta, c->prm.K, weight_src(c), o, dw, c->stream);
+  c->launches += g_launches;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w, dw, sizeof(double) * c->n_theta * nK, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "efficiency weights");
+  return MLQP_OK;
+}
+
+mlqp_status mlqp_efficiency_weight_gradient(mlqp_ctx* c, mlqp_ctx* const* moved, double t, const int* orders,
+                                            int n_orders, double* grad) {
+  if (!c) return MLQP_EINVAL;
+  if (!c->bound) return fail(c, MLQP_ESTATE, "mlqp_bind must come first");
+  if (!c->amps_ready) return fail(c, MLQP_ESTATE, "no amplitudes: run a solve for the bound angles first");
+  if (!(std::isfinite(t) && t != 0.0)) return fail(c, MLQP_EINVAL, "t: a finite nonzero step");
+  if (!grad) return fail(c, MLQP_EINVAL, "grad is required");
+  mlqp_status st = check_moved(c, moved);
+  if (st != MLQP_OK) return st;
+  OrderSet o{};
+  if ((st = order_set(c, orders, n_orders, &o)) != MLQP_OK) return st;
+  WeightSrc m[4];
+  for (int s = 0; s < 4; ++s) m[s] = weight_src(moved[s]);
+  // the moved contexts' angle tables were uploaded on their own streams
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < 4 && e == cudaSuccess; ++s) e = cudaStreamSynchronize(moved[s]->stream);
+  double* dg = at<double>(c, c->r_WEFF);
+  g_launches = 0;
+  if (e == cudaSuccess) e = launch_eff_weight_grad(c->n_theta, c->prm.K, c->D.AMP, m, o, t, dg, c->stream);
+  c->launches += g_launches;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(grad, dg, sizeof(double) * c->n_theta, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "efficiency weight gradient");
+  return MLQP_OK;
 }
 
 mlqp_status mlqp_fd_gradient(mlqp_ctx* c, mlqp_ctx* const* moved, double t, const void* d_g, void* d_work,

@@ -314,11 +314,6 @@ __device__ double interface_height_at(const Dev& D, int i, double x) {
   return y;
 }
 
-__device__ cplx vertical_wavenumber(cplx k, double kappa) {
-  cplx w = csqrt_(k * k - C(kappa * kappa));
-  if (w.im < 0.0) w = -w;
-  return w;
-}
 
 __global__ void k_geom_misc(Dev D, double* scal) {
   const int t = threadIdx.x;
@@ -382,15 +377,14 @@ __global__ void k_geom_misc(Dev D, double* scal) {
   const cplx kl = C(D.kre[2 * D.I], D.kre[2 * D.I + 1]);
   for (int e = t; e < D.n_theta * D.nK; e += blockDim.x) {
     const int a = e / D.nK, n = e % D.nK - D.K;
-    const double ct = cos(D.theta[a]);
-    const double kap = k1 * ct + TWO_PI * n / D.d;
+    const double kap = bloch_kappa(k1, D.theta[a], n, D.d);
     D.KAPPA[e] = kap;
     const cplx u = vertical_wavenumber(C(k1), kap), w = vertical_wavenumber(kl, kap);
     D.KU[e] = make_double2(u.re, u.im);
     D.KD[e] = make_double2(w.re, w.im);
     if (n == 0) {
       double s, c;
-      sincos(D.d * k1 * ct, &s, &c);
+      sincos(D.d * k1 * cos(D.theta[a]), &s, &c);
       D.ALPHA[a] = make_double2(c, s);
     }
   }

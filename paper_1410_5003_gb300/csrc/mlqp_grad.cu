@@ -19,6 +19,8 @@
 //     dJ/dp = 2 Re[(F(-2t) - 8 F(-t) + 8 F(t) - F(2t)) / (12 t)]   (+ dw |a|^2).
 // The base context supplies mu, eta, xi, y and, after a fill at t = 0, Q'y
 // and r; each moved context supplies one evaluation of F over its own blocks.
+#include <algorithm>
+
 #include "mlqp_internal.h"
 #include "mlqp_math.cuh"
 
@@ -211,6 +213,55 @@ __global__ void k_grad_combine(Dev D, GradVecs V, double t) {
 }
 
 // ---------------------------------------------------------------------------
+// Reflected efficiency weights (Remark r:flux, eq. fluxerror): the vertical
+// flux of reflected order n over the incident flux k_1 |sin theta| is
+// w_n |a^U_n|^2 with w_n = k^U_n / (k_1 |sin theta|) where k^U_n is real and
+// positive (a propagating order), 0 otherwise.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double eff_weight(const WeightSrc& s, int a, int n) {
+  const double th = s.theta[a];
+  const cplx u = vertical_wavenumber(C(s.k1), bloch_kappa(s.k1, th, n, s.d));
+  return (u.im == 0.0 && u.re > 0.0) ? u.re / (s.k1 * fabs(sin(th))) : 0.0;
+}
+
+// True if order n is in the set and q is its first position there.
+__device__ __forceinline__ bool first_in(const OrderSet& o, int n, int q) {
+  for (int r = 0; r < o.n; ++r)
+    if (o.v[r] == n) return r == q;
+  return false;
+}
+
+__global__ void k_eff_weights(int n_theta, int K, WeightSrc s, OrderSet o, double* w) {
+  const int nK = 2 * K + 1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_theta * nK; e += gridDim.x * blockDim.x) {
+    const int a = e / nK, n = e % nK - K;
+    bool on = false;
+    for (int q = 0; q < o.n; ++q) on = on || o.v[q] == n;
+    w[e] = on ? eff_weight(s, a, n) : 0.0;
+  }
+}
+
+// grad[a] = sum over the orders n of dw_n |a^U_n|^2, dw the fourth-order
+// central difference of the weights of the four moved problems.
+__global__ void k_eff_weight_grad(int n_theta, int K, const double2* AMP, WeightSrc m0, WeightSrc m1,
+                                  WeightSrc m2, WeightSrc m3, OrderSet o, double t, double* grad) {
+  const int nK = 2 * K + 1;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n_theta; a += gridDim.x * blockDim.x) {
+    double g = 0.0;
+    for (int q = 0; q < o.n; ++q) {
+      const int n = o.v[q];
+      if (!first_in(o, n, q)) continue;
+      // grouped so that equal weights (a parameter that does not move them) give exactly 0
+      const double dw = ((eff_weight(m0, a, n) - eff_weight(m3, a, n)) +
+                         8.0 * (eff_weight(m2, a, n) - eff_weight(m1, a, n))) / (12.0 * t);
+      const double2 u = AMP[(size_t)a * 2 * nK + K + n];
+      g = fma(dw, u.x * u.x + u.y * u.y, g);
+    }
+    grad[a] = g;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers (stream s; all angles per launch)
 // ---------------------------------------------------------------------------
 // The sensitivities of the solved base context: mu, psi, xi and y.
@@ -252,6 +303,22 @@ cudaError_t launch_grad_form(const Dev& Dm, const GradVecs& V, int slot, const i
 cudaError_t launch_grad_combine(const Dev& D, const GradVecs& V, double t, cudaStream_t s) {
   ++g_launches;
   k_grad_combine<<<1, 128, 0, s>>>(D, V, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eff_weights(int n_theta, int K, const WeightSrc& src, const OrderSet& o, double* w,
+                               cudaStream_t s) {
+  ++g_launches;
+  const int tot = n_theta * (2 * K + 1);
+  k_eff_weights<<<std::max(1, std::min(152, (tot + 255) / 256)), 256, 0, s>>>(n_theta, K, src, o, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eff_weight_grad(int n_theta, int K, const double2* amp, const WeightSrc* m, const OrderSet& o,
+                                   double t, double* grad, cudaStream_t s) {
+  ++g_launches;
+  k_eff_weight_grad<<<std::max(1, std::min(152, (n_theta + 127) / 128)), 128, 0, s>>>(n_theta, K, amp, m[0], m[1],
+                                                                                     m[2], m[3], o, t, grad);
   return cudaGetLastError();
 }
 

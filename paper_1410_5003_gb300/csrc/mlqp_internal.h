@@ -200,6 +200,18 @@ struct Dev {
   const TcPlan* tc;  // host side: tensor-core products of the cyclic reduction (MLQP_CYCLIC)
 };
 
+// Reflected efficiency weights: the Bloch data of one problem (k_1, the
+// period, its device angle table) and a set of orders (at most 64).
+struct WeightSrc {
+  double k1, d;
+  const double* theta;
+};
+constexpr int MAX_ORDERS = 64;
+struct OrderSet {
+  int n;
+  int v[MAX_ORDERS];
+};
+
 // Per-angle vectors of the gradient, carved from the caller's work buffer.
 struct GradVecs {
   double2* eta;   // n_theta x n_den: the base solution

@@ -85,6 +85,17 @@ __device__ __forceinline__ cplx csqrt_(cplx a) {
   if (a.re >= 0.0) return C(t, 0.5 * a.im / t);
   return C(0.5 * fabs(a.im) / t, copysign(t, a.im));
 }
+// Bloch data (Sec. 1): the horizontal wavenumber of order n, kappa_n =
+// k_1 cos theta + 2 pi n / d, and the vertical wavenumber sqrt(k^2 - kappa^2)
+// on the branch Im >= 0 (real and positive for a propagating order).
+__device__ __forceinline__ double bloch_kappa(double k1, double theta, int n, double d) {
+  return k1 * cos(theta) + 6.28318530717958647693 * n / d;
+}
+__device__ __forceinline__ cplx vertical_wavenumber(cplx k, double kappa) {
+  cplx w = csqrt_(k * k - C(kappa * kappa));
+  if (w.im < 0.0) w = -w;
+  return w;
+}
 __device__ __forceinline__ cplx ld2(const double2* p) {
   double2 v = *p;
   return C(v.x, v.y);

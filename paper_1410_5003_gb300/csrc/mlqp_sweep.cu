@@ -535,6 +535,61 @@ __global__ void __launch_bounds__(UpdShape<UTT>::TH) k_lu_update(Dev D, int t, i
 }
 
 // ---------------------------------------------------------------------------
+// The next panel's columns of the top rows in FP64 (look-ahead mode 1):
+// C[v, u] -= sum_k L[v, k] U12[k, u] for the trailing top rows v and the
+// wn <= 16 columns u of the next panel.  It lies on the critical path to the
+// next panel, and GB300's FP64 pipe (2 FMA per clock per SM, one warp
+// instruction per 64 clocks on each of an SM's four schedulers) is its
+// bound: so it is spread over as many SMs as it has rows / NARROW_ROWS, with
+// all four warps of a CTA busy.  One warp per row, two lanes per column (the
+// two halves of k, summed by a shuffle), complex products in four FMAs.
+// ---------------------------------------------------------------------------
+constexpr int NARROW_ROWS = 4;
+
+__global__ void __launch_bounds__(32 * NARROW_ROWS) k_lu_narrow(Dev D, int t, int k, int a0, int wn) {
+  const int a = a0 + blockIdx.y;
+  const Step S = make_step(D, t);
+  const IfaceDesc ft = D.ifc[t];
+  const int w = min(NB, S.nt - k);
+  const int tr = S.nt - k - w;
+  const int v = blockIdx.x * NARROW_ROWS + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31, u = lane & 15, half = lane >> 4;
+  double2* top = D.ROW + a * D.r_stride + ft.row_off;
+  const size_t ldt = S.nt;
+  const bool live = v < tr && u < wn;
+  double re = 0.0, im = 0.0;
+  if (live) {
+    double2 l[NB / 2], x[NB / 2];
+#pragma unroll
+    for (int q = 0; q < NB / 2; ++q) {
+      const int kk = half * (NB / 2) + q;
+      l[q] = make_double2(0.0, 0.0);
+      x[q] = make_double2(0.0, 0.0);
+      if (kk < w) {
+        l[q] = top[(S.nlt + k + kk) * ldt + k + w + v];
+        x[q] = top[(S.nlt + k + w + u) * ldt + k + kk];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB / 2; ++q) {
+      re = fma(l[q].x, x[q].x, re);
+      re = fma(-l[q].y, x[q].y, re);
+      im = fma(l[q].x, x[q].y, im);
+      im = fma(l[q].y, x[q].x, im);
+    }
+  }
+  re += __shfl_xor_sync(0xffffffffu, re, 16);
+  im += __shfl_xor_sync(0xffffffffu, im, 16);
+  if (live && half == 0) {
+    double2* p = top + (S.nlt + k + w + u) * ldt + k + w + v;
+    double2 c = *p;
+    c.x -= re;
+    c.y -= im;
+    *p = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The FP64 trailing update on the tensor cores (mlqp_oz.cuh): the same rows,
 // columns, operands and look-ahead modes as k_lu_update, in 64 x 64 tiles.
 // ---------------------------------------------------------------------------
@@ -699,15 +754,14 @@ __global__ void __launch_bounds__(128) k_recover(Dev D) {
 // nb bottom rows, na angles from a0.  FP32 (the mixed form's factorisation):
 // k_lu_update's square tiles of edge ut.  FP64: the tensor-core update
 // (k_oz_update) in 64 x 64 tiles, except the next panel's columns (mode 1),
-// which k_lu_update does in FP64 on the SIMT pipe: a narrow update whose
+// which k_lu_narrow does in FP64 on the SIMT pipe: a narrow update whose
 // latency, not its work, matters, on the critical path to the next panel.
 template <typename R>
 static void launch_update(const Dev& D, int ut, int tr, int nb, int na, cudaStream_t s, int t, int k, int a0,
                           int mode, int wn) {
   const int nrows = (mode == 1) ? tr : tr + nb, ncols = tr + nb + 1;
   if (sizeof(R) == 8 && mode == 1) {  // the next panel's columns: a narrow update, FP64 on the SIMT pipe
-    const dim3 grid((tr + 15) / 16, na);
-    k_lu_update<R, 16><<<grid, UpdShape<16>::TH, 0, s>>>(D, t, k, a0, 1, wn);
+    k_lu_narrow<<<dim3((tr + NARROW_ROWS - 1) / NARROW_ROWS, na), 32 * NARROW_ROWS, 0, s>>>(D, t, k, a0, wn);
     return;
   }
   if constexpr (sizeof(R) == 8) {

@@ -22,33 +22,14 @@ def block_solve(ctx, f):
     return BlockSolve.apply(f, ctx)
 
 
-def reflected_weights(prob, orders=(0, -1)):
-    """(n_theta, 2K+1) weights w with w_n |a^U_n|^2 the reflected efficiency
-    of order n (the vertical energy flux of the reflected Rayleigh-Bloch mode
-    over the incident one, Sec. 2): k^U_n / (k_1 |sin theta|) for the
-    propagating orders among `orders`, with kappa_n = k_1 cos theta + 2 pi n/d
-    and k^U_n = sqrt(k_1^2 - kappa_n^2) > 0; 0 for the other orders."""
-    import math
-    import numpy as np
-    K = prob.params.K
-    k1 = float(np.real(prob.k[0]))
-    w = np.zeros((prob.n_theta, 2 * K + 1))
-    for a, th in enumerate(np.asarray(prob.theta, dtype=float)):
-        for n in orders:
-            kap = k1 * math.cos(th) + 2.0 * math.pi * n / prob.d
-            q = k1 * k1 - kap * kap
-            if q > 0.0:
-                w[a, K + n] = math.sqrt(q) / (k1 * abs(math.sin(th)))
-    return w
-
-
 class BraggEfficiency(torch.autograd.Function):
     """J(p) = sum over the angles and `orders` of the reflected efficiencies
     of make_problem(p).  Forward: one solve (mlqp_solve); backward, per
     parameter p_q: the sensitivities of the solve, formed once
     (mlqp_gradient_prepare), contracted with the blocks of make_problem(p +
     s t e_q), s = -2, -1, 1, 2 (mlqp_gradient_eval), plus the weights' own
-    fourth-order difference times |a^U|^2.  The four moved contexts are made
+    fourth-order difference times |a^U|^2 (mlqp_efficiency_weight_gradient;
+    the weights themselves come from mlqp_efficiency_weights).  The four moved contexts are made
     once and moved to each parameter's problems by mlqp_set_problem.  make_problem must keep the
     discretisation and the angles; backward runs once (no retain_graph)."""
 
@@ -61,7 +42,7 @@ class BraggEfficiency(torch.autograd.Function):
             prob = make_problem(pv)
             ctx = new_context(prob)
             aU = np.asarray(ctx.solve_host()["aU"])
-            w = reflected_weights(prob, orders)
+            w = ctx.efficiency_weights(orders)
         except Exception as e:  # noqa: BLE001 -- re-raised below, on every rank
             err = e
             if ctx is not None:
@@ -110,9 +91,7 @@ class BraggEfficiency(torch.autograd.Function):
                     gq = float(np.sum(ctx.gradient_eval_local(moved, step, work, *where)))
                 else:
                     gq = float(np.sum(ctx.gradient_eval(moved, step, work)))
-                wm = [reflected_weights(mp, orders) for mp in probs]
-                dw = (wm[0] - 8.0 * wm[1] + 8.0 * wm[2] - wm[3]) / (12.0 * step)
-                grad[q] = gq + float(np.sum(dw * np.abs(aU) ** 2))
+                grad[q] = gq + float(np.sum(ctx.efficiency_weight_gradient(moved, step, orders)))
         except Exception as e:  # noqa: BLE001 -- re-raised below, after the ranks agree
             err = e
         finally:

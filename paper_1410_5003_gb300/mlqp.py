@@ -102,6 +102,10 @@ def load(path: str = LIB_PATH):
     lib.mlqp_gradient_eval.restype = I
     lib.mlqp_gradient_eval_local.argtypes = [P, ct.POINTER(P), D, V, Z, I, I, ct.POINTER(D)]
     lib.mlqp_gradient_eval_local.restype = I
+    lib.mlqp_efficiency_weights.argtypes = [P, ct.POINTER(I), I, ct.POINTER(D)]
+    lib.mlqp_efficiency_weights.restype = I
+    lib.mlqp_efficiency_weight_gradient.argtypes = [P, ct.POINTER(P), D, ct.POINTER(I), I, ct.POINTER(D)]
+    lib.mlqp_efficiency_weight_gradient.restype = I
     lib.mlqp_check_device.argtypes = [P]
     lib.mlqp_check_device.restype = I
     lib.mlqp_solve.argtypes = [P, V, V, V, V]
@@ -130,7 +134,7 @@ EXPORTED = ["mlqp_setup", "mlqp_sizes", "mlqp_workspace_bytes", "mlqp_bind", "ml
             "mlqp_autotune", "mlqp_set_shape",
             "mlqp_solve_rhs", "mlqp_adjoint_solve", "mlqp_lsq_adjoint", "mlqp_x_elements",
             "mlqp_gradient_work_bytes", "mlqp_fd_gradient", "mlqp_gradient_prepare", "mlqp_gradient_eval",
-            "mlqp_gradient_eval_local",
+            "mlqp_gradient_eval_local", "mlqp_efficiency_weights", "mlqp_efficiency_weight_gradient",
             "mlqp_solve_device",
             "mlqp_check_device", "mlqp_solve", "mlqp_run_stage", "mlqp_block_info", "mlqp_last_error",
             "mlqp_destroy", "mlqp_debug_hankel", "mlqp_launch_count", "mlqp_upload_bytes",
@@ -416,6 +420,26 @@ class Context:
                                                                _dptr(out)))
         return out
 
+    def efficiency_weights(self, orders=(0, -1)):
+        """mlqp_efficiency_weights: (n_theta, 2K+1) weights w with w_n |a^U_n|^2
+        the reflected efficiency of order n, for the orders listed (0 for the
+        others and for evanescent or grazing orders)."""
+        o = (ct.c_int * max(1, len(orders)))(*[int(n) for n in orders])
+        w = np.zeros((self.n_theta, self.n_modes))
+        _check(self.ctx, self.lib.mlqp_efficiency_weights(self.ctx, o, len(orders), _dptr(w)))
+        return w
+
+    def efficiency_weight_gradient(self, moved, t, orders=(0, -1)):
+        """mlqp_efficiency_weight_gradient: per angle, sum_n dw_n/dp |a^U_n|^2
+        from this context's last amplitudes and the weights of the four moved
+        contexts (fourth-order central difference, step t)."""
+        arr = (ct.c_void_p * 4)(*[m.ctx for m in moved])
+        o = (ct.c_int * max(1, len(orders)))(*[int(n) for n in orders])
+        out = np.zeros(self.n_theta)
+        _check(self.ctx, self.lib.mlqp_efficiency_weight_gradient(self.ctx, ct.cast(arr, ct.POINTER(ct.c_void_p)),
+                                                                  float(t), o, len(orders), _dptr(out)))
+        return out
+
     def host_outputs(self, eta=False, pinned=False):
         t = self.torch
         mk = lambda shape, dt: t.empty(shape, dtype=dt, pin_memory=pinned)
@@ -482,7 +506,7 @@ def tc_cgemm(A, B, C, beta):
 
 def oz_update(A, B, C):
     """mlqp_debug_oz_update: C - A B (complex128 CUDA tensors; A rows x K,
-    B K x cols, K <= 16) by the FP64 tensor-core update of the block LU."""
+    B K x cols, K <= 128) by the FP64 tensor-core products."""
     import torch
     lib = load()
     rows, K = A.shape

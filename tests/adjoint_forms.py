@@ -70,7 +70,18 @@ class OracleContext:
         asm = O.Assembler(self.prob)
         aU = np.array([O.solve(self.prob, a, asm)["aU"] for a in range(self.prob.n_theta)])
         self.factored = True
+        self.aU = aU
         return {"aU": aU}
+
+    def efficiency_weights(self, orders=(0, -1)):
+        pr = self.prob
+        return np.array([O.reflected_weights(pr, float(th), O.bloch(pr, float(th)), tuple(orders))
+                         for th in pr.theta])
+
+    def efficiency_weight_gradient(self, moved, t, orders=(0, -1)):
+        wm = [m.efficiency_weights(orders) for m in moved]
+        dw = ((wm[0] - wm[3]) + 8.0 * (wm[2] - wm[1])) / (12.0 * t)
+        return np.sum(dw * np.abs(self.aU) ** 2, axis=1)
 
     def fd_gradient(self, moved, t, g):
         if not self.factored:

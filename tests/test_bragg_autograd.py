@@ -9,19 +9,8 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from oracle import mlqp_oracle as O  # noqa: E402
-from paper_1410_5003_gb300.diff import bragg_efficiency, reflected_weights  # noqa: E402
+from paper_1410_5003_gb300.diff import bragg_efficiency  # noqa: E402
 from tests.adjoint_forms import OracleContext, gradient_family  # noqa: E402
-
-
-def test_reflected_weights_match_the_oracle():
-    prob, make_problem, _, _ = gradient_family()
-    for pv in (np.zeros(5), np.array([0.3, 0, 0, 0, 0])):
-        pr = make_problem(pv)
-        w = reflected_weights(pr, (0, -1, 1))
-        for a in range(pr.n_theta):
-            th = float(pr.theta[a])
-            ref = O.reflected_weights(pr, th, O.bloch(pr, th), (0, -1, 1))
-            assert np.allclose(w[a], ref, rtol=1e-14, atol=0.0)
 
 
 def test_bragg_efficiency_value_and_gradient_on_the_oracle():
@@ -74,22 +63,37 @@ def test_bragg_efficiency_edge_cases_on_the_oracle():
         J.backward()
 
 
-def test_reflected_weights_vanish_for_evanescent_and_grazing_orders():
-    """w_n = 0 where k^U_n is imaginary or zero (a Wood anomaly), and the
-    specular weight is 1 (k^U_0 = k_1 |sin theta|)."""
+def weight_cases():
+    """A grazing angle of order +1 (kappa_1 = k_1, a Wood anomaly) and an
+    ordinary one, on a one-interface stack with K = 8."""
     import math
     from dataclasses import replace
     from workloads import small_stack
     prob = small_stack(I=1, N=40, P=40, Mw=24, K=8, M=30)
     k1, d = float(np.real(prob.k[0])), prob.d
-    th_w = -math.acos(1.0 - 2.0 * math.pi / (d * k1))  # order +1 grazing: kappa_1 = k_1
-    pr = replace(prob).with_angles([th_w, -0.9])
-    w = reflected_weights(pr, orders=(0, 1, -8, 8))
-    K = pr.params.K
+    th_w = -math.acos(1.0 - 2.0 * math.pi / (d * k1))
+    return replace(prob).with_angles([th_w, -0.9]), k1, d, th_w
+
+
+def check_weight_cases(w, K, k1, d, th_w):
+    """w_n = 0 where k^U_n is imaginary or zero, and the specular weight is 1
+    (k^U_0 = k_1 |sin theta|)."""
+    import math
     assert abs(w[0, K] - 1.0) < 1e-14 and abs(w[1, K] - 1.0) < 1e-14
     kap = k1 * math.cos(th_w) + 2 * math.pi / d
     assert w[0, K + 1] == 0.0 or k1 * k1 - kap * kap <= 1e-12 * k1 * k1
     assert w[1, K + 8] == 0.0 and w[1, K - 8] == 0.0  # evanescent at |n| = 8
+    for n in range(-K, K + 1):  # orders not asked for weigh nothing
+        if n not in (0, 1, -8, 8):
+            assert w[0, K + n] == 0.0 and w[1, K + n] == 0.0
+
+
+def test_reflected_weights_vanish_for_evanescent_and_grazing_orders():
+    """The oracle's weights on the special cases: the specular weight is 1
+    whatever the angle, evanescent and grazing orders weigh 0."""
+    pr, k1, d, th_w = weight_cases()
+    w = OracleContext(pr).efficiency_weights(orders=(0, 1, -8, 8))
+    check_weight_cases(w, pr.params.K, k1, d, th_w)
 
 
 def test_parameter_locality_is_read_from_the_moved_problems():

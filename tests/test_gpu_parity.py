@@ -990,6 +990,74 @@ def test_bragg_efficiency_autograd(M):
         assert abs(g[q] - fd) < 1e-6 * max(abs(fd), 1e-3), (nm, g[q], fd)
 
 
+def test_efficiency_weights_through_the_abi(M):
+    """mlqp_efficiency_weights (the reflected efficiency weights k^U_n /
+    (k_1 |sin theta|), Remark r:flux) against the oracle's to 1e-14 on the
+    gradient stack, unmoved and with k_1 moved; on a grazing angle of order
+    +1 and an ordinary angle: specular weight 1, evanescent and grazing orders
+    0, orders not asked for 0; orders outside -K..K and too many orders
+    refused."""
+    from tests.adjoint_forms import gradient_family
+    from tests.test_bragg_autograd import check_weight_cases, weight_cases
+    prob, make_problem, _, _ = gradient_family()
+    for pv in (np.zeros(5), np.array([0.3, 0, 0, 0, 0])):
+        pr = make_problem(pv)
+        ctx = M.Context(pr)
+        w = ctx.efficiency_weights((0, -1, 1))
+        for a in range(pr.n_theta):
+            th = float(pr.theta[a])
+            ref = O.reflected_weights(pr, th, O.bloch(pr, th), (0, -1, 1))
+            assert np.allclose(w[a], ref, rtol=1e-14, atol=0.0), (a, w[a], ref)
+        ctx.close()
+    pr, k1, d, th_w = weight_cases()
+    ctx = M.Context(pr)
+    check_weight_cases(ctx.efficiency_weights(orders=(0, 1, -8, 8)), pr.params.K, k1, d, th_w)
+    assert np.array_equal(ctx.efficiency_weights(orders=(0, 0, -1)), ctx.efficiency_weights(orders=(0, -1)))
+    assert not np.any(ctx.efficiency_weights(orders=()))
+    for bad in ((pr.params.K + 1,), (-pr.params.K - 1,), tuple(range(65))):
+        with pytest.raises(M.MlqpError) as e:
+            ctx.efficiency_weights(orders=bad)
+        assert e.value.status == M.MLQP_EINVAL
+    ctx.close()
+
+
+def test_efficiency_weight_gradient_through_the_abi(M):
+    """mlqp_efficiency_weight_gradient = sum_n dw_n |a^U_n|^2 per angle, dw the
+    fourth-order central difference of the oracle's weights of the four moved
+    problems and a^U the context's own solve: for k_1 (which moves the
+    weights) to 1e-9 relative plus 1e-12 sum_n |a^U_n|^2 (a weight carries
+    about 1e-16 relative rounding, which the difference divides by t =
+    1e-3), and for a shape coefficient (which does not move them: 0
+    exactly).  Before a solve the call is refused (MLQP_ESTATE)."""
+    from tests.adjoint_forms import gradient_family
+    prob, make_problem, _, _ = gradient_family()
+    t = 1e-3
+    ctx = M.Context(prob)
+    moved = [M.Context(make_problem(np.array([s_ * t, 0, 0, 0, 0]))) for s_ in (-2, -1, 1, 2)]
+    with pytest.raises(M.MlqpError) as e:
+        ctx.efficiency_weight_gradient(moved, t)
+    assert e.value.status == M.MLQP_ESTATE
+    aU = np.asarray(ctx.solve_host()["aU"])
+    for q in (0, 3):
+        probs = [make_problem(np.eye(5)[q] * s_ * t) for s_ in (-2, -1, 1, 2)]
+        for m, mp in zip(moved, probs):
+            m.set_problem(mp)
+        got = ctx.efficiency_weight_gradient(moved, t)
+        wm = [np.array([O.reflected_weights(mp, float(th), O.bloch(mp, float(th))) for th in mp.theta])
+              for mp in probs]
+        dw = ((wm[0] - wm[3]) + 8.0 * (wm[2] - wm[1])) / (12.0 * t)
+        ref = np.sum(dw * np.abs(aU) ** 2, axis=1)
+        if q == 0:
+            tol = 1e-9 * np.abs(ref) + 1e-12 * np.sum(np.abs(aU) ** 2, axis=1)
+            assert np.all(np.abs(ref) > 100 * tol), (ref, tol)
+            assert np.all(np.abs(got - ref) <= tol), (got, ref)
+        else:
+            assert not np.any(got) and not np.any(ref)
+    for m in moved:
+        m.close()
+    ctx.close()
+
+
 def test_block_solve_is_differentiable(M):
     """paper_1410_5003_gb300.diff.block_solve: eta = A'^{-1} f with
     torch autograd; the gradient of L = Re(c^H eta) agrees with central
