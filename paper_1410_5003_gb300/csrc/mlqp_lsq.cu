@@ -368,10 +368,10 @@ struct OzSchur {
     const double2* X = D.Xb + ang * D.x_stride;
     return (k < T.k1) ? X[T.b1_off + (size_t)u * T.ldb1 + k] : X[T.b2_off + (size_t)u * T.ldb2 + (k - T.k1)];
   }
-  __device__ bool keep(int v, int u) const { return v < T.rows && u < T.cols; }
-  __device__ double* ptr(int v, int u, int p) const {
-    return reinterpret_cast<double*>(D.ROW + ang * D.r_stride + T.c_off + (size_t)u * T.ldc + v) + p;
+  __device__ OzRow row(int v) const {
+    return OzRow{D.ROW + ang * D.r_stride + T.c_off + v, 0, v < T.rows ? T.cols : 0, true};
   }
+  __device__ long long col_off(bool, int u) const { return (long long)u * T.ldc; }
 };
 
 // ---------------------------------------------------------------------------

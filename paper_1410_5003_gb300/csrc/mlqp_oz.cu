@@ -30,8 +30,8 @@ struct OzPlain {
   __device__ double2 b(int k, int u) const {
     return (u < cols && k < K) ? B[(size_t)u * ldb + k] : make_double2(0.0, 0.0);
   }
-  __device__ bool keep(int v, int u) const { return v < rows && u < cols; }
-  __device__ double* ptr(int v, int u, int p) const { return reinterpret_cast<double*>(C + (size_t)u * ldc + v) + p; }
+  __device__ OzRow row(int v) const { return OzRow{C + v, 0, v < rows ? cols : 0, true}; }
+  __device__ long long col_off(bool, int u) const { return (long long)u * ldc; }
 };
 
 }  // namespace mlqp

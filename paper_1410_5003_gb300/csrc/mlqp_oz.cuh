@@ -49,10 +49,11 @@ constexpr int OZ_SLICES = 7;
 constexpr int OZ_LEVELS = 8;      // l = s + t - 2 for s + t <= 9
 constexpr uint32_t OZ_XTILE = 128 * 128;   // bytes of one pair of X slices (128 rows x 128 bytes)
 constexpr uint32_t OZ_YTILE = 64 * 128;    // bytes of one pair of Y slices (64 rows x 128 bytes)
-constexpr size_t OZ_SMEM = 4 * OZ_XTILE + 4 * OZ_YTILE + 1024 + 1024;
+constexpr size_t OZ_SMEM = 4 * OZ_XTILE + 4 * OZ_YTILE + 1024 + 2048 + 1024;
 // 120 KB of dynamic shared memory keeps one CTA per SM: its 512 tensor-memory
 // columns are then never contended.
 constexpr size_t OZ_SMEM_LAUNCH = 120 * 1024;
+static_assert(OZ_SMEM <= OZ_SMEM_LAUNCH, "tile state exceeds the launch's shared memory");
 constexpr int OZ_TIMEOUT_CODE = 5;  // MLQP_ETIMEOUT
 
 // Instruction descriptor of tcgen05.mma kind::f16 with BF16 A and B (bits
@@ -97,17 +98,28 @@ __device__ __forceinline__ unsigned long long oz_fixed(double x, int emax) {
   return (sh <= -53) ? 0ull : (M >> (-sh));
 }
 
+// A digit 0 <= d <= 255 with sign bit sgn (0 or 0x80000000) as the bits of
+// an exact FP32 value: 2^23 + d has d in its low mantissa bits, and
+// subtracting 2^23 leaves d exactly (FP32 add, not the conversion unit).
+__device__ __forceinline__ uint32_t oz_digit_f32(uint32_t d, uint32_t sgn) {
+  return __float_as_uint(__uint_as_float(0x4B000000u | d) - 8388608.0f) ^ sgn;
+}
+
 // Writes the 7 digit slices of 32 values (one row of X or column of Y) into
 // the slice-pair tiles at `base` (row r of tiles of `tile_bytes`), 128-byte
-// swizzle: 16-byte chunk c of row r at chunk c ^ (r mod 8).
+// swizzle: 16-byte chunk c of row r at chunk c ^ (r mod 8).  Digit s of a
+// value is bits [56 - 8s, 64 - 8s) of its 56-bit magnitude q: s = 1..3 from
+// the high word of q, s = 4..7 from the low word.  BF16 is the high half of
+// the FP32 bits (exact: a digit has at most 8 significant bits).
 __device__ __forceinline__ void oz_store_digits(unsigned char* base, uint32_t tile_bytes, int r, const double* val,
                                                 int emax) {
-  unsigned long long q[32];
-  uint32_t neg = 0;
+  uint32_t hi[32], lo[32], sg[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
-    q[i] = oz_fixed(val[i], emax);
-    neg |= static_cast<uint32_t>(static_cast<unsigned long long>(__double_as_longlong(val[i])) >> 63) << i;
+    const unsigned long long q = oz_fixed(val[i], emax);
+    hi[i] = static_cast<uint32_t>(q >> 32);
+    lo[i] = static_cast<uint32_t>(q);
+    sg[i] = static_cast<uint32_t>(static_cast<unsigned long long>(__double_as_longlong(val[i])) >> 32) & 0x80000000u;
   }
 #pragma unroll
   for (int s = 1; s <= OZ_SLICES; ++s) {
@@ -118,19 +130,49 @@ __device__ __forceinline__ void oz_store_digits(unsigned char* base, uint32_t ti
       uint32_t w[4];
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
-        uint32_t pair = 0;
+        uint32_t f[2];
 #pragma unroll
         for (int e2 = 0; e2 < 2; ++e2) {
           const int i = 8 * c + 2 * h + e2;
-          const int d = static_cast<int>((q[i] >> (56 - 8 * s)) & 0xFFull);
-          const float f = static_cast<float>((neg >> i) & 1u ? -d : d);  // exact: |d| <= 255
-          pair |= (__float_as_uint(f) >> 16) << (16 * e2);
+          const uint32_t d = (s <= 3) ? (hi[i] >> (8 * (3 - s))) & 0xFFu : (lo[i] >> (8 * (7 - s))) & 0xFFu;
+          f[e2] = oz_digit_f32(d, sg[i]);
         }
-        w[h] = pair;
+        w[h] = __byte_perm(f[0], f[1], 0x7632);
       }
       const int chunk = (half * 4 + c) ^ (r & 7);
       *reinterpret_cast<uint4*>(row + chunk * 16) = make_uint4(w[0], w[1], w[2], w[3]);
     }
+  }
+}
+
+// Eight consecutive FP32 accumulator columns of this thread's TMEM lane, not
+// yet waited for: the caller issues several, then oz_tmem_wait.
+__device__ __forceinline__ void oz_tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void oz_tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// After the wait: ties the registers of one load to it, so that no use of
+// them is scheduled before the wait.
+__device__ __forceinline__ void oz_pin8(uint32_t* r) {
+  asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
+}
+
+// The eight level accumulators of 8 columns (a[l][j], FP32 bits of exact
+// integers) as 64-bit integers in the unit 2^(e + f - 48): levels 0..4 weigh
+// 2^(32 - 8l), levels 5..7 2^(-8 (l - 4)), combined exactly then shifted.
+__device__ __forceinline__ void oz_levels(const uint32_t (*a)[8], long long* out) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    long long V = 0, T = 0;
+#pragma unroll
+    for (int l = 0; l < OZ_LEVELS; ++l) {
+      const long long iv = static_cast<long long>(__float2int_rn(__uint_as_float(a[l][j])));
+      if (l <= 4) V += iv * (1LL << (32 - 8 * l));
+      else T += iv * (1LL << (8 * (7 - l)));
+    }
+    out[j] = V + (T >> 24);
   }
 }
 
@@ -164,28 +206,126 @@ __device__ __forceinline__ double oz_neg(double x) {  // sign flip without the F
   return __longlong_as_double(__double_as_longlong(x) ^ static_cast<long long>(0x8000000000000000ull));
 }
 
+// One output row of C as the geometry G describes it: element (v, u) is at
+// base + col_off(upper, u) for u in [lo, hi) (the columns kept for row v);
+// `upper` picks one of two column-offset families (the top and bottom block
+// rows of the sweep; one family elsewhere).
+struct OzRow {
+  double2* base;
+  int lo, hi;
+  bool upper;
+};
+
+// The shared state of one tile: the digit slices of X and Y, the row and
+// column scales, the column offsets of C, the MMA barrier and the TMEM slot.
+struct OzShared {
+  unsigned char *xs, *ys;
+  int *fexp, *eexp;
+  long long* coff;  // [2][OZ_TILE]
+  uint64_t* done;
+  uint32_t* tslot;
+};
+
+__device__ __forceinline__ OzShared oz_shared(unsigned char* raw) {
+  OzShared S;
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  S.xs = base;
+  S.ys = base + 4 * OZ_XTILE;
+  S.coff = reinterpret_cast<long long*>(S.ys + 4 * OZ_YTILE);
+  S.fexp = reinterpret_cast<int*>(S.coff + 2 * OZ_TILE);
+  S.eexp = S.fexp + OZ_TILE;
+  S.done = reinterpret_cast<uint64_t*>(S.eexp + 2 * OZ_TILE);
+  S.tslot = reinterpret_cast<uint32_t*>(S.done + 1);
+  return S;
+}
+
+// Thread 0: the 72 BF16 MMAs of one chunk of K' = 32 (the 36 slice pairs
+// s + t <= 9, two K = 16 steps each) into the eight level accumulators; the
+// first product of each level overwrites it unless `accumulate`.
+__device__ __forceinline__ void oz_issue(const OzShared& S, uint32_t tmem, bool accumulate) {
+  const uint32_t idesc = oz_idesc_bf16(2 * OZ_TILE, OZ_TILE);
+  const uint32_t xa = tc_smem(S.xs), ya = tc_smem(S.ys);
+  uint32_t started = accumulate ? 0xFFu : 0u;
+  for (int s = 1; s <= OZ_SLICES; ++s)
+    for (int t = 1; t <= OZ_SLICES && s + t <= 9; ++t) {
+      const int l = s + t - 2;
+      const uint32_t xo = xa + ((s - 1) >> 1) * OZ_XTILE + ((s - 1) & 1) * 64;
+      const uint32_t yo = ya + ((t - 1) >> 1) * OZ_YTILE + ((t - 1) & 1) * 64;
+      const uint32_t acc = tmem + static_cast<uint32_t>(l * OZ_TILE);
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {  // K' = 32 as two K = 16 steps, 32 bytes apart
+        oz_mma_bf16(acc, tc_desc_sw128(xo + ks * 32), tc_desc_sw128(yo + ks * 32), idesc,
+                    ((started >> l) & 1u) ? 1u : 0u);
+        started |= 1u << l;
+      }
+    }
+  tc_commit(S.done);
+}
+
+// Reads the eight levels of 8 columns (c0 .. c0 + 7 of the tile) of this
+// thread's lane and combines them into 64-bit integers.
+__device__ __forceinline__ void oz_read8(uint32_t lane_addr, int c0, long long* out) {
+  uint32_t a[OZ_LEVELS][8];
+#pragma unroll
+  for (int l = 0; l < OZ_LEVELS; ++l) oz_tmem_ld8(lane_addr + static_cast<uint32_t>(l * OZ_TILE + c0), a[l]);
+  oz_tmem_wait();
+#pragma unroll
+  for (int l = 0; l < OZ_LEVELS; ++l) oz_pin8(a[l]);
+  oz_levels(a, out);
+}
+
+// C[v, u] -= tot 2^sc (one real part p of the complex entry), by the integer
+// rounding of oz_i2d (two power-of-two factors outside its range).
+__device__ __forceinline__ double oz_value(long long tot, int sc) {
+  bool fine = true;
+  double d = oz_i2d(tot, sc, fine);
+  if (!fine) {
+    const int h1 = sc / 2, h2 = sc - h1;
+    d = (static_cast<double>(tot) * __longlong_as_double((long long)(h1 + 1023) << 52)) *
+        __longlong_as_double((long long)(h2 + 1023) << 52);
+  }
+  return d;
+}
+
+// Per-tile set-up shared by both kernels: barrier, tensor memory, column offsets.
 template <class G>
-__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(G g, int* status) {
-  extern __shared__ unsigned char oz_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz_raw) + 1023) &
-                                                         ~static_cast<uintptr_t>(1023));
-  unsigned char* xs = base;
-  unsigned char* ys = base + 4 * OZ_XTILE;
-  int* fexp = reinterpret_cast<int*>(ys + 4 * OZ_YTILE);   // 64 column exponents
-  int* eexp = fexp + OZ_TILE;                               // 128 row exponents
-  uint64_t* done = reinterpret_cast<uint64_t*>(eexp + 2 * OZ_TILE);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+__device__ __forceinline__ void oz_begin(const G& g, const OzShared& S, int u0) {
   const int tid = threadIdx.x, warp = tid >> 5;
-  if (!g.setup()) return;  // uniform: the whole tile lies outside the block
-  const int v0 = g.v0(), u0 = g.u0();
   if (tid == 0) {
-    tc_bar_init(done, 1);
+    tc_bar_init(S.done, 1);
     tc_fence_bar_init();
   }
   if (warp == 0) {
-    tc_tmem_alloc(tslot, OZ_LEVELS * OZ_TILE);
+    tc_tmem_alloc(S.tslot, OZ_LEVELS * OZ_TILE);
     tc_tmem_relinquish();
   }
+  if (tid >= 2 * OZ_TILE && tid < 4 * OZ_TILE) {
+    const int j = tid - 2 * OZ_TILE;  // 0..127: family j / 64, column j % 64
+    S.coff[j] = g.col_off(j < OZ_TILE, u0 + (j & (OZ_TILE - 1)));
+  }
+}
+
+template <class G>
+__device__ __forceinline__ void oz_end(const OzShared& S, uint32_t tmem, bool ok, int* status) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (!ok && tid == 0) atomicExch(status, OZ_TIMEOUT_CODE);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tc_tmem_dealloc(tmem, OZ_LEVELS * OZ_TILE);
+  }
+}
+
+template <class G>
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(G g, int* status) {
+  extern __shared__ unsigned char oz_raw[];
+  const OzShared S = oz_shared(oz_raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (!g.setup()) return;  // uniform: the whole tile lies outside the block
+  const int v0 = g.v0(), u0 = g.u0();
+  oz_begin(g, S, u0);
   const int m = tid & 127, vl = m >> 1, p = m & 1, half = tid >> 7;
   if (half == 0) {  // one row of X: Out row m = 2 (v - v0) + p
     double val[32];
@@ -199,8 +339,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(G g, int* status) {
     int emax = 0;
 #pragma unroll
     for (int i = 0; i < 32; ++i) emax = max(emax, oz_expo(val[i]));
-    oz_store_digits(xs, OZ_XTILE, m, val, emax);
-    eexp[m] = emax;
+    oz_store_digits(S.xs, OZ_XTILE, m, val, emax);
+    S.eexp[m] = emax;
   } else if (m < OZ_TILE) {  // one column of Y
     double val[32];
     const int u = u0 + m;
@@ -213,87 +353,48 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(G g, int* status) {
     int emax = 0;
 #pragma unroll
     for (int i = 0; i < 32; ++i) emax = max(emax, oz_expo(val[i]));
-    oz_store_digits(ys, OZ_YTILE, m, val, emax);
-    fexp[m] = emax;
+    oz_store_digits(S.ys, OZ_YTILE, m, val, emax);
+    S.fexp[m] = emax;
   }
   oz_fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
-  if (tid == 0) {
-    const uint32_t idesc = oz_idesc_bf16(2 * OZ_TILE, OZ_TILE);
-    const uint32_t xa = tc_smem(xs), ya = tc_smem(ys);
-    uint32_t started = 0;
-    for (int s = 1; s <= OZ_SLICES; ++s)
-      for (int t = 1; t <= OZ_SLICES && s + t <= 9; ++t) {
-        const int l = s + t - 2;
-        const uint32_t xo = xa + ((s - 1) >> 1) * OZ_XTILE + ((s - 1) & 1) * 64;
-        const uint32_t yo = ya + ((t - 1) >> 1) * OZ_YTILE + ((t - 1) & 1) * 64;
-        const uint32_t acc = tmem + static_cast<uint32_t>(l * OZ_TILE);
-#pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {  // K' = 32 as two K = 16 steps, 32 bytes apart
-          oz_mma_bf16(acc, tc_desc_sw128(xo + ks * 32), tc_desc_sw128(yo + ks * 32), idesc,
-                      ((started >> l) & 1u) ? 1u : 0u);
-          started |= 1u << l;
-        }
-      }
-    tc_commit(done);
-  }
+  const uint32_t tmem = *S.tslot;
+  if (tid == 0) oz_issue(S, tmem, false);
   // the epilogue: Out row m (TMEM lane m), columns half * 32 .. half * 32 + 31
   const int v = v0 + vl;
-  const int emax_x = eexp[m];
-  bool ok = tc_wait(done, 0);
+  const OzRow R = g.row(v);
+  const long long* coff = S.coff + (R.upper ? 0 : OZ_TILE);
+  const int emax_x = S.eexp[m];
+  bool ok = tc_wait(S.done, 0);
   ok = __all_sync(0xffffffffu, ok);
   tc_fence_after();
   if (ok) {
     const uint32_t lane_addr = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
 #pragma unroll 1
-    for (int ch = 0; ch < 2; ++ch) {
-      const int c0 = half * 32 + ch * 16;  // local column of this chunk
+    for (int ch = 0; ch < 4; ++ch) {
+      const int c0 = half * 32 + ch * 8;  // local column of this chunk
       // the chunk's entries of C first: their latency overlaps the accumulator reads
-      double cv[16];
+      double cv[8];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) cv[j] = g.keep(v, u0 + c0 + j) ? *g.ptr(v, u0 + c0 + j, p) : 0.0;
-      long long V[16], T[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) V[j] = T[j] = 0;
-#pragma unroll 1
-      for (int l = 0; l < OZ_LEVELS; ++l) {
-        float a[16];
-        tc_tmem_ld16(lane_addr + static_cast<uint32_t>(l * OZ_TILE + c0), a);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const long long iv = static_cast<long long>(__float2int_rn(a[j]));
-          if (l <= 4) V[j] += iv * (1LL << (32 - 8 * l));
-          else T[j] += iv * (1LL << (8 * (7 - l)));
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
+      for (int j = 0; j < 8; ++j) {
         const int u = u0 + c0 + j;
-        if (!g.keep(v, u)) continue;
+        cv[j] = (u >= R.lo && u < R.hi) ? reinterpret_cast<const double*>(R.base + coff[c0 + j])[p] : 0.0;
+      }
+      long long tot[8];
+      oz_read8(lane_addr, c0, tot);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + c0 + j;
+        if (u < R.lo || u >= R.hi) continue;
         // unit 2^(e + f - 48) with e = emax_x - 1022, f = fexp - 1022
-        const int sc = emax_x + fexp[c0 + j] - 2044 - 48;
-        const long long tot = V[j] + (T[j] >> 24);
-        bool fine = true;
-        double d = oz_i2d(tot, sc, fine);
-        if (!fine) {  // outside one power of two's normal range: two factors
-          const int h1 = sc / 2, h2 = sc - h1;
-          d = (static_cast<double>(tot) * __longlong_as_double((long long)(h1 + 1023) << 52)) *
-              __longlong_as_double((long long)(h2 + 1023) << 52);
-        }
-        *g.ptr(v, u, p) = cv[j] - d;
+        const double d = oz_value(tot[j], emax_x + S.fexp[c0 + j] - 2044 - 48);
+        reinterpret_cast<double*>(R.base + coff[c0 + j])[p] = cv[j] - d;
       }
     }
   }
-  if (!ok && tid == 0) atomicExch(status, OZ_TIMEOUT_CODE);
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    tc_tmem_dealloc(tmem, OZ_LEVELS * OZ_TILE);
-  }
+  oz_end<G>(S, tmem, ok, status);
 }
 
 // The same product over a longer inner dimension, C -= sum_k A[v, k] B[k, u]
@@ -306,25 +407,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(G g, int* status) {
 template <class G>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(G g, int* status) {
   extern __shared__ unsigned char oz_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz_raw) + 1023) &
-                                                         ~static_cast<uintptr_t>(1023));
-  unsigned char* xs = base;
-  unsigned char* ys = base + 4 * OZ_XTILE;
-  int* fexp = reinterpret_cast<int*>(ys + 4 * OZ_YTILE);
-  int* eexp = fexp + OZ_TILE;
-  uint64_t* done = reinterpret_cast<uint64_t*>(eexp + 2 * OZ_TILE);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  const OzShared S = oz_shared(oz_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (!g.setup()) return;
   const int v0 = g.v0(), u0 = g.u0(), nk = g.nk(), nch = (nk + 15) / 16;
-  if (tid == 0) {
-    tc_bar_init(done, 1);
-    tc_fence_bar_init();
-  }
-  if (warp == 0) {
-    tc_tmem_alloc(tslot, OZ_LEVELS * OZ_TILE);
-    tc_tmem_relinquish();
-  }
+  oz_begin(g, S, u0);
   const int m = tid & 127, vl = m >> 1, p = m & 1, half = tid >> 7;
   const int v = v0 + vl;
   // the scales: largest exponent of each row (column) over the whole K
@@ -334,20 +421,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(G g, int* status) {
       const double2 a = g.a(v, k);
       emax = max(emax, max(oz_expo(a.x), oz_expo(a.y)));
     }
-    eexp[m] = emax;
+    S.eexp[m] = emax;
   } else if (m < OZ_TILE) {
     int emax = 0;
     for (int k = 0; k < nk; ++k) {
       const double2 b = g.b(k, u0 + m);
       emax = max(emax, max(oz_expo(b.x), oz_expo(b.y)));
     }
-    fexp[m] = emax;
+    S.fexp[m] = emax;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
-  const int emax_x = eexp[m];
+  const uint32_t tmem = *S.tslot;
+  const int emax_x = S.eexp[m];
   long long V[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) V[j] = 0;
@@ -362,7 +449,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(G g, int* status) {
         val[2 * k] = p ? a.y : a.x;
         val[2 * k + 1] = p ? a.x : oz_neg(a.y);
       }
-      oz_store_digits(xs, OZ_XTILE, m, val, emax_x);
+      oz_store_digits(S.xs, OZ_XTILE, m, val, emax_x);
     } else if (m < OZ_TILE) {
       double val[32];
 #pragma unroll
@@ -371,54 +458,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(G g, int* status) {
         val[2 * k] = b.x;
         val[2 * k + 1] = b.y;
       }
-      oz_store_digits(ys, OZ_YTILE, m, val, fexp[m]);
+      oz_store_digits(S.ys, OZ_YTILE, m, val, S.fexp[m]);
     }
     oz_fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tid == 0) {
-      const uint32_t idesc = oz_idesc_bf16(2 * OZ_TILE, OZ_TILE);
-      const uint32_t xa = tc_smem(xs), ya = tc_smem(ys);
-      uint32_t started = 0;
-      for (int s = 1; s <= OZ_SLICES; ++s)
-        for (int t = 1; t <= OZ_SLICES && s + t <= 9; ++t) {
-          const int l = s + t - 2;
-          const uint32_t xo = xa + ((s - 1) >> 1) * OZ_XTILE + ((s - 1) & 1) * 64;
-          const uint32_t yo = ya + ((t - 1) >> 1) * OZ_YTILE + ((t - 1) & 1) * 64;
-          const uint32_t acc = tmem + static_cast<uint32_t>(l * OZ_TILE);
-#pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            oz_mma_bf16(acc, tc_desc_sw128(xo + ks * 32), tc_desc_sw128(yo + ks * 32), idesc,
-                        ((started >> l) & 1u) ? 1u : 0u);
-            started |= 1u << l;
-          }
-        }
-      tc_commit(done);
-    }
-    ok = tc_wait(done, static_cast<uint32_t>(ch & 1));
+    if (tid == 0) oz_issue(S, tmem, false);
+    ok = tc_wait(S.done, static_cast<uint32_t>(ch & 1));
     ok = __syncthreads_and(ok);
     tc_fence_after();
     if (ok) {
       const uint32_t lane_addr = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
 #pragma unroll
-      for (int sub = 0; sub < 2; ++sub) {
-        long long T[16];
+      for (int sub = 0; sub < 4; ++sub) {
+        long long tot[8];
+        oz_read8(lane_addr, half * 32 + sub * 8, tot);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) T[j] = 0;
-#pragma unroll 1
-        for (int l = 0; l < OZ_LEVELS; ++l) {
-          float a[16];
-          tc_tmem_ld16(lane_addr + static_cast<uint32_t>(l * OZ_TILE + half * 32 + sub * 16), a);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const long long iv = static_cast<long long>(__float2int_rn(a[j]));
-            if (l <= 4) V[sub * 16 + j] += iv * (1LL << (32 - 8 * l));
-            else T[j] += iv * (1LL << (8 * (7 - l)));
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) V[sub * 16 + j] += T[j] >> 24;
+        for (int j = 0; j < 8; ++j) V[sub * 8 + j] += tot[j];
       }
     }
     // the accumulators and the operand tiles are reused by the next chunk
@@ -427,29 +484,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(G g, int* status) {
     tc_fence_after();
   }
   if (ok) {
+    const OzRow R = g.row(v);
+    const long long* coff = S.coff + (R.upper ? 0 : OZ_TILE);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-      const int u = u0 + half * 32 + j;
-      if (!g.keep(v, u)) continue;
-      const int sc = emax_x + fexp[half * 32 + j] - 2044 - 48;
-      bool fine = true;
-      double d = oz_i2d(V[j], sc, fine);
-      if (!fine) {
-        const int h1 = sc / 2, h2 = sc - h1;
-        d = (static_cast<double>(V[j]) * __longlong_as_double((long long)(h1 + 1023) << 52)) *
-            __longlong_as_double((long long)(h2 + 1023) << 52);
-      }
-      double* c = g.ptr(v, u, p);
-      *c = *c - d;
+      const int c = half * 32 + j, u = u0 + c;
+      if (u < R.lo || u >= R.hi) continue;
+      double* cp = reinterpret_cast<double*>(R.base + coff[c]) + p;
+      *cp = *cp - oz_value(V[j], emax_x + S.fexp[c] - 2044 - 48);
     }
   }
-  if (!ok && tid == 0) atomicExch(status, OZ_TIMEOUT_CODE);
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    tc_tmem_dealloc(tmem, OZ_LEVELS * OZ_TILE);
-  }
+  oz_end<G>(S, tmem, ok, status);
 }
 
 }  // namespace mlqp

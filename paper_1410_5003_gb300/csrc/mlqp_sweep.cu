@@ -640,23 +640,30 @@ struct OzSweep {
     if (u < tr + nb) return top[(size_t)(nlt + nt + (u - tr)) * ldt + row];
     return ftop[row];
   }
-  __device__ bool keep(int v, int u) const {
-    if (v >= nrows || u >= ncols) return false;
-    const bool next_block = v < tr && u < wn;
-    return mode == 0 || (mode == 1) == next_block;
-  }
-  __device__ double* ptr(int v, int u, int p) const {
-    double2* c;
+  // Row v: the top rows (v < tr) in the E, T and right-hand-side columns of
+  // block row t, the bottom rows in those of block row t + 1; the look-ahead
+  // modes keep the next panel's columns of the top rows (mode 1) or the rest
+  // (mode 2).
+  __device__ OzRow row(int v) const {
+    if (v >= nrows) return OzRow{top, 0, 0, true};
     if (v < tr) {
-      const int row = k + w + v;
-      c = (u < tr) ? top + (size_t)(nlt + k + w + u) * ldt + row
-                   : (u < tr + nb) ? top + (size_t)(nlt + nt + (u - tr)) * ldt + row : ftop + row;
-    } else {
-      const int row = v - tr;
-      c = (u < tr) ? bot + (size_t)(k + w + u) * ldb + row
-                   : (u < tr + nb) ? bot + (size_t)(nt + (u - tr)) * ldb + row : fbot + row;
+      const int lo = (mode == 2) ? wn : 0, hi = (mode == 1) ? wn : ncols;
+      return OzRow{top + (k + w + v), lo, hi, true};
     }
-    return reinterpret_cast<double*>(c) + p;
+    return OzRow{bot + (v - tr), 0, ncols, false};
+  }
+  // Element offset of column u from a row's base: E columns, T columns, then
+  // the right-hand side (a separate array: the pointer difference).
+  __device__ long long col_off(bool upper, int u) const {
+    if (upper) {
+      if (u < tr) return (long long)(nlt + k + w + u) * ldt;
+      if (u < tr + nb) return (long long)(nlt + nt + (u - tr)) * ldt;
+      return ftop - top;
+    }
+    if (!bot) return 0;
+    if (u < tr) return (long long)(k + w + u) * ldb;
+    if (u < tr + nb) return (long long)(nt + (u - tr)) * ldb;
+    return fbot - bot;
   }
 };
 
