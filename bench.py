@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-small", action="store_true", help="skip the 20-interface leg")
     ap.add_argument("--lookahead", type=int, choices=[0, 1], default=None,
                     help="with --no-autotune: the block LU's look-ahead shape (default 0)")
+    ap.add_argument("--panel-cluster", type=int, choices=[8, 16], default=None,
+                    help="with --no-autotune: CTAs per panel cluster of the block LU (default 8)")
     ap.add_argument("--gradient", action="store_true",
                     help="also time mlqp_fd_gradient on the 20-interface stack (one shape parameter)")
     ap.add_argument("--config5", action="store_true",
@@ -488,7 +490,7 @@ def angle_sweep(mlqp, dev, chunk=32):
 # proportion to the interfaces: every interface's sweep step touches the same
 # sizes); None until captured for the current kernels.
 SWEEP_TRAFFIC_BYTES_PER_INTERFACE = 37.45e6
-SWEEP_TRAFFIC_SHAPES = {"angle_groups": 1, "lookahead": 1}  # the shapes the FP64 sweep depends on
+SWEEP_TRAFFIC_SHAPES = {"angle_groups": 1, "lookahead": 1, "panel_cluster": 8}  # the shapes the FP64 sweep depends on
 SWEEP_TRAFFIC_NOTE = ("DRAM bytes read + written by the sweep kernels per step: 37.4 MB per interface from one ncu "
                       "capture of the first 40 interfaces (launch shapes SWEEP_TRAFFIC_SHAPES), times the interfaces")
 
@@ -606,8 +608,10 @@ def main():
     ctx = mlqp.Context(prob, device=dev)
     # launch shapes timed on this problem (untimed setup)
     if args.no_autotune:
-        tuned = {"qr_cluster": 8, "angle_groups": 1, "update_tile": None, "lookahead": args.lookahead or 0}
+        tuned = {"qr_cluster": 8, "angle_groups": 1, "update_tile": None, "lookahead": args.lookahead or 0,
+                 "panel_cluster": args.panel_cluster or 8}
         ctx.set_shape(mlqp.TUNE_LOOKAHEAD, tuned["lookahead"])
+        ctx.set_shape(mlqp.TUNE_PANEL, tuned["panel_cluster"])
     else:
         tuned = ctx.autotune()
     out = ctx.outputs()
@@ -653,6 +657,7 @@ def main():
                                              "angle_groups": shape(tuned["angle_groups"]),
                                              "update_tile": shape(tuned.get("update_tile")),
                                              "lookahead": shape(tuned.get("lookahead")),
+                                             "panel_cluster": shape(tuned.get("panel_cluster")),
                                              "source": "defaults" if args.no_autotune else "mlqp_autotune"}},
                 "flux_error": flux, "meets_flux_gate_1e-9": flux <= 1e-9,
                 "stage_ms": stage_ms, "dominant_stage": max(stage_ms, key=stage_ms.get),
@@ -701,7 +706,7 @@ def main():
                "block_solver": "sweep" if solver == mlqp.MLQP_SWEEP else "cyclic reduction",
                "launch_shapes": {k: shape(v) for k, v in mtuned.items()
                                  if k in ("qr_cluster", "angle_groups", "cr_cluster_cap", "update_tile",
-                                          "lookahead")},
+                                          "lookahead", "panel_cluster")},
                "dtype": "f32 Schur/LU + f64 refinement (fill, least squares, residuals in f64)"}
         res.update(refine_info(mlqp, mctx))
         mctx.close()

@@ -348,27 +348,31 @@ mlqp_status mlqp_set_problem(mlqp_ctx* ctx, const mlqp_interface* ifaces, int I,
  * tensor cores in fixed 64 x 64 tiles), look-ahead in the block LU (off or on: the
  * next panel factored on a second stream beside the rest of each trailing
  * update, its CTAs reserving their SMs; not with MLQP_CYCLIC) and, with
- * MLQP_CYCLIC, the largest cluster of the cyclic-reduction LU (1, 2, 4, 8).  which selects them (MLQP_TUNE_*
+ * MLQP_CYCLIC, the largest cluster of the cyclic-reduction LU (1, 2, 4, 8),
+ * and the CTAs per panel cluster of the block LU (8, or 16 where the GPU
+ * offers non-portable clusters of 16; not with MLQP_CYCLIC).  which selects them (MLQP_TUNE_*
  * bits; MLQP_TUNE_ALL or 0 for all); the fastest of each is kept for later
  * solves.  None of them changes the arithmetic: results are bitwise those of
  * the default shapes.  report (may be NULL) receives MLQP_TUNE_REPORT
  * doubles: [QR cluster chosen, LSQ-stage ms for 1, 2, 4, 8; angle groups
  * chosen, block-solve ms for 1, 2, 3, 4 groups; CR cluster cap chosen,
  * block-solve ms for 1, 2, 4, 8; update tile chosen, block-solve ms for 16,
- * 32; look-ahead chosen (0 or 1), block-solve ms without and with it], NaN
+ * 32; look-ahead chosen (0 or 1), block-solve ms without and with it;
+ * panel cluster chosen, block-solve ms for 8 and 16 CTAs], NaN
  * where a candidate does not apply.  Sec. 3.4's angle
  * sweep is the intended use: tune on the first chunk, then mlqp_set_angles.
  * Errors: MLQP_ESTATE (not bound), MLQP_EINVAL (report too short),
  * MLQP_ECUDA. */
-enum { MLQP_TUNE_REPORT = 21 };
+enum { MLQP_TUNE_REPORT = 24 };
 enum { MLQP_TUNE_QR = 1, MLQP_TUNE_TILE = 2, MLQP_TUNE_GROUPS = 4, MLQP_TUNE_CR = 8, MLQP_TUNE_LOOKAHEAD = 16,
-       MLQP_TUNE_ALL = 31 };
+       MLQP_TUNE_PANEL = 32, MLQP_TUNE_ALL = 63 };
 mlqp_status mlqp_autotune(mlqp_ctx* ctx, int which, double* report, int report_len);
 
 /* Sets one launch shape of a bound context by hand (which: one MLQP_TUNE_*
  * bit; value: a candidate mlqp_autotune would try: QR cluster 1, 2, 4, 8;
  * update tile 16, 32; angle groups 1..min(n_theta, 4); cyclic-reduction
- * cluster cap 1, 2, 4, 8; look-ahead 0, 1).  The stage graphs are re-captured
+ * cluster cap 1, 2, 4, 8; look-ahead 0, 1; panel cluster 8, 16 (16:
+ * MLQP_EINVAL where the GPU does not offer it)).  The stage graphs are re-captured
  * at the next solve; the arithmetic, and so every result, is unchanged.
  * Errors: MLQP_ESTATE (not bound), MLQP_EINVAL, MLQP_ECUDA. */
 mlqp_status mlqp_set_shape(mlqp_ctx* ctx, int which, int value);

@@ -31,7 +31,7 @@ namespace mlqp {
 extern thread_local long g_launches;
 __global__ void k_compose_perm(Dev D, int* permv);
 __global__ void k_back_matvec(Dev D, int t, int a0);
-__global__ void k_back_trsv(Dev D, int t, int a0);
+cudaError_t launch_back_trsv(const Dev& D, int t, int a0, int na, int n, cudaStream_t s);
 
 __device__ __forceinline__ double wsum(double v) {
 #pragma unroll
@@ -261,7 +261,8 @@ cudaError_t launch_solve_rhs(const Dev& D, const int* n_host, const double2* f, 
   for (int t = D.I - 1; t >= 0; --t) {
     g_launches += 2;
     k_back_matvec<<<dim3((n_host[t] + 7) / 8, nt), 256, 0, s>>>(D, t, 0);
-    k_back_trsv<<<nt, TRSV_THREADS, sizeof(double2) * n_host[t], s>>>(D, t, 0);
+    const cudaError_t e = launch_back_trsv(D, t, 0, nt, n_host[t], s);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

@@ -22,6 +22,7 @@ cudaError_t launch_schur(const Dev& D, int max_tiles, cudaStream_t s);
 cudaError_t launch_sweep(const Dev& D, const int* n_host, const AngleStreams& A);
 cudaError_t launch_recover(const Dev& D, cudaStream_t s);
 cudaError_t sweep_configure(int maxn);
+bool sweep_panel16_ok();
 cudaError_t launch_schur32(const Dev& D, int max_tiles, cudaStream_t s);
 cudaError_t launch_solve_rhs(const Dev& D, const int* n_host, const double2* f, int* permv, double2* G,
                              cudaStream_t s);
@@ -100,7 +101,7 @@ struct mlqp_ctx {
   // launch shapes (mlqp_autotune): QR cluster size, cyclic-reduction LU
   // cluster cap, angle groups of the sweep (0: min(n_theta, MAX_ANGLE_STREAMS)),
   // tile edge of the block LU's trailing update
-  int qr_cl = 8, cr_cl_max = 8, angle_groups = 0, upd_tile = 16, lookahead = 0;
+  int qr_cl = 8, cr_cl_max = 8, angle_groups = 0, upd_tile = 16, lookahead = 0, panel_cl = 8;
   // the cyclic reduction's survivor updates on the tensor cores: survivors per
   // launch group, the job / prep tables (uploaded with the descriptors), the
   // launch groups in order, and the plan the launches read (tensor maps)
@@ -572,6 +573,7 @@ mlqp_status mlqp_bind(mlqp_ctx* c, void* dev_ws, size_t bytes, void* stream) {
   D.cr_cl_max = c->cr_cl_max;
   D.upd_tile = c->upd_tile;
   D.lookahead = c->lookahead;
+  D.panel_cl = c->panel_cl;
   D.yU = q.gap_U;  // the geometry kernel turns the gaps into y_U, y_D (stored in scal)
   D.yD = q.gap_D;
   D.maxN = c->maxN;
@@ -978,6 +980,12 @@ mlqp_status mlqp_set_shape(mlqp_ctx* c, int which, int value) {
       if (value != 0 && value != 1) return fail(c, MLQP_EINVAL, "look-ahead must be 0 or 1");
       c->lookahead = value;
       break;
+    case MLQP_TUNE_PANEL:
+      if (value != 8 && value != 16) return fail(c, MLQP_EINVAL, "panel cluster must be 8 or 16");
+      if (value == 16 && !sweep_panel16_ok())
+        return fail(c, MLQP_EINVAL, "clusters of 16 panel CTAs are not offered by this GPU");
+      c->panel_cl = value;
+      break;
     default:
       return fail(c, MLQP_EINVAL, "unknown launch shape %d", which);
   }
@@ -1058,7 +1066,25 @@ mlqp_status mlqp_autotune(mlqp_ctx* c, int which, double* report, int report_len
     c->lookahead = best;
     rep[18] = best;
   }
-  // 5. cluster cap of the cyclic-reduction LU
+  // 5. CTAs per panel cluster of the block LU
+  if (st == MLQP_OK && (which & MLQP_TUNE_PANEL) &&
+      !(c->prm.precision == MLQP_MIXED && c->prm.block_solver == MLQP_CYCLIC)) {
+    const int cand[2] = {8, 16};
+    int best = c->panel_cl;
+    double tb = INFINITY;
+    for (int q = 0; q < 2 && st == MLQP_OK; ++q) {
+      if (cand[q] == 16 && !sweep_panel16_ok()) continue;
+      c->panel_cl = cand[q];
+      double t = 0;
+      if ((st = apply_shapes(c)) == MLQP_OK && (st = time_stage(c, MLQP_STAGE_SWEEP, 3, &t)) == MLQP_OK) {
+        rep[22 + q] = t;
+        if (t < tb) tb = t, best = cand[q];
+      }
+    }
+    c->panel_cl = best;
+    rep[21] = best;
+  }
+  // 6. cluster cap of the cyclic-reduction LU
   if (st == MLQP_OK && (which & MLQP_TUNE_CR) && c->prm.block_solver == MLQP_CYCLIC) {
     const int cand[4] = {1, 2, 4, 8};
     int best = c->cr_cl_max;

@@ -197,6 +197,7 @@ struct Dev {
   int cr_cl_max;  // largest cluster of the cyclic-reduction LU (1..8)
   int upd_tile;   // tile edge of the block LU's trailing update (16 or 32)
   int lookahead;  // 1: the next panel factored beside the rest of each trailing update
+  int panel_cl;   // CTAs per panel cluster of the block LU (8 or 16)
   const TcPlan* tc;  // host side: tensor-core products of the cyclic reduction (MLQP_CYCLIC)
 };
 

@@ -50,9 +50,15 @@ constexpr int OZ_LEVELS = 8;      // l = s + t - 2 for s + t <= 9
 constexpr uint32_t OZ_XTILE = 128 * 128;   // bytes of one pair of X slices (128 rows x 128 bytes)
 constexpr uint32_t OZ_YTILE = 64 * 128;    // bytes of one pair of Y slices (64 rows x 128 bytes)
 constexpr size_t OZ_SMEM = 4 * OZ_XTILE + 4 * OZ_YTILE + 1024 + 2048 + 1024;
-// 120 KB of dynamic shared memory keeps one CTA per SM: its 512 tensor-memory
-// columns are then never contended.
-constexpr size_t OZ_SMEM_LAUNCH = 120 * 1024;
+// 100 KB of dynamic shared memory: with the 200-register bound and 256 threads
+// one update CTA fits on an SM (its 512 tensor-memory columns are then never
+// contended) and leaves room for one panel CTA (at least 116 KB), not two.
+constexpr size_t OZ_SMEM_LAUNCH = 100 * 1024;
+// Registers per thread of the update kernel: 256 x 200 leaves 14 K of an SM's
+// 64 K registers, room for a block-LU panel CTA (128 threads x at most 112)
+// beside an update CTA, so that the panel of the next step starts at once
+// under look-ahead instead of waiting for update CTAs to drain.
+constexpr int OZ_MAXREG = 200;
 static_assert(OZ_SMEM <= OZ_SMEM_LAUNCH, "tile state exceeds the launch's shared memory");
 constexpr int OZ_TIMEOUT_CODE = 5;  // MLQP_ETIMEOUT
 
@@ -319,7 +325,7 @@ __device__ __forceinline__ void oz_end(const OzShared& S, uint32_t tmem, bool ok
 }
 
 template <class G>
-__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(G g, int* status) {
+__global__ void __maxnreg__(OZ_MAXREG) k_oz_update(G g, int* status) {
   extern __shared__ unsigned char oz_raw[];
   const OzShared S = oz_shared(oz_raw);
   const int tid = threadIdx.x, warp = tid >> 5;

@@ -13,15 +13,17 @@
 // left block holds the multipliers.  Everything stays in place in the block
 // rows R_{i-1}, R_i.  The backward sweep solves U_i eta_i = g_i - U12_i eta_{i+1}.
 //
-// Each panel of NB columns takes three kernels: the panel factorisation (a
-// cluster of PCL CTAs per angle, panel rows split over their shared memory),
-// the row swaps / U12 rows / bottom multipliers (column- and row-parallel),
-// and the trailing update (16 x 16 or 32 x 32 tiles, complex 3M products).
-// With look-ahead (a launch shape, D.lookahead, chosen by mlqp_autotune), the
-// update first finishes the next panel's columns, and that panel is factored
-// on a second stream while the rest of the update runs; the panel CTAs then
-// reserve nearly all of their SMs' shared memory, so that no update CTA shares
-// an SM (and its FP64 pipes) with the latency-bound panel.
+// Each panel of NB columns takes: the panel factorisation (a cluster of 8 or
+// 16 CTAs per angle, panel rows split over their shared memory), the row
+// swaps and U12 rows (column-parallel), the bottom multipliers (row-parallel)
+// and the trailing update (FP64: on the tensor cores, mlqp_oz.cuh; FP32:
+// 16 x 16 or 32 x 32 tiles, complex 3M products).  With look-ahead (a launch
+// shape, D.lookahead, chosen by mlqp_autotune), the next panel's columns are
+// updated first, and that panel is factored on a second stream beside the
+// bottom multipliers and the rest of the update.  A panel CTA takes more than
+// half of an SM's shared memory (no two share an SM's FP64 pipes) but leaves
+// room, in shared memory and registers, for one update CTA beside it, so the
+// panel starts at once whatever the order in which the two are dispatched.
 // Angle groups run on streams of their own.  The kernels are templates on the
 // real type: FP64 for the plain path, FP32 for the factorisation of the
 // mixed-precision path (whose solves are refined in FP64, mlqp_mixed.cu).
@@ -117,16 +119,15 @@ __device__ void write_row_map(const Dev& D, int a, int k, int w, const int* s_pi
 // which every reader of the previous use has passed: one barrier per column.
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
-constexpr int PCL = 8;
+constexpr int PCL = 8;          // the portable cluster size; 16 (non-portable) where the GPU offers it
 constexpr int PCL_THREADS = 128;
-constexpr int PCL_SLOTS = 4;  // rows per lane: RC <= 32 PCL_SLOTS, so n_i <= 1024
+constexpr int PCL_SLOTS = 4;  // rows per lane: RC <= 32 PCL_SLOTS, so n_i <= 1024 with 8 CTAs
 constexpr int PCL_WARPS = PCL_THREADS / 32;
-constexpr size_t PANEL_SMEM_MIN = 116 * 1024;  // more than half of an SM's shared memory
-constexpr size_t PANEL_SMEM_RESERVE = 216 * 1024;  // look-ahead: leaves less than an update CTA's 12 KB
+constexpr size_t PANEL_SMEM_MIN = 116 * 1024;  // more than half of an SM's shared memory: one panel CTA per SM
+constexpr int PANEL_MAXREG = 112;  // with an update CTA (256 x 200 registers) on the same SM
 
-template <typename R>
-__global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
-    k_lu_panel_cl(Dev D, int t, int k, int a0) {
+template <typename R, int PC>
+__global__ void __maxnreg__(PANEL_MAXREG) k_lu_panel_cl(Dev D, int t, int k, int a0) {
   cg::cluster_group cl = cg::this_cluster();
   const int q = (int)cl.block_rank();
   const int a = a0 + blockIdx.y;
@@ -134,7 +135,7 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
   const IfaceDesc ft = D.ifc[t];
   const int w = min(NB, S.nt - k);
   const int rows = S.nt - k;
-  const int RC = (rows + PCL - 1) / PCL;
+  const int RC = (rows + PC - 1) / PC;
   const int p0 = q * RC;
   const int nown = max(0, min(rows, p0 + RC) - p0);
   vec2<R>* top = Mats<R>::rows(D) + a * D.r_stride + ft.row_off;
@@ -148,8 +149,8 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
   __shared__ __align__(16) vec2<R> s_crinv[2];
   __shared__ __align__(16) vec2<R> s_cand[2][NB];
   __shared__ __align__(16) vec2<R> s_rowc[2][NB];
-  __shared__ __align__(16) vec2<R> s_all[PCL][NB];
-  __shared__ __align__(16) vec2<R> s_arinv[PCL];
+  __shared__ __align__(16) vec2<R> s_all[PC][NB];
+  __shared__ __align__(16) vec2<R> s_arinv[PC];
   __shared__ __align__(16) vec2<R> s_rowcl[NB];
   __shared__ __align__(16) vec2<R> s_prow[NB];
   __shared__ __align__(16) vec2<R> s_prinv;
@@ -216,7 +217,7 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
     if (warp == 0) {
       // every remote load is issued before any shared-memory store, so they
       // overlap (the stores could otherwise alias the generic remote pointers)
-      constexpr int GU = (PCL * NB) / 32;
+      constexpr int GU = (PC * NB) / 32;
       vec2<R> cand[GU];
 #pragma unroll
       for (int u = 0; u < GU; ++u) {
@@ -226,7 +227,7 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
       unsigned key = 0;
       int ix = 0x7fffffff;
       vec2<R> rinv_r, rowc_r;
-      if (lane < PCL) {
+      if (lane < PC) {
         key = *cl.map_shared_rank(&s_key[cb], lane);
         ix = *cl.map_shared_rank(&s_idx[cb], lane);
         rinv_r = *cl.map_shared_rank(&s_crinv[cb], lane);
@@ -237,9 +238,9 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(PCL_THREADS)
         const int e = lane + 32 * u, rk = e / NB, j = e % NB;
         if (j < w) s_all[rk][j] = cand[u];
       }
-      if (lane < PCL) s_arinv[lane] = rinv_r;
+      if (lane < PC) s_arinv[lane] = rinv_r;
       if (lane < w) s_rowcl[lane] = rowc_r;
-      const unsigned pos = (lane < PCL && ix != 0x7fffffff) ? (unsigned)ix : 0xffffffffu;
+      const unsigned pos = (lane < PC && ix != 0x7fffffff) ? (unsigned)ix : 0xffffffffu;
       const unsigned kmax = __reduce_max_sync(0xffffffffu, (pos != 0xffffffffu) ? key : 0u);
       const unsigned pr_u = __reduce_min_sync(0xffffffffu, (pos != 0xffffffffu && key == kmax) ? pos : 0xffffffffu);
       __syncwarp();
@@ -707,13 +708,127 @@ __global__ void __launch_bounds__(256) k_back_matvec(Dev D, int t, int a0) {
   }
 }
 
-__global__ void __launch_bounds__(TRSV_THREADS) k_back_trsv(Dev D, int t, int a0) {
-  const int a = a0 + blockIdx.x;
+// U_t eta_t = y (y = g_t - U12_t eta_{t+1} in ETA on entry) on a cluster of BC
+// CTAs per angle: on one SM the n^2/2 complex MACs alone take about 130 us
+// for n = 512 at GB300's FP64 rate (2 FMA per clock per SM).  32-row blocks;
+// block b belongs to CTA b mod BC, which keeps its rows of y and its
+// diagonal blocks (columns scaled by 1/U_jj) in shared memory.  From the last
+// block up: the owner solves its diagonal block (one warp, shuffle
+// recurrence: v_r -= (U_rj / U_jj) v_j, then eta_j = v_j / U_jj) and
+// publishes eta_b; one cluster barrier; every CTA subtracts U[own rows,
+// block b] eta_b from its own blocks above b (8 threads per row, entries of U
+// loaded before the barrier).
+// ---------------------------------------------------------------------------
+constexpr int BT_THREADS = 256;
+
+template <int BC>
+__global__ void __launch_bounds__(BT_THREADS) k_back_trsv_cl(Dev D, int t, int a0) {
+  constexpr int MAXOWN = (32 + BC - 1) / BC;  // n <= 1024: at most 32 blocks
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank();
+  const int a = a0 + blockIdx.y;
   const IfaceDesc ft = D.ifc[t];
-  extern __shared__ __align__(16) unsigned char trsv_raw[];
-  upper_solve<double>(D.ROW + a * D.r_stride + ft.row_off + (size_t)ft.nl * ft.n, ft.n,
-                      D.UDINV + a * D.piv_stride + ft.eta_off, D.ETA + a * D.eta_stride + ft.eta_off,
-                      reinterpret_cast<double2*>(trsv_raw));
+  const int n = ft.n, nblk = (n + 31) / 32;
+  const double2* U = D.ROW + a * D.r_stride + ft.row_off + (size_t)ft.nl * n;
+  const double2* udinv = D.UDINV + a * D.piv_stride + ft.eta_off;
+  double2* y = D.ETA + a * D.eta_stride + ft.eta_off;
+  extern __shared__ __align__(16) unsigned char bt_raw[];
+  auto dg = reinterpret_cast<double2(*)[32][33]>(bt_raw);  // own diagonal blocks, [i][column j][row r]
+  __shared__ double2 ys[MAXOWN][32];
+  __shared__ double2 xpub[2][32];
+  __shared__ double2 xb[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nown = (nblk > q) ? (nblk - q + BC - 1) / BC : 0;  // own blocks b = q + BC i, i < nown
+  for (int i = 0; i < nown; ++i) {
+    const int i0 = 32 * (q + BC * i), w = min(32, n - i0);
+    for (int e = tid; e < 32; e += BT_THREADS) ys[i][e] = (e < w) ? y[i0 + e] : make_double2(0.0, 0.0);
+    for (int e = tid; e < w * w; e += BT_THREADS) {
+      const int r = e % w, j = e / w;
+      const cplx m = ld2(&U[(size_t)(i0 + j) * n + i0 + r]) * ld2(&udinv[i0 + j]);
+      dg[i][j][r] = make_double2(m.re, m.im);
+    }
+  }
+  __syncthreads();
+  const int r = tid >> 3, p = tid & 7;  // the update: row r of a block, columns 4p .. 4p + 3
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int owner = b % BC, i0 = 32 * b, w = min(32, n - i0);
+    double2 u[MAXOWN][4];
+#pragma unroll
+    for (int i = 0; i < MAXOWN; ++i) {
+      const int bb = q + BC * i;
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int j = 4 * p + jj;
+        u[i][jj] = (i < nown && bb < b && j < w) ? U[(size_t)(i0 + j) * n + 32 * bb + r] : make_double2(0.0, 0.0);
+      }
+    }
+    if (q == owner && warp == 0) {
+      const int ib = b / BC;
+      cplx v = (lane < w) ? ld2(&ys[ib][lane]) : C(0.0);
+      for (int j = w - 1; j > 0; --j) {
+        const double xr = __shfl_sync(0xffffffffu, v.re, j), xi = __shfl_sync(0xffffffffu, v.im, j);
+        if (lane < j) v = cfms(ld2(&dg[ib][j][lane]), C(xr, xi), v);
+      }
+      if (lane < w) {
+        v = v * ld2(&udinv[i0 + lane]);
+        st2(&ys[ib][lane], v);
+        st2(&xpub[b & 1][lane], v);
+      } else {
+        xpub[b & 1][lane] = make_double2(0.0, 0.0);
+      }
+    }
+    cl.sync();  // eta_b published
+    if (tid < 32) xb[tid] = *cl.map_shared_rank(&xpub[b & 1][tid], owner);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < MAXOWN; ++i) {
+      const int bb = q + BC * i;
+      if (i < nown && bb < b) {  // uniform over the CTA
+        cplx s = C(0.0);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) s = cfma(ld2(&u[i][jj]), ld2(&xb[4 * p + jj]), s);
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+          s.re += __shfl_xor_sync(0xffffffffu, s.re, o);
+          s.im += __shfl_xor_sync(0xffffffffu, s.im, o);
+        }
+        if (p == 0) st2(&ys[i][r], ld2(&ys[i][r]) - s);
+      }
+    }
+    __syncthreads();
+  }
+  cl.sync();  // no CTA exits while another may still read its published block
+  for (int i = 0; i < nown; ++i) {
+    const int i0 = 32 * (q + BC * i), w = min(32, n - i0);
+    for (int e = tid; e < w; e += BT_THREADS) y[i0 + e] = ys[i][e];
+  }
+}
+
+template <int BC>
+static cudaError_t launch_back_trsv_bc(const Dev& D, int t, int a0, int na, int n, cudaStream_t s) {
+  const int nblk = (n + 31) / 32;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(BC, na);
+  cfg.blockDim = dim3(BT_THREADS);
+  cfg.dynamicSmemBytes = (size_t)((nblk + BC - 1) / BC) * 32 * 33 * sizeof(double2);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = BC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_back_trsv_cl<BC>, D, t, a0);
+}
+
+bool sweep_panel16_ok();
+
+// The back substitution of interface t for angles a0 .. a0 + na - 1 (n its
+// unknowns): clusters of 16 CTAs where the GPU offers them, else 8.
+cudaError_t launch_back_trsv(const Dev& D, int t, int a0, int na, int n, cudaStream_t s) {
+  return sweep_panel16_ok() ? launch_back_trsv_bc<16>(D, t, a0, na, n, s)
+                            : launch_back_trsv_bc<8>(D, t, a0, na, n, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -756,6 +871,38 @@ __global__ void __launch_bounds__(128) k_recover(Dev D) {
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+// The panel on a cluster of PC CTAs per angle (extensible launch: the cluster
+// size is a launch attribute, so one kernel serves 8 and 16), at the highest
+// scheduling priority: it is the critical path, and the block scheduler then
+// prefers its CTAs to the trailing update's when both wait for SMs.
+static int highest_priority() {
+  static int prio = 1;
+  if (prio > 0) {
+    int least = 0, greatest = 0;
+    prio = (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess) ? greatest : 0;
+  }
+  return prio;
+}
+
+template <typename R, int PC>
+static cudaError_t launch_panel(const Dev& D, int t, int k, int a0, int na, size_t smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(PC, na);
+  cfg.blockDim = dim3(PCL_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = PC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributePriority;
+  at[1].val.priority = highest_priority();
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k_lu_panel_cl<R, PC>, D, t, k, a0);
+}
+
 // Trailing update of panel k (mode 0: everything; look-ahead: mode 1 the next
 // panel's columns of the top rows, mode 2 the rest), tr trailing top rows,
 // nb bottom rows, na angles from a0.  FP32 (the mixed form's factorisation):
@@ -805,15 +952,18 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
     const int nlt = (t > 0) ? n_host[t - 1] : 0;
     auto panel = [&](int k, cudaStream_t st) {
       const int w = (nt - k < NB) ? nt - k : NB;
-      const size_t rc = (size_t)((nt - k + PCL - 1) / PCL);
-      // FP64: at least PANEL_SMEM_MIN, so that no two panel CTAs share an SM's
-      // FP64 pipes.  FP32 (the mixed form's factorisation) is not FP64-bound:
-      // its panels may share SMs, which lets large angle batches run in one wave.
+      const int pc = (D.panel_cl == 16) ? 16 : PCL;
+      const size_t rc = (size_t)((nt - k + pc - 1) / pc);
+      // FP64 and under look-ahead: at least PANEL_SMEM_MIN, so that no two panel
+      // CTAs share an SM's FP64 pipes while an update CTA still fits beside one.
+      // FP32 without look-ahead: panels may share SMs, which lets large angle
+      // batches run in one wave.
       const size_t smem = std::max(rc * (w + 1) * sizeof(vec2<R>) + rc * sizeof(unsigned),
-                                   D.lookahead ? PANEL_SMEM_RESERVE
-                                               : (sizeof(R) == 8 ? PANEL_SMEM_MIN : size_t(0)));
+                                   (D.lookahead || sizeof(R) == 8) ? PANEL_SMEM_MIN : size_t(0));
       ++g_launches;
-      k_lu_panel_cl<R><<<dim3(PCL, na), PCL_THREADS, smem, st>>>(D, t, k, a0);
+      const cudaError_t el = (pc == 16) ? launch_panel<R, 16>(D, t, k, a0, na, smem, st)
+                                        : launch_panel<R, PCL>(D, t, k, a0, na, smem, st);
+      if (e == cudaSuccess) e = el;
     };
     panel(0, s);
     for (int k = 0; k < nt && e == cudaSuccess; k += NB) {
@@ -821,12 +971,14 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
       const int ncol = nlt + nt + nb + 1;
       const int n_col_ctas = (ncol + PREP_COLS - 1) / PREP_COLS;
       const int n_row_ctas = (nb + PREP_COLS - 1) / PREP_COLS;
+      // the row swaps and U12 rows, and the bottom multipliers, in one launch
+      // (with the multipliers a launch of their own beside the next panel, the
+      // sweep took 1.9 times as long: their FP64 work shared the panel's SMs)
       ++g_launches;
       k_lu_prep<R><<<dim3(n_col_ctas + n_row_ctas, na), PREP_THREADS, 0, s>>>(D, t, k, n_col_ctas, a0);
       const int tr = nt - k - w;
-      const int nrows = tr + nb, ncols = tr + nb + 1;
+      const int nrows = tr + nb;
       const int UT = (D.upd_tile == 16) ? 16 : 32;
-      const int tiles = ((nrows + UT - 1) / UT) * ((ncols + UT - 1) / UT);
       const int k2 = k + w;
       if (D.lookahead && k2 < nt) {
         // look-ahead: the next panel's columns first, then its factorisation on
@@ -899,8 +1051,8 @@ cudaError_t launch_sweep(const Dev& D, const int* n_host, const AngleStreams& A)
       ++g_launches;
       k_back_matvec<<<dim3((n_host[t] + 7) / 8, na), 256, 0, s>>>(D, t, a0);
       ++g_launches;
-      k_back_trsv<<<na, TRSV_THREADS, sizeof(double2) * n_host[t], s>>>(D, t, a0);
-      e = cudaGetLastError();
+      e = launch_back_trsv(D, t, a0, na, n_host[t], s);
+      if (e == cudaSuccess) e = cudaGetLastError();
     }
   }
   const cudaError_t j = join(A);
@@ -915,14 +1067,52 @@ cudaError_t launch_recover(const Dev& D, cudaStream_t s) {
 
 size_t sweep_panel_smem_max(int maxn) {
   const size_t rc = (size_t)((maxn + PCL - 1) / PCL);
-  return std::max(rc * (NB + 1) * sizeof(double2) + rc * sizeof(unsigned), PANEL_SMEM_RESERVE);
+  return std::max(rc * (NB + 1) * sizeof(double2) + rc * sizeof(unsigned), PANEL_SMEM_MIN);
+}
+
+template <typename R, int PC>
+static cudaError_t panel_configure(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_lu_panel_cl<R, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && PC > 8)
+    e = cudaFuncSetAttribute(k_lu_panel_cl<R, PC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+// True if clusters of 16 panel CTAs, each with more than half of an SM's
+// shared memory, can be resident on this GPU.
+bool sweep_panel16_ok() {
+  static int ok = -1;
+  if (ok >= 0) return ok == 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16, 1);
+  cfg.blockDim = dim3(PCL_THREADS);
+  cfg.dynamicSmemBytes = PANEL_SMEM_MIN;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 16;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  cudaError_t e = panel_configure<double, 16>(PANEL_SMEM_MIN);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_lu_panel_cl<double, 16>, &cfg);
+  if (e != cudaSuccess) cudaGetLastError();  // not offered: clear the error, keep clusters of 8
+  ok = (e == cudaSuccess && n > 0) ? 1 : 0;
+  return ok == 1;
 }
 
 cudaError_t sweep_configure(int maxn) {
   const size_t smem = sweep_panel_smem_max(maxn);
-  cudaError_t e = cudaFuncSetAttribute(k_lu_panel_cl<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_lu_panel_cl<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = panel_configure<double, PCL>(smem);
+  if (e == cudaSuccess) e = panel_configure<float, PCL>(smem);
+  if (e == cudaSuccess && sweep_panel16_ok()) {
+    e = panel_configure<double, 16>(smem);
+    if (e == cudaSuccess) e = panel_configure<float, 16>(smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_back_trsv_cl<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+  if (e == cudaSuccess)  // up to 4 diagonal blocks of 32 x 33 complex per CTA (n <= 1024 on 8 CTAs)
+    e = cudaFuncSetAttribute(k_back_trsv_cl<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 32 * 33 * 16);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_oz_update<OzSweep>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM_LAUNCH);
   return e;

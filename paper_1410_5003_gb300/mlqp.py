@@ -21,7 +21,7 @@ MLQP_FP64, MLQP_MIXED = 0, 1
 MLQP_SWEEP, MLQP_CYCLIC = 0, 1
 MLQP_IR, MLQP_GMRES_IR, MLQP_IR_GMRES = 0, 1, 2
 PARAM_INTERFACE, PARAM_LAYER = 1, 2
-TUNE_QR, TUNE_TILE, TUNE_GROUPS, TUNE_CR, TUNE_LOOKAHEAD, TUNE_ALL = 1, 2, 4, 8, 16, 31
+TUNE_QR, TUNE_TILE, TUNE_GROUPS, TUNE_CR, TUNE_LOOKAHEAD, TUNE_PANEL, TUNE_ALL = 1, 2, 4, 8, 16, 32, 63
 STAGE_GEOM, STAGE_FILL, STAGE_LSQ, STAGE_SCHUR, STAGE_SWEEP, STAGE_RECOVER = range(6)
 BLK_ROW, BLK_B, BLK_QP, BLK_CP, BLK_X, BLK_RHS, BLK_NODES, BLK_ETA, BLK_AMP, BLK_REFINE = range(10)
 
@@ -250,7 +250,7 @@ class Context:
         self.prob = prob
         self._keep = keep
 
-    TUNE_REPORT = 21
+    TUNE_REPORT = 24
 
     def autotune(self, which=TUNE_ALL):
         """mlqp_autotune: times candidate launch shapes (the TUNE_* bits of
@@ -263,7 +263,8 @@ class Context:
                 "angle_groups": r[5], "sweep_ms_by_groups": dict(zip((1, 2, 3, 4), r[6:10])),
                 "cr_cluster_cap": r[10], "sweep_ms_by_cr_cluster": dict(zip((1, 2, 4, 8), r[11:15])),
                 "update_tile": r[15], "sweep_ms_by_update_tile": dict(zip((16, 32), r[16:18])),
-                "lookahead": r[18], "sweep_ms_by_lookahead": dict(zip((0, 1), r[19:21]))}
+                "lookahead": r[18], "sweep_ms_by_lookahead": dict(zip((0, 1), r[19:21])),
+                "panel_cluster": r[21], "sweep_ms_by_panel_cluster": dict(zip((8, 16), r[22:24]))}
 
     def set_shape(self, which, value):
         """mlqp_set_shape: one launch shape (a TUNE_* bit) set by hand."""

@@ -178,9 +178,10 @@ def test_autotune_needs_a_bound_context(M):
     from workloads import small_stack
     import ctypes as ct
     ctx, _ = M.mlqp_setup(small_stack(I=2))
-    rep = (ct.c_double * 21)()
-    assert lib.mlqp_autotune(ctx, 0, rep, 21) == M.MLQP_ESTATE
-    assert lib.mlqp_autotune(None, 0, rep, 21) == M.MLQP_EINVAL
+    rep = (ct.c_double * 24)()
+    assert lib.mlqp_autotune(ctx, 0, rep, 24) == M.MLQP_ESTATE
+    assert lib.mlqp_autotune(None, 0, rep, 24) == M.MLQP_EINVAL
+    assert lib.mlqp_set_shape(ctx, M.TUNE_PANEL, 16) == M.MLQP_ESTATE
     assert lib.mlqp_set_shape(ctx, M.TUNE_LOOKAHEAD, 1) == M.MLQP_ESTATE
     assert lib.mlqp_set_shape(None, M.TUNE_LOOKAHEAD, 1) == M.MLQP_EINVAL
     lib.mlqp_destroy(ctx)

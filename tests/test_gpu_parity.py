@@ -526,10 +526,11 @@ def test_autotune_keeps_results_bitwise(M, form):
     assert 1 <= rep["angle_groups"] <= min(4, prob.n_theta)
     if form == "mixed_cyclic":
         assert rep["cr_cluster_cap"] in (1, 2, 4, 8) and math.isnan(rep["update_tile"])
-        assert math.isnan(rep["lookahead"])
+        assert math.isnan(rep["lookahead"]) and math.isnan(rep["panel_cluster"])
     else:
         assert math.isnan(rep["cr_cluster_cap"]) and math.isnan(rep["update_tile"])  # FP64: tensor-core update
         assert rep["lookahead"] in (0, 1) and all(t > 0 for t in rep["sweep_ms_by_lookahead"].values())
+        assert rep["panel_cluster"] in (8, 16) and rep["sweep_ms_by_panel_cluster"][8] > 0
     r1 = ctx.solve_host()
     ctx.close()
     assert np.array_equal(r0["aU"], r1["aU"]) and np.array_equal(r0["aD"], r1["aD"])
@@ -540,14 +541,22 @@ def test_lookahead_keeps_results_bitwise(M, name, precision):
     """The block LU with look-ahead (the next panel factored on a second
     stream beside the rest of each trailing update, mlqp_set_shape) gives
     bitwise the amplitudes of the LU without it, in FP64 and in the mixed
-    form's FP32 factorisation, with one angle group and with two."""
+    form's FP32 factorisation, with one angle group and with two, and with
+    panel clusters of 8 and (where offered) 16 CTAs."""
     prob = PROBLEMS[name]()
     kw = dict(precision=M.MLQP_MIXED) if precision else {}
     outs = []
-    for la, groups in ((0, 1), (1, 1), (1, min(2, prob.n_theta))):
+    shapes = [(0, 1, 8), (1, 1, 8), (1, min(2, prob.n_theta), 8), (1, 1, 16), (0, min(2, prob.n_theta), 16)]
+    for la, groups, pc in shapes:
         ctx = M.Context(prob, **kw)
         ctx.set_shape(M.TUNE_LOOKAHEAD, la)
         ctx.set_shape(M.TUNE_GROUPS, groups)
+        try:
+            ctx.set_shape(M.TUNE_PANEL, pc)
+        except M.MlqpError as e:  # clusters of 16 not offered by this GPU
+            assert pc == 16 and e.status == M.MLQP_EINVAL
+            ctx.close()
+            continue
         outs.append(ctx.solve_host())
         ctx.close()
     for o in outs[1:]:
