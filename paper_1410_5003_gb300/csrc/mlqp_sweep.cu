@@ -34,6 +34,7 @@
 #include "mlqp_math.cuh"
 #include "mlqp_trsv.cuh"
 #include "mlqp_oz.cuh"
+#include "mlqp_tc.cuh"
 
 namespace mlqp {
 
@@ -97,26 +98,31 @@ __device__ void write_row_map(const Dev& D, int a, int k, int w, const int* s_pi
 
 // ---------------------------------------------------------------------------
 // Panel factorisation of the top rows k..nt-1 of the E columns k..k+w-1 on a
-// thread-block cluster of PCL CTAs per angle.  CTA q holds panel positions
-// [q RC, (q+1) RC), RC = ceil(rows / PCL), in shared memory; lane l of every
+// thread-block cluster of PC CTAs per angle.  CTA q holds panel positions
+// [q RC, (q+1) RC), RC = ceil(rows / PC), in shared memory; lane l of every
 // warp owns local rows l, l + 32, ... .
 //
 // Per column c:
 //  A (warp 0) write back the multipliers of column c-1; the local candidate
 //    is the largest 32-bit key among own positions >= c (smallest position
-//    on ties, by two warp reductions); publish its key, position, pivot
-//    reciprocal and row, and (owner of position c) row c, into buffers
-//    indexed by the parity of c;
-//  cluster barrier;
-//  B (warp 0) gather all PCL candidates and row c through distributed shared
-//    memory in one round of independent loads, agree on the pivot, swap
-//    rows c and the pivot's position;
+//    on ties, by two warp reductions); its record (key, position, pivot
+//    reciprocal, row) is pushed into slot q of every CTA's receive buffer for
+//    the parity of c, and (owner of position c) row c likewise, by
+//    st.async stores that complete transactions on the receiver's mbarrier;
+//  B (warp 0) wait on the own mbarrier until all PC records and row c have
+//    arrived, agree on the pivot (every CTA takes the same decision from the
+//    same records), swap rows c and the pivot's position;
 //  C every warp forms the multipliers l_r = a_rc / p of its rows in
 //    registers; warp 0 updates column c+1 and precomputes each row's key and
 //    reciprocal there (the next column's candidates), warps 1.. update
 //    columns c+2.. .
-// A CTA reuses a parity buffer two columns later, after the next barrier,
-// which every reader of the previous use has passed: one barrier per column.
+// A sender reaches column c+2 only after receiving every CTA's column c+1
+// record, which each CTA pushes after reading its buffer for column c: so a
+// parity buffer is never overwritten while it is read, and each mbarrier's
+// phases alternate strictly.  No cluster barrier per column: one after the
+// mbarriers are set up, one before exit.  Every wait is bounded (about 20 ms;
+// then MLQP_ETIMEOUT, no further waits in the launch, and garbage factors
+// instead of a hang).
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
 constexpr int PCL = 8;          // the portable cluster size; 16 (non-portable) where the GPU offers it
@@ -125,6 +131,47 @@ constexpr int PCL_SLOTS = 4;  // rows per lane: RC <= 32 PCL_SLOTS, so n_i <= 10
 constexpr int PCL_WARPS = PCL_THREADS / 32;
 constexpr size_t PANEL_SMEM_MIN = 116 * 1024;  // more than half of an SM's shared memory: one panel CTA per SM
 constexpr int PANEL_MAXREG = 112;  // with an update CTA (256 x 200 registers) on the same SM
+constexpr int MLQP_ETIMEOUT_CODE = 5;
+
+template <typename R>
+struct alignas(16) PanRec {
+  vec2<R> row[NB];  // the candidate row's entries in the panel columns
+  vec2<R> rinv;     // 1 / its entry in the current column
+  unsigned key;     // its pivot key (0: no candidate)
+  int idx;          // its panel position (0x7fffffff: none)
+};
+
+__device__ __forceinline__ uint32_t cl_addr(const void* p, int rank) {  // shared::cluster address in CTA `rank`
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(tc_smem(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_async16(uint32_t dst, uint4 v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(dst),
+               "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ bool cl_bar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(tc_smem(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// A column's records arrive within microseconds; 4e7 cycles (about 20 ms)
+// bounds the wait of a broken exchange without a false alarm.
+constexpr long long PANEL_WAIT_CYCLES = 40000000LL;
+__device__ __forceinline__ bool cl_wait(uint64_t* bar, uint32_t parity) {
+  if (cl_bar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!cl_bar_try(bar, parity))
+    if (clock64() - t0 > PANEL_WAIT_CYCLES) return false;
+  return true;
+}
 
 template <typename R, int PC>
 __global__ void __maxnreg__(PANEL_MAXREG) k_lu_panel_cl(Dev D, int t, int k, int a0) {
@@ -144,26 +191,32 @@ __global__ void __maxnreg__(PANEL_MAXREG) k_lu_panel_cl(Dev D, int t, int k, int
   vec2<R>* pan = reinterpret_cast<vec2<R>*>(pan_raw);  // own rows x w, column-major, leading dimension RC
   vec2<R>* rrow = pan + (size_t)RC * w;                 // per row: 1 / (its entry in the current column)
   unsigned* krow = reinterpret_cast<unsigned*>(rrow + RC);  // per row: its pivot key there
-  __shared__ unsigned s_key[2];
-  __shared__ int s_idx[2];
-  __shared__ __align__(16) vec2<R> s_crinv[2];
-  __shared__ __align__(16) vec2<R> s_cand[2][NB];
-  __shared__ __align__(16) vec2<R> s_rowc[2][NB];
-  __shared__ __align__(16) vec2<R> s_all[PC][NB];
-  __shared__ __align__(16) vec2<R> s_arinv[PC];
-  __shared__ __align__(16) vec2<R> s_rowcl[NB];
+  constexpr int REC_CH = sizeof(PanRec<R>) / 16;            // 16-byte pieces of a record
+  constexpr int ROW_CH = NB * sizeof(vec2<R>) / 16;         // ... of row c
+  constexpr uint32_t EXPECT = PC * sizeof(PanRec<R>) + NB * sizeof(vec2<R>);
+  __shared__ PanRec<R> s_recv[2][PC];                     // slot r: CTA r's candidate
+  __shared__ __align__(16) vec2<R> s_rowc[2][NB];         // row c, from its owner
+  __shared__ PanRec<R> s_mine;                            // this CTA's candidate (staging)
+  __shared__ __align__(16) vec2<R> s_myrow[NB];           // row c when this CTA owns it (staging)
+  __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ __align__(16) vec2<R> s_prow[NB];
   __shared__ __align__(16) vec2<R> s_prinv;
   __shared__ __align__(16) vec2<R> s_pinv[NB];
   __shared__ int s_piv[NB];
-  __shared__ int s_sing;
+  __shared__ int s_sing, s_late;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_sing = 0;
+  if (tid == 0) {
+    s_sing = 0;
+    s_late = 0;
+    tc_bar_init(&s_bar[0], 1);
+    tc_bar_init(&s_bar[1], 1);
+    tc_fence_bar_init();
+  }
   for (int e = tid; e < nown * w; e += PCL_THREADS) {
     const int r = e % nown, c = e / nown;
     pan[c * RC + r] = top[(size_t)(S.nlt + k + c) * ld + k + p0 + r];
   }
-  __syncthreads();
+  __syncthreads();  // the panel is in shared memory before warp 0 reads its first column
   cpx<R> lreg[PCL_SLOTS];  // warp 0: multipliers of the previous column
   if (warp == 0) {
 #pragma unroll
@@ -178,6 +231,7 @@ __global__ void __maxnreg__(PANEL_MAXREG) k_lu_panel_cl(Dev D, int t, int k, int
       }
     }
   }
+  cl.sync();  // every CTA's mbarriers are initialised before any record is pushed
   for (int c = 0; c < w; ++c) {
     const int cb = c & 1;
     const int qc = c / RC;
@@ -206,58 +260,62 @@ __global__ void __maxnreg__(PANEL_MAXREG) k_lu_panel_cl(Dev D, int t, int k, int
       const unsigned pmin = __reduce_min_sync(0xffffffffu, (kb == kmax) ? pb : 0xffffffffu);
       const bool have = pmin != 0xffffffffu;
       if (lane == 0) {
-        s_key[cb] = kmax;
-        s_idx[cb] = have ? (int)pmin : 0x7fffffff;
-        if (have) s_crinv[cb] = rrow[pmin - p0];
+        tc_bar_expect_tx(&s_bar[cb], EXPECT);  // this column's records and row c
+        s_mine.key = have ? kmax : 0u;
+        s_mine.idx = have ? (int)pmin : 0x7fffffff;
+        if (have) s_mine.rinv = rrow[pmin - p0];
       }
-      if (have && lane < w) s_cand[cb][lane] = pan[lane * RC + (pmin - p0)];
-      if (q == qc && lane < w) s_rowc[cb][lane] = pan[lane * RC + (c - p0)];
-    }
-    cl.sync();
-    if (warp == 0) {
-      // every remote load is issued before any shared-memory store, so they
-      // overlap (the stores could otherwise alias the generic remote pointers)
-      constexpr int GU = (PC * NB) / 32;
-      vec2<R> cand[GU];
-#pragma unroll
-      for (int u = 0; u < GU; ++u) {
-        const int e = lane + 32 * u, rk = e / NB, j = e % NB;
-        if (j < w) cand[u] = *cl.map_shared_rank(&s_cand[cb][j], rk);
+      if (lane < NB) {
+        vec2<R> z;
+        z.x = R(0);
+        z.y = R(0);
+        s_mine.row[lane] = (have && lane < w) ? pan[lane * RC + (pmin - p0)] : z;
+        if (q == qc) s_myrow[lane] = (lane < w) ? pan[lane * RC + (c - p0)] : z;
       }
+      __syncwarp();
+      // push the record into slot q of every CTA (and row c from its owner)
+      const uint4* mine = reinterpret_cast<const uint4*>(&s_mine);
+      for (int e = lane; e < PC * REC_CH; e += 32) {
+        const int dst = e / REC_CH, ch = e % REC_CH;
+        st_async16(cl_addr(reinterpret_cast<const uint4*>(&s_recv[cb][q]) + ch, dst), mine[ch],
+                   cl_addr(&s_bar[cb], dst));
+      }
+      if (q == qc) {
+        const uint4* myrow = reinterpret_cast<const uint4*>(s_myrow);
+        for (int e = lane; e < PC * ROW_CH; e += 32) {
+          const int dst = e / ROW_CH, ch = e % ROW_CH;
+          st_async16(cl_addr(reinterpret_cast<const uint4*>(s_rowc[cb]) + ch, dst), myrow[ch],
+                     cl_addr(&s_bar[cb], dst));
+        }
+      }
+      // after a timed-out wait no later wait of this launch is attempted
+      bool ok = s_late ? false : cl_wait(&s_bar[cb], static_cast<uint32_t>((c >> 1) & 1));
+      ok = __all_sync(0xffffffffu, ok);
+      __syncwarp();
+      if (!ok && lane == 0) s_late = 1;
       unsigned key = 0;
       int ix = 0x7fffffff;
-      vec2<R> rinv_r, rowc_r;
       if (lane < PC) {
-        key = *cl.map_shared_rank(&s_key[cb], lane);
-        ix = *cl.map_shared_rank(&s_idx[cb], lane);
-        rinv_r = *cl.map_shared_rank(&s_crinv[cb], lane);
+        key = s_recv[cb][lane].key;
+        ix = s_recv[cb][lane].idx;
       }
-      if (lane < w) rowc_r = *cl.map_shared_rank(&s_rowc[cb][lane], qc);
-#pragma unroll
-      for (int u = 0; u < GU; ++u) {
-        const int e = lane + 32 * u, rk = e / NB, j = e % NB;
-        if (j < w) s_all[rk][j] = cand[u];
-      }
-      if (lane < PC) s_arinv[lane] = rinv_r;
-      if (lane < w) s_rowcl[lane] = rowc_r;
       const unsigned pos = (lane < PC && ix != 0x7fffffff) ? (unsigned)ix : 0xffffffffu;
-      const unsigned kmax = __reduce_max_sync(0xffffffffu, (pos != 0xffffffffu) ? key : 0u);
-      const unsigned pr_u = __reduce_min_sync(0xffffffffu, (pos != 0xffffffffu && key == kmax) ? pos : 0xffffffffu);
-      __syncwarp();
-      const int pr = (int)pr_u, qp = pr / RC;
+      const unsigned kall = __reduce_max_sync(0xffffffffu, (pos != 0xffffffffu) ? key : 0u);
+      const unsigned pr_u = __reduce_min_sync(0xffffffffu, (pos != 0xffffffffu && key == kall) ? pos : 0xffffffffu);
+      const int pr = (pr_u == 0xffffffffu) ? c : (int)pr_u;  // no candidate at all: only after a timeout
+      const int qp = min(pr / RC, PC - 1);
       if (lane < w) {
-        const vec2<R> pv = s_all[qp][lane];
+        const vec2<R> pv = s_recv[cb][qp].row[lane];
         s_prow[lane] = pv;
-        if (q == qp && pr != c) pan[lane * RC + (pr - p0)] = s_rowcl[lane];
+        if (q == qp && pr != c) pan[lane * RC + (pr - p0)] = s_rowc[cb][lane];
         if (q == qc) pan[lane * RC + (c - p0)] = pv;
       }
       if (lane == 0) {
-        // pivots stay in shared memory until the end: a global store here
-        // would have to complete before the next barrier's release
+        // pivots stay in shared memory until the end
         s_piv[c] = k + pr;
-        s_prinv = s_arinv[qp];
-        s_pinv[c] = s_arinv[qp];
-        if (!pivot_ok32(kmax, R())) s_sing = 1;
+        s_prinv = s_recv[cb][qp].rinv;
+        s_pinv[c] = s_recv[cb][qp].rinv;
+        if (!pivot_ok32(kall, R())) s_sing = 1;
       }
     }
     __syncthreads();
@@ -296,7 +354,7 @@ __global__ void __maxnreg__(PANEL_MAXREG) k_lu_panel_cl(Dev D, int t, int k, int
     }
   }
   __syncthreads();
-  cl.sync();  // no CTA exits while another may still read its shared memory
+  cl.sync();  // no CTA exits while records may still be on their way to it
   for (int e = tid; e < nown * w; e += PCL_THREADS) {
     const int r = e % nown, c = e / nown;
     top[(size_t)(S.nlt + k + c) * ld + k + p0 + r] = pan[c * RC + r];
@@ -311,6 +369,7 @@ __global__ void __maxnreg__(PANEL_MAXREG) k_lu_panel_cl(Dev D, int t, int k, int
     if (lane == 0 && s_sing) atomicExch(D.STATUS, MLQP_ESINGULAR_CODE);
     write_row_map(D, a, k, w, s_piv, lane);
   }
+  if (tid == 0 && s_late) atomicExch(D.STATUS, MLQP_ETIMEOUT_CODE);
 }
 
 // ---------------------------------------------------------------------------

@@ -453,12 +453,15 @@ def test_gmres_refinement_matches_oracle(M, name, solver):
 def test_gmres_refinement_where_plain_refinement_stalls(M):
     """100-interface angle-sweep stack, three of its angles where plain
     refinement stalls (omega 5e-10 to 3e-9 after 20 corrections):
-    kappa(A') eps_32 is near 1 there.  Flexible GMRES refinement brings the
-    backward error below 1e-15 in at most two corrections.  At the first two
-    angles the amplitudes then agree with the plain FP64 path to 1e-9.  The
-    third angle is ill-conditioned: two backward-stable FP64 solutions differ
-    there by about 1e-5 (below the discretisation's flux-balance error at that
-    angle, 3e-6), so only the backward error is checked."""
+    kappa(A') eps_32 is near 1 there, so kappa(A') is about 1e7 and two
+    backward-stable FP64 solutions may differ by kappa eps_64, a few 1e-9.
+    Flexible GMRES refinement brings the backward error below 1e-15 in at
+    most two corrections.  At the first two angles the amplitudes then agree
+    with the plain FP64 path to COND_TOL = 1e-8 (about 3 kappa eps_64).  The
+    third angle is worse conditioned: two backward-stable FP64 solutions
+    differ there by about 1e-5 (below the discretisation's flux-balance error
+    at that angle, 3e-6), so only the backward error is checked."""
+    COND_TOL = 1e-8
     th = np.asarray(config4().theta)
     prob = config4().with_angles(th[[64, 192, 224]])
     plain = M.Context(prob)
@@ -473,7 +476,7 @@ def test_gmres_refinement_where_plain_refinement_stalls(M):
         assert 1 <= inner <= 2 * 40 and inner_res < 1e-9, (a, inner, inner_res)
         if a < 2:
             ag = np.concatenate([out["aU"][a], out["aD"][a]])
-            assert rel(ag, np.concatenate([ref["aU"][a], ref["aD"][a]])) < AMP_TOL, a
+            assert rel(ag, np.concatenate([ref["aU"][a], ref["aD"][a]])) < COND_TOL, a
     ctx.close()
     # the default refinement (MLQP_IR_GMRES) starts plain, sees the stall and
     # finishes with GMRES corrections
@@ -485,7 +488,7 @@ def test_gmres_refinement_where_plain_refinement_stalls(M):
         assert omega <= 1e-15 and inner >= 1, (a, omega, steps, inner)
         if a < 2:
             ag = np.concatenate([out["aU"][a], out["aD"][a]])
-            assert rel(ag, np.concatenate([ref["aU"][a], ref["aD"][a]])) < AMP_TOL, a
+            assert rel(ag, np.concatenate([ref["aU"][a], ref["aD"][a]])) < COND_TOL, a
     auto.close()
 
 
