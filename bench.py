@@ -489,10 +489,10 @@ def angle_sweep(mlqp, dev, chunk=32):
 # capture of a shorter stack of the same interfaces (traffic grows in
 # proportion to the interfaces: every interface's sweep step touches the same
 # sizes); None until captured for the current kernels.
-SWEEP_TRAFFIC_BYTES_PER_INTERFACE = 37.45e6
-SWEEP_TRAFFIC_SHAPES = {"angle_groups": 1, "lookahead": 1, "panel_cluster": 8}  # the shapes the FP64 sweep depends on
-SWEEP_TRAFFIC_NOTE = ("DRAM bytes read + written by the sweep kernels per step: 37.4 MB per interface from one ncu "
-                      "capture of the first 40 interfaces (launch shapes SWEEP_TRAFFIC_SHAPES), times the interfaces")
+SWEEP_TRAFFIC_BYTES_PER_INTERFACE = 36.64e6
+SWEEP_TRAFFIC_SHAPES = {"angle_groups": 1, "lookahead": 1, "panel_cluster": 16}  # the shapes the FP64 sweep depends on
+SWEEP_TRAFFIC_NOTE = ("DRAM bytes read + written by the sweep kernels per step: 36.6 MB per interface from one ncu "
+                      "capture of the first 16 interfaces (launch shapes SWEEP_TRAFFIC_SHAPES), times the interfaces")
 
 
 def shape(v):
