@@ -248,24 +248,29 @@ __device__ __forceinline__ OzShared oz_shared(unsigned char* raw) {
 
 // Thread 0: the 72 BF16 MMAs of one chunk of K' = 32 (the 36 slice pairs
 // s + t <= 9, two K = 16 steps each) into the eight level accumulators; the
-// first product of each level overwrites it unless `accumulate`.
-__device__ __forceinline__ void oz_issue(const OzShared& S, uint32_t tmem, bool accumulate) {
+// first product of each level overwrites it.  Fully unrolled: the operand
+// descriptors differ from the tiles' base descriptors only in the start
+// address field (bits 0-13, address / 16, below 2^14 for any shared-memory
+// address), so each MMA costs an add and the issue, not a descriptor build.
+__device__ __forceinline__ void oz_issue(const OzShared& S, uint32_t tmem) {
   const uint32_t idesc = oz_idesc_bf16(2 * OZ_TILE, OZ_TILE);
-  const uint32_t xa = tc_smem(S.xs), ya = tc_smem(S.ys);
-  uint32_t started = accumulate ? 0xFFu : 0u;
-  for (int s = 1; s <= OZ_SLICES; ++s)
-    for (int t = 1; t <= OZ_SLICES && s + t <= 9; ++t) {
+  const uint64_t xd = tc_desc_sw128(tc_smem(S.xs)), yd = tc_desc_sw128(tc_smem(S.ys));
+#pragma unroll
+  for (int s = 1; s <= OZ_SLICES; ++s) {
+#pragma unroll
+    for (int t = 1; t <= OZ_SLICES; ++t) {
+      if (s + t > 9) continue;
       const int l = s + t - 2;
-      const uint32_t xo = xa + ((s - 1) >> 1) * OZ_XTILE + ((s - 1) & 1) * 64;
-      const uint32_t yo = ya + ((t - 1) >> 1) * OZ_YTILE + ((t - 1) & 1) * 64;
+      const bool first = s == (l - 5 > 1 ? l - 5 : 1);  // the level's first pair in this order
+      const uint32_t xo = ((s - 1) >> 1) * OZ_XTILE + ((s - 1) & 1) * 64;
+      const uint32_t yo = ((t - 1) >> 1) * OZ_YTILE + ((t - 1) & 1) * 64;
       const uint32_t acc = tmem + static_cast<uint32_t>(l * OZ_TILE);
 #pragma unroll
-      for (int ks = 0; ks < 2; ++ks) {  // K' = 32 as two K = 16 steps, 32 bytes apart
-        oz_mma_bf16(acc, tc_desc_sw128(xo + ks * 32), tc_desc_sw128(yo + ks * 32), idesc,
-                    ((started >> l) & 1u) ? 1u : 0u);
-        started |= 1u << l;
-      }
+      for (int ks = 0; ks < 2; ++ks)  // K' = 32 as two K = 16 steps, 32 bytes apart
+        oz_mma_bf16(acc, xd + ((xo + ks * 32) >> 4), yd + ((yo + ks * 32) >> 4), idesc,
+                    (first && ks == 0) ? 0u : 1u);
     }
+  }
   tc_commit(S.done);
 }
 
@@ -367,7 +372,7 @@ __global__ void __maxnreg__(OZ_MAXREG) k_oz_update(G g, int* status) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *S.tslot;
-  if (tid == 0) oz_issue(S, tmem, false);
+  if (tid == 0) oz_issue(S, tmem);
   // the epilogue: Out row m (TMEM lane m), columns half * 32 .. half * 32 + 31
   const int v = v0 + vl;
   const OzRow R = g.row(v);
@@ -470,7 +475,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(G g, int* status) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tid == 0) oz_issue(S, tmem, false);
+    if (tid == 0) oz_issue(S, tmem);
     ok = tc_wait(S.done, static_cast<uint32_t>(ch & 1));
     ok = __syncthreads_and(ok);
     tc_fence_after();
