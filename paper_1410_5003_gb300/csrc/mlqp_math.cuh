@@ -7,7 +7,7 @@
 //                  - J_{n+1} (A&S 9.12), normalised by e^{-iz} = J_0 + 2 sum
 //                  (-i)^n J_n; Y_0 from Neumann's series Y_0 = (2/pi)(ln(z/2)
 //                  + gamma) J_0 - (4/pi) sum (-1)^k J_{2k}/k (A&S 9.1.88) and
-//                  Y_1 = -Y_0' from the same J_n.  Real z < 64: degree-16
+//                  Y_1 = -Y_0' from the same J_n.  Real z < 64: degree-12
 //                  Taylor expansions about the centres of half-unit intervals
 //                  (coefficients from 30-digit derivatives, generated by
 //                  gen_bessel_taylor.py into mlqp_bessel_taylor.inc)
@@ -237,20 +237,22 @@ static __device__ __noinline__ Hank hankel_real(double x) {
     Y0 = TWO_OVER_PI * (L * J0 - sy0);
     Y1 = -TWO_OVER_PI / x + TWO_OVER_PI * L * J1 - 0.5 * INV_PI * x * sy1;
   } else if (x < 64.0) {
-    // local Taylor expansions of J0, J1, Y0, Y1 about the centre of x's
-    // half-unit interval (mlqp_bessel_taylor.inc), Horner in four independent
-    // chains: 64 FMAs instead of a Miller recurrence of 40-56 dependent steps
-    // (x < 20) or up to 40 asymptotic terms with a sincos (x >= 20)
+    // local Taylor expansions (degree 12) of J0, J1, Y0, Y1 about the centre
+    // of x's half-unit interval (mlqp_bessel_taylor.inc), Horner in four
+    // independent chains: 48 FMAs instead of a Miller recurrence of 40-56
+    // dependent steps (x < 20) or up to 40 asymptotic terms with a sincos
+    // (x >= 20)
+    constexpr int NC = BESSEL_TAYLOR_DEG + 1;
     const int m = min((int)((x - 4.0) * 2.0), 119);
     const double t = x - (4.25 + 0.5 * m);
-    const double* c = BESSEL_TAYLOR + m * 68;
-    double a0 = __ldg(c + 16), a1 = __ldg(c + 33), a2 = __ldg(c + 50), a3 = __ldg(c + 67);
+    const double* c = BESSEL_TAYLOR + m * 4 * NC;
+    double a0 = __ldg(c + NC - 1), a1 = __ldg(c + 2 * NC - 1), a2 = __ldg(c + 3 * NC - 1), a3 = __ldg(c + 4 * NC - 1);
 #pragma unroll
-    for (int k = 15; k >= 0; --k) {
+    for (int k = NC - 2; k >= 0; --k) {
       a0 = fma(a0, t, __ldg(c + k));
-      a1 = fma(a1, t, __ldg(c + 17 + k));
-      a2 = fma(a2, t, __ldg(c + 34 + k));
-      a3 = fma(a3, t, __ldg(c + 51 + k));
+      a1 = fma(a1, t, __ldg(c + NC + k));
+      a2 = fma(a2, t, __ldg(c + 2 * NC + k));
+      a3 = fma(a3, t, __ldg(c + 3 * NC + k));
     }
     J0 = a0;
     J1 = a1;
