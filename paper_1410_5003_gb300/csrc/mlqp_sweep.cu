@@ -59,6 +59,14 @@ __device__ __forceinline__ Step make_step(const Dev& D, int t) {
   return s;
 }
 
+// Programmatic dependent launch (look-ahead chain prep -> next panel's columns
+// -> next panel -> next prep, one stream): a kernel lets its dependent launch
+// once all its CTAs have started, and waits for its own predecessor's
+// completion (and memory) before touching any data.  Without the launch
+// attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Pivot rule of the panel factorisation: largest |re| + |im| (smallest
 // position on ties), compared as the bit patterns of the non-negative values
@@ -175,6 +183,8 @@ __device__ __forceinline__ bool cl_wait(uint64_t* bar, uint32_t parity) {
 
 template <typename R, int PC>
 __global__ void __maxnreg__(PANEL_MAXREG) k_lu_panel_cl(Dev D, int t, int k, int a0) {
+  pdl_wait();
+  pdl_release();
   cg::cluster_group cl = cg::this_cluster();
   const int q = (int)cl.block_rank();
   const int a = a0 + blockIdx.y;
@@ -385,6 +395,8 @@ constexpr int PREP_COLS = PREP_THREADS / 16;  // columns (or rows) per CTA
 
 template <typename R>
 __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, int n_col_ctas, int a0) {
+  pdl_wait();
+  pdl_release();
   const int a = a0 + blockIdx.y;
   const Step S = make_step(D, t);
   const IfaceDesc ft = D.ifc[t];
@@ -448,14 +460,22 @@ __global__ void __launch_bounds__(PREP_THREADS) k_lu_prep(Dev D, int t, int k, i
     const IfaceDesc fb = D.ifc[S.b];
     vec2<R>* bot = Mats<R>::rows(D) + a * D.r_stride + fb.row_off;  // left block = E columns
     const int ldb = S.nb;
+    // the strict upper triangle of U11 with row q scaled by 1/U_qq (in place:
+    // a row CTA alone reads it), so that the recurrence below carries the
+    // unscaled sums and the divisions leave its dependency chain
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int rr = e % w, cc = e / w;  // blk[cc w + rr] = U(rr, cc)
+      if (rr < cc) stv<R>(&blk[e], ldv<R>(&blk[e]) * ldv<R>(&sinv[rr]));
+    }
+    __syncthreads();
     cpx<R> x = mkc<R>(R(0));
     if (live && lane16 < w) x = ldv<R>(&bot[(size_t)(k + lane16) * ldb + r]);
     for (int q = 0; q < w; ++q) {
-      // lane q finalises x_q = (a_q - sum_{q' < q} x_q' U_q'q) / U_qq, then all lanes c > q use it
-      if (lane16 == q) x = x * ldv<R>(&sinv[q]);
+      // s_j -= s_q (U_qj / U_qq) for j > q, s_j = a_j - sum_{q < j} x_q U_qj: lane q's sum is final here
       const R xr = __shfl_sync(hmask, x.re, q, 16), xi = __shfl_sync(hmask, x.im, q, 16);
       if (lane16 > q && lane16 < w) x = cfms(mkc<R>(xr, xi), ldv<R>(&blk[lane16 * w + q]), x);
     }
+    if (lane16 < w) x = x * ldv<R>(&sinv[lane16]);  // x_j = s_j / U_jj
     if (live && lane16 < w) stv<R>(&bot[(size_t)(k + lane16) * ldb + r], x);
   }
 }
@@ -607,6 +627,8 @@ __global__ void __launch_bounds__(UpdShape<UTT>::TH) k_lu_update(Dev D, int t, i
 constexpr int NARROW_ROWS = 4;
 
 __global__ void __launch_bounds__(32 * NARROW_ROWS) k_lu_narrow(Dev D, int t, int k, int a0, int wn) {
+  pdl_wait();
+  pdl_release();
   const int a = a0 + blockIdx.y;
   const Step S = make_step(D, t);
   const IfaceDesc ft = D.ifc[t];
@@ -944,22 +966,41 @@ static int highest_priority() {
 }
 
 template <typename R, int PC>
-static cudaError_t launch_panel(const Dev& D, int t, int k, int a0, int na, size_t smem, cudaStream_t st) {
+static cudaError_t launch_panel(const Dev& D, int t, int k, int a0, int na, size_t smem, cudaStream_t st, bool pdl) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(PC, na);
   cfg.blockDim = dim3(PCL_THREADS);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[2];
+  cudaLaunchAttribute at[3];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = PC;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   at[1].id = cudaLaunchAttributePriority;
   at[1].val.priority = highest_priority();
+  at[2].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[2].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 2;
+  cfg.numAttrs = pdl ? 3 : 2;
   return cudaLaunchKernelEx(&cfg, k_lu_panel_cl<R, PC>, D, t, k, a0);
+}
+
+// A launch that may start before its stream predecessor completes (which
+// must then release it, and which it waits for: pdl_release / pdl_wait).
+template <typename... P, typename... A>
+static cudaError_t launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, cudaStream_t st, bool pdl, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 // Trailing update of panel k (mode 0: everything; look-ahead: mode 1 the next
@@ -971,10 +1012,11 @@ static cudaError_t launch_panel(const Dev& D, int t, int k, int a0, int na, size
 // latency, not its work, matters, on the critical path to the next panel.
 template <typename R>
 static void launch_update(const Dev& D, int ut, int tr, int nb, int na, cudaStream_t s, int t, int k, int a0,
-                          int mode, int wn) {
+                          int mode, int wn, bool pdl = false) {
   const int nrows = (mode == 1) ? tr : tr + nb, ncols = tr + nb + 1;
   if (sizeof(R) == 8 && mode == 1) {  // the next panel's columns: a narrow update, FP64 on the SIMT pipe
-    k_lu_narrow<<<dim3((tr + NARROW_ROWS - 1) / NARROW_ROWS, na), 32 * NARROW_ROWS, 0, s>>>(D, t, k, a0, wn);
+    launch_pdl(k_lu_narrow, dim3((tr + NARROW_ROWS - 1) / NARROW_ROWS, na), dim3(32 * NARROW_ROWS), s, pdl, D, t, k,
+               a0, wn);
     return;
   }
   if constexpr (sizeof(R) == 8) {
@@ -1002,14 +1044,14 @@ static void launch_update(const Dev& D, int ut, int tr, int nb, int na, cudaStre
 // FP32: factorisation of the mixed path on ROW32/F32), for angles a0..a0+na-1.
 template <typename R>
 cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaStream_t s, cudaStream_t ps,
-                          cudaEvent_t ev_next, cudaEvent_t ev_panel) {
+                          cudaEvent_t ev_next, cudaEvent_t ev_update) {
   const int I = D.I;
   cudaError_t e = cudaSuccess;
   for (int t = 0; t < I && e == cudaSuccess; ++t) {
     const int nt = n_host[t];
     const int nb = (t + 1 < I) ? n_host[t + 1] : 0;
     const int nlt = (t > 0) ? n_host[t - 1] : 0;
-    auto panel = [&](int k, cudaStream_t st) {
+    auto panel = [&](int k, cudaStream_t st, bool pdl) {
       const int w = (nt - k < NB) ? nt - k : NB;
       const int pc = (D.panel_cl == 16) ? 16 : PCL;
       const size_t rc = (size_t)((nt - k + pc - 1) / pc);
@@ -1020,11 +1062,11 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
       const size_t smem = std::max(rc * (w + 1) * sizeof(vec2<R>) + rc * sizeof(unsigned),
                                    (D.lookahead || sizeof(R) == 8) ? PANEL_SMEM_MIN : size_t(0));
       ++g_launches;
-      const cudaError_t el = (pc == 16) ? launch_panel<R, 16>(D, t, k, a0, na, smem, st)
-                                        : launch_panel<R, PCL>(D, t, k, a0, na, smem, st);
+      const cudaError_t el = (pc == 16) ? launch_panel<R, 16>(D, t, k, a0, na, smem, st, pdl)
+                                        : launch_panel<R, PCL>(D, t, k, a0, na, smem, st, pdl);
       if (e == cudaSuccess) e = el;
     };
-    panel(0, s);
+    panel(0, s, false);
     for (int k = 0; k < nt && e == cudaSuccess; k += NB) {
       const int w = (nt - k < NB) ? nt - k : NB;
       const int ncol = nlt + nt + nb + 1;
@@ -1033,25 +1075,29 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
       // the row swaps and U12 rows, and the bottom multipliers, in one launch
       // (with the multipliers a launch of their own beside the next panel, the
       // sweep took 1.9 times as long: their FP64 work shared the panel's SMs)
+      // under look-ahead the previous step's panel is this prep's stream predecessor
       ++g_launches;
-      k_lu_prep<R><<<dim3(n_col_ctas + n_row_ctas, na), PREP_THREADS, 0, s>>>(D, t, k, n_col_ctas, a0);
+      const cudaError_t ep = launch_pdl(k_lu_prep<R>, dim3(n_col_ctas + n_row_ctas, na), dim3(PREP_THREADS), s,
+                                        D.lookahead && k > 0, D, t, k, n_col_ctas, a0);
+      if (e == cudaSuccess) e = ep;
       const int tr = nt - k - w;
       const int nrows = tr + nb;
       const int UT = (D.upd_tile == 16) ? 16 : 32;
       const int k2 = k + w;
       if (D.lookahead && k2 < nt) {
-        // look-ahead: the next panel's columns first, then its factorisation on
-        // the panel stream beside the rest of this update
+        // look-ahead: the chain prep -> next panel's columns -> next panel runs
+        // on stream s (programmatic launches), the rest of this update on the
+        // second stream beside the next panel; the next prep waits for both
         const int wn = (nt - k2 < NB) ? nt - k2 : NB;
         ++g_launches;
-        launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 1, wn);
+        launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 1, wn, /*pdl=*/sizeof(R) == 8);
         if ((e = cudaEventRecord(ev_next, s)) != cudaSuccess) break;
         if ((e = cudaStreamWaitEvent(ps, ev_next, 0)) != cudaSuccess) break;
-        panel(k2, ps);
-        if ((e = cudaEventRecord(ev_panel, ps)) != cudaSuccess) break;
         ++g_launches;
-        launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 2, wn);
-        e = cudaStreamWaitEvent(s, ev_panel, 0);
+        launch_update<R>(D, UT, tr, nb, na, ps, t, k, a0, 2, wn);
+        if ((e = cudaEventRecord(ev_update, ps)) != cudaSuccess) break;
+        panel(k2, s, sizeof(R) == 8);
+        e = cudaStreamWaitEvent(s, ev_update, 0);
       } else {
         if (nrows > 0) {
           if (sizeof(R) == 8 && k2 < nt) {
@@ -1066,7 +1112,7 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
             launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 0, 0);
           }
         }
-        if (k2 < nt) panel(k2, s);
+        if (k2 < nt) panel(k2, s, false);
       }
     }
     if (e == cudaSuccess) e = cudaGetLastError();
