@@ -514,6 +514,8 @@ __device__ __forceinline__ V* row_col_ptr(V* top, int ldt, V* ftop, V* bot, int 
 
 template <typename R, int UTT>
 __global__ void __launch_bounds__(UpdShape<UTT>::TH) k_lu_update(Dev D, int t, int k, int a0, int mode, int wn) {
+  pdl_wait();
+  pdl_release();
   constexpr int UT = UTT, UPD_THREADS = UpdShape<UTT>::TH, RQ = UpdShape<UTT>::RQ, CZ = UpdShape<UTT>::CZ,
                 TXN = UpdShape<UTT>::TXN;
   // mode 0: the whole trailing block.  Look-ahead split: mode 1 updates only
@@ -1034,9 +1036,9 @@ static void launch_update(const Dev& D, int ut, int tr, int nb, int na, cudaStre
     const int tc = (mode == 1) ? 1 : (ncols + ut - 1) / ut;
     const dim3 grid(((nrows + ut - 1) / ut) * tc, na);
     if (ut == 16)
-      k_lu_update<R, 16><<<grid, UpdShape<16>::TH, 0, s>>>(D, t, k, a0, mode, wn);
+      launch_pdl(k_lu_update<R, 16>, grid, dim3(UpdShape<16>::TH), s, pdl, D, t, k, a0, mode, wn);
     else
-      k_lu_update<R, 32><<<grid, UpdShape<32>::TH, 0, s>>>(D, t, k, a0, mode, wn);
+      launch_pdl(k_lu_update<R, 32>, grid, dim3(UpdShape<32>::TH), s, pdl, D, t, k, a0, mode, wn);
   }
 }
 
@@ -1090,13 +1092,13 @@ cudaError_t launch_factor(const Dev& D, const int* n_host, int a0, int na, cudaS
         // second stream beside the next panel; the next prep waits for both
         const int wn = (nt - k2 < NB) ? nt - k2 : NB;
         ++g_launches;
-        launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 1, wn, /*pdl=*/sizeof(R) == 8);
+        launch_update<R>(D, UT, tr, nb, na, s, t, k, a0, 1, wn, /*pdl=*/true);
         if ((e = cudaEventRecord(ev_next, s)) != cudaSuccess) break;
         if ((e = cudaStreamWaitEvent(ps, ev_next, 0)) != cudaSuccess) break;
         ++g_launches;
         launch_update<R>(D, UT, tr, nb, na, ps, t, k, a0, 2, wn);
         if ((e = cudaEventRecord(ev_update, ps)) != cudaSuccess) break;
-        panel(k2, s, sizeof(R) == 8);
+        panel(k2, s, true);
         e = cudaStreamWaitEvent(s, ev_update, 0);
       } else {
         if (nrows > 0) {
